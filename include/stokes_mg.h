@@ -1,0 +1,163 @@
+/*
+ * stokes_mg.h -- C-ABI of the GB300 coupled multigrid solver for the generalized Stokes system
+ *
+ *     -Lap u + beta u + grad p = f,   div u = g   in (0,1)^2,   u = 0 on the boundary,  int p = 0
+ *
+ * (Takacs, "A robust multigrid method for the time-dependent Stokes problem", SINUM 53(6), 2015:
+ * problem statement Sec. 1, eq. stokes; variational form Sec. 2, eq. gen:bil; matrix form
+ * eq. gen:bil:mv).  Discretisation: Taylor-Hood P2 velocity / P1 pressure on the unit square split
+ * into 8 triangles around its centre (level 0) and refined uniformly k times (Sec. 5), so level k
+ * has N = 2^(k+1) element legs per side.
+ *
+ * DATA LAYOUT (all arrays are caller-owned DEVICE memory of the current CUDA device, float64,
+ * dense, row-major with y outer and x inner):
+ *   u : 2 x (2N+1) x (2N+1)   velocity nodal values on the P2 lattice (spacing 1/(2N)),
+ *                             component x first.  Boundary lattice points hold 0 on output and
+ *                             are ignored (treated as 0) on input.
+ *   p : (N+1) x (N+1)         pressure nodal values at the vertices (spacing 1/N).  The paper's
+ *                             weak form carries +(p, div v) (Sec. 2), so p approximates -p of the
+ *                             strong form written in Sec. 1.  Returned with zero mean int p = 0.
+ *   f : 2 x (2N+1) x (2N+1)   the velocity right-hand side as a LOAD VECTOR (f, phi_i) (the
+ *                             underlined f_k of eq. gen:bil:mv); boundary entries ignored.
+ *   g : (N+1) x (N+1)         the pressure load vector (g, psi_i); its entries must sum to 0
+ *                             (solvability, Sec. 1); stokes_load_vectors() produces such g.
+ * Use stokes_load_vectors() to turn nodal values of f, g into load vectors.
+ *
+ * STREAMS: every call is asynchronous on the stream given to stokes_setup() unless it returns a
+ * host-side result (stokes_solve, stokes_residual_norm), which synchronises that stream.
+ *
+ * ERRORS: every call returns a stokes_status; no call aborts or exits the process.  After
+ * STOKES_ERR_CUDA the handle should be destroyed.
+ */
+#ifndef STOKES_MG_H
+#define STOKES_MG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum stokes_status {
+    STOKES_OK = 0,
+    STOKES_ERR_BAD_ARG = 1,      /* null pointer, levels out of range, beta < 0 or NaN, ... */
+    STOKES_ERR_OOM = 2,          /* device allocation failed */
+    STOKES_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+    STOKES_NOT_CONVERGED = 4,    /* solve reached max_cycles above tol (result still returned) */
+    STOKES_DIVERGED = 5,         /* residual became NaN/Inf or grew 1e3-fold over the initial one */
+    STOKES_ERR_TIMEOUT = 6       /* a bounded device-side wait gave up (batched persistent kernel) */
+} stokes_status;
+
+typedef enum stokes_smoother {
+    STOKES_UZAWA = 0,            /* Uzawa-type smoother, Sec. 4 (default, tau = sigma = 0.8) */
+    STOKES_NORMAL_EQ = 1         /* preconditioned normal-equation smoother, Sec. 4 (tau = 0.35) */
+} stokes_smoother;
+
+typedef enum stokes_precision {
+    STOKES_FP64 = 0,             /* every level and every step in float64 */
+    STOKES_MIXED = 1             /* float32 cycles inside float64 iterative refinement */
+} stokes_precision;
+
+typedef struct stokes_params {
+    int levels;        /* number of grid levels; the finest is k = levels-1; 1 <= levels <= 13 */
+    double beta;       /* >= 0 (Sec. 1 assumes beta > 0; beta = 0 is the stationary Stokes case) */
+    int nu_pre;        /* pre-smoothing steps  (Sec. 5 uses 3) */
+    int nu_post;       /* post-smoothing steps (Sec. 5 uses 3) */
+    double tau;        /* smoother damping tau   (Sec. 5: 0.8 Uzawa, 0.35 normal equation) */
+    double sigma;      /* Uzawa pressure damping (Sec. 5: 0.8) */
+    int smoother;      /* stokes_smoother */
+    int gamma;         /* 1 = V-cycle, 2 = W-cycle (Sec. 3) */
+    int precision;     /* stokes_precision */
+    int inner_cycles;  /* STOKES_MIXED: float32 cycles per refinement step (>= 1) */
+} stokes_params;
+
+/* Paper defaults: Uzawa, nu = 3+3, tau = sigma = 0.8, V-cycle, float64, one inner cycle. */
+void stokes_default_params(stokes_params* prm, int levels, double beta);
+
+typedef struct stokes_handle_t stokes_handle;
+
+typedef struct stokes_report {
+    int cycles;              /* cycles (FP64) or refinement steps (MIXED) performed */
+    double rel_residual;     /* final ||F - A x||_2 / ||F||_2 over the unknowns (float64) */
+    double mean_rate;        /* geometric mean of the per-cycle residual reduction (Sec. 5 q) */
+    double initial_residual; /* ||F - A x0||_2 */
+    double rhs_norm;         /* ||F||_2 */
+} stokes_report;
+
+/* Builds the level hierarchy (Sec. 2 nesting), the per-level diagonals Ahat = diag A_k and
+ * Shat = diag(B_k Ahat^{-1} B_k^T) (Sec. 5, eq. numintroduc) and the level-0 factorisation
+ * (Sec. 3: exact coarsest solve).  `stream` is a cudaStream_t (NULL = legacy default stream).
+ * The library owns the handle and all internal buffers (cudaMalloc); free with stokes_destroy. */
+stokes_status stokes_setup(const stokes_params* prm, void* stream, stokes_handle** out);
+
+/* Changes beta: rebuilds the diagonals and the coarse factorisation only. */
+stokes_status stokes_set_beta(stokes_handle* h, double beta);
+
+void stokes_destroy(stokes_handle* h);
+
+const char* stokes_status_str(stokes_status s);
+
+/* N and array lengths of the finest level: n_vel = 2 (2N+1)^2, n_p = (N+1)^2, ndof = number of
+ * unknowns 2 (2N-1)^2 + (N+1)^2. */
+stokes_status stokes_sizes(const stokes_handle* h, int* N, size_t* n_vel, size_t* n_p, size_t* ndof);
+
+/* One multigrid iteration on the finest level (Sec. 3; V or W by params.gamma), in place on
+ * (u, p), followed by the zero-mean projection of p.  Under STOKES_MIXED it is one refinement
+ * step: float64 residual, params.inner_cycles float32 cycles on the correction, float64 update. */
+stokes_status stokes_cycle(stokes_handle* h, double* u, double* p, const double* f, const double* g);
+
+/* Iterates stokes_cycle from the given (u, p) until ||F - A x||_2 <= tol ||F||_2 or max_cycles.
+ * Returns STOKES_OK, STOKES_NOT_CONVERGED or STOKES_DIVERGED; `rep` (caller-owned, may be NULL)
+ * receives the statistics; `history` (caller-owned host array of max_cycles+1 doubles, may be
+ * NULL) receives the residual norm before the first and after every cycle. */
+stokes_status stokes_solve(stokes_handle* h, double* u, double* p, const double* f, const double* g,
+                           double tol, int max_cycles, stokes_report* rep, double* history);
+
+/* r = F - A x on the finest level (eq. gen:bil:mv), float64; ru / rp have the layouts of u / p
+ * (boundary entries of ru set to 0).  Asynchronous. */
+stokes_status stokes_residual(stokes_handle* h, const double* u, const double* p, const double* f,
+                              const double* g, double* ru, double* rp);
+
+/* ||F - A x||_2 over the unknowns, float64; synchronises the stream. */
+stokes_status stokes_residual_norm(stokes_handle* h, const double* u, const double* p, const double* f,
+                                   const double* g, double* norm);
+
+/* nu steps of the configured smoother (Sec. 4) on the finest level, in place on (u, p), with the
+ * float64 arithmetic of the FP64 path.  Exposed for verification of the smoother alone. */
+stokes_status stokes_smooth(stokes_handle* h, double* u, double* p, const double* f, const double* g, int nu);
+
+/* Canonical transfers (Sec. 3) between finest level k and level k-1 (requires levels >= 2):
+ * restriction  (fc, gc) = I_k^{k-1} (fu, fp)   with coarse layouts of level k-1,
+ * prolongation (uf, pf) += I_{k-1}^k (uc, pc). */
+stokes_status stokes_restrict(stokes_handle* h, const double* fu, const double* fp, double* fc, double* gc);
+stokes_status stokes_prolong_add(stokes_handle* h, const double* uc, const double* pc, double* uf, double* pf);
+
+/* Load vectors of nodal data: f = (f_h, phi_i) on interior P2 nodes (the P2 interpolant f_h of the
+ * nodal values on the FULL lattice, boundary values included) and g = (g_h, psi_i) on all
+ * vertices.  With project_g != 0 the P1 function g_h is first shifted to zero mean
+ * (g_h <- g_h - int g_h), the solvability condition of Sec. 1. */
+stokes_status stokes_load_vectors(stokes_handle* h, const double* f_nodal, const double* g_nodal,
+                                  int project_g, double* f, double* g);
+
+/* dot = a^T M_U b for two velocity arrays a, b (layout of u, boundary entries ignored), where M_U
+ * is the velocity mass matrix (the beta-part of A_k = K + beta M_U, Sec. 2); float64, synchronises
+ * the stream.  Gives the beta-derivative of a loss through the adjoint: dL/dbeta = -lambda_u^T M_U u. */
+stokes_status stokes_mass_dot(stokes_handle* h, const double* a, const double* b, double* dot);
+
+/* Timing of the hot kernels inside the captured cycle: with enable != 0, the cycle graph is
+ * rebuilt with CUDA event records (cudaEventRecordExternal) around every finest-level smoothing
+ * step and around the float64 finest-level residual, and stokes_solve accumulates their durations
+ * (milliseconds, counts) until the next stokes_set_timing call, which also resets the totals. */
+stokes_status stokes_set_timing(stokes_handle* h, int enable);
+stokes_status stokes_get_timing(const stokes_handle* h, double* smooth_ms, long long* smooth_count,
+                                double* resid_ms, long long* resid_count);
+
+/* Number of CUDA kernels this handle has launched so far (kernel nodes of replayed graphs
+ * included); for accounting in benchmarks. */
+unsigned long long stokes_kernel_launches(const stokes_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

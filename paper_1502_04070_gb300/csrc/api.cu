@@ -1,0 +1,614 @@
+// api.cu -- the C-ABI of include/stokes_mg.h: level hierarchy, cycle orchestration, solve loop.
+//
+// The multigrid iteration is the one of Sec. 3: nu_pre smoothing steps, restriction of the defect
+// with the transposed embedding, gamma recursive iterations on the coarser level from zero (an exact
+// solve on level 0), prolongation and correction, nu_post smoothing steps.  The whole iteration,
+// the zero-mean pressure projection and the residual norm are captured once into a CUDA graph and
+// replayed per cycle; the host reads one scalar per cycle to test convergence.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "../../include/stokes_mg.h"
+#include "elements.h"
+#include "kernels.cuh"
+
+using namespace smg;
+
+namespace {
+
+#define CK(call)                                   \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) return fail(e_);    \
+    } while (0)
+
+stokes_status fail(cudaError_t e) {
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return STOKES_ERR_OOM;
+    }
+    return STOKES_ERR_CUDA;
+}
+
+template <typename T>
+struct Level {
+    int n = 0;
+    size_t n2 = 0, n1 = 0;   // (2n+1)^2 and (n+1)^2
+    T *u = nullptr, *p = nullptr, *f = nullptr, *g = nullptr;
+    T *tu = nullptr, *tp = nullptr, *sinv = nullptr;
+    void* slab = nullptr;
+    OpCoef<T> c{};
+};
+
+template <typename T>
+stokes_status alloc_level(Level<T>& L, int k) {
+    L.n = 1 << (k + 1);
+    L.n2 = (size_t)(2 * L.n + 1) * (2 * L.n + 1);
+    L.n1 = (size_t)(L.n + 1) * (L.n + 1);
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t bu = al(2 * L.n2 * sizeof(T)), bp = al(L.n1 * sizeof(T));
+    const size_t total = 3 * bu + 4 * bp;
+    CK(cudaMalloc(&L.slab, total));
+    char* q = (char*)L.slab;
+    L.u = (T*)q; q += bu;
+    L.f = (T*)q; q += bu;
+    L.tu = (T*)q; q += bu;
+    L.p = (T*)q; q += bp;
+    L.g = (T*)q; q += bp;
+    L.tp = (T*)q; q += bp;
+    L.sinv = (T*)q;
+    CK(cudaMemset(L.slab, 0, total));
+    return STOKES_OK;
+}
+
+template <typename T>
+void free_level(Level<T>& L) {
+    if (L.slab) cudaFree(L.slab);
+    L.slab = nullptr;
+}
+
+const SquareMatrices& squares() {
+    static SquareMatrices S = square_matrices();
+    return S;
+}
+
+template <typename T>
+OpCoef<T> make_coef(int n, double beta) {
+    const SquareMatrices& S = squares();
+    const double h = 1.0 / n;
+    OpCoef<T> c;
+    for (int o = 0; o < 2; ++o) {
+        for (int l = 0; l < 9; ++l)
+            for (int m = 0; m < 9; ++m) c.A[o][l][m] = (T)(S.K[o][l][m] + beta * h * h * S.M[o][l][m]);
+        for (int q = 0; q < 4; ++q)
+            for (int m = 0; m < 9; ++m) {
+                c.Bx[o][q][m] = (T)(h * S.Bx[o][q][m]);
+                c.By[o][q][m] = (T)(h * S.By[o][q][m]);
+            }
+    }
+    return c;
+}
+
+template <typename T>
+MassCoef<T> make_mass(int n) {
+    const SquareMatrices& S = squares();
+    const double h = 1.0 / n;
+    MassCoef<T> m;
+    for (int o = 0; o < 2; ++o) {
+        for (int l = 0; l < 9; ++l)
+            for (int k = 0; k < 9; ++k) m.M[o][l][k] = (T)(h * h * S.M[o][l][k]);
+        for (int q = 0; q < 4; ++q)
+            for (int r = 0; r < 4; ++r) m.MP[o][q][r] = (T)(h * h * S.MP[o][q][r]);
+    }
+    return m;
+}
+
+std::mutex g_dev_mu;
+unsigned long long g_dev_weights = 0;   // devices whose constant transfer table is set
+
+stokes_status ensure_weights() {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    if (dev < 64 && (g_dev_weights >> dev) & 1ull) return STOKES_OK;
+    static TransferWeights W = transfer_weights();
+    CK(upload_transfer_weights(&W.P2[0][0][0][0]));
+    if (dev < 64) g_dev_weights |= 1ull << dev;
+    return STOKES_OK;
+}
+
+}  // namespace
+
+struct stokes_handle_t {
+    stokes_params prm{};
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    int L = 0;                              // number of levels
+    std::vector<Level<double>> h64;         // FP64: all levels; MIXED: finest only
+    std::vector<Level<float>> h32;          // MIXED: all levels
+    double* inv = nullptr;                  // level-0 bordered inverse (27 x 27)
+    double* partial = nullptr;
+    int npartial = 0;
+    double* scal = nullptr;                 // device scalars
+    double* hscal = nullptr;                // pinned host mirror
+    MassCoef<double> mass{};
+    cudaGraphExec_t step = nullptr;         // one cycle + projection + residual norm
+    int step_kernels = 0;                   // kernel nodes in `step`
+    unsigned long long launches = 0;        // kernels launched by this handle (graph nodes included)
+    // optional timing of the finest-level smoothing steps and of the float64 residual: event
+    // pairs recorded inside the captured graph (cudaEventRecordExternal)
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;            // pairs: [2i] start, [2i+1] end
+    int ev_smooth = 0, ev_resid = 0;        // pairs used by one graph launch
+    int ev_cursor = 0;                      // pair index while capturing
+    double t_smooth = 0.0, t_resid = 0.0;   // accumulated milliseconds
+    long long n_smooth = 0, n_resid = 0;    // accumulated launches (groups)
+
+    Level<double>& fin() { return h64.back(); }
+    bool mixed() const { return prm.precision == STOKES_MIXED; }
+};
+
+namespace {
+
+int ev_begin(stokes_handle* h) {
+    if (!h->timing || h->ev_cursor * 2 + 1 >= (int)h->ev.size()) return -1;
+    const int k = h->ev_cursor++;
+    cudaEventRecordWithFlags(h->ev[2 * k], h->st, cudaEventRecordExternal);
+    return k;
+}
+void ev_end(stokes_handle* h, int k) {
+    if (k >= 0) cudaEventRecordWithFlags(h->ev[2 * k + 1], h->st, cudaEventRecordExternal);
+}
+
+template <typename T>
+void smooth_level(stokes_handle* h, Level<T>& lv, int steps, bool timed = false) {
+    const stokes_params& P = h->prm;
+    for (int s = 0; s < steps; ++s) {
+        const int k = timed ? ev_begin(h) : -1;
+        if (k >= 0) h->ev_smooth++;
+        if (P.smoother == STOKES_NORMAL_EQ)
+            launch_normal_eq<T>(h->st, lv.n, lv.c, (T)P.tau, lv.u, lv.p, lv.f, lv.g, lv.sinv, lv.tu, lv.tp);
+        else
+            launch_uzawa<T>(h->st, lv.n, lv.c, (T)P.tau, (T)P.sigma, lv.u, lv.p, lv.f, lv.g, lv.sinv, lv.tu, lv.tp);
+        ev_end(h, k);
+    }
+}
+
+// Sec. 3: one multigrid iteration on level l of hierarchy H (x = (u, p), F = (f, g) of the level)
+template <typename T>
+void mg_cycle(stokes_handle* h, std::vector<Level<T>>& H, int l) {
+    Level<T>& lv = H[l];
+    if (l == 0) {
+        launch_coarse_solve<T>(h->st, h->inv, lv.f, lv.g, lv.u, lv.p);
+        return;
+    }
+    const bool top = l == (int)H.size() - 1;
+    smooth_level(h, lv, h->prm.nu_pre, top);
+    Level<T>& cl = H[l - 1];
+    launch_residual<T, T>(h->st, lv.n, lv.c, lv.u, lv.p, lv.f, lv.g, lv.tu, lv.tp, nullptr);
+    launch_restrict<T>(h->st, cl.n, lv.tu, lv.tp, cl.f, cl.g);
+    cudaMemsetAsync(cl.u, 0, 2 * cl.n2 * sizeof(T), h->st);
+    cudaMemsetAsync(cl.p, 0, cl.n1 * sizeof(T), h->st);
+    for (int r = 0; r < h->prm.gamma; ++r) mg_cycle(h, H, l - 1);
+    launch_prolong_add<T>(h->st, cl.n, cl.u, cl.p, lv.u, lv.p);
+    smooth_level(h, lv, h->prm.nu_post, top);
+}
+
+// residual norm^2 of the finest FP64 state into scal[0]; in MIXED mode the residual is also the
+// float32 right-hand side of the next correction problem
+void residual_norm_fin(stokes_handle* h, bool timed = false) {
+    Level<double>& F = h->fin();
+    const int k = timed ? ev_begin(h) : -1;
+    if (k >= 0) h->ev_resid++;
+    if (h->mixed()) {
+        Level<float>& E = h->h32.back();
+        launch_residual<double, float>(h->st, F.n, F.c, F.u, F.p, F.f, F.g, E.f, E.g, h->partial);
+    } else {
+        launch_residual<double, double>(h->st, F.n, F.c, F.u, F.p, F.f, F.g, F.tu, F.tp, h->partial);
+    }
+    ev_end(h, k);
+    launch_reduce(h->st, h->partial, cells_blocks(F.n), h->scal);
+}
+
+// One outer iteration on the internal finest state, ending with ||F - A x||^2 in scal[0].
+void record_step(stokes_handle* h) {
+    Level<double>& F = h->fin();
+    if (h->mixed()) {
+        Level<float>& E = h->h32.back();
+        cudaMemsetAsync(E.u, 0, 2 * E.n2 * sizeof(float), h->st);
+        cudaMemsetAsync(E.p, 0, E.n1 * sizeof(float), h->st);
+        for (int c = 0; c < h->prm.inner_cycles; ++c) mg_cycle<float>(h, h->h32, h->L - 1);
+        launch_add_f32(h->st, 2 * F.n2, E.u, F.u);
+        launch_add_f32(h->st, F.n1, E.p, F.p);
+    } else {
+        mg_cycle<double>(h, h->h64, h->L - 1);
+    }
+    launch_pmean<double>(h->st, F.n, F.p, h->partial, h->scal + 1);
+    residual_norm_fin(h, true);
+}
+
+stokes_status build_graph(stokes_handle* h) {
+    if (h->step) return STOKES_OK;
+    cudaGraph_t g = nullptr;
+    h->ev_cursor = h->ev_smooth = h->ev_resid = 0;
+    CK(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
+    record_step(h);
+    cudaError_t e = cudaStreamEndCapture(h->st, &g);
+    if (e != cudaSuccess) return fail(e);
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    cudaGraphGetNodes(g, nodes.data(), &nn);
+    h->step_kernels = 0;
+    for (auto nd : nodes) {
+        cudaGraphNodeType ty;
+        if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) h->step_kernels++;
+    }
+    e = cudaGraphInstantiate(&h->step, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        h->step = nullptr;
+        return fail(e);
+    }
+    return STOKES_OK;
+}
+
+stokes_status launch_step(stokes_handle* h) {
+    CK(cudaGraphLaunch(h->step, h->st));
+    h->launches += h->step_kernels;
+    return STOKES_OK;
+}
+
+// after the stream is synchronised: add the event intervals of the last graph launch
+void collect_timing(stokes_handle* h) {
+    if (!h->timing) return;
+    int k = 0;
+    for (int i = 0; i < h->ev_smooth + h->ev_resid; ++i, ++k) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->ev[2 * k], h->ev[2 * k + 1]) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        // capture order: smoothing steps of the cycle first, the residual last
+        if (i < h->ev_smooth) {
+            h->t_smooth += ms;
+            h->n_smooth++;
+        } else {
+            h->t_resid += ms;
+            h->n_resid++;
+        }
+    }
+}
+
+stokes_status rebuild_beta(stokes_handle* h) {
+    const double beta = h->prm.beta;
+    for (auto& lv : h->h64) {
+        lv.c = make_coef<double>(lv.n, beta);
+        launch_schur_diag<double>(h->st, lv.n, lv.c, lv.sinv);
+    }
+    for (auto& lv : h->h32) {
+        lv.c = make_coef<float>(lv.n, beta);
+        launch_schur_diag<float>(h->st, lv.n, make_coef<double>(lv.n, beta), lv.sinv);
+    }
+    CK(cudaGetLastError());
+    double inv[27 * 27];
+    if (!coarse_inverse(squares(), beta, inv)) return STOKES_ERR_BAD_ARG;
+    CK(cudaMemcpyAsync(h->inv, inv, sizeof(inv), cudaMemcpyHostToDevice, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    if (h->step) {
+        cudaGraphExecDestroy(h->step);
+        h->step = nullptr;
+    }
+    return STOKES_OK;
+}
+
+stokes_status copy_in(stokes_handle* h, const double* u, const double* p, const double* f, const double* g) {
+    Level<double>& F = h->fin();
+    CK(cudaMemcpyAsync(F.u, u, 2 * F.n2 * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(F.p, p, F.n1 * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(F.f, f, 2 * F.n2 * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(F.g, g, F.n1 * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    return STOKES_OK;
+}
+
+stokes_status copy_out(stokes_handle* h, double* u, double* p) {
+    Level<double>& F = h->fin();
+    CK(cudaMemcpyAsync(u, F.u, 2 * F.n2 * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(p, F.p, F.n1 * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    return STOKES_OK;
+}
+
+stokes_status read_scalar(stokes_handle* h, int idx, double* out) {
+    CK(cudaMemcpyAsync(h->hscal + idx, h->scal + idx, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    *out = h->hscal[idx];
+    return STOKES_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void stokes_default_params(stokes_params* prm, int levels, double beta) {
+    if (!prm) return;
+    std::memset(prm, 0, sizeof(*prm));
+    prm->levels = levels;
+    prm->beta = beta;
+    prm->nu_pre = 3;
+    prm->nu_post = 3;
+    prm->tau = 0.8;
+    prm->sigma = 0.8;
+    prm->smoother = STOKES_UZAWA;
+    prm->gamma = 1;
+    prm->precision = STOKES_FP64;
+    prm->inner_cycles = 1;
+}
+
+const char* stokes_status_str(stokes_status s) {
+    switch (s) {
+        case STOKES_OK: return "ok";
+        case STOKES_ERR_BAD_ARG: return "bad argument";
+        case STOKES_ERR_OOM: return "out of device memory";
+        case STOKES_ERR_CUDA: return "CUDA error";
+        case STOKES_NOT_CONVERGED: return "not converged";
+        case STOKES_DIVERGED: return "diverged";
+        case STOKES_ERR_TIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+void stokes_destroy(stokes_handle* h) {
+    if (!h) return;
+    if (h->st) cudaStreamSynchronize(h->st);
+    if (h->step) cudaGraphExecDestroy(h->step);
+    for (auto e : h->ev) cudaEventDestroy(e);
+    for (auto& l : h->h64) free_level(l);
+    for (auto& l : h->h32) free_level(l);
+    if (h->inv) cudaFree(h->inv);
+    if (h->partial) cudaFree(h->partial);
+    if (h->scal) cudaFree(h->scal);
+    if (h->hscal) cudaFreeHost(h->hscal);
+    if (h->own_stream && h->st) cudaStreamDestroy(h->st);
+    delete h;
+}
+
+stokes_status stokes_setup(const stokes_params* prm, void* stream, stokes_handle** out) {
+    if (!prm || !out) return STOKES_ERR_BAD_ARG;
+    *out = nullptr;
+    const stokes_params& P = *prm;
+    if (P.levels < 1 || P.levels > 13 || !(P.beta >= 0.0) || !std::isfinite(P.beta) || P.nu_pre < 0 ||
+        P.nu_post < 0 || !(P.tau > 0.0) || !(P.sigma > 0.0) || (P.gamma != 1 && P.gamma != 2) ||
+        (P.smoother != STOKES_UZAWA && P.smoother != STOKES_NORMAL_EQ) ||
+        (P.precision != STOKES_FP64 && P.precision != STOKES_MIXED) ||
+        (P.precision == STOKES_MIXED && P.inner_cycles < 1))
+        return STOKES_ERR_BAD_ARG;
+    stokes_status s = ensure_weights();
+    if (s != STOKES_OK) return s;
+    stokes_handle* h = new stokes_handle_t();
+    h->prm = P;
+    h->L = P.levels;
+    if (stream) {
+        h->st = (cudaStream_t)stream;
+    } else {
+        // a blocking stream: implicitly ordered with the legacy default stream, but capturable
+        if (cudaStreamCreate(&h->st) != cudaSuccess) {
+            delete h;
+            return STOKES_ERR_CUDA;
+        }
+        h->own_stream = true;
+    }
+    auto bail = [&](stokes_status e) {
+        stokes_destroy(h);
+        return e;
+    };
+    const int kfin = P.levels - 1;
+    if (P.precision == STOKES_FP64) {
+        h->h64.resize(P.levels);
+        for (int k = 0; k < P.levels; ++k)
+            if ((s = alloc_level(h->h64[k], k)) != STOKES_OK) return bail(s);
+    } else {
+        h->h64.resize(1);
+        if ((s = alloc_level(h->h64[0], kfin)) != STOKES_OK) return bail(s);
+        h->h32.resize(P.levels);
+        for (int k = 0; k < P.levels; ++k)
+            if ((s = alloc_level(h->h32[k], k)) != STOKES_OK) return bail(s);
+    }
+    h->mass = make_mass<double>(h->fin().n);
+    h->npartial = cells_blocks(h->fin().n);
+    if (cudaMalloc(&h->inv, 27 * 27 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&h->partial, (size_t)h->npartial * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&h->scal, 8 * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&h->hscal, 8 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(STOKES_ERR_OOM);
+    }
+    if ((s = rebuild_beta(h)) != STOKES_OK) return bail(s);
+    *out = h;
+    return STOKES_OK;
+}
+
+stokes_status stokes_set_beta(stokes_handle* h, double beta) {
+    if (!h || !(beta >= 0.0) || !std::isfinite(beta)) return STOKES_ERR_BAD_ARG;
+    h->prm.beta = beta;
+    return rebuild_beta(h);
+}
+
+stokes_status stokes_sizes(const stokes_handle* h, int* N, size_t* n_vel, size_t* n_p, size_t* ndof) {
+    if (!h) return STOKES_ERR_BAD_ARG;
+    const int n = 1 << h->L;
+    if (N) *N = n;
+    if (n_vel) *n_vel = 2 * (size_t)(2 * n + 1) * (2 * n + 1);
+    if (n_p) *n_p = (size_t)(n + 1) * (n + 1);
+    if (ndof) *ndof = 2 * (size_t)(2 * n - 1) * (2 * n - 1) + (size_t)(n + 1) * (n + 1);
+    return STOKES_OK;
+}
+
+stokes_status stokes_cycle(stokes_handle* h, double* u, double* p, const double* f, const double* g) {
+    if (!h || !u || !p || !f || !g) return STOKES_ERR_BAD_ARG;
+    stokes_status s;
+    if ((s = copy_in(h, u, p, f, g)) != STOKES_OK) return s;
+    if (h->mixed()) {
+        residual_norm_fin(h);   // right-hand side of the float32 correction problem
+        h->launches += 2;
+    }
+    if ((s = build_graph(h)) != STOKES_OK) return s;
+    stokes_status s2 = launch_step(h);
+    if (s2 != STOKES_OK) return s2;
+    return copy_out(h, u, p);
+}
+
+stokes_status stokes_solve(stokes_handle* h, double* u, double* p, const double* f, const double* g,
+                           double tol, int max_cycles, stokes_report* rep, double* history) {
+    if (!h || !u || !p || !f || !g || max_cycles < 0 || !(tol >= 0.0)) return STOKES_ERR_BAD_ARG;
+    stokes_status s;
+    if ((s = copy_in(h, u, p, f, g)) != STOKES_OK) return s;
+    if ((s = build_graph(h)) != STOKES_OK) return s;
+    Level<double>& F = h->fin();
+    double nF2 = 0.0;
+    launch_rhs_norm(h->st, F.n, F.f, F.g, h->partial);
+    launch_reduce(h->st, h->partial, cells_blocks(F.n), h->scal + 2);
+    h->launches += 2;
+    if ((s = read_scalar(h, 2, &nF2)) != STOKES_OK) return s;
+    const double nF = std::sqrt(nF2);
+    residual_norm_fin(h);
+    h->launches += 2;
+    double r2 = 0.0;
+    if ((s = read_scalar(h, 0, &r2)) != STOKES_OK) return s;
+    double r0 = std::sqrt(r2), r = r0;
+    if (history) history[0] = r0;
+    int cycles = 0;
+    stokes_status result = STOKES_OK;
+    while (!(r <= tol * nF)) {
+        if (!std::isfinite(r) || r > 1e3 * (r0 > 0 ? r0 : 1.0)) {
+            result = STOKES_DIVERGED;
+            break;
+        }
+        if (cycles >= max_cycles) {
+            result = STOKES_NOT_CONVERGED;
+            break;
+        }
+        if ((s = launch_step(h)) != STOKES_OK) return s;
+        if ((s = read_scalar(h, 0, &r2)) != STOKES_OK) return s;
+        collect_timing(h);
+        r = std::sqrt(r2);
+        ++cycles;
+        if (history) history[cycles] = r;
+    }
+    if ((s = copy_out(h, u, p)) != STOKES_OK) return s;
+    CK(cudaStreamSynchronize(h->st));
+    if (rep) {
+        rep->cycles = cycles;
+        rep->rhs_norm = nF;
+        rep->initial_residual = r0;
+        rep->rel_residual = nF > 0 ? r / nF : r;
+        rep->mean_rate = cycles > 0 && r0 > 0 ? std::pow(r / r0, 1.0 / cycles) : 0.0;
+    }
+    return result;
+}
+
+stokes_status stokes_residual(stokes_handle* h, const double* u, const double* p, const double* f,
+                              const double* g, double* ru, double* rp) {
+    if (!h || !u || !p || !f || !g || !ru || !rp) return STOKES_ERR_BAD_ARG;
+    Level<double>& F = h->fin();
+    launch_residual<double, double>(h->st, F.n, F.c, u, p, f, g, ru, rp, nullptr);
+    h->launches += 1;
+    CK(cudaGetLastError());
+    return STOKES_OK;
+}
+
+stokes_status stokes_residual_norm(stokes_handle* h, const double* u, const double* p, const double* f,
+                                   const double* g, double* norm) {
+    if (!h || !u || !p || !f || !g || !norm) return STOKES_ERR_BAD_ARG;
+    Level<double>& F = h->fin();
+    launch_residual<double, double>(h->st, F.n, F.c, u, p, f, g, F.tu, F.tp, h->partial);
+    launch_reduce(h->st, h->partial, cells_blocks(F.n), h->scal + 3);
+    h->launches += 2;
+    double v;
+    stokes_status s = read_scalar(h, 3, &v);
+    if (s != STOKES_OK) return s;
+    *norm = std::sqrt(v);
+    return STOKES_OK;
+}
+
+stokes_status stokes_smooth(stokes_handle* h, double* u, double* p, const double* f, const double* g, int nu) {
+    if (!h || !u || !p || !f || !g || nu < 0) return STOKES_ERR_BAD_ARG;
+    Level<double> lv = h->fin();   // coefficients, diagonals and temporaries of the finest level
+    lv.u = u;
+    lv.p = p;
+    lv.f = const_cast<double*>(f);
+    lv.g = const_cast<double*>(g);
+    smooth_level<double>(h, lv, nu);
+    h->launches += 3ull * nu;
+    CK(cudaGetLastError());
+    return STOKES_OK;
+}
+
+stokes_status stokes_restrict(stokes_handle* h, const double* fu, const double* fp, double* fc, double* gc) {
+    if (!h || !fu || !fp || !fc || !gc || h->L < 2) return STOKES_ERR_BAD_ARG;
+    launch_restrict<double>(h->st, h->fin().n / 2, fu, fp, fc, gc);
+    h->launches += 1;
+    CK(cudaGetLastError());
+    return STOKES_OK;
+}
+
+stokes_status stokes_prolong_add(stokes_handle* h, const double* uc, const double* pc, double* uf, double* pf) {
+    if (!h || !uc || !pc || !uf || !pf || h->L < 2) return STOKES_ERR_BAD_ARG;
+    launch_prolong_add<double>(h->st, h->fin().n / 2, uc, pc, uf, pf);
+    h->launches += 1;
+    CK(cudaGetLastError());
+    return STOKES_OK;
+}
+
+stokes_status stokes_load_vectors(stokes_handle* h, const double* f_nodal, const double* g_nodal, int project_g,
+                                  double* f, double* g) {
+    if (!h || !f_nodal || !g_nodal || !f || !g) return STOKES_ERR_BAD_ARG;
+    launch_load<double>(h->st, h->fin().n, h->mass, f_nodal, g_nodal, f, g, project_g, h->partial, h->scal + 4);
+    h->launches += project_g ? 3 : 1;
+    CK(cudaGetLastError());
+    return STOKES_OK;
+}
+
+stokes_status stokes_mass_dot(stokes_handle* h, const double* a, const double* b, double* dot) {
+    if (!h || !a || !b || !dot) return STOKES_ERR_BAD_ARG;
+    const int n = h->fin().n;
+    launch_mass_dot(h->st, n, h->mass, a, b, h->partial);
+    launch_reduce(h->st, h->partial, cells_blocks(n), h->scal + 5);
+    h->launches += 2;
+    return read_scalar(h, 5, dot);
+}
+
+stokes_status stokes_set_timing(stokes_handle* h, int enable) {
+    if (!h) return STOKES_ERR_BAD_ARG;
+    const bool on = enable != 0;
+    if (on && h->ev.empty()) {
+        const int pairs = (h->prm.nu_pre + h->prm.nu_post) * (h->mixed() ? h->prm.inner_cycles : 1) + 1;
+        h->ev.resize(2 * pairs);
+        for (auto& e : h->ev) CK(cudaEventCreate(&e));
+    }
+    if (on != h->timing && h->step) {
+        cudaGraphExecDestroy(h->step);
+        h->step = nullptr;
+    }
+    h->timing = on;
+    h->t_smooth = h->t_resid = 0.0;
+    h->n_smooth = h->n_resid = 0;
+    return STOKES_OK;
+}
+
+stokes_status stokes_get_timing(const stokes_handle* h, double* smooth_ms, long long* smooth_count,
+                                double* resid_ms, long long* resid_count) {
+    if (!h) return STOKES_ERR_BAD_ARG;
+    if (smooth_ms) *smooth_ms = h->t_smooth;
+    if (smooth_count) *smooth_count = h->n_smooth;
+    if (resid_ms) *resid_ms = h->t_resid;
+    if (resid_count) *resid_count = h->n_resid;
+    return STOKES_OK;
+}
+
+unsigned long long stokes_kernel_launches(const stokes_handle* h) { return h ? h->launches : 0ull; }
+
+}  // extern "C"

@@ -1,0 +1,129 @@
+// common.cuh -- data structures and device helpers shared by the solver's kernels.
+//
+// Geometry (Sec. 5): level k of the unit square has N = 2^(k+1) squares per side; square (si, sj)
+// covers [si/N, (si+1)/N] x [sj/N, (sj+1)/N] and is cut by one diagonal.  Refining the 8-triangle
+// coarse mesh (the fan around the centre) keeps the diagonal direction of each quadrant:
+//     orientation 0 ("/", from (0,0) to (1,1) of the square) in the SW and NE quadrants,
+//     orientation 1 ("\", from (1,0) to (0,1))                in the SE and NW quadrants.
+// A square carries 9 P2 nodes (local index m = 3*b + a at P2-lattice point (2si+a, 2sj+b)) and
+// 4 P1 vertices (local q = 2*b' + a' at vertex (si+a', sj+b')).
+//
+// The operator of eq. gen:bil:mv is applied element-by-element per square ("matrix free"):
+// a velocity row of A_k (= K + beta M_U, Sec. 2) is the sum, over the 1, 2 or 4 squares that
+// contain the node, of one row of the square's 9x9 local matrix; likewise for B_k (4x9 per
+// component) and B_k^T.  The local matrices are assembled on the host from exact P2/P1 element
+// integrals and passed to kernels by value (constant bank).
+//
+// A thread "owns" cell (i, j), i, j in [0, N]: the vertex node V = (2i, 2j), the horizontal-edge
+// node H = (2i+1, 2j), the vertical-edge node E = (2i, 2j+1), the centre node C = (2i+1, 2j+1)
+// and the pressure vertex (i, j).  Nodes that fall outside the lattice do not exist.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace smg {
+
+template <typename T>
+struct OpCoef {            // local square matrices of one level
+    T A[2][9][9];          // K + beta h^2 Mhat        (h-independent stiffness, mass ~ h^2)
+    T Bx[2][4][9];         // (d phi_m / dx, psi_q)    (~ h)
+    T By[2][4][9];
+};
+
+template <typename T>
+struct MassCoef {          // mass matrices of one level (load vectors, adjoint)
+    T M[2][9][9];
+    T MP[2][4][4];
+};
+
+// triangle membership of local P2 nodes, per orientation (bit m set if node m lies in the triangle)
+//  o = 0: T0 = {(0,0),(2,0),(2,2)} -> nodes {0,1,2,4,5,8};  T1 = {(0,0),(2,2),(0,2)} -> {0,3,4,6,7,8}
+//  o = 1: T0 = {(0,0),(2,0),(0,2)} -> nodes {0,1,2,3,4,6};  T1 = {(2,0),(2,2),(0,2)} -> {2,4,5,6,7,8}
+__host__ __device__ constexpr unsigned tri_mask(int o, int t) {
+    return o == 0 ? (t == 0 ? 0x137u : 0x1D9u) : (t == 0 ? 0x05Fu : 0x1F4u);
+}
+__host__ __device__ constexpr bool couple(int o, int l, int m) {
+    return (((tri_mask(o, 0) >> l) & 1u) && ((tri_mask(o, 0) >> m) & 1u)) ||
+           (((tri_mask(o, 1) >> l) & 1u) && ((tri_mask(o, 1) >> m) & 1u));
+}
+__host__ __device__ constexpr int corner_node(int q) { return q == 0 ? 0 : q == 1 ? 2 : q == 2 ? 6 : 8; }
+
+__device__ __forceinline__ int orient(int si, int sj, int n) {
+    const int h = n >> 1;
+    return (si < h) != (sj < h);
+}
+
+// row L of A (orientation O) times the 9 square values
+template <int O, int L, typename T>
+__device__ __forceinline__ T arow(const T (&A)[2][9][9], const T (&v)[9]) {
+    T s = T(0);
+#pragma unroll
+    for (int m = 0; m < 9; ++m)
+        if (couple(O, L, m)) s = fma(A[O][L][m], v[m], s);
+    return s;
+}
+// (B^T p) restricted to row L: sum_q B[q][L] p[q]
+template <int O, int L, typename T>
+__device__ __forceinline__ T btrow(const T (&B)[2][4][9], const T (&p)[4]) {
+    T s = T(0);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (couple(O, corner_node(q), L)) s = fma(B[O][q][L], p[q], s);
+    return s;
+}
+// (B u) restricted to pressure row Q
+template <int O, int Q, typename T>
+__device__ __forceinline__ T brow(const T (&B)[2][4][9], const T (&v)[9]) {
+    T s = T(0);
+#pragma unroll
+    for (int m = 0; m < 9; ++m)
+        if (couple(O, corner_node(Q), m)) s = fma(B[O][Q][m], v[m], s);
+    return s;
+}
+
+// Is P2-lattice point (X, Y) an interior velocity node of a level with N = n?
+__device__ __forceinline__ bool interior2(int X, int Y, int n) {
+    return X > 0 && Y > 0 && X < 2 * n && Y < 2 * n;
+}
+
+// Which owned nodes of cell (i, j) exist / are unknowns.
+struct CellNodes {
+    bool v, h, e, c;   // unknown velocity nodes
+    bool hx, ex, cx;   // node exists in the lattice (may be a boundary node)
+};
+__device__ __forceinline__ CellNodes cell_nodes(int i, int j, int n) {
+    CellNodes c;
+    c.hx = i < n;
+    c.ex = j < n;
+    c.cx = i < n && j < n;
+    c.v = i > 0 && j > 0 && i < n && j < n;
+    c.h = c.hx && j > 0 && j < n;
+    c.e = c.ex && i > 0 && i < n;
+    c.c = c.cx;
+    return c;
+}
+
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+
+// Block-wide sum of one double per thread; returns the total in thread 0.
+template <int NT>
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double red[NT / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (warp == 0) {
+        s = lane < NT / 32 ? red[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    }
+    return s;
+}
+
+}  // namespace smg

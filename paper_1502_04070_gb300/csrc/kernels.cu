@@ -1,0 +1,830 @@
+// kernels.cu -- matrix-free kernels of the coupled multigrid cycle (Secs. 3-5).
+//
+// Every kernel runs one thread per cell (i, j) of a level, i, j in [0, N] (see common.cuh for the
+// owned nodes and the square-local matrices).  The operator rows are gathered from the 1-4 squares
+// around the cell, each square's orientation selecting a specialised code path (warp-uniform except
+// on the two mid-lines x = 1/2, y = 1/2), so that structurally-zero local entries cost nothing.
+#include <cstdio>
+
+#include "kernels.cuh"
+
+namespace smg {
+
+__constant__ double c_W2d[2][9][5][5];
+__constant__ float c_W2f[2][9][5][5];
+
+template <typename T> __device__ __forceinline__ T W2(int o, int L, int fb, int fa);
+template <> __device__ __forceinline__ double W2<double>(int o, int L, int fb, int fa) { return c_W2d[o][L][fb][fa]; }
+template <> __device__ __forceinline__ float W2<float>(int o, int L, int fb, int fa) { return c_W2f[o][L][fb][fa]; }
+
+cudaError_t upload_transfer_weights(const double* P2) {
+    float tmp[2 * 9 * 25];
+    for (int i = 0; i < 2 * 9 * 25; ++i) tmp[i] = (float)P2[i];
+    cudaError_t e = cudaMemcpyToSymbol(c_W2d, P2, sizeof(double) * 2 * 9 * 25);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyToSymbol(c_W2f, tmp, sizeof(float) * 2 * 9 * 25);
+}
+
+constexpr int BX = 32, BY = 8, NT = BX * BY;
+
+int cells_blocks(int n) { return ((n + 1 + BX - 1) / BX) * ((n + 1 + BY - 1) / BY); }
+static dim3 cells_grid(int n) { return dim3((n + 1 + BX - 1) / BX, (n + 1 + BY - 1) / BY); }
+
+// ------------------------------------------------------------------------------------------
+// rows of the square at position SQ relative to the cell: SQ 0 = (i, j), 1 = (i-1, j),
+// 2 = (i, j-1), 3 = (i-1, j-1).  The cell's vertex is corner Q = SQ of that square.
+__host__ __device__ constexpr int sq_nrows(int SQ) { return SQ == 0 ? 4 : (SQ == 3 ? 1 : 2); }
+__host__ __device__ constexpr int sq_row(int SQ, int r) {
+    // slot 0 = V, 1 = H, 2 = E, 3 = C.  SQ 0: V->0 H->1 E->3 C->4; SQ 1: V->2 E->5; SQ 2: V->6 H->7; SQ 3: V->8
+    return SQ == 0 ? (r == 0 ? 0 : r == 1 ? 1 : r == 2 ? 3 : 4)
+         : SQ == 1 ? (r == 0 ? 2 : 5)
+         : SQ == 2 ? (r == 0 ? 6 : 7)
+                   : 8;
+}
+__host__ __device__ constexpr int sq_slot(int SQ, int r) {
+    return SQ == 0 ? r : SQ == 1 ? (r == 0 ? 0 : 2) : SQ == 2 ? (r == 0 ? 0 : 1) : 0;
+}
+
+template <typename T>
+struct Acc {
+    T au[2][4];   // (A u) at the owned velocity nodes V, H, E, C
+    T bt[2][4];   // (B^T p)
+    T dg[4];      // diag A
+    T bu;         // (B u) at the owned vertex
+};
+
+template <bool MASK, typename T>
+__device__ __forceinline__ void load_sq(const T* __restrict__ u, int n, int si, int sj, T (&v)[9]) {
+    const int ld = 2 * n + 1;
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int X = 2 * si + a, Y = 2 * sj + b;
+            T val = __ldg(u + (size_t)Y * ld + X);
+            if (MASK && !interior2(X, Y, n)) val = T(0);
+            v[3 * b + a] = val;
+        }
+}
+
+template <typename T>
+__device__ __forceinline__ void load_sq_p(const T* __restrict__ p, int n, int si, int sj, T (&q)[4]) {
+    const int ld = n + 1;
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int a = 0; a < 2; ++a) q[2 * b + a] = __ldg(p + (size_t)(sj + b) * ld + si + a);
+}
+
+template <bool DA, bool DBT, bool DD, int O, int SQ, int R, typename T>
+__device__ __forceinline__ void sq_rows(const T (&A)[2][9][9], const OpCoef<T>& c, const T (&vx)[9],
+                                        const T (&vy)[9], const T (&pq)[4], Acc<T>& a) {
+    if constexpr (R < sq_nrows(SQ)) {
+        constexpr int L = sq_row(SQ, R), s = sq_slot(SQ, R);
+        if constexpr (DA) {
+            a.au[0][s] += arow<O, L>(A, vx);
+            a.au[1][s] += arow<O, L>(A, vy);
+        }
+        if constexpr (DBT) {
+            a.bt[0][s] += btrow<O, L>(c.Bx, pq);
+            a.bt[1][s] += btrow<O, L>(c.By, pq);
+        }
+        if constexpr (DD) a.dg[s] += A[O][L][L];
+        sq_rows<DA, DBT, DD, O, SQ, R + 1>(A, c, vx, vy, pq, a);
+    }
+}
+
+template <bool DA, bool DBT, bool DB, bool DD, bool MASK, int SQ, typename T>
+__device__ __forceinline__ void visit(int i, int j, int n, const T (&A)[2][9][9], const OpCoef<T>& c,
+                                      const T* __restrict__ ux, const T* __restrict__ uy,
+                                      const T* __restrict__ p, Acc<T>& a) {
+    const int si = i - (SQ & 1), sj = j - (SQ >> 1);
+    if (si < 0 || sj < 0 || si >= n || sj >= n) return;
+    T vx[9], vy[9], pq[4];
+    if constexpr (DA || DB) {
+        load_sq<MASK>(ux, n, si, sj, vx);
+        load_sq<MASK>(uy, n, si, sj, vy);
+    }
+    if constexpr (DBT) load_sq_p(p, n, si, sj, pq);
+    if (orient(si, sj, n)) {
+        sq_rows<DA, DBT, DD, 1, SQ, 0>(A, c, vx, vy, pq, a);
+        if constexpr (DB) a.bu += brow<1, SQ>(c.Bx, vx) + brow<1, SQ>(c.By, vy);
+    } else {
+        sq_rows<DA, DBT, DD, 0, SQ, 0>(A, c, vx, vy, pq, a);
+        if constexpr (DB) a.bu += brow<0, SQ>(c.Bx, vx) + brow<0, SQ>(c.By, vy);
+    }
+}
+
+template <bool DA, bool DBT, bool DB, bool DD, bool MASK, typename T>
+__device__ __forceinline__ void cell_apply(int i, int j, int n, const T (&A)[2][9][9], const OpCoef<T>& c,
+                                           const T* ux, const T* uy, const T* p, Acc<T>& a) {
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        a.au[0][s] = a.au[1][s] = a.bt[0][s] = a.bt[1][s] = a.dg[s] = T(0);
+    }
+    a.bu = T(0);
+    visit<DA, DBT, DB, DD, MASK, 0>(i, j, n, A, c, ux, uy, p, a);
+    visit<DA, DBT, DB, DD, MASK, 1>(i, j, n, A, c, ux, uy, p, a);
+    visit<DA, DBT, DB, DD, MASK, 2>(i, j, n, A, c, ux, uy, p, a);
+    visit<DA, DBT, DB, DD, MASK, 3>(i, j, n, A, c, ux, uy, p, a);
+}
+
+// lattice position and existence / unknown flags of slot s of cell (i, j)
+__device__ __forceinline__ void slot_pos(int i, int j, int s, int& X, int& Y) {
+    X = 2 * i + (s & 1);
+    Y = 2 * j + (s >> 1);
+}
+__device__ __forceinline__ bool slot_exists(const CellNodes& cn, int s) {
+    return s == 0 ? true : s == 1 ? cn.hx : s == 2 ? cn.ex : cn.cx;
+}
+__device__ __forceinline__ bool slot_unknown(const CellNodes& cn, int s) {
+    return s == 0 ? cn.v : s == 1 ? cn.h : s == 2 ? cn.e : cn.c;
+}
+
+#define CELL_INDEX                                          \
+    const int i = blockIdx.x * BX + threadIdx.x;            \
+    const int j = blockIdx.y * BY + threadIdx.y;            \
+    const bool active = i <= n && j <= n;                   \
+    const int tid = threadIdx.y * BX + threadIdx.x;         \
+    (void)tid;
+
+// Block sum (thread-linear id tid) of one double; result valid in tid 0.
+__device__ __forceinline__ double block_sum2d(double v, int tid) {
+    __shared__ double red[NT / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (tid < 32) {
+        s = tid < NT / 32 ? red[tid] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    }
+    return s;
+}
+
+// ------------------------------------------------------------------------------------------
+// r = F - A x  (eq. gen:bil:mv), optional sum of squares
+template <typename T, typename TO>
+__global__ void __launch_bounds__(NT) k_residual(int n, const __grid_constant__ OpCoef<T> c,
+                                                 const T* __restrict__ u, const T* __restrict__ p,
+                                                 const T* __restrict__ f, const T* __restrict__ g,
+                                                 TO* __restrict__ ru, TO* __restrict__ rp,
+                                                 double* __restrict__ partial) {
+    CELL_INDEX
+    const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
+    double ss = 0.0;
+    if (active) {
+        Acc<T> a;
+        cell_apply<true, true, true, false, true>(i, j, n, c.A, c, u, u + n2, p, a);
+        const CellNodes cn = cell_nodes(i, j, n);
+        const int ld = 2 * n + 1;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            if (!slot_exists(cn, s)) continue;
+            int X, Y;
+            slot_pos(i, j, s, X, Y);
+            const size_t idx = (size_t)Y * ld + X;
+#pragma unroll
+            for (int comp = 0; comp < 2; ++comp) {
+                TO r = TO(0);
+                if (slot_unknown(cn, s)) {
+                    const T rr = f[comp * n2 + idx] - a.au[comp][s] - a.bt[comp][s];
+                    r = (TO)rr;
+                    ss += (double)rr * (double)rr;
+                }
+                ru[comp * n2 + idx] = r;
+            }
+        }
+        const size_t vi = (size_t)j * (n + 1) + i;
+        const T r = g[vi] - a.bu;
+        rp[vi] = (TO)r;
+        ss += (double)r * (double)r;
+    }
+    if (partial) {
+        const double t = block_sum2d(ss, tid);
+        if (tid == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = t;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_uzawa_u(int n, const __grid_constant__ OpCoef<T> c, T tau,
+                                                const T* __restrict__ u, const T* __restrict__ p,
+                                                const T* __restrict__ f, T* __restrict__ uh) {
+    CELL_INDEX
+    if (!active) return;
+    const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
+    Acc<T> a;
+    cell_apply<true, true, false, true, true>(i, j, n, c.A, c, u, u + n2, p, a);
+    const CellNodes cn = cell_nodes(i, j, n);
+    const int ld = 2 * n + 1;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        if (!slot_exists(cn, s)) continue;
+        int X, Y;
+        slot_pos(i, j, s, X, Y);
+        const size_t idx = (size_t)Y * ld + X;
+        const bool unk = slot_unknown(cn, s);
+#pragma unroll
+        for (int comp = 0; comp < 2; ++comp) {
+            const size_t k = comp * n2 + idx;
+            uh[k] = unk ? u[k] + tau * (f[k] - a.au[comp][s] - a.bt[comp][s]) / a.dg[s] : T(0);
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_uzawa_p(int n, const __grid_constant__ OpCoef<T> c, T sigma,
+                                                const T* __restrict__ uh, T* __restrict__ p,
+                                                const T* __restrict__ g, const T* __restrict__ sinv,
+                                                T* __restrict__ dp) {
+    CELL_INDEX
+    if (!active) return;
+    const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
+    Acc<T> a;
+    cell_apply<false, false, true, false, false>(i, j, n, c.A, c, uh, uh + n2, (const T*)nullptr, a);
+    const size_t vi = (size_t)j * (n + 1) + i;
+    // p^{m} = p^{m-1} - sigma Shat^{-1} (g - B u^{m-1/2})
+    const T d = sigma * sinv[vi] * (a.bu - g[vi]);
+    p[vi] += d;
+    dp[vi] = d;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_uzawa_u2(int n, const __grid_constant__ OpCoef<T> c, T tau,
+                                                 const T* __restrict__ uh, const T* __restrict__ dp,
+                                                 T* __restrict__ u) {
+    CELL_INDEX
+    if (!active) return;
+    const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
+    Acc<T> a;
+    cell_apply<false, true, false, true, false>(i, j, n, c.A, c, (const T*)nullptr, (const T*)nullptr, dp, a);
+    const CellNodes cn = cell_nodes(i, j, n);
+    const int ld = 2 * n + 1;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        if (!slot_exists(cn, s)) continue;
+        int X, Y;
+        slot_pos(i, j, s, X, Y);
+        const size_t idx = (size_t)Y * ld + X;
+        const bool unk = slot_unknown(cn, s);
+#pragma unroll
+        for (int comp = 0; comp < 2; ++comp) {
+            const size_t k = comp * n2 + idx;
+            // u^{m} = u^{m-1/2} - tau Ahat^{-1} B^T (p^{m} - p^{m-1})
+            u[k] = unk ? uh[k] - tau * a.bt[comp][s] / a.dg[s] : T(0);
+        }
+    }
+}
+
+template <typename T>
+void launch_uzawa(cudaStream_t s, int n, const OpCoef<T>& c, T tau, T sigma, T* u, T* p, const T* f,
+                  const T* g, const T* sinv, T* uh, T* dp) {
+    const dim3 grid = cells_grid(n), blk(BX, BY);
+    k_uzawa_u<T><<<grid, blk, 0, s>>>(n, c, tau, u, p, f, uh);
+    k_uzawa_p<T><<<grid, blk, 0, s>>>(n, c, sigma, uh, p, g, sinv, dp);
+    k_uzawa_u2<T><<<grid, blk, 0, s>>>(n, c, tau, uh, dp, u);
+}
+
+// ------------------------------------------------------------------------------------------
+// normal-equation smoother: z = L^{-1} r  then  x += tau L^{-1} A z
+template <typename T>
+__global__ void __launch_bounds__(NT) k_scale_L(int n, const __grid_constant__ OpCoef<T> c,
+                                                T* __restrict__ zu, T* __restrict__ zp,
+                                                const T* __restrict__ sinv) {
+    CELL_INDEX
+    if (!active) return;
+    const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
+    Acc<T> a;
+    cell_apply<false, false, false, true, false>(i, j, n, c.A, c, (const T*)nullptr, (const T*)nullptr,
+                                                 (const T*)nullptr, a);
+    const CellNodes cn = cell_nodes(i, j, n);
+    const int ld = 2 * n + 1;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        if (!slot_unknown(cn, s)) continue;
+        int X, Y;
+        slot_pos(i, j, s, X, Y);
+        const size_t idx = (size_t)Y * ld + X;
+        zu[idx] /= a.dg[s];
+        zu[n2 + idx] /= a.dg[s];
+    }
+    const size_t vi = (size_t)j * (n + 1) + i;
+    zp[vi] *= sinv[vi];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_normal_update(int n, const __grid_constant__ OpCoef<T> c, T tau,
+                                                      const T* __restrict__ zu, const T* __restrict__ zp,
+                                                      const T* __restrict__ sinv, T* __restrict__ u,
+                                                      T* __restrict__ p) {
+    CELL_INDEX
+    if (!active) return;
+    const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
+    Acc<T> a;
+    cell_apply<true, true, true, true, false>(i, j, n, c.A, c, zu, zu + n2, zp, a);
+    const CellNodes cn = cell_nodes(i, j, n);
+    const int ld = 2 * n + 1;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        if (!slot_unknown(cn, s)) continue;
+        int X, Y;
+        slot_pos(i, j, s, X, Y);
+        const size_t idx = (size_t)Y * ld + X;
+#pragma unroll
+        for (int comp = 0; comp < 2; ++comp) u[comp * n2 + idx] += tau * (a.au[comp][s] + a.bt[comp][s]) / a.dg[s];
+    }
+    const size_t vi = (size_t)j * (n + 1) + i;
+    p[vi] += tau * sinv[vi] * a.bu;
+}
+
+template <typename T>
+void launch_normal_eq(cudaStream_t s, int n, const OpCoef<T>& c, T tau, T* u, T* p, const T* f,
+                      const T* g, const T* sinv, T* zu, T* zp) {
+    const dim3 grid = cells_grid(n), blk(BX, BY);
+    k_residual<T, T><<<grid, blk, 0, s>>>(n, c, u, p, f, g, zu, zp, nullptr);
+    k_scale_L<T><<<grid, blk, 0, s>>>(n, c, zu, zp, sinv);
+    k_normal_update<T><<<grid, blk, 0, s>>>(n, c, tau, zu, zp, sinv, u, p);
+}
+
+template <typename T, typename TO>
+void launch_residual(cudaStream_t s, int n, const OpCoef<T>& c, const T* u, const T* p, const T* f,
+                     const T* g, TO* ru, TO* rp, double* partial) {
+    k_residual<T, TO><<<cells_grid(n), dim3(BX, BY), 0, s>>>(n, c, u, p, f, g, ru, rp, partial);
+}
+
+// ------------------------------------------------------------------------------------------
+// Restriction (Sec. 3): coarse value = sum over fine points of (coarse basis at the point) x r.
+// Every fine point is owned by one coarse square (local fine offsets 0..3 in each direction);
+// points on the far edges belong to the neighbouring square, where the weights of the nodes not
+// shared with it vanish, so the sum over the 1-4 squares of a coarse node's patch is exact.
+template <int O, int SQ, int R, typename T>
+__device__ __forceinline__ void restrict_rows(const T (&v)[2][4][4], T (&acc)[2][4]) {
+    if constexpr (R < sq_nrows(SQ)) {
+        constexpr int L = sq_row(SQ, R), s = sq_slot(SQ, R);
+#pragma unroll
+        for (int fb = 0; fb < 4; ++fb)
+#pragma unroll
+            for (int fa = 0; fa < 4; ++fa) {
+                const T w = W2<T>(O, L, fb, fa);
+                acc[0][s] = fma(w, v[0][fb][fa], acc[0][s]);
+                acc[1][s] = fma(w, v[1][fb][fa], acc[1][s]);
+            }
+        restrict_rows<O, SQ, R + 1>(v, acc);
+    }
+}
+
+template <int SQ, typename T>
+__device__ __forceinline__ void restrict_visit(int I, int J, int nc, const T* __restrict__ ru, T (&acc)[2][4]) {
+    const int SI = I - (SQ & 1), SJ = J - (SQ >> 1);
+    if (SI < 0 || SJ < 0 || SI >= nc || SJ >= nc) return;
+    const int nf = 2 * nc, ldf = 2 * nf + 1;
+    const size_t n2f = (size_t)ldf * ldf;
+    T v[2][4][4];
+#pragma unroll
+    for (int fb = 0; fb < 4; ++fb)
+#pragma unroll
+        for (int fa = 0; fa < 4; ++fa) {
+            const size_t k = (size_t)(4 * SJ + fb) * ldf + 4 * SI + fa;
+            v[0][fb][fa] = __ldg(ru + k);
+            v[1][fb][fa] = __ldg(ru + n2f + k);
+        }
+    if (orient(SI, SJ, nc)) restrict_rows<1, SQ, 0>(v, acc);
+    else restrict_rows<0, SQ, 0>(v, acc);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_restrict(int nc, const T* __restrict__ ru, const T* __restrict__ rp,
+                                                 T* __restrict__ fc, T* __restrict__ gc) {
+    const int n = nc;
+    CELL_INDEX
+    if (!active) return;
+    T acc[2][4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) acc[0][s] = acc[1][s] = T(0);
+    restrict_visit<0>(i, j, nc, ru, acc);
+    restrict_visit<1>(i, j, nc, ru, acc);
+    restrict_visit<2>(i, j, nc, ru, acc);
+    restrict_visit<3>(i, j, nc, ru, acc);
+    const CellNodes cn = cell_nodes(i, j, nc);
+    const int ldc = 2 * nc + 1;
+    const size_t n2c = (size_t)ldc * ldc;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        if (!slot_exists(cn, s)) continue;
+        int X, Y;
+        slot_pos(i, j, s, X, Y);
+        const size_t k = (size_t)Y * ldc + X;
+        const bool unk = slot_unknown(cn, s);
+        fc[k] = unk ? acc[0][s] : T(0);
+        fc[n2c + k] = unk ? acc[1][s] : T(0);
+    }
+    // P1: the coarse hat function is 1 at (2i, 2j), 1/2 at the fine vertices halfway along the
+    // coarse edges through it (horizontal, vertical, and the diagonal of each square whose cut
+    // passes through the vertex), 0 elsewhere.
+    const int nf = 2 * nc, ldf = nf + 1;
+    const int x = 2 * i, y = 2 * j;
+    T s = rp[(size_t)y * ldf + x];
+    T half = T(0);
+    if (x > 0) half += rp[(size_t)y * ldf + x - 1];
+    if (x < nf) half += rp[(size_t)y * ldf + x + 1];
+    if (y > 0) half += rp[(size_t)(y - 1) * ldf + x];
+    if (y < nf) half += rp[(size_t)(y + 1) * ldf + x];
+    // diagonal neighbours (dx, dy): square (i + min(dx,0), j + min(dy,0)); orientation 0 joins
+    // (dx, dy) = (+,+) / (-,-), orientation 1 joins (+,-) / (-,+)
+    if (x < nf && y < nf && orient(i, j, nc) == 0) half += rp[(size_t)(y + 1) * ldf + x + 1];
+    if (x > 0 && y > 0 && orient(i - 1, j - 1, nc) == 0) half += rp[(size_t)(y - 1) * ldf + x - 1];
+    if (x < nf && y > 0 && orient(i, j - 1, nc) == 1) half += rp[(size_t)(y - 1) * ldf + x + 1];
+    if (x > 0 && y < nf && orient(i - 1, j, nc) == 1) half += rp[(size_t)(y + 1) * ldf + x - 1];
+    gc[(size_t)j * (nc + 1) + i] = s + T(0.5) * half;
+}
+
+template <typename T>
+void launch_restrict(cudaStream_t s, int nc, const T* ru, const T* rp, T* fc, T* gc) {
+    k_restrict<T><<<cells_grid(nc), dim3(BX, BY), 0, s>>>(nc, ru, rp, fc, gc);
+}
+
+// Prolongation (Sec. 3, canonical embedding): every fine point owned by coarse square (I, J) is
+// the coarse P2 function of that square evaluated there; P1 values are vertex injection and
+// averages along coarse edges.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_prolong(int nc, const T* __restrict__ uc, const T* __restrict__ pc,
+                                                T* __restrict__ u, T* __restrict__ p) {
+    const int n = nc;
+    CELL_INDEX
+    if (!active) return;
+    const int nf = 2 * nc, ldf = 2 * nf + 1, ldc = 2 * nc + 1;
+    const size_t n2f = (size_t)ldf * ldf, n2c = (size_t)ldc * ldc;
+    if (i < nc && j < nc) {
+        T z[2][9];
+#pragma unroll
+        for (int m = 0; m < 9; ++m) {
+            const size_t k = (size_t)(2 * j + m / 3) * ldc + 2 * i + m % 3;
+            z[0][m] = __ldg(uc + k);
+            z[1][m] = __ldg(uc + n2c + k);
+        }
+        const int o = orient(i, j, nc);
+#pragma unroll
+        for (int fb = 0; fb < 4; ++fb)
+#pragma unroll
+            for (int fa = 0; fa < 4; ++fa) {
+                const int X = 4 * i + fa, Y = 4 * j + fb;
+                if (!interior2(X, Y, nf)) continue;
+                T sx = T(0), sy = T(0);
+#pragma unroll
+                for (int L = 0; L < 9; ++L) {
+                    const T w = W2<T>(o, L, fb, fa);
+                    sx = fma(w, z[0][L], sx);
+                    sy = fma(w, z[1][L], sy);
+                }
+                const size_t k = (size_t)Y * ldf + X;
+                u[k] += sx;
+                u[n2f + k] += sy;
+            }
+    }
+    const int ldp = nc + 1, ldpf = nf + 1;
+    auto P = [&](int a, int b) { return __ldg(pc + (size_t)b * ldp + a); };
+    const T p00 = P(i, j);
+    p[(size_t)(2 * j) * ldpf + 2 * i] += p00;
+    if (i < nc) p[(size_t)(2 * j) * ldpf + 2 * i + 1] += T(0.5) * (p00 + P(i + 1, j));
+    if (j < nc) p[(size_t)(2 * j + 1) * ldpf + 2 * i] += T(0.5) * (p00 + P(i, j + 1));
+    if (i < nc && j < nc) {
+        const T d = orient(i, j, nc) == 0 ? p00 + P(i + 1, j + 1) : P(i + 1, j) + P(i, j + 1);
+        p[(size_t)(2 * j + 1) * ldpf + 2 * i + 1] += T(0.5) * d;
+    }
+}
+
+template <typename T>
+void launch_prolong_add(cudaStream_t s, int nc, const T* uc, const T* pc, T* u, T* p) {
+    k_prolong<T><<<cells_grid(nc), dim3(BX, BY), 0, s>>>(nc, uc, pc, u, p);
+}
+
+// ------------------------------------------------------------------------------------------
+// Level 0 (N = 2): x = inv b with the bordered inverse; 27 unknowns (see elements.cpp).
+template <typename T>
+__global__ void k_coarse(const double* __restrict__ inv, const T* __restrict__ f, const T* __restrict__ g,
+                         T* __restrict__ u, T* __restrict__ p) {
+    __shared__ double b[27];
+    const int t = threadIdx.x;
+    auto vpos = [](int t, int& c, int& k) {
+        c = t / 9;
+        const int r = t % 9;
+        k = (1 + r / 3) * 5 + 1 + r % 3;
+    };
+    if (t < 27) {
+        if (t < 18) {
+            int c, k;
+            vpos(t, c, k);
+            b[t] = (double)f[c * 25 + k];
+        } else {
+            b[t] = (double)g[t - 18];
+        }
+    }
+    __syncthreads();
+    // zero the velocity boundary of level 0 (50 entries), then write the solution
+    for (int k = t; k < 50; k += blockDim.x) {
+        const int r = k % 25, X = r % 5, Y = r / 5;
+        if (X == 0 || Y == 0 || X == 4 || Y == 4) u[k] = T(0);
+    }
+    if (t < 27) {
+        double x = 0.0;
+        for (int s = 0; s < 27; ++s) x = fma(inv[t * 27 + s], b[s], x);
+        if (t < 18) {
+            int c, k;
+            vpos(t, c, k);
+            u[c * 25 + k] = (T)x;
+        } else {
+            p[t - 18] = (T)x;
+        }
+    }
+}
+
+template <typename T>
+void launch_coarse_solve(cudaStream_t s, const double* inv, const T* f, const T* g, T* u, T* p) {
+    k_coarse<T><<<1, 32, 0, s>>>(inv, f, g, u, p);
+}
+
+// ------------------------------------------------------------------------------------------
+// Shat = diag(B Ahat^{-1} B^T), Ahat = diag A (Sec. 5, eq. numintroduc): for vertex (i, j),
+// sum over interior velocity nodes l and both components of B_{(i,j), l}^2 / A_{ll}.
+__device__ double diagA_at(int X, int Y, int n, const OpCoef<double>& c) {
+    double d = 0.0;
+    const int sx0 = (X & 1) ? (X - 1) / 2 : X / 2 - 1, sx1 = (X & 1) ? sx0 : X / 2;
+    const int sy0 = (Y & 1) ? (Y - 1) / 2 : Y / 2 - 1, sy1 = (Y & 1) ? sy0 : Y / 2;
+    for (int sj = sy0; sj <= sy1; ++sj)
+        for (int si = sx0; si <= sx1; ++si) {
+            if (si < 0 || sj < 0 || si >= n || sj >= n) continue;
+            const int a = X - 2 * si, b = Y - 2 * sj, o = orient(si, sj, n);
+            d += c.A[o][3 * b + a][3 * b + a];
+        }
+    return d;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_schur(int n, const __grid_constant__ OpCoef<double> c, T* __restrict__ sinv) {
+    CELL_INDEX
+    if (!active) return;
+    double bx[5][5], by[5][5];
+    for (int b = 0; b < 5; ++b)
+        for (int a = 0; a < 5; ++a) bx[b][a] = by[b][a] = 0.0;
+    for (int SQ = 0; SQ < 4; ++SQ) {
+        const int si = i - (SQ & 1), sj = j - (SQ >> 1);
+        if (si < 0 || sj < 0 || si >= n || sj >= n) continue;
+        const int o = orient(si, sj, n);
+        for (int m = 0; m < 9; ++m) {
+            const int px = 2 * (si - i) + 2 + m % 3, py = 2 * (sj - j) + 2 + m / 3;
+            bx[py][px] += c.Bx[o][SQ][m];
+            by[py][px] += c.By[o][SQ][m];
+        }
+    }
+    double s = 0.0;
+    for (int py = 0; py < 5; ++py)
+        for (int px = 0; px < 5; ++px) {
+            const int X = 2 * i - 2 + px, Y = 2 * j - 2 + py;
+            if (!interior2(X, Y, n)) continue;
+            s += (bx[py][px] * bx[py][px] + by[py][px] * by[py][px]) / diagA_at(X, Y, n, c);
+        }
+    sinv[(size_t)j * (n + 1) + i] = (T)(1.0 / s);
+}
+
+template <typename T>
+void launch_schur_diag(cudaStream_t s, int n, const OpCoef<double>& c, T* sinv) {
+    k_schur<T><<<cells_grid(n), dim3(BX, BY), 0, s>>>(n, c, sinv);
+}
+
+// ------------------------------------------------------------------------------------------
+// w_i = int psi_i = (number of triangles at vertex i) h^2 / 6
+__device__ __forceinline__ double vertex_weight(int i, int j, int n) {
+    int cnt = 0;
+#pragma unroll
+    for (int SQ = 0; SQ < 4; ++SQ) {
+        const int si = i - (SQ & 1), sj = j - (SQ >> 1);
+        if (si < 0 || sj < 0 || si >= n || sj >= n) continue;
+        const int o = orient(si, sj, n), node = corner_node(SQ);
+        cnt += ((tri_mask(o, 0) >> node) & 1u) + ((tri_mask(o, 1) >> node) & 1u);
+    }
+    const double h = 1.0 / n;
+    return cnt * h * h / 6.0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_pmean_partial(int n, const T* __restrict__ p, double* __restrict__ partial) {
+    CELL_INDEX
+    double v = 0.0;
+    if (active) v = vertex_weight(i, j, n) * (double)p[(size_t)j * (n + 1) + i];
+    const double t = block_sum2d(v, tid);
+    if (tid == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = t;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_psub(int n, T* __restrict__ p, const double* __restrict__ scalar) {
+    CELL_INDEX
+    if (!active) return;
+    p[(size_t)j * (n + 1) + i] -= (T)(*scalar);   // sum_i w_i = |Omega| = 1
+}
+
+__global__ void k_reduce(const double* __restrict__ partial, int count, double* __restrict__ out) {
+    // fixed-order tree: deterministic for a given count
+    __shared__ double red[1024];
+    double s = 0.0;
+    for (int k = threadIdx.x; k < count; k += blockDim.x) s += partial[k];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = red[0];
+}
+
+void launch_reduce(cudaStream_t s, const double* partial, int count, double* out) {
+    k_reduce<<<1, 1024, 0, s>>>(partial, count, out);
+}
+
+template <typename T>
+void launch_pmean(cudaStream_t s, int n, T* p, double* partial, double* scalar) {
+    const dim3 grid = cells_grid(n), blk(BX, BY);
+    k_pmean_partial<T><<<grid, blk, 0, s>>>(n, p, partial);
+    k_reduce<<<1, 1024, 0, s>>>(partial, grid.x * grid.y, scalar);
+    k_psub<T><<<grid, blk, 0, s>>>(n, p, scalar);
+}
+
+// ------------------------------------------------------------------------------------------
+// load vectors (data f, g of Sec. 1 given by nodal values)
+template <typename T>
+__device__ __forceinline__ void mp_row(int i, int j, int n, const MassCoef<T>& m, const T* __restrict__ gn,
+                                       T& mg, double& w) {
+    mg = T(0);
+    w = 0.0;
+#pragma unroll
+    for (int SQ = 0; SQ < 4; ++SQ) {
+        const int si = i - (SQ & 1), sj = j - (SQ >> 1);
+        if (si < 0 || sj < 0 || si >= n || sj >= n) continue;
+        const int o = orient(si, sj, n);
+        T q[4];
+        load_sq_p(gn, n, si, sj, q);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            mg = fma(m.MP[o][SQ][r], q[r], mg);
+            w += (double)m.MP[o][SQ][r];
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_load(int n, const __grid_constant__ MassCoef<T> m, const __grid_constant__ OpCoef<T> c,
+                                             const T* __restrict__ fn, const T* __restrict__ gn,
+                                             T* __restrict__ f, T* __restrict__ g, double* __restrict__ partial) {
+    CELL_INDEX
+    const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
+    double wg = 0.0;
+    if (active) {
+        Acc<T> a;
+        cell_apply<true, false, false, false, false>(i, j, n, m.M, c, fn, fn + n2, (const T*)nullptr, a);
+        const CellNodes cn = cell_nodes(i, j, n);
+        const int ld = 2 * n + 1;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            if (!slot_exists(cn, s)) continue;
+            int X, Y;
+            slot_pos(i, j, s, X, Y);
+            const size_t k = (size_t)Y * ld + X;
+            const bool unk = slot_unknown(cn, s);
+            f[k] = unk ? a.au[0][s] : T(0);
+            f[n2 + k] = unk ? a.au[1][s] : T(0);
+        }
+        T mg;
+        double w;
+        mp_row(i, j, n, m, gn, mg, w);
+        const size_t vi = (size_t)j * (n + 1) + i;
+        g[vi] = mg;
+        wg = w * (double)gn[vi];
+    }
+    const double t = block_sum2d(wg, tid);
+    if (tid == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = t;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_gproj(int n, const __grid_constant__ MassCoef<T> m, T* __restrict__ g,
+                                              const double* __restrict__ scalar) {
+    CELL_INDEX
+    if (!active) return;
+    double w = 0.0;
+#pragma unroll
+    for (int SQ = 0; SQ < 4; ++SQ) {
+        const int si = i - (SQ & 1), sj = j - (SQ >> 1);
+        if (si < 0 || sj < 0 || si >= n || sj >= n) continue;
+        const int o = orient(si, sj, n);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) w += (double)m.MP[o][SQ][r];
+    }
+    // M_P (g - c 1) = M_P g - c w,  c = int g_h = sum_i w_i g_i
+    g[(size_t)j * (n + 1) + i] -= (T)(w * (*scalar));
+}
+
+template <typename T>
+void launch_load(cudaStream_t s, int n, const MassCoef<T>& m, const T* fn, const T* gn, T* f, T* g,
+                 int project_g, double* partial, double* scalar) {
+    const dim3 grid = cells_grid(n), blk(BX, BY);
+    OpCoef<T> dummy{};
+    k_load<T><<<grid, blk, 0, s>>>(n, m, dummy, fn, gn, f, g, partial);
+    if (project_g) {
+        k_reduce<<<1, 1024, 0, s>>>(partial, grid.x * grid.y, scalar);
+        k_gproj<T><<<grid, blk, 0, s>>>(n, m, g, scalar);
+    }
+}
+
+__global__ void __launch_bounds__(NT) k_mass_dot(int n, const __grid_constant__ MassCoef<double> m,
+                                                 const __grid_constant__ OpCoef<double> c,
+                                                 const double* __restrict__ av, const double* __restrict__ bv,
+                                                 double* __restrict__ partial) {
+    CELL_INDEX
+    const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
+    double acc = 0.0;
+    if (active) {
+        Acc<double> a;
+        cell_apply<true, false, false, false, true>(i, j, n, m.M, c, bv, bv + n2, (const double*)nullptr, a);
+        const CellNodes cn = cell_nodes(i, j, n);
+        const int ld = 2 * n + 1;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            if (!slot_unknown(cn, s)) continue;
+            int X, Y;
+            slot_pos(i, j, s, X, Y);
+            const size_t k = (size_t)Y * ld + X;
+            acc += av[k] * a.au[0][s] + av[n2 + k] * a.au[1][s];
+        }
+    }
+    const double t = block_sum2d(acc, tid);
+    if (tid == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = t;
+}
+
+void launch_mass_dot(cudaStream_t s, int n, const MassCoef<double>& m, const double* a, const double* b,
+                     double* partial) {
+    OpCoef<double> dummy{};
+    k_mass_dot<<<cells_grid(n), dim3(BX, BY), 0, s>>>(n, m, dummy, a, b, partial);
+}
+
+__global__ void __launch_bounds__(NT) k_rhs_norm(int n, const double* __restrict__ f, const double* __restrict__ g,
+                                                 double* __restrict__ partial) {
+    CELL_INDEX
+    const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
+    double ss = 0.0;
+    if (active) {
+        const CellNodes cn = cell_nodes(i, j, n);
+        const int ld = 2 * n + 1;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            if (!slot_unknown(cn, s)) continue;
+            int X, Y;
+            slot_pos(i, j, s, X, Y);
+            const size_t k = (size_t)Y * ld + X;
+            ss += f[k] * f[k] + f[n2 + k] * f[n2 + k];
+        }
+        const double v = g[(size_t)j * (n + 1) + i];
+        ss += v * v;
+    }
+    const double t = block_sum2d(ss, tid);
+    if (tid == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = t;
+}
+
+void launch_rhs_norm(cudaStream_t s, int n, const double* f, const double* g, double* partial) {
+    k_rhs_norm<<<cells_grid(n), dim3(BX, BY), 0, s>>>(n, f, g, partial);
+}
+
+__global__ void k_add_f32(size_t count, const float* __restrict__ e, double* __restrict__ x) {
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < count; k += (size_t)gridDim.x * blockDim.x)
+        x[k] += (double)e[k];
+}
+
+void launch_add_f32(cudaStream_t s, size_t count, const float* e, double* x) {
+    const int blocks = (int)((count + 255) / 256 < 152 * 16 ? (count + 255) / 256 : 152 * 16);
+    k_add_f32<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(count, e, x);
+}
+
+// ------------------------------------------------------------------------------------------
+#define INST(T)                                                                                         \
+    template void launch_uzawa<T>(cudaStream_t, int, const OpCoef<T>&, T, T, T*, T*, const T*, const T*, \
+                                  const T*, T*, T*);                                                      \
+    template void launch_normal_eq<T>(cudaStream_t, int, const OpCoef<T>&, T, T*, T*, const T*, const T*, \
+                                      const T*, T*, T*);                                                  \
+    template void launch_restrict<T>(cudaStream_t, int, const T*, const T*, T*, T*);                      \
+    template void launch_prolong_add<T>(cudaStream_t, int, const T*, const T*, T*, T*);                   \
+    template void launch_coarse_solve<T>(cudaStream_t, const double*, const T*, const T*, T*, T*);        \
+    template void launch_schur_diag<T>(cudaStream_t, int, const OpCoef<double>&, T*);                     \
+    template void launch_pmean<T>(cudaStream_t, int, T*, double*, double*);                               \
+    template void launch_load<T>(cudaStream_t, int, const MassCoef<T>&, const T*, const T*, T*, T*, int,  \
+                                 double*, double*);
+INST(float)
+INST(double)
+template void launch_residual<double, double>(cudaStream_t, int, const OpCoef<double>&, const double*,
+                                              const double*, const double*, const double*, double*, double*,
+                                              double*);
+template void launch_residual<float, float>(cudaStream_t, int, const OpCoef<float>&, const float*, const float*,
+                                            const float*, const float*, float*, float*, double*);
+template void launch_residual<double, float>(cudaStream_t, int, const OpCoef<double>&, const double*,
+                                             const double*, const double*, const double*, float*, float*,
+                                             double*);
+
+}  // namespace smg

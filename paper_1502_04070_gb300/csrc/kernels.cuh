@@ -1,0 +1,72 @@
+// kernels.cuh -- launch wrappers of the solver's CUDA kernels (defined in kernels.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace smg {
+
+// Partial-sum buffer capacity (blocks of the largest level) is computed by the caller with
+// cells_blocks(n).
+int cells_blocks(int n);
+
+// Transfer weight table (constant memory), set once per device.
+cudaError_t upload_transfer_weights(const double* P2 /* [2][9][5][5] */);
+
+// r = F - A x with per-block partial sums of r.r (over unknowns) in `partial` (may be null).
+template <typename T, typename TO>
+void launch_residual(cudaStream_t s, int n, const OpCoef<T>& c, const T* u, const T* p, const T* f,
+                     const T* g, TO* ru, TO* rp, double* partial);
+
+// Uzawa step (Sec. 4), three kernels:
+//   uh = u + tau Ahat^{-1} (f - A u - B^T p)
+//   dp = sigma Shat^{-1} (B uh - g);  p += dp
+//   u  = uh - tau Ahat^{-1} B^T dp
+template <typename T>
+void launch_uzawa(cudaStream_t s, int n, const OpCoef<T>& c, T tau, T sigma, T* u, T* p, const T* f,
+                  const T* g, const T* sinv, T* uh, T* dp);
+
+// Normal-equation step (Sec. 4): x += tau L^{-1} A L^{-1} (F - A x),  L = diag(Ahat, Shat).
+template <typename T>
+void launch_normal_eq(cudaStream_t s, int n, const OpCoef<T>& c, T tau, T* u, T* p, const T* f,
+                      const T* g, const T* sinv, T* zu, T* zp);
+
+// (fc, gc) = I^T (ru, rp): fine level n = 2 nc.
+template <typename T>
+void launch_restrict(cudaStream_t s, int nc, const T* ru, const T* rp, T* fc, T* gc);
+
+// (u, p) += I (uc, pc)
+template <typename T>
+void launch_prolong_add(cudaStream_t s, int nc, const T* uc, const T* pc, T* u, T* p);
+
+// level-0 exact solve with the bordered inverse (27 x 27, float64)
+template <typename T>
+void launch_coarse_solve(cudaStream_t s, const double* inv, const T* f, const T* g, T* u, T* p);
+
+// Shat^{-1} per vertex (float64 computation, stored as T)
+template <typename T>
+void launch_schur_diag(cudaStream_t s, int n, const OpCoef<double>& c, T* sinv);
+
+// p <- p - sum_i w_i p_i  (w = M_P 1, sum w = 1): partial sums then subtraction
+template <typename T>
+void launch_pmean(cudaStream_t s, int n, T* p, double* partial, double* scalar);
+
+// out[0] = sum of partial[0..count)
+void launch_reduce(cudaStream_t s, const double* partial, int count, double* out);
+
+// load vectors: f = M_U f_nodal (interior rows), g = M_P g_nodal, with optional zero-mean shift
+template <typename T>
+void launch_load(cudaStream_t s, int n, const MassCoef<T>& m, const T* fn, const T* gn, T* f, T* g,
+                 int project_g, double* partial, double* scalar);
+
+// partial sums of a^T M_U b
+void launch_mass_dot(cudaStream_t s, int n, const MassCoef<double>& m, const double* a, const double* b,
+                     double* partial);
+
+// partial sums of ||F||^2 over the unknowns (f at interior velocity nodes, all of g)
+void launch_rhs_norm(cudaStream_t s, int n, const double* f, const double* g, double* partial);
+
+// x64 += e32 (count elements), and float64 -> float32 conversion
+void launch_add_f32(cudaStream_t s, size_t count, const float* e, double* x);
+
+}  // namespace smg

@@ -1,0 +1,194 @@
+"""Python front end of the CUDA solver: torch tensors in, torch tensors out.
+
+Every step runs in the CUDA library (include/stokes_mg.h); this module only checks shapes and
+passes device pointers and the current stream.
+
+Layouts (float64, CUDA, contiguous):  u (2, 2N+1, 2N+1), p (N+1, N+1), with N = 2^levels.
+"""
+import ctypes
+import math
+
+import torch
+
+from . import _binding as B
+
+_SMOOTHERS = {"uzawa": B.UZAWA, "normal": B.NORMAL_EQ}
+_PREC = {"fp64": B.FP64, "mixed": B.MIXED}
+
+
+class Report:
+    def __init__(self, r: B.Report, history, status):
+        self.cycles = r.cycles
+        self.rel_residual = r.rel_residual
+        self.mean_rate = r.mean_rate
+        self.initial_residual = r.initial_residual
+        self.rhs_norm = r.rhs_norm
+        self.history = history
+        self.status = status
+
+    @property
+    def converged(self):
+        return self.status == B.OK
+
+    def __repr__(self):
+        return "Report(cycles=%d, rel_residual=%.3e, mean_rate=%.4f)" % (self.cycles, self.rel_residual, self.mean_rate)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """Coupled multigrid solver for [A + beta M, B^T; B, 0] on level k = levels - 1."""
+
+    def __init__(self, levels: int, beta: float, *, nu_pre=3, nu_post=3, tau=None, sigma=0.8,
+                 smoother="uzawa", gamma=1, precision="fp64", inner_cycles=1, stream=None, device=None):
+        self._lib = B.load()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        prm = B.Params()
+        self._lib.stokes_default_params(ctypes.byref(prm), levels, float(beta))
+        prm.nu_pre, prm.nu_post = nu_pre, nu_post
+        prm.smoother = _SMOOTHERS[smoother]
+        prm.tau = (0.8 if smoother == "uzawa" else 0.35) if tau is None else tau
+        prm.sigma = sigma
+        prm.gamma = gamma
+        prm.precision = _PREC[precision]
+        prm.inner_cycles = inner_cycles
+        self.params = prm
+        self.levels = levels
+        self.beta = float(beta)
+        self.N = 2 ** levels
+        self.precision = precision
+        with torch.cuda.device(self.device):
+            s = torch.cuda.current_stream() if stream is None else stream
+            self._stream = s
+            h = ctypes.c_void_p()
+            B.check(self._lib.stokes_setup(ctypes.byref(prm), ctypes.c_void_p(s.cuda_stream), ctypes.byref(h)),
+                    "stokes_setup")
+        self._h = h
+
+    # ------------------------------------------------------------------ helpers
+    @property
+    def shape_u(self):
+        return (2, 2 * self.N + 1, 2 * self.N + 1)
+
+    @property
+    def shape_p(self):
+        return (self.N + 1, self.N + 1)
+
+    @property
+    def ndof(self):
+        return 2 * (2 * self.N - 1) ** 2 + (self.N + 1) ** 2
+
+    def _chk(self, t, shape, name):
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or t.device != self.device \
+                or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+            raise ValueError("%s must be a contiguous float64 tensor of shape %s on %s" % (name, shape, self.device))
+        return _ptr(t)
+
+    def zeros_u(self):
+        return torch.zeros(self.shape_u, dtype=torch.float64, device=self.device)
+
+    def zeros_p(self):
+        return torch.zeros(self.shape_p, dtype=torch.float64, device=self.device)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.stokes_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ API
+    def set_beta(self, beta):
+        B.check(self._lib.stokes_set_beta(self._h, float(beta)), "stokes_set_beta")
+        self.beta = float(beta)
+
+    def load_vectors(self, f_nodal, g_nodal, project_g=True):
+        f, g = self.zeros_u(), self.zeros_p()
+        B.check(self._lib.stokes_load_vectors(self._h, self._chk(f_nodal, self.shape_u, "f_nodal"),
+                                              self._chk(g_nodal, self.shape_p, "g_nodal"), int(project_g),
+                                              _ptr(f), _ptr(g)), "stokes_load_vectors")
+        return f, g
+
+    def solve(self, f, g, tol=1e-10, max_cycles=100, u=None, p=None, raise_on_fail=False):
+        u = self.zeros_u() if u is None else u
+        p = self.zeros_p() if p is None else p
+        rep = B.Report()
+        hist = (ctypes.c_double * (max_cycles + 1))()
+        st = self._lib.stokes_solve(self._h, self._chk(u, self.shape_u, "u"), self._chk(p, self.shape_p, "p"),
+                                    self._chk(f, self.shape_u, "f"), self._chk(g, self.shape_p, "g"),
+                                    float(tol), int(max_cycles), ctypes.byref(rep), hist)
+        if st not in (B.OK, B.NOT_CONVERGED, B.DIVERGED) or (raise_on_fail and st != B.OK):
+            B.check(st, "stokes_solve")
+        return u, p, Report(rep, [hist[i] for i in range(rep.cycles + 1)], st)
+
+    def cycle(self, u, p, f, g):
+        B.check(self._lib.stokes_cycle(self._h, self._chk(u, self.shape_u, "u"), self._chk(p, self.shape_p, "p"),
+                                       self._chk(f, self.shape_u, "f"), self._chk(g, self.shape_p, "g")),
+                "stokes_cycle")
+        return u, p
+
+    def residual(self, u, p, f, g):
+        ru, rp = self.zeros_u(), self.zeros_p()
+        B.check(self._lib.stokes_residual(self._h, self._chk(u, self.shape_u, "u"), self._chk(p, self.shape_p, "p"),
+                                          self._chk(f, self.shape_u, "f"), self._chk(g, self.shape_p, "g"),
+                                          _ptr(ru), _ptr(rp)), "stokes_residual")
+        return ru, rp
+
+    def residual_norm(self, u, p, f, g):
+        out = ctypes.c_double()
+        B.check(self._lib.stokes_residual_norm(self._h, self._chk(u, self.shape_u, "u"),
+                                               self._chk(p, self.shape_p, "p"), self._chk(f, self.shape_u, "f"),
+                                               self._chk(g, self.shape_p, "g"), ctypes.byref(out)),
+                "stokes_residual_norm")
+        return out.value
+
+    def smooth(self, u, p, f, g, nu=1):
+        B.check(self._lib.stokes_smooth(self._h, self._chk(u, self.shape_u, "u"), self._chk(p, self.shape_p, "p"),
+                                        self._chk(f, self.shape_u, "f"), self._chk(g, self.shape_p, "g"), int(nu)),
+                "stokes_smooth")
+        return u, p
+
+    def _coarse_shapes(self):
+        nc = self.N // 2
+        return (2, 2 * nc + 1, 2 * nc + 1), (nc + 1, nc + 1)
+
+    def restrict(self, ru, rp):
+        su, sp = self._coarse_shapes()
+        fc = torch.zeros(su, dtype=torch.float64, device=self.device)
+        gc = torch.zeros(sp, dtype=torch.float64, device=self.device)
+        B.check(self._lib.stokes_restrict(self._h, self._chk(ru, self.shape_u, "ru"), self._chk(rp, self.shape_p, "rp"),
+                                          _ptr(fc), _ptr(gc)), "stokes_restrict")
+        return fc, gc
+
+    def prolong_add(self, uc, pc, u, p):
+        su, sp = self._coarse_shapes()
+        B.check(self._lib.stokes_prolong_add(self._h, self._chk(uc, su, "uc"), self._chk(pc, sp, "pc"),
+                                             self._chk(u, self.shape_u, "u"), self._chk(p, self.shape_p, "p")),
+                "stokes_prolong_add")
+        return u, p
+
+    def set_timing(self, enable=True):
+        B.check(self._lib.stokes_set_timing(self._h, int(enable)), "stokes_set_timing")
+
+    def timing(self):
+        """(smoothing ms total, smoothing steps, residual ms total, residual launches) since set_timing."""
+        sm, rm = ctypes.c_double(), ctypes.c_double()
+        sc, rc = ctypes.c_longlong(), ctypes.c_longlong()
+        B.check(self._lib.stokes_get_timing(self._h, ctypes.byref(sm), ctypes.byref(sc), ctypes.byref(rm),
+                                            ctypes.byref(rc)), "stokes_get_timing")
+        return sm.value, sc.value, rm.value, rc.value
+
+    def kernel_launches(self):
+        return int(self._lib.stokes_kernel_launches(self._h))
+
+    def mass_dot(self, a, b):
+        out = ctypes.c_double()
+        B.check(self._lib.stokes_mass_dot(self._h, self._chk(a, self.shape_u, "a"), self._chk(b, self.shape_u, "b"),
+                                          ctypes.byref(out)), "stokes_mass_dot")
+        return out.value
