@@ -1,0 +1,410 @@
+#!/usr/bin/env python
+"""Benchmark: robust coupled multigrid solves of the generalized Stokes system on one GB300.
+
+Workload (one "step"): the robustness sweep at h = 1/512 (level k = 8, 2,356,227 unknowns):
+six solves, beta in {0, 1, 1e2, 1e4, 1e6, 1e8}, f and g with i.i.d. uniform[-1, 1] nodal values
+(seed 1 + rank, g shifted to zero mean), each from zero to 1e-8 relative residual (float64) with
+V(3,3) Uzawa cycles (tau = sigma = 0.8).  The headline path is float32 cycles inside float64
+iterative refinement (--precision mixed, default); the plain float64 multigrid is timed on the same
+workload for comparison.
+
+Metric: unknowns solved per second (DoF/s) = 6 x 2,356,227 x steps x ranks / time.
+Multi-GPU: every rank solves its own sweep (independent problems, no collective on the data path):
+weak scaling.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BETAS = [0.0, 1.0, 1e2, 1e4, 1e6, 1e8]
+K_LEVEL = 8
+TOL = 1e-8
+METRIC = "DoF/s to 1e-8 relative residual (robustness sweep h=1/512, 6 beta values)"
+WORKLOAD = ("robustness sweep: unit square, Taylor-Hood P2-P1, h=1/512 (k=8, 2356227 DoF), "
+            "beta in {0,1,1e2,1e4,1e6,1e8}, f,g uniform[-1,1] nodal (seed 1, g zero-mean), "
+            "V(3,3) Uzawa tau=sigma=0.8, solve from 0 to 1e-8 relative residual")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=2, help="steps of the plain float64 comparison")
+    return ap.parse_args()
+
+
+def dofs(k):
+    n = 2 ** (k + 1)
+    return 2 * (2 * n - 1) ** 2 + (n + 1) ** 2
+
+
+def golden_cycles():
+    """Cycle counts to 1e-8 per beta, written by the oracle (tests/golden/make_sweep_golden.py)."""
+    path = os.path.join(ROOT, "tests", "golden", "sweep_k8.json")
+    with open(path) as fh:
+        g = json.load(fh)
+    return {r["beta"]: r["cycles"] for r in g["k8_sweep"]["runs"]}
+
+
+# ------------------------------------------------------------------------------ CPU oracle
+def oracle_sample(n_cycles_per_beta=1, betas=(1.0,)):
+    """Times the oracle (CPU float64 SciPy, as it stands) on a bounded sample of the workload:
+    n_cycles_per_beta V-cycles per listed beta at k = 8; scaled to DoF/s with the oracle's own
+    cycle counts to 1e-8 for the full sweep.  Setup (assembly) is excluded and reported."""
+    import numpy as np
+
+    from oracle import fem
+    from oracle import multigrid as mg
+    from paper_1502_04070_gb300 import workloads
+
+    t0 = time.perf_counter()
+    ds = fem.discretizations(K_LEVEL + 1)
+    d = ds[-1]
+    fn, gn = workloads.random_nodal(K_LEVEL, 1)
+    F = d.load(fn, gn, project_g=True)
+    hs = {b: mg.Hierarchy(K_LEVEL + 1, b, ds) for b in betas}
+    setup = time.perf_counter() - t0
+    per_cycle = {}
+    for b in betas:
+        x = np.zeros_like(F)
+        t = time.perf_counter()
+        for _ in range(n_cycles_per_beta):
+            x = hs[b].project_mean(K_LEVEL, hs[b].cycle(K_LEVEL, x, F, mg.Params()))
+        per_cycle[b] = (time.perf_counter() - t) / n_cycles_per_beta
+    return per_cycle, setup
+
+
+def oracle_dofs_per_s(per_cycle):
+    cyc = golden_cycles()
+    mean_cycle = statistics.mean(per_cycle.values())
+    total_time = sum(per_cycle.get(b, mean_cycle) * cyc[b] for b in BETAS)
+    return len(BETAS) * dofs(K_LEVEL) / total_time
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from oracle import fem
+    from oracle import multigrid as mg
+    from paper_1502_04070_gb300 import workloads
+    import numpy as np
+
+    t0 = time.perf_counter()
+    ds = fem.discretizations(K_LEVEL + 1)
+    d = ds[-1]
+    fn, gn = workloads.random_nodal(K_LEVEL, 1)
+    F = d.load(fn, gn, project_g=True)
+    hs = {b: mg.Hierarchy(K_LEVEL + 1, b, ds) for b in BETAS}
+    setup = time.perf_counter() - t0
+    xs = {b: np.zeros_like(F) for b in BETAS}
+
+    def step(i):
+        b = BETAS[i % len(BETAS)]
+        t = time.perf_counter()
+        xs[b] = hs[b].project_mean(K_LEVEL, hs[b].cycle(K_LEVEL, xs[b], F, mg.Params()))
+        return b, time.perf_counter() - t
+
+    for i in range(args.warmup):
+        step(i)
+    times = {}
+    t = time.perf_counter()
+    for i in range(args.steps):
+        b, dt = step(args.warmup + i)
+        times.setdefault(b, []).append(dt)
+    wall = time.perf_counter() - t
+    per_cycle = {b: statistics.mean(v) for b, v in times.items()}
+    value = oracle_dofs_per_s(per_cycle)
+    sample = ("%d oracle V(3,3) cycles at k=8 (one per step, beta rotating over the sweep), scaled by "
+              "the oracle's own cycle counts to 1e-8 (tests/golden/sweep_k8.json); assembly %.1f s excluded"
+              % (args.steps, setup))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * wall / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------ ours
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_1502_04070_gb300 import workloads
+    from paper_1502_04070_gb300.solver import Solver
+
+    torch.cuda.set_device(local_rank)
+    dist = world > 1
+    if dist:
+        import torch.distributed as td
+
+    def barrier():
+        if dist:
+            td.barrier()
+
+    def max_over_ranks(v):
+        if not dist:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        td.all_reduce(t, op=td.ReduceOp.MAX)
+        return float(t.item())
+
+    levels = K_LEVEL + 1
+    fn_np, gn_np = workloads.random_nodal(K_LEVEL, 1 + rank)
+    fn_h = torch.from_numpy(fn_np).pin_memory()
+    gn_h = torch.from_numpy(gn_np).pin_memory()
+    fn, gn = fn_h.cuda(), gn_h.cuda()
+
+    def make(prec):
+        return {b: Solver(levels, b, precision=prec) for b in BETAS}
+
+    solvers = make(args.precision)
+    S0 = solvers[BETAS[0]]
+    f, g = S0.load_vectors(fn, gn, project_g=True)
+    us = {b: S0.zeros_u() for b in BETAS}
+    ps = {b: S0.zeros_p() for b in BETAS}
+    flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")   # > 129 MB L2
+
+    reports = {}
+
+    def step(sv):
+        for b in BETAS:
+            us[b].zero_()
+            ps[b].zero_()
+            _, _, rep = sv[b].solve(f, g, tol=TOL, max_cycles=100, u=us[b], p=ps[b])
+            if not rep.converged:
+                raise RuntimeError("beta=%g did not converge: %r" % (b, rep))
+            reports[b] = rep
+
+    for s in solvers.values():
+        s.set_timing(True)
+    for _ in range(args.warmup):
+        step(solvers)
+    for s in solvers.values():
+        s.set_timing(True)        # reset the accumulated kernel timings
+    launches0 = sum(s.kernel_launches() for s in solvers.values())
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        step(solvers)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    launches = sum(s.kernel_launches() for s in solvers.values()) - launches0
+    n_dof = dofs(K_LEVEL)
+    value = len(BETAS) * n_dof * args.steps * world / (ms / 1000.0)
+    cycles = {str(b): reports[b].cycles for b in BETAS}
+    rates = {str(b): round(reports[b].mean_rate, 4) for b in BETAS}
+
+    # kernel timings (CUDA events recorded inside the captured cycle, on the library's stream)
+    sm_ms = sm_n = rs_ms = rs_n = 0.0
+    for s in solvers.values():
+        a, b_, c, d = s.timing()
+        sm_ms += a
+        sm_n += b_
+        rs_ms += c
+        rs_n += d
+    N = 2 ** (K_LEVEL + 1)
+    word = 4 if args.precision == "mixed" else 8
+    # Uzawa step on the finest level: read u (8N^2), f (8N^2), p, g, Shat^{-1} (N^2 each);
+    # write u (8N^2), p (N^2): 28 N^2 words
+    smooth_bytes = 28 * N * N * word
+    # float64 residual: read x and F (18 N^2 float64), write r (9 N^2, float32 in mixed mode)
+    resid_bytes = 18 * N * N * 8 + 9 * N * N * word
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
+    hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
+    sm_avg = sm_ms / max(sm_n, 1)
+    rs_avg = rs_ms / max(rs_n, 1)
+    kernels = {
+        "uzawa_step_finest": {"ms_per_launch": sm_avg, "launches": int(sm_n), "total_ms": sm_ms,
+                              "algorithmic_bytes": smooth_bytes,
+                              "achieved_gbs": smooth_bytes / (sm_avg * 1e6) if sm_avg > 0 else None},
+        "residual_fp64_finest": {"ms_per_launch": rs_avg, "launches": int(rs_n), "total_ms": rs_ms,
+                                 "algorithmic_bytes": resid_bytes,
+                                 "achieved_gbs": resid_bytes / (rs_avg * 1e6) if rs_avg > 0 else None},
+    }
+    dom = max(kernels, key=lambda k: kernels[k]["total_ms"])
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        try:
+            tj = json.load(open(tpath))
+            ent = tj.get(args.precision, {}).get(dom)
+            if ent and ent.get("source_sha") == _kernel_source_sha():
+                traffic = ent["bytes_per_launch"]
+        except Exception:
+            traffic = None
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": kernels[dom]["achieved_gbs"], "peak": hbm_peak,
+                "unit": "GB/s", "frac": (kernels[dom]["achieved_gbs"] or 0.0) / hbm_peak,
+                "traffic": traffic, "peak_source": "measured" if peaks else "fallback",
+                "note": "algorithmic bytes per launch / CUDA-event duration inside the timed solves"}
+
+    # ---------------------------------------------------------------- end to end (host buffers)
+    e2e_steps = max(1, min(args.steps, 3))
+    h2d = (fn_h.numel() + gn_h.numel()) * 8 * len(BETAS)
+    d2h = (us[0.0].numel() + ps[0.0].numel()) * 8 * len(BETAS)
+    u_host = {b: torch.empty(us[b].shape, dtype=torch.float64).pin_memory() for b in BETAS}
+    p_host = {b: torch.empty(ps[b].shape, dtype=torch.float64).pin_memory() for b in BETAS}
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for b in BETAS:
+            fd = fn_h.to("cuda", non_blocking=True)
+            gd = gn_h.to("cuda", non_blocking=True)
+            ff, gg = solvers[b].load_vectors(fd, gd, project_g=True)
+            u, p, rep = solvers[b].solve(ff, gg, tol=TOL, max_cycles=100)
+            u_host[b].copy_(u)
+            p_host[b].copy_(p)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_value = len(BETAS) * n_dof * e2e_steps * world / e2e_s
+
+    # ---------------------------------------------------------------- plain float64 comparison
+    fp64 = None
+    if args.precision == "mixed" and args.fp64_steps > 0:
+        s64 = make("fp64")
+        step(s64)   # warm-up (graph capture)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.fp64_steps):
+            step(s64)
+        torch.cuda.synchronize()
+        dt = max_over_ranks(time.perf_counter() - t0)
+        v64 = len(BETAS) * n_dof * args.fp64_steps * world / dt
+        fp64 = {"value": v64, "unit": "DoF/s", "ms_per_step": 1000 * dt / args.fp64_steps,
+                "cycles": {str(b): reports[b].cycles for b in BETAS}, "speedup_of_mixed": value / v64}
+        for s in s64.values():
+            s.close()
+
+    # ---------------------------------------------------------------- CPU oracle baseline
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        per_cycle, setup = oracle_sample(n_cycles_per_beta=2, betas=(1.0,))
+        cpu = {"value": oracle_dofs_per_s(per_cycle), "unit": "DoF/s", "cores": 1, "kind": "oracle",
+               "sample": "2 oracle V(3,3) cycles at k=8, beta=1 (%.2f s each), scaled by the oracle's cycle "
+                         "counts to 1e-8 over the 6-beta sweep; SciPy CSR products run on 1 core; "
+                         "assembly %.1f s excluded; host has %d cores" % (per_cycle[1.0], setup, os.cpu_count())}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32 cycles + f64 refinement" if args.precision == "mixed" else "f64",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "precision": args.precision, "dof_per_solve": n_dof,
+                           "solves_per_step": len(BETAS), "solves_per_s": len(BETAS) * args.steps * world / (ms / 1000),
+                           "l2": "256 MB buffer written between steps (inside the timed region)",
+                           "cycles_per_beta": cycles, "mean_rate_per_beta": rates},
+                "roofline": roofline, "kernels": kernels, "clocks": clk,
+                "e2e": {"value": e2e_value, "unit": "DoF/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                        "steps": e2e_steps},
+                "gpu_launches": int(launches), "fp64_plain": fp64, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+
+
+def _kernel_source_sha():
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1502_04070_gb300", "csrc")
+    for nm in sorted(os.listdir(csrc)):
+        if nm.endswith((".cu", ".cuh", ".h", ".cpp")):
+            h.update(open(os.path.join(csrc, nm), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    from paper_1502_04070_gb300 import build as _b
+    _b.build()
+    if world > 1:
+        import torch
+        import torch.distributed as td
+        torch.cuda.set_device(local_rank)
+        td.init_process_group(backend="nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as td
+        td.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

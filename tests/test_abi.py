@@ -1,0 +1,67 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every entry point that
+include/stokes_mg.h declares (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", fn)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*[A-Za-z_][\w\s\*]*?\b(stokes_\w+)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1502_04070_gb300 import _binding, build
+    build.build()
+    lib = _binding.load()
+    names = declared_functions()
+    assert len(names) >= 15
+    for nm in sorted(names):
+        assert hasattr(lib, nm), nm
+        assert nm in _binding.SIGNATURES, "binding lacks " + nm
+
+
+def test_status_strings_and_defaults_without_gpu():
+    from paper_1502_04070_gb300 import _binding
+    lib = _binding.load()
+    assert lib.stokes_status_str(0) == b"ok"
+    assert lib.stokes_status_str(5) == b"diverged"
+    prm = _binding.Params()
+    lib.stokes_default_params(ctypes.byref(prm), 5, 1.0)
+    assert (prm.nu_pre, prm.nu_post, prm.tau, prm.sigma, prm.gamma) == (3, 3, 0.8, 0.8, 1)
+
+
+def test_setup_rejects_bad_arguments_without_touching_the_gpu():
+    from paper_1502_04070_gb300 import _binding
+    lib = _binding.load()
+    h = ctypes.c_void_p()
+    prm = _binding.Params()
+    lib.stokes_default_params(ctypes.byref(prm), 0, 1.0)        # levels < 1
+    assert lib.stokes_setup(ctypes.byref(prm), None, ctypes.byref(h)) == _binding.ERR_BAD_ARG
+    lib.stokes_default_params(ctypes.byref(prm), 4, -1.0)       # beta < 0
+    assert lib.stokes_setup(ctypes.byref(prm), None, ctypes.byref(h)) == _binding.ERR_BAD_ARG
+    lib.stokes_default_params(ctypes.byref(prm), 4, float("nan"))
+    assert lib.stokes_setup(ctypes.byref(prm), None, ctypes.byref(h)) == _binding.ERR_BAD_ARG
+    assert lib.stokes_setup(None, None, ctypes.byref(h)) == _binding.ERR_BAD_ARG
+
+
+def test_product_path_fails_loudly_without_library(tmp_path):
+    from paper_1502_04070_gb300 import _binding
+    saved = _binding._lib
+    try:
+        _binding._lib = None
+        with pytest.raises(RuntimeError):
+            _binding.load(str(tmp_path / "missing.so"))
+    finally:
+        _binding._lib = saved
