@@ -42,7 +42,53 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=2, help="steps of the plain float64 comparison")
+    ap.add_argument("--kernel", default=None, choices=["uzawa_f32", "uzawa_f64", "residual_f64", "mixed_solve"],
+                    help="microbenchmark one kernel (for profiler captures) instead of the workload")
+    ap.add_argument("--level", type=int, default=9)
+    ap.add_argument("--reps", type=int, default=5)
     return ap.parse_args()
+
+
+def run_kernel(args):
+    """Runs one hot kernel alone on level --level with random data (profiler captures)."""
+    import numpy as np
+    import torch
+
+    from paper_1502_04070_gb300 import workloads
+    from paper_1502_04070_gb300.solver import Solver
+
+    k = args.level
+    u, p = workloads.random_state(k, 5)
+    f, g = workloads.random_nodal(k, 6)
+    g = g - g.mean()
+    prec = "mixed" if args.kernel in ("uzawa_f32", "mixed_solve") else "fp64"
+    S = Solver(k + 1, 1e4, precision=prec)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if args.kernel == "uzawa_f32":
+        t = [torch.from_numpy(a).cuda().float().contiguous() for a in (u, p, f, g)]
+        S.smooth_f32(*t, 1)
+        torch.cuda.synchronize()
+        ev0.record()
+        S.smooth_f32(*t, args.reps)
+    elif args.kernel in ("uzawa_f64", "residual_f64"):
+        t = [torch.from_numpy(a).cuda().contiguous() for a in (u, p, f, g)]
+        S.smooth(*t, 1) if args.kernel == "uzawa_f64" else S.residual(*t)
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(args.reps):
+            S.smooth(*t, 1) if args.kernel == "uzawa_f64" else S.residual(*t)
+    else:
+        fn, gn = torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda()
+        F, G = S.load_vectors(fn, gn, project_g=True)
+        S.solve(F, G, tol=1e-8, max_cycles=3)
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(args.reps):
+            S.solve(F, G, tol=1e-8, max_cycles=3)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.reps
+    print(json.dumps({"kernel": args.kernel, "level": k, "ms_per_rep": ms}), flush=True)
 
 
 def dofs(k):
@@ -280,8 +326,11 @@ def run_ours(args, rank, world, local_rank):
     # Uzawa step on the finest level: read u (8N^2), f (8N^2), p, g, Shat^{-1} (N^2 each);
     # write u (8N^2), p (N^2): 28 N^2 words
     smooth_bytes = 28 * N * N * word
-    # float64 residual: read x and F (18 N^2 float64), write r (9 N^2, float32 in mixed mode)
-    resid_bytes = 18 * N * N * 8 + 9 * N * N * word
+    # outer step on the finest level.  fp64: the float64 residual reads x and F (18 N^2 words) and
+    # writes r (9 N^2).  mixed: the refinement update reads e (9 N^2 float32), x and r (float64),
+    # writes x, r (float64) and r32 (float32): 9 N^2 (4 + 8 + 8 + 8 + 8 + 4) bytes
+    resid_name = "ir_update_finest" if args.precision == "mixed" else "residual_fp64_finest"
+    resid_bytes = 9 * N * N * 40 if args.precision == "mixed" else 27 * N * N * 8
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
     hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
@@ -291,7 +340,7 @@ def run_ours(args, rank, world, local_rank):
         "uzawa_step_finest": {"ms_per_launch": sm_avg, "launches": int(sm_n), "total_ms": sm_ms,
                               "algorithmic_bytes": smooth_bytes,
                               "achieved_gbs": smooth_bytes / (sm_avg * 1e6) if sm_avg > 0 else None},
-        "residual_fp64_finest": {"ms_per_launch": rs_avg, "launches": int(rs_n), "total_ms": rs_ms,
+        resid_name: {"ms_per_launch": rs_avg, "launches": int(rs_n), "total_ms": rs_ms,
                                  "algorithmic_bytes": resid_bytes,
                                  "achieved_gbs": resid_bytes / (rs_avg * 1e6) if rs_avg > 0 else None},
     }
@@ -387,6 +436,11 @@ def _kernel_source_sha():
 
 def main():
     args = parse()
+    if args.kernel:
+        from paper_1502_04070_gb300 import build as _b
+        _b.build()
+        run_kernel(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -45,7 +45,7 @@ typedef enum stokes_status {
     STOKES_ERR_OOM = 2,          /* device allocation failed */
     STOKES_ERR_CUDA = 3,         /* a CUDA runtime call failed */
     STOKES_NOT_CONVERGED = 4,    /* solve reached max_cycles above tol (result still returned) */
-    STOKES_DIVERGED = 5,         /* residual became NaN/Inf or grew 1e3-fold over the initial one */
+    STOKES_DIVERGED = 5,         /* residual became NaN/Inf or grew in 8 consecutive cycles */
     STOKES_ERR_TIMEOUT = 6       /* a bounded device-side wait gave up (batched persistent kernel) */
 } stokes_status;
 
@@ -126,6 +126,11 @@ stokes_status stokes_residual_norm(stokes_handle* h, const double* u, const doub
 /* nu steps of the configured smoother (Sec. 4) on the finest level, in place on (u, p), with the
  * float64 arithmetic of the FP64 path.  Exposed for verification of the smoother alone. */
 stokes_status stokes_smooth(stokes_handle* h, double* u, double* p, const double* f, const double* g, int nu);
+
+/* nu steps of the float32 smoother used inside STOKES_MIXED refinement (the fused one-kernel Uzawa
+ * step), on float32 arrays of the finest-level layouts; requires a STOKES_MIXED handle.  Exposed for
+ * verification of the float32 path alone. */
+stokes_status stokes_smooth_f32(stokes_handle* h, float* u, float* p, const float* f, const float* g, int nu);
 
 /* Canonical transfers (Sec. 3) between finest level k and level k-1 (requires levels >= 2):
  * restriction  (fc, gc) = I_k^{k-1} (fu, fp)   with coarse layouts of level k-1,

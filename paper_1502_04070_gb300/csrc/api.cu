@@ -136,6 +136,7 @@ struct stokes_handle_t {
     double* scal = nullptr;                 // device scalars
     double* hscal = nullptr;                // pinned host mirror
     MassCoef<double> mass{};
+    OpCoef<float> chi{}, clo{};             // MIXED: finest float64 coefficients split hi + lo
     cudaGraphExec_t step = nullptr;         // one cycle + projection + residual norm
     int step_kernels = 0;                   // kernel nodes in `step`
     unsigned long long launches = 0;        // kernels launched by this handle (graph nodes included)
@@ -164,21 +165,36 @@ void ev_end(stokes_handle* h, int k) {
     if (k >= 0) cudaEventRecordWithFlags(h->ev[2 * k + 1], h->st, cudaEventRecordExternal);
 }
 
+// nu smoothing steps on level lv.  The state is in (u, p) when `sw` is false and in (tu, tp)
+// when true; returns where it is afterwards.  The fused float32 Uzawa kernel writes the other
+// buffer pair (ping-pong); the float64 and normal-equation steps work in place and use the other
+// pair as scratch.
 template <typename T>
-void smooth_level(stokes_handle* h, Level<T>& lv, int steps, bool timed = false) {
+bool smooth_level(stokes_handle* h, Level<T>& lv, int steps, bool timed, bool sw) {
     const stokes_params& P = h->prm;
+    const bool fused = sizeof(T) == 4 && P.smoother == STOKES_UZAWA;
     for (int s = 0; s < steps; ++s) {
         const int k = timed ? ev_begin(h) : -1;
         if (k >= 0) h->ev_smooth++;
-        if (P.smoother == STOKES_NORMAL_EQ)
-            launch_normal_eq<T>(h->st, lv.n, lv.c, (T)P.tau, lv.u, lv.p, lv.f, lv.g, lv.sinv, lv.tu, lv.tp);
-        else
-            launch_uzawa<T>(h->st, lv.n, lv.c, (T)P.tau, (T)P.sigma, lv.u, lv.p, lv.f, lv.g, lv.sinv, lv.tu, lv.tp);
+        T* xu = sw ? lv.tu : lv.u;
+        T* xp = sw ? lv.tp : lv.p;
+        T* ou = sw ? lv.u : lv.tu;
+        T* op = sw ? lv.p : lv.tp;
+        if (P.smoother == STOKES_NORMAL_EQ) {
+            launch_normal_eq<T>(h->st, lv.n, lv.c, (T)P.tau, xu, xp, lv.f, lv.g, lv.sinv, ou, op);
+        } else if (fused) {
+            launch_uzawa_fused<T>(h->st, lv.n, lv.c, (T)P.tau, (T)P.sigma, xu, xp, lv.f, lv.g, lv.sinv, ou, op);
+            sw = !sw;
+        } else {
+            launch_uzawa<T>(h->st, lv.n, lv.c, (T)P.tau, (T)P.sigma, xu, xp, lv.f, lv.g, lv.sinv, ou, op);
+        }
         ev_end(h, k);
     }
+    return sw;
 }
 
-// Sec. 3: one multigrid iteration on level l of hierarchy H (x = (u, p), F = (f, g) of the level)
+// Sec. 3: one multigrid iteration on level l of hierarchy H (x = (u, p), F = (f, g) of the level);
+// the iterate is in (u, p) on entry and on exit.
 template <typename T>
 void mg_cycle(stokes_handle* h, std::vector<Level<T>>& H, int l) {
     Level<T>& lv = H[l];
@@ -187,26 +203,35 @@ void mg_cycle(stokes_handle* h, std::vector<Level<T>>& H, int l) {
         return;
     }
     const bool top = l == (int)H.size() - 1;
-    smooth_level(h, lv, h->prm.nu_pre, top);
+    bool sw = smooth_level(h, lv, h->prm.nu_pre, top, false);
+    T* xu = sw ? lv.tu : lv.u;
+    T* xp = sw ? lv.tp : lv.p;
+    T* ru = sw ? lv.u : lv.tu;
+    T* rp = sw ? lv.p : lv.tp;
     Level<T>& cl = H[l - 1];
-    launch_residual<T, T>(h->st, lv.n, lv.c, lv.u, lv.p, lv.f, lv.g, lv.tu, lv.tp, nullptr);
-    launch_restrict<T>(h->st, cl.n, lv.tu, lv.tp, cl.f, cl.g);
+    launch_residual<T, T>(h->st, lv.n, lv.c, xu, xp, lv.f, lv.g, ru, rp, nullptr);
+    launch_restrict<T>(h->st, cl.n, ru, rp, cl.f, cl.g);
     cudaMemsetAsync(cl.u, 0, 2 * cl.n2 * sizeof(T), h->st);
     cudaMemsetAsync(cl.p, 0, cl.n1 * sizeof(T), h->st);
     for (int r = 0; r < h->prm.gamma; ++r) mg_cycle(h, H, l - 1);
-    launch_prolong_add<T>(h->st, cl.n, cl.u, cl.p, lv.u, lv.p);
-    smooth_level(h, lv, h->prm.nu_post, top);
+    launch_prolong_add<T>(h->st, cl.n, cl.u, cl.p, xu, xp);
+    sw = smooth_level(h, lv, h->prm.nu_post, top, sw);
+    if (sw) {   // odd number of ping-pong steps: bring the iterate back to (u, p)
+        cudaMemcpyAsync(lv.u, lv.tu, 2 * lv.n2 * sizeof(T), cudaMemcpyDeviceToDevice, h->st);
+        cudaMemcpyAsync(lv.p, lv.tp, lv.n1 * sizeof(T), cudaMemcpyDeviceToDevice, h->st);
+    }
 }
 
-// residual norm^2 of the finest FP64 state into scal[0]; in MIXED mode the residual is also the
-// float32 right-hand side of the next correction problem
+// True float64 residual of the finest state, its norm^2 into scal[0].  In MIXED mode the residual
+// is kept in float64 (the finest temporaries) for the refinement updates and copied to float32 as
+// the right-hand side of the next correction problem.
 void residual_norm_fin(stokes_handle* h, bool timed = false) {
     Level<double>& F = h->fin();
     const int k = timed ? ev_begin(h) : -1;
     if (k >= 0) h->ev_resid++;
     if (h->mixed()) {
         Level<float>& E = h->h32.back();
-        launch_residual<double, float>(h->st, F.n, F.c, F.u, F.p, F.f, F.g, E.f, E.g, h->partial);
+        launch_residual<double, double>(h->st, F.n, F.c, F.u, F.p, F.f, F.g, F.tu, F.tp, h->partial, E.f, E.g);
     } else {
         launch_residual<double, double>(h->st, F.n, F.c, F.u, F.p, F.f, F.g, F.tu, F.tp, h->partial);
     }
@@ -222,13 +247,18 @@ void record_step(stokes_handle* h) {
         cudaMemsetAsync(E.u, 0, 2 * E.n2 * sizeof(float), h->st);
         cudaMemsetAsync(E.p, 0, E.n1 * sizeof(float), h->st);
         for (int c = 0; c < h->prm.inner_cycles; ++c) mg_cycle<float>(h, h->h32, h->L - 1);
-        launch_add_f32(h->st, 2 * F.n2, E.u, F.u);
-        launch_add_f32(h->st, F.n1, E.p, F.p);
+        // x += e, r -= A e (float64 storage, error-free float32 products), r32 = float(r)
+        const int k = ev_begin(h);
+        if (k >= 0) h->ev_resid++;
+        launch_ir_update(h->st, F.n, h->chi, h->clo, E.u, E.p, F.u, F.p, F.tu, F.tp, E.f, E.g, h->partial);
+        ev_end(h, k);
+        launch_reduce(h->st, h->partial, cells_blocks(F.n), h->scal);
+        launch_pmean<double>(h->st, F.n, F.p, h->partial, h->scal + 1);
     } else {
         mg_cycle<double>(h, h->h64, h->L - 1);
+        launch_pmean<double>(h->st, F.n, F.p, h->partial, h->scal + 1);
+        residual_norm_fin(h, true);
     }
-    launch_pmean<double>(h->st, F.n, F.p, h->partial, h->scal + 1);
-    residual_norm_fin(h, true);
 }
 
 stokes_status build_graph(stokes_handle* h) {
@@ -293,6 +323,17 @@ stokes_status rebuild_beta(stokes_handle* h) {
     for (auto& lv : h->h32) {
         lv.c = make_coef<float>(lv.n, beta);
         launch_schur_diag<float>(h->st, lv.n, make_coef<double>(lv.n, beta), lv.sinv);
+    }
+    if (h->mixed()) {
+        const OpCoef<double>& c = h->fin().c;
+        const double* src = &c.A[0][0][0];
+        float* hi = &h->chi.A[0][0][0];
+        float* lo = &h->clo.A[0][0][0];
+        const size_t cnt = sizeof(OpCoef<double>) / sizeof(double);
+        for (size_t q = 0; q < cnt; ++q) {
+            hi[q] = (float)src[q];
+            lo[q] = (float)(src[q] - (double)hi[q]);
+        }
     }
     CK(cudaGetLastError());
     double inv[27 * 27];
@@ -388,6 +429,8 @@ stokes_status stokes_setup(const stokes_params* prm, void* stream, stokes_handle
         return STOKES_ERR_BAD_ARG;
     stokes_status s = ensure_weights();
     if (s != STOKES_OK) return s;
+    if (prepare_uzawa_fused<float>() != cudaSuccess || prepare_uzawa_fused<double>() != cudaSuccess)
+        return STOKES_ERR_CUDA;
     stokes_handle* h = new stokes_handle_t();
     h->prm = P;
     h->L = P.levels;
@@ -452,7 +495,7 @@ stokes_status stokes_cycle(stokes_handle* h, double* u, double* p, const double*
     stokes_status s;
     if ((s = copy_in(h, u, p, f, g)) != STOKES_OK) return s;
     if (h->mixed()) {
-        residual_norm_fin(h);   // right-hand side of the float32 correction problem
+        residual_norm_fin(h);   // float64 residual and the float32 right-hand side of the correction
         h->launches += 2;
     }
     if ((s = build_graph(h)) != STOKES_OK) return s;
@@ -480,10 +523,25 @@ stokes_status stokes_solve(stokes_handle* h, double* u, double* p, const double*
     if ((s = read_scalar(h, 0, &r2)) != STOKES_OK) return s;
     double r0 = std::sqrt(r2), r = r0;
     if (history) history[0] = r0;
-    int cycles = 0;
+    int cycles = 0, grow_run = 0;
+    double prev_r = r;
     stokes_status result = STOKES_OK;
-    while (!(r <= tol * nF)) {
-        if (!std::isfinite(r) || r > 1e3 * (r0 > 0 ? r0 : 1.0)) {
+    for (;;) {
+        if (r <= tol * nF) {
+            if (!h->mixed()) break;
+            // the refinement residual is updated, not recomputed: confirm with the true one
+            residual_norm_fin(h);
+            h->launches += 2;
+            if ((s = read_scalar(h, 0, &r2)) != STOKES_OK) return s;
+            r = std::sqrt(r2);
+            if (history) history[cycles] = r;
+            if (r <= tol * nF) break;
+        }
+        // diverged: NaN/Inf, or growth in each of the last 8 cycles (the first cycles from x = 0
+        // may raise the Euclidean residual by orders of magnitude before it decays)
+        grow_run = (cycles > 0 && r > prev_r) ? grow_run + 1 : 0;
+        prev_r = r;
+        if (!std::isfinite(r) || grow_run >= 8) {
             result = STOKES_DIVERGED;
             break;
         }
@@ -541,8 +599,25 @@ stokes_status stokes_smooth(stokes_handle* h, double* u, double* p, const double
     lv.p = p;
     lv.f = const_cast<double*>(f);
     lv.g = const_cast<double*>(g);
-    smooth_level<double>(h, lv, nu);
+    smooth_level<double>(h, lv, nu, false, false);
     h->launches += 3ull * nu;
+    CK(cudaGetLastError());
+    return STOKES_OK;
+}
+
+stokes_status stokes_smooth_f32(stokes_handle* h, float* u, float* p, const float* f, const float* g, int nu) {
+    if (!h || !u || !p || !f || !g || nu < 0 || !h->mixed()) return STOKES_ERR_BAD_ARG;
+    Level<float> lv = h->h32.back();   // coefficients, diagonals and ping-pong partners of the finest level
+    lv.u = u;
+    lv.p = p;
+    lv.f = const_cast<float*>(f);
+    lv.g = const_cast<float*>(g);
+    const bool sw = smooth_level<float>(h, lv, nu, false, false);
+    if (sw) {
+        CK(cudaMemcpyAsync(u, lv.tu, 2 * lv.n2 * sizeof(float), cudaMemcpyDeviceToDevice, h->st));
+        CK(cudaMemcpyAsync(p, lv.tp, lv.n1 * sizeof(float), cudaMemcpyDeviceToDevice, h->st));
+    }
+    h->launches += (unsigned long long)nu;
     CK(cudaGetLastError());
     return STOKES_OK;
 }

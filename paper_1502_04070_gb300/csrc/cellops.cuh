@@ -1,0 +1,163 @@
+// cellops.cuh -- per-cell gather of operator rows (see common.cuh for the cell / square layout).
+//
+// A "view" maps P2-lattice coordinates (X, Y) (or vertex coordinates for pressure) to values; the
+// same row code reads global memory through the read-only path or a shared-memory tile.
+#pragma once
+#include "common.cuh"
+
+namespace smg {
+
+constexpr int BX = 32, BY = 8, NT = BX * BY;
+
+int cells_blocks(int n);
+inline dim3 cells_grid(int n) { return dim3((n + 1 + BX - 1) / BX, (n + 1 + BY - 1) / BY); }
+
+// ------------------------------------------------------------------------------------------
+// rows of the square at position SQ relative to the cell: SQ 0 = (i, j), 1 = (i-1, j),
+// 2 = (i, j-1), 3 = (i-1, j-1).  The cell's vertex is corner Q = SQ of that square.
+__host__ __device__ constexpr int sq_nrows(int SQ) { return SQ == 0 ? 4 : (SQ == 3 ? 1 : 2); }
+__host__ __device__ constexpr int sq_row(int SQ, int r) {
+    // slot 0 = V, 1 = H, 2 = E, 3 = C.  SQ 0: V->0 H->1 E->3 C->4; SQ 1: V->2 E->5; SQ 2: V->6 H->7; SQ 3: V->8
+    return SQ == 0 ? (r == 0 ? 0 : r == 1 ? 1 : r == 2 ? 3 : 4)
+         : SQ == 1 ? (r == 0 ? 2 : 5)
+         : SQ == 2 ? (r == 0 ? 6 : 7)
+                   : 8;
+}
+__host__ __device__ constexpr int sq_slot(int SQ, int r) {
+    return SQ == 0 ? r : SQ == 1 ? (r == 0 ? 0 : 2) : SQ == 2 ? (r == 0 ? 0 : 1) : 0;
+}
+
+template <typename T>
+struct Acc {
+    T au[2][4];   // (A u) at the owned velocity nodes V, H, E, C
+    T bt[2][4];   // (B^T p)
+    T dg[4];      // diag A
+    T bu;         // (B u) at the owned vertex
+};
+
+// value of a P2-lattice array at (X, Y): global memory (read-only path) or a shared tile
+template <typename T>
+struct GView {
+    const T* p;
+    int ld;
+    __device__ __forceinline__ T operator()(int X, int Y) const { return __ldg(p + (size_t)Y * ld + X); }
+};
+template <typename T>
+struct SView {
+    const T* p;
+    int ld, x0, y0;
+    __device__ __forceinline__ T operator()(int X, int Y) const { return p[(Y - y0) * ld + (X - x0)]; }
+};
+template <typename T>
+__device__ __forceinline__ GView<T> gview(const T* p, int ld) { return GView<T>{p, ld}; }
+
+template <bool MASK, typename T, typename V>
+__device__ __forceinline__ void load_sq(const V& u, int n, int si, int sj, T (&v)[9]) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int X = 2 * si + a, Y = 2 * sj + b;
+            T val = u(X, Y);
+            if (MASK && !interior2(X, Y, n)) val = T(0);
+            v[3 * b + a] = val;
+        }
+}
+
+template <typename T, typename V>
+__device__ __forceinline__ void load_sq_p(const V& p, int si, int sj, T (&q)[4]) {
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int a = 0; a < 2; ++a) q[2 * b + a] = p(si + a, sj + b);
+}
+
+template <bool DA, bool DBT, bool DD, int O, int SQ, int R, typename T>
+__device__ __forceinline__ void sq_rows(const T (&A)[2][9][9], const OpCoef<T>& c, const T (&vx)[9],
+                                        const T (&vy)[9], const T (&pq)[4], Acc<T>& a) {
+    if constexpr (R < sq_nrows(SQ)) {
+        constexpr int L = sq_row(SQ, R), s = sq_slot(SQ, R);
+        if constexpr (DA) {
+            a.au[0][s] += arow<O, L>(A, vx);
+            a.au[1][s] += arow<O, L>(A, vy);
+        }
+        if constexpr (DBT) {
+            a.bt[0][s] += btrow<O, L>(c.Bx, pq);
+            a.bt[1][s] += btrow<O, L>(c.By, pq);
+        }
+        if constexpr (DD) a.dg[s] += A[O][L][L];
+        sq_rows<DA, DBT, DD, O, SQ, R + 1>(A, c, vx, vy, pq, a);
+    }
+}
+
+template <bool DA, bool DBT, bool DB, bool DD, bool MASK, int SQ, typename T, typename VU, typename VP>
+__device__ __forceinline__ void visit(int i, int j, int n, const T (&A)[2][9][9], const OpCoef<T>& c,
+                                      const VU& ux, const VU& uy, const VP& p, Acc<T>& a) {
+    const int si = i - (SQ & 1), sj = j - (SQ >> 1);
+    if (si < 0 || sj < 0 || si >= n || sj >= n) return;
+    T vx[9], vy[9], pq[4];
+    if constexpr (DA || DB) {
+        load_sq<MASK>(ux, n, si, sj, vx);
+        load_sq<MASK>(uy, n, si, sj, vy);
+    }
+    if constexpr (DBT) load_sq_p(p, si, sj, pq);
+    if (orient(si, sj, n)) {
+        sq_rows<DA, DBT, DD, 1, SQ, 0>(A, c, vx, vy, pq, a);
+        if constexpr (DB) a.bu += brow<1, SQ>(c.Bx, vx) + brow<1, SQ>(c.By, vy);
+    } else {
+        sq_rows<DA, DBT, DD, 0, SQ, 0>(A, c, vx, vy, pq, a);
+        if constexpr (DB) a.bu += brow<0, SQ>(c.Bx, vx) + brow<0, SQ>(c.By, vy);
+    }
+}
+
+template <bool DA, bool DBT, bool DB, bool DD, bool MASK, typename T, typename VU, typename VP>
+__device__ __forceinline__ void cell_apply(int i, int j, int n, const T (&A)[2][9][9], const OpCoef<T>& c,
+                                           const VU& ux, const VU& uy, const VP& p, Acc<T>& a) {
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        a.au[0][s] = a.au[1][s] = a.bt[0][s] = a.bt[1][s] = a.dg[s] = T(0);
+    }
+    a.bu = T(0);
+    visit<DA, DBT, DB, DD, MASK, 0>(i, j, n, A, c, ux, uy, p, a);
+    visit<DA, DBT, DB, DD, MASK, 1>(i, j, n, A, c, ux, uy, p, a);
+    visit<DA, DBT, DB, DD, MASK, 2>(i, j, n, A, c, ux, uy, p, a);
+    visit<DA, DBT, DB, DD, MASK, 3>(i, j, n, A, c, ux, uy, p, a);
+}
+
+// lattice position and existence / unknown flags of slot s of cell (i, j)
+__device__ __forceinline__ void slot_pos(int i, int j, int s, int& X, int& Y) {
+    X = 2 * i + (s & 1);
+    Y = 2 * j + (s >> 1);
+}
+__device__ __forceinline__ bool slot_exists(const CellNodes& cn, int s) {
+    return s == 0 ? true : s == 1 ? cn.hx : s == 2 ? cn.ex : cn.cx;
+}
+__device__ __forceinline__ bool slot_unknown(const CellNodes& cn, int s) {
+    return s == 0 ? cn.v : s == 1 ? cn.h : s == 2 ? cn.e : cn.c;
+}
+
+#define CELL_INDEX                                          \
+    const int i = blockIdx.x * BX + threadIdx.x;            \
+    const int j = blockIdx.y * BY + threadIdx.y;            \
+    const bool active = i <= n && j <= n;                   \
+    const int tid = threadIdx.y * BX + threadIdx.x;         \
+    (void)tid;
+
+// Block sum (thread-linear id tid) of one double; result valid in tid 0.
+__device__ __forceinline__ double block_sum2d(double v, int tid) {
+    __shared__ double red[NT / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (tid < 32) {
+        s = tid < NT / 32 ? red[tid] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    }
+    return s;
+}
+
+
+}  // namespace smg

@@ -6,9 +6,12 @@
 // on the two mid-lines x = 1/2, y = 1/2), so that structurally-zero local entries cost nothing.
 #include <cstdio>
 
+#include "cellops.cuh"
 #include "kernels.cuh"
 
 namespace smg {
+
+int cells_blocks(int n) { return ((n + 1 + BX - 1) / BX) * ((n + 1 + BY - 1) / BY); }
 
 __constant__ double c_W2d[2][9][5][5];
 __constant__ float c_W2f[2][9][5][5];
@@ -25,145 +28,6 @@ cudaError_t upload_transfer_weights(const double* P2) {
     return cudaMemcpyToSymbol(c_W2f, tmp, sizeof(float) * 2 * 9 * 25);
 }
 
-constexpr int BX = 32, BY = 8, NT = BX * BY;
-
-int cells_blocks(int n) { return ((n + 1 + BX - 1) / BX) * ((n + 1 + BY - 1) / BY); }
-static dim3 cells_grid(int n) { return dim3((n + 1 + BX - 1) / BX, (n + 1 + BY - 1) / BY); }
-
-// ------------------------------------------------------------------------------------------
-// rows of the square at position SQ relative to the cell: SQ 0 = (i, j), 1 = (i-1, j),
-// 2 = (i, j-1), 3 = (i-1, j-1).  The cell's vertex is corner Q = SQ of that square.
-__host__ __device__ constexpr int sq_nrows(int SQ) { return SQ == 0 ? 4 : (SQ == 3 ? 1 : 2); }
-__host__ __device__ constexpr int sq_row(int SQ, int r) {
-    // slot 0 = V, 1 = H, 2 = E, 3 = C.  SQ 0: V->0 H->1 E->3 C->4; SQ 1: V->2 E->5; SQ 2: V->6 H->7; SQ 3: V->8
-    return SQ == 0 ? (r == 0 ? 0 : r == 1 ? 1 : r == 2 ? 3 : 4)
-         : SQ == 1 ? (r == 0 ? 2 : 5)
-         : SQ == 2 ? (r == 0 ? 6 : 7)
-                   : 8;
-}
-__host__ __device__ constexpr int sq_slot(int SQ, int r) {
-    return SQ == 0 ? r : SQ == 1 ? (r == 0 ? 0 : 2) : SQ == 2 ? (r == 0 ? 0 : 1) : 0;
-}
-
-template <typename T>
-struct Acc {
-    T au[2][4];   // (A u) at the owned velocity nodes V, H, E, C
-    T bt[2][4];   // (B^T p)
-    T dg[4];      // diag A
-    T bu;         // (B u) at the owned vertex
-};
-
-template <bool MASK, typename T>
-__device__ __forceinline__ void load_sq(const T* __restrict__ u, int n, int si, int sj, T (&v)[9]) {
-    const int ld = 2 * n + 1;
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const int X = 2 * si + a, Y = 2 * sj + b;
-            T val = __ldg(u + (size_t)Y * ld + X);
-            if (MASK && !interior2(X, Y, n)) val = T(0);
-            v[3 * b + a] = val;
-        }
-}
-
-template <typename T>
-__device__ __forceinline__ void load_sq_p(const T* __restrict__ p, int n, int si, int sj, T (&q)[4]) {
-    const int ld = n + 1;
-#pragma unroll
-    for (int b = 0; b < 2; ++b)
-#pragma unroll
-        for (int a = 0; a < 2; ++a) q[2 * b + a] = __ldg(p + (size_t)(sj + b) * ld + si + a);
-}
-
-template <bool DA, bool DBT, bool DD, int O, int SQ, int R, typename T>
-__device__ __forceinline__ void sq_rows(const T (&A)[2][9][9], const OpCoef<T>& c, const T (&vx)[9],
-                                        const T (&vy)[9], const T (&pq)[4], Acc<T>& a) {
-    if constexpr (R < sq_nrows(SQ)) {
-        constexpr int L = sq_row(SQ, R), s = sq_slot(SQ, R);
-        if constexpr (DA) {
-            a.au[0][s] += arow<O, L>(A, vx);
-            a.au[1][s] += arow<O, L>(A, vy);
-        }
-        if constexpr (DBT) {
-            a.bt[0][s] += btrow<O, L>(c.Bx, pq);
-            a.bt[1][s] += btrow<O, L>(c.By, pq);
-        }
-        if constexpr (DD) a.dg[s] += A[O][L][L];
-        sq_rows<DA, DBT, DD, O, SQ, R + 1>(A, c, vx, vy, pq, a);
-    }
-}
-
-template <bool DA, bool DBT, bool DB, bool DD, bool MASK, int SQ, typename T>
-__device__ __forceinline__ void visit(int i, int j, int n, const T (&A)[2][9][9], const OpCoef<T>& c,
-                                      const T* __restrict__ ux, const T* __restrict__ uy,
-                                      const T* __restrict__ p, Acc<T>& a) {
-    const int si = i - (SQ & 1), sj = j - (SQ >> 1);
-    if (si < 0 || sj < 0 || si >= n || sj >= n) return;
-    T vx[9], vy[9], pq[4];
-    if constexpr (DA || DB) {
-        load_sq<MASK>(ux, n, si, sj, vx);
-        load_sq<MASK>(uy, n, si, sj, vy);
-    }
-    if constexpr (DBT) load_sq_p(p, n, si, sj, pq);
-    if (orient(si, sj, n)) {
-        sq_rows<DA, DBT, DD, 1, SQ, 0>(A, c, vx, vy, pq, a);
-        if constexpr (DB) a.bu += brow<1, SQ>(c.Bx, vx) + brow<1, SQ>(c.By, vy);
-    } else {
-        sq_rows<DA, DBT, DD, 0, SQ, 0>(A, c, vx, vy, pq, a);
-        if constexpr (DB) a.bu += brow<0, SQ>(c.Bx, vx) + brow<0, SQ>(c.By, vy);
-    }
-}
-
-template <bool DA, bool DBT, bool DB, bool DD, bool MASK, typename T>
-__device__ __forceinline__ void cell_apply(int i, int j, int n, const T (&A)[2][9][9], const OpCoef<T>& c,
-                                           const T* ux, const T* uy, const T* p, Acc<T>& a) {
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-        a.au[0][s] = a.au[1][s] = a.bt[0][s] = a.bt[1][s] = a.dg[s] = T(0);
-    }
-    a.bu = T(0);
-    visit<DA, DBT, DB, DD, MASK, 0>(i, j, n, A, c, ux, uy, p, a);
-    visit<DA, DBT, DB, DD, MASK, 1>(i, j, n, A, c, ux, uy, p, a);
-    visit<DA, DBT, DB, DD, MASK, 2>(i, j, n, A, c, ux, uy, p, a);
-    visit<DA, DBT, DB, DD, MASK, 3>(i, j, n, A, c, ux, uy, p, a);
-}
-
-// lattice position and existence / unknown flags of slot s of cell (i, j)
-__device__ __forceinline__ void slot_pos(int i, int j, int s, int& X, int& Y) {
-    X = 2 * i + (s & 1);
-    Y = 2 * j + (s >> 1);
-}
-__device__ __forceinline__ bool slot_exists(const CellNodes& cn, int s) {
-    return s == 0 ? true : s == 1 ? cn.hx : s == 2 ? cn.ex : cn.cx;
-}
-__device__ __forceinline__ bool slot_unknown(const CellNodes& cn, int s) {
-    return s == 0 ? cn.v : s == 1 ? cn.h : s == 2 ? cn.e : cn.c;
-}
-
-#define CELL_INDEX                                          \
-    const int i = blockIdx.x * BX + threadIdx.x;            \
-    const int j = blockIdx.y * BY + threadIdx.y;            \
-    const bool active = i <= n && j <= n;                   \
-    const int tid = threadIdx.y * BX + threadIdx.x;         \
-    (void)tid;
-
-// Block sum (thread-linear id tid) of one double; result valid in tid 0.
-__device__ __forceinline__ double block_sum2d(double v, int tid) {
-    __shared__ double red[NT / 32];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if ((tid & 31) == 0) red[tid >> 5] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (tid < 32) {
-        s = tid < NT / 32 ? red[tid] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    }
-    return s;
-}
-
 // ------------------------------------------------------------------------------------------
 // r = F - A x  (eq. gen:bil:mv), optional sum of squares
 template <typename T, typename TO>
@@ -171,13 +35,14 @@ __global__ void __launch_bounds__(NT) k_residual(int n, const __grid_constant__ 
                                                  const T* __restrict__ u, const T* __restrict__ p,
                                                  const T* __restrict__ f, const T* __restrict__ g,
                                                  TO* __restrict__ ru, TO* __restrict__ rp,
-                                                 double* __restrict__ partial) {
+                                                 double* __restrict__ partial, float* __restrict__ ru2,
+                                                 float* __restrict__ rp2) {
     CELL_INDEX
     const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
     double ss = 0.0;
     if (active) {
         Acc<T> a;
-        cell_apply<true, true, true, false, true>(i, j, n, c.A, c, u, u + n2, p, a);
+        cell_apply<true, true, true, false, true>(i, j, n, c.A, c, gview(u, 2 * n + 1), gview(u + n2, 2 * n + 1), gview(p, n + 1), a);
         const CellNodes cn = cell_nodes(i, j, n);
         const int ld = 2 * n + 1;
 #pragma unroll
@@ -195,11 +60,13 @@ __global__ void __launch_bounds__(NT) k_residual(int n, const __grid_constant__ 
                     ss += (double)rr * (double)rr;
                 }
                 ru[comp * n2 + idx] = r;
+                if (ru2) ru2[comp * n2 + idx] = (float)r;
             }
         }
         const size_t vi = (size_t)j * (n + 1) + i;
         const T r = g[vi] - a.bu;
         rp[vi] = (TO)r;
+        if (rp2) rp2[vi] = (float)r;
         ss += (double)r * (double)r;
     }
     if (partial) {
@@ -216,7 +83,7 @@ __global__ void __launch_bounds__(NT) k_uzawa_u(int n, const __grid_constant__ O
     if (!active) return;
     const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
     Acc<T> a;
-    cell_apply<true, true, false, true, true>(i, j, n, c.A, c, u, u + n2, p, a);
+    cell_apply<true, true, false, true, true>(i, j, n, c.A, c, gview(u, 2 * n + 1), gview(u + n2, 2 * n + 1), gview(p, n + 1), a);
     const CellNodes cn = cell_nodes(i, j, n);
     const int ld = 2 * n + 1;
 #pragma unroll
@@ -243,7 +110,7 @@ __global__ void __launch_bounds__(NT) k_uzawa_p(int n, const __grid_constant__ O
     if (!active) return;
     const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
     Acc<T> a;
-    cell_apply<false, false, true, false, false>(i, j, n, c.A, c, uh, uh + n2, (const T*)nullptr, a);
+    cell_apply<false, false, true, false, false>(i, j, n, c.A, c, gview(uh, 2 * n + 1), gview(uh + n2, 2 * n + 1), gview((const T*)nullptr, n + 1), a);
     const size_t vi = (size_t)j * (n + 1) + i;
     // p^{m} = p^{m-1} - sigma Shat^{-1} (g - B u^{m-1/2})
     const T d = sigma * sinv[vi] * (a.bu - g[vi]);
@@ -259,7 +126,7 @@ __global__ void __launch_bounds__(NT) k_uzawa_u2(int n, const __grid_constant__ 
     if (!active) return;
     const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
     Acc<T> a;
-    cell_apply<false, true, false, true, false>(i, j, n, c.A, c, (const T*)nullptr, (const T*)nullptr, dp, a);
+    cell_apply<false, true, false, true, false>(i, j, n, c.A, c, gview((const T*)nullptr, 2 * n + 1), gview((const T*)nullptr, 2 * n + 1), gview(dp, n + 1), a);
     const CellNodes cn = cell_nodes(i, j, n);
     const int ld = 2 * n + 1;
 #pragma unroll
@@ -297,8 +164,8 @@ __global__ void __launch_bounds__(NT) k_scale_L(int n, const __grid_constant__ O
     if (!active) return;
     const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
     Acc<T> a;
-    cell_apply<false, false, false, true, false>(i, j, n, c.A, c, (const T*)nullptr, (const T*)nullptr,
-                                                 (const T*)nullptr, a);
+    cell_apply<false, false, false, true, false>(i, j, n, c.A, c, gview((const T*)nullptr, 2 * n + 1),
+                                                 gview((const T*)nullptr, 2 * n + 1), gview((const T*)nullptr, n + 1), a);
     const CellNodes cn = cell_nodes(i, j, n);
     const int ld = 2 * n + 1;
 #pragma unroll
@@ -323,7 +190,7 @@ __global__ void __launch_bounds__(NT) k_normal_update(int n, const __grid_consta
     if (!active) return;
     const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
     Acc<T> a;
-    cell_apply<true, true, true, true, false>(i, j, n, c.A, c, zu, zu + n2, zp, a);
+    cell_apply<true, true, true, true, false>(i, j, n, c.A, c, gview(zu, 2 * n + 1), gview(zu + n2, 2 * n + 1), gview(zp, n + 1), a);
     const CellNodes cn = cell_nodes(i, j, n);
     const int ld = 2 * n + 1;
 #pragma unroll
@@ -343,15 +210,15 @@ template <typename T>
 void launch_normal_eq(cudaStream_t s, int n, const OpCoef<T>& c, T tau, T* u, T* p, const T* f,
                       const T* g, const T* sinv, T* zu, T* zp) {
     const dim3 grid = cells_grid(n), blk(BX, BY);
-    k_residual<T, T><<<grid, blk, 0, s>>>(n, c, u, p, f, g, zu, zp, nullptr);
+    k_residual<T, T><<<grid, blk, 0, s>>>(n, c, u, p, f, g, zu, zp, nullptr, nullptr, nullptr);
     k_scale_L<T><<<grid, blk, 0, s>>>(n, c, zu, zp, sinv);
     k_normal_update<T><<<grid, blk, 0, s>>>(n, c, tau, zu, zp, sinv, u, p);
 }
 
 template <typename T, typename TO>
 void launch_residual(cudaStream_t s, int n, const OpCoef<T>& c, const T* u, const T* p, const T* f,
-                     const T* g, TO* ru, TO* rp, double* partial) {
-    k_residual<T, TO><<<cells_grid(n), dim3(BX, BY), 0, s>>>(n, c, u, p, f, g, ru, rp, partial);
+                     const T* g, TO* ru, TO* rp, double* partial, float* ru2, float* rp2) {
+    k_residual<T, TO><<<cells_grid(n), dim3(BX, BY), 0, s>>>(n, c, u, p, f, g, ru, rp, partial, ru2, rp2);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -663,7 +530,7 @@ __device__ __forceinline__ void mp_row(int i, int j, int n, const MassCoef<T>& m
         if (si < 0 || sj < 0 || si >= n || sj >= n) continue;
         const int o = orient(si, sj, n);
         T q[4];
-        load_sq_p(gn, n, si, sj, q);
+        load_sq_p(gview(gn, n + 1), si, sj, q);
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             mg = fma(m.MP[o][SQ][r], q[r], mg);
@@ -681,7 +548,7 @@ __global__ void __launch_bounds__(NT) k_load(int n, const __grid_constant__ Mass
     double wg = 0.0;
     if (active) {
         Acc<T> a;
-        cell_apply<true, false, false, false, false>(i, j, n, m.M, c, fn, fn + n2, (const T*)nullptr, a);
+        cell_apply<true, false, false, false, false>(i, j, n, m.M, c, gview(fn, 2 * n + 1), gview(fn + n2, 2 * n + 1), gview((const T*)nullptr, n + 1), a);
         const CellNodes cn = cell_nodes(i, j, n);
         const int ld = 2 * n + 1;
 #pragma unroll
@@ -744,7 +611,7 @@ __global__ void __launch_bounds__(NT) k_mass_dot(int n, const __grid_constant__ 
     double acc = 0.0;
     if (active) {
         Acc<double> a;
-        cell_apply<true, false, false, false, true>(i, j, n, m.M, c, bv, bv + n2, (const double*)nullptr, a);
+        cell_apply<true, false, false, false, true>(i, j, n, m.M, c, gview(bv, 2 * n + 1), gview(bv + n2, 2 * n + 1), gview((const double*)nullptr, n + 1), a);
         const CellNodes cn = cell_nodes(i, j, n);
         const int ld = 2 * n + 1;
 #pragma unroll
@@ -820,11 +687,11 @@ INST(float)
 INST(double)
 template void launch_residual<double, double>(cudaStream_t, int, const OpCoef<double>&, const double*,
                                               const double*, const double*, const double*, double*, double*,
-                                              double*);
+                                              double*, float*, float*);
 template void launch_residual<float, float>(cudaStream_t, int, const OpCoef<float>&, const float*, const float*,
-                                            const float*, const float*, float*, float*, double*);
+                                            const float*, const float*, float*, float*, double*, float*, float*);
 template void launch_residual<double, float>(cudaStream_t, int, const OpCoef<double>&, const double*,
                                              const double*, const double*, const double*, float*, float*,
-                                             double*);
+                                             double*, float*, float*);
 
 }  // namespace smg

@@ -13,10 +13,18 @@ int cells_blocks(int n);
 // Transfer weight table (constant memory), set once per device.
 cudaError_t upload_transfer_weights(const double* P2 /* [2][9][5][5] */);
 
-// r = F - A x with per-block partial sums of r.r (over unknowns) in `partial` (may be null).
+// r = F - A x with per-block partial sums of r.r (over unknowns) in `partial` (may be null) and an
+// optional float32 copy of r in (ru2, rp2).
 template <typename T, typename TO>
 void launch_residual(cudaStream_t s, int n, const OpCoef<T>& c, const T* u, const T* p, const T* f,
-                     const T* g, TO* ru, TO* rp, double* partial);
+                     const T* g, TO* ru, TO* rp, double* partial, float* ru2 = nullptr, float* rp2 = nullptr);
+
+// Refinement update (float32 correction e of a float64 iterate x with float64 residual r):
+//   x += e,  r -= A e  (products with error-free float32 transformations, ~2^-48 relative),
+//   r32 = float(r), partial sums of r.r.
+void launch_ir_update(cudaStream_t s, int n, const OpCoef<float>& chi, const OpCoef<float>& clo,
+                      const float* eu, const float* ep, double* xu, double* xp, double* ru, double* rp,
+                      float* r32u, float* r32p, double* partial);
 
 // Uzawa step (Sec. 4), three kernels:
 //   uh = u + tau Ahat^{-1} (f - A u - B^T p)
@@ -25,6 +33,14 @@ void launch_residual(cudaStream_t s, int n, const OpCoef<T>& c, const T* u, cons
 template <typename T>
 void launch_uzawa(cudaStream_t s, int n, const OpCoef<T>& c, T tau, T sigma, T* u, T* p, const T* f,
                   const T* g, const T* sinv, T* uh, T* dp);
+
+// The same Uzawa step fused into one kernel with shared-memory halos: reads (u, p), writes
+// (u_out, p_out) (distinct buffers).
+template <typename T>
+cudaError_t prepare_uzawa_fused();   // raises the kernel's shared-memory limit on the current device
+template <typename T>
+cudaError_t launch_uzawa_fused(cudaStream_t s, int n, const OpCoef<T>& c, T tau, T sigma, const T* u, const T* p,
+                               const T* f, const T* g, const T* sinv, T* u_out, T* p_out);
 
 // Normal-equation step (Sec. 4): x += tau L^{-1} A L^{-1} (F - A x),  L = diag(Ahat, Shat).
 template <typename T>

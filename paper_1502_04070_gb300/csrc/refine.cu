@@ -1,0 +1,144 @@
+// refine.cu -- the float64 side of mixed-precision iterative refinement.
+//
+// Each refinement step solves A e = r approximately with float32 cycles and then updates
+//     x <- x + e,     r <- r - A e
+// in float64 storage.  GB300 has few float64 units, so A e is formed from float32 operations
+// that lose nothing: the float32 correction e is exact, every float64 coefficient is split as
+// c = c_hi + c_lo (two floats), the product c_hi * e is made exact with an FMA (TwoProduct), and
+// the products are summed with TwoSum into a (hi, lo) pair, which is accurate to about 2^-48
+// relative to sum |c| |e|.  Because e shrinks with the residual, the accumulated error of the
+// updated residual stays far below the refinement tolerance; the solver still recomputes the true
+// float64 residual before it reports convergence.
+#include "cellops.cuh"
+#include "kernels.cuh"
+
+namespace smg {
+
+struct DF {
+    float hi, lo;
+};
+
+// s += (chi + clo) * v ; the intrinsics keep the compiler from fusing the exact steps
+__device__ __forceinline__ void df_fma(DF& s, float chi, float clo, float v) {
+    const float p = __fmul_rn(chi, v);
+    const float pe = fmaf(chi, v, -p);            // chi * v = p + pe exactly
+    const float t = __fadd_rn(s.hi, p);           // TwoSum(s.hi, p)
+    const float bb = __fsub_rn(t, s.hi);
+    const float e = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+    s.hi = t;
+    s.lo += e + pe + clo * v;
+}
+
+__device__ __forceinline__ double df_value(const DF& s) { return (double)s.hi + (double)s.lo; }
+
+struct DFAcc {
+    DF au[2][4];
+    DF bu;
+};
+
+template <int O, int SQ, int R>
+__device__ __forceinline__ void sq_rows_df(const OpCoef<float>& h, const OpCoef<float>& l, const float (&vx)[9],
+                                           const float (&vy)[9], const float (&pq)[4], DFAcc& a) {
+    if constexpr (R < sq_nrows(SQ)) {
+        constexpr int L = sq_row(SQ, R), s = sq_slot(SQ, R);
+#pragma unroll
+        for (int m = 0; m < 9; ++m)
+            if (couple(O, L, m)) {
+                df_fma(a.au[0][s], h.A[O][L][m], l.A[O][L][m], vx[m]);
+                df_fma(a.au[1][s], h.A[O][L][m], l.A[O][L][m], vy[m]);
+            }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (couple(O, corner_node(q), L)) {
+                df_fma(a.au[0][s], h.Bx[O][q][L], l.Bx[O][q][L], pq[q]);
+                df_fma(a.au[1][s], h.By[O][q][L], l.By[O][q][L], pq[q]);
+            }
+        sq_rows_df<O, SQ, R + 1>(h, l, vx, vy, pq, a);
+    }
+}
+
+template <int O, int SQ>
+__device__ __forceinline__ void sq_b_df(const OpCoef<float>& h, const OpCoef<float>& l, const float (&vx)[9],
+                                        const float (&vy)[9], DFAcc& a) {
+#pragma unroll
+    for (int m = 0; m < 9; ++m)
+        if (couple(O, corner_node(SQ), m)) {
+            df_fma(a.bu, h.Bx[O][SQ][m], l.Bx[O][SQ][m], vx[m]);
+            df_fma(a.bu, h.By[O][SQ][m], l.By[O][SQ][m], vy[m]);
+        }
+}
+
+template <int SQ>
+__device__ __forceinline__ void visit_df(int i, int j, int n, const OpCoef<float>& h, const OpCoef<float>& l,
+                                         const float* __restrict__ eu, const float* __restrict__ ep, DFAcc& a) {
+    const int si = i - (SQ & 1), sj = j - (SQ >> 1);
+    if (si < 0 || sj < 0 || si >= n || sj >= n) return;
+    const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
+    float vx[9], vy[9], pq[4];
+    load_sq<true>(gview(eu, 2 * n + 1), n, si, sj, vx);
+    load_sq<true>(gview(eu + n2, 2 * n + 1), n, si, sj, vy);
+    load_sq_p(gview(ep, n + 1), si, sj, pq);
+    if (orient(si, sj, n)) {
+        sq_rows_df<1, SQ, 0>(h, l, vx, vy, pq, a);
+        sq_b_df<1, SQ>(h, l, vx, vy, a);
+    } else {
+        sq_rows_df<0, SQ, 0>(h, l, vx, vy, pq, a);
+        sq_b_df<0, SQ>(h, l, vx, vy, a);
+    }
+}
+
+__global__ void __launch_bounds__(NT) k_ir_update(int n, const __grid_constant__ OpCoef<float> ch,
+                                                  const __grid_constant__ OpCoef<float> cl,
+                                                  const float* __restrict__ eu, const float* __restrict__ ep,
+                                                  double* __restrict__ xu, double* __restrict__ xp,
+                                                  double* __restrict__ ru, double* __restrict__ rp,
+                                                  float* __restrict__ r32u, float* __restrict__ r32p,
+                                                  double* __restrict__ partial) {
+    CELL_INDEX
+    const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
+    double ss = 0.0;
+    if (active) {
+        DFAcc a;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) a.au[0][s] = a.au[1][s] = DF{0.f, 0.f};
+        a.bu = DF{0.f, 0.f};
+        visit_df<0>(i, j, n, ch, cl, eu, ep, a);
+        visit_df<1>(i, j, n, ch, cl, eu, ep, a);
+        visit_df<2>(i, j, n, ch, cl, eu, ep, a);
+        visit_df<3>(i, j, n, ch, cl, eu, ep, a);
+        const CellNodes cn = cell_nodes(i, j, n);
+        const int ld = 2 * n + 1;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            if (!slot_unknown(cn, s)) continue;
+            int X, Y;
+            slot_pos(i, j, s, X, Y);
+            const size_t idx = (size_t)Y * ld + X;
+#pragma unroll
+            for (int comp = 0; comp < 2; ++comp) {
+                const size_t k = comp * n2 + idx;
+                xu[k] += (double)eu[k];
+                const double r = ru[k] - df_value(a.au[comp][s]);
+                ru[k] = r;
+                r32u[k] = (float)r;
+                ss += r * r;
+            }
+        }
+        const size_t vi = (size_t)j * (n + 1) + i;
+        xp[vi] += (double)ep[vi];
+        const double r = rp[vi] - df_value(a.bu);
+        rp[vi] = r;
+        r32p[vi] = (float)r;
+        ss += r * r;
+    }
+    const double t = block_sum2d(ss, tid);
+    if (tid == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = t;
+}
+
+void launch_ir_update(cudaStream_t s, int n, const OpCoef<float>& chi, const OpCoef<float>& clo,
+                      const float* eu, const float* ep, double* xu, double* xp, double* ru, double* rp,
+                      float* r32u, float* r32p, double* partial) {
+    k_ir_update<<<cells_grid(n), dim3(BX, BY), 0, s>>>(n, chi, clo, eu, ep, xu, xp, ru, rp, r32u, r32p, partial);
+}
+
+}  // namespace smg

@@ -1,0 +1,195 @@
+// uzawa_fused.cu -- one whole Uzawa smoothing step (Sec. 4) in one kernel.
+//
+//   u^{m-1/2} = u^{m-1} + tau Ahat^{-1} (f - A u^{m-1} - B^T p^{m-1})
+//   dp        = sigma Shat^{-1} (B u^{m-1/2} - g),      p^{m} = p^{m-1} + dp
+//   u^{m}     = u^{m-1/2} - tau Ahat^{-1} B^T dp
+//
+// A CTA owns a TX x TY tile of cells.  It stages u and p with a halo of three cells in shared
+// memory, computes u^{m-1/2} on the tile plus two cells, dp on the tile plus one vertex, and the
+// new (u, p) on the tile, so every HBM word of u, p, f, g, Shat^{-1} is read about once and u, p
+// are written once (the halo re-reads hit L2).  The step reads (u, p) and writes (u_out, p_out):
+// neighbouring tiles still need the old values as halo, so the caller ping-pongs two buffers.
+#include <cstdio>
+
+#include "cellops.cuh"
+#include "kernels.cuh"
+
+namespace smg {
+
+template <typename T, int TX, int TY>
+struct FusedTile {
+    static constexpr int UW = 2 * (TX + 6), UH = 2 * (TY + 6);   // u: cells [i0-3, i0+TX+3)
+    static constexpr int PW = TX + 6, PH = TY + 6;               // p: vertices [i0-3, i0+TX+3)
+    static constexpr int HW = 2 * (TX + 4), HH = 2 * (TY + 4);   // u^{m-1/2}: cells [i0-2, i0+TX+2)
+    static constexpr int DW = TX + 2, DH = TY + 2;               // dp: vertices [i0-1, i0+TX+1)
+    static constexpr int U_OFF = 0;
+    static constexpr int P_OFF = U_OFF + 2 * UW * UH;
+    static constexpr int H_OFF = P_OFF + PW * PH;
+    static constexpr int D_OFF = H_OFF + 2 * HW * HH;
+    static constexpr int TOTAL = D_OFF + DW * DH;
+    static constexpr size_t BYTES = sizeof(T) * (size_t)TOTAL;
+};
+
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY, (sizeof(T) == 4 ? 2 : 1)) k_uzawa_fused(int n, const __grid_constant__ OpCoef<T> c, T tau, T sigma,
+                                                        const T* __restrict__ u, const T* __restrict__ p,
+                                                        const T* __restrict__ f, const T* __restrict__ g,
+                                                        const T* __restrict__ sinv, T* __restrict__ u_out,
+                                                        T* __restrict__ p_out) {
+    using G = FusedTile<T, TX, TY>;
+    constexpr int NTH = TX * TY;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sm = reinterpret_cast<T*>(smem_raw);
+    T* sU = sm + G::U_OFF;
+    T* sP = sm + G::P_OFF;
+    T* sH = sm + G::H_OFF;
+    T* sD = sm + G::D_OFF;
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+    const int ld = 2 * n + 1;
+    const size_t n2 = (size_t)ld * ld;
+
+    // ---- stage u (both components) and p with their halos; zero outside / on the boundary
+    const int X0 = 2 * (i0 - 3), Y0 = 2 * (j0 - 3);
+    for (int q = tid; q < G::UW * G::UH; q += NTH) {
+        const int x = q % G::UW, y = q / G::UW;
+        const int X = X0 + x, Y = Y0 + y;
+        T vx = T(0), vy = T(0);
+        if (interior2(X, Y, n)) {
+            const size_t k = (size_t)Y * ld + X;
+            vx = __ldg(u + k);
+            vy = __ldg(u + n2 + k);
+        }
+        sU[q] = vx;
+        sU[G::UW * G::UH + q] = vy;
+    }
+    for (int q = tid; q < G::PW * G::PH; q += NTH) {
+        const int x = q % G::PW, y = q / G::PW;
+        const int I = i0 - 3 + x, J = j0 - 3 + y;
+        sP[q] = (I >= 0 && J >= 0 && I <= n && J <= n) ? __ldg(p + (size_t)J * (n + 1) + I) : T(0);
+    }
+    __syncthreads();
+
+    const SView<T> vux{sU, G::UW, X0, Y0}, vuy{sU + G::UW * G::UH, G::UW, X0, Y0};
+    const SView<T> vp{sP, G::PW, i0 - 3, j0 - 3};
+
+    // ---- u^{m-1/2} on cells [i0-2, i0+TX+2) x [j0-2, j0+TY+2)
+    const int HX0 = 2 * (i0 - 2), HY0 = 2 * (j0 - 2);
+    for (int q = tid; q < (TX + 4) * (TY + 4); q += NTH) {
+        const int ci = i0 - 2 + q % (TX + 4), cj = j0 - 2 + q / (TX + 4);
+        T hx[4] = {T(0), T(0), T(0), T(0)}, hy[4] = {T(0), T(0), T(0), T(0)};
+        if (ci >= 0 && cj >= 0 && ci <= n && cj <= n) {
+            Acc<T> a;
+            cell_apply<true, true, false, true, false>(ci, cj, n, c.A, c, vux, vuy, vp, a);
+            const CellNodes cn = cell_nodes(ci, cj, n);
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                if (!slot_unknown(cn, s)) continue;
+                int X, Y;
+                slot_pos(ci, cj, s, X, Y);
+                const size_t k = (size_t)Y * ld + X;
+                const T w = tau / a.dg[s];
+                hx[s] = vux(X, Y) + w * (__ldg(f + k) - a.au[0][s] - a.bt[0][s]);
+                hy[s] = vuy(X, Y) + w * (__ldg(f + n2 + k) - a.au[1][s] - a.bt[1][s]);
+            }
+        }
+        const int hx0 = 2 * ci - HX0, hy0 = 2 * cj - HY0;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const int o = (hy0 + (s >> 1)) * G::HW + hx0 + (s & 1);
+            sH[o] = hx[s];
+            sH[G::HW * G::HH + o] = hy[s];
+        }
+    }
+    __syncthreads();
+
+    const SView<T> vhx{sH, G::HW, HX0, HY0}, vhy{sH + G::HW * G::HH, G::HW, HX0, HY0};
+
+    // ---- dp on vertices [i0-1, i0+TX+1) x [j0-1, j0+TY+1)
+    for (int q = tid; q < G::DW * G::DH; q += NTH) {
+        const int vi = i0 - 1 + q % G::DW, vj = j0 - 1 + q / G::DW;
+        T d = T(0);
+        if (vi >= 0 && vj >= 0 && vi <= n && vj <= n) {
+            Acc<T> a;
+            cell_apply<false, false, true, false, false>(vi, vj, n, c.A, c, vhx, vhy, vp, a);
+            const size_t k = (size_t)vj * (n + 1) + vi;
+            d = sigma * __ldg(sinv + k) * (a.bu - __ldg(g + k));
+        }
+        sD[q] = d;
+    }
+    __syncthreads();
+
+    // ---- new (u, p) on the owned tile
+    const int ci = i0 + threadIdx.x, cj = j0 + threadIdx.y;
+    if (ci > n || cj > n) return;
+    const SView<T> vd{sD, G::DW, i0 - 1, j0 - 1};
+    Acc<T> a;
+    cell_apply<false, true, false, true, false>(ci, cj, n, c.A, c, vhx, vhy, vd, a);
+    const CellNodes cn = cell_nodes(ci, cj, n);
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        if (!slot_exists(cn, s)) continue;
+        int X, Y;
+        slot_pos(ci, cj, s, X, Y);
+        const size_t k = (size_t)Y * ld + X;
+        T ox = T(0), oy = T(0);
+        if (slot_unknown(cn, s)) {
+            const T w = tau / a.dg[s];
+            ox = vhx(X, Y) - w * a.bt[0][s];
+            oy = vhy(X, Y) - w * a.bt[1][s];
+        }
+        u_out[k] = ox;
+        u_out[n2 + k] = oy;
+    }
+    p_out[(size_t)cj * (n + 1) + ci] = vp(ci, cj) + vd(ci, cj);
+}
+
+template <typename T, int TX, int TY>
+static cudaError_t launch_fused_t(cudaStream_t s, int n, const OpCoef<T>& c, T tau, T sigma, const T* u,
+                                  const T* p, const T* f, const T* g, const T* sinv, T* u_out, T* p_out) {
+    using G = FusedTile<T, TX, TY>;
+    static unsigned long long attr = 0;   // devices on which the shared-memory limit is raised
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 64 || !((attr >> dev) & 1ull)) {
+        cudaError_t e = cudaFuncSetAttribute(k_uzawa_fused<T, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)G::BYTES);
+        if (e != cudaSuccess) return e;
+        if (dev < 64) attr |= 1ull << dev;
+    }
+    const dim3 grid((n + 1 + TX - 1) / TX, (n + 1 + TY - 1) / TY), blk(TX, TY);
+    k_uzawa_fused<T, TX, TY><<<grid, blk, G::BYTES, s>>>(n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t prepare_uzawa_fused() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if constexpr (sizeof(T) == 4)
+        return cudaFuncSetAttribute(k_uzawa_fused<T, 32, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)FusedTile<T, 32, 16>::BYTES);
+    else
+        return cudaFuncSetAttribute(k_uzawa_fused<T, 32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)FusedTile<T, 32, 8>::BYTES);
+}
+template cudaError_t prepare_uzawa_fused<float>();
+template cudaError_t prepare_uzawa_fused<double>();
+
+template <typename T>
+cudaError_t launch_uzawa_fused(cudaStream_t s, int n, const OpCoef<T>& c, T tau, T sigma, const T* u, const T* p,
+                               const T* f, const T* g, const T* sinv, T* u_out, T* p_out) {
+    // tile: 32 x 16 cells (55.6 KB of float32 shared memory), 32 x 8 for float64 (74 KB)
+    if constexpr (sizeof(T) == 4)
+        return launch_fused_t<T, 32, 16>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
+    else
+        return launch_fused_t<T, 32, 8>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
+}
+
+template cudaError_t launch_uzawa_fused<float>(cudaStream_t, int, const OpCoef<float>&, float, float, const float*,
+                                               const float*, const float*, const float*, const float*, float*, float*);
+template cudaError_t launch_uzawa_fused<double>(cudaStream_t, int, const OpCoef<double>&, double, double,
+                                                const double*, const double*, const double*, const double*,
+                                                const double*, double*, double*);
+
+}  // namespace smg

@@ -154,6 +154,14 @@ class Solver:
                 "stokes_smooth")
         return u, p
 
+    def smooth_f32(self, u, p, f, g, nu=1):
+        """float32 smoothing steps of the mixed-precision inner cycle (float32 tensors)."""
+        for t, sh, nm in ((u, self.shape_u, "u"), (p, self.shape_p, "p"), (f, self.shape_u, "f"), (g, self.shape_p, "g")):
+            if t.dtype != torch.float32 or tuple(t.shape) != tuple(sh) or not t.is_contiguous() or t.device != self.device:
+                raise ValueError("%s must be a contiguous float32 tensor of shape %s" % (nm, sh))
+        B.check(self._lib.stokes_smooth_f32(self._h, _ptr(u), _ptr(p), _ptr(f), _ptr(g), int(nu)), "stokes_smooth_f32")
+        return u, p
+
     def _coarse_shapes(self):
         nc = self.N // 2
         return (2, 2 * nc + 1, 2 * nc + 1), (nc + 1, nc + 1)

@@ -176,3 +176,57 @@ def test_solve_mixed_precision(discs, Solver, beta):
     assert np.linalg.norm(r) <= 1e-8 * np.linalg.norm(F) * 1.0001
     err = rel_err(x, xo)
     assert err < 1e-5, err
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 5, 6])
+@pytest.mark.parametrize("beta", [0.0, 1e3, 1e8])
+@pytest.mark.parametrize("nu", [1, 3])
+def test_smoother_float32_fused(discs, Solver, k, beta, nu):
+    """The fused one-kernel float32 Uzawa step of the mixed-precision path against the float64
+    oracle.  Bound: float32 rounding of row sums of about 30 terms, measured relative to the
+    largest entry of the result (2e-5)."""
+    import torch
+    H = mg.Hierarchy(k + 1, beta, discs[:k + 1])
+    d = H.discs[-1]
+    u, p, f, g = _state(k, 70 + k)
+    x = d.to_vec(u, p)
+    F = d.to_vec(f, g)
+    for _ in range(nu):
+        x = H.uzawa_step(H.finest, x, F, mg.Params())
+    S = Solver(k + 1, beta, precision="mixed")
+    t = lambda a: dev(a).float().contiguous()
+    tu, tp = t(u), t(p)
+    S.smooth_f32(tu, tp, t(f), t(g), nu)
+    uo, po = d.from_vec(x)
+    got = np.concatenate([host(tu.double()).ravel(), host(tp.double()).ravel()])
+    ref = np.concatenate([uo.ravel(), po.ravel()])
+    assert rel_err(got, ref) < 2e-5
+
+
+@pytest.mark.parametrize("k", [3, 5])
+@pytest.mark.parametrize("nu_pre,nu_post,gamma", [(3, 3, 2), (4, 3, 2), (3, 2, 1)])
+def test_mixed_cycle_variants(discs, Solver, k, nu_pre, nu_post, gamma):
+    """W-cycles and odd smoothing counts (the float32 ping-pong ends in the scratch buffer) in the
+    mixed path converge to the oracle's exact discrete solution.  (nu = 2+1 is not tested: like
+    2+2 in Sec. 5, Table 1, it diverges.)"""
+    d = discs[k]
+    fn, gn = workloads.random_nodal(k, 80 + k)
+    S = Solver(k + 1, 10.0, precision="mixed", nu_pre=nu_pre, nu_post=nu_post, gamma=gamma)
+    f, g = S.load_vectors(dev(fn), dev(gn), project_g=True)
+    u, p, rep = S.solve(f, g, tol=1e-9, max_cycles=300)
+    F = d.load(fn, gn, project_g=True)
+    xo = mg.direct_solve(d.system(10.0), d, F)
+    assert rep.converged, rep
+    assert rel_err(d.to_vec(host(u), host(p)), xo) < 1e-6
+
+
+def test_divergence_is_reported(Solver):
+    """Sec. 5, Table 1: the Uzawa smoother with nu = 1+1 diverges; the solver must stop with
+    STOKES_DIVERGED instead of running to max_cycles or raising."""
+    from paper_1502_04070_gb300 import _binding
+    k = 4
+    fn, gn = workloads.random_nodal(k, 90)
+    S = Solver(k + 1, 1.0, nu_pre=1, nu_post=1)
+    f, g = S.load_vectors(dev(fn), dev(gn), project_g=True)
+    u, p, rep = S.solve(f, g, tol=1e-9, max_cycles=400)
+    assert rep.status == _binding.DIVERGED
