@@ -145,6 +145,11 @@ stokes_status stokes_prolong_add(stokes_handle* h, const double* uc, const doubl
 stokes_status stokes_load_vectors(stokes_handle* h, const double* f_nodal, const double* g_nodal,
                                   int project_g, double* f, double* g);
 
+/* g <- g - (1^T g) w,  w = M_P 1 (w sums to 1): makes a pressure right-hand side orthogonal to the
+ * constant pressure, the kernel of the matrix of eq. gen:bil:mv (Sec. 1: int g = 0).  Needed for
+ * adjoint right-hand sides whose pressure part does not sum to zero.  In place, asynchronous. */
+stokes_status stokes_make_consistent(stokes_handle* h, double* g);
+
 /* dot = a^T M_U b for two velocity arrays a, b (layout of u, boundary entries ignored), where M_U
  * is the velocity mass matrix (the beta-part of A_k = K + beta M_U, Sec. 2); float64, synchronises
  * the stream.  Gives the beta-derivative of a loss through the adjoint: dL/dbeta = -lambda_u^T M_U u. */

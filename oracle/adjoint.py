@@ -7,8 +7,8 @@ and for a loss L(x):
     lambda = first block of the bordered solve with right-hand side [dL/dx; 0]
     dL/dF  = lambda                         (dL/df = lambda_u, dL/dg = lambda_p)
     dL/dbeta = -lambda^T (dS/dbeta) x = -lambda_u^T M_U u.
-dL/dg is returned shifted to zero sum (the Euclidean projection onto the admissible directions
-sum(dg) = 0); that shift does not change any admissible directional derivative.
+lambda_p is the representative with w^T lambda_p = 0 that the bordered solve produces; any constant
+shift of it gives the same derivative in every admissible direction (sum(dg) = 0).
 """
 import numpy as np
 
@@ -17,16 +17,14 @@ from . import multigrid as mg
 
 def solve_and_gradients(H: mg.Hierarchy, F, dL_dx_fn):
     """Direct solve of the finest level, then the adjoint solve.  dL_dx_fn(x) -> dL/dx.
-    Returns x, dL/dF (with the g-part projected to zero sum), dL/dbeta."""
+    Returns x, dL/dF, dL/dbeta."""
     l = len(H.levels) - 1
     d = H.discs[l]
     x = H.direct(F)
     lam = mg.direct_solve(H.levels[l].S, d, dL_dx_fn(x))
     u, lam_u = x[:d.nu], lam[:d.nu]
     dbeta = -lam_u @ (d.mass_u() @ u)
-    grad = lam.copy()
-    grad[d.nu:] -= grad[d.nu:].mean()
-    return x, grad, dbeta
+    return x, lam, dbeta
 
 
 def loss_velocity_mass(d, x, u_target):

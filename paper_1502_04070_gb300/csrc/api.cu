@@ -647,6 +647,14 @@ stokes_status stokes_load_vectors(stokes_handle* h, const double* f_nodal, const
     return STOKES_OK;
 }
 
+stokes_status stokes_make_consistent(stokes_handle* h, double* g) {
+    if (!h || !g) return STOKES_ERR_BAD_ARG;
+    launch_make_consistent(h->st, h->fin().n, g, h->partial, h->scal + 6);
+    h->launches += 3;
+    CK(cudaGetLastError());
+    return STOKES_OK;
+}
+
 stokes_status stokes_mass_dot(stokes_handle* h, const double* a, const double* b, double* dot) {
     if (!h || !a || !b || !dot) return STOKES_ERR_BAD_ARG;
     const int n = h->fin().n;

@@ -660,6 +660,26 @@ void launch_rhs_norm(cudaStream_t s, int n, const double* f, const double* g, do
     k_rhs_norm<<<cells_grid(n), dim3(BX, BY), 0, s>>>(n, f, g, partial);
 }
 
+__global__ void __launch_bounds__(NT) k_sum_partial(int n, const double* __restrict__ g, double* __restrict__ partial) {
+    CELL_INDEX
+    const double v = active ? g[(size_t)j * (n + 1) + i] : 0.0;
+    const double t = block_sum2d(v, tid);
+    if (tid == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(NT) k_sub_w(int n, double* __restrict__ g, const double* __restrict__ scalar) {
+    CELL_INDEX
+    if (!active) return;
+    g[(size_t)j * (n + 1) + i] -= (*scalar) * vertex_weight(i, j, n);   // sum_i w_i = 1
+}
+
+void launch_make_consistent(cudaStream_t s, int n, double* g, double* partial, double* scalar) {
+    const dim3 grid = cells_grid(n), blk(BX, BY);
+    k_sum_partial<<<grid, blk, 0, s>>>(n, g, partial);
+    k_reduce<<<1, 1024, 0, s>>>(partial, grid.x * grid.y, scalar);
+    k_sub_w<<<grid, blk, 0, s>>>(n, g, scalar);
+}
+
 __global__ void k_add_f32(size_t count, const float* __restrict__ e, double* __restrict__ x) {
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < count; k += (size_t)gridDim.x * blockDim.x)
         x[k] += (double)e[k];

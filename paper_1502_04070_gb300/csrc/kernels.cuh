@@ -82,6 +82,10 @@ void launch_mass_dot(cudaStream_t s, int n, const MassCoef<double>& m, const dou
 // partial sums of ||F||^2 over the unknowns (f at interior velocity nodes, all of g)
 void launch_rhs_norm(cudaStream_t s, int n, const double* f, const double* g, double* partial);
 
+// g <- g - (1^T g) w  with w = M_P 1: the pressure right-hand side becomes orthogonal to the
+// constant pressure (the kernel of the saddle-point matrix)
+void launch_make_consistent(cudaStream_t s, int n, double* g, double* partial, double* scalar);
+
 // x64 += e32 (count elements), and float64 -> float32 conversion
 void launch_add_f32(cudaStream_t s, size_t count, const float* e, double* x);
 

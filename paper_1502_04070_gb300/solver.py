@@ -195,6 +195,16 @@ class Solver:
     def kernel_launches(self):
         return int(self._lib.stokes_kernel_launches(self._h))
 
+    def make_consistent(self, g):
+        """g <- g - (sum g) M_P 1 in place (pressure right-hand side orthogonal to constants)."""
+        B.check(self._lib.stokes_make_consistent(self._h, self._chk(g, self.shape_p, "g")), "stokes_make_consistent")
+        return g
+
+    def mass_apply(self, a):
+        """M_U a for a velocity array (boundary entries of a count as given; rows on the boundary are 0)."""
+        f, _ = self.load_vectors(a, self.zeros_p(), project_g=False)
+        return f
+
     def mass_dot(self, a, b):
         out = ctypes.c_double()
         B.check(self._lib.stokes_mass_dot(self._h, self._chk(a, self.shape_u, "a"), self._chk(b, self.shape_u, "b"),
