@@ -230,8 +230,9 @@ void residual_norm_fin(stokes_handle* h, bool timed = false) {
     const int k = timed ? ev_begin(h) : -1;
     if (k >= 0) h->ev_resid++;
     if (h->mixed()) {
+        // x in float64; r kept as two floats for the refinement updates, r32 = its float32 value
         Level<float>& E = h->h32.back();
-        launch_residual<double, double>(h->st, F.n, F.c, F.u, F.p, F.f, F.g, F.tu, F.tp, h->partial, E.f, E.g);
+        launch_residual_df(h->st, F.n, F.c, F.u, F.p, F.f, F.g, F.tu, F.tp, E.f, E.g, h->partial);
     } else {
         launch_residual<double, double>(h->st, F.n, F.c, F.u, F.p, F.f, F.g, F.tu, F.tp, h->partial);
     }
@@ -247,13 +248,13 @@ void record_step(stokes_handle* h) {
         cudaMemsetAsync(E.u, 0, 2 * E.n2 * sizeof(float), h->st);
         cudaMemsetAsync(E.p, 0, E.n1 * sizeof(float), h->st);
         for (int c = 0; c < h->prm.inner_cycles; ++c) mg_cycle<float>(h, h->h32, h->L - 1);
-        // x += e, r -= A e (float64 storage, error-free float32 products), r32 = float(r)
+        // x += e, r -= A e (two-float state, error-free float32 products), r32 = float(r)
         const int k = ev_begin(h);
         if (k >= 0) h->ev_resid++;
-        launch_ir_update(h->st, F.n, h->chi, h->clo, E.u, E.p, F.u, F.p, F.tu, F.tp, E.f, E.g, h->partial);
+        launch_ir_update_df(h->st, F.n, h->chi, h->clo, E.u, E.p, F.u, F.p, F.tu, F.tp, E.f, E.g, h->partial);
         ev_end(h, k);
         launch_reduce(h->st, h->partial, cells_blocks(F.n), h->scal);
-        launch_pmean<double>(h->st, F.n, F.p, h->partial, h->scal + 1);
+        launch_pmean_df(h->st, F.n, F.p, h->partial, h->scal + 1);
     } else {
         mg_cycle<double>(h, h->h64, h->L - 1);
         launch_pmean<double>(h->st, F.n, F.p, h->partial, h->scal + 1);
@@ -354,6 +355,14 @@ stokes_status copy_in(stokes_handle* h, const double* u, const double* p, const 
     CK(cudaMemcpyAsync(F.f, f, 2 * F.n2 * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
     CK(cudaMemcpyAsync(F.g, g, F.n1 * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
     return STOKES_OK;
+}
+
+// MIXED: switch the finest iterate between float64 and the two-float loop representation
+void x_repr(stokes_handle* h, bool to_df) {
+    Level<double>& F = h->fin();
+    launch_to_df(h->st, 2 * F.n2, F.u, to_df);
+    launch_to_df(h->st, F.n1, F.p, to_df);
+    h->launches += 2;
 }
 
 stokes_status copy_out(stokes_handle* h, double* u, double* p) {
@@ -497,10 +506,16 @@ stokes_status stokes_cycle(stokes_handle* h, double* u, double* p, const double*
     if (h->mixed()) {
         residual_norm_fin(h);   // float64 residual and the float32 right-hand side of the correction
         h->launches += 2;
+        x_repr(h, true);
     }
     if ((s = build_graph(h)) != STOKES_OK) return s;
     stokes_status s2 = launch_step(h);
     if (s2 != STOKES_OK) return s2;
+    if (h->mixed()) {
+        x_repr(h, false);
+        launch_pmean<double>(h->st, h->fin().n, h->fin().p, h->partial, h->scal + 1);
+        h->launches += 3;
+    }
     return copy_out(h, u, p);
 }
 
@@ -519,6 +534,11 @@ stokes_status stokes_solve(stokes_handle* h, double* u, double* p, const double*
     const double nF = std::sqrt(nF2);
     residual_norm_fin(h);
     h->launches += 2;
+    bool x_df = false;
+    if (h->mixed()) {
+        x_repr(h, true);
+        x_df = true;
+    }
     double r2 = 0.0;
     if ((s = read_scalar(h, 0, &r2)) != STOKES_OK) return s;
     double r0 = std::sqrt(r2), r = r0;
@@ -530,12 +550,16 @@ stokes_status stokes_solve(stokes_handle* h, double* u, double* p, const double*
         if (r <= tol * nF) {
             if (!h->mixed()) break;
             // the refinement residual is updated, not recomputed: confirm with the true one
+            x_repr(h, false);
+            x_df = false;
             residual_norm_fin(h);
             h->launches += 2;
             if ((s = read_scalar(h, 0, &r2)) != STOKES_OK) return s;
             r = std::sqrt(r2);
             if (history) history[cycles] = r;
             if (r <= tol * nF) break;
+            x_repr(h, true);
+            x_df = true;
         }
         // diverged: NaN/Inf, or growth in each of the last 8 cycles (the first cycles from x = 0
         // may raise the Euclidean residual by orders of magnitude before it decays)
@@ -555,6 +579,11 @@ stokes_status stokes_solve(stokes_handle* h, double* u, double* p, const double*
         r = std::sqrt(r2);
         ++cycles;
         if (history) history[cycles] = r;
+    }
+    if (h->mixed()) {
+        if (x_df) x_repr(h, false);
+        launch_pmean<double>(h->st, F.n, F.p, h->partial, h->scal + 1);
+        h->launches += 3;
     }
     if ((s = copy_out(h, u, p)) != STOKES_OK) return s;
     CK(cudaStreamSynchronize(h->st));

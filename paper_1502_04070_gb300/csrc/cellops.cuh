@@ -35,21 +35,43 @@ struct Acc {
     T bu;         // (B u) at the owned vertex
 };
 
-// value of a P2-lattice array at (X, Y): global memory (read-only path) or a shared tile
+// Views map P2-lattice points to values.  A velocity view answers at(si, sj, a, b), the value at
+// lattice point (2 si + a, 2 sj + b) (a, b are compile-time in every caller, so a square's nine
+// loads share one address computation), and (X, Y) for a single point.  A vertex view answers
+// (i, j).  GView reads global memory through the read-only path; SLat / SVert read shared tiles.
 template <typename T>
 struct GView {
     const T* p;
     int ld;
     __device__ __forceinline__ T operator()(int X, int Y) const { return __ldg(p + (size_t)Y * ld + X); }
-};
-template <typename T>
-struct SView {
-    const T* p;
-    int ld, x0, y0;
-    __device__ __forceinline__ T operator()(int X, int Y) const { return p[(Y - y0) * ld + (X - x0)]; }
+    __device__ __forceinline__ T at(int si, int sj, int a, int b) const {
+        return __ldg(p + (size_t)(2 * sj + b) * ld + 2 * si + a);
+    }
 };
 template <typename T>
 __device__ __forceinline__ GView<T> gview(const T* p, int ld) { return GView<T>{p, ld}; }
+
+// Shared-memory lattice tile split by the parity of X: plane (X - 2 xh0) & 1 holds the points of
+// that parity, so a warp reading one local node of 32 consecutive squares touches 32 consecutive
+// words.  WH words per row, PL words per plane (padded so the two planes fall on different banks).
+template <typename T, int WH, int PL>
+struct SLat {
+    const T* p;
+    int xh0, y0;   // tile origin: X0 = 2 xh0, Y0 = y0
+    __device__ __forceinline__ T at(int si, int sj, int a, int b) const {
+        return p[(a & 1) * PL + (2 * sj + b - y0) * WH + (si - xh0) + (a >> 1)];
+    }
+    __device__ __forceinline__ T operator()(int X, int Y) const {
+        const int dx = X - 2 * xh0;
+        return p[(dx & 1) * PL + (Y - y0) * WH + (dx >> 1)];
+    }
+};
+template <typename T, int LD>
+struct SVert {
+    const T* p;
+    int x0, y0;
+    __device__ __forceinline__ T operator()(int i, int j) const { return p[(j - y0) * LD + (i - x0)]; }
+};
 
 template <bool MASK, typename T, typename V>
 __device__ __forceinline__ void load_sq(const V& u, int n, int si, int sj, T (&v)[9]) {
@@ -57,9 +79,8 @@ __device__ __forceinline__ void load_sq(const V& u, int n, int si, int sj, T (&v
     for (int b = 0; b < 3; ++b)
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const int X = 2 * si + a, Y = 2 * sj + b;
-            T val = u(X, Y);
-            if (MASK && !interior2(X, Y, n)) val = T(0);
+            T val = u.at(si, sj, a, b);
+            if (MASK && !interior2(2 * si + a, 2 * sj + b, n)) val = T(0);
             v[3 * b + a] = val;
         }
 }

@@ -34,6 +34,17 @@ template <typename T>
 void launch_uzawa(cudaStream_t s, int n, const OpCoef<T>& c, T tau, T sigma, T* u, T* p, const T* f,
                   const T* g, const T* sinv, T* uh, T* dp);
 
+// Two-float refinement state (see refine.cu): x, r stored as (hi, lo) float pairs in the 8-byte
+// slots of float64 arrays during the refinement loop.
+void launch_ir_update_df(cudaStream_t s, int n, const OpCoef<float>& chi, const OpCoef<float>& clo,
+                         const float* eu, const float* ep, double* xu, double* xp, double* ru, double* rp,
+                         float* r32u, float* r32p, double* partial);
+void launch_residual_df(cudaStream_t s, int n, const OpCoef<double>& c, const double* u, const double* p,
+                        const double* f, const double* g, double* ru, double* rp, float* r32u, float* r32p,
+                        double* partial);
+void launch_to_df(cudaStream_t s, size_t count, double* x, bool to_df);
+void launch_pmean_df(cudaStream_t s, int n, double* p, double* partial, double* scalar);
+
 // The same Uzawa step fused into one kernel with shared-memory halos: reads (u, p), writes
 // (u_out, p_out) (distinct buffers).
 template <typename T>

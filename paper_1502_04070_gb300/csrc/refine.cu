@@ -9,6 +9,12 @@
 // relative to sum |c| |e|.  Because e shrinks with the residual, the accumulated error of the
 // updated residual stays far below the refinement tolerance; the solver still recomputes the true
 // float64 residual before it reports convergence.
+//
+// GB300 also runs conversions and additions in float64 on its narrow float64 pipe, so during the
+// refinement loop the iterate x and the residual r are kept as unevaluated sums of two floats
+// (hi + lo, about 48 significant bits) stored in the float64 arrays' own 8-byte slots; the loop
+// then issues no float64 instruction per unknown.  x is converted back to float64 for the true
+// residual check and for the caller.
 #include "cellops.cuh"
 #include "kernels.cuh"
 
@@ -133,6 +139,196 @@ __global__ void __launch_bounds__(NT) k_ir_update(int n, const __grid_constant__
     }
     const double t = block_sum2d(ss, tid);
     if (tid == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = t;
+}
+
+// ---------------------------------------------------------------------------------------------
+// two-float ("double-float") state
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ float2 renorm(float s, float e) {
+    const float hi = __fadd_rn(s, e);
+    return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, s)));
+}
+// a + b, b a float
+__device__ __forceinline__ float2 df_add(float2 a, float b) {
+    float s, e;
+    two_sum(a.x, b, s, e);
+    return renorm(s, __fadd_rn(e, a.y));
+}
+// a - (b.hi + b.lo)
+__device__ __forceinline__ float2 df_sub(float2 a, const DF& b) {
+    float s, e;
+    two_sum(a.x, -b.hi, s, e);
+    return renorm(s, __fadd_rn(e, __fsub_rn(a.y, b.lo)));
+}
+
+__global__ void __launch_bounds__(NT) k_ir_update_df(int n, const __grid_constant__ OpCoef<float> ch,
+                                                     const __grid_constant__ OpCoef<float> cl,
+                                                     const float* __restrict__ eu, const float* __restrict__ ep,
+                                                     float2* __restrict__ xu, float2* __restrict__ xp,
+                                                     float2* __restrict__ ru, float2* __restrict__ rp,
+                                                     float* __restrict__ r32u, float* __restrict__ r32p,
+                                                     double* __restrict__ partial) {
+    CELL_INDEX
+    const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
+    float ss = 0.f;
+    if (active) {
+        DFAcc a;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) a.au[0][s] = a.au[1][s] = DF{0.f, 0.f};
+        a.bu = DF{0.f, 0.f};
+        visit_df<0>(i, j, n, ch, cl, eu, ep, a);
+        visit_df<1>(i, j, n, ch, cl, eu, ep, a);
+        visit_df<2>(i, j, n, ch, cl, eu, ep, a);
+        visit_df<3>(i, j, n, ch, cl, eu, ep, a);
+        const CellNodes cn = cell_nodes(i, j, n);
+        const int ld = 2 * n + 1;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            if (!slot_unknown(cn, s)) continue;
+            int X, Y;
+            slot_pos(i, j, s, X, Y);
+            const size_t idx = (size_t)Y * ld + X;
+#pragma unroll
+            for (int comp = 0; comp < 2; ++comp) {
+                const size_t k = comp * n2 + idx;
+                xu[k] = df_add(xu[k], eu[k]);
+                const float2 r = df_sub(ru[k], a.au[comp][s]);
+                ru[k] = r;
+                r32u[k] = r.x;
+                ss = fmaf(r.x, r.x, ss);
+            }
+        }
+        const size_t vi = (size_t)j * (n + 1) + i;
+        xp[vi] = df_add(xp[vi], ep[vi]);
+        const float2 r = df_sub(rp[vi], a.bu);
+        rp[vi] = r;
+        r32p[vi] = r.x;
+        ss = fmaf(r.x, r.x, ss);
+    }
+    const double t = block_sum2d((double)ss, tid);
+    if (tid == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = t;
+}
+
+// true float64 residual r = F - A x (x, F float64), written as two-float r and float32 r32
+__global__ void __launch_bounds__(NT) k_residual_df(int n, const __grid_constant__ OpCoef<double> c,
+                                                    const double* __restrict__ u, const double* __restrict__ p,
+                                                    const double* __restrict__ f, const double* __restrict__ g,
+                                                    float2* __restrict__ ru, float2* __restrict__ rp,
+                                                    float* __restrict__ r32u, float* __restrict__ r32p,
+                                                    double* __restrict__ partial) {
+    CELL_INDEX
+    const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
+    double ss = 0.0;
+    if (active) {
+        Acc<double> a;
+        cell_apply<true, true, true, false, true>(i, j, n, c.A, c, gview(u, 2 * n + 1), gview(u + n2, 2 * n + 1),
+                                                  gview(p, n + 1), a);
+        const CellNodes cn = cell_nodes(i, j, n);
+        const int ld = 2 * n + 1;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            if (!slot_exists(cn, s)) continue;
+            int X, Y;
+            slot_pos(i, j, s, X, Y);
+            const size_t idx = (size_t)Y * ld + X;
+#pragma unroll
+            for (int comp = 0; comp < 2; ++comp) {
+                const size_t k = comp * n2 + idx;
+                double r = 0.0;
+                if (slot_unknown(cn, s)) r = f[k] - a.au[comp][s] - a.bt[comp][s];
+                const float hi = (float)r;
+                ru[k] = make_float2(hi, (float)(r - (double)hi));
+                r32u[k] = hi;
+                ss += r * r;
+            }
+        }
+        const size_t vi = (size_t)j * (n + 1) + i;
+        const double r = g[vi] - a.bu;
+        const float hi = (float)r;
+        rp[vi] = make_float2(hi, (float)(r - (double)hi));
+        r32p[vi] = hi;
+        ss += r * r;
+    }
+    const double t = block_sum2d(ss, tid);
+    if (tid == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = t;
+}
+
+// in-place conversions between float64 and two-float storage of the same 8-byte slots
+__global__ void k_to_df(size_t count, double* __restrict__ x) {
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < count; k += (size_t)gridDim.x * blockDim.x) {
+        const double v = x[k];
+        const float hi = (float)v;
+        reinterpret_cast<float2*>(x)[k] = make_float2(hi, (float)(v - (double)hi));
+    }
+}
+__global__ void k_from_df(size_t count, double* __restrict__ x) {
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < count; k += (size_t)gridDim.x * blockDim.x) {
+        const float2 v = reinterpret_cast<const float2*>(x)[k];
+        x[k] = (double)v.x + (double)v.y;
+    }
+}
+
+// zero-mean projection of a two-float pressure: partial sums of w_i p_i (float per thread), then
+// p <- p - c.  c only shifts p by a constant, which no residual sees (B^T 1 = 0); the float64
+// projection is redone when x returns to float64.
+__global__ void __launch_bounds__(NT) k_pmean_partial_df(int n, const float2* __restrict__ p,
+                                                         double* __restrict__ partial) {
+    CELL_INDEX
+    float v = 0.f;
+    if (active) {
+        int cnt = 0;
+#pragma unroll
+        for (int SQ = 0; SQ < 4; ++SQ) {
+            const int si = i - (SQ & 1), sj = j - (SQ >> 1);
+            if (si < 0 || sj < 0 || si >= n || sj >= n) continue;
+            const int o = orient(si, sj, n), node = corner_node(SQ);
+            cnt += ((tri_mask(o, 0) >> node) & 1u) + ((tri_mask(o, 1) >> node) & 1u);
+        }
+        const float h = 1.f / n;
+        v = cnt * h * h * (1.f / 6.f) * p[(size_t)j * (n + 1) + i].x;
+    }
+    const double t = block_sum2d((double)v, tid);
+    if (tid == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = t;
+}
+__global__ void __launch_bounds__(NT) k_psub_df(int n, float2* __restrict__ p, const double* __restrict__ scalar) {
+    CELL_INDEX
+    if (!active) return;
+    const size_t vi = (size_t)j * (n + 1) + i;
+    p[vi] = df_add(p[vi], -(float)(*scalar));
+}
+
+void launch_ir_update_df(cudaStream_t s, int n, const OpCoef<float>& chi, const OpCoef<float>& clo,
+                         const float* eu, const float* ep, double* xu, double* xp, double* ru, double* rp,
+                         float* r32u, float* r32p, double* partial) {
+    k_ir_update_df<<<cells_grid(n), dim3(BX, BY), 0, s>>>(
+        n, chi, clo, eu, ep, reinterpret_cast<float2*>(xu), reinterpret_cast<float2*>(xp),
+        reinterpret_cast<float2*>(ru), reinterpret_cast<float2*>(rp), r32u, r32p, partial);
+}
+
+void launch_residual_df(cudaStream_t s, int n, const OpCoef<double>& c, const double* u, const double* p,
+                        const double* f, const double* g, double* ru, double* rp, float* r32u, float* r32p,
+                        double* partial) {
+    k_residual_df<<<cells_grid(n), dim3(BX, BY), 0, s>>>(n, c, u, p, f, g, reinterpret_cast<float2*>(ru),
+                                                         reinterpret_cast<float2*>(rp), r32u, r32p, partial);
+}
+
+void launch_to_df(cudaStream_t s, size_t count, double* x, bool to_df) {
+    const size_t want = (count + 255) / 256;
+    const int blocks = (int)(want < 152 * 16 ? (want > 0 ? want : 1) : 152 * 16);
+    if (to_df) k_to_df<<<blocks, 256, 0, s>>>(count, x);
+    else k_from_df<<<blocks, 256, 0, s>>>(count, x);
+}
+
+void launch_pmean_df(cudaStream_t s, int n, double* p, double* partial, double* scalar) {
+    const dim3 grid = cells_grid(n), blk(BX, BY);
+    k_pmean_partial_df<<<grid, blk, 0, s>>>(n, reinterpret_cast<const float2*>(p), partial);
+    launch_reduce(s, partial, grid.x * grid.y, scalar);
+    k_psub_df<<<grid, blk, 0, s>>>(n, reinterpret_cast<float2*>(p), scalar);
 }
 
 void launch_ir_update(cudaStream_t s, int n, const OpCoef<float>& chi, const OpCoef<float>& clo,

@@ -16,16 +16,25 @@
 
 namespace smg {
 
+// plane size padded so that the two parity planes of one row start half a bank cycle apart
+// (16 words for float32, 8 doubles for float64): staging writes of consecutive X are conflict-free
+template <typename T>
+__host__ __device__ constexpr int pad_plane(int w) {
+    return sizeof(T) == 4 ? ((w + 31) / 32) * 32 + 16 : ((w + 15) / 16) * 16 + 8;
+}
+
 template <typename T, int TX, int TY>
 struct FusedTile {
-    static constexpr int UW = 2 * (TX + 6), UH = 2 * (TY + 6);   // u: cells [i0-3, i0+TX+3)
+    // u: cells [i0-3, i0+TX+3) -> lattice columns [2(i0-3), 2(i0+TX+3)), split by parity
+    static constexpr int UWH = TX + 6, UH = 2 * (TY + 6), UPL = pad_plane<T>(UWH * UH);
     static constexpr int PW = TX + 6, PH = TY + 6;               // p: vertices [i0-3, i0+TX+3)
-    static constexpr int HW = 2 * (TX + 4), HH = 2 * (TY + 4);   // u^{m-1/2}: cells [i0-2, i0+TX+2)
+    // u^{m-1/2}: cells [i0-2, i0+TX+2)
+    static constexpr int HWH = TX + 4, HH = 2 * (TY + 4), HPL = pad_plane<T>(HWH * HH);
     static constexpr int DW = TX + 2, DH = TY + 2;               // dp: vertices [i0-1, i0+TX+1)
-    static constexpr int U_OFF = 0;
-    static constexpr int P_OFF = U_OFF + 2 * UW * UH;
+    static constexpr int U_OFF = 0;                              // u_x planes, then u_y planes
+    static constexpr int P_OFF = U_OFF + 4 * UPL;
     static constexpr int H_OFF = P_OFF + PW * PH;
-    static constexpr int D_OFF = H_OFF + 2 * HW * HH;
+    static constexpr int D_OFF = H_OFF + 4 * HPL;
     static constexpr int TOTAL = D_OFF + DW * DH;
     static constexpr size_t BYTES = sizeof(T) * (size_t)TOTAL;
 };
@@ -49,10 +58,12 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 4 ? 2 : 1)) k_uzawa_fuse
     const int ld = 2 * n + 1;
     const size_t n2 = (size_t)ld * ld;
 
-    // ---- stage u (both components) and p with their halos; zero outside / on the boundary
+    // ---- stage u (both components) and p with their halos; zero outside / on the boundary.
+    // Global reads run along X (coalesced); the parity split sends even / odd X to the two planes.
     const int X0 = 2 * (i0 - 3), Y0 = 2 * (j0 - 3);
-    for (int q = tid; q < G::UW * G::UH; q += NTH) {
-        const int x = q % G::UW, y = q / G::UW;
+    constexpr int UW = 2 * G::UWH;
+    for (int q = tid; q < UW * G::UH; q += NTH) {
+        const int x = q % UW, y = q / UW;
         const int X = X0 + x, Y = Y0 + y;
         T vx = T(0), vy = T(0);
         if (interior2(X, Y, n)) {
@@ -60,8 +71,9 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 4 ? 2 : 1)) k_uzawa_fuse
             vx = __ldg(u + k);
             vy = __ldg(u + n2 + k);
         }
-        sU[q] = vx;
-        sU[G::UW * G::UH + q] = vy;
+        const int o = (x & 1) * G::UPL + y * G::UWH + (x >> 1);
+        sU[o] = vx;
+        sU[2 * G::UPL + o] = vy;
     }
     for (int q = tid; q < G::PW * G::PH; q += NTH) {
         const int x = q % G::PW, y = q / G::PW;
@@ -70,11 +82,13 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 4 ? 2 : 1)) k_uzawa_fuse
     }
     __syncthreads();
 
-    const SView<T> vux{sU, G::UW, X0, Y0}, vuy{sU + G::UW * G::UH, G::UW, X0, Y0};
-    const SView<T> vp{sP, G::PW, i0 - 3, j0 - 3};
+    using ULat = SLat<T, G::UWH, G::UPL>;
+    using HLat = SLat<T, G::HWH, G::HPL>;
+    const ULat vux{sU, i0 - 3, Y0}, vuy{sU + 2 * G::UPL, i0 - 3, Y0};
+    const SVert<T, G::PW> vp{sP, i0 - 3, j0 - 3};
 
     // ---- u^{m-1/2} on cells [i0-2, i0+TX+2) x [j0-2, j0+TY+2)
-    const int HX0 = 2 * (i0 - 2), HY0 = 2 * (j0 - 2);
+    const int HY0 = 2 * (j0 - 2);
     for (int q = tid; q < (TX + 4) * (TY + 4); q += NTH) {
         const int ci = i0 - 2 + q % (TX + 4), cj = j0 - 2 + q / (TX + 4);
         T hx[4] = {T(0), T(0), T(0), T(0)}, hy[4] = {T(0), T(0), T(0), T(0)};
@@ -89,21 +103,21 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 4 ? 2 : 1)) k_uzawa_fuse
                 slot_pos(ci, cj, s, X, Y);
                 const size_t k = (size_t)Y * ld + X;
                 const T w = tau / a.dg[s];
-                hx[s] = vux(X, Y) + w * (__ldg(f + k) - a.au[0][s] - a.bt[0][s]);
-                hy[s] = vuy(X, Y) + w * (__ldg(f + n2 + k) - a.au[1][s] - a.bt[1][s]);
+                hx[s] = vux.at(ci, cj, s & 1, s >> 1) + w * (__ldg(f + k) - a.au[0][s] - a.bt[0][s]);
+                hy[s] = vuy.at(ci, cj, s & 1, s >> 1) + w * (__ldg(f + n2 + k) - a.au[1][s] - a.bt[1][s]);
             }
         }
-        const int hx0 = 2 * ci - HX0, hy0 = 2 * cj - HY0;
+        const int hc = ci - (i0 - 2), hy0 = 2 * cj - HY0;
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
-            const int o = (hy0 + (s >> 1)) * G::HW + hx0 + (s & 1);
+            const int o = (s & 1) * G::HPL + (hy0 + (s >> 1)) * G::HWH + hc;
             sH[o] = hx[s];
-            sH[G::HW * G::HH + o] = hy[s];
+            sH[2 * G::HPL + o] = hy[s];
         }
     }
     __syncthreads();
 
-    const SView<T> vhx{sH, G::HW, HX0, HY0}, vhy{sH + G::HW * G::HH, G::HW, HX0, HY0};
+    const HLat vhx{sH, i0 - 2, HY0}, vhy{sH + 2 * G::HPL, i0 - 2, HY0};
 
     // ---- dp on vertices [i0-1, i0+TX+1) x [j0-1, j0+TY+1)
     for (int q = tid; q < G::DW * G::DH; q += NTH) {
@@ -122,7 +136,7 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 4 ? 2 : 1)) k_uzawa_fuse
     // ---- new (u, p) on the owned tile
     const int ci = i0 + threadIdx.x, cj = j0 + threadIdx.y;
     if (ci > n || cj > n) return;
-    const SView<T> vd{sD, G::DW, i0 - 1, j0 - 1};
+    const SVert<T, G::DW> vd{sD, i0 - 1, j0 - 1};
     Acc<T> a;
     cell_apply<false, true, false, true, false>(ci, cj, n, c.A, c, vhx, vhy, vd, a);
     const CellNodes cn = cell_nodes(ci, cj, n);
@@ -135,8 +149,8 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 4 ? 2 : 1)) k_uzawa_fuse
         T ox = T(0), oy = T(0);
         if (slot_unknown(cn, s)) {
             const T w = tau / a.dg[s];
-            ox = vhx(X, Y) - w * a.bt[0][s];
-            oy = vhy(X, Y) - w * a.bt[1][s];
+            ox = vhx.at(ci, cj, s & 1, s >> 1) - w * a.bt[0][s];
+            oy = vhy.at(ci, cj, s & 1, s >> 1) - w * a.bt[1][s];
         }
         u_out[k] = ox;
         u_out[n2 + k] = oy;
