@@ -155,6 +155,25 @@ stokes_status stokes_make_consistent(stokes_handle* h, double* g);
  * the stream.  Gives the beta-derivative of a loss through the adjoint: dL/dbeta = -lambda_u^T M_U u. */
 stokes_status stokes_mass_dot(stokes_handle* h, const double* a, const double* b, double* dot);
 
+/* ||F - A x||_2^2 of the finest level, like stokes_residual_norm, but without a handle and without
+ * allocating any device memory.  The paper has no counterpart: this exists for callers that cannot
+ * call cudaMalloc -- code that runs while a stream is being captured, code that lives inside a
+ * fixed memory budget handed out by another framework, or code on a device that is already full.
+ *   levels, beta : as in stokes_params; levels <= 11 (N <= 2048), larger sizes return
+ *                  STOKES_ERR_BAD_ARG before any GPU work
+ *   u, p, f, g   : caller-owned device arrays with the layouts described at the top of this file
+ *   norm2        : caller-owned device double that receives the squared norm (not synchronised)
+ *   stream       : cudaStream_t to run on (NULL = legacy default stream)
+ * The per-block partial sums live in one fixed array inside the library (about 131 KB of device
+ * memory on every GPU that loads the library, kept until the process exits).  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) and builds the host-side
+ * element tables; make that first call before any stream capture.  Every call overwrites the whole
+ * part of the array it reads, so nothing needs clearing, but all calls share the one array: calls
+ * whose GPU work overlaps (different streams or threads without ordering) race and give wrong
+ * results. */
+stokes_status stokes_residual_norm2_noalloc(int levels, double beta, const double* u, const double* p,
+                                            const double* f, const double* g, double* norm2, void* stream);
+
 /* Timing of the hot kernels inside the captured cycle: with enable != 0, the cycle graph is
  * rebuilt with CUDA event records (cudaEventRecordExternal) around every finest-level smoothing
  * step and around the float64 finest-level residual, and stokes_solve accumulates their durations
