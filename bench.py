@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--kernel", default=None, choices=["uzawa_f32", "uzawa_f64", "residual_f64", "mixed_solve"],
                     help="microbenchmark one kernel (for profiler captures) instead of the workload")
     ap.add_argument("--level", type=int, default=9)
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-solver measurement")
+    ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--reps", type=int, default=5)
     return ap.parse_args()
 
@@ -398,6 +400,11 @@ def run_ours(args, rank, world, local_rank):
         for s in s64.values():
             s.close()
 
+    # ---------------------------------------------------------------- batched solves (one graph launch)
+    batch = None
+    if not args.no_batch:
+        batch = run_batch(args, rank, world)
+
     # ---------------------------------------------------------------- CPU oracle baseline
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -420,8 +427,58 @@ def run_ours(args, rank, world, local_rank):
                 "roofline": roofline, "kernels": kernels, "clocks": clk,
                 "e2e": {"value": e2e_value, "unit": "DoF/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "steps": e2e_steps},
-                "gpu_launches": int(launches), "fp64_plain": fp64, "cpu_baseline": cpu}
+                "gpu_launches": int(launches), "fp64_plain": fp64, "batch": batch, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
+
+
+def run_batch(args, rank, world):
+    """Batched workload: args.batch_count instances, levels uniform in k = 4..8 (h = 1/32 .. 1/512),
+    beta log-uniform in [1e-2, 1e8], f and g uniform[-1,1] nodal (seed 3 + rank, g zero-mean),
+    float32 cycles in float64 refinement to 1e-8, all instances in one CUDA-graph launch."""
+    import torch
+
+    from paper_1502_04070_gb300 import workloads
+    from paper_1502_04070_gb300.solver import BatchSolver, Solver
+
+    ks, betas, seeds = workloads.batch_spec(args.batch_count, 3 + rank, k_min=4, k_max=8)
+    t0 = time.perf_counter()
+    B = BatchSolver([k + 1 for k in ks], betas, precision="mixed", autotune=True)
+    setup_s = time.perf_counter() - t0
+    loaders = {}
+    fs, gs = [], []
+    for k, seed in zip(ks, seeds):
+        if k not in loaders:
+            loaders[k] = Solver(k + 1, 1.0)
+        fn, gn = workloads.random_nodal(k, seed)
+        f, g = loaders[k].load_vectors(torch.from_numpy(fn).cuda(), torch.from_numpy(gn).cuda(), project_g=True)
+        fs.append(f)
+        gs.append(g)
+    us = [torch.zeros(B.shapes(i)[0], dtype=torch.float64, device="cuda") for i in range(B.count)]
+    ps = [torch.zeros(B.shapes(i)[1], dtype=torch.float64, device="cuda") for i in range(B.count)]
+    B.solve(fs, gs, tol=TOL, max_cycles=200, us=us, ps=ps)          # warm-up: builds the graph
+    reps = 2
+    torch.cuda.synchronize()
+    launches0 = B.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        for u, p in zip(us, ps):
+            u.zero_()
+            p.zero_()
+        _, _, cyc, rel, st = B.solve(fs, gs, tol=TOL, max_cycles=200, us=us, ps=ps)
+        if st != 0:
+            raise RuntimeError("batched solve failed: status %d" % st)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    total_dof = sum(dofs(k) for k in ks)
+    out = {"value": total_dof / (ms / 1000.0), "unit": "DoF/s", "solves_per_s": B.count / (ms / 1000.0),
+           "ms_per_batch": ms, "instances": B.count, "total_dof": total_dof, "levels_k": "4..8",
+           "max_rel_residual": max(rel), "mean_steps": sum(cyc) / len(cyc), "max_steps": max(cyc),
+           "setup_s": setup_s, "gpu_launches_per_batch": (B.kernel_launches() - launches0) // reps,
+           "host_launches_per_batch": 1}
+    B.close()
+    return out
 
 
 def _kernel_source_sha():

@@ -174,6 +174,31 @@ stokes_status stokes_mass_dot(stokes_handle* h, const double* a, const double* b
 stokes_status stokes_residual_norm2_noalloc(int levels, double beta, const double* u, const double* p,
                                             const double* f, const double* g, double* norm2, void* stream);
 
+/* ---- batches: many independent solves (right-hand sides, beta values, mesh levels) in one launch.
+ * stokes_batch_setup builds `count` solvers; instance i has levels[i] levels and beta betas[i], the
+ * other parameters from `base` (STOKES_MIXED is the intended precision).  With autotune != 0 the
+ * tile shape of the float32 Uzawa kernel is chosen per level size by timing the candidates on the
+ * instances' own buffers (the choice is kept process-wide).  The library owns all buffers. */
+typedef struct stokes_batch_t stokes_batch;
+stokes_status stokes_batch_setup(int count, const int* levels, const double* betas, const stokes_params* base,
+                                 void* stream, int autotune, stokes_batch** out);
+
+/* Solves every instance from its (u[i], p[i]) to ||F - A x|| <= tol ||F|| (at most max_cycles steps)
+ * in ONE launch of a CUDA graph: per instance a prologue, a conditional WHILE node whose body is one
+ * cycle (MIXED: one refinement step) followed by a device-side convergence test, and an epilogue that
+ * checks the true float64 residual and writes (u[i], p[i]).  Instances run concurrently.  u, p, f, g
+ * are host arrays of `count` device pointers with the per-instance layouts above.  The graph is
+ * rebuilt only when the pointers, tol or max_cycles change.  An instance whose true residual misses
+ * tol after the graph (not expected) continues through stokes_solve.  cycles / rel_residual
+ * (caller-owned host arrays of `count`, may be NULL) receive the steps taken and the final relative
+ * residuals.  Synchronises the batch's stream. */
+stokes_status stokes_batch_solve(stokes_batch* b, double* const* u, double* const* p, const double* const* f,
+                                 const double* const* g, double tol, int max_cycles, int* cycles,
+                                 double* rel_residual);
+void stokes_batch_destroy(stokes_batch* b);
+/* Kernels executed by stokes_batch_solve calls so far (loop bodies counted per executed step). */
+unsigned long long stokes_batch_kernel_launches(const stokes_batch* b);
+
 /* Timing of the hot kernels inside the captured cycle: with enable != 0, the cycle graph is
  * rebuilt with CUDA event records (cudaEventRecordExternal) around every finest-level smoothing
  * step and around the float64 finest-level residual, and stokes_solve accumulates their durations

@@ -63,6 +63,12 @@ SIGNATURES = {
     "stokes_mass_dot": (_I, [_P, _P, _P, ctypes.POINTER(_D)]),
     "stokes_make_consistent": (_I, [_P, _P]),
     "stokes_residual_norm2_noalloc": (_I, [_I, _D, _P, _P, _P, _P, _P, _P]),
+    "stokes_batch_setup": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(Params), _P, _I,
+                                ctypes.POINTER(_P)]),
+    "stokes_batch_solve": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "stokes_batch_destroy": (None, [_P]),
+    "stokes_batch_kernel_launches": (ctypes.c_ulonglong, [_P]),
     "stokes_set_timing": (_I, [_P, _I]),
     "stokes_get_timing": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D),
                                ctypes.POINTER(ctypes.c_longlong)]),

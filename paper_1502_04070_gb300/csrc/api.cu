@@ -248,13 +248,13 @@ void record_step(stokes_handle* h) {
         cudaMemsetAsync(E.u, 0, 2 * E.n2 * sizeof(float), h->st);
         cudaMemsetAsync(E.p, 0, E.n1 * sizeof(float), h->st);
         for (int c = 0; c < h->prm.inner_cycles; ++c) mg_cycle<float>(h, h->h32, h->L - 1);
-        // x += e, r -= A e (two-float state, error-free float32 products), r32 = float(r)
+        // x += e, r -= A e (two-float residual, error-free float32 products), r32 = float(r)
         const int k = ev_begin(h);
         if (k >= 0) h->ev_resid++;
         launch_ir_update_df(h->st, F.n, h->chi, h->clo, E.u, E.p, F.u, F.p, F.tu, F.tp, E.f, E.g, h->partial);
         ev_end(h, k);
         launch_reduce(h->st, h->partial, cells_blocks(F.n), h->scal);
-        launch_pmean_df(h->st, F.n, F.p, h->partial, h->scal + 1);
+        launch_pmean<double>(h->st, F.n, F.p, h->partial, h->scal + 1);
     } else {
         mg_cycle<double>(h, h->h64, h->L - 1);
         launch_pmean<double>(h->st, F.n, F.p, h->partial, h->scal + 1);
@@ -355,14 +355,6 @@ stokes_status copy_in(stokes_handle* h, const double* u, const double* p, const 
     CK(cudaMemcpyAsync(F.f, f, 2 * F.n2 * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
     CK(cudaMemcpyAsync(F.g, g, F.n1 * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
     return STOKES_OK;
-}
-
-// MIXED: switch the finest iterate between float64 and the two-float loop representation
-void x_repr(stokes_handle* h, bool to_df) {
-    Level<double>& F = h->fin();
-    launch_to_df(h->st, 2 * F.n2, F.u, to_df);
-    launch_to_df(h->st, F.n1, F.p, to_df);
-    h->launches += 2;
 }
 
 stokes_status copy_out(stokes_handle* h, double* u, double* p) {
@@ -506,16 +498,10 @@ stokes_status stokes_cycle(stokes_handle* h, double* u, double* p, const double*
     if (h->mixed()) {
         residual_norm_fin(h);   // float64 residual and the float32 right-hand side of the correction
         h->launches += 2;
-        x_repr(h, true);
     }
     if ((s = build_graph(h)) != STOKES_OK) return s;
     stokes_status s2 = launch_step(h);
     if (s2 != STOKES_OK) return s2;
-    if (h->mixed()) {
-        x_repr(h, false);
-        launch_pmean<double>(h->st, h->fin().n, h->fin().p, h->partial, h->scal + 1);
-        h->launches += 3;
-    }
     return copy_out(h, u, p);
 }
 
@@ -534,11 +520,7 @@ stokes_status stokes_solve(stokes_handle* h, double* u, double* p, const double*
     const double nF = std::sqrt(nF2);
     residual_norm_fin(h);
     h->launches += 2;
-    bool x_df = false;
-    if (h->mixed()) {
-        x_repr(h, true);
-        x_df = true;
-    }
+
     double r2 = 0.0;
     if ((s = read_scalar(h, 0, &r2)) != STOKES_OK) return s;
     double r0 = std::sqrt(r2), r = r0;
@@ -550,16 +532,12 @@ stokes_status stokes_solve(stokes_handle* h, double* u, double* p, const double*
         if (r <= tol * nF) {
             if (!h->mixed()) break;
             // the refinement residual is updated, not recomputed: confirm with the true one
-            x_repr(h, false);
-            x_df = false;
             residual_norm_fin(h);
             h->launches += 2;
             if ((s = read_scalar(h, 0, &r2)) != STOKES_OK) return s;
             r = std::sqrt(r2);
             if (history) history[cycles] = r;
             if (r <= tol * nF) break;
-            x_repr(h, true);
-            x_df = true;
         }
         // diverged: NaN/Inf, or growth in each of the last 8 cycles (the first cycles from x = 0
         // may raise the Euclidean residual by orders of magnitude before it decays)
@@ -579,11 +557,6 @@ stokes_status stokes_solve(stokes_handle* h, double* u, double* p, const double*
         r = std::sqrt(r2);
         ++cycles;
         if (history) history[cycles] = r;
-    }
-    if (h->mixed()) {
-        if (x_df) x_repr(h, false);
-        launch_pmean<double>(h->st, F.n, F.p, h->partial, h->scal + 1);
-        h->launches += 3;
     }
     if ((s = copy_out(h, u, p)) != STOKES_OK) return s;
     CK(cudaStreamSynchronize(h->st));
@@ -722,5 +695,222 @@ stokes_status stokes_get_timing(const stokes_handle* h, double* smooth_ms, long 
 }
 
 unsigned long long stokes_kernel_launches(const stokes_handle* h) { return h ? h->launches : 0ull; }
+
+// ----------------------------------------------------------------------------------- batches
+
+struct stokes_batch_t {
+    int count = 0;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    std::vector<stokes_handle*> inst;
+    std::vector<int> body_kernels;      // kernels per loop iteration of each instance
+    cudaGraphExec_t exec = nullptr;
+    std::vector<const void*> key;       // pointers, tol and max_cycles the graph was built for
+    double tol = -1.0;
+    int max_cycles = -1;
+    int* d_count = nullptr;             // device: refinement steps per instance
+    double* d_res = nullptr;            // device: per instance (true ||r||^2, ||F||^2, steps)
+    double* h_res = nullptr;            // pinned mirror
+    unsigned long long launches = 0;
+};
+
+void stokes_batch_destroy(stokes_batch* b) {
+    if (!b) return;
+    if (b->st) cudaStreamSynchronize(b->st);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (auto h : b->inst) stokes_destroy(h);
+    if (b->d_count) cudaFree(b->d_count);
+    if (b->d_res) cudaFree(b->d_res);
+    if (b->h_res) cudaFreeHost(b->h_res);
+    if (b->own_stream && b->st) cudaStreamDestroy(b->st);
+    delete b;
+}
+
+stokes_status stokes_batch_setup(int count, const int* levels, const double* betas, const stokes_params* base,
+                                 void* stream, int autotune, stokes_batch** out) {
+    if (count < 1 || !levels || !betas || !base || !out) return STOKES_ERR_BAD_ARG;
+    *out = nullptr;
+    stokes_batch* b = new stokes_batch_t();
+    b->count = count;
+    if (stream) {
+        b->st = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreate(&b->st) != cudaSuccess) {
+            delete b;
+            return STOKES_ERR_CUDA;
+        }
+        b->own_stream = true;
+    }
+    stokes_status s;
+    for (int i = 0; i < count; ++i) {
+        stokes_params prm = *base;
+        prm.levels = levels[i];
+        prm.beta = betas[i];
+        stokes_handle* h = nullptr;
+        if ((s = stokes_setup(&prm, b->st, &h)) != STOKES_OK) {
+            stokes_batch_destroy(b);
+            return s;
+        }
+        b->inst.push_back(h);
+    }
+    if (cudaMalloc(&b->d_count, sizeof(int) * count) != cudaSuccess ||
+        cudaMalloc(&b->d_res, sizeof(double) * 3 * count) != cudaSuccess ||
+        cudaMallocHost(&b->h_res, sizeof(double) * 3 * count) != cudaSuccess) {
+        cudaGetLastError();
+        stokes_batch_destroy(b);
+        return STOKES_ERR_OOM;
+    }
+    if (autotune && base->precision == STOKES_MIXED && base->smoother == STOKES_UZAWA) {
+        // tile shape of the fused float32 Uzawa step, per level size, timed on an instance's buffers
+        std::vector<bool> done(14, false);
+        for (auto h : b->inst)
+            for (int l = 1; l < (int)h->h32.size(); ++l) {
+                if (done[l]) continue;
+                done[l] = true;
+                Level<float>& lv = h->h32[l];
+                cudaError_t e = autotune_uzawa_fused(b->st, lv.n, lv.c, (float)h->prm.tau, (float)h->prm.sigma, lv.u,
+                                                     lv.p, lv.f, lv.g, lv.sinv, lv.tu, lv.tp, nullptr, nullptr);
+                if (e != cudaSuccess) {
+                    stokes_batch_destroy(b);
+                    return fail(e);
+                }
+                // leave the level buffers as a fresh handle has them
+                cudaMemsetAsync(lv.u, 0, 2 * lv.n2 * sizeof(float), b->st);
+                cudaMemsetAsync(lv.p, 0, lv.n1 * sizeof(float), b->st);
+                cudaMemsetAsync(lv.tu, 0, 2 * lv.n2 * sizeof(float), b->st);
+                cudaMemsetAsync(lv.tp, 0, lv.n1 * sizeof(float), b->st);
+            }
+        if (cudaStreamSynchronize(b->st) != cudaSuccess) {
+            stokes_batch_destroy(b);
+            return STOKES_ERR_CUDA;
+        }
+    }
+    *out = b;
+    return STOKES_OK;
+}
+
+static stokes_status batch_build(stokes_batch* b, double* const* u, double* const* p, const double* const* f,
+                                 const double* const* g, double tol, int max_cycles) {
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    cudaStream_t st = b->st;
+    cudaGraph_t top = nullptr;
+    CK(cudaGraphCreate(&top, 0));
+    b->body_kernels.assign(b->count, 0);
+    auto count_kernels = [](cudaGraph_t gr) {
+        size_t nn = 0;
+        cudaGraphGetNodes(gr, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        cudaGraphGetNodes(gr, nodes.data(), &nn);
+        int k = 0;
+        for (auto nd : nodes) {
+            cudaGraphNodeType ty;
+            if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++k;
+        }
+        return k;
+    };
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < b->count && e == cudaSuccess; ++i) {
+        stokes_handle* h = b->inst[i];
+        Level<double>& F = h->fin();
+        const bool mixed = h->mixed();
+        // prologue: inputs in, ||F||, true residual, step counter
+        cudaGraph_t gp = nullptr;
+        if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) break;
+        copy_in(h, u[i], p[i], f[i], g[i]);
+        launch_rhs_norm(st, F.n, F.f, F.g, h->partial);
+        launch_reduce(st, h->partial, cells_blocks(F.n), h->scal + 2);
+        residual_norm_fin(h);
+        cudaMemsetAsync(b->d_count + i, 0, sizeof(int), st);
+        if ((e = cudaStreamEndCapture(st, &gp)) != cudaSuccess) break;
+        cudaGraphNode_t np, nc, ne;
+        e = cudaGraphAddChildGraphNode(&np, top, nullptr, 0, gp);
+        cudaGraphDestroy(gp);
+        if (e != cudaSuccess) break;
+        // loop: WHILE the step's residual is above the tolerance (with a 2x margin in MIXED mode,
+        // whose updated residual is confirmed by the true one in the epilogue)
+        cudaGraphConditionalHandle hnd;
+        if ((e = cudaGraphConditionalHandleCreate(&hnd, top, 1, cudaGraphCondAssignDefault)) != cudaSuccess) break;
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = hnd;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        if ((e = cudaGraphAddNode(&nc, top, &np, nullptr, 1, &cp)) != cudaSuccess) break;
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        if ((e = cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+            cudaSuccess)
+            break;
+        record_step(h);
+        const double t = mixed ? 0.5 * tol : tol;
+        launch_batch_check(st, hnd, h->scal, t * t, max_cycles, b->d_count + i);
+        if ((e = cudaStreamEndCapture(st, &body)) != cudaSuccess) break;
+        b->body_kernels[i] = count_kernels(body);
+        // epilogue: true residual, results out
+        cudaGraph_t ge = nullptr;
+        if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) break;
+        residual_norm_fin(h);
+        launch_batch_store(st, h->scal, b->d_count + i, b->d_res + 3 * i);
+        copy_out(h, u[i], p[i]);
+        if ((e = cudaStreamEndCapture(st, &ge)) != cudaSuccess) break;
+        e = cudaGraphAddChildGraphNode(&ne, top, &nc, 1, ge);
+        cudaGraphDestroy(ge);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, top, 0);
+    cudaGraphDestroy(top);
+    if (e != cudaSuccess) {
+        b->exec = nullptr;
+        return fail(e);
+    }
+    return STOKES_OK;
+}
+
+stokes_status stokes_batch_solve(stokes_batch* b, double* const* u, double* const* p, const double* const* f,
+                                 const double* const* g, double tol, int max_cycles, int* cycles,
+                                 double* rel_residual) {
+    if (!b || !u || !p || !f || !g || !(tol > 0.0) || max_cycles < 1) return STOKES_ERR_BAD_ARG;
+    std::vector<const void*> key;
+    for (int i = 0; i < b->count; ++i) {
+        if (!u[i] || !p[i] || !f[i] || !g[i]) return STOKES_ERR_BAD_ARG;
+        key.insert(key.end(), {u[i], p[i], f[i], g[i]});
+    }
+    stokes_status s;
+    if (!b->exec || key != b->key || tol != b->tol || max_cycles != b->max_cycles) {
+        if ((s = batch_build(b, u, p, f, g, tol, max_cycles)) != STOKES_OK) return s;
+        b->key = key;
+        b->tol = tol;
+        b->max_cycles = max_cycles;
+    }
+    CK(cudaGraphLaunch(b->exec, b->st));
+    CK(cudaMemcpyAsync(b->h_res, b->d_res, sizeof(double) * 3 * b->count, cudaMemcpyDeviceToHost, b->st));
+    CK(cudaStreamSynchronize(b->st));
+    stokes_status result = STOKES_OK;
+    for (int i = 0; i < b->count; ++i) {
+        stokes_handle* h = b->inst[i];
+        const int steps = (int)b->h_res[3 * i + 2];
+        const double nF = std::sqrt(b->h_res[3 * i + 1]);
+        double r = std::sqrt(b->h_res[3 * i]);
+        b->launches += 4 + 3 + (unsigned long long)steps * (b->body_kernels[i] + 1);
+        int total = steps;
+        if (!(r <= tol * nF)) {
+            // rare: the true residual misses the tolerance; continue this instance on its own
+            stokes_report rep{};
+            const unsigned long long before = h->launches;
+            stokes_status si = stokes_solve(h, u[i], p[i], f[i], g[i], tol, max_cycles > steps ? max_cycles - steps : 1,
+                                            &rep, nullptr);
+            b->launches += h->launches - before;
+            total += rep.cycles;
+            r = rep.rel_residual * nF;
+            if (si != STOKES_OK && result == STOKES_OK) result = si;
+        }
+        if (cycles) cycles[i] = total;
+        if (rel_residual) rel_residual[i] = nF > 0 ? r / nF : r;
+    }
+    return result;
+}
+
+unsigned long long stokes_batch_kernel_launches(const stokes_batch* b) { return b ? b->launches : 0ull; }
 
 }  // extern "C"

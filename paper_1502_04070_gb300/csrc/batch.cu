@@ -1,0 +1,41 @@
+// batch.cu -- device-side loop control of the batched solver.
+//
+// Every instance of a batch runs its refinement steps inside a conditional WHILE node of one CUDA
+// graph; after each step this kernel decides on the device whether the instance goes on, so the
+// whole batch runs to convergence in one graph launch without returning to the host.
+#include <cuda_runtime.h>
+
+#include "kernels.cuh"
+
+namespace smg {
+
+// scal[0] = ||r||^2 of the last step, scal[2] = ||F||^2.  Continue while ||r||^2 > tol2 ||F||^2,
+// the step count is below max_cycles and the residual is finite.
+__global__ void k_batch_check(cudaGraphConditionalHandle hnd, const double* __restrict__ scal, double tol2,
+                              int max_cycles, int* __restrict__ count) {
+    if (threadIdx.x != 0) return;
+    const int c = *count + 1;
+    *count = c;
+    const double r2 = scal[0];
+    const bool go = isfinite(r2) && r2 > tol2 * scal[2] && c < max_cycles;
+    cudaGraphSetConditional(hnd, go ? 1u : 0u);
+}
+
+__global__ void k_batch_store(const double* __restrict__ scal, const int* __restrict__ count,
+                              double* __restrict__ out) {
+    if (threadIdx.x != 0) return;
+    out[0] = scal[0];
+    out[1] = scal[2];
+    out[2] = (double)*count;
+}
+
+void launch_batch_check(cudaStream_t s, cudaGraphConditionalHandle hnd, const double* scal, double tol2,
+                        int max_cycles, int* count) {
+    k_batch_check<<<1, 32, 0, s>>>(hnd, scal, tol2, max_cycles, count);
+}
+
+void launch_batch_store(cudaStream_t s, const double* scal, const int* count, double* out) {
+    k_batch_store<<<1, 32, 0, s>>>(scal, count, out);
+}
+
+}  // namespace smg

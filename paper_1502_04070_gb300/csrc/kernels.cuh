@@ -19,12 +19,6 @@ template <typename T, typename TO>
 void launch_residual(cudaStream_t s, int n, const OpCoef<T>& c, const T* u, const T* p, const T* f,
                      const T* g, TO* ru, TO* rp, double* partial, float* ru2 = nullptr, float* rp2 = nullptr);
 
-// Refinement update (float32 correction e of a float64 iterate x with float64 residual r):
-//   x += e,  r -= A e  (products with error-free float32 transformations, ~2^-48 relative),
-//   r32 = float(r), partial sums of r.r.
-void launch_ir_update(cudaStream_t s, int n, const OpCoef<float>& chi, const OpCoef<float>& clo,
-                      const float* eu, const float* ep, double* xu, double* xp, double* ru, double* rp,
-                      float* r32u, float* r32p, double* partial);
 
 // Uzawa step (Sec. 4), three kernels:
 //   uh = u + tau Ahat^{-1} (f - A u - B^T p)
@@ -34,16 +28,16 @@ template <typename T>
 void launch_uzawa(cudaStream_t s, int n, const OpCoef<T>& c, T tau, T sigma, T* u, T* p, const T* f,
                   const T* g, const T* sinv, T* uh, T* dp);
 
-// Two-float refinement state (see refine.cu): x, r stored as (hi, lo) float pairs in the 8-byte
-// slots of float64 arrays during the refinement loop.
+// Refinement update (see refine.cu): float32 correction e, float64 iterate x, residual r stored as
+// (hi, lo) float pairs in the 8-byte slots of a float64 array:
+//   x += e,  r -= A e  (error-free float32 products, ~2^-48 relative),  r32 = float(r),
+//   partial sums of r.r.
 void launch_ir_update_df(cudaStream_t s, int n, const OpCoef<float>& chi, const OpCoef<float>& clo,
                          const float* eu, const float* ep, double* xu, double* xp, double* ru, double* rp,
                          float* r32u, float* r32p, double* partial);
 void launch_residual_df(cudaStream_t s, int n, const OpCoef<double>& c, const double* u, const double* p,
                         const double* f, const double* g, double* ru, double* rp, float* r32u, float* r32p,
                         double* partial);
-void launch_to_df(cudaStream_t s, size_t count, double* x, bool to_df);
-void launch_pmean_df(cudaStream_t s, int n, double* p, double* partial, double* scalar);
 
 // The same Uzawa step fused into one kernel with shared-memory halos: reads (u, p), writes
 // (u_out, p_out) (distinct buffers).
@@ -52,6 +46,11 @@ cudaError_t prepare_uzawa_fused();   // raises the kernel's shared-memory limit 
 template <typename T>
 cudaError_t launch_uzawa_fused(cudaStream_t s, int n, const OpCoef<T>& c, T tau, T sigma, const T* u, const T* p,
                                const T* f, const T* g, const T* sinv, T* u_out, T* p_out);
+// Picks the fastest float32 tile shape for level size n by timing each on these buffers (their
+// contents are overwritten); returns the variant index and its time per step.
+cudaError_t autotune_uzawa_fused(cudaStream_t s, int n, const OpCoef<float>& c, float tau, float sigma, float* u,
+                                 float* p, const float* f, const float* g, const float* sinv, float* u_out,
+                                 float* p_out, int* chosen, float* best_ms);
 
 // Normal-equation step (Sec. 4): x += tau L^{-1} A L^{-1} (F - A x),  L = diag(Ahat, Shat).
 template <typename T>
@@ -96,6 +95,11 @@ void launch_rhs_norm(cudaStream_t s, int n, const double* f, const double* g, do
 // g <- g - (1^T g) w  with w = M_P 1: the pressure right-hand side becomes orthogonal to the
 // constant pressure (the kernel of the saddle-point matrix)
 void launch_make_consistent(cudaStream_t s, int n, double* g, double* partial, double* scalar);
+
+// batched solver: device-side WHILE condition and result store (batch.cu)
+void launch_batch_check(cudaStream_t s, cudaGraphConditionalHandle hnd, const double* scal, double tol2,
+                        int max_cycles, int* count);
+void launch_batch_store(cudaStream_t s, const double* scal, const int* count, double* out);
 
 // x64 += e32 (count elements), and float64 -> float32 conversion
 void launch_add_f32(cudaStream_t s, size_t count, const float* e, double* x);

@@ -11,10 +11,11 @@
 // float64 residual before it reports convergence.
 //
 // GB300 also runs conversions and additions in float64 on its narrow float64 pipe, so during the
-// refinement loop the iterate x and the residual r are kept as unevaluated sums of two floats
-// (hi + lo, about 48 significant bits) stored in the float64 arrays' own 8-byte slots; the loop
-// then issues no float64 instruction per unknown.  x is converted back to float64 for the true
-// residual check and for the caller.
+// refinement loop the residual r is kept as an unevaluated sum of two floats (hi + lo, about 48
+// significant bits) in the float64 array's own 8-byte slots; per unknown the loop issues only the
+// two float64 instructions of x += e.  x itself stays float64: its precision bounds the attainable
+// residual, and with two floats the solve stalled at 1.8e-8 relative residual for beta = 1e8 on
+// h = 1/512, where |A| |x| is large against |F|.
 #include "cellops.cuh"
 #include "kernels.cuh"
 
@@ -93,54 +94,6 @@ __device__ __forceinline__ void visit_df(int i, int j, int n, const OpCoef<float
     }
 }
 
-__global__ void __launch_bounds__(NT) k_ir_update(int n, const __grid_constant__ OpCoef<float> ch,
-                                                  const __grid_constant__ OpCoef<float> cl,
-                                                  const float* __restrict__ eu, const float* __restrict__ ep,
-                                                  double* __restrict__ xu, double* __restrict__ xp,
-                                                  double* __restrict__ ru, double* __restrict__ rp,
-                                                  float* __restrict__ r32u, float* __restrict__ r32p,
-                                                  double* __restrict__ partial) {
-    CELL_INDEX
-    const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
-    double ss = 0.0;
-    if (active) {
-        DFAcc a;
-#pragma unroll
-        for (int s = 0; s < 4; ++s) a.au[0][s] = a.au[1][s] = DF{0.f, 0.f};
-        a.bu = DF{0.f, 0.f};
-        visit_df<0>(i, j, n, ch, cl, eu, ep, a);
-        visit_df<1>(i, j, n, ch, cl, eu, ep, a);
-        visit_df<2>(i, j, n, ch, cl, eu, ep, a);
-        visit_df<3>(i, j, n, ch, cl, eu, ep, a);
-        const CellNodes cn = cell_nodes(i, j, n);
-        const int ld = 2 * n + 1;
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            if (!slot_unknown(cn, s)) continue;
-            int X, Y;
-            slot_pos(i, j, s, X, Y);
-            const size_t idx = (size_t)Y * ld + X;
-#pragma unroll
-            for (int comp = 0; comp < 2; ++comp) {
-                const size_t k = comp * n2 + idx;
-                xu[k] += (double)eu[k];
-                const double r = ru[k] - df_value(a.au[comp][s]);
-                ru[k] = r;
-                r32u[k] = (float)r;
-                ss += r * r;
-            }
-        }
-        const size_t vi = (size_t)j * (n + 1) + i;
-        xp[vi] += (double)ep[vi];
-        const double r = rp[vi] - df_value(a.bu);
-        rp[vi] = r;
-        r32p[vi] = (float)r;
-        ss += r * r;
-    }
-    const double t = block_sum2d(ss, tid);
-    if (tid == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = t;
-}
-
 // ---------------------------------------------------------------------------------------------
 // two-float ("double-float") state
 
@@ -153,12 +106,6 @@ __device__ __forceinline__ float2 renorm(float s, float e) {
     const float hi = __fadd_rn(s, e);
     return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, s)));
 }
-// a + b, b a float
-__device__ __forceinline__ float2 df_add(float2 a, float b) {
-    float s, e;
-    two_sum(a.x, b, s, e);
-    return renorm(s, __fadd_rn(e, a.y));
-}
 // a - (b.hi + b.lo)
 __device__ __forceinline__ float2 df_sub(float2 a, const DF& b) {
     float s, e;
@@ -169,7 +116,7 @@ __device__ __forceinline__ float2 df_sub(float2 a, const DF& b) {
 __global__ void __launch_bounds__(NT) k_ir_update_df(int n, const __grid_constant__ OpCoef<float> ch,
                                                      const __grid_constant__ OpCoef<float> cl,
                                                      const float* __restrict__ eu, const float* __restrict__ ep,
-                                                     float2* __restrict__ xu, float2* __restrict__ xp,
+                                                     double* __restrict__ xu, double* __restrict__ xp,
                                                      float2* __restrict__ ru, float2* __restrict__ rp,
                                                      float* __restrict__ r32u, float* __restrict__ r32p,
                                                      double* __restrict__ partial) {
@@ -196,7 +143,7 @@ __global__ void __launch_bounds__(NT) k_ir_update_df(int n, const __grid_constan
 #pragma unroll
             for (int comp = 0; comp < 2; ++comp) {
                 const size_t k = comp * n2 + idx;
-                xu[k] = df_add(xu[k], eu[k]);
+                xu[k] += (double)eu[k];
                 const float2 r = df_sub(ru[k], a.au[comp][s]);
                 ru[k] = r;
                 r32u[k] = r.x;
@@ -204,7 +151,7 @@ __global__ void __launch_bounds__(NT) k_ir_update_df(int n, const __grid_constan
             }
         }
         const size_t vi = (size_t)j * (n + 1) + i;
-        xp[vi] = df_add(xp[vi], ep[vi]);
+        xp[vi] += (double)ep[vi];
         const float2 r = df_sub(rp[vi], a.bu);
         rp[vi] = r;
         r32p[vi] = r.x;
@@ -258,56 +205,11 @@ __global__ void __launch_bounds__(NT) k_residual_df(int n, const __grid_constant
     if (tid == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = t;
 }
 
-// in-place conversions between float64 and two-float storage of the same 8-byte slots
-__global__ void k_to_df(size_t count, double* __restrict__ x) {
-    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < count; k += (size_t)gridDim.x * blockDim.x) {
-        const double v = x[k];
-        const float hi = (float)v;
-        reinterpret_cast<float2*>(x)[k] = make_float2(hi, (float)(v - (double)hi));
-    }
-}
-__global__ void k_from_df(size_t count, double* __restrict__ x) {
-    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < count; k += (size_t)gridDim.x * blockDim.x) {
-        const float2 v = reinterpret_cast<const float2*>(x)[k];
-        x[k] = (double)v.x + (double)v.y;
-    }
-}
-
-// zero-mean projection of a two-float pressure: partial sums of w_i p_i (float per thread), then
-// p <- p - c.  c only shifts p by a constant, which no residual sees (B^T 1 = 0); the float64
-// projection is redone when x returns to float64.
-__global__ void __launch_bounds__(NT) k_pmean_partial_df(int n, const float2* __restrict__ p,
-                                                         double* __restrict__ partial) {
-    CELL_INDEX
-    float v = 0.f;
-    if (active) {
-        int cnt = 0;
-#pragma unroll
-        for (int SQ = 0; SQ < 4; ++SQ) {
-            const int si = i - (SQ & 1), sj = j - (SQ >> 1);
-            if (si < 0 || sj < 0 || si >= n || sj >= n) continue;
-            const int o = orient(si, sj, n), node = corner_node(SQ);
-            cnt += ((tri_mask(o, 0) >> node) & 1u) + ((tri_mask(o, 1) >> node) & 1u);
-        }
-        const float h = 1.f / n;
-        v = cnt * h * h * (1.f / 6.f) * p[(size_t)j * (n + 1) + i].x;
-    }
-    const double t = block_sum2d((double)v, tid);
-    if (tid == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = t;
-}
-__global__ void __launch_bounds__(NT) k_psub_df(int n, float2* __restrict__ p, const double* __restrict__ scalar) {
-    CELL_INDEX
-    if (!active) return;
-    const size_t vi = (size_t)j * (n + 1) + i;
-    p[vi] = df_add(p[vi], -(float)(*scalar));
-}
-
 void launch_ir_update_df(cudaStream_t s, int n, const OpCoef<float>& chi, const OpCoef<float>& clo,
                          const float* eu, const float* ep, double* xu, double* xp, double* ru, double* rp,
                          float* r32u, float* r32p, double* partial) {
-    k_ir_update_df<<<cells_grid(n), dim3(BX, BY), 0, s>>>(
-        n, chi, clo, eu, ep, reinterpret_cast<float2*>(xu), reinterpret_cast<float2*>(xp),
-        reinterpret_cast<float2*>(ru), reinterpret_cast<float2*>(rp), r32u, r32p, partial);
+    k_ir_update_df<<<cells_grid(n), dim3(BX, BY), 0, s>>>(n, chi, clo, eu, ep, xu, xp, reinterpret_cast<float2*>(ru),
+                                                          reinterpret_cast<float2*>(rp), r32u, r32p, partial);
 }
 
 void launch_residual_df(cudaStream_t s, int n, const OpCoef<double>& c, const double* u, const double* p,
@@ -315,26 +217,6 @@ void launch_residual_df(cudaStream_t s, int n, const OpCoef<double>& c, const do
                         double* partial) {
     k_residual_df<<<cells_grid(n), dim3(BX, BY), 0, s>>>(n, c, u, p, f, g, reinterpret_cast<float2*>(ru),
                                                          reinterpret_cast<float2*>(rp), r32u, r32p, partial);
-}
-
-void launch_to_df(cudaStream_t s, size_t count, double* x, bool to_df) {
-    const size_t want = (count + 255) / 256;
-    const int blocks = (int)(want < 152 * 16 ? (want > 0 ? want : 1) : 152 * 16);
-    if (to_df) k_to_df<<<blocks, 256, 0, s>>>(count, x);
-    else k_from_df<<<blocks, 256, 0, s>>>(count, x);
-}
-
-void launch_pmean_df(cudaStream_t s, int n, double* p, double* partial, double* scalar) {
-    const dim3 grid = cells_grid(n), blk(BX, BY);
-    k_pmean_partial_df<<<grid, blk, 0, s>>>(n, reinterpret_cast<const float2*>(p), partial);
-    launch_reduce(s, partial, grid.x * grid.y, scalar);
-    k_psub_df<<<grid, blk, 0, s>>>(n, reinterpret_cast<float2*>(p), scalar);
-}
-
-void launch_ir_update(cudaStream_t s, int n, const OpCoef<float>& chi, const OpCoef<float>& clo,
-                      const float* eu, const float* ep, double* xu, double* xp, double* ru, double* rp,
-                      float* r32u, float* r32p, double* partial) {
-    k_ir_update<<<cells_grid(n), dim3(BX, BY), 0, s>>>(n, chi, clo, eu, ep, xu, xp, ru, rp, r32u, r32p, partial);
 }
 
 }  // namespace smg

@@ -158,46 +158,106 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 4 ? 2 : 1)) k_uzawa_fuse
     p_out[(size_t)cj * (n + 1) + ci] = vp(ci, cj) + vd(ci, cj);
 }
 
+// Tile shapes (TX x TY cells) the autotuner chooses from, per level, for float32; float64 uses 32 x 8.
+// 0: 32 x 16, 1: 32 x 8, 2: 64 x 8, 3: 16 x 16.
+constexpr int kFusedVariants = 4;
+static int g_tile_choice[32] = {};   // per level k (N = 2^(k+1)), default variant 0
+
+static int level_of(int n) {
+    int k = 0;
+    while ((2 << k) < n) ++k;
+    return k < 32 ? k : 31;
+}
+
 template <typename T, int TX, int TY>
-static cudaError_t launch_fused_t(cudaStream_t s, int n, const OpCoef<T>& c, T tau, T sigma, const T* u,
-                                  const T* p, const T* f, const T* g, const T* sinv, T* u_out, T* p_out) {
-    using G = FusedTile<T, TX, TY>;
-    static unsigned long long attr = 0;   // devices on which the shared-memory limit is raised
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev >= 64 || !((attr >> dev) & 1ull)) {
-        cudaError_t e = cudaFuncSetAttribute(k_uzawa_fused<T, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)G::BYTES);
-        if (e != cudaSuccess) return e;
-        if (dev < 64) attr |= 1ull << dev;
-    }
-    const dim3 grid((n + 1 + TX - 1) / TX, (n + 1 + TY - 1) / TY), blk(TX, TY);
-    k_uzawa_fused<T, TX, TY><<<grid, blk, G::BYTES, s>>>(n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
-    return cudaSuccess;
+static cudaError_t set_smem_attr() {
+    return cudaFuncSetAttribute(k_uzawa_fused<T, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)FusedTile<T, TX, TY>::BYTES);
 }
 
 template <typename T>
 cudaError_t prepare_uzawa_fused() {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if constexpr (sizeof(T) == 4)
-        return cudaFuncSetAttribute(k_uzawa_fused<T, 32, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)FusedTile<T, 32, 16>::BYTES);
-    else
-        return cudaFuncSetAttribute(k_uzawa_fused<T, 32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)FusedTile<T, 32, 8>::BYTES);
+    if constexpr (sizeof(T) == 4) {
+        cudaError_t e;
+        if ((e = set_smem_attr<T, 32, 16>()) != cudaSuccess) return e;
+        if ((e = set_smem_attr<T, 32, 8>()) != cudaSuccess) return e;
+        if ((e = set_smem_attr<T, 64, 8>()) != cudaSuccess) return e;
+        return set_smem_attr<T, 16, 16>();
+    } else {
+        return set_smem_attr<T, 32, 8>();
+    }
 }
 template cudaError_t prepare_uzawa_fused<float>();
 template cudaError_t prepare_uzawa_fused<double>();
 
+template <typename T, int TX, int TY>
+static void launch_v(cudaStream_t s, int n, const OpCoef<T>& c, T tau, T sigma, const T* u, const T* p, const T* f,
+                     const T* g, const T* sinv, T* u_out, T* p_out) {
+    using G = FusedTile<T, TX, TY>;
+    const dim3 grid((n + 1 + TX - 1) / TX, (n + 1 + TY - 1) / TY), blk(TX, TY);
+    k_uzawa_fused<T, TX, TY><<<grid, blk, G::BYTES, s>>>(n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
+}
+
+template <typename T>
+static void launch_variant(int v, cudaStream_t s, int n, const OpCoef<T>& c, T tau, T sigma, const T* u, const T* p,
+                           const T* f, const T* g, const T* sinv, T* u_out, T* p_out) {
+    if constexpr (sizeof(T) == 4) {
+        switch (v) {
+            case 1: launch_v<T, 32, 8>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out); return;
+            case 2: launch_v<T, 64, 8>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out); return;
+            case 3: launch_v<T, 16, 16>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out); return;
+            default: launch_v<T, 32, 16>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out); return;
+        }
+    } else {
+        launch_v<T, 32, 8>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
+    }
+}
+
 template <typename T>
 cudaError_t launch_uzawa_fused(cudaStream_t s, int n, const OpCoef<T>& c, T tau, T sigma, const T* u, const T* p,
                                const T* f, const T* g, const T* sinv, T* u_out, T* p_out) {
-    // tile: 32 x 16 cells (55.6 KB of float32 shared memory), 32 x 8 for float64 (74 KB)
-    if constexpr (sizeof(T) == 4)
-        return launch_fused_t<T, 32, 16>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
-    else
-        return launch_fused_t<T, 32, 8>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
+    launch_variant<T>(sizeof(T) == 4 ? g_tile_choice[level_of(n)] : 0, s, n, c, tau, sigma, u, p, f, g, sinv,
+                      u_out, p_out);
+    return cudaSuccess;
+}
+
+// Times every tile shape on the given level buffers (the step is applied to (u, p) -> (u_out, p_out)
+// repeatedly; the caller's data are overwritten) and keeps the fastest for this level size.
+cudaError_t autotune_uzawa_fused(cudaStream_t s, int n, const OpCoef<float>& c, float tau, float sigma, float* u,
+                                 float* p, const float* f, const float* g, const float* sinv, float* u_out,
+                                 float* p_out, int* chosen, float* best_ms) {
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return cudaErrorUnknown;
+    int best = 0;
+    float bms = 1e30f;
+    const int reps = n >= 512 ? 5 : 20;
+    for (int v = 0; v < kFusedVariants; ++v) {
+        launch_variant<float>(v, s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);   // warm-up
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps; ++r)
+            launch_variant<float>(v, s, n, c, tau, sigma, (r & 1) ? u_out : u, (r & 1) ? p_out : p, f, g, sinv,
+                                  (r & 1) ? u : u_out, (r & 1) ? p : p_out);
+        cudaEventRecord(e1, s);
+        cudaError_t err = cudaEventSynchronize(e1);
+        if (err != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return err;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= reps;
+        if (ms < bms) {
+            bms = ms;
+            best = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    g_tile_choice[level_of(n)] = best;
+    if (chosen) *chosen = best;
+    if (best_ms) *best_ms = bms;
+    return cudaGetLastError();
 }
 
 template cudaError_t launch_uzawa_fused<float>(cudaStream_t, int, const OpCoef<float>&, float, float, const float*,

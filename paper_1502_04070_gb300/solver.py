@@ -210,3 +210,68 @@ class Solver:
         B.check(self._lib.stokes_mass_dot(self._h, self._chk(a, self.shape_u, "a"), self._chk(b, self.shape_u, "b"),
                                           ctypes.byref(out)), "stokes_mass_dot")
         return out.value
+
+
+class BatchSolver:
+    """Many independent solves (levels, beta per instance) run to convergence in one CUDA-graph
+    launch (stokes_batch_setup / stokes_batch_solve)."""
+
+    def __init__(self, levels, betas, *, precision="mixed", nu_pre=3, nu_post=3, tau=0.8, sigma=0.8, gamma=1,
+                 autotune=True, device=None):
+        self._lib = B.load()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.levels = [int(l) for l in levels]
+        self.betas = [float(b) for b in betas]
+        assert len(self.levels) == len(self.betas) and len(self.levels) > 0
+        prm = B.Params()
+        self._lib.stokes_default_params(ctypes.byref(prm), 1, 0.0)
+        prm.nu_pre, prm.nu_post, prm.tau, prm.sigma, prm.gamma = nu_pre, nu_post, tau, sigma, gamma
+        prm.precision = _PREC[precision]
+        n = len(self.levels)
+        lv = (ctypes.c_int * n)(*self.levels)
+        bt = (ctypes.c_double * n)(*self.betas)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            s = torch.cuda.current_stream()
+            B.check(self._lib.stokes_batch_setup(n, lv, bt, ctypes.byref(prm), ctypes.c_void_p(s.cuda_stream),
+                                                 int(autotune), ctypes.byref(h)), "stokes_batch_setup")
+        self._h = h
+        self.count = n
+
+    def shapes(self, i):
+        N = 2 ** self.levels[i]
+        return (2, 2 * N + 1, 2 * N + 1), (N + 1, N + 1)
+
+    def solve(self, fs, gs, tol=1e-8, max_cycles=200, us=None, ps=None):
+        n = self.count
+        us = [torch.zeros(self.shapes(i)[0], dtype=torch.float64, device=self.device) for i in range(n)] \
+            if us is None else us
+        ps = [torch.zeros(self.shapes(i)[1], dtype=torch.float64, device=self.device) for i in range(n)] \
+            if ps is None else ps
+        for i in range(n):
+            su, sp = self.shapes(i)
+            for t, sh in ((us[i], su), (ps[i], sp), (fs[i], su), (gs[i], sp)):
+                if t.dtype != torch.float64 or tuple(t.shape) != sh or not t.is_contiguous() or t.device != self.device:
+                    raise ValueError("instance %d: expected contiguous float64 tensors of shape %s" % (i, sh))
+        arr = lambda ts: (ctypes.c_void_p * n)(*[t.data_ptr() for t in ts])
+        cyc = (ctypes.c_int * n)()
+        rel = (ctypes.c_double * n)()
+        st = self._lib.stokes_batch_solve(self._h, arr(us), arr(ps), arr(fs), arr(gs), float(tol), int(max_cycles),
+                                          cyc, rel)
+        if st not in (B.OK, B.NOT_CONVERGED, B.DIVERGED):
+            B.check(st, "stokes_batch_solve")
+        return us, ps, list(cyc), list(rel), st
+
+    def kernel_launches(self):
+        return int(self._lib.stokes_batch_kernel_launches(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.stokes_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
