@@ -174,6 +174,16 @@ stokes_status stokes_mass_dot(stokes_handle* h, const double* a, const double* b
 stokes_status stokes_residual_norm2_noalloc(int levels, double beta, const double* u, const double* p,
                                             const double* f, const double* g, double* norm2, void* stream);
 
+/* Chooses, for every level of a STOKES_MIXED handle whose size has not been tuned in this process,
+ * the fastest float32 Uzawa step variant (fused one-kernel tiles of several shapes, or the
+ * three-kernel step with several block shapes) by timing each on the handle's buffers; the choice
+ * is kept process-wide per level size.  Untuned levels use the three-kernel step below N = 128 and
+ * the 32 x 16 fused tile above.  Synchronises the stream. */
+stokes_status stokes_autotune(stokes_handle* h);
+/* The step variant currently used for a float32 level with `levels` levels (N = 2^levels), -1 if
+ * out of range: 0-3 fused tiles 32x16, 32x8, 64x8, 16x16; 4-6 three-kernel step, blocks 32x8, 16x8, 8x8. */
+int stokes_step_variant(int levels);
+
 /* ---- batches: many independent solves (right-hand sides, beta values, mesh levels) in one launch.
  * stokes_batch_setup builds `count` solvers; instance i has levels[i] levels and beta betas[i], the
  * other parameters from `base` (STOKES_MIXED is the intended precision).  With autotune != 0 the

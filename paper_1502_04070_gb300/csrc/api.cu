@@ -139,6 +139,12 @@ struct stokes_handle_t {
     OpCoef<float> chi{}, clo{};             // MIXED: finest float64 coefficients split hi + lo
     cudaGraphExec_t step = nullptr;         // one cycle + projection + residual norm
     int step_kernels = 0;                   // kernel nodes in `step`
+    cudaGraphExec_t loop = nullptr;         // WHILE(not converged) { step; device-side test }
+    int loop_kernels = 0;                   // kernels per loop iteration
+    double* dctl = nullptr;                 // loop control (see k_solve_check), device
+    int* ictl = nullptr;
+    double* dhist = nullptr;                // residual^2 per step, device (kHistCap entries)
+    double* hhist = nullptr;                // pinned mirror
     unsigned long long launches = 0;        // kernels launched by this handle (graph nodes included)
     // optional timing of the finest-level smoothing steps and of the float64 residual: event
     // pairs recorded inside the captured graph (cudaEventRecordExternal)
@@ -149,6 +155,7 @@ struct stokes_handle_t {
     double t_smooth = 0.0, t_resid = 0.0;   // accumulated milliseconds
     long long n_smooth = 0, n_resid = 0;    // accumulated launches (groups)
 
+    static constexpr int kHistCap = 4096;
     Level<double>& fin() { return h64.back(); }
     bool mixed() const { return prm.precision == STOKES_MIXED; }
 };
@@ -172,7 +179,7 @@ void ev_end(stokes_handle* h, int k) {
 template <typename T>
 bool smooth_level(stokes_handle* h, Level<T>& lv, int steps, bool timed, bool sw) {
     const stokes_params& P = h->prm;
-    const bool fused = sizeof(T) == 4 && P.smoother == STOKES_UZAWA;
+    const bool f32 = sizeof(T) == 4 && P.smoother == STOKES_UZAWA;
     for (int s = 0; s < steps; ++s) {
         const int k = timed ? ev_begin(h) : -1;
         if (k >= 0) h->ev_smooth++;
@@ -182,9 +189,10 @@ bool smooth_level(stokes_handle* h, Level<T>& lv, int steps, bool timed, bool sw
         T* op = sw ? lv.p : lv.tp;
         if (P.smoother == STOKES_NORMAL_EQ) {
             launch_normal_eq<T>(h->st, lv.n, lv.c, (T)P.tau, xu, xp, lv.f, lv.g, lv.sinv, ou, op);
-        } else if (fused) {
-            launch_uzawa_fused<T>(h->st, lv.n, lv.c, (T)P.tau, (T)P.sigma, xu, xp, lv.f, lv.g, lv.sinv, ou, op);
-            sw = !sw;
+        } else if constexpr (sizeof(T) == 4) {
+            if (f32 && launch_uzawa_auto(h->st, lv.n, lv.c, (float)P.tau, (float)P.sigma, xu, xp, lv.f, lv.g,
+                                         lv.sinv, ou, op))
+                sw = !sw;
         } else {
             launch_uzawa<T>(h->st, lv.n, lv.c, (T)P.tau, (T)P.sigma, xu, xp, lv.f, lv.g, lv.sinv, ou, op);
         }
@@ -288,6 +296,55 @@ stokes_status build_graph(stokes_handle* h) {
     return STOKES_OK;
 }
 
+// The solve loop on the device: one conditional WHILE node whose body is one step followed by
+// k_solve_check (convergence, step limit, divergence).  No event records (not allowed in bodies).
+stokes_status build_loop(stokes_handle* h) {
+    if (h->loop) return STOKES_OK;
+    cudaGraph_t top = nullptr;
+    CK(cudaGraphCreate(&top, 0));
+    cudaError_t e;
+    cudaGraphConditionalHandle hnd;
+    cudaGraphNode_t nc;
+    cudaGraphNodeParams cp = {};
+    const bool timing = h->timing;
+    h->timing = false;
+    if ((e = cudaGraphConditionalHandleCreate(&hnd, top, 1, cudaGraphCondAssignDefault)) == cudaSuccess) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = hnd;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&nc, top, nullptr, nullptr, 0, &cp);
+    }
+    if (e == cudaSuccess) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(h->st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            record_step(h);
+            launch_solve_check(h->st, hnd, h->scal, h->dctl, h->ictl, h->dhist, stokes_handle_t::kHistCap);
+            e = cudaStreamEndCapture(h->st, &body);
+        }
+        if (e == cudaSuccess) {
+            size_t nn = 0;
+            cudaGraphGetNodes(body, nullptr, &nn);
+            std::vector<cudaGraphNode_t> nodes(nn);
+            cudaGraphGetNodes(body, nodes.data(), &nn);
+            h->loop_kernels = 0;
+            for (auto nd : nodes) {
+                cudaGraphNodeType ty;
+                if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) h->loop_kernels++;
+            }
+        }
+    }
+    h->timing = timing;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->loop, top, 0);
+    cudaGraphDestroy(top);
+    if (e != cudaSuccess) {
+        h->loop = nullptr;
+        return fail(e);
+    }
+    return STOKES_OK;
+}
+
 stokes_status launch_step(stokes_handle* h) {
     CK(cudaGraphLaunch(h->step, h->st));
     h->launches += h->step_kernels;
@@ -344,6 +401,10 @@ stokes_status rebuild_beta(stokes_handle* h) {
     if (h->step) {
         cudaGraphExecDestroy(h->step);
         h->step = nullptr;
+    }
+    if (h->loop) {
+        cudaGraphExecDestroy(h->loop);
+        h->loop = nullptr;
     }
     return STOKES_OK;
 }
@@ -407,6 +468,11 @@ void stokes_destroy(stokes_handle* h) {
     if (!h) return;
     if (h->st) cudaStreamSynchronize(h->st);
     if (h->step) cudaGraphExecDestroy(h->step);
+    if (h->loop) cudaGraphExecDestroy(h->loop);
+    if (h->dctl) cudaFree(h->dctl);
+    if (h->ictl) cudaFree(h->ictl);
+    if (h->dhist) cudaFree(h->dhist);
+    if (h->hhist) cudaFreeHost(h->hhist);
     for (auto e : h->ev) cudaEventDestroy(e);
     for (auto& l : h->h64) free_level(l);
     for (auto& l : h->h32) free_level(l);
@@ -466,13 +532,32 @@ stokes_status stokes_setup(const stokes_params* prm, void* stream, stokes_handle
     if (cudaMalloc(&h->inv, 27 * 27 * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&h->partial, (size_t)h->npartial * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&h->scal, 8 * sizeof(double)) != cudaSuccess ||
-        cudaMallocHost(&h->hscal, 8 * sizeof(double)) != cudaSuccess) {
+        cudaMallocHost(&h->hscal, 8 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&h->dctl, 4 * sizeof(double)) != cudaSuccess || cudaMalloc(&h->ictl, 4 * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&h->dhist, stokes_handle_t::kHistCap * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&h->hhist, stokes_handle_t::kHistCap * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         return bail(STOKES_ERR_OOM);
     }
     if ((s = rebuild_beta(h)) != STOKES_OK) return bail(s);
     *out = h;
     return STOKES_OK;
+}
+
+static stokes_status autotune_levels(stokes_handle* h, cudaStream_t st);
+
+stokes_status stokes_autotune(stokes_handle* h) {
+    if (!h) return STOKES_ERR_BAD_ARG;
+    stokes_status s = autotune_levels(h, h->st);
+    if (s == STOKES_OK && h->step) {   // the captured cycle holds the old choices
+        cudaGraphExecDestroy(h->step);
+        h->step = nullptr;
+    }
+    if (s == STOKES_OK && h->loop) {
+        cudaGraphExecDestroy(h->loop);
+        h->loop = nullptr;
+    }
+    return s;
 }
 
 stokes_status stokes_set_beta(stokes_handle* h, double beta) {
@@ -528,35 +613,83 @@ stokes_status stokes_solve(stokes_handle* h, double* u, double* p, const double*
     int cycles = 0, grow_run = 0;
     double prev_r = r;
     stokes_status result = STOKES_OK;
-    for (;;) {
-        if (r <= tol * nF) {
-            if (!h->mixed()) break;
-            // the refinement residual is updated, not recomputed: confirm with the true one
-            residual_norm_fin(h);
-            h->launches += 2;
+    if (!h->timing) {
+        // device-side loop: the host waits once per graph launch instead of once per cycle
+        if ((s = build_loop(h)) != STOKES_OK) return s;
+        for (;;) {
+            if (r <= tol * nF) {
+                if (!h->mixed()) break;
+                residual_norm_fin(h);     // the updated residual of the refinement: confirm it
+                h->launches += 2;
+                if ((s = read_scalar(h, 0, &r2)) != STOKES_OK) return s;
+                r = std::sqrt(r2);
+                if (history) history[cycles] = r;
+                if (r <= tol * nF) break;
+            }
+            if (!std::isfinite(r)) {
+                result = STOKES_DIVERGED;
+                break;
+            }
+            if (cycles >= max_cycles) {
+                result = STOKES_NOT_CONVERGED;
+                break;
+            }
+            const double t = h->mixed() ? 0.5 * tol : tol;
+            double ctl[3] = {t * t, (double)(max_cycles - cycles), r * r};
+            int ictl[2] = {0, 0};
+            CK(cudaMemcpyAsync(h->dctl, ctl, sizeof(ctl), cudaMemcpyHostToDevice, h->st));
+            CK(cudaMemcpyAsync(h->ictl, ictl, sizeof(ictl), cudaMemcpyHostToDevice, h->st));
+            CK(cudaGraphLaunch(h->loop, h->st));
+            CK(cudaMemcpyAsync(ictl, h->ictl, sizeof(ictl), cudaMemcpyDeviceToHost, h->st));
+            CK(cudaStreamSynchronize(h->st));
+            const int done = ictl[0];
+            CK(cudaMemcpyAsync(h->hhist, h->dhist, sizeof(double) * std::min(done + 1, stokes_handle_t::kHistCap),
+                               cudaMemcpyDeviceToHost, h->st));
+            CK(cudaStreamSynchronize(h->st));
+            h->launches += (unsigned long long)done * (h->loop_kernels);
+            for (int c = 1; c <= done; ++c) {
+                const double rc = c < stokes_handle_t::kHistCap ? std::sqrt(h->hhist[c]) : r;
+                if (history) history[cycles + c] = rc;
+            }
+            cycles += done;
+            r = done < stokes_handle_t::kHistCap ? std::sqrt(h->hhist[done]) : r;
+            if (ictl[1] >= 8) {
+                result = STOKES_DIVERGED;
+                break;
+            }
+            if (done == 0) break;   // nothing ran (cannot happen with the default condition 1)
+        }
+    } else {
+        for (;;) {
+            if (r <= tol * nF) {
+                if (!h->mixed()) break;
+                // the refinement residual is updated, not recomputed: confirm with the true one
+                residual_norm_fin(h);
+                h->launches += 2;
+                if ((s = read_scalar(h, 0, &r2)) != STOKES_OK) return s;
+                r = std::sqrt(r2);
+                if (history) history[cycles] = r;
+                if (r <= tol * nF) break;
+            }
+            // diverged: NaN/Inf, or growth in each of the last 8 cycles (the first cycles from x = 0
+            // may raise the Euclidean residual by orders of magnitude before it decays)
+            grow_run = (cycles > 0 && r > prev_r) ? grow_run + 1 : 0;
+            prev_r = r;
+            if (!std::isfinite(r) || grow_run >= 8) {
+                result = STOKES_DIVERGED;
+                break;
+            }
+            if (cycles >= max_cycles) {
+                result = STOKES_NOT_CONVERGED;
+                break;
+            }
+            if ((s = launch_step(h)) != STOKES_OK) return s;
             if ((s = read_scalar(h, 0, &r2)) != STOKES_OK) return s;
+            collect_timing(h);
             r = std::sqrt(r2);
+            ++cycles;
             if (history) history[cycles] = r;
-            if (r <= tol * nF) break;
         }
-        // diverged: NaN/Inf, or growth in each of the last 8 cycles (the first cycles from x = 0
-        // may raise the Euclidean residual by orders of magnitude before it decays)
-        grow_run = (cycles > 0 && r > prev_r) ? grow_run + 1 : 0;
-        prev_r = r;
-        if (!std::isfinite(r) || grow_run >= 8) {
-            result = STOKES_DIVERGED;
-            break;
-        }
-        if (cycles >= max_cycles) {
-            result = STOKES_NOT_CONVERGED;
-            break;
-        }
-        if ((s = launch_step(h)) != STOKES_OK) return s;
-        if ((s = read_scalar(h, 0, &r2)) != STOKES_OK) return s;
-        collect_timing(h);
-        r = std::sqrt(r2);
-        ++cycles;
-        if (history) history[cycles] = r;
     }
     if ((s = copy_out(h, u, p)) != STOKES_OK) return s;
     CK(cudaStreamSynchronize(h->st));
@@ -698,6 +831,27 @@ unsigned long long stokes_kernel_launches(const stokes_handle* h) { return h ? h
 
 // ----------------------------------------------------------------------------------- batches
 
+// Times the float32 Uzawa step variants on each not-yet-tuned level of h's float32 hierarchy
+// (process-wide choice per level size) and leaves the buffers zero as a fresh handle has them.
+static stokes_status autotune_levels(stokes_handle* h, cudaStream_t st) {
+    if (!h->mixed() || h->prm.smoother != STOKES_UZAWA) return STOKES_OK;
+    for (int l = 1; l < (int)h->h32.size(); ++l) {
+        Level<float>& lv = h->h32[l];
+        if (uzawa_tuned(lv.n)) continue;
+        cudaError_t e = autotune_uzawa_fused(st, lv.n, lv.c, (float)h->prm.tau, (float)h->prm.sigma, lv.u, lv.p, lv.f,
+                                             lv.g, lv.sinv, lv.tu, lv.tp, nullptr, nullptr);
+        if (e != cudaSuccess) return fail(e);
+        cudaMemsetAsync(lv.u, 0, 2 * lv.n2 * sizeof(float), st);
+        cudaMemsetAsync(lv.p, 0, lv.n1 * sizeof(float), st);
+        cudaMemsetAsync(lv.tu, 0, 2 * lv.n2 * sizeof(float), st);
+        cudaMemsetAsync(lv.tp, 0, lv.n1 * sizeof(float), st);
+    }
+    CK(cudaStreamSynchronize(st));
+    return STOKES_OK;
+}
+
+int stokes_step_variant(int levels) { return levels >= 2 && levels <= 31 ? uzawa_choice(1 << levels) : -1; }
+
 struct stokes_batch_t {
     int count = 0;
     cudaStream_t st = nullptr;
@@ -760,30 +914,12 @@ stokes_status stokes_batch_setup(int count, const int* levels, const double* bet
         stokes_batch_destroy(b);
         return STOKES_ERR_OOM;
     }
-    if (autotune && base->precision == STOKES_MIXED && base->smoother == STOKES_UZAWA) {
-        // tile shape of the fused float32 Uzawa step, per level size, timed on an instance's buffers
-        std::vector<bool> done(14, false);
+    if (autotune) {
         for (auto h : b->inst)
-            for (int l = 1; l < (int)h->h32.size(); ++l) {
-                if (done[l]) continue;
-                done[l] = true;
-                Level<float>& lv = h->h32[l];
-                cudaError_t e = autotune_uzawa_fused(b->st, lv.n, lv.c, (float)h->prm.tau, (float)h->prm.sigma, lv.u,
-                                                     lv.p, lv.f, lv.g, lv.sinv, lv.tu, lv.tp, nullptr, nullptr);
-                if (e != cudaSuccess) {
-                    stokes_batch_destroy(b);
-                    return fail(e);
-                }
-                // leave the level buffers as a fresh handle has them
-                cudaMemsetAsync(lv.u, 0, 2 * lv.n2 * sizeof(float), b->st);
-                cudaMemsetAsync(lv.p, 0, lv.n1 * sizeof(float), b->st);
-                cudaMemsetAsync(lv.tu, 0, 2 * lv.n2 * sizeof(float), b->st);
-                cudaMemsetAsync(lv.tp, 0, lv.n1 * sizeof(float), b->st);
+            if ((s = autotune_levels(h, b->st)) != STOKES_OK) {
+                stokes_batch_destroy(b);
+                return s;
             }
-        if (cudaStreamSynchronize(b->st) != cudaSuccess) {
-            stokes_batch_destroy(b);
-            return STOKES_ERR_CUDA;
-        }
     }
     *out = b;
     return STOKES_OK;

@@ -29,6 +29,28 @@ __global__ void k_batch_store(const double* __restrict__ scal, const int* __rest
     out[2] = (double)*count;
 }
 
+// Single solves: the same device-side loop, with a residual history and a divergence test.
+// ctl: [0] threshold factor (stop when r^2 <= ctl[0] * ||F||^2), [1] max steps, [2] previous r^2;
+// ictl: [0] step count, [1] consecutive growths.  hist[c] = r^2 after step c (c < cap).
+__global__ void k_solve_check(cudaGraphConditionalHandle hnd, const double* __restrict__ scal,
+                              double* __restrict__ ctl, int* __restrict__ ictl, double* __restrict__ hist, int cap) {
+    if (threadIdx.x != 0) return;
+    const int c = ictl[0] + 1;
+    ictl[0] = c;
+    const double r2 = scal[0];
+    if (c < cap) hist[c] = r2;
+    const int grow = r2 > ctl[2] ? ictl[1] + 1 : 0;
+    ictl[1] = grow;
+    ctl[2] = r2;
+    const bool go = isfinite(r2) && r2 > ctl[0] * scal[2] && c < (int)ctl[1] && grow < 8;
+    cudaGraphSetConditional(hnd, go ? 1u : 0u);
+}
+
+void launch_solve_check(cudaStream_t s, cudaGraphConditionalHandle hnd, const double* scal, double* ctl, int* ictl,
+                        double* hist, int cap) {
+    k_solve_check<<<1, 32, 0, s>>>(hnd, scal, ctl, ictl, hist, cap);
+}
+
 void launch_batch_check(cudaStream_t s, cudaGraphConditionalHandle hnd, const double* scal, double tol2,
                         int max_cycles, int* count) {
     k_batch_check<<<1, 32, 0, s>>>(hnd, scal, tol2, max_cycles, count);

@@ -157,11 +157,12 @@ __device__ __forceinline__ bool slot_unknown(const CellNodes& cn, int s) {
     return s == 0 ? cn.v : s == 1 ? cn.h : s == 2 ? cn.e : cn.c;
 }
 
+// (kernels that reduce over the block with block_sum2d are launched with BX x BY threads)
 #define CELL_INDEX                                          \
-    const int i = blockIdx.x * BX + threadIdx.x;            \
-    const int j = blockIdx.y * BY + threadIdx.y;            \
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;    \
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;    \
     const bool active = i <= n && j <= n;                   \
-    const int tid = threadIdx.y * BX + threadIdx.x;         \
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x; \
     (void)tid;
 
 // Block sum (thread-linear id tid) of one double; result valid in tid 0.

@@ -147,8 +147,8 @@ __global__ void __launch_bounds__(NT) k_uzawa_u2(int n, const __grid_constant__ 
 
 template <typename T>
 void launch_uzawa(cudaStream_t s, int n, const OpCoef<T>& c, T tau, T sigma, T* u, T* p, const T* f,
-                  const T* g, const T* sinv, T* uh, T* dp) {
-    const dim3 grid = cells_grid(n), blk(BX, BY);
+                  const T* g, const T* sinv, T* uh, T* dp, int bx, int by) {
+    const dim3 blk(bx, by), grid((n + 1 + bx - 1) / bx, (n + 1 + by - 1) / by);
     k_uzawa_u<T><<<grid, blk, 0, s>>>(n, c, tau, u, p, f, uh);
     k_uzawa_p<T><<<grid, blk, 0, s>>>(n, c, sigma, uh, p, g, sinv, dp);
     k_uzawa_u2<T><<<grid, blk, 0, s>>>(n, c, tau, uh, dp, u);
@@ -693,7 +693,7 @@ void launch_add_f32(cudaStream_t s, size_t count, const float* e, double* x) {
 // ------------------------------------------------------------------------------------------
 #define INST(T)                                                                                         \
     template void launch_uzawa<T>(cudaStream_t, int, const OpCoef<T>&, T, T, T*, T*, const T*, const T*, \
-                                  const T*, T*, T*);                                                      \
+                                  const T*, T*, T*, int, int);                                                      \
     template void launch_normal_eq<T>(cudaStream_t, int, const OpCoef<T>&, T, T*, T*, const T*, const T*, \
                                       const T*, T*, T*);                                                  \
     template void launch_restrict<T>(cudaStream_t, int, const T*, const T*, T*, T*);                      \

@@ -26,7 +26,7 @@ void launch_residual(cudaStream_t s, int n, const OpCoef<T>& c, const T* u, cons
 //   u  = uh - tau Ahat^{-1} B^T dp
 template <typename T>
 void launch_uzawa(cudaStream_t s, int n, const OpCoef<T>& c, T tau, T sigma, T* u, T* p, const T* f,
-                  const T* g, const T* sinv, T* uh, T* dp);
+                  const T* g, const T* sinv, T* uh, T* dp, int bx = 32, int by = 8);
 
 // Refinement update (see refine.cu): float32 correction e, float64 iterate x, residual r stored as
 // (hi, lo) float pairs in the 8-byte slots of a float64 array:
@@ -46,6 +46,13 @@ cudaError_t prepare_uzawa_fused();   // raises the kernel's shared-memory limit 
 template <typename T>
 cudaError_t launch_uzawa_fused(cudaStream_t s, int n, const OpCoef<T>& c, T tau, T sigma, const T* u, const T* p,
                                const T* f, const T* g, const T* sinv, T* u_out, T* p_out);
+// One float32 Uzawa step with the variant the autotuner chose for level size n: either a fused
+// one-kernel step from (u, p) into (u_out, p_out) (returns true), or the three-kernel step in place
+// on (u, p) with (u_out, p_out) as scratch (returns false).
+bool uzawa_tuned(int n);
+int uzawa_choice(int n);
+bool launch_uzawa_auto(cudaStream_t s, int n, const OpCoef<float>& c, float tau, float sigma, float* u, float* p,
+                       const float* f, const float* g, const float* sinv, float* u_out, float* p_out);
 // Picks the fastest float32 tile shape for level size n by timing each on these buffers (their
 // contents are overwritten); returns the variant index and its time per step.
 cudaError_t autotune_uzawa_fused(cudaStream_t s, int n, const OpCoef<float>& c, float tau, float sigma, float* u,
@@ -100,6 +107,8 @@ void launch_make_consistent(cudaStream_t s, int n, double* g, double* partial, d
 void launch_batch_check(cudaStream_t s, cudaGraphConditionalHandle hnd, const double* scal, double tol2,
                         int max_cycles, int* count);
 void launch_batch_store(cudaStream_t s, const double* scal, const int* count, double* out);
+void launch_solve_check(cudaStream_t s, cudaGraphConditionalHandle hnd, const double* scal, double* ctl, int* ictl,
+                        double* hist, int cap);
 
 // x64 += e32 (count elements), and float64 -> float32 conversion
 void launch_add_f32(cudaStream_t s, size_t count, const float* e, double* x);

@@ -158,10 +158,18 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 4 ? 2 : 1)) k_uzawa_fuse
     p_out[(size_t)cj * (n + 1) + ci] = vp(ci, cj) + vd(ci, cj);
 }
 
-// Tile shapes (TX x TY cells) the autotuner chooses from, per level, for float32; float64 uses 32 x 8.
-// 0: 32 x 16, 1: 32 x 8, 2: 64 x 8, 3: 16 x 16.
+// Step variants the autotuner chooses from, per level, for float32 (float64 uses the three-kernel
+// step).  Fused one-kernel tiles (TX x TY cells): 0: 32 x 16, 1: 32 x 8, 2: 64 x 8, 3: 16 x 16.
+// Three-kernel step (one thread per cell and phase, no halo recomputation; short per-thread work
+// suits the small levels, whose few fused tiles are issue-bound) with blocks 4: 32 x 8, 5: 16 x 8,
+// 6: 8 x 8.
 constexpr int kFusedVariants = 4;
-static int g_tile_choice[32] = {};   // per level k (N = 2^(k+1)), default variant 0
+constexpr int kStepVariants = 7;
+// per level k (N = 2^(k+1)): chosen variant; until tuned, the three-kernel step below N = 128 and the
+// 32 x 16 fused tile from N = 128 up
+static int g_tile_choice[32] = {5, 5, 5, 5, 5, 5, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0,
+                                0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+static bool g_tuned[32] = {};
 
 static int level_of(int n) {
     int k = 0;
@@ -213,6 +221,18 @@ static void launch_variant(int v, cudaStream_t s, int n, const OpCoef<T>& c, T t
     }
 }
 
+static bool launch_step_variant(int v, cudaStream_t s, int n, const OpCoef<float>& c, float tau, float sigma,
+                                float* u, float* p, const float* f, const float* g, const float* sinv, float* u_out,
+                                float* p_out) {
+    if (v < kFusedVariants) {
+        launch_variant<float>(v, s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
+        return true;
+    }
+    const int bx = v == 4 ? 32 : (v == 5 ? 16 : 8), by = 8;
+    launch_uzawa<float>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out, bx, by);
+    return false;
+}
+
 template <typename T>
 cudaError_t launch_uzawa_fused(cudaStream_t s, int n, const OpCoef<T>& c, T tau, T sigma, const T* u, const T* p,
                                const T* f, const T* g, const T* sinv, T* u_out, T* p_out) {
@@ -231,12 +251,13 @@ cudaError_t autotune_uzawa_fused(cudaStream_t s, int n, const OpCoef<float>& c, 
     int best = 0;
     float bms = 1e30f;
     const int reps = n >= 512 ? 5 : 20;
-    for (int v = 0; v < kFusedVariants; ++v) {
-        launch_variant<float>(v, s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);   // warm-up
+    for (int v = 0; v < kStepVariants; ++v) {
+        bool sw = launch_step_variant(v, s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);   // warm-up
         cudaEventRecord(e0, s);
-        for (int r = 0; r < reps; ++r)
-            launch_variant<float>(v, s, n, c, tau, sigma, (r & 1) ? u_out : u, (r & 1) ? p_out : p, f, g, sinv,
-                                  (r & 1) ? u : u_out, (r & 1) ? p : p_out);
+        for (int r = 0; r < reps; ++r) {
+            float *xu = sw ? u_out : u, *xp = sw ? p_out : p, *ou = sw ? u : u_out, *op = sw ? p : p_out;
+            if (launch_step_variant(v, s, n, c, tau, sigma, xu, xp, f, g, sinv, ou, op)) sw = !sw;
+        }
         cudaEventRecord(e1, s);
         cudaError_t err = cudaEventSynchronize(e1);
         if (err != cudaSuccess) {
@@ -255,9 +276,18 @@ cudaError_t autotune_uzawa_fused(cudaStream_t s, int n, const OpCoef<float>& c, 
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     g_tile_choice[level_of(n)] = best;
+    g_tuned[level_of(n)] = true;
     if (chosen) *chosen = best;
     if (best_ms) *best_ms = bms;
     return cudaGetLastError();
+}
+
+bool uzawa_tuned(int n) { return g_tuned[level_of(n)]; }
+int uzawa_choice(int n) { return g_tile_choice[level_of(n)]; }
+
+bool launch_uzawa_auto(cudaStream_t s, int n, const OpCoef<float>& c, float tau, float sigma, float* u, float* p,
+                       const float* f, const float* g, const float* sinv, float* u_out, float* p_out) {
+    return launch_step_variant(g_tile_choice[level_of(n)], s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
 }
 
 template cudaError_t launch_uzawa_fused<float>(cudaStream_t, int, const OpCoef<float>&, float, float, const float*,

@@ -181,6 +181,10 @@ class Solver:
                 "stokes_prolong_add")
         return u, p
 
+    def autotune(self):
+        """Time the float32 step variants on this solver's levels and keep the fastest per level."""
+        B.check(self._lib.stokes_autotune(self._h), "stokes_autotune")
+
     def set_timing(self, enable=True):
         B.check(self._lib.stokes_set_timing(self._h, int(enable)), "stokes_set_timing")
 
