@@ -90,6 +90,7 @@ OpCoef<T> make_coef(int n, double beta) {
                 c.By[o][q][m] = (T)(h * S.By[o][q][m]);
             }
     }
+    fill_merged(c);
     return c;
 }
 
@@ -634,8 +635,8 @@ stokes_status stokes_solve(stokes_handle* h, double* u, double* p, const double*
                 result = STOKES_NOT_CONVERGED;
                 break;
             }
-            const double t = h->mixed() ? 0.5 * tol : tol;
-            double ctl[3] = {t * t, (double)(max_cycles - cycles), r * r};
+            // the device loop stops on the (updated) residual; MIXED then confirms with the true one
+            double ctl[3] = {tol * tol, (double)(max_cycles - cycles), r * r};
             int ictl[2] = {0, 0};
             CK(cudaMemcpyAsync(h->dctl, ctl, sizeof(ctl), cudaMemcpyHostToDevice, h->st));
             CK(cudaMemcpyAsync(h->ictl, ictl, sizeof(ictl), cudaMemcpyHostToDevice, h->st));
@@ -965,8 +966,8 @@ static stokes_status batch_build(stokes_batch* b, double* const* u, double* cons
         e = cudaGraphAddChildGraphNode(&np, top, nullptr, 0, gp);
         cudaGraphDestroy(gp);
         if (e != cudaSuccess) break;
-        // loop: WHILE the step's residual is above the tolerance (with a 2x margin in MIXED mode,
-        // whose updated residual is confirmed by the true one in the epilogue)
+        // loop: WHILE the step's residual is above the tolerance (MIXED: the updated residual; the
+        // epilogue computes the true one, and the rare instance that misses continues on the host)
         cudaGraphConditionalHandle hnd;
         if ((e = cudaGraphConditionalHandleCreate(&hnd, top, 1, cudaGraphCondAssignDefault)) != cudaSuccess) break;
         cudaGraphNodeParams cp = {};
@@ -980,8 +981,7 @@ static stokes_status batch_build(stokes_batch* b, double* const* u, double* cons
             cudaSuccess)
             break;
         record_step(h);
-        const double t = mixed ? 0.5 * tol : tol;
-        launch_batch_check(st, hnd, h->scal, t * t, max_cycles, b->d_count + i);
+        launch_batch_check(st, hnd, h->scal, tol * tol, max_cycles, b->d_count + i);
         if ((e = cudaStreamEndCapture(st, &body)) != cudaSuccess) break;
         b->body_kernels[i] = count_kernels(body);
         // epilogue: true residual, results out

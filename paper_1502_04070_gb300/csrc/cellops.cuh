@@ -145,6 +145,95 @@ __device__ __forceinline__ void cell_apply(int i, int j, int n, const T (&A)[2][
     visit<DA, DBT, DB, DD, MASK, 3>(i, j, n, A, c, ux, uy, p, a);
 }
 
+// ---- merged node stencils for cells off the mid-lines (all four squares share orientation O)
+__host__ __device__ constexpr bool need_win(int O, bool DA, bool DB, int w) {
+    return (DA && (nz_MA(O, 0, w) || nz_MA(O, 1, w) || nz_MA(O, 2, w) || nz_MA(O, 3, w))) || (DB && nz_MB(O, w));
+}
+__host__ __device__ constexpr bool need_vwin(int O, int v) {
+    return nz_MBT(O, 0, v) || nz_MBT(O, 1, v) || nz_MBT(O, 2, v) || nz_MBT(O, 3, v);
+}
+
+template <int O, int S, typename T>
+__device__ __forceinline__ T ma_row(const OpCoef<T>& c, const T (&w)[25]) {
+    T s = T(0);
+#pragma unroll
+    for (int k = 0; k < 25; ++k)
+        if (nz_MA(O, S, k)) s = fma(c.MA[O][S][k], w[k], s);
+    return s;
+}
+template <int O, int S, typename T>
+__device__ __forceinline__ T mbt_row(const T (&B)[2][4][9], const T (&pw)[9]) {
+    T s = T(0);
+#pragma unroll
+    for (int k = 0; k < 9; ++k)
+        if (nz_MBT(O, S, k)) s = fma(B[O][S][k], pw[k], s);
+    return s;
+}
+
+template <bool DA, bool DBT, bool DB, bool DD, bool MASK, int O, typename T, typename VU, typename VP>
+__device__ __forceinline__ void cell_apply_merged(int i, int j, int n, const OpCoef<T>& c, const VU& ux, const VU& uy,
+                                                  const VP& p, Acc<T>& a) {
+    T wx[25], wy[25], pw[9];
+    if constexpr (DA || DB) {
+#pragma unroll
+        for (int w = 0; w < 25; ++w) {
+            if (!need_win(O, DA, DB, w)) continue;
+            const int dx = w % 5 - 2, dy = w / 5 - 2;
+            const int X = 2 * i + dx, Y = 2 * j + dy;
+            const bool ok = MASK ? interior2(X, Y, n) : (X >= 0 && Y >= 0 && X <= 2 * n && Y <= 2 * n);
+            wx[w] = ok ? ux.at(i - 1, j - 1, dx + 2, dy + 2) : T(0);
+            wy[w] = ok ? uy.at(i - 1, j - 1, dx + 2, dy + 2) : T(0);
+        }
+    }
+    if constexpr (DBT) {
+#pragma unroll
+        for (int v = 0; v < 9; ++v) {
+            if (!need_vwin(O, v)) continue;
+            const int I = i + v % 3 - 1, J = j + v / 3 - 1;
+            pw[v] = (I >= 0 && J >= 0 && I <= n && J <= n) ? p(I, J) : T(0);
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < 4; ++s) a.au[0][s] = a.au[1][s] = a.bt[0][s] = a.bt[1][s] = a.dg[s] = T(0);
+    a.bu = T(0);
+    if constexpr (DA) {
+        a.au[0][0] = ma_row<O, 0>(c, wx); a.au[1][0] = ma_row<O, 0>(c, wy);
+        a.au[0][1] = ma_row<O, 1>(c, wx); a.au[1][1] = ma_row<O, 1>(c, wy);
+        a.au[0][2] = ma_row<O, 2>(c, wx); a.au[1][2] = ma_row<O, 2>(c, wy);
+        a.au[0][3] = ma_row<O, 3>(c, wx); a.au[1][3] = ma_row<O, 3>(c, wy);
+    }
+    if constexpr (DBT) {
+        a.bt[0][0] = mbt_row<O, 0>(c.MBTx, pw); a.bt[1][0] = mbt_row<O, 0>(c.MBTy, pw);
+        a.bt[0][1] = mbt_row<O, 1>(c.MBTx, pw); a.bt[1][1] = mbt_row<O, 1>(c.MBTy, pw);
+        a.bt[0][2] = mbt_row<O, 2>(c.MBTx, pw); a.bt[1][2] = mbt_row<O, 2>(c.MBTy, pw);
+        a.bt[0][3] = mbt_row<O, 3>(c.MBTx, pw); a.bt[1][3] = mbt_row<O, 3>(c.MBTy, pw);
+    }
+    if constexpr (DD) {
+        a.dg[0] = c.MA[O][0][12];   // window index of node s: ((s >> 1) + 2) * 5 + (s & 1) + 2
+        a.dg[1] = c.MA[O][1][13];
+        a.dg[2] = c.MA[O][2][17];
+        a.dg[3] = c.MA[O][3][18];
+    }
+    if constexpr (DB) {
+        T s = T(0);
+#pragma unroll
+        for (int w = 0; w < 25; ++w)
+            if (nz_MB(O, w)) s = fma(c.MBx[O][w], wx[w], fma(c.MBy[O][w], wy[w], s));
+        a.bu = s;
+    }
+}
+
+// Operator rows of cell (i, j): merged stencils off the mid-lines, the square-by-square gather on
+// them (where the four squares around a node do not all share one orientation).
+template <bool DA, bool DBT, bool DB, bool DD, bool MASK, typename T, typename VU, typename VP>
+__device__ __forceinline__ void cell_apply_auto(int i, int j, int n, const OpCoef<T>& c, const VU& ux, const VU& uy,
+                                                const VP& p, Acc<T>& a) {
+    const int h = n >> 1;
+    if (i == h || j == h) cell_apply<DA, DBT, DB, DD, MASK>(i, j, n, c.A, c, ux, uy, p, a);
+    else if (orient(i, j, n)) cell_apply_merged<DA, DBT, DB, DD, MASK, 1>(i, j, n, c, ux, uy, p, a);
+    else cell_apply_merged<DA, DBT, DB, DD, MASK, 0>(i, j, n, c, ux, uy, p, a);
+}
+
 // lattice position and existence / unknown flags of slot s of cell (i, j)
 __device__ __forceinline__ void slot_pos(int i, int j, int s, int& X, int& Y) {
     X = 2 * i + (s & 1);

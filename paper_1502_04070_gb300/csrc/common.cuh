@@ -28,6 +28,15 @@ struct OpCoef {            // local square matrices of one level
     T A[2][9][9];          // K + beta h^2 Mhat        (h-independent stiffness, mass ~ h^2)
     T Bx[2][4][9];         // (d phi_m / dx, psi_q)    (~ h)
     T By[2][4][9];
+    // The same operator as node stencils for cells whose four squares share orientation o (all
+    // cells off the two mid-lines): the rows of the four owned velocity nodes s (V, H, E, C) over the
+    // 5 x 5 lattice window of the cell (offsets dx, dy in -2..2 from (2i, 2j)), their B^T rows over
+    // the 3 x 3 vertex window, and the B row of the owned vertex.  Built by fill_merged().
+    T MA[2][4][25];        // [o][s][(dy+2)*5 + dx+2]
+    T MBTx[2][4][9];       // [o][s][(dj+1)*3 + di+1]
+    T MBTy[2][4][9];
+    T MBx[2][25];          // [o][(dy+2)*5 + dx+2]
+    T MBy[2][25];
 };
 
 template <typename T>
@@ -47,6 +56,85 @@ __host__ __device__ constexpr bool couple(int o, int l, int m) {
            (((tri_mask(o, 1) >> l) & 1u) && ((tri_mask(o, 1) >> m) & 1u));
 }
 __host__ __device__ constexpr int corner_node(int q) { return q == 0 ? 0 : q == 1 ? 2 : q == 2 ? 6 : 8; }
+
+// Squares around cell (i, j): SQ 0 = (i, j), 1 = (i-1, j), 2 = (i, j-1), 3 = (i-1, j-1); the
+// cell's vertex is corner SQ of square SQ.  Owned node s (0 V, 1 H, 2 E, 3 C) sits at local node
+// sq_local(SQ, s) of square SQ, or -1 if the square does not contain it.
+__host__ __device__ constexpr int sq_local(int SQ, int s) {
+    // node offset from the cell origin (2i, 2j): (s & 1, s >> 1); square origin: (-2 (SQ & 1), -2 (SQ >> 1))
+    return ((s & 1) + 2 * (SQ & 1) > 2 || (s >> 1) + 2 * (SQ >> 1) > 2)
+               ? -1
+               : 3 * ((s >> 1) + 2 * (SQ >> 1)) + (s & 1) + 2 * (SQ & 1);
+}
+// lattice offset (from (2i, 2j)) of local node m of square SQ, as a 5 x 5 window index
+__host__ __device__ constexpr int sq_win(int SQ, int m) { return (m / 3 - 2 * (SQ >> 1) + 2) * 5 + (m % 3 - 2 * (SQ & 1) + 2); }
+// vertex offset (from (i, j)) of corner q of square SQ, as a 3 x 3 window index
+__host__ __device__ constexpr int sq_vwin(int SQ, int q) { return (q / 2 - (SQ >> 1) + 1) * 3 + (q % 2 - (SQ & 1) + 1); }
+
+// structural nonzeros of the merged stencils (compile-time)
+__host__ __device__ constexpr bool nz_MA(int o, int s, int w) {
+    for (int SQ = 0; SQ < 4; ++SQ) {
+        const int L = sq_local(SQ, s);
+        if (L < 0) continue;
+        for (int m = 0; m < 9; ++m)
+            if (sq_win(SQ, m) == w && couple(o, L, m)) return true;
+    }
+    return false;
+}
+__host__ __device__ constexpr bool nz_MBT(int o, int s, int v) {
+    for (int SQ = 0; SQ < 4; ++SQ) {
+        const int L = sq_local(SQ, s);
+        if (L < 0) continue;
+        for (int q = 0; q < 4; ++q)
+            if (sq_vwin(SQ, q) == v && couple(o, corner_node(q), L)) return true;
+    }
+    return false;
+}
+__host__ __device__ constexpr bool nz_MB(int o, int w) {
+    for (int SQ = 0; SQ < 4; ++SQ)
+        for (int m = 0; m < 9; ++m)
+            if (sq_win(SQ, m) == w && couple(o, corner_node(SQ), m)) return true;
+    return false;
+}
+
+// host: merged stencils from the square-local matrices (sums over the squares that share a node)
+template <typename T>
+inline void fill_merged(OpCoef<T>& c) {
+    for (int o = 0; o < 2; ++o) {
+        for (int s = 0; s < 4; ++s) {
+            for (int w = 0; w < 25; ++w) c.MA[o][s][w] = T(0);
+            for (int v = 0; v < 9; ++v) c.MBTx[o][s][v] = c.MBTy[o][s][v] = T(0);
+            double ma[25] = {}, bx[9] = {}, by[9] = {};
+            for (int SQ = 0; SQ < 4; ++SQ) {
+                const int L = sq_local(SQ, s);
+                if (L < 0) continue;
+                for (int m = 0; m < 9; ++m)
+                    if (couple(o, L, m)) ma[sq_win(SQ, m)] += (double)c.A[o][L][m];
+                for (int q = 0; q < 4; ++q)
+                    if (couple(o, corner_node(q), L)) {
+                        bx[sq_vwin(SQ, q)] += (double)c.Bx[o][q][L];
+                        by[sq_vwin(SQ, q)] += (double)c.By[o][q][L];
+                    }
+            }
+            for (int w = 0; w < 25; ++w) c.MA[o][s][w] = (T)ma[w];
+            for (int v = 0; v < 9; ++v) {
+                c.MBTx[o][s][v] = (T)bx[v];
+                c.MBTy[o][s][v] = (T)by[v];
+            }
+        }
+        double mx[25] = {}, my[25] = {};
+        for (int SQ = 0; SQ < 4; ++SQ)
+            for (int m = 0; m < 9; ++m)
+                if (couple(o, corner_node(SQ), m)) {
+                    mx[sq_win(SQ, m)] += (double)c.Bx[o][SQ][m];
+                    my[sq_win(SQ, m)] += (double)c.By[o][SQ][m];
+                }
+        for (int w = 0; w < 25; ++w) {
+            c.MBx[o][w] = (T)mx[w];
+            c.MBy[o][w] = (T)my[w];
+        }
+    }
+}
 
 __device__ __forceinline__ int orient(int si, int sj, int n) {
     const int h = n >> 1;

@@ -103,6 +103,7 @@ extern "C" stokes_status stokes_residual_norm2_noalloc(int levels, double beta, 
                 c.By[o][q][m] = h * g_noalloc_sq.By[o][q][m];
             }
     }
+    fill_merged(c);
     cudaStream_t s = (cudaStream_t)stream;
     k_residual_sumsq<<<cells_grid(n), dim3(BX, BY), 0, s>>>(n, c, u, p, f, g, scratch);
     launch_reduce(s, scratch, cells_blocks(n), norm2);

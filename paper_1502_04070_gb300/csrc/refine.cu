@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(NT) k_residual_df(int n, const __grid_constant
     double ss = 0.0;
     if (active) {
         Acc<double> a;
-        cell_apply<true, true, true, false, true>(i, j, n, c.A, c, gview(u, 2 * n + 1), gview(u + n2, 2 * n + 1),
+        cell_apply_auto<true, true, true, false, true>(i, j, n, c, gview(u, 2 * n + 1), gview(u + n2, 2 * n + 1),
                                                   gview(p, n + 1), a);
         const CellNodes cn = cell_nodes(i, j, n);
         const int ld = 2 * n + 1;

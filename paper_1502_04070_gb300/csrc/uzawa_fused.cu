@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 4 ? 2 : 1)) k_uzawa_fuse
         T hx[4] = {T(0), T(0), T(0), T(0)}, hy[4] = {T(0), T(0), T(0), T(0)};
         if (ci >= 0 && cj >= 0 && ci <= n && cj <= n) {
             Acc<T> a;
-            cell_apply<true, true, false, true, false>(ci, cj, n, c.A, c, vux, vuy, vp, a);
+            cell_apply_auto<true, true, false, true, false>(ci, cj, n, c, vux, vuy, vp, a);
             const CellNodes cn = cell_nodes(ci, cj, n);
 #pragma unroll
             for (int s = 0; s < 4; ++s) {
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 4 ? 2 : 1)) k_uzawa_fuse
         T d = T(0);
         if (vi >= 0 && vj >= 0 && vi <= n && vj <= n) {
             Acc<T> a;
-            cell_apply<false, false, true, false, false>(vi, vj, n, c.A, c, vhx, vhy, vp, a);
+            cell_apply_auto<false, false, true, false, false>(vi, vj, n, c, vhx, vhy, vp, a);
             const size_t k = (size_t)vj * (n + 1) + vi;
             d = sigma * __ldg(sinv + k) * (a.bu - __ldg(g + k));
         }
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 4 ? 2 : 1)) k_uzawa_fuse
     if (ci > n || cj > n) return;
     const SVert<T, G::DW> vd{sD, i0 - 1, j0 - 1};
     Acc<T> a;
-    cell_apply<false, true, false, true, false>(ci, cj, n, c.A, c, vhx, vhy, vd, a);
+    cell_apply_auto<false, true, false, true, false>(ci, cj, n, c, vhx, vhy, vd, a);
     const CellNodes cn = cell_nodes(ci, cj, n);
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
