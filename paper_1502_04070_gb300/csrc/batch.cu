@@ -5,6 +5,7 @@
 // whole batch runs to convergence in one graph launch without returning to the host.
 #include <cuda_runtime.h>
 
+#include "cellops.cuh"
 #include "kernels.cuh"
 
 namespace smg {
@@ -13,6 +14,7 @@ namespace smg {
 // the step count is below max_cycles and the residual is finite.
 __global__ void k_batch_check(cudaGraphConditionalHandle hnd, const double* __restrict__ scal, double tol2,
                               int max_cycles, int* __restrict__ count) {
+    pdl_enter();
     if (threadIdx.x != 0) return;
     const int c = *count + 1;
     *count = c;
@@ -23,6 +25,7 @@ __global__ void k_batch_check(cudaGraphConditionalHandle hnd, const double* __re
 
 __global__ void k_batch_store(const double* __restrict__ scal, const int* __restrict__ count,
                               double* __restrict__ out) {
+    pdl_enter();
     if (threadIdx.x != 0) return;
     out[0] = scal[0];
     out[1] = scal[2];
@@ -34,6 +37,7 @@ __global__ void k_batch_store(const double* __restrict__ scal, const int* __rest
 // ictl: [0] step count, [1] consecutive growths.  hist[c] = r^2 after step c (c < cap).
 __global__ void k_solve_check(cudaGraphConditionalHandle hnd, const double* __restrict__ scal,
                               double* __restrict__ ctl, int* __restrict__ ictl, double* __restrict__ hist, int cap) {
+    pdl_enter();
     if (threadIdx.x != 0) return;
     const int c = ictl[0] + 1;
     ictl[0] = c;
@@ -48,16 +52,16 @@ __global__ void k_solve_check(cudaGraphConditionalHandle hnd, const double* __re
 
 void launch_solve_check(cudaStream_t s, cudaGraphConditionalHandle hnd, const double* scal, double* ctl, int* ictl,
                         double* hist, int cap) {
-    k_solve_check<<<1, 32, 0, s>>>(hnd, scal, ctl, ictl, hist, cap);
+    launch_pdl(k_solve_check, 1, 32, 0, s, hnd, scal, ctl, ictl, hist, cap);
 }
 
 void launch_batch_check(cudaStream_t s, cudaGraphConditionalHandle hnd, const double* scal, double tol2,
                         int max_cycles, int* count) {
-    k_batch_check<<<1, 32, 0, s>>>(hnd, scal, tol2, max_cycles, count);
+    launch_pdl(k_batch_check, 1, 32, 0, s, hnd, scal, tol2, max_cycles, count);
 }
 
 void launch_batch_store(cudaStream_t s, const double* scal, const int* count, double* out) {
-    k_batch_store<<<1, 32, 0, s>>>(scal, count, out);
+    launch_pdl(k_batch_store, 1, 32, 0, s, scal, count, out);
 }
 
 }  // namespace smg

@@ -35,12 +35,37 @@ struct Acc {
     T bu;         // (B u) at the owned vertex
 };
 
+// Programmatic dependent launch: the kernels of a cycle are launched with programmatic stream
+// serialisation, so a kernel's CTAs can be scheduled while its predecessor drains; each such kernel
+// first lets its own successor launch, then waits until every predecessor has completed and its
+// memory is visible, before it touches global memory.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
+
 // Views map P2-lattice points to values.  A velocity view answers at(si, sj, a, b), the value at
 // lattice point (2 si + a, 2 sj + b) (a, b are compile-time in every caller, so a square's nine
 // loads share one address computation), and (X, Y) for a single point.  A vertex view answers
 // (i, j).  GView reads global memory through the read-only path; SLat / SVert read shared tiles.
 template <typename T>
 struct GView {
+    static constexpr bool zero_filled = false;   // reads outside the array are not allowed
     const T* p;
     int ld;
     __device__ __forceinline__ T operator()(int X, int Y) const { return __ldg(p + (size_t)Y * ld + X); }
@@ -56,6 +81,7 @@ __device__ __forceinline__ GView<T> gview(const T* p, int ld) { return GView<T>{
 // words.  WH words per row, PL words per plane (padded so the two planes fall on different banks).
 template <typename T, int WH, int PL>
 struct SLat {
+    static constexpr bool zero_filled = true;    // the tile covers every window and holds 0 off the domain
     const T* p;
     int xh0, y0;   // tile origin: X0 = 2 xh0, Y0 = y0
     __device__ __forceinline__ T at(int si, int sj, int a, int b) const {
@@ -68,6 +94,7 @@ struct SLat {
 };
 template <typename T, int LD>
 struct SVert {
+    static constexpr bool zero_filled = true;
     const T* p;
     int x0, y0;
     __device__ __forceinline__ T operator()(int i, int j) const { return p[(j - y0) * LD + (i - x0)]; }
@@ -180,9 +207,14 @@ __device__ __forceinline__ void cell_apply_merged(int i, int j, int n, const OpC
             if (!need_win(O, DA, DB, w)) continue;
             const int dx = w % 5 - 2, dy = w / 5 - 2;
             const int X = 2 * i + dx, Y = 2 * j + dy;
-            const bool ok = MASK ? interior2(X, Y, n) : (X >= 0 && Y >= 0 && X <= 2 * n && Y <= 2 * n);
-            wx[w] = ok ? ux.at(i - 1, j - 1, dx + 2, dy + 2) : T(0);
-            wy[w] = ok ? uy.at(i - 1, j - 1, dx + 2, dy + 2) : T(0);
+            if constexpr (VU::zero_filled && !MASK) {
+                wx[w] = ux.at(i - 1, j - 1, dx + 2, dy + 2);
+                wy[w] = uy.at(i - 1, j - 1, dx + 2, dy + 2);
+            } else {
+                const bool ok = MASK ? interior2(X, Y, n) : (X >= 0 && Y >= 0 && X <= 2 * n && Y <= 2 * n);
+                wx[w] = ok ? ux.at(i - 1, j - 1, dx + 2, dy + 2) : T(0);
+                wy[w] = ok ? uy.at(i - 1, j - 1, dx + 2, dy + 2) : T(0);
+            }
         }
     }
     if constexpr (DBT) {
@@ -190,7 +222,8 @@ __device__ __forceinline__ void cell_apply_merged(int i, int j, int n, const OpC
         for (int v = 0; v < 9; ++v) {
             if (!need_vwin(O, v)) continue;
             const int I = i + v % 3 - 1, J = j + v / 3 - 1;
-            pw[v] = (I >= 0 && J >= 0 && I <= n && J <= n) ? p(I, J) : T(0);
+            if constexpr (VP::zero_filled) pw[v] = p(I, J);
+            else pw[v] = (I >= 0 && J >= 0 && I <= n && J <= n) ? p(I, J) : T(0);
         }
     }
 #pragma unroll

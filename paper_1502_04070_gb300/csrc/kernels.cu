@@ -37,6 +37,7 @@ __global__ void __launch_bounds__(NT) k_residual(int n, const __grid_constant__ 
                                                  TO* __restrict__ ru, TO* __restrict__ rp,
                                                  double* __restrict__ partial, float* __restrict__ ru2,
                                                  float* __restrict__ rp2) {
+    pdl_enter();
     CELL_INDEX
     const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
     double ss = 0.0;
@@ -79,6 +80,7 @@ template <typename T>
 __global__ void __launch_bounds__(NT) k_uzawa_u(int n, const __grid_constant__ OpCoef<T> c, T tau,
                                                 const T* __restrict__ u, const T* __restrict__ p,
                                                 const T* __restrict__ f, T* __restrict__ uh) {
+    pdl_enter();
     CELL_INDEX
     if (!active) return;
     const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
@@ -106,6 +108,7 @@ __global__ void __launch_bounds__(NT) k_uzawa_p(int n, const __grid_constant__ O
                                                 const T* __restrict__ uh, T* __restrict__ p,
                                                 const T* __restrict__ g, const T* __restrict__ sinv,
                                                 T* __restrict__ dp) {
+    pdl_enter();
     CELL_INDEX
     if (!active) return;
     const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
@@ -122,6 +125,7 @@ template <typename T>
 __global__ void __launch_bounds__(NT) k_uzawa_u2(int n, const __grid_constant__ OpCoef<T> c, T tau,
                                                  const T* __restrict__ uh, const T* __restrict__ dp,
                                                  T* __restrict__ u) {
+    pdl_enter();
     CELL_INDEX
     if (!active) return;
     const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
@@ -149,9 +153,9 @@ template <typename T>
 void launch_uzawa(cudaStream_t s, int n, const OpCoef<T>& c, T tau, T sigma, T* u, T* p, const T* f,
                   const T* g, const T* sinv, T* uh, T* dp, int bx, int by) {
     const dim3 blk(bx, by), grid((n + 1 + bx - 1) / bx, (n + 1 + by - 1) / by);
-    k_uzawa_u<T><<<grid, blk, 0, s>>>(n, c, tau, u, p, f, uh);
-    k_uzawa_p<T><<<grid, blk, 0, s>>>(n, c, sigma, uh, p, g, sinv, dp);
-    k_uzawa_u2<T><<<grid, blk, 0, s>>>(n, c, tau, uh, dp, u);
+    launch_pdl(k_uzawa_u<T>, grid, blk, 0, s, n, c, tau, u, p, f, uh);
+    launch_pdl(k_uzawa_p<T>, grid, blk, 0, s, n, c, sigma, uh, p, g, sinv, dp);
+    launch_pdl(k_uzawa_u2<T>, grid, blk, 0, s, n, c, tau, uh, dp, u);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -160,6 +164,7 @@ template <typename T>
 __global__ void __launch_bounds__(NT) k_scale_L(int n, const __grid_constant__ OpCoef<T> c,
                                                 T* __restrict__ zu, T* __restrict__ zp,
                                                 const T* __restrict__ sinv) {
+    pdl_enter();
     CELL_INDEX
     if (!active) return;
     const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
@@ -186,6 +191,7 @@ __global__ void __launch_bounds__(NT) k_normal_update(int n, const __grid_consta
                                                       const T* __restrict__ zu, const T* __restrict__ zp,
                                                       const T* __restrict__ sinv, T* __restrict__ u,
                                                       T* __restrict__ p) {
+    pdl_enter();
     CELL_INDEX
     if (!active) return;
     const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
@@ -210,15 +216,15 @@ template <typename T>
 void launch_normal_eq(cudaStream_t s, int n, const OpCoef<T>& c, T tau, T* u, T* p, const T* f,
                       const T* g, const T* sinv, T* zu, T* zp) {
     const dim3 grid = cells_grid(n), blk(BX, BY);
-    k_residual<T, T><<<grid, blk, 0, s>>>(n, c, u, p, f, g, zu, zp, nullptr, nullptr, nullptr);
-    k_scale_L<T><<<grid, blk, 0, s>>>(n, c, zu, zp, sinv);
-    k_normal_update<T><<<grid, blk, 0, s>>>(n, c, tau, zu, zp, sinv, u, p);
+    launch_pdl(k_residual<T, T>, grid, blk, 0, s, n, c, u, p, f, g, zu, zp, nullptr, nullptr, nullptr);
+    launch_pdl(k_scale_L<T>, grid, blk, 0, s, n, c, zu, zp, sinv);
+    launch_pdl(k_normal_update<T>, grid, blk, 0, s, n, c, tau, zu, zp, sinv, u, p);
 }
 
 template <typename T, typename TO>
 void launch_residual(cudaStream_t s, int n, const OpCoef<T>& c, const T* u, const T* p, const T* f,
                      const T* g, TO* ru, TO* rp, double* partial, float* ru2, float* rp2) {
-    k_residual<T, TO><<<cells_grid(n), dim3(BX, BY), 0, s>>>(n, c, u, p, f, g, ru, rp, partial, ru2, rp2);
+    launch_pdl(k_residual<T, TO>, cells_grid(n), dim3(BX, BY), 0, s, n, c, u, p, f, g, ru, rp, partial, ru2, rp2);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -264,6 +270,7 @@ __device__ __forceinline__ void restrict_visit(int I, int J, int nc, const T* __
 template <typename T>
 __global__ void __launch_bounds__(NT) k_restrict(int nc, const T* __restrict__ ru, const T* __restrict__ rp,
                                                  T* __restrict__ fc, T* __restrict__ gc) {
+    pdl_enter();
     const int n = nc;
     CELL_INDEX
     if (!active) return;
@@ -309,7 +316,7 @@ __global__ void __launch_bounds__(NT) k_restrict(int nc, const T* __restrict__ r
 
 template <typename T>
 void launch_restrict(cudaStream_t s, int nc, const T* ru, const T* rp, T* fc, T* gc) {
-    k_restrict<T><<<cells_grid(nc), dim3(BX, BY), 0, s>>>(nc, ru, rp, fc, gc);
+    launch_pdl(k_restrict<T>, cells_grid(nc), dim3(BX, BY), 0, s, nc, ru, rp, fc, gc);
 }
 
 // Prolongation (Sec. 3, canonical embedding): every fine point owned by coarse square (I, J) is
@@ -318,6 +325,7 @@ void launch_restrict(cudaStream_t s, int nc, const T* ru, const T* rp, T* fc, T*
 template <typename T>
 __global__ void __launch_bounds__(NT) k_prolong(int nc, const T* __restrict__ uc, const T* __restrict__ pc,
                                                 T* __restrict__ u, T* __restrict__ p) {
+    pdl_enter();
     const int n = nc;
     CELL_INDEX
     if (!active) return;
@@ -364,7 +372,7 @@ __global__ void __launch_bounds__(NT) k_prolong(int nc, const T* __restrict__ uc
 
 template <typename T>
 void launch_prolong_add(cudaStream_t s, int nc, const T* uc, const T* pc, T* u, T* p) {
-    k_prolong<T><<<cells_grid(nc), dim3(BX, BY), 0, s>>>(nc, uc, pc, u, p);
+    launch_pdl(k_prolong<T>, cells_grid(nc), dim3(BX, BY), 0, s, nc, uc, pc, u, p);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -372,6 +380,7 @@ void launch_prolong_add(cudaStream_t s, int nc, const T* uc, const T* pc, T* u, 
 template <typename T>
 __global__ void k_coarse(const double* __restrict__ inv, const T* __restrict__ f, const T* __restrict__ g,
                          T* __restrict__ u, T* __restrict__ p) {
+    pdl_enter();
     __shared__ double b[27];
     const int t = threadIdx.x;
     auto vpos = [](int t, int& c, int& k) {
@@ -409,7 +418,7 @@ __global__ void k_coarse(const double* __restrict__ inv, const T* __restrict__ f
 
 template <typename T>
 void launch_coarse_solve(cudaStream_t s, const double* inv, const T* f, const T* g, T* u, T* p) {
-    k_coarse<T><<<1, 32, 0, s>>>(inv, f, g, u, p);
+    launch_pdl(k_coarse<T>, 1, 32, 0, s, inv, f, g, u, p);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -477,6 +486,7 @@ __device__ __forceinline__ double vertex_weight(int i, int j, int n) {
 
 template <typename T>
 __global__ void __launch_bounds__(NT) k_pmean_partial(int n, const T* __restrict__ p, double* __restrict__ partial) {
+    pdl_enter();
     CELL_INDEX
     double v = 0.0;
     if (active) v = vertex_weight(i, j, n) * (double)p[(size_t)j * (n + 1) + i];
@@ -486,12 +496,14 @@ __global__ void __launch_bounds__(NT) k_pmean_partial(int n, const T* __restrict
 
 template <typename T>
 __global__ void __launch_bounds__(NT) k_psub(int n, T* __restrict__ p, const double* __restrict__ scalar) {
+    pdl_enter();
     CELL_INDEX
     if (!active) return;
     p[(size_t)j * (n + 1) + i] -= (T)(*scalar);   // sum_i w_i = |Omega| = 1
 }
 
 __global__ void k_reduce(const double* __restrict__ partial, int count, double* __restrict__ out) {
+    pdl_enter();
     // fixed-order tree: deterministic for a given count
     __shared__ double red[1024];
     double s = 0.0;
@@ -506,15 +518,15 @@ __global__ void k_reduce(const double* __restrict__ partial, int count, double* 
 }
 
 void launch_reduce(cudaStream_t s, const double* partial, int count, double* out) {
-    k_reduce<<<1, 1024, 0, s>>>(partial, count, out);
+    launch_pdl(k_reduce, 1, 1024, 0, s, partial, count, out);
 }
 
 template <typename T>
 void launch_pmean(cudaStream_t s, int n, T* p, double* partial, double* scalar) {
     const dim3 grid = cells_grid(n), blk(BX, BY);
-    k_pmean_partial<T><<<grid, blk, 0, s>>>(n, p, partial);
-    k_reduce<<<1, 1024, 0, s>>>(partial, grid.x * grid.y, scalar);
-    k_psub<T><<<grid, blk, 0, s>>>(n, p, scalar);
+    launch_pdl(k_pmean_partial<T>, grid, blk, 0, s, n, p, partial);
+    launch_pdl(k_reduce, 1, 1024, 0, s, partial, grid.x * grid.y, scalar);
+    launch_pdl(k_psub<T>, grid, blk, 0, s, n, p, scalar);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -597,7 +609,7 @@ void launch_load(cudaStream_t s, int n, const MassCoef<T>& m, const T* fn, const
     OpCoef<T> dummy{};
     k_load<T><<<grid, blk, 0, s>>>(n, m, dummy, fn, gn, f, g, partial);
     if (project_g) {
-        k_reduce<<<1, 1024, 0, s>>>(partial, grid.x * grid.y, scalar);
+        launch_pdl(k_reduce, 1, 1024, 0, s, partial, grid.x * grid.y, scalar);
         k_gproj<T><<<grid, blk, 0, s>>>(n, m, g, scalar);
     }
 }
@@ -676,7 +688,7 @@ __global__ void __launch_bounds__(NT) k_sub_w(int n, double* __restrict__ g, con
 void launch_make_consistent(cudaStream_t s, int n, double* g, double* partial, double* scalar) {
     const dim3 grid = cells_grid(n), blk(BX, BY);
     k_sum_partial<<<grid, blk, 0, s>>>(n, g, partial);
-    k_reduce<<<1, 1024, 0, s>>>(partial, grid.x * grid.y, scalar);
+    launch_pdl(k_reduce, 1, 1024, 0, s, partial, grid.x * grid.y, scalar);
     k_sub_w<<<grid, blk, 0, s>>>(n, g, scalar);
 }
 

@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(NT) k_ir_update_df(int n, const __grid_constan
                                                      float2* __restrict__ ru, float2* __restrict__ rp,
                                                      float* __restrict__ r32u, float* __restrict__ r32p,
                                                      double* __restrict__ partial) {
+    pdl_enter();
     CELL_INDEX
     const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
     float ss = 0.f;
@@ -168,6 +169,7 @@ __global__ void __launch_bounds__(NT) k_residual_df(int n, const __grid_constant
                                                     float2* __restrict__ ru, float2* __restrict__ rp,
                                                     float* __restrict__ r32u, float* __restrict__ r32p,
                                                     double* __restrict__ partial) {
+    pdl_enter();
     CELL_INDEX
     const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
     double ss = 0.0;
@@ -208,14 +210,14 @@ __global__ void __launch_bounds__(NT) k_residual_df(int n, const __grid_constant
 void launch_ir_update_df(cudaStream_t s, int n, const OpCoef<float>& chi, const OpCoef<float>& clo,
                          const float* eu, const float* ep, double* xu, double* xp, double* ru, double* rp,
                          float* r32u, float* r32p, double* partial) {
-    k_ir_update_df<<<cells_grid(n), dim3(BX, BY), 0, s>>>(n, chi, clo, eu, ep, xu, xp, reinterpret_cast<float2*>(ru),
+    launch_pdl(k_ir_update_df, cells_grid(n), dim3(BX, BY), 0, s, n, chi, clo, eu, ep, xu, xp, reinterpret_cast<float2*>(ru),
                                                           reinterpret_cast<float2*>(rp), r32u, r32p, partial);
 }
 
 void launch_residual_df(cudaStream_t s, int n, const OpCoef<double>& c, const double* u, const double* p,
                         const double* f, const double* g, double* ru, double* rp, float* r32u, float* r32p,
                         double* partial) {
-    k_residual_df<<<cells_grid(n), dim3(BX, BY), 0, s>>>(n, c, u, p, f, g, reinterpret_cast<float2*>(ru),
+    launch_pdl(k_residual_df, cells_grid(n), dim3(BX, BY), 0, s, n, c, u, p, f, g, reinterpret_cast<float2*>(ru),
                                                          reinterpret_cast<float2*>(rp), r32u, r32p, partial);
 }
 

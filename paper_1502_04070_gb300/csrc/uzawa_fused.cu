@@ -45,6 +45,7 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 4 ? 2 : 1)) k_uzawa_fuse
                                                         const T* __restrict__ f, const T* __restrict__ g,
                                                         const T* __restrict__ sinv, T* __restrict__ u_out,
                                                         T* __restrict__ p_out) {
+    pdl_enter();
     using G = FusedTile<T, TX, TY>;
     constexpr int NTH = TX * TY;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -203,7 +204,7 @@ static void launch_v(cudaStream_t s, int n, const OpCoef<T>& c, T tau, T sigma, 
                      const T* g, const T* sinv, T* u_out, T* p_out) {
     using G = FusedTile<T, TX, TY>;
     const dim3 grid((n + 1 + TX - 1) / TX, (n + 1 + TY - 1) / TY), blk(TX, TY);
-    k_uzawa_fused<T, TX, TY><<<grid, blk, G::BYTES, s>>>(n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
+    launch_pdl(k_uzawa_fused<T, TX, TY>, grid, blk, G::BYTES, s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
 }
 
 template <typename T>
