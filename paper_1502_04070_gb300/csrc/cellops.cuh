@@ -3,6 +3,8 @@
 // A "view" maps P2-lattice coordinates (X, Y) (or vertex coordinates for pressure) to values; the
 // same row code reads global memory through the read-only path or a shared-memory tile.
 #pragma once
+#include <utility>
+
 #include "common.cuh"
 
 namespace smg {
@@ -31,7 +33,7 @@ template <typename T>
 struct Acc {
     T au[2][4];   // (A u) at the owned velocity nodes V, H, E, C
     T bt[2][4];   // (B^T p)
-    T dg[4];      // diag A
+    T idg[4];     // 1 / diag A
     T bu;         // (B u) at the owned vertex
 };
 
@@ -68,9 +70,10 @@ struct GView {
     static constexpr bool zero_filled = false;   // reads outside the array are not allowed
     const T* p;
     int ld;
-    __device__ __forceinline__ T operator()(int X, int Y) const { return __ldg(p + (size_t)Y * ld + X); }
+    // 32-bit offsets: one array holds at most (2N+1)^2 < 2^31 values for every supported level
+    __device__ __forceinline__ T operator()(int X, int Y) const { return __ldg(p + (Y * ld + X)); }
     __device__ __forceinline__ T at(int si, int sj, int a, int b) const {
-        return __ldg(p + (size_t)(2 * sj + b) * ld + 2 * si + a);
+        return __ldg(p + ((2 * sj + b) * ld + 2 * si + a));
     }
 };
 template <typename T>
@@ -133,7 +136,7 @@ __device__ __forceinline__ void sq_rows(const T (&A)[2][9][9], const OpCoef<T>& 
             a.bt[0][s] += btrow<O, L>(c.Bx, pq);
             a.bt[1][s] += btrow<O, L>(c.By, pq);
         }
-        if constexpr (DD) a.dg[s] += A[O][L][L];
+        if constexpr (DD) a.idg[s] += A[O][L][L];   // the diagonal; inverted in cell_apply
         sq_rows<DA, DBT, DD, O, SQ, R + 1>(A, c, vx, vy, pq, a);
     }
 }
@@ -163,16 +166,21 @@ __device__ __forceinline__ void cell_apply(int i, int j, int n, const T (&A)[2][
                                            const VU& ux, const VU& uy, const VP& p, Acc<T>& a) {
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
-        a.au[0][s] = a.au[1][s] = a.bt[0][s] = a.bt[1][s] = a.dg[s] = T(0);
+        a.au[0][s] = a.au[1][s] = a.bt[0][s] = a.bt[1][s] = a.idg[s] = T(0);
     }
     a.bu = T(0);
     visit<DA, DBT, DB, DD, MASK, 0>(i, j, n, A, c, ux, uy, p, a);
     visit<DA, DBT, DB, DD, MASK, 1>(i, j, n, A, c, ux, uy, p, a);
     visit<DA, DBT, DB, DD, MASK, 2>(i, j, n, A, c, ux, uy, p, a);
     visit<DA, DBT, DB, DD, MASK, 3>(i, j, n, A, c, ux, uy, p, a);
+    if constexpr (DD) {
+#pragma unroll
+        for (int s = 0; s < 4; ++s) a.idg[s] = T(1) / a.idg[s];   // nodes without squares: inf, never used
+    }
 }
 
-// ---- merged node stencils for cells off the mid-lines (all four squares share orientation O)
+// ---- merged node stencils for cells off the mid-lines (all four squares share orientation O).
+// Every structural-zero test below is a template argument, so it is decided at compile time.
 __host__ __device__ constexpr bool need_win(int O, bool DA, bool DB, int w) {
     return (DA && (nz_MA(O, 0, w) || nz_MA(O, 1, w) || nz_MA(O, 2, w) || nz_MA(O, 3, w))) || (DB && nz_MB(O, w));
 }
@@ -180,20 +188,79 @@ __host__ __device__ constexpr bool need_vwin(int O, int v) {
     return nz_MBT(O, 0, v) || nz_MBT(O, 1, v) || nz_MBT(O, 2, v) || nz_MBT(O, 3, v);
 }
 
+template <int O, bool DA, bool DB, bool MASK, int W, typename T, typename VU>
+__device__ __forceinline__ void win_load1(int i, int j, int n, const VU& ux, const VU& uy, T (&wx)[25], T (&wy)[25]) {
+    if constexpr (need_win(O, DA, DB, W)) {
+        constexpr int dx = W % 5 - 2, dy = W / 5 - 2;
+        if constexpr (VU::zero_filled && !MASK) {
+            wx[W] = ux.at(i - 1, j - 1, dx + 2, dy + 2);
+            wy[W] = uy.at(i - 1, j - 1, dx + 2, dy + 2);
+        } else {
+            const int X = 2 * i + dx, Y = 2 * j + dy;
+            const bool ok = MASK ? interior2(X, Y, n) : (X >= 0 && Y >= 0 && X <= 2 * n && Y <= 2 * n);
+            wx[W] = ok ? ux.at(i - 1, j - 1, dx + 2, dy + 2) : T(0);
+            wy[W] = ok ? uy.at(i - 1, j - 1, dx + 2, dy + 2) : T(0);
+        }
+    }
+}
+template <int O, bool DA, bool DB, bool MASK, typename T, typename VU, int... W>
+__device__ __forceinline__ void win_load(int i, int j, int n, const VU& ux, const VU& uy, T (&wx)[25], T (&wy)[25],
+                                         std::integer_sequence<int, W...>) {
+    (win_load1<O, DA, DB, MASK, W>(i, j, n, ux, uy, wx, wy), ...);
+}
+
+template <int O, int V, typename T, typename VP>
+__device__ __forceinline__ void vwin_load1(int i, int j, int n, const VP& p, T (&pw)[9]) {
+    if constexpr (need_vwin(O, V)) {
+        const int I = i + V % 3 - 1, J = j + V / 3 - 1;
+        if constexpr (VP::zero_filled) pw[V] = p(I, J);
+        else pw[V] = (I >= 0 && J >= 0 && I <= n && J <= n) ? p(I, J) : T(0);
+    }
+}
+template <int O, typename T, typename VP, int... V>
+__device__ __forceinline__ void vwin_load(int i, int j, int n, const VP& p, T (&pw)[9], std::integer_sequence<int, V...>) {
+    (vwin_load1<O, V>(i, j, n, p, pw), ...);
+}
+
+template <int O, int S, int K, typename T>
+__device__ __forceinline__ void ma_term(const OpCoef<T>& c, const T (&w)[25], T& s) {
+    if constexpr (nz_MA(O, S, K)) s = fma(c.MA[O][S][K], w[K], s);
+}
+template <int O, int S, typename T, int... K>
+__device__ __forceinline__ T ma_row_i(const OpCoef<T>& c, const T (&w)[25], std::integer_sequence<int, K...>) {
+    T s = T(0);
+    (ma_term<O, S, K>(c, w, s), ...);
+    return s;
+}
 template <int O, int S, typename T>
 __device__ __forceinline__ T ma_row(const OpCoef<T>& c, const T (&w)[25]) {
+    return ma_row_i<O, S>(c, w, std::make_integer_sequence<int, 25>{});
+}
+
+template <int O, int S, int K, typename T>
+__device__ __forceinline__ void mbt_term(const T (&B)[2][4][9], const T (&pw)[9], T& s) {
+    if constexpr (nz_MBT(O, S, K)) s = fma(B[O][S][K], pw[K], s);
+}
+template <int O, int S, typename T, int... K>
+__device__ __forceinline__ T mbt_row_i(const T (&B)[2][4][9], const T (&pw)[9], std::integer_sequence<int, K...>) {
     T s = T(0);
-#pragma unroll
-    for (int k = 0; k < 25; ++k)
-        if (nz_MA(O, S, k)) s = fma(c.MA[O][S][k], w[k], s);
+    (mbt_term<O, S, K>(B, pw, s), ...);
     return s;
 }
 template <int O, int S, typename T>
 __device__ __forceinline__ T mbt_row(const T (&B)[2][4][9], const T (&pw)[9]) {
+    return mbt_row_i<O, S>(B, pw, std::make_integer_sequence<int, 9>{});
+}
+
+template <int O, int K, typename T>
+__device__ __forceinline__ void mb_term(const OpCoef<T>& c, const T (&wx)[25], const T (&wy)[25], T& s) {
+    if constexpr (nz_MB(O, K)) s = fma(c.MBx[O][K], wx[K], fma(c.MBy[O][K], wy[K], s));
+}
+template <int O, typename T, int... K>
+__device__ __forceinline__ T mb_row_i(const OpCoef<T>& c, const T (&wx)[25], const T (&wy)[25],
+                                      std::integer_sequence<int, K...>) {
     T s = T(0);
-#pragma unroll
-    for (int k = 0; k < 9; ++k)
-        if (nz_MBT(O, S, k)) s = fma(B[O][S][k], pw[k], s);
+    (mb_term<O, K>(c, wx, wy, s), ...);
     return s;
 }
 
@@ -201,33 +268,10 @@ template <bool DA, bool DBT, bool DB, bool DD, bool MASK, int O, typename T, typ
 __device__ __forceinline__ void cell_apply_merged(int i, int j, int n, const OpCoef<T>& c, const VU& ux, const VU& uy,
                                                   const VP& p, Acc<T>& a) {
     T wx[25], wy[25], pw[9];
-    if constexpr (DA || DB) {
+    if constexpr (DA || DB) win_load<O, DA, DB, MASK>(i, j, n, ux, uy, wx, wy, std::make_integer_sequence<int, 25>{});
+    if constexpr (DBT) vwin_load<O>(i, j, n, p, pw, std::make_integer_sequence<int, 9>{});
 #pragma unroll
-        for (int w = 0; w < 25; ++w) {
-            if (!need_win(O, DA, DB, w)) continue;
-            const int dx = w % 5 - 2, dy = w / 5 - 2;
-            const int X = 2 * i + dx, Y = 2 * j + dy;
-            if constexpr (VU::zero_filled && !MASK) {
-                wx[w] = ux.at(i - 1, j - 1, dx + 2, dy + 2);
-                wy[w] = uy.at(i - 1, j - 1, dx + 2, dy + 2);
-            } else {
-                const bool ok = MASK ? interior2(X, Y, n) : (X >= 0 && Y >= 0 && X <= 2 * n && Y <= 2 * n);
-                wx[w] = ok ? ux.at(i - 1, j - 1, dx + 2, dy + 2) : T(0);
-                wy[w] = ok ? uy.at(i - 1, j - 1, dx + 2, dy + 2) : T(0);
-            }
-        }
-    }
-    if constexpr (DBT) {
-#pragma unroll
-        for (int v = 0; v < 9; ++v) {
-            if (!need_vwin(O, v)) continue;
-            const int I = i + v % 3 - 1, J = j + v / 3 - 1;
-            if constexpr (VP::zero_filled) pw[v] = p(I, J);
-            else pw[v] = (I >= 0 && J >= 0 && I <= n && J <= n) ? p(I, J) : T(0);
-        }
-    }
-#pragma unroll
-    for (int s = 0; s < 4; ++s) a.au[0][s] = a.au[1][s] = a.bt[0][s] = a.bt[1][s] = a.dg[s] = T(0);
+    for (int s = 0; s < 4; ++s) a.au[0][s] = a.au[1][s] = a.bt[0][s] = a.bt[1][s] = a.idg[s] = T(0);
     a.bu = T(0);
     if constexpr (DA) {
         a.au[0][0] = ma_row<O, 0>(c, wx); a.au[1][0] = ma_row<O, 0>(c, wy);
@@ -242,18 +286,10 @@ __device__ __forceinline__ void cell_apply_merged(int i, int j, int n, const OpC
         a.bt[0][3] = mbt_row<O, 3>(c.MBTx, pw); a.bt[1][3] = mbt_row<O, 3>(c.MBTy, pw);
     }
     if constexpr (DD) {
-        a.dg[0] = c.MA[O][0][12];   // window index of node s: ((s >> 1) + 2) * 5 + (s & 1) + 2
-        a.dg[1] = c.MA[O][1][13];
-        a.dg[2] = c.MA[O][2][17];
-        a.dg[3] = c.MA[O][3][18];
-    }
-    if constexpr (DB) {
-        T s = T(0);
 #pragma unroll
-        for (int w = 0; w < 25; ++w)
-            if (nz_MB(O, w)) s = fma(c.MBx[O][w], wx[w], fma(c.MBy[O][w], wy[w], s));
-        a.bu = s;
+        for (int s = 0; s < 4; ++s) a.idg[s] = c.MIdg[O][s];
     }
+    if constexpr (DB) a.bu = mb_row_i<O>(c, wx, wy, std::make_integer_sequence<int, 25>{});
 }
 
 // Operator rows of cell (i, j): merged stencils off the mid-lines, the square-by-square gather on

@@ -19,6 +19,7 @@
 // and the pressure vertex (i, j).  Nodes that fall outside the lattice do not exist.
 #pragma once
 #include <cstdint>
+#include <utility>
 #include <cuda_runtime.h>
 
 namespace smg {
@@ -37,6 +38,7 @@ struct OpCoef {            // local square matrices of one level
     T MBTy[2][4][9];
     T MBx[2][25];          // [o][(dy+2)*5 + dx+2]
     T MBy[2][25];
+    T MIdg[2][4];          // 1 / diag A of the four owned nodes, [o][s]
 };
 
 template <typename T>
@@ -117,6 +119,7 @@ inline void fill_merged(OpCoef<T>& c) {
                     }
             }
             for (int w = 0; w < 25; ++w) c.MA[o][s][w] = (T)ma[w];
+            c.MIdg[o][s] = (T)(1.0 / ma[((s >> 1) + 2) * 5 + (s & 1) + 2]);
             for (int v = 0; v < 9; ++v) {
                 c.MBTx[o][s][v] = (T)bx[v];
                 c.MBTy[o][s][v] = (T)by[v];
@@ -141,32 +144,49 @@ __device__ __forceinline__ int orient(int si, int sj, int n) {
     return (si < h) != (sj < h);
 }
 
-// row L of A (orientation O) times the 9 square values
-template <int O, int L, typename T>
-__device__ __forceinline__ T arow(const T (&A)[2][9][9], const T (&v)[9]) {
+// row L of A (orientation O) times the 9 square values; zero couplings dropped at compile time
+template <int O, int L, int M, typename T>
+__device__ __forceinline__ void a_term(const T (&A)[2][9][9], const T (&v)[9], T& s) {
+    if constexpr (couple(O, L, M)) s = fma(A[O][L][M], v[M], s);
+}
+template <int O, int L, typename T, int... M>
+__device__ __forceinline__ T arow_i(const T (&A)[2][9][9], const T (&v)[9], std::integer_sequence<int, M...>) {
     T s = T(0);
-#pragma unroll
-    for (int m = 0; m < 9; ++m)
-        if (couple(O, L, m)) s = fma(A[O][L][m], v[m], s);
+    (a_term<O, L, M>(A, v, s), ...);
     return s;
 }
+template <int O, int L, typename T>
+__device__ __forceinline__ T arow(const T (&A)[2][9][9], const T (&v)[9]) {
+    return arow_i<O, L>(A, v, std::make_integer_sequence<int, 9>{});
+}
 // (B^T p) restricted to row L: sum_q B[q][L] p[q]
+template <int O, int L, int Q, typename T>
+__device__ __forceinline__ void bt_term(const T (&B)[2][4][9], const T (&p)[4], T& s) {
+    if constexpr (couple(O, corner_node(Q), L)) s = fma(B[O][Q][L], p[Q], s);
+}
 template <int O, int L, typename T>
 __device__ __forceinline__ T btrow(const T (&B)[2][4][9], const T (&p)[4]) {
     T s = T(0);
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-        if (couple(O, corner_node(q), L)) s = fma(B[O][q][L], p[q], s);
+    bt_term<O, L, 0>(B, p, s);
+    bt_term<O, L, 1>(B, p, s);
+    bt_term<O, L, 2>(B, p, s);
+    bt_term<O, L, 3>(B, p, s);
     return s;
 }
 // (B u) restricted to pressure row Q
+template <int O, int Q, int M, typename T>
+__device__ __forceinline__ void b_term(const T (&B)[2][4][9], const T (&v)[9], T& s) {
+    if constexpr (couple(O, corner_node(Q), M)) s = fma(B[O][Q][M], v[M], s);
+}
+template <int O, int Q, typename T, int... M>
+__device__ __forceinline__ T brow_i(const T (&B)[2][4][9], const T (&v)[9], std::integer_sequence<int, M...>) {
+    T s = T(0);
+    (b_term<O, Q, M>(B, v, s), ...);
+    return s;
+}
 template <int O, int Q, typename T>
 __device__ __forceinline__ T brow(const T (&B)[2][4][9], const T (&v)[9]) {
-    T s = T(0);
-#pragma unroll
-    for (int m = 0; m < 9; ++m)
-        if (couple(O, corner_node(Q), m)) s = fma(B[O][Q][m], v[m], s);
-    return s;
+    return brow_i<O, Q>(B, v, std::make_integer_sequence<int, 9>{});
 }
 
 // Is P2-lattice point (X, Y) an interior velocity node of a level with N = n?

@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(NT) k_uzawa_u(int n, const __grid_constant__ O
 #pragma unroll
         for (int comp = 0; comp < 2; ++comp) {
             const size_t k = comp * n2 + idx;
-            uh[k] = unk ? u[k] + tau * (f[k] - a.au[comp][s] - a.bt[comp][s]) / a.dg[s] : T(0);
+            uh[k] = unk ? u[k] + tau * (f[k] - a.au[comp][s] - a.bt[comp][s]) * a.idg[s] : T(0);
         }
     }
 }
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(NT) k_uzawa_u2(int n, const __grid_constant__ 
         for (int comp = 0; comp < 2; ++comp) {
             const size_t k = comp * n2 + idx;
             // u^{m} = u^{m-1/2} - tau Ahat^{-1} B^T (p^{m} - p^{m-1})
-            u[k] = unk ? uh[k] - tau * a.bt[comp][s] / a.dg[s] : T(0);
+            u[k] = unk ? uh[k] - tau * a.bt[comp][s] * a.idg[s] : T(0);
         }
     }
 }
@@ -179,8 +179,8 @@ __global__ void __launch_bounds__(NT) k_scale_L(int n, const __grid_constant__ O
         int X, Y;
         slot_pos(i, j, s, X, Y);
         const size_t idx = (size_t)Y * ld + X;
-        zu[idx] /= a.dg[s];
-        zu[n2 + idx] /= a.dg[s];
+        zu[idx] *= a.idg[s];
+        zu[n2 + idx] *= a.idg[s];
     }
     const size_t vi = (size_t)j * (n + 1) + i;
     zp[vi] *= sinv[vi];
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(NT) k_normal_update(int n, const __grid_consta
         slot_pos(i, j, s, X, Y);
         const size_t idx = (size_t)Y * ld + X;
 #pragma unroll
-        for (int comp = 0; comp < 2; ++comp) u[comp * n2 + idx] += tau * (a.au[comp][s] + a.bt[comp][s]) / a.dg[s];
+        for (int comp = 0; comp < 2; ++comp) u[comp * n2 + idx] += tau * (a.au[comp][s] + a.bt[comp][s]) * a.idg[s];
     }
     const size_t vi = (size_t)j * (n + 1) + i;
     p[vi] += tau * sinv[vi] * a.bu;

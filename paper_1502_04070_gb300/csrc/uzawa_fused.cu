@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 4 ? 2 : 1)) k_uzawa_fuse
     const int tid = threadIdx.y * TX + threadIdx.x;
     const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
     const int ld = 2 * n + 1;
-    const size_t n2 = (size_t)ld * ld;
+    const int n2 = ld * ld;   // < 2^31 for every supported level
 
     // ---- stage u (both components) and p with their halos; zero outside / on the boundary.
     // Global reads run along X (coalesced); the parity split sends even / odd X to the two planes.
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 4 ? 2 : 1)) k_uzawa_fuse
         const int X = X0 + x, Y = Y0 + y;
         T vx = T(0), vy = T(0);
         if (interior2(X, Y, n)) {
-            const size_t k = (size_t)Y * ld + X;
+            const int k = Y * ld + X;
             vx = __ldg(u + k);
             vy = __ldg(u + n2 + k);
         }
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 4 ? 2 : 1)) k_uzawa_fuse
     for (int q = tid; q < G::PW * G::PH; q += NTH) {
         const int x = q % G::PW, y = q / G::PW;
         const int I = i0 - 3 + x, J = j0 - 3 + y;
-        sP[q] = (I >= 0 && J >= 0 && I <= n && J <= n) ? __ldg(p + (size_t)J * (n + 1) + I) : T(0);
+        sP[q] = (I >= 0 && J >= 0 && I <= n && J <= n) ? __ldg(p + (J * (n + 1) + I)) : T(0);
     }
     __syncthreads();
 
@@ -102,8 +102,8 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 4 ? 2 : 1)) k_uzawa_fuse
                 if (!slot_unknown(cn, s)) continue;
                 int X, Y;
                 slot_pos(ci, cj, s, X, Y);
-                const size_t k = (size_t)Y * ld + X;
-                const T w = tau / a.dg[s];
+                const int k = Y * ld + X;
+                const T w = tau * a.idg[s];
                 hx[s] = vux.at(ci, cj, s & 1, s >> 1) + w * (__ldg(f + k) - a.au[0][s] - a.bt[0][s]);
                 hy[s] = vuy.at(ci, cj, s & 1, s >> 1) + w * (__ldg(f + n2 + k) - a.au[1][s] - a.bt[1][s]);
             }
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 4 ? 2 : 1)) k_uzawa_fuse
         if (vi >= 0 && vj >= 0 && vi <= n && vj <= n) {
             Acc<T> a;
             cell_apply_auto<false, false, true, false, false>(vi, vj, n, c, vhx, vhy, vp, a);
-            const size_t k = (size_t)vj * (n + 1) + vi;
+            const int k = vj * (n + 1) + vi;
             d = sigma * __ldg(sinv + k) * (a.bu - __ldg(g + k));
         }
         sD[q] = d;
@@ -146,17 +146,17 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 4 ? 2 : 1)) k_uzawa_fuse
         if (!slot_exists(cn, s)) continue;
         int X, Y;
         slot_pos(ci, cj, s, X, Y);
-        const size_t k = (size_t)Y * ld + X;
+        const int k = Y * ld + X;
         T ox = T(0), oy = T(0);
         if (slot_unknown(cn, s)) {
-            const T w = tau / a.dg[s];
+            const T w = tau * a.idg[s];
             ox = vhx.at(ci, cj, s & 1, s >> 1) - w * a.bt[0][s];
             oy = vhy.at(ci, cj, s & 1, s >> 1) - w * a.bt[1][s];
         }
         u_out[k] = ox;
         u_out[n2 + k] = oy;
     }
-    p_out[(size_t)cj * (n + 1) + ci] = vp(ci, cj) + vd(ci, cj);
+    p_out[cj * (n + 1) + ci] = vp(ci, cj) + vd(ci, cj);
 }
 
 // Step variants the autotuner chooses from, per level, for float32 (float64 uses the three-kernel
