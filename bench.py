@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=2, help="steps of the plain float64 comparison")
-    ap.add_argument("--kernel", default=None, choices=["uzawa_f32", "uzawa_f64", "residual_f64", "mixed_solve"],
+    ap.add_argument("--kernel", default=None, choices=["uzawa_f32", "uzawa_f64", "residual_f64", "mixed_solve", "ir_steps"],
                     help="microbenchmark one kernel (for profiler captures) instead of the workload")
     ap.add_argument("--level", type=int, default=9)
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solver measurement")
@@ -79,6 +79,20 @@ def run_kernel(args):
         ev0.record()
         for _ in range(args.reps):
             S.smooth(*t, 1) if args.kernel == "uzawa_f64" else S.residual(*t)
+    elif args.kernel == "ir_steps":
+        # args.reps refinement steps in one device-side loop (tol 0: the loop runs them all)
+        S.autotune()
+        fn, gn = torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda()
+        F, G = S.load_vectors(fn, gn, project_g=True)
+        S.solve(F, G, tol=0.0, max_cycles=args.reps)
+        torch.cuda.synchronize()
+        ev0.record()
+        S.solve(F, G, tol=0.0, max_cycles=args.reps)
+        ev1.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"kernel": "ir_steps", "level": k, "ms_per_step": ev0.elapsed_time(ev1) / args.reps}),
+              flush=True)
+        return
     else:
         fn, gn = torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda()
         F, G = S.load_vectors(fn, gn, project_g=True)
