@@ -63,7 +63,7 @@ def run_kernel(args):
     u, p = workloads.random_state(k, 5)
     f, g = workloads.random_nodal(k, 6)
     g = g - g.mean()
-    prec = "mixed" if args.kernel in ("uzawa_f32", "mixed_solve") else "fp64"
+    prec = "mixed" if args.kernel in ("uzawa_f32", "mixed_solve", "ir_steps") else "fp64"
     S = Solver(k + 1, 1e4, precision=prec)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if args.kernel == "uzawa_f32":

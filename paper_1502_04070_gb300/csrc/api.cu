@@ -138,6 +138,7 @@ struct stokes_handle_t {
     double* hscal = nullptr;                // pinned host mirror
     MassCoef<double> mass{};
     OpCoef<float> chi{}, clo{};             // MIXED: finest float64 coefficients split hi + lo
+    bool coarse_kernel = true;              // float32 levels <= 4 in one shared-memory kernel
     cudaGraphExec_t step = nullptr;         // one cycle + projection + residual norm
     int step_kernels = 0;                   // kernel nodes in `step`
     cudaGraphExec_t loop = nullptr;         // WHILE(not converged) { step; device-side test }
@@ -210,6 +211,28 @@ void mg_cycle(stokes_handle* h, std::vector<Level<T>>& H, int l) {
     if (l == 0) {
         launch_coarse_solve<T>(h->st, h->inv, lv.f, lv.g, lv.u, lv.p);
         return;
+    }
+    if constexpr (sizeof(T) == 4) {
+        // small levels: the whole V-cycle from level l down in one CTA (shared memory)
+        if (l <= kCoarseCycleTop && h->prm.gamma == 1 && h->prm.smoother == STOKES_UZAWA && h->coarse_kernel) {
+            CoarseCycleArgs a;
+            for (int k = 1; k <= l; ++k) {
+                a.c[k - 1] = H[k].c;
+                a.sinv[k - 1] = H[k].sinv;
+            }
+            a.inv = h->inv;
+            a.u = lv.u;
+            a.p = lv.p;
+            a.f = lv.f;
+            a.g = lv.g;
+            a.tau = (float)h->prm.tau;
+            a.sigma = (float)h->prm.sigma;
+            a.nu_pre = h->prm.nu_pre;
+            a.nu_post = h->prm.nu_post;
+            a.top = l;
+            launch_coarse_cycle(h->st, a);
+            return;
+        }
     }
     const bool top = l == (int)H.size() - 1;
     bool sw = smooth_level(h, lv, h->prm.nu_pre, top, false);
@@ -497,7 +520,8 @@ stokes_status stokes_setup(const stokes_params* prm, void* stream, stokes_handle
         return STOKES_ERR_BAD_ARG;
     stokes_status s = ensure_weights();
     if (s != STOKES_OK) return s;
-    if (prepare_uzawa_fused<float>() != cudaSuccess || prepare_uzawa_fused<double>() != cudaSuccess)
+    if (prepare_uzawa_fused<float>() != cudaSuccess || prepare_uzawa_fused<double>() != cudaSuccess ||
+        prepare_coarse_cycle() != cudaSuccess)
         return STOKES_ERR_CUDA;
     stokes_handle* h = new stokes_handle_t();
     h->prm = P;

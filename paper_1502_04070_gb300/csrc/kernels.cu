@@ -248,7 +248,14 @@ __device__ __forceinline__ void restrict_rows(const T (&v)[2][4][4], T (&acc)[2]
     }
 }
 
-template <int SQ, typename T>
+// global arrays go through the read-only path; shared-memory arrays (the coarse sub-cycle) do not
+template <bool LDG, typename T>
+__device__ __forceinline__ T ldv(const T* p) {
+    if constexpr (LDG) return __ldg(p);
+    else return *p;
+}
+
+template <int SQ, bool LDG, typename T>
 __device__ __forceinline__ void restrict_visit(int I, int J, int nc, const T* __restrict__ ru, T (&acc)[2][4]) {
     const int SI = I - (SQ & 1), SJ = J - (SQ >> 1);
     if (SI < 0 || SJ < 0 || SI >= nc || SJ >= nc) return;
@@ -260,27 +267,24 @@ __device__ __forceinline__ void restrict_visit(int I, int J, int nc, const T* __
 #pragma unroll
         for (int fa = 0; fa < 4; ++fa) {
             const size_t k = (size_t)(4 * SJ + fb) * ldf + 4 * SI + fa;
-            v[0][fb][fa] = __ldg(ru + k);
-            v[1][fb][fa] = __ldg(ru + n2f + k);
+            v[0][fb][fa] = ldv<LDG>(ru + k);
+            v[1][fb][fa] = ldv<LDG>(ru + n2f + k);
         }
     if (orient(SI, SJ, nc)) restrict_rows<1, SQ, 0>(v, acc);
     else restrict_rows<0, SQ, 0>(v, acc);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(NT) k_restrict(int nc, const T* __restrict__ ru, const T* __restrict__ rp,
-                                                 T* __restrict__ fc, T* __restrict__ gc) {
-    pdl_enter();
-    const int n = nc;
-    CELL_INDEX
-    if (!active) return;
+// coarse cell (i, j) of level nc: its owned coarse velocity nodes and vertex
+template <bool LDG, typename T>
+__device__ __forceinline__ void restrict_cell(int i, int j, int nc, const T* __restrict__ ru, const T* __restrict__ rp,
+                                              T* __restrict__ fc, T* __restrict__ gc) {
     T acc[2][4];
 #pragma unroll
     for (int s = 0; s < 4; ++s) acc[0][s] = acc[1][s] = T(0);
-    restrict_visit<0>(i, j, nc, ru, acc);
-    restrict_visit<1>(i, j, nc, ru, acc);
-    restrict_visit<2>(i, j, nc, ru, acc);
-    restrict_visit<3>(i, j, nc, ru, acc);
+    restrict_visit<0, LDG>(i, j, nc, ru, acc);
+    restrict_visit<1, LDG>(i, j, nc, ru, acc);
+    restrict_visit<2, LDG>(i, j, nc, ru, acc);
+    restrict_visit<3, LDG>(i, j, nc, ru, acc);
     const CellNodes cn = cell_nodes(i, j, nc);
     const int ldc = 2 * nc + 1;
     const size_t n2c = (size_t)ldc * ldc;
@@ -315,6 +319,16 @@ __global__ void __launch_bounds__(NT) k_restrict(int nc, const T* __restrict__ r
 }
 
 template <typename T>
+__global__ void __launch_bounds__(NT) k_restrict(int nc, const T* __restrict__ ru, const T* __restrict__ rp,
+                                                 T* __restrict__ fc, T* __restrict__ gc) {
+    pdl_enter();
+    const int n = nc;
+    CELL_INDEX
+    if (!active) return;
+    restrict_cell<true>(i, j, nc, ru, rp, fc, gc);
+}
+
+template <typename T>
 void launch_restrict(cudaStream_t s, int nc, const T* ru, const T* rp, T* fc, T* gc) {
     launch_pdl(k_restrict<T>, cells_grid(nc), dim3(BX, BY), 0, s, nc, ru, rp, fc, gc);
 }
@@ -322,13 +336,9 @@ void launch_restrict(cudaStream_t s, int nc, const T* ru, const T* rp, T* fc, T*
 // Prolongation (Sec. 3, canonical embedding): every fine point owned by coarse square (I, J) is
 // the coarse P2 function of that square evaluated there; P1 values are vertex injection and
 // averages along coarse edges.
-template <typename T>
-__global__ void __launch_bounds__(NT) k_prolong(int nc, const T* __restrict__ uc, const T* __restrict__ pc,
-                                                T* __restrict__ u, T* __restrict__ p) {
-    pdl_enter();
-    const int n = nc;
-    CELL_INDEX
-    if (!active) return;
+template <bool LDG, typename T>
+__device__ __forceinline__ void prolong_cell(int i, int j, int nc, const T* __restrict__ uc, const T* __restrict__ pc,
+                                             T* __restrict__ u, T* __restrict__ p) {
     const int nf = 2 * nc, ldf = 2 * nf + 1, ldc = 2 * nc + 1;
     const size_t n2f = (size_t)ldf * ldf, n2c = (size_t)ldc * ldc;
     if (i < nc && j < nc) {
@@ -336,8 +346,8 @@ __global__ void __launch_bounds__(NT) k_prolong(int nc, const T* __restrict__ uc
 #pragma unroll
         for (int m = 0; m < 9; ++m) {
             const size_t k = (size_t)(2 * j + m / 3) * ldc + 2 * i + m % 3;
-            z[0][m] = __ldg(uc + k);
-            z[1][m] = __ldg(uc + n2c + k);
+            z[0][m] = ldv<LDG>(uc + k);
+            z[1][m] = ldv<LDG>(uc + n2c + k);
         }
         const int o = orient(i, j, nc);
 #pragma unroll
@@ -359,7 +369,7 @@ __global__ void __launch_bounds__(NT) k_prolong(int nc, const T* __restrict__ uc
             }
     }
     const int ldp = nc + 1, ldpf = nf + 1;
-    auto P = [&](int a, int b) { return __ldg(pc + (size_t)b * ldp + a); };
+    auto P = [&](int a, int b) { return ldv<LDG>(pc + (size_t)b * ldp + a); };
     const T p00 = P(i, j);
     p[(size_t)(2 * j) * ldpf + 2 * i] += p00;
     if (i < nc) p[(size_t)(2 * j) * ldpf + 2 * i + 1] += T(0.5) * (p00 + P(i + 1, j));
@@ -368,6 +378,16 @@ __global__ void __launch_bounds__(NT) k_prolong(int nc, const T* __restrict__ uc
         const T d = orient(i, j, nc) == 0 ? p00 + P(i + 1, j + 1) : P(i + 1, j) + P(i, j + 1);
         p[(size_t)(2 * j + 1) * ldpf + 2 * i + 1] += T(0.5) * d;
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_prolong(int nc, const T* __restrict__ uc, const T* __restrict__ pc,
+                                                T* __restrict__ u, T* __restrict__ p) {
+    pdl_enter();
+    const int n = nc;
+    CELL_INDEX
+    if (!active) return;
+    prolong_cell<true>(i, j, nc, uc, pc, u, p);
 }
 
 template <typename T>
@@ -701,6 +721,8 @@ void launch_add_f32(cudaStream_t s, size_t count, const float* e, double* x) {
     const int blocks = (int)((count + 255) / 256 < 152 * 16 ? (count + 255) / 256 : 152 * 16);
     k_add_f32<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(count, e, x);
 }
+
+#include "coarse_cycle.cuh"
 
 // ------------------------------------------------------------------------------------------
 #define INST(T)                                                                                         \

@@ -103,6 +103,24 @@ void launch_rhs_norm(cudaStream_t s, int n, const double* f, const double* g, do
 // constant pressure (the kernel of the saddle-point matrix)
 void launch_make_consistent(cudaStream_t s, int n, double* g, double* partial, double* scalar);
 
+// The float32 V-cycle of levels 0..a.top (top <= 4) in one CTA with shared-memory arrays
+// (coarse_cycle.cuh); the kernel's shared-memory limit is raised by prepare_coarse_cycle().
+constexpr int kCoarseCycleTop = 4;
+struct CoarseCycleArgs {
+    OpCoef<float> c[kCoarseCycleTop];     // levels 1..top at index l - 1
+    const float* sinv[kCoarseCycleTop];   // Shat^{-1} of levels 1..top (global)
+    const double* inv;                    // level-0 bordered inverse (27 x 27, global)
+    float* u;                             // iterate of level `top` (global; read at start, written at end)
+    float* p;
+    const float* f;                       // right-hand side of level `top` (global)
+    const float* g;
+    float tau, sigma;
+    int nu_pre, nu_post;
+    int top;                              // 1 <= top <= kCoarseCycleTop
+};
+cudaError_t prepare_coarse_cycle();
+void launch_coarse_cycle(cudaStream_t s, const CoarseCycleArgs& a);
+
 // batched solver: device-side WHILE condition and result store (batch.cu)
 void launch_batch_check(cudaStream_t s, cudaGraphConditionalHandle hnd, const double* scal, double tol2,
                         int max_cycles, int* count);
