@@ -4,9 +4,11 @@
 Workload (one "step"): the robustness sweep at h = 1/512 (level k = 8, 2,356,227 unknowns):
 six solves, beta in {0, 1, 1e2, 1e4, 1e6, 1e8}, f and g with i.i.d. uniform[-1, 1] nodal values
 (seed 1 + rank, g shifted to zero mean), each from zero to 1e-8 relative residual (float64) with
-V(3,3) Uzawa cycles (tau = sigma = 0.8).  The headline path is float32 cycles inside float64
-iterative refinement (--precision mixed, default); the plain float64 multigrid is timed on the same
-workload for comparison.
+V(3,3) Uzawa cycles (tau = sigma = 0.8).  The six solves are independent and run concurrently in
+one CUDA-graph launch (each with its own device-side loop); the same solves one after another
+through the single-solve API are reported beside it.  The headline path is float32 cycles inside
+float64 iterative refinement (--precision mixed, default); the plain float64 multigrid is timed on
+the same workload for comparison.
 
 Metric: unknowns solved per second (DoF/s) = 6 x 2,356,227 x steps x ranks / time.
 Multi-GPU: every rank solves its own sweep (independent problems, no collective on the data path):
@@ -48,6 +50,11 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solver measurement")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--host-loop", action="store_true",
+                    help="kernel modes: drive refinement steps from the host, one cycle graph per step, so that a "
+                         "profiler lists every kernel (the device-side loop hides the loop body from it)")
+    ap.add_argument("--variant", type=int, default=None,
+                    help="kernel modes: force this float32 Uzawa step variant (0-6) on every level")
     return ap.parse_args()
 
 
@@ -65,6 +72,12 @@ def run_kernel(args):
     g = g - g.mean()
     prec = "mixed" if args.kernel in ("uzawa_f32", "mixed_solve", "ir_steps") else "fp64"
     S = Solver(k + 1, 1e4, precision=prec)
+    if args.variant is not None:
+        from paper_1502_04070_gb300.solver import set_step_variant
+        for l in range(2, k + 2):
+            set_step_variant(l, args.variant)
+    if args.host_loop:
+        S.set_timing(True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if args.kernel == "uzawa_f32":
         t = [torch.from_numpy(a).cuda().float().contiguous() for a in (u, p, f, g)]
@@ -289,26 +302,32 @@ def run_ours(args, rank, world, local_rank):
     if args.precision == "mixed":
         S0.autotune()     # float32 step variant per level (process-wide), before any graph capture
     from paper_1502_04070_gb300 import _binding as _B
+    from paper_1502_04070_gb300.solver import BatchSolver
     variants = {"k=%d" % (l - 1): _B.load().stokes_step_variant(l) for l in range(2, levels + 1)}
     f, g = S0.load_vectors(fn, gn, project_g=True)
-    us = {b: S0.zeros_u() for b in BETAS}
-    ps = {b: S0.zeros_p() for b in BETAS}
+    nb = len(BETAS)
     flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")   # > 129 MB L2
 
-    reports = {}
+    # The six solves of the sweep are independent: one graph launch runs them concurrently, each
+    # instance with its own device-side loop to 1e-8 (small levels of one instance overlap the
+    # others' work).
+    sweep = BatchSolver([levels] * nb, BETAS, precision=args.precision, autotune=args.precision == "mixed")
+    us = [torch.zeros(sweep.shapes(0)[0], dtype=torch.float64, device="cuda") for _ in BETAS]
+    ps = [torch.zeros(sweep.shapes(0)[1], dtype=torch.float64, device="cuda") for _ in BETAS]
+    result = {}
 
-    def step(sv):
-        for b in BETAS:
-            us[b].zero_()
-            ps[b].zero_()
-            _, _, rep = sv[b].solve(f, g, tol=TOL, max_cycles=100, u=us[b], p=ps[b])
-            if not rep.converged:
-                raise RuntimeError("beta=%g did not converge: %r" % (b, rep))
-            reports[b] = rep
+    def sweep_step(B, fs, gs):
+        for u, p in zip(us, ps):
+            u.zero_()
+            p.zero_()
+        _, _, cyc, rel, st = B.solve(fs, gs, tol=TOL, max_cycles=100, us=us, ps=ps)
+        if st != 0 or max(rel) > TOL:
+            raise RuntimeError("sweep did not converge: status %d, residuals %r" % (st, rel))
+        result["cycles"], result["rel"] = cyc, rel
 
     for _ in range(args.warmup):
-        step(solvers)
-    launches0 = sum(s.kernel_launches() for s in solvers.values())
+        sweep_step(sweep, [f] * nb, [g] * nb)
+    launches0 = sweep.kernel_launches()
     clocks = ClockSampler(local_rank)
     clocks.start()
     barrier()
@@ -317,17 +336,44 @@ def run_ours(args, rank, world, local_rank):
     e0.record()
     for _ in range(args.steps):
         flush.fill_(1.0)
-        step(solvers)
+        sweep_step(sweep, [f] * nb, [g] * nb)
     e1.record()
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
     ms = max_over_ranks(e0.elapsed_time(e1))
-    launches = sum(s.kernel_launches() for s in solvers.values()) - launches0
+    launches = sweep.kernel_launches() - launches0
     n_dof = dofs(K_LEVEL)
-    value = len(BETAS) * n_dof * args.steps * world / (ms / 1000.0)
-    cycles = {str(b): reports[b].cycles for b in BETAS}
-    rates = {str(b): round(reports[b].mean_rate, 4) for b in BETAS}
+    value = nb * n_dof * args.steps * world / (ms / 1000.0)
+    cycles = {str(b): c for b, c in zip(BETAS, result["cycles"])}
+    # mean rate per cycle of the relative residual (the start x = 0 has residual ||F||)
+    rates = {str(b): round(r ** (1.0 / c), 4) for b, c, r in zip(BETAS, result["cycles"], result["rel"])}
+    final_rel = {str(b): r for b, r in zip(BETAS, result["rel"])}
+
+    # the same six solves one after another through the single-solve API (one solve in flight)
+    reports = {}
+
+    def step(sv):
+        for b in BETAS:
+            u = S0.zeros_u()
+            p = S0.zeros_p()
+            _, _, rep = sv[b].solve(f, g, tol=TOL, max_cycles=100, u=u, p=p)
+            if not rep.converged:
+                raise RuntimeError("beta=%g did not converge: %r" % (b, rep))
+            reports[b] = rep
+
+    step(solvers)
+    seq_steps = max(1, min(args.steps, 2))
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(seq_steps):
+        flush.fill_(1.0)
+        step(solvers)
+    e1.record()
+    torch.cuda.synchronize()
+    seq_ms = max_over_ranks(e0.elapsed_time(e1)) / seq_steps
+    sequential = {"value": nb * n_dof * world / (seq_ms / 1000.0), "unit": "DoF/s", "ms_per_step": seq_ms,
+                  "steps": seq_steps, "cycles": {str(b): reports[b].cycles for b in BETAS}}
 
     # kernel timings: a second timed pass over the same workload with CUDA event records inside
     # the captured cycle (on the library's stream).  Event records cannot sit inside the device-side
@@ -387,42 +433,51 @@ def run_ours(args, rank, world, local_rank):
                         "pass of %d steps of the same workload with event records in the captured cycle" % kern_steps}
 
     # ---------------------------------------------------------------- end to end (host buffers)
+    # per step: six copies of the nodal data host -> device, load vectors, the batched solve, six
+    # solutions device -> host
     e2e_steps = max(1, min(args.steps, 3))
-    h2d = (fn_h.numel() + gn_h.numel()) * 8 * len(BETAS)
-    d2h = (us[0.0].numel() + ps[0.0].numel()) * 8 * len(BETAS)
-    u_host = {b: torch.empty(us[b].shape, dtype=torch.float64).pin_memory() for b in BETAS}
-    p_host = {b: torch.empty(ps[b].shape, dtype=torch.float64).pin_memory() for b in BETAS}
+    h2d = (fn_h.numel() + gn_h.numel()) * 8 * nb
+    d2h = (us[0].numel() + ps[0].numel()) * 8 * nb
+    u_host = [torch.empty(us[0].shape, dtype=torch.float64).pin_memory() for _ in BETAS]
+    p_host = [torch.empty(ps[0].shape, dtype=torch.float64).pin_memory() for _ in BETAS]
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        for b in BETAS:
+        fs, gs = [], []
+        for _b in BETAS:
             fd = fn_h.to("cuda", non_blocking=True)
             gd = gn_h.to("cuda", non_blocking=True)
-            ff, gg = solvers[b].load_vectors(fd, gd, project_g=True)
-            u, p, rep = solvers[b].solve(ff, gg, tol=TOL, max_cycles=100)
-            u_host[b].copy_(u)
-            p_host[b].copy_(p)
+            ff, gg = S0.load_vectors(fd, gd, project_g=True)
+            fs.append(ff)
+            gs.append(gg)
+        sweep_step(sweep, fs, gs)
+        for i in range(nb):
+            u_host[i].copy_(us[i])
+            p_host[i].copy_(ps[i])
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0)
-    e2e_value = len(BETAS) * n_dof * e2e_steps * world / e2e_s
+    e2e_value = nb * n_dof * e2e_steps * world / e2e_s
 
     # ---------------------------------------------------------------- plain float64 comparison
     fp64 = None
     if args.precision == "mixed" and args.fp64_steps > 0:
-        s64 = make("fp64")
-        step(s64)   # warm-up (graph capture)
+        sw64 = BatchSolver([levels] * nb, BETAS, precision="fp64", autotune=False)
+        sweep_step(sw64, [f] * nb, [g] * nb)   # warm-up (graph capture)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        e0.record()
         for _ in range(args.fp64_steps):
-            step(s64)
+            flush.fill_(1.0)
+            sweep_step(sw64, [f] * nb, [g] * nb)
+        e1.record()
         torch.cuda.synchronize()
-        dt = max_over_ranks(time.perf_counter() - t0)
-        v64 = len(BETAS) * n_dof * args.fp64_steps * world / dt
+        dt = max_over_ranks(e0.elapsed_time(e1)) / 1000.0
+        v64 = nb * n_dof * args.fp64_steps * world / dt
         fp64 = {"value": v64, "unit": "DoF/s", "ms_per_step": 1000 * dt / args.fp64_steps,
-                "cycles": {str(b): reports[b].cycles for b in BETAS}, "speedup_of_mixed": value / v64}
-        for s in s64.values():
-            s.close()
+                "cycles": {str(b): c for b, c in zip(BETAS, result["cycles"])},
+                "note": "the same six solves in one batched launch, float64 throughout",
+                "speedup_of_mixed": value / v64}
+        sw64.close()
 
     # ---------------------------------------------------------------- batched solves (one graph launch)
     batch = None
@@ -448,11 +503,14 @@ def run_ours(args, rank, world, local_rank):
                            "solves_per_step": len(BETAS), "solves_per_s": len(BETAS) * args.steps * world / (ms / 1000),
                            "l2": "256 MB buffer written between steps (inside the timed region)",
                            "cycles_per_beta": cycles, "mean_rate_per_beta": rates,
+                           "final_rel_residual_per_beta": final_rel,
+                           "execution": "the six solves in one CUDA-graph launch (one device-side loop each)",
                            "float32_step_variant_per_level": variants},
                 "roofline": roofline, "kernels": kernels, "clocks": clk,
                 "e2e": {"value": e2e_value, "unit": "DoF/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "steps": e2e_steps},
-                "gpu_launches": int(launches), "fp64_plain": fp64, "batch": batch, "cpu_baseline": cpu}
+                "gpu_launches": int(launches), "fp64_plain": fp64, "sequential_single_solves": sequential,
+                "batch": batch, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
 
 

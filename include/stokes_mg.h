@@ -183,6 +183,12 @@ stokes_status stokes_autotune(stokes_handle* h);
 /* The step variant currently used for a float32 level with `levels` levels (N = 2^levels), -1 if
  * out of range: 0-3 fused tiles 32x16, 32x8, 64x8, 16x16; 4-6 three-kernel step, blocks 32x8, 16x8, 8x8. */
 int stokes_step_variant(int levels);
+/* Sets the step variant (0-6, as above) for float32 levels with `levels` levels (N = 2^levels),
+ * process-wide, and marks that size as tuned (stokes_autotune keeps it).  Takes effect for direct
+ * smoothing calls (stokes_smooth_f32) and for cycle graphs captured afterwards; graphs a handle has
+ * already captured keep their variant.  Not thread-safe against concurrent setup or capture.
+ * Returns STOKES_ERR_BAD_ARG for levels outside 2..31 or an unknown variant. */
+stokes_status stokes_set_step_variant(int levels, int variant);
 
 /* ---- batches: many independent solves (right-hand sides, beta values, mesh levels) in one launch.
  * stokes_batch_setup builds `count` solvers; instance i has levels[i] levels and beta betas[i], the

@@ -71,6 +71,7 @@ SIGNATURES = {
     "stokes_batch_kernel_launches": (ctypes.c_ulonglong, [_P]),
     "stokes_autotune": (_I, [_P]),
     "stokes_step_variant": (_I, [_I]),
+    "stokes_set_step_variant": (_I, [_I, _I]),
     "stokes_set_timing": (_I, [_P, _I]),
     "stokes_get_timing": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D),
                                ctypes.POINTER(ctypes.c_longlong)]),

@@ -877,6 +877,11 @@ static stokes_status autotune_levels(stokes_handle* h, cudaStream_t st) {
 
 int stokes_step_variant(int levels) { return levels >= 2 && levels <= 31 ? uzawa_choice(1 << levels) : -1; }
 
+stokes_status stokes_set_step_variant(int levels, int variant) {
+    if (levels < 2 || levels > 31 || !set_uzawa_choice(1 << levels, variant)) return STOKES_ERR_BAD_ARG;
+    return STOKES_OK;
+}
+
 struct stokes_batch_t {
     int count = 0;
     cudaStream_t st = nullptr;

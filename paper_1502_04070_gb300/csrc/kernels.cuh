@@ -51,6 +51,7 @@ cudaError_t launch_uzawa_fused(cudaStream_t s, int n, const OpCoef<T>& c, T tau,
 // on (u, p) with (u_out, p_out) as scratch (returns false).
 bool uzawa_tuned(int n);
 int uzawa_choice(int n);
+bool set_uzawa_choice(int n, int v);   // false if v is not a step variant
 bool launch_uzawa_auto(cudaStream_t s, int n, const OpCoef<float>& c, float tau, float sigma, float* u, float* p,
                        const float* f, const float* g, const float* sinv, float* u_out, float* p_out);
 // Picks the fastest float32 tile shape for level size n by timing each on these buffers (their

@@ -285,6 +285,12 @@ cudaError_t autotune_uzawa_fused(cudaStream_t s, int n, const OpCoef<float>& c, 
 
 bool uzawa_tuned(int n) { return g_tuned[level_of(n)]; }
 int uzawa_choice(int n) { return g_tile_choice[level_of(n)]; }
+bool set_uzawa_choice(int n, int v) {
+    if (v < 0 || v >= kStepVariants) return false;
+    g_tile_choice[level_of(n)] = v;
+    g_tuned[level_of(n)] = true;
+    return true;
+}
 
 bool launch_uzawa_auto(cudaStream_t s, int n, const OpCoef<float>& c, float tau, float sigma, float* u, float* p,
                        const float* f, const float* g, const float* sinv, float* u_out, float* p_out) {

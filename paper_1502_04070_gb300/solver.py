@@ -216,6 +216,18 @@ class Solver:
         return out.value
 
 
+def step_variant(levels):
+    """Float32 Uzawa step variant used for levels with N = 2^levels (0-3 fused tiles 32x16, 32x8,
+    64x8, 16x16; 4-6 three-kernel step with blocks 32x8, 16x8, 8x8)."""
+    return int(B.load().stokes_step_variant(int(levels)))
+
+
+def set_step_variant(levels, variant):
+    """Forces the float32 Uzawa step variant for levels with N = 2^levels (process-wide; graphs
+    captured earlier keep theirs)."""
+    B.check(B.load().stokes_set_step_variant(int(levels), int(variant)), "stokes_set_step_variant")
+
+
 class BatchSolver:
     """Many independent solves (levels, beta per instance) run to convergence in one CUDA-graph
     launch (stokes_batch_setup / stokes_batch_solve)."""

@@ -56,6 +56,22 @@ def test_setup_rejects_bad_arguments_without_touching_the_gpu():
     assert lib.stokes_setup(None, None, ctypes.byref(h)) == _binding.ERR_BAD_ARG
 
 
+def test_step_variant_selection_without_gpu():
+    """The variant table is host state: out-of-range sizes and variants are rejected, a valid
+    choice reads back."""
+    from paper_1502_04070_gb300 import _binding
+    lib = _binding.load()
+    assert lib.stokes_set_step_variant(1, 0) == _binding.ERR_BAD_ARG
+    assert lib.stokes_set_step_variant(32, 0) == _binding.ERR_BAD_ARG
+    assert lib.stokes_set_step_variant(5, 7) == _binding.ERR_BAD_ARG
+    assert lib.stokes_set_step_variant(5, -1) == _binding.ERR_BAD_ARG
+    assert lib.stokes_step_variant(1) == -1
+    old = lib.stokes_step_variant(5)
+    assert lib.stokes_set_step_variant(5, 6) == _binding.OK
+    assert lib.stokes_step_variant(5) == 6
+    assert lib.stokes_set_step_variant(5, old) == _binding.OK
+
+
 def test_product_path_fails_loudly_without_library(tmp_path):
     from paper_1502_04070_gb300 import _binding
     saved = _binding._lib

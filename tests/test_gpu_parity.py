@@ -203,6 +203,36 @@ def test_smoother_float32_fused(discs, Solver, k, beta, nu):
     assert rel_err(got, ref) < 2e-5
 
 
+@pytest.mark.parametrize("k", [3, 5, 6])
+@pytest.mark.parametrize("variant", range(7))
+def test_smoother_float32_every_variant(discs, Solver, k, variant):
+    """Every float32 step variant the autotuner may choose (four fused tile shapes, the three-kernel
+    step with three block shapes) gives the oracle's three Uzawa steps at a size whose cells do not
+    fill the last tile or block (N + 1 = 2^(k+1) + 1 per side).  Bound as above (2e-5)."""
+    from paper_1502_04070_gb300.solver import set_step_variant, step_variant
+    beta = 1e2
+    H = mg.Hierarchy(k + 1, beta, discs[:k + 1])
+    d = H.discs[-1]
+    u, p, f, g = _state(k, 170 + k)
+    x = d.to_vec(u, p)
+    F = d.to_vec(f, g)
+    for _ in range(3):
+        x = H.uzawa_step(H.finest, x, F, mg.Params())
+    S = Solver(k + 1, beta, precision="mixed")
+    t = lambda a: dev(a).float().contiguous()
+    tu, tp = t(u), t(p)
+    old = step_variant(k + 1)
+    set_step_variant(k + 1, variant)
+    try:
+        S.smooth_f32(tu, tp, t(f), t(g), 3)
+    finally:
+        set_step_variant(k + 1, old)
+    uo, po = d.from_vec(x)
+    got = np.concatenate([host(tu.double()).ravel(), host(tp.double()).ravel()])
+    ref = np.concatenate([uo.ravel(), po.ravel()])
+    assert rel_err(got, ref) < 2e-5
+
+
 @pytest.mark.parametrize("k", [3, 5])
 @pytest.mark.parametrize("nu_pre,nu_post,gamma", [(3, 3, 2), (4, 3, 2), (3, 2, 1)])
 def test_mixed_cycle_variants(discs, Solver, k, nu_pre, nu_post, gamma):
