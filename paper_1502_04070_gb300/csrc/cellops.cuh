@@ -79,6 +79,29 @@ struct GView {
 template <typename T>
 __device__ __forceinline__ GView<T> gview(const T* p, int ld) { return GView<T>{p, ld}; }
 
+// The same reads without any test: only for cells whose 5 x 5 lattice window and 3 x 3 vertex
+// window lie inside the arrays (block_interior).  Declared zero-filled, so the row code neither
+// tests the range nor masks the Dirichlet ring; with margin 2 no window reaches the ring at all.
+template <typename T>
+struct GViewU {
+    static constexpr bool zero_filled = true;
+    const T* p;
+    int ld;
+    __device__ __forceinline__ T operator()(int X, int Y) const { return __ldg(p + (Y * ld + X)); }
+    __device__ __forceinline__ T at(int si, int sj, int a, int b) const {
+        return __ldg(p + ((2 * sj + b) * ld + 2 * si + a));
+    }
+};
+template <typename T>
+__device__ __forceinline__ GViewU<T> gviewu(const T* p, int ld) { return GViewU<T>{p, ld}; }
+
+// True when every cell (i, j) of this block has m <= i, j <= n - m (block-uniform).  Margin 1: the
+// windows stay inside the arrays; margin 2: they also avoid the Dirichlet ring.
+__device__ __forceinline__ bool block_interior(int n, int m) {
+    const int i0 = blockIdx.x * blockDim.x, j0 = blockIdx.y * blockDim.y;
+    return i0 >= m && j0 >= m && i0 + (int)blockDim.x - 1 <= n - m && j0 + (int)blockDim.y - 1 <= n - m;
+}
+
 // Shared-memory lattice tile split by the parity of X: plane (X - 2 xh0) & 1 holds the points of
 // that parity, so a warp reading one local node of 32 consecutive squares touches 32 consecutive
 // words.  WH words per row, PL words per plane (padded so the two planes fall on different banks).

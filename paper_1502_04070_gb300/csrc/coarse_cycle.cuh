@@ -20,6 +20,64 @@ struct PView {
     __device__ __forceinline__ T at(int si, int sj, int a, int b) const { return p[(2 * sj + b) * ld + 2 * si + a]; }
 };
 
+// The same arrays read without tests, for cells whose windows lie inside (see cc_cell).
+template <typename T>
+struct PViewU {
+    static constexpr bool zero_filled = true;
+    const T* p;
+    int ld;
+    __device__ __forceinline__ T operator()(int X, int Y) const { return p[Y * ld + X]; }
+    __device__ __forceinline__ T at(int si, int sj, int a, int b) const { return p[(2 * sj + b) * ld + 2 * si + a]; }
+};
+
+// Work item q of a level with n cells per side -> cell (i, j) and its code path, ordered so that
+// a warp mostly stays on one path: first the cells with 2 <= i, j <= n - 2 off the mid-lines,
+// quadrant by quadrant (SW, NE: orientation 0, class 0; SE, NW: orientation 1, class 1), whose
+// windows lie inside the lattice; then (class 2) the rows 0, 1, n/2, n - 1, n in full and the
+// columns 0, 1, n/2, n - 1, n of the other rows.  Covers every cell once for n >= 4.
+__device__ __forceinline__ void cc_cell(int q, int n, int& i, int& j, int& cls) {
+    const int h = n >> 1, m = h - 2, nin = m * m;
+    if (q < 4 * nin) {
+        const int quad = q / nin, r = q - quad * nin;
+        const int di = r % m, dj = r / m;
+        i = (quad == 0 || quad == 3) ? 2 + di : h + 1 + di;
+        j = (quad == 0 || quad == 2) ? 2 + dj : h + 1 + dj;
+        cls = quad < 2 ? 0 : 1;
+        return;
+    }
+    int r = q - 4 * nin;
+    auto sel = [&](int t) { return t == 0 ? 0 : t == 1 ? 1 : t == 2 ? h : t == 3 ? n - 1 : n; };
+    if (r < 5 * (n + 1)) {
+        j = sel(r / (n + 1));
+        i = r % (n + 1);
+    } else {
+        r -= 5 * (n + 1);
+        const int row = r / 5;
+        i = sel(r % 5);
+        j = row < m ? 2 + row : h + 1 + (row - m);
+    }
+    cls = 2;
+}
+
+// operator rows of work item q on a shared-memory level (velocity arrays ux, uy, vertex array vp)
+template <bool DA, bool DBT, bool DB, bool DD>
+__device__ __forceinline__ void cc_apply(int q, int n, const OpCoef<float>& c, const float* ux, const float* uy,
+                                         const float* vp, int& i, int& j, Acc<float>& a) {
+    int cls;
+    cc_cell(q, n, i, j, cls);
+    const int ld = 2 * n + 1;
+    if (cls == 0) {
+        cell_apply_merged<DA, DBT, DB, DD, false, 0>(i, j, n, c, PViewU<float>{ux, ld}, PViewU<float>{uy, ld},
+                                                     PViewU<float>{vp, n + 1}, a);
+    } else if (cls == 1) {
+        cell_apply_merged<DA, DBT, DB, DD, false, 1>(i, j, n, c, PViewU<float>{ux, ld}, PViewU<float>{uy, ld},
+                                                     PViewU<float>{vp, n + 1}, a);
+    } else {
+        cell_apply_auto<DA, DBT, DB, DD, false>(i, j, n, c, PView<float>{ux, ld}, PView<float>{uy, ld},
+                                                PView<float>{vp, n + 1}, a);
+    }
+}
+
 __host__ __device__ constexpr int cc_n2(int l) { return ((4 << l) + 1) * ((4 << l) + 1); }
 __host__ __device__ constexpr int cc_n1(int l) { return ((2 << l) + 1) * ((2 << l) + 1); }
 // floats of one level: u, f, tu (2 n2 each), p, g, tp, sinv (n1 each)
@@ -53,11 +111,10 @@ __device__ __forceinline__ CCLevel cc_level(float* base, int l) {
 // one Uzawa step (Sec. 4) on a shared-memory level: u^{m-1/2} -> tu, dp -> tp, then u
 __device__ void cc_smooth(const CCLevel& L, const OpCoef<float>& c, float tau, float sigma) {
     const int n = L.n, ld = 2 * n + 1, n2 = ld * ld, cells = (n + 1) * (n + 1);
-    const PView<float> vux{L.u, ld}, vuy{L.u + n2, ld}, vp{L.p, n + 1};
     for (int q = threadIdx.x; q < cells; q += blockDim.x) {
-        const int i = q % (n + 1), j = q / (n + 1);
+        int i, j;
         Acc<float> a;
-        cell_apply_auto<true, true, false, true, false>(i, j, n, c, vux, vuy, vp, a);
+        cc_apply<true, true, false, true>(q, n, c, L.u, L.u + n2, L.p, i, j, a);
         const CellNodes cn = cell_nodes(i, j, n);
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
@@ -71,21 +128,20 @@ __device__ void cc_smooth(const CCLevel& L, const OpCoef<float>& c, float tau, f
         }
     }
     __syncthreads();
-    const PView<float> vhx{L.tu, ld}, vhy{L.tu + n2, ld};
     for (int q = threadIdx.x; q < cells; q += blockDim.x) {
-        const int i = q % (n + 1), j = q / (n + 1);
+        int i, j;
         Acc<float> a;
-        cell_apply_auto<false, false, true, false, false>(i, j, n, c, vhx, vhy, vp, a);
-        const float d = sigma * L.sv[q] * (a.bu - L.g[q]);
-        L.p[q] += d;
-        L.tp[q] = d;
+        cc_apply<false, false, true, false>(q, n, c, L.tu, L.tu + n2, L.p, i, j, a);
+        const int v = j * (n + 1) + i;
+        const float d = sigma * L.sv[v] * (a.bu - L.g[v]);
+        L.p[v] += d;
+        L.tp[v] = d;
     }
     __syncthreads();
-    const PView<float> vd{L.tp, n + 1};
     for (int q = threadIdx.x; q < cells; q += blockDim.x) {
-        const int i = q % (n + 1), j = q / (n + 1);
+        int i, j;
         Acc<float> a;
-        cell_apply_auto<false, true, false, true, false>(i, j, n, c, vhx, vhy, vd, a);
+        cc_apply<false, true, false, true>(q, n, c, L.tu, L.tu + n2, L.tp, i, j, a);
         const CellNodes cn = cell_nodes(i, j, n);
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
@@ -104,11 +160,10 @@ __device__ void cc_smooth(const CCLevel& L, const OpCoef<float>& c, float tau, f
 // r = F - A x on a shared-memory level into (tu, tp)
 __device__ void cc_residual(const CCLevel& L, const OpCoef<float>& c) {
     const int n = L.n, ld = 2 * n + 1, n2 = ld * ld, cells = (n + 1) * (n + 1);
-    const PView<float> vux{L.u, ld}, vuy{L.u + n2, ld}, vp{L.p, n + 1};
     for (int q = threadIdx.x; q < cells; q += blockDim.x) {
-        const int i = q % (n + 1), j = q / (n + 1);
+        int i, j;
         Acc<float> a;
-        cell_apply_auto<true, true, true, false, false>(i, j, n, c, vux, vuy, vp, a);
+        cc_apply<true, true, true, false>(q, n, c, L.u, L.u + n2, L.p, i, j, a);
         const CellNodes cn = cell_nodes(i, j, n);
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
@@ -120,7 +175,7 @@ __device__ void cc_residual(const CCLevel& L, const OpCoef<float>& c) {
             L.tu[k] = unk ? L.f[k] - a.au[0][s] - a.bt[0][s] : 0.f;
             L.tu[n2 + k] = unk ? L.f[n2 + k] - a.au[1][s] - a.bt[1][s] : 0.f;
         }
-        L.tp[q] = L.g[q] - a.bu;
+        L.tp[j * (n + 1) + i] = L.g[j * (n + 1) + i] - a.bu;
     }
     __syncthreads();
 }

@@ -43,7 +43,12 @@ __global__ void __launch_bounds__(NT) k_residual(int n, const __grid_constant__ 
     double ss = 0.0;
     if (active) {
         Acc<T> a;
-        cell_apply_auto<true, true, true, false, true>(i, j, n, c, gview(u, 2 * n + 1), gview(u + n2, 2 * n + 1), gview(p, n + 1), a);
+        if (block_interior(n, 2))
+            cell_apply_auto<true, true, true, false, false>(i, j, n, c, gviewu(u, 2 * n + 1), gviewu(u + n2, 2 * n + 1),
+                                                            gviewu(p, n + 1), a);
+        else
+            cell_apply_auto<true, true, true, false, true>(i, j, n, c, gview(u, 2 * n + 1), gview(u + n2, 2 * n + 1),
+                                                           gview(p, n + 1), a);
         const CellNodes cn = cell_nodes(i, j, n);
         const int ld = 2 * n + 1;
 #pragma unroll
@@ -85,7 +90,12 @@ __global__ void __launch_bounds__(NT) k_uzawa_u(int n, const __grid_constant__ O
     if (!active) return;
     const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
     Acc<T> a;
-    cell_apply_auto<true, true, false, true, true>(i, j, n, c, gview(u, 2 * n + 1), gview(u + n2, 2 * n + 1), gview(p, n + 1), a);
+    if (block_interior(n, 2))
+        cell_apply_auto<true, true, false, true, false>(i, j, n, c, gviewu(u, 2 * n + 1), gviewu(u + n2, 2 * n + 1),
+                                                        gviewu(p, n + 1), a);
+    else
+        cell_apply_auto<true, true, false, true, true>(i, j, n, c, gview(u, 2 * n + 1), gview(u + n2, 2 * n + 1),
+                                                       gview(p, n + 1), a);
     const CellNodes cn = cell_nodes(i, j, n);
     const int ld = 2 * n + 1;
 #pragma unroll
@@ -113,7 +123,12 @@ __global__ void __launch_bounds__(NT) k_uzawa_p(int n, const __grid_constant__ O
     if (!active) return;
     const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
     Acc<T> a;
-    cell_apply_auto<false, false, true, false, false>(i, j, n, c, gview(uh, 2 * n + 1), gview(uh + n2, 2 * n + 1), gview((const T*)nullptr, n + 1), a);
+    if (block_interior(n, 1))
+        cell_apply_auto<false, false, true, false, false>(i, j, n, c, gviewu(uh, 2 * n + 1), gviewu(uh + n2, 2 * n + 1),
+                                                          gviewu((const T*)nullptr, n + 1), a);
+    else
+        cell_apply_auto<false, false, true, false, false>(i, j, n, c, gview(uh, 2 * n + 1), gview(uh + n2, 2 * n + 1),
+                                                          gview((const T*)nullptr, n + 1), a);
     const size_t vi = (size_t)j * (n + 1) + i;
     // p^{m} = p^{m-1} - sigma Shat^{-1} (g - B u^{m-1/2})
     const T d = sigma * sinv[vi] * (a.bu - g[vi]);
@@ -130,7 +145,12 @@ __global__ void __launch_bounds__(NT) k_uzawa_u2(int n, const __grid_constant__ 
     if (!active) return;
     const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
     Acc<T> a;
-    cell_apply_auto<false, true, false, true, false>(i, j, n, c, gview((const T*)nullptr, 2 * n + 1), gview((const T*)nullptr, 2 * n + 1), gview(dp, n + 1), a);
+    if (block_interior(n, 1))
+        cell_apply_auto<false, true, false, true, false>(i, j, n, c, gviewu((const T*)nullptr, 2 * n + 1),
+                                                         gviewu((const T*)nullptr, 2 * n + 1), gviewu(dp, n + 1), a);
+    else
+        cell_apply_auto<false, true, false, true, false>(i, j, n, c, gview((const T*)nullptr, 2 * n + 1),
+                                                         gview((const T*)nullptr, 2 * n + 1), gview(dp, n + 1), a);
     const CellNodes cn = cell_nodes(i, j, n);
     const int ld = 2 * n + 1;
 #pragma unroll
