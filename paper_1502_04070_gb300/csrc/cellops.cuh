@@ -202,18 +202,19 @@ __device__ __forceinline__ void cell_apply(int i, int j, int n, const T (&A)[2][
     }
 }
 
-// ---- merged node stencils for cells off the mid-lines (all four squares share orientation O).
-// Every structural-zero test below is a template argument, so it is decided at compile time.
-__host__ __device__ constexpr bool need_win(int O, bool DA, bool DB, int w) {
-    return (DA && (nz_MA(O, 0, w) || nz_MA(O, 1, w) || nz_MA(O, 2, w) || nz_MA(O, 3, w))) || (DB && nz_MB(O, w));
+// ---- merged node stencils: the rows of a cell's nodes summed over its four squares, per stencil
+// class (common.cuh).  Every structural-zero test below is a template argument (the class C), so
+// it is decided at compile time.
+__host__ __device__ constexpr bool need_win(int C, bool DA, bool DB, int w) {
+    return (DA && (nz_MA(C, 0, w) || nz_MA(C, 1, w) || nz_MA(C, 2, w) || nz_MA(C, 3, w))) || (DB && nz_MB(C, w));
 }
-__host__ __device__ constexpr bool need_vwin(int O, int v) {
-    return nz_MBT(O, 0, v) || nz_MBT(O, 1, v) || nz_MBT(O, 2, v) || nz_MBT(O, 3, v);
+__host__ __device__ constexpr bool need_vwin(int C, int v) {
+    return nz_MBT(C, 0, v) || nz_MBT(C, 1, v) || nz_MBT(C, 2, v) || nz_MBT(C, 3, v);
 }
 
-template <int O, bool DA, bool DB, bool MASK, int W, typename T, typename VU>
+template <int C, bool DA, bool DB, bool MASK, int W, typename T, typename VU>
 __device__ __forceinline__ void win_load1(int i, int j, int n, const VU& ux, const VU& uy, T (&wx)[25], T (&wy)[25]) {
-    if constexpr (need_win(O, DA, DB, W)) {
+    if constexpr (need_win(C, DA, DB, W)) {
         constexpr int dx = W % 5 - 2, dy = W / 5 - 2;
         if constexpr (VU::zero_filled && !MASK) {
             wx[W] = ux.at(i - 1, j - 1, dx + 2, dy + 2);
@@ -226,104 +227,110 @@ __device__ __forceinline__ void win_load1(int i, int j, int n, const VU& ux, con
         }
     }
 }
-template <int O, bool DA, bool DB, bool MASK, typename T, typename VU, int... W>
+template <int C, bool DA, bool DB, bool MASK, typename T, typename VU, int... W>
 __device__ __forceinline__ void win_load(int i, int j, int n, const VU& ux, const VU& uy, T (&wx)[25], T (&wy)[25],
                                          std::integer_sequence<int, W...>) {
-    (win_load1<O, DA, DB, MASK, W>(i, j, n, ux, uy, wx, wy), ...);
+    (win_load1<C, DA, DB, MASK, W>(i, j, n, ux, uy, wx, wy), ...);
 }
 
-template <int O, int V, typename T, typename VP>
+template <int C, int V, typename T, typename VP>
 __device__ __forceinline__ void vwin_load1(int i, int j, int n, const VP& p, T (&pw)[9]) {
-    if constexpr (need_vwin(O, V)) {
+    if constexpr (need_vwin(C, V)) {
         const int I = i + V % 3 - 1, J = j + V / 3 - 1;
         if constexpr (VP::zero_filled) pw[V] = p(I, J);
         else pw[V] = (I >= 0 && J >= 0 && I <= n && J <= n) ? p(I, J) : T(0);
     }
 }
-template <int O, typename T, typename VP, int... V>
+template <int C, typename T, typename VP, int... V>
 __device__ __forceinline__ void vwin_load(int i, int j, int n, const VP& p, T (&pw)[9], std::integer_sequence<int, V...>) {
-    (vwin_load1<O, V>(i, j, n, p, pw), ...);
+    (vwin_load1<C, V>(i, j, n, p, pw), ...);
 }
 
-template <int O, int S, int K, typename T>
+template <int C, int S, int K, typename T>
 __device__ __forceinline__ void ma_term(const OpCoef<T>& c, const T (&w)[25], T& s) {
-    if constexpr (nz_MA(O, S, K)) s = fma(c.MA[O][S][K], w[K], s);
+    if constexpr (nz_MA(C, S, K)) s = fma(c.MA[C][S][K], w[K], s);
 }
-template <int O, int S, typename T, int... K>
+template <int C, int S, typename T, int... K>
 __device__ __forceinline__ T ma_row_i(const OpCoef<T>& c, const T (&w)[25], std::integer_sequence<int, K...>) {
     T s = T(0);
-    (ma_term<O, S, K>(c, w, s), ...);
+    (ma_term<C, S, K>(c, w, s), ...);
     return s;
 }
-template <int O, int S, typename T>
+template <int C, int S, typename T>
 __device__ __forceinline__ T ma_row(const OpCoef<T>& c, const T (&w)[25]) {
-    return ma_row_i<O, S>(c, w, std::make_integer_sequence<int, 25>{});
+    return ma_row_i<C, S>(c, w, std::make_integer_sequence<int, 25>{});
 }
 
-template <int O, int S, int K, typename T>
-__device__ __forceinline__ void mbt_term(const T (&B)[2][4][9], const T (&pw)[9], T& s) {
-    if constexpr (nz_MBT(O, S, K)) s = fma(B[O][S][K], pw[K], s);
+template <int C, int S, int K, typename T>
+__device__ __forceinline__ void mbt_term(const T (&B)[kStencilClasses][4][9], const T (&pw)[9], T& s) {
+    if constexpr (nz_MBT(C, S, K)) s = fma(B[C][S][K], pw[K], s);
 }
-template <int O, int S, typename T, int... K>
-__device__ __forceinline__ T mbt_row_i(const T (&B)[2][4][9], const T (&pw)[9], std::integer_sequence<int, K...>) {
+template <int C, int S, typename T, int... K>
+__device__ __forceinline__ T mbt_row_i(const T (&B)[kStencilClasses][4][9], const T (&pw)[9],
+                                       std::integer_sequence<int, K...>) {
     T s = T(0);
-    (mbt_term<O, S, K>(B, pw, s), ...);
+    (mbt_term<C, S, K>(B, pw, s), ...);
     return s;
 }
-template <int O, int S, typename T>
-__device__ __forceinline__ T mbt_row(const T (&B)[2][4][9], const T (&pw)[9]) {
-    return mbt_row_i<O, S>(B, pw, std::make_integer_sequence<int, 9>{});
+template <int C, int S, typename T>
+__device__ __forceinline__ T mbt_row(const T (&B)[kStencilClasses][4][9], const T (&pw)[9]) {
+    return mbt_row_i<C, S>(B, pw, std::make_integer_sequence<int, 9>{});
 }
 
-template <int O, int K, typename T>
+template <int C, int K, typename T>
 __device__ __forceinline__ void mb_term(const OpCoef<T>& c, const T (&wx)[25], const T (&wy)[25], T& s) {
-    if constexpr (nz_MB(O, K)) s = fma(c.MBx[O][K], wx[K], fma(c.MBy[O][K], wy[K], s));
+    if constexpr (nz_MB(C, K)) s = fma(c.MBx[C][K], wx[K], fma(c.MBy[C][K], wy[K], s));
 }
-template <int O, typename T, int... K>
+template <int C, typename T, int... K>
 __device__ __forceinline__ T mb_row_i(const OpCoef<T>& c, const T (&wx)[25], const T (&wy)[25],
                                       std::integer_sequence<int, K...>) {
     T s = T(0);
-    (mb_term<O, K>(c, wx, wy, s), ...);
+    (mb_term<C, K>(c, wx, wy, s), ...);
     return s;
 }
 
-template <bool DA, bool DBT, bool DB, bool DD, bool MASK, int O, typename T, typename VU, typename VP>
+template <bool DA, bool DBT, bool DB, bool DD, bool MASK, int C, typename T, typename VU, typename VP>
 __device__ __forceinline__ void cell_apply_merged(int i, int j, int n, const OpCoef<T>& c, const VU& ux, const VU& uy,
                                                   const VP& p, Acc<T>& a) {
     T wx[25], wy[25], pw[9];
-    if constexpr (DA || DB) win_load<O, DA, DB, MASK>(i, j, n, ux, uy, wx, wy, std::make_integer_sequence<int, 25>{});
-    if constexpr (DBT) vwin_load<O>(i, j, n, p, pw, std::make_integer_sequence<int, 9>{});
+    if constexpr (DA || DB) win_load<C, DA, DB, MASK>(i, j, n, ux, uy, wx, wy, std::make_integer_sequence<int, 25>{});
+    if constexpr (DBT) vwin_load<C>(i, j, n, p, pw, std::make_integer_sequence<int, 9>{});
 #pragma unroll
     for (int s = 0; s < 4; ++s) a.au[0][s] = a.au[1][s] = a.bt[0][s] = a.bt[1][s] = a.idg[s] = T(0);
     a.bu = T(0);
     if constexpr (DA) {
-        a.au[0][0] = ma_row<O, 0>(c, wx); a.au[1][0] = ma_row<O, 0>(c, wy);
-        a.au[0][1] = ma_row<O, 1>(c, wx); a.au[1][1] = ma_row<O, 1>(c, wy);
-        a.au[0][2] = ma_row<O, 2>(c, wx); a.au[1][2] = ma_row<O, 2>(c, wy);
-        a.au[0][3] = ma_row<O, 3>(c, wx); a.au[1][3] = ma_row<O, 3>(c, wy);
+        a.au[0][0] = ma_row<C, 0>(c, wx); a.au[1][0] = ma_row<C, 0>(c, wy);
+        a.au[0][1] = ma_row<C, 1>(c, wx); a.au[1][1] = ma_row<C, 1>(c, wy);
+        a.au[0][2] = ma_row<C, 2>(c, wx); a.au[1][2] = ma_row<C, 2>(c, wy);
+        a.au[0][3] = ma_row<C, 3>(c, wx); a.au[1][3] = ma_row<C, 3>(c, wy);
     }
     if constexpr (DBT) {
-        a.bt[0][0] = mbt_row<O, 0>(c.MBTx, pw); a.bt[1][0] = mbt_row<O, 0>(c.MBTy, pw);
-        a.bt[0][1] = mbt_row<O, 1>(c.MBTx, pw); a.bt[1][1] = mbt_row<O, 1>(c.MBTy, pw);
-        a.bt[0][2] = mbt_row<O, 2>(c.MBTx, pw); a.bt[1][2] = mbt_row<O, 2>(c.MBTy, pw);
-        a.bt[0][3] = mbt_row<O, 3>(c.MBTx, pw); a.bt[1][3] = mbt_row<O, 3>(c.MBTy, pw);
+        a.bt[0][0] = mbt_row<C, 0>(c.MBTx, pw); a.bt[1][0] = mbt_row<C, 0>(c.MBTy, pw);
+        a.bt[0][1] = mbt_row<C, 1>(c.MBTx, pw); a.bt[1][1] = mbt_row<C, 1>(c.MBTy, pw);
+        a.bt[0][2] = mbt_row<C, 2>(c.MBTx, pw); a.bt[1][2] = mbt_row<C, 2>(c.MBTy, pw);
+        a.bt[0][3] = mbt_row<C, 3>(c.MBTx, pw); a.bt[1][3] = mbt_row<C, 3>(c.MBTy, pw);
     }
     if constexpr (DD) {
 #pragma unroll
-        for (int s = 0; s < 4; ++s) a.idg[s] = c.MIdg[O][s];
+        for (int s = 0; s < 4; ++s) a.idg[s] = c.MIdg[C][s];
     }
-    if constexpr (DB) a.bu = mb_row_i<O>(c, wx, wy, std::make_integer_sequence<int, 25>{});
+    if constexpr (DB) a.bu = mb_row_i<C>(c, wx, wy, std::make_integer_sequence<int, 25>{});
 }
 
-// Operator rows of cell (i, j): merged stencils off the mid-lines, the square-by-square gather on
-// them (where the four squares around a node do not all share one orientation).
+// Operator rows of cell (i, j) from the merged stencils of its class (branch uniform across a warp
+// except where the warp meets a mid-line).
 template <bool DA, bool DBT, bool DB, bool DD, bool MASK, typename T, typename VU, typename VP>
 __device__ __forceinline__ void cell_apply_auto(int i, int j, int n, const OpCoef<T>& c, const VU& ux, const VU& uy,
                                                 const VP& p, Acc<T>& a) {
-    const int h = n >> 1;
-    if (i == h || j == h) cell_apply<DA, DBT, DB, DD, MASK>(i, j, n, c.A, c, ux, uy, p, a);
-    else if (orient(i, j, n)) cell_apply_merged<DA, DBT, DB, DD, MASK, 1>(i, j, n, c, ux, uy, p, a);
-    else cell_apply_merged<DA, DBT, DB, DD, MASK, 0>(i, j, n, c, ux, uy, p, a);
+    switch (stencil_class(i, j, n)) {
+        case 0: cell_apply_merged<DA, DBT, DB, DD, MASK, 0>(i, j, n, c, ux, uy, p, a); break;
+        case 1: cell_apply_merged<DA, DBT, DB, DD, MASK, 1>(i, j, n, c, ux, uy, p, a); break;
+        case 2: cell_apply_merged<DA, DBT, DB, DD, MASK, 2>(i, j, n, c, ux, uy, p, a); break;
+        case 3: cell_apply_merged<DA, DBT, DB, DD, MASK, 3>(i, j, n, c, ux, uy, p, a); break;
+        case 4: cell_apply_merged<DA, DBT, DB, DD, MASK, 4>(i, j, n, c, ux, uy, p, a); break;
+        case 5: cell_apply_merged<DA, DBT, DB, DD, MASK, 5>(i, j, n, c, ux, uy, p, a); break;
+        default: cell_apply_merged<DA, DBT, DB, DD, MASK, 6>(i, j, n, c, ux, uy, p, a); break;
+    }
 }
 
 // lattice position and existence / unknown flags of slot s of cell (i, j)

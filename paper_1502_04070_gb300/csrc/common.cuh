@@ -24,21 +24,34 @@
 
 namespace smg {
 
+// Stencil classes of a cell by the orientations of its four squares (bit SQ of the pattern is the
+// orientation of square SQ, numbered as in sq_local below: 0 = (i, j), 1 = (i-1, j), 2 = (i, j-1),
+// 3 = (i-1, j-1)).  Classes 0 / 1: every cell off the two mid-lines (all four squares orientation
+// 0 / 1).  On the mid-line x = 1/2 (i = N/2): class 2 below the centre, 3 above; on y = 1/2
+// (j = N/2): class 4 left of the centre, 5 right; class 6 the centre cell.  Squares outside the
+// domain get a pattern bit too: every lattice value they touch is a Dirichlet zero or outside the
+// arrays (read as zero), so their terms vanish.
+constexpr int kStencilClasses = 7;
+__host__ __device__ constexpr unsigned stencil_pattern(int k) {
+    return k == 0 ? 0x0u : k == 1 ? 0xFu : k == 2 ? 0x5u : k == 3 ? 0xAu : k == 4 ? 0x3u : k == 5 ? 0xCu : 0x6u;
+}
+__host__ __device__ constexpr int sq_orient(int k, int SQ) { return (int)((stencil_pattern(k) >> SQ) & 1u); }
+
 template <typename T>
 struct OpCoef {            // local square matrices of one level
     T A[2][9][9];          // K + beta h^2 Mhat        (h-independent stiffness, mass ~ h^2)
     T Bx[2][4][9];         // (d phi_m / dx, psi_q)    (~ h)
     T By[2][4][9];
-    // The same operator as node stencils for cells whose four squares share orientation o (all
-    // cells off the two mid-lines): the rows of the four owned velocity nodes s (V, H, E, C) over the
-    // 5 x 5 lattice window of the cell (offsets dx, dy in -2..2 from (2i, 2j)), their B^T rows over
-    // the 3 x 3 vertex window, and the B row of the owned vertex.  Built by fill_merged().
-    T MA[2][4][25];        // [o][s][(dy+2)*5 + dx+2]
-    T MBTx[2][4][9];       // [o][s][(dj+1)*3 + di+1]
-    T MBTy[2][4][9];
-    T MBx[2][25];          // [o][(dy+2)*5 + dx+2]
-    T MBy[2][25];
-    T MIdg[2][4];          // 1 / diag A of the four owned nodes, [o][s]
+    // The same operator as node stencils, per stencil class k: the rows of the four owned velocity
+    // nodes s (V, H, E, C) over the 5 x 5 lattice window of the cell (offsets dx, dy in -2..2 from
+    // (2i, 2j)), their B^T rows over the 3 x 3 vertex window, and the B row of the owned vertex.
+    // Built by fill_merged().
+    T MA[kStencilClasses][4][25];    // [k][s][(dy+2)*5 + dx+2]
+    T MBTx[kStencilClasses][4][9];   // [k][s][(dj+1)*3 + di+1]
+    T MBTy[kStencilClasses][4][9];
+    T MBx[kStencilClasses][25];      // [k][(dy+2)*5 + dx+2]
+    T MBy[kStencilClasses][25];
+    T MIdg[kStencilClasses][4];      // 1 / diag A of the four owned nodes, [k][s]
 };
 
 template <typename T>
@@ -73,42 +86,40 @@ __host__ __device__ constexpr int sq_win(int SQ, int m) { return (m / 3 - 2 * (S
 // vertex offset (from (i, j)) of corner q of square SQ, as a 3 x 3 window index
 __host__ __device__ constexpr int sq_vwin(int SQ, int q) { return (q / 2 - (SQ >> 1) + 1) * 3 + (q % 2 - (SQ & 1) + 1); }
 
-// structural nonzeros of the merged stencils (compile-time)
-__host__ __device__ constexpr bool nz_MA(int o, int s, int w) {
+// structural nonzeros of the merged stencils of class k (compile-time)
+__host__ __device__ constexpr bool nz_MA(int k, int s, int w) {
     for (int SQ = 0; SQ < 4; ++SQ) {
         const int L = sq_local(SQ, s);
         if (L < 0) continue;
         for (int m = 0; m < 9; ++m)
-            if (sq_win(SQ, m) == w && couple(o, L, m)) return true;
+            if (sq_win(SQ, m) == w && couple(sq_orient(k, SQ), L, m)) return true;
     }
     return false;
 }
-__host__ __device__ constexpr bool nz_MBT(int o, int s, int v) {
+__host__ __device__ constexpr bool nz_MBT(int k, int s, int v) {
     for (int SQ = 0; SQ < 4; ++SQ) {
         const int L = sq_local(SQ, s);
         if (L < 0) continue;
         for (int q = 0; q < 4; ++q)
-            if (sq_vwin(SQ, q) == v && couple(o, corner_node(q), L)) return true;
+            if (sq_vwin(SQ, q) == v && couple(sq_orient(k, SQ), corner_node(q), L)) return true;
     }
     return false;
 }
-__host__ __device__ constexpr bool nz_MB(int o, int w) {
+__host__ __device__ constexpr bool nz_MB(int k, int w) {
     for (int SQ = 0; SQ < 4; ++SQ)
         for (int m = 0; m < 9; ++m)
-            if (sq_win(SQ, m) == w && couple(o, corner_node(SQ), m)) return true;
+            if (sq_win(SQ, m) == w && couple(sq_orient(k, SQ), corner_node(SQ), m)) return true;
     return false;
 }
 
 // host: merged stencils from the square-local matrices (sums over the squares that share a node)
 template <typename T>
 inline void fill_merged(OpCoef<T>& c) {
-    for (int o = 0; o < 2; ++o) {
+    for (int k = 0; k < kStencilClasses; ++k) {
         for (int s = 0; s < 4; ++s) {
-            for (int w = 0; w < 25; ++w) c.MA[o][s][w] = T(0);
-            for (int v = 0; v < 9; ++v) c.MBTx[o][s][v] = c.MBTy[o][s][v] = T(0);
             double ma[25] = {}, bx[9] = {}, by[9] = {};
             for (int SQ = 0; SQ < 4; ++SQ) {
-                const int L = sq_local(SQ, s);
+                const int L = sq_local(SQ, s), o = sq_orient(k, SQ);
                 if (L < 0) continue;
                 for (int m = 0; m < 9; ++m)
                     if (couple(o, L, m)) ma[sq_win(SQ, m)] += (double)c.A[o][L][m];
@@ -118,30 +129,41 @@ inline void fill_merged(OpCoef<T>& c) {
                         by[sq_vwin(SQ, q)] += (double)c.By[o][q][L];
                     }
             }
-            for (int w = 0; w < 25; ++w) c.MA[o][s][w] = (T)ma[w];
-            c.MIdg[o][s] = (T)(1.0 / ma[((s >> 1) + 2) * 5 + (s & 1) + 2]);
+            for (int w = 0; w < 25; ++w) c.MA[k][s][w] = (T)ma[w];
+            c.MIdg[k][s] = (T)(1.0 / ma[((s >> 1) + 2) * 5 + (s & 1) + 2]);
             for (int v = 0; v < 9; ++v) {
-                c.MBTx[o][s][v] = (T)bx[v];
-                c.MBTy[o][s][v] = (T)by[v];
+                c.MBTx[k][s][v] = (T)bx[v];
+                c.MBTy[k][s][v] = (T)by[v];
             }
         }
         double mx[25] = {}, my[25] = {};
-        for (int SQ = 0; SQ < 4; ++SQ)
+        for (int SQ = 0; SQ < 4; ++SQ) {
+            const int o = sq_orient(k, SQ);
             for (int m = 0; m < 9; ++m)
                 if (couple(o, corner_node(SQ), m)) {
                     mx[sq_win(SQ, m)] += (double)c.Bx[o][SQ][m];
                     my[sq_win(SQ, m)] += (double)c.By[o][SQ][m];
                 }
+        }
         for (int w = 0; w < 25; ++w) {
-            c.MBx[o][w] = (T)mx[w];
-            c.MBy[o][w] = (T)my[w];
+            c.MBx[k][w] = (T)mx[w];
+            c.MBy[k][w] = (T)my[w];
         }
     }
 }
 
-__device__ __forceinline__ int orient(int si, int sj, int n) {
+__host__ __device__ __forceinline__ int orient(int si, int sj, int n) {
     const int h = n >> 1;
     return (si < h) != (sj < h);
+}
+
+// stencil class (see stencil_pattern) of cell (i, j) of a level with N = n
+__host__ __device__ __forceinline__ int stencil_class(int i, int j, int n) {
+    const int h = n >> 1;
+    if (i != h && j != h) return orient(i, j, n);
+    if (i == h && j == h) return 6;
+    if (i == h) return j < h ? 2 : 3;
+    return i < h ? 4 : 5;
 }
 
 // row L of A (orientation O) times the 9 square values; zero couplings dropped at compile time

@@ -1,9 +1,10 @@
 // kernels.cu -- matrix-free kernels of the coupled multigrid cycle (Secs. 3-5).
 //
 // Every kernel runs one thread per cell (i, j) of a level, i, j in [0, N] (see common.cuh for the
-// owned nodes and the square-local matrices).  The operator rows are gathered from the 1-4 squares
-// around the cell, each square's orientation selecting a specialised code path (warp-uniform except
-// on the two mid-lines x = 1/2, y = 1/2), so that structurally-zero local entries cost nothing.
+// owned nodes and the square-local matrices).  The operator rows are the merged node stencils of
+// the cell's stencil class (the orientations of its four squares; warp-uniform except where a warp
+// meets one of the mid-lines x = 1/2, y = 1/2), with structurally-zero entries removed at compile
+// time.  Blocks whose cells all lie at least two cells inside the boundary read without any test.
 #include <cstdio>
 
 #include "cellops.cuh"

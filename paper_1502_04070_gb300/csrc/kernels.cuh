@@ -119,6 +119,9 @@ struct CoarseCycleArgs {
     int nu_pre, nu_post;
     int top;                              // 1 <= top <= kCoarseCycleTop
 };
+// kernel parameters are limited to 32,764 bytes
+static_assert(sizeof(CoarseCycleArgs) <= 32764, "coarse-cycle parameters exceed the launch limit");
+
 cudaError_t prepare_coarse_cycle();
 void launch_coarse_cycle(cudaStream_t s, const CoarseCycleArgs& a);
 
