@@ -59,6 +59,51 @@ __device__ __forceinline__ void cc_cell(int q, int n, int& i, int& j, int& cls) 
     cls = 2;
 }
 
+// Rows of a cell of any stencil class k, as rolled loops over the full 5 x 5 and 3 x 3 windows
+// with tested reads: little code for the few cells on the boundary ring and the mid-lines (the
+// whole cycle of this kernel runs on one SM, whose instruction cache it has to fit).
+template <bool DA, bool DBT, bool DB, bool DD>
+__device__ __noinline__ void cc_apply_rolled(int i, int j, int n, int k, const OpCoef<float>& c, const float* ux,
+                                             const float* uy, const float* vp, Acc<float>& a) {
+    const int ld = 2 * n + 1;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) a.au[0][s] = a.au[1][s] = a.bt[0][s] = a.bt[1][s] = a.idg[s] = 0.f;
+    a.bu = 0.f;
+    if constexpr (DA || DB) {
+#pragma unroll 1
+        for (int w = 0; w < 25; ++w) {
+            const int X = 2 * i + w % 5 - 2, Y = 2 * j + w / 5 - 2;
+            if (X < 0 || Y < 0 || X > 2 * n || Y > 2 * n) continue;
+            const float vx = ux[Y * ld + X], vy = uy[Y * ld + X];
+            if constexpr (DA) {
+#pragma unroll
+                for (int s = 0; s < 4; ++s) {
+                    a.au[0][s] = fmaf(c.MA[k][s][w], vx, a.au[0][s]);
+                    a.au[1][s] = fmaf(c.MA[k][s][w], vy, a.au[1][s]);
+                }
+            }
+            if constexpr (DB) a.bu = fmaf(c.MBx[k][w], vx, fmaf(c.MBy[k][w], vy, a.bu));
+        }
+    }
+    if constexpr (DBT) {
+#pragma unroll 1
+        for (int v = 0; v < 9; ++v) {
+            const int I = i + v % 3 - 1, J = j + v / 3 - 1;
+            if (I < 0 || J < 0 || I > n || J > n) continue;
+            const float pv = vp[J * (n + 1) + I];
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                a.bt[0][s] = fmaf(c.MBTx[k][s][v], pv, a.bt[0][s]);
+                a.bt[1][s] = fmaf(c.MBTy[k][s][v], pv, a.bt[1][s]);
+            }
+        }
+    }
+    if constexpr (DD) {
+#pragma unroll
+        for (int s = 0; s < 4; ++s) a.idg[s] = c.MIdg[k][s];
+    }
+}
+
 // operator rows of work item q on a shared-memory level (velocity arrays ux, uy, vertex array vp)
 template <bool DA, bool DBT, bool DB, bool DD>
 __device__ __forceinline__ void cc_apply(int q, int n, const OpCoef<float>& c, const float* ux, const float* uy,
@@ -73,8 +118,7 @@ __device__ __forceinline__ void cc_apply(int q, int n, const OpCoef<float>& c, c
         cell_apply_merged<DA, DBT, DB, DD, false, 1>(i, j, n, c, PViewU<float>{ux, ld}, PViewU<float>{uy, ld},
                                                      PViewU<float>{vp, n + 1}, a);
     } else {
-        cell_apply_auto<DA, DBT, DB, DD, false>(i, j, n, c, PView<float>{ux, ld}, PView<float>{uy, ld},
-                                                PView<float>{vp, n + 1}, a);
+        cc_apply_rolled<DA, DBT, DB, DD>(i, j, n, stencil_class(i, j, n), c, ux, uy, vp, a);
     }
 }
 
@@ -183,9 +227,18 @@ __device__ void cc_residual(const CCLevel& L, const OpCoef<float>& c) {
 __global__ void __launch_bounds__(kCoarseThreads, 1) k_coarse_cycle(const __grid_constant__ CoarseCycleArgs A) {
     pdl_enter();
     extern __shared__ __align__(16) float cc_smem[];
+    // The operator coefficients of every level, copied from the parameter bank: the cycle indexes
+    // levels at run time, and run-time-indexed parameter reads would each wait on the constant cache.
+    __shared__ OpCoef<float> sc[kCoarseTop];
     double* bvec = reinterpret_cast<double*>(cc_smem);            // 27 doubles for the level-0 solve
     float* base = cc_smem + 2 * 64;                                 // after 64 doubles of scratch
     const int top = A.top;
+    {
+        const float* src = reinterpret_cast<const float*>(&A.c[0]);
+        float* dst = reinterpret_cast<float*>(&sc[0]);
+        const int words = top * (int)(sizeof(OpCoef<float>) / sizeof(float));
+        for (int q = threadIdx.x; q < words; q += blockDim.x) dst[q] = src[q];
+    }
     {   // state of the top level, its right-hand side, and Shat^{-1} of every level
         const CCLevel T = cc_level(base, top);
         const int n2 = cc_n2(top), n1 = cc_n1(top);
@@ -206,7 +259,7 @@ __global__ void __launch_bounds__(kCoarseThreads, 1) k_coarse_cycle(const __grid
     // down: smooth, residual, restrict (and start the coarser iterate from zero)
     for (int l = top; l >= 1; --l) {
         const CCLevel L = cc_level(base, l), C = cc_level(base, l - 1);
-        const OpCoef<float>& c = A.c[l - 1];
+        const OpCoef<float>& c = sc[l - 1];
         for (int m = 0; m < A.nu_pre; ++m) cc_smooth(L, c, A.tau, A.sigma);
         cc_residual(L, c);
         const int nc = C.n, ldc = 2 * nc + 1, n2c = ldc * ldc;
@@ -257,7 +310,7 @@ __global__ void __launch_bounds__(kCoarseThreads, 1) k_coarse_cycle(const __grid
         for (int q = threadIdx.x; q < (nc + 1) * (nc + 1); q += blockDim.x)
             prolong_cell<false>(q % (nc + 1), q / (nc + 1), nc, C.u, C.p, L.u, L.p);
         __syncthreads();
-        for (int m = 0; m < A.nu_post; ++m) cc_smooth(L, A.c[l - 1], A.tau, A.sigma);
+        for (int m = 0; m < A.nu_post; ++m) cc_smooth(L, sc[l - 1], A.tau, A.sigma);
     }
     {
         const CCLevel T = cc_level(base, top);
