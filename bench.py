@@ -54,7 +54,7 @@ def parse():
                     help="kernel modes: drive refinement steps from the host, one cycle graph per step, so that a "
                          "profiler lists every kernel (the device-side loop hides the loop body from it)")
     ap.add_argument("--variant", type=int, default=None,
-                    help="kernel modes: force this float32 Uzawa step variant (0-6) on every level")
+                    help="kernel modes: force this float32 Uzawa step variant (0-8) on every level")
     return ap.parse_args()
 
 

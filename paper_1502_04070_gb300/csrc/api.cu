@@ -521,7 +521,7 @@ stokes_status stokes_setup(const stokes_params* prm, void* stream, stokes_handle
     stokes_status s = ensure_weights();
     if (s != STOKES_OK) return s;
     if (prepare_uzawa_fused<float>() != cudaSuccess || prepare_uzawa_fused<double>() != cudaSuccess ||
-        prepare_coarse_cycle() != cudaSuccess)
+        prepare_coarse_cycle() != cudaSuccess || prepare_uzawa_pair() != cudaSuccess)
         return STOKES_ERR_CUDA;
     stokes_handle* h = new stokes_handle_t();
     h->prm = P;

@@ -43,6 +43,12 @@ void launch_residual_df(cudaStream_t s, int n, const OpCoef<double>& c, const do
 // (u_out, p_out) (distinct buffers).
 template <typename T>
 cudaError_t prepare_uzawa_fused();   // raises the kernel's shared-memory limit on the current device
+// The float32 step on component-pair tiles with packed FP32x2 arithmetic (uzawa_pair.cu); variant 0:
+// 28 x 16 cells per CTA, 1: 28 x 8.  Reads (u, p), writes (u_out, p_out).
+void launch_uzawa_pair(int variant, cudaStream_t s, int n, const OpCoef<float>& c, float tau, float sigma,
+                       const float* u, const float* p, const float* f, const float* g, const float* sinv,
+                       float* u_out, float* p_out);
+cudaError_t prepare_uzawa_pair();
 template <typename T>
 cudaError_t launch_uzawa_fused(cudaStream_t s, int n, const OpCoef<T>& c, T tau, T sigma, const T* u, const T* p,
                                const T* f, const T* g, const T* sinv, T* u_out, T* p_out);

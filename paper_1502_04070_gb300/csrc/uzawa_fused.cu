@@ -163,9 +163,11 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 4 ? 2 : 1)) k_uzawa_fuse
 // step).  Fused one-kernel tiles (TX x TY cells): 0: 32 x 16, 1: 32 x 8, 2: 64 x 8, 3: 16 x 16.
 // Three-kernel step (one thread per cell and phase, no halo recomputation; short per-thread work
 // suits the small levels, whose few fused tiles are issue-bound) with blocks 4: 32 x 8, 5: 16 x 8,
-// 6: 8 x 8.
+// 6: 8 x 8.  Fused step on component-pair tiles with packed FP32x2 arithmetic (uzawa_pair.cu):
+// 7: 28 x 16 cells, 8 warps; 8: 28 x 8 cells, 4 warps.
 constexpr int kFusedVariants = 4;
-constexpr int kStepVariants = 7;
+constexpr int kPairVariant0 = 7;
+constexpr int kStepVariants = 9;
 // per level k (N = 2^(k+1)): chosen variant; until tuned, the three-kernel step below N = 128 and the
 // 32 x 16 fused tile from N = 128 up
 static int g_tile_choice[32] = {5, 5, 5, 5, 5, 5, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0,
@@ -227,6 +229,10 @@ static bool launch_step_variant(int v, cudaStream_t s, int n, const OpCoef<float
                                 float* p_out) {
     if (v < kFusedVariants) {
         launch_variant<float>(v, s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
+        return true;
+    }
+    if (v >= kPairVariant0) {
+        launch_uzawa_pair(v - kPairVariant0, s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
         return true;
     }
     const int bx = v == 4 ? 32 : (v == 5 ? 16 : 8), by = 8;

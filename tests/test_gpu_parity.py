@@ -204,11 +204,13 @@ def test_smoother_float32_fused(discs, Solver, k, beta, nu):
 
 
 @pytest.mark.parametrize("k", [3, 5, 6])
-@pytest.mark.parametrize("variant", range(7))
+@pytest.mark.parametrize("variant", range(9))
 def test_smoother_float32_every_variant(discs, Solver, k, variant):
     """Every float32 step variant the autotuner may choose (four fused tile shapes, the three-kernel
-    step with three block shapes) gives the oracle's three Uzawa steps at a size whose cells do not
-    fill the last tile or block (N + 1 = 2^(k+1) + 1 per side).  Bound as above (2e-5)."""
+    step with three block shapes, the component-pair tiles in two shapes) gives the oracle's three
+    Uzawa steps at a size whose cells do not fill the last tile or block (N + 1 = 2^(k+1) + 1 per
+    side); at k = 6 the pair tiles take both their interior and their general path.  Bound as
+    above (2e-5)."""
     from paper_1502_04070_gb300.solver import set_step_variant, step_variant
     beta = 1e2
     H = mg.Hierarchy(k + 1, beta, discs[:k + 1])
