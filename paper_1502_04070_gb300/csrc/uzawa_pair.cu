@@ -9,12 +9,14 @@
 // B^T pair an x and a y coefficient with one value, so with (u_x, u_y) stored as one float2 a row
 // term is one 64-bit shared load and one packed fused multiply-add (FFMA2) for both components.
 //
-// A CTA owns a 28 x TY tile of cells; its NW warps stage u and p with a three-cell halo, compute
+// A CTA owns a 28 x ty tile of cells; its NW warps stage u and p with a three-cell halo, compute
 // u^{m-1/2} on the tile plus two cells (32 cells per row: one row per warp pass), dp on the tile
 // plus one vertex, and the new (u, p) on the tile.  Tiles whose staged region lies strictly inside
 // the domain and off the two mid-lines (most of them) take a path with every structural test
 // decided at compile time for the tile's one stencil class; the other tiles run the general
 // merged-stencil rows of cellops.cuh on the same shared tiles.
+#include <algorithm>
+
 #include "cellops.cuh"
 #include "kernels.cuh"
 
@@ -41,33 +43,41 @@ static PairCoef make_pair_coef(const OpCoef<float>& c, float tau) {
     return q;
 }
 
-template <int TX, int TY>
+// Tile geometry for TX = 28 columns of cells and a run-time number of rows ty (chosen per level
+// so that the tiles fill whole waves of resident CTAs, see pair_rows).
 struct PairTile {
+    static constexpr int TX = 28;
     static_assert(TX + 4 == 32, "one warp covers a row of the u^{m-1/2} region");
-    // u: cells [i0-3, i0+TX+3) x [j0-3, j0+TY+3); lattice columns split by parity into two planes
-    static constexpr int UWH = TX + 6, UH = 2 * (TY + 6), UPL = UWH * UH;   // float2 per plane
-    // u^{m-1/2}: cells [i0-2, i0+TX+2) x [j0-2, j0+TY+2)
-    static constexpr int HWH = TX + 4, HH = 2 * (TY + 4), HPL = HWH * HH;
-    static constexpr int PW = TX + 6, PH = TY + 6;   // p: vertices [i0-3, i0+TX+3)
-    static constexpr int DW = TX + 2, DH = TY + 2;   // dp: vertices [i0-1, i0+TX+1)
-    static constexpr size_t BYTES = 8 * (size_t)(2 * UPL + 2 * HPL) + 4 * (size_t)(PW * PH + DW * DH);
+    // u: cells [i0-3, i0+TX+3) x [j0-3, j0+ty+3); lattice columns split by parity into two planes
+    static constexpr int UWH = TX + 6;   // float2 per plane row
+    // u^{m-1/2}: cells [i0-2, i0+TX+2) x [j0-2, j0+ty+2)
+    static constexpr int HWH = TX + 4;
+    static constexpr int PW = TX + 6;    // p: vertices [i0-3, i0+TX+3)
+    static constexpr int DW = TX + 2;    // dp: vertices [i0-1, i0+TX+1)
+    __host__ __device__ static constexpr int upl(int ty) { return UWH * 2 * (ty + 6); }
+    __host__ __device__ static constexpr int hpl(int ty) { return HWH * 2 * (ty + 4); }
+    __host__ __device__ static constexpr size_t bytes(int ty) {
+        return 8 * (size_t)(2 * upl(ty) + 2 * hpl(ty)) + 4 * (size_t)(PW * (ty + 6) + DW * (ty + 2));
+    }
 };
+constexpr int kPairMaxRows = 20;
 
 // One component of a float2 lattice tile (general path; same addressing as SLat).  The component
 // is a member so that both views share one type; it is a constant wherever a view is built.
-template <int WH, int PL>
+template <int WH>
 struct PairLat {
     static constexpr bool zero_filled = true;
     const float2* p;
+    int pl;        // float2 per parity plane
     int xh0, y0;   // tile origin: X0 = 2 xh0, Y0 = y0
     bool ycomp;
     __device__ __forceinline__ float at(int si, int sj, int a, int b) const {
-        const float2 e = p[(a & 1) * PL + (2 * sj + b - y0) * WH + (si - xh0) + (a >> 1)];
+        const float2 e = p[(a & 1) * pl + (2 * sj + b - y0) * WH + (si - xh0) + (a >> 1)];
         return ycomp ? e.y : e.x;
     }
     __device__ __forceinline__ float operator()(int X, int Y) const {
         const int dx = X - 2 * xh0;
-        const float2 e = p[(dx & 1) * PL + (Y - y0) * WH + (dx >> 1)];
+        const float2 e = p[(dx & 1) * pl + (Y - y0) * WH + (dx >> 1)];
         return ycomp ? e.y : e.x;
     }
 };
@@ -76,20 +86,22 @@ __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b
 
 // ---- fast path (class C, every node an unknown, every window inside the tile)
 // window point W (5 x 5 around the cell's vertex) of a float2 lattice tile; `b` addresses the cell
-template <int WH, int PL, int W>
-__device__ __forceinline__ float2 win2(const float2* t, int b) {
+// t0 / t1: the cell's position in the even / odd parity plane
+template <int WH, int W>
+__device__ __forceinline__ float2 win2(const float2* t0, const float2* t1) {
     constexpr int dx = W % 5 - 2, dy = W / 5 - 2;
-    return t[b + (dx & 1) * PL + dy * WH + (dx >> 1)];
+    return ((dx & 1) ? t1 : t0)[dy * WH + (dx >> 1)];
 }
 
 template <int C, int S, int W>
 __device__ __forceinline__ void ma_pair(const PairCoef& q, float2 w, float2 (&au)[4]) {
     if constexpr (nz_MA(C, S, W)) au[S] = __ffma2_rn(q.MA[C][S][W], w, au[S]);
 }
-template <int C, int WH, int PL, int W>
-__device__ __forceinline__ void phase1_w(const PairCoef& q, const float2* sU, int b, float2 (&au)[4], float2 (&ctr)[4]) {
+template <int C, int WH, int W>
+__device__ __forceinline__ void phase1_w(const PairCoef& q, const float2* t0, const float2* t1, float2 (&au)[4],
+                                         float2 (&ctr)[4]) {
     if constexpr (need_win(C, true, false, W)) {
-        const float2 w = win2<WH, PL, W>(sU, b);
+        const float2 w = win2<WH, W>(t0, t1);
         ma_pair<C, 0, W>(q, w, au);
         ma_pair<C, 1, W>(q, w, au);
         ma_pair<C, 2, W>(q, w, au);
@@ -121,35 +133,38 @@ __device__ __forceinline__ void bt_rows(const PairCoef& q, const float* sp, int 
                                         std::integer_sequence<int, V...>) {
     (bt_v<C, PW, V>(q, sp, b, bt), ...);
 }
-template <int C, int WH, int PL, int... W>
-__device__ __forceinline__ void a_rows(const PairCoef& q, const float2* sU, int b, float2 (&au)[4], float2 (&ctr)[4],
+template <int C, int WH, int... W>
+__device__ __forceinline__ void a_rows(const PairCoef& q, const float2* t0, const float2* t1, float2 (&au)[4],
+                                       float2 (&ctr)[4], std::integer_sequence<int, W...>) {
+    (phase1_w<C, WH, W>(q, t0, t1, au, ctr), ...);
+}
+template <int C, int WH, int W>
+__device__ __forceinline__ void b_w(const PairCoef& q, const float2* t0, const float2* t1, float2& acc) {
+    if constexpr (nz_MB(C, W)) acc = __ffma2_rn(q.MB[C][W], win2<WH, W>(t0, t1), acc);
+}
+template <int C, int WH, int... W>
+__device__ __forceinline__ float b_row(const PairCoef& q, const float2* t0, const float2* t1,
                                        std::integer_sequence<int, W...>) {
-    (phase1_w<C, WH, PL, W>(q, sU, b, au, ctr), ...);
-}
-template <int C, int WH, int PL, int W>
-__device__ __forceinline__ void b_w(const PairCoef& q, const float2* sH, int b, float2& acc) {
-    if constexpr (nz_MB(C, W)) acc = __ffma2_rn(q.MB[C][W], win2<WH, PL, W>(sH, b), acc);
-}
-template <int C, int WH, int PL, int... W>
-__device__ __forceinline__ float b_row(const PairCoef& q, const float2* sH, int b, std::integer_sequence<int, W...>) {
     float2 acc = f2(0.f, 0.f);
-    (b_w<C, WH, PL, W>(q, sH, b, acc), ...);
+    (b_w<C, WH, W>(q, t0, t1, acc), ...);
     return acc.x + acc.y;
 }
 
-template <int TX, int TY, int NW>
-__global__ void __launch_bounds__(32 * NW, (TY > 8 ? 3 : 6))
-    k_uzawa_pair(int n, const __grid_constant__ OpCoef<float> c, const __grid_constant__ PairCoef q, float tau,
+template <int NW>
+__global__ void __launch_bounds__(32 * NW, (NW > 4 ? 3 : 6))
+    k_uzawa_pair(int n, int TY, const __grid_constant__ OpCoef<float> c, const __grid_constant__ PairCoef q, float tau,
                  float sigma, const float* __restrict__ u, const float* __restrict__ p, const float* __restrict__ f,
                  const float* __restrict__ g, const float* __restrict__ sinv, float* __restrict__ u_out,
                  float* __restrict__ p_out) {
     pdl_enter();
-    using G = PairTile<TX, TY>;
+    using G = PairTile;
+    constexpr int TX = G::TX;
+    const int UPL = G::upl(TY), HPL = G::hpl(TY);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* sU = reinterpret_cast<float2*>(smem_raw);
-    float2* sH = sU + 2 * G::UPL;
-    float* sP = reinterpret_cast<float*>(sH + 2 * G::HPL);
-    float* sD = sP + G::PW * G::PH;
+    float2* sH = sU + 2 * UPL;
+    float* sP = reinterpret_cast<float*>(sH + 2 * HPL);
+    float* sD = sP + G::PW * (TY + 6);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
     const int ld = 2 * n + 1, n2 = ld * ld, h = n >> 1;
@@ -160,7 +175,7 @@ __global__ void __launch_bounds__(32 * NW, (TY > 8 ? 3 : 6))
 
     // ---- stage u as (u_x, u_y) pairs and p; zero outside the domain and on its boundary
     const int X0 = 2 * (i0 - 3), Y0 = 2 * (j0 - 3);
-    for (int y = warp; y < G::UH; y += NW) {
+    for (int y = warp; y < 2 * (TY + 6); y += NW) {
         const int Y = Y0 + y;
         for (int x = lane; x < 2 * G::UWH; x += 32) {
             const int X = X0 + x;
@@ -169,10 +184,10 @@ __global__ void __launch_bounds__(32 * NW, (TY > 8 ? 3 : 6))
                 const int k = Y * ld + X;
                 v = f2(__ldg(u + k), __ldg(u + n2 + k));
             }
-            sU[(x & 1) * G::UPL + y * G::UWH + (x >> 1)] = v;
+            sU[(x & 1) * UPL + y * G::UWH + (x >> 1)] = v;
         }
     }
-    for (int y = warp; y < G::PH; y += NW) {
+    for (int y = warp; y < TY + 6; y += NW) {
         const int J = j0 - 3 + y;
         for (int x = lane; x < G::PW; x += 32) {
             const int I = i0 - 3 + x;
@@ -181,8 +196,8 @@ __global__ void __launch_bounds__(32 * NW, (TY > 8 ? 3 : 6))
     }
     __syncthreads();
 
-    using UL = PairLat<G::UWH, G::UPL>;
-    using HL = PairLat<G::HWH, G::HPL>;
+    using UL = PairLat<G::UWH>;
+    using HL = PairLat<G::HWH>;
 
     // ---- u^{m-1/2} on cells (i0 - 2 + lane, j0 - 2 + r)
     for (int r = warp; r < TY + 4; r += NW) {
@@ -192,12 +207,14 @@ __global__ void __launch_bounds__(32 * NW, (TY > 8 ? 3 : 6))
             float2 au[4], bt[4], ctr[4];
 #pragma unroll
             for (int s = 0; s < 4; ++s) au[s] = bt[s] = ctr[s] = f2(0.f, 0.f);
-            const int bu = 2 * (r + 1) * G::UWH + lane + 1, bp = (r + 1) * G::PW + lane + 1;
+            const float2* t0 = sU + 2 * (r + 1) * G::UWH + lane + 1;
+            const float2* t1 = t0 + UPL;
+            const int bp = (r + 1) * G::PW + lane + 1;
             if (cls == 0) {
-                a_rows<0, G::UWH, G::UPL>(q, sU, bu, au, ctr, std::make_integer_sequence<int, 25>{});
+                a_rows<0, G::UWH>(q, t0, t1, au, ctr, std::make_integer_sequence<int, 25>{});
                 bt_rows<0, G::PW>(q, sP, bp, bt, std::make_integer_sequence<int, 9>{});
             } else {
-                a_rows<1, G::UWH, G::UPL>(q, sU, bu, au, ctr, std::make_integer_sequence<int, 25>{});
+                a_rows<1, G::UWH>(q, t0, t1, au, ctr, std::make_integer_sequence<int, 25>{});
                 bt_rows<1, G::PW>(q, sP, bp, bt, std::make_integer_sequence<int, 9>{});
             }
 #pragma unroll
@@ -211,8 +228,8 @@ __global__ void __launch_bounds__(32 * NW, (TY > 8 ? 3 : 6))
 #pragma unroll
             for (int s = 0; s < 4; ++s) hv[s] = f2(0.f, 0.f);
             if (ci >= 0 && cj >= 0 && ci <= n && cj <= n) {
-                const UL vux{sU, i0 - 3, Y0, false};
-                const UL vuy{sU, i0 - 3, Y0, true};
+                const UL vux{sU, UPL, i0 - 3, Y0, false};
+                const UL vuy{sU, UPL, i0 - 3, Y0, true};
                 const SVert<float, G::PW> vp{sP, i0 - 3, j0 - 3};
                 Acc<float> a;
                 cell_apply_auto<true, true, false, true, false>(ci, cj, n, c, vux, vuy, vp, a);
@@ -228,7 +245,7 @@ __global__ void __launch_bounds__(32 * NW, (TY > 8 ? 3 : 6))
             }
         }
 #pragma unroll
-        for (int s = 0; s < 4; ++s) sH[(s & 1) * G::HPL + (2 * r + (s >> 1)) * G::HWH + lane] = hv[s];
+        for (int s = 0; s < 4; ++s) sH[(s & 1) * HPL + (2 * r + (s >> 1)) * G::HWH + lane] = hv[s];
     }
     __syncthreads();
 
@@ -238,14 +255,15 @@ __global__ void __launch_bounds__(32 * NW, (TY > 8 ? 3 : 6))
         const int vi = i0 - 1 + lane, vj = j0 - 1 + r;
         float d = 0.f;
         if (fast) {
-            const int b = 2 * (r + 1) * G::HWH + lane + 1;
-            const float bu = cls == 0 ? b_row<0, G::HWH, G::HPL>(q, sH, b, std::make_integer_sequence<int, 25>{})
-                                      : b_row<1, G::HWH, G::HPL>(q, sH, b, std::make_integer_sequence<int, 25>{});
+            const float2* t0 = sH + 2 * (r + 1) * G::HWH + lane + 1;
+            const float2* t1 = t0 + HPL;
+            const float bu = cls == 0 ? b_row<0, G::HWH>(q, t0, t1, std::make_integer_sequence<int, 25>{})
+                                      : b_row<1, G::HWH>(q, t0, t1, std::make_integer_sequence<int, 25>{});
             const int k = vj * (n + 1) + vi;
             d = sigma * __ldg(sinv + k) * (bu - __ldg(g + k));
         } else if (vi >= 0 && vj >= 0 && vi <= n && vj <= n) {
-            const HL vhx{sH, i0 - 2, 2 * (j0 - 2), false};
-            const HL vhy{sH, i0 - 2, 2 * (j0 - 2), true};
+            const HL vhx{sH, HPL, i0 - 2, 2 * (j0 - 2), false};
+            const HL vhy{sH, HPL, i0 - 2, 2 * (j0 - 2), true};
             const SVert<float, G::PW> vp{sP, i0 - 3, j0 - 3};
             Acc<float> a;
             cell_apply_auto<false, false, true, false, false>(vi, vj, n, c, vhx, vhy, vp, a);
@@ -271,7 +289,7 @@ __global__ void __launch_bounds__(32 * NW, (TY > 8 ? 3 : 6))
             else bt_rows<1, G::DW>(q, sD, bd, bt, std::make_integer_sequence<int, 9>{});
 #pragma unroll
             for (int s = 0; s < 4; ++s) {
-                const float2 hc = sH[(s & 1) * G::HPL + (2 * (r + 2) + (s >> 1)) * G::HWH + lane + 2];
+                const float2 hc = sH[(s & 1) * HPL + (2 * (r + 2) + (s >> 1)) * G::HWH + lane + 2];
                 const float ti = -q.TI[cls][s];
                 o[s] = __ffma2_rn(f2(ti, ti), bt[s], hc);
             }
@@ -282,8 +300,8 @@ __global__ void __launch_bounds__(32 * NW, (TY > 8 ? 3 : 6))
                 u_out[n2 + k] = o[s].y;
             }
         } else {
-            const HL vhx{sH, i0 - 2, 2 * (j0 - 2), false};
-            const HL vhy{sH, i0 - 2, 2 * (j0 - 2), true};
+            const HL vhx{sH, HPL, i0 - 2, 2 * (j0 - 2), false};
+            const HL vhy{sH, HPL, i0 - 2, 2 * (j0 - 2), true};
             const SVert<float, G::DW> vd{sD, i0 - 1, j0 - 1};
             Acc<float> a;
             cell_apply_auto<false, true, false, true, false>(ci, cj, n, c, vhx, vhy, vd, a);
@@ -306,32 +324,66 @@ __global__ void __launch_bounds__(32 * NW, (TY > 8 ? 3 : 6))
     }
 }
 
-template <int TX, int TY, int NW>
+template <int NW>
 static cudaError_t pair_smem_attr() {
-    return cudaFuncSetAttribute(k_uzawa_pair<TX, TY, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)PairTile<TX, TY>::BYTES);
+    return cudaFuncSetAttribute(k_uzawa_pair<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)PairTile::bytes(kPairMaxRows));
 }
 
 cudaError_t prepare_uzawa_pair() {
-    cudaError_t e = pair_smem_attr<28, 16, 8>();
+    cudaError_t e = pair_smem_attr<8>();
     if (e != cudaSuccess) return e;
-    return pair_smem_attr<28, 8, 4>();
+    return pair_smem_attr<4>();
 }
 
-template <int TX, int TY, int NW>
+// Rows per tile for level size n: the least work on the busiest SM, (tiles per SM, rounded up) x
+// (work of one tile, about ty + 4 rows of the u^{m-1/2} region), among the tile heights that keep
+// at least two CTAs resident per SM.
+template <int NW>
+static int pair_rows(int n) {
+    static int cache[2][32] = {};
+    const int lv = 31 - __builtin_clz((unsigned)n);
+    int& r = cache[NW > 4][lv & 31];
+    if (r) return r;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int cols = (n + 1 + PairTile::TX - 1) / PairTile::TX;
+    double best = 1e300;
+    int best_ty = 16;
+    for (int ty = 8; ty <= kPairMaxRows; ++ty) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_uzawa_pair<NW>, 32 * NW, PairTile::bytes(ty)) !=
+                cudaSuccess || per_sm < 2)
+            continue;
+        const long tiles = (long)cols * ((n + 1 + ty - 1) / ty);
+        const long m = std::max(sms, 1);
+        const double cost = (double)((tiles + m - 1) / m) * (ty + 4);
+        if (cost < best) {
+            best = cost;
+            best_ty = ty;
+        }
+    }
+    cudaGetLastError();
+    r = best_ty;
+    return r;
+}
+
+template <int NW>
 static void launch_pair_v(cudaStream_t s, int n, const OpCoef<float>& c, float tau, float sigma, const float* u,
                           const float* p, const float* f, const float* g, const float* sinv, float* u_out,
                           float* p_out) {
-    const dim3 grid((n + 1 + TX - 1) / TX, (n + 1 + TY - 1) / TY), blk(32 * NW);
-    launch_pdl(k_uzawa_pair<TX, TY, NW>, grid, blk, PairTile<TX, TY>::BYTES, s, n, c, make_pair_coef(c, tau), tau,
-               sigma, u, p, f, g, sinv, u_out, p_out);
+    const int ty = pair_rows<NW>(n);
+    const dim3 grid((n + 1 + PairTile::TX - 1) / PairTile::TX, (n + 1 + ty - 1) / ty), blk(32 * NW);
+    launch_pdl(k_uzawa_pair<NW>, grid, blk, PairTile::bytes(ty), s, n, ty, c, make_pair_coef(c, tau), tau, sigma, u,
+               p, f, g, sinv, u_out, p_out);
 }
 
 void launch_uzawa_pair(int variant, cudaStream_t s, int n, const OpCoef<float>& c, float tau, float sigma,
                        const float* u, const float* p, const float* f, const float* g, const float* sinv,
                        float* u_out, float* p_out) {
-    if (variant == 0) launch_pair_v<28, 16, 8>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
-    else launch_pair_v<28, 8, 4>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
+    if (variant == 0) launch_pair_v<8>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
+    else launch_pair_v<4>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
 }
 
 }  // namespace smg
