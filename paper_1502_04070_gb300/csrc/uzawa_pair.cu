@@ -11,10 +11,11 @@
 //
 // A CTA owns a 28 x ty tile of cells; its NW warps stage u and p with a three-cell halo, compute
 // u^{m-1/2} on the tile plus two cells (32 cells per row: one row per warp pass), dp on the tile
-// plus one vertex, and the new (u, p) on the tile.  Tiles whose staged region lies strictly inside
-// the domain and off the two mid-lines (most of them) take a path with every structural test
-// decided at compile time for the tile's one stencil class; the other tiles run the general
-// merged-stencil rows of cellops.cuh on the same shared tiles.
+// plus one vertex, and the new (u, p) on the tile.  Tiles away from the two mid-lines (all but a
+// few) take a path with every structural test decided at compile time for the tile's one stencil
+// class (at the boundary the zero-filled halo stands for the Dirichlet values, and only unknowns
+// are written); the tiles at the mid-lines run the general merged-stencil rows of cellops.cuh, cell
+// by cell, on the same shared tiles.
 #include <algorithm>
 
 #include "cellops.cuh"
@@ -168,9 +169,11 @@ __global__ void __launch_bounds__(32 * NW, (NW > 4 ? 3 : 6))
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
     const int ld = 2 * n + 1, n2 = ld * ld, h = n >> 1;
-    // staged lattice region strictly inside the domain and the u^{m-1/2} region off the mid-lines
-    const bool fast = i0 >= 4 && j0 >= 4 && i0 + TX + 3 <= n && j0 + TY + 3 <= n && (h < i0 - 2 || h >= i0 + TX + 2) &&
-                      (h < j0 - 2 || h >= j0 + TY + 2);
+    // fast: the u^{m-1/2} region is off the mid-lines, so every cell of the tile has the stencil
+    // class of its quadrant; inner: besides, the staged region lies strictly inside the domain, so
+    // nothing needs a range test or a Dirichlet mask
+    const bool fast = (h < i0 - 2 || h >= i0 + TX + 2) && (h < j0 - 2 || h >= j0 + TY + 2);
+    const bool inner = fast && i0 >= 4 && j0 >= 4 && i0 + TX + 3 <= n && j0 + TY + 3 <= n;
     const int cls = orient(i0, j0, n);
 
     // ---- stage u as (u_x, u_y) pairs and p; zero outside the domain and on its boundary
@@ -180,7 +183,7 @@ __global__ void __launch_bounds__(32 * NW, (NW > 4 ? 3 : 6))
         for (int x = lane; x < 2 * G::UWH; x += 32) {
             const int X = X0 + x;
             float2 v = f2(0.f, 0.f);
-            if (fast || interior2(X, Y, n)) {
+            if (inner || interior2(X, Y, n)) {
                 const int k = Y * ld + X;
                 v = f2(__ldg(u + k), __ldg(u + n2 + k));
             }
@@ -191,7 +194,7 @@ __global__ void __launch_bounds__(32 * NW, (NW > 4 ? 3 : 6))
         const int J = j0 - 3 + y;
         for (int x = lane; x < G::PW; x += 32) {
             const int I = i0 - 3 + x;
-            sP[y * G::PW + x] = (fast || (I >= 0 && J >= 0 && I <= n && J <= n)) ? __ldg(p + (J * (n + 1) + I)) : 0.f;
+            sP[y * G::PW + x] = (inner || (I >= 0 && J >= 0 && I <= n && J <= n)) ? __ldg(p + (J * (n + 1) + I)) : 0.f;
         }
     }
     __syncthreads();
@@ -217,12 +220,21 @@ __global__ void __launch_bounds__(32 * NW, (NW > 4 ? 3 : 6))
                 a_rows<1, G::UWH>(q, t0, t1, au, ctr, std::make_integer_sequence<int, 25>{});
                 bt_rows<1, G::PW>(q, sP, bp, bt, std::make_integer_sequence<int, 9>{});
             }
+            // on a tile at the boundary the rows are the same (the staged zeros stand for the
+            // Dirichlet values and for everything outside); only unknowns keep their value
+            const bool ci_in = ci > 0 && ci < n, cj_in = cj > 0 && cj < n;
+            const bool ci_h = ci >= 0 && ci < n, cj_h = cj >= 0 && cj < n;
+            const bool unk[4] = {inner || (ci_in && cj_in), inner || (ci_h && cj_in), inner || (ci_in && cj_h),
+                                 inner || (ci_h && cj_h)};
 #pragma unroll
             for (int s = 0; s < 4; ++s) {
-                const int k = (2 * cj + (s >> 1)) * ld + 2 * ci + (s & 1);
-                const float2 fs = f2(__ldg(f + k), __ldg(f + n2 + k));
-                const float ti = q.TI[cls][s];
-                hv[s] = __ffma2_rn(f2(ti, ti), f2(fs.x - au[s].x - bt[s].x, fs.y - au[s].y - bt[s].y), ctr[s]);
+                hv[s] = f2(0.f, 0.f);
+                if (unk[s]) {
+                    const int k = (2 * cj + (s >> 1)) * ld + 2 * ci + (s & 1);
+                    const float2 fs = f2(__ldg(f + k), __ldg(f + n2 + k));
+                    const float ti = q.TI[cls][s];
+                    hv[s] = __ffma2_rn(f2(ti, ti), f2(fs.x - au[s].x - bt[s].x, fs.y - au[s].y - bt[s].y), ctr[s]);
+                }
             }
         } else {
 #pragma unroll
@@ -254,14 +266,14 @@ __global__ void __launch_bounds__(32 * NW, (NW > 4 ? 3 : 6))
         if (lane >= TX + 2) break;
         const int vi = i0 - 1 + lane, vj = j0 - 1 + r;
         float d = 0.f;
-        if (fast) {
+        if (fast && (inner || (vi >= 0 && vj >= 0 && vi <= n && vj <= n))) {
             const float2* t0 = sH + 2 * (r + 1) * G::HWH + lane + 1;
             const float2* t1 = t0 + HPL;
             const float bu = cls == 0 ? b_row<0, G::HWH>(q, t0, t1, std::make_integer_sequence<int, 25>{})
                                       : b_row<1, G::HWH>(q, t0, t1, std::make_integer_sequence<int, 25>{});
             const int k = vj * (n + 1) + vi;
             d = sigma * __ldg(sinv + k) * (bu - __ldg(g + k));
-        } else if (vi >= 0 && vj >= 0 && vi <= n && vj <= n) {
+        } else if (!fast && vi >= 0 && vj >= 0 && vi <= n && vj <= n) {
             const HL vhx{sH, HPL, i0 - 2, 2 * (j0 - 2), false};
             const HL vhy{sH, HPL, i0 - 2, 2 * (j0 - 2), true};
             const SVert<float, G::PW> vp{sP, i0 - 3, j0 - 3};
@@ -293,11 +305,23 @@ __global__ void __launch_bounds__(32 * NW, (NW > 4 ? 3 : 6))
                 const float ti = -q.TI[cls][s];
                 o[s] = __ffma2_rn(f2(ti, ti), bt[s], hc);
             }
+            if (inner) {
 #pragma unroll
-            for (int s = 0; s < 4; ++s) {
-                const int k = (2 * cj + (s >> 1)) * ld + 2 * ci + (s & 1);
-                u_out[k] = o[s].x;
-                u_out[n2 + k] = o[s].y;
+                for (int s = 0; s < 4; ++s) {
+                    const int k = (2 * cj + (s >> 1)) * ld + 2 * ci + (s & 1);
+                    u_out[k] = o[s].x;
+                    u_out[n2 + k] = o[s].y;
+                }
+            } else {
+                const CellNodes cn = cell_nodes(ci, cj, n);
+#pragma unroll
+                for (int s = 0; s < 4; ++s) {
+                    if (!slot_exists(cn, s)) continue;
+                    const int k = (2 * cj + (s >> 1)) * ld + 2 * ci + (s & 1);
+                    const bool uk = slot_unknown(cn, s);
+                    u_out[k] = uk ? o[s].x : 0.f;
+                    u_out[n2 + k] = uk ? o[s].y : 0.f;
+                }
             }
         } else {
             const HL vhx{sH, HPL, i0 - 2, 2 * (j0 - 2), false};
