@@ -94,6 +94,56 @@ __device__ __forceinline__ void visit_df(int i, int j, int n, const OpCoef<float
     }
 }
 
+// The same rows from the merged stencils of class C (blocks off the mid-lines and at least two
+// cells inside the boundary: every window lies inside the arrays, every term is decided at compile
+// time).
+template <int C, int S, int K>
+__device__ __forceinline__ void ma_df(const OpCoef<float>& h, const OpCoef<float>& l, const float (&wx)[25],
+                                      const float (&wy)[25], DFAcc& a) {
+    if constexpr (nz_MA(C, S, K)) {
+        df_fma(a.au[0][S], h.MA[C][S][K], l.MA[C][S][K], wx[K]);
+        df_fma(a.au[1][S], h.MA[C][S][K], l.MA[C][S][K], wy[K]);
+    }
+}
+template <int C, int K>
+__device__ __forceinline__ void win_df(const OpCoef<float>& h, const OpCoef<float>& l, const float (&wx)[25],
+                                       const float (&wy)[25], DFAcc& a) {
+    ma_df<C, 0, K>(h, l, wx, wy, a);
+    ma_df<C, 1, K>(h, l, wx, wy, a);
+    ma_df<C, 2, K>(h, l, wx, wy, a);
+    ma_df<C, 3, K>(h, l, wx, wy, a);
+    if constexpr (nz_MB(C, K)) {
+        df_fma(a.bu, h.MBx[C][K], l.MBx[C][K], wx[K]);
+        df_fma(a.bu, h.MBy[C][K], l.MBy[C][K], wy[K]);
+    }
+}
+template <int C, int S, int V>
+__device__ __forceinline__ void mbt_df(const OpCoef<float>& h, const OpCoef<float>& l, const float (&pw)[9], DFAcc& a) {
+    if constexpr (nz_MBT(C, S, V)) {
+        df_fma(a.au[0][S], h.MBTx[C][S][V], l.MBTx[C][S][V], pw[V]);
+        df_fma(a.au[1][S], h.MBTy[C][S][V], l.MBTy[C][S][V], pw[V]);
+    }
+}
+template <int C, int V>
+__device__ __forceinline__ void vwin_df(const OpCoef<float>& h, const OpCoef<float>& l, const float (&pw)[9], DFAcc& a) {
+    mbt_df<C, 0, V>(h, l, pw, a);
+    mbt_df<C, 1, V>(h, l, pw, a);
+    mbt_df<C, 2, V>(h, l, pw, a);
+    mbt_df<C, 3, V>(h, l, pw, a);
+}
+template <int C, int... K, int... V>
+__device__ __forceinline__ void merged_df(int i, int j, int n, const OpCoef<float>& h, const OpCoef<float>& l,
+                                          const float* __restrict__ eu, const float* __restrict__ ep, DFAcc& a,
+                                          std::integer_sequence<int, K...>, std::integer_sequence<int, V...>) {
+    const int n2 = (2 * n + 1) * (2 * n + 1);
+    float wx[25], wy[25], pw[9];
+    win_load<C, true, true, false>(i, j, n, gviewu(eu, 2 * n + 1), gviewu(eu + n2, 2 * n + 1), wx, wy,
+                                   std::make_integer_sequence<int, 25>{});
+    vwin_load<C>(i, j, n, gviewu(ep, n + 1), pw, std::make_integer_sequence<int, 9>{});
+    (win_df<C, K>(h, l, wx, wy, a), ...);
+    (vwin_df<C, V>(h, l, pw, a), ...);
+}
+
 // ---------------------------------------------------------------------------------------------
 // two-float ("double-float") state
 
@@ -129,10 +179,21 @@ __global__ void __launch_bounds__(NT) k_ir_update_df(int n, const __grid_constan
 #pragma unroll
         for (int s = 0; s < 4; ++s) a.au[0][s] = a.au[1][s] = DF{0.f, 0.f};
         a.bu = DF{0.f, 0.f};
-        visit_df<0>(i, j, n, ch, cl, eu, ep, a);
-        visit_df<1>(i, j, n, ch, cl, eu, ep, a);
-        visit_df<2>(i, j, n, ch, cl, eu, ep, a);
-        visit_df<3>(i, j, n, ch, cl, eu, ep, a);
+        const int hh = n >> 1, bi0 = blockIdx.x * blockDim.x, bj0 = blockIdx.y * blockDim.y;
+        const bool single = (hh < bi0 || hh >= bi0 + (int)blockDim.x) && (hh < bj0 || hh >= bj0 + (int)blockDim.y);
+        if (single && block_interior(n, 2)) {
+            if (orient(bi0, bj0, n) == 0)
+                merged_df<0>(i, j, n, ch, cl, eu, ep, a, std::make_integer_sequence<int, 25>{},
+                             std::make_integer_sequence<int, 9>{});
+            else
+                merged_df<1>(i, j, n, ch, cl, eu, ep, a, std::make_integer_sequence<int, 25>{},
+                             std::make_integer_sequence<int, 9>{});
+        } else {
+            visit_df<0>(i, j, n, ch, cl, eu, ep, a);
+            visit_df<1>(i, j, n, ch, cl, eu, ep, a);
+            visit_df<2>(i, j, n, ch, cl, eu, ep, a);
+            visit_df<3>(i, j, n, ch, cl, eu, ep, a);
+        }
         const CellNodes cn = cell_nodes(i, j, n);
         const int ld = 2 * n + 1;
 #pragma unroll

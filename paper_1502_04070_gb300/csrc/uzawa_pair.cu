@@ -151,9 +151,50 @@ __device__ __forceinline__ float b_row(const PairCoef& q, const float2* t0, cons
     return acc.x + acc.y;
 }
 
+// Order in which the CTAs take the tiles: first the tiles whose u^{m-1/2} region meets a mid-line
+// (their cells run the slower per-cell rows), column band then row band, then all others, so that
+// the block scheduler hands the long tiles out first and fills in with short ones.
+struct TileOrder {
+    int cols, rows;   // tiles per row and per column
+    int c0, nc;       // tile columns c0 .. c0 + nc - 1 meet the mid-line x = 1/2
+    int r0, nr;       // tile rows r0 .. r0 + nr - 1 meet y = 1/2
+    __device__ __forceinline__ void tile(int b, int& c, int& r) const {
+        const int na = nc * rows;
+        if (b < na) {
+            c = c0 + b % nc;
+            r = b / nc;
+            return;
+        }
+        b -= na;
+        const int nb = nr * (cols - nc);
+        if (b < nb) {
+            r = r0 + b % nr;
+            const int cc = b / nr;
+            c = cc < c0 ? cc : cc + nc;
+            return;
+        }
+        b -= nb;
+        const int cc = b % (cols - nc), rr = b / (cols - nc);
+        c = cc < c0 ? cc : cc + nc;
+        r = rr < r0 ? rr : rr + nr;
+    }
+};
+
+// tiles of size `len` whose region [t len - 2, t len + len + 2) contains h: first and count
+static void mid_band(int h, int len, int tiles, int& first, int& count) {
+    first = -1;
+    count = 0;
+    for (int t = 0; t < tiles; ++t)
+        if (t * len - 2 <= h && h < t * len + len + 2) {
+            if (first < 0) first = t;
+            ++count;
+        }
+    if (first < 0) first = 0;
+}
+
 template <int NW>
 __global__ void __launch_bounds__(32 * NW, (NW > 4 ? 3 : 6))
-    k_uzawa_pair(int n, int TY, const __grid_constant__ OpCoef<float> c, const __grid_constant__ PairCoef q, float tau,
+    k_uzawa_pair(int n, int TY, TileOrder ord, const __grid_constant__ OpCoef<float> c, const __grid_constant__ PairCoef q, float tau,
                  float sigma, const float* __restrict__ u, const float* __restrict__ p, const float* __restrict__ f,
                  const float* __restrict__ g, const float* __restrict__ sinv, float* __restrict__ u_out,
                  float* __restrict__ p_out) {
@@ -167,7 +208,9 @@ __global__ void __launch_bounds__(32 * NW, (NW > 4 ? 3 : 6))
     float* sP = reinterpret_cast<float*>(sH + 2 * HPL);
     float* sD = sP + G::PW * (TY + 6);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+    int tc, tr;
+    ord.tile(blockIdx.x, tc, tr);
+    const int i0 = tc * TX, j0 = tr * TY;
     const int ld = 2 * n + 1, n2 = ld * ld, h = n >> 1;
     // fast: the u^{m-1/2} region is off the mid-lines, so every cell of the tile has the stencil
     // class of its quadrant; inner: besides, the staged region lies strictly inside the domain, so
@@ -360,9 +403,9 @@ cudaError_t prepare_uzawa_pair() {
     return pair_smem_attr<4>();
 }
 
-// Rows per tile for level size n: the least work on the busiest SM, (tiles per SM, rounded up) x
-// (work of one tile, about ty + 4 rows of the u^{m-1/2} region), among the tile heights that keep
-// at least two CTAs resident per SM.
+// Rows per tile for level size n.  Estimated makespan: the work of all tiles (about ty + 4 rows of
+// the u^{m-1/2} region each, the mid-line tiles counted three times) spread over the SMs, plus
+// three tiles for the last ones to finish; only heights that keep at least two CTAs per SM.
 template <int NW>
 static int pair_rows(int n) {
     static int cache[2][32] = {};
@@ -372,6 +415,7 @@ static int pair_rows(int n) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    sms = std::max(sms, 1);
     const int cols = (n + 1 + PairTile::TX - 1) / PairTile::TX;
     double best = 1e300;
     int best_ty = 16;
@@ -380,9 +424,12 @@ static int pair_rows(int n) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_uzawa_pair<NW>, 32 * NW, PairTile::bytes(ty)) !=
                 cudaSuccess || per_sm < 2)
             continue;
-        const long tiles = (long)cols * ((n + 1 + ty - 1) / ty);
-        const long m = std::max(sms, 1);
-        const double cost = (double)((tiles + m - 1) / m) * (ty + 4);
+        const int rows = (n + 1 + ty - 1) / ty;
+        int c0, nc, r0, nr;
+        mid_band(n / 2, PairTile::TX, cols, c0, nc);
+        mid_band(n / 2, ty, rows, r0, nr);
+        const double mid = (double)nc * rows + (double)nr * (cols - nc);
+        const double cost = ((double)cols * rows + 2.0 * mid) * (ty + 4) / sms + 3.0 * (ty + 4);
         if (cost < best) {
             best = cost;
             best_ty = ty;
@@ -398,9 +445,14 @@ static void launch_pair_v(cudaStream_t s, int n, const OpCoef<float>& c, float t
                           const float* p, const float* f, const float* g, const float* sinv, float* u_out,
                           float* p_out) {
     const int ty = pair_rows<NW>(n);
-    const dim3 grid((n + 1 + PairTile::TX - 1) / PairTile::TX, (n + 1 + ty - 1) / ty), blk(32 * NW);
-    launch_pdl(k_uzawa_pair<NW>, grid, blk, PairTile::bytes(ty), s, n, ty, c, make_pair_coef(c, tau), tau, sigma, u,
-               p, f, g, sinv, u_out, p_out);
+    TileOrder ord;
+    ord.cols = (n + 1 + PairTile::TX - 1) / PairTile::TX;
+    ord.rows = (n + 1 + ty - 1) / ty;
+    mid_band(n / 2, PairTile::TX, ord.cols, ord.c0, ord.nc);
+    mid_band(n / 2, ty, ord.rows, ord.r0, ord.nr);
+    const dim3 grid(ord.cols * ord.rows), blk(32 * NW);
+    launch_pdl(k_uzawa_pair<NW>, grid, blk, PairTile::bytes(ty), s, n, ty, ord, c, make_pair_coef(c, tau), tau,
+               sigma, u, p, f, g, sinv, u_out, p_out);
 }
 
 void launch_uzawa_pair(int variant, cudaStream_t s, int n, const OpCoef<float>& c, float tau, float sigma,
