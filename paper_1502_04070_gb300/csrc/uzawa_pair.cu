@@ -403,9 +403,9 @@ cudaError_t prepare_uzawa_pair() {
     return pair_smem_attr<4>();
 }
 
-// Rows per tile for level size n.  Estimated makespan: the work of all tiles (about ty + 4 rows of
-// the u^{m-1/2} region each, the mid-line tiles counted three times) spread over the SMs, plus
-// three tiles for the last ones to finish; only heights that keep at least two CTAs per SM.
+// Rows per tile for level size n: the least work on the busiest SM, (tiles per SM, rounded up) x
+// (work of one tile, about ty + 4 rows of the u^{m-1/2} region), among the tile heights that keep
+// at least two CTAs resident per SM.
 template <int NW>
 static int pair_rows(int n) {
     static int cache[2][32] = {};
@@ -424,12 +424,8 @@ static int pair_rows(int n) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_uzawa_pair<NW>, 32 * NW, PairTile::bytes(ty)) !=
                 cudaSuccess || per_sm < 2)
             continue;
-        const int rows = (n + 1 + ty - 1) / ty;
-        int c0, nc, r0, nr;
-        mid_band(n / 2, PairTile::TX, cols, c0, nc);
-        mid_band(n / 2, ty, rows, r0, nr);
-        const double mid = (double)nc * rows + (double)nr * (cols - nc);
-        const double cost = ((double)cols * rows + 2.0 * mid) * (ty + 4) / sms + 3.0 * (ty + 4);
+        const long tiles = (long)cols * ((n + 1 + ty - 1) / ty);
+        const double cost = (double)((tiles + sms - 1) / sms) * (ty + 4);
         if (cost < best) {
             best = cost;
             best_ty = ty;
