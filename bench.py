@@ -55,6 +55,9 @@ def parse():
                          "profiler lists every kernel (the device-side loop hides the loop body from it)")
     ap.add_argument("--variant", type=int, default=None,
                     help="kernel modes: force this float32 Uzawa step variant (0-8) on every level")
+    ap.add_argument("--variants", default=None,
+                    help="kernel modes: float32 Uzawa step variant per level, 'k:v,k:v,...' (as the workload's "
+                         "float32_step_variant_per_level reports them); levels not named are autotuned")
     return ap.parse_args()
 
 
@@ -72,10 +75,14 @@ def run_kernel(args):
     g = g - g.mean()
     prec = "mixed" if args.kernel in ("uzawa_f32", "mixed_solve", "ir_steps") else "fp64"
     S = Solver(k + 1, 1e4, precision=prec)
-    if args.variant is not None:
+    if args.variant is not None or args.variants:
         from paper_1502_04070_gb300.solver import set_step_variant
-        for l in range(2, k + 2):
-            set_step_variant(l, args.variant)
+        if args.variant is not None:
+            for l in range(2, k + 2):
+                set_step_variant(l, args.variant)
+        for item in (args.variants.split(",") if args.variants else []):
+            kl, v = item.split(":")
+            set_step_variant(int(kl) + 1, int(v))
     if args.host_loop:
         S.set_timing(True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
