@@ -193,7 +193,7 @@ static void mid_band(int h, int len, int tiles, int& first, int& count) {
 }
 
 template <int NW>
-__global__ void __launch_bounds__(32 * NW, (NW > 4 ? 3 : 6))
+__global__ void __launch_bounds__(32 * NW, (NW > 8 ? 2 : NW > 4 ? 3 : 6))
     k_uzawa_pair(int n, int TY, TileOrder ord, const __grid_constant__ OpCoef<float> c, const __grid_constant__ PairCoef q, float tau,
                  float sigma, const float* __restrict__ u, const float* __restrict__ p, const float* __restrict__ f,
                  const float* __restrict__ g, const float* __restrict__ sinv, float* __restrict__ u_out,
@@ -220,24 +220,34 @@ __global__ void __launch_bounds__(32 * NW, (NW > 4 ? 3 : 6))
     const int cls = orient(i0, j0, n);
 
     // ---- stage u as (u_x, u_y) pairs and p; zero outside the domain and on its boundary
+    // A lane stages lattice columns x = lane + 32 t of every row it takes: the parity plane
+    // (lane & 1) and the plane column (lane >> 1) + 16 t are fixed per lane, so a row costs one
+    // address computation and the loads and stores use constant offsets from it.
     const int X0 = 2 * (i0 - 3), Y0 = 2 * (j0 - 3);
-    for (int y = warp; y < 2 * (TY + 6); y += NW) {
-        const int Y = Y0 + y;
-        for (int x = lane; x < 2 * G::UWH; x += 32) {
-            const int X = X0 + x;
-            float2 v = f2(0.f, 0.f);
-            if (inner || interior2(X, Y, n)) {
-                const int k = Y * ld + X;
-                v = f2(__ldg(u + k), __ldg(u + n2 + k));
+    static_assert(2 * G::UWH == 68 && G::PW == 34, "staging loops below assume 68 lattice columns, 34 vertices");
+    {
+        float2* srow = sU + (lane & 1) * UPL + (lane >> 1);
+        for (int y = warp; y < 2 * (TY + 6); y += NW) {
+            const int Y = Y0 + y;
+            const int k = Y * ld + X0 + lane;
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                if (t == 2 && lane >= 4) break;
+                float2 v = f2(0.f, 0.f);
+                if (inner || interior2(X0 + lane + 32 * t, Y, n)) v = f2(__ldg(u + k + 32 * t), __ldg(u + n2 + k + 32 * t));
+                srow[y * G::UWH + 16 * t] = v;
             }
-            sU[(x & 1) * UPL + y * G::UWH + (x >> 1)] = v;
         }
     }
     for (int y = warp; y < TY + 6; y += NW) {
         const int J = j0 - 3 + y;
-        for (int x = lane; x < G::PW; x += 32) {
-            const int I = i0 - 3 + x;
-            sP[y * G::PW + x] = (inner || (I >= 0 && J >= 0 && I <= n && J <= n)) ? __ldg(p + (J * (n + 1) + I)) : 0.f;
+        const int k = J * (n + 1) + i0 - 3 + lane;
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            if (t == 1 && lane >= 2) break;
+            const int I = i0 - 3 + lane + 32 * t;
+            sP[y * G::PW + lane + 32 * t] =
+                (inner || (I >= 0 && J >= 0 && I <= n && J <= n)) ? __ldg(p + k + 32 * t) : 0.f;
         }
     }
     __syncthreads();
@@ -399,8 +409,9 @@ static cudaError_t pair_smem_attr() {
 
 cudaError_t prepare_uzawa_pair() {
     cudaError_t e = pair_smem_attr<8>();
-    if (e != cudaSuccess) return e;
-    return pair_smem_attr<4>();
+    if (e == cudaSuccess) e = pair_smem_attr<4>();
+    if (e == cudaSuccess) e = pair_smem_attr<12>();
+    return e;
 }
 
 // Rows per tile for level size n: the least work on the busiest SM, (tiles per SM, rounded up) x
@@ -408,9 +419,9 @@ cudaError_t prepare_uzawa_pair() {
 // at least two CTAs resident per SM.
 template <int NW>
 static int pair_rows(int n) {
-    static int cache[2][32] = {};
+    static int cache[3][32] = {};
     const int lv = 31 - __builtin_clz((unsigned)n);
-    int& r = cache[NW > 4][lv & 31];
+    int& r = cache[NW > 8 ? 2 : NW > 4 ? 1 : 0][lv & 31];
     if (r) return r;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -436,11 +447,13 @@ static int pair_rows(int n) {
     return r;
 }
 
+// rows = 0: chosen by pair_rows; otherwise fixed (rows + 4 = NW puts one row of the u^{m-1/2}
+// region on each warp: the shortest CTA, for the small, latency-bound levels)
 template <int NW>
-static void launch_pair_v(cudaStream_t s, int n, const OpCoef<float>& c, float tau, float sigma, const float* u,
-                          const float* p, const float* f, const float* g, const float* sinv, float* u_out,
-                          float* p_out) {
-    const int ty = pair_rows<NW>(n);
+static void launch_pair_v(cudaStream_t s, int n, int rows, const OpCoef<float>& c, float tau, float sigma,
+                          const float* u, const float* p, const float* f, const float* g, const float* sinv,
+                          float* u_out, float* p_out) {
+    const int ty = rows > 0 ? rows : pair_rows<NW>(n);
     TileOrder ord;
     ord.cols = (n + 1 + PairTile::TX - 1) / PairTile::TX;
     ord.rows = (n + 1 + ty - 1) / ty;
@@ -454,8 +467,9 @@ static void launch_pair_v(cudaStream_t s, int n, const OpCoef<float>& c, float t
 void launch_uzawa_pair(int variant, cudaStream_t s, int n, const OpCoef<float>& c, float tau, float sigma,
                        const float* u, const float* p, const float* f, const float* g, const float* sinv,
                        float* u_out, float* p_out) {
-    if (variant == 0) launch_pair_v<8>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
-    else launch_pair_v<4>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
+    if (variant == 0) launch_pair_v<8>(s, n, 0, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
+    else if (variant == 1) launch_pair_v<4>(s, n, 0, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
+    else launch_pair_v<12>(s, n, 8, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
 }
 
 }  // namespace smg
