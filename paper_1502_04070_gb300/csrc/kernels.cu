@@ -276,20 +276,32 @@ __device__ __forceinline__ T ldv(const T* p) {
     else return *p;
 }
 
+// Strides of the arrays a transfer reads and writes, each pointer at the array's (0, 0) entry:
+// the dense level arrays (dense_layout), or the padded shared-memory arrays of the coarse cycle.
+struct XferLayout {
+    int ldf, n2f;   // fine velocity: row stride, component stride
+    int ldpf;       // fine vertex array: row stride
+    int ldc, n2c;   // coarse velocity
+    int ldpc;       // coarse vertex array
+};
+__host__ __device__ __forceinline__ XferLayout dense_layout(int nc) {
+    const int ldf = 4 * nc + 1, ldc = 2 * nc + 1;
+    return XferLayout{ldf, ldf * ldf, 2 * nc + 1, ldc, ldc * ldc, nc + 1};
+}
+
 template <int SQ, bool LDG, typename T>
-__device__ __forceinline__ void restrict_visit(int I, int J, int nc, const T* __restrict__ ru, T (&acc)[2][4]) {
+__device__ __forceinline__ void restrict_visit(int I, int J, int nc, const T* __restrict__ ru, T (&acc)[2][4],
+                                               const XferLayout& lay) {
     const int SI = I - (SQ & 1), SJ = J - (SQ >> 1);
     if (SI < 0 || SJ < 0 || SI >= nc || SJ >= nc) return;
-    const int nf = 2 * nc, ldf = 2 * nf + 1;
-    const size_t n2f = (size_t)ldf * ldf;
     T v[2][4][4];
 #pragma unroll
     for (int fb = 0; fb < 4; ++fb)
 #pragma unroll
         for (int fa = 0; fa < 4; ++fa) {
-            const size_t k = (size_t)(4 * SJ + fb) * ldf + 4 * SI + fa;
+            const int k = (4 * SJ + fb) * lay.ldf + 4 * SI + fa;
             v[0][fb][fa] = ldv<LDG>(ru + k);
-            v[1][fb][fa] = ldv<LDG>(ru + n2f + k);
+            v[1][fb][fa] = ldv<LDG>(ru + lay.n2f + k);
         }
     if (orient(SI, SJ, nc)) restrict_rows<1, SQ, 0>(v, acc);
     else restrict_rows<0, SQ, 0>(v, acc);
@@ -298,45 +310,43 @@ __device__ __forceinline__ void restrict_visit(int I, int J, int nc, const T* __
 // coarse cell (i, j) of level nc: its owned coarse velocity nodes and vertex
 template <bool LDG, typename T>
 __device__ __forceinline__ void restrict_cell(int i, int j, int nc, const T* __restrict__ ru, const T* __restrict__ rp,
-                                              T* __restrict__ fc, T* __restrict__ gc) {
+                                              T* __restrict__ fc, T* __restrict__ gc, const XferLayout& lay) {
     T acc[2][4];
 #pragma unroll
     for (int s = 0; s < 4; ++s) acc[0][s] = acc[1][s] = T(0);
-    restrict_visit<0, LDG>(i, j, nc, ru, acc);
-    restrict_visit<1, LDG>(i, j, nc, ru, acc);
-    restrict_visit<2, LDG>(i, j, nc, ru, acc);
-    restrict_visit<3, LDG>(i, j, nc, ru, acc);
+    restrict_visit<0, LDG>(i, j, nc, ru, acc, lay);
+    restrict_visit<1, LDG>(i, j, nc, ru, acc, lay);
+    restrict_visit<2, LDG>(i, j, nc, ru, acc, lay);
+    restrict_visit<3, LDG>(i, j, nc, ru, acc, lay);
     const CellNodes cn = cell_nodes(i, j, nc);
-    const int ldc = 2 * nc + 1;
-    const size_t n2c = (size_t)ldc * ldc;
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
         if (!slot_exists(cn, s)) continue;
         int X, Y;
         slot_pos(i, j, s, X, Y);
-        const size_t k = (size_t)Y * ldc + X;
+        const int k = Y * lay.ldc + X;
         const bool unk = slot_unknown(cn, s);
         fc[k] = unk ? acc[0][s] : T(0);
-        fc[n2c + k] = unk ? acc[1][s] : T(0);
+        fc[lay.n2c + k] = unk ? acc[1][s] : T(0);
     }
     // P1: the coarse hat function is 1 at (2i, 2j), 1/2 at the fine vertices halfway along the
     // coarse edges through it (horizontal, vertical, and the diagonal of each square whose cut
     // passes through the vertex), 0 elsewhere.
-    const int nf = 2 * nc, ldf = nf + 1;
+    const int nf = 2 * nc, ldf = lay.ldpf;
     const int x = 2 * i, y = 2 * j;
-    T s = rp[(size_t)y * ldf + x];
+    T s = rp[y * ldf + x];
     T half = T(0);
-    if (x > 0) half += rp[(size_t)y * ldf + x - 1];
-    if (x < nf) half += rp[(size_t)y * ldf + x + 1];
-    if (y > 0) half += rp[(size_t)(y - 1) * ldf + x];
-    if (y < nf) half += rp[(size_t)(y + 1) * ldf + x];
+    if (x > 0) half += rp[y * ldf + x - 1];
+    if (x < nf) half += rp[y * ldf + x + 1];
+    if (y > 0) half += rp[(y - 1) * ldf + x];
+    if (y < nf) half += rp[(y + 1) * ldf + x];
     // diagonal neighbours (dx, dy): square (i + min(dx,0), j + min(dy,0)); orientation 0 joins
     // (dx, dy) = (+,+) / (-,-), orientation 1 joins (+,-) / (-,+)
-    if (x < nf && y < nf && orient(i, j, nc) == 0) half += rp[(size_t)(y + 1) * ldf + x + 1];
-    if (x > 0 && y > 0 && orient(i - 1, j - 1, nc) == 0) half += rp[(size_t)(y - 1) * ldf + x - 1];
-    if (x < nf && y > 0 && orient(i, j - 1, nc) == 1) half += rp[(size_t)(y - 1) * ldf + x + 1];
-    if (x > 0 && y < nf && orient(i - 1, j, nc) == 1) half += rp[(size_t)(y + 1) * ldf + x - 1];
-    gc[(size_t)j * (nc + 1) + i] = s + T(0.5) * half;
+    if (x < nf && y < nf && orient(i, j, nc) == 0) half += rp[(y + 1) * ldf + x + 1];
+    if (x > 0 && y > 0 && orient(i - 1, j - 1, nc) == 0) half += rp[(y - 1) * ldf + x - 1];
+    if (x < nf && y > 0 && orient(i, j - 1, nc) == 1) half += rp[(y - 1) * ldf + x + 1];
+    if (x > 0 && y < nf && orient(i - 1, j, nc) == 1) half += rp[(y + 1) * ldf + x - 1];
+    gc[j * lay.ldpc + i] = s + T(0.5) * half;
 }
 
 template <typename T>
@@ -346,7 +356,7 @@ __global__ void __launch_bounds__(NT) k_restrict(int nc, const T* __restrict__ r
     const int n = nc;
     CELL_INDEX
     if (!active) return;
-    restrict_cell<true>(i, j, nc, ru, rp, fc, gc);
+    restrict_cell<true>(i, j, nc, ru, rp, fc, gc, dense_layout(nc));
 }
 
 template <typename T>
@@ -359,16 +369,15 @@ void launch_restrict(cudaStream_t s, int nc, const T* ru, const T* rp, T* fc, T*
 // averages along coarse edges.
 template <bool LDG, typename T>
 __device__ __forceinline__ void prolong_cell(int i, int j, int nc, const T* __restrict__ uc, const T* __restrict__ pc,
-                                             T* __restrict__ u, T* __restrict__ p) {
-    const int nf = 2 * nc, ldf = 2 * nf + 1, ldc = 2 * nc + 1;
-    const size_t n2f = (size_t)ldf * ldf, n2c = (size_t)ldc * ldc;
+                                             T* __restrict__ u, T* __restrict__ p, const XferLayout& lay) {
+    const int nf = 2 * nc;
     if (i < nc && j < nc) {
         T z[2][9];
 #pragma unroll
         for (int m = 0; m < 9; ++m) {
-            const size_t k = (size_t)(2 * j + m / 3) * ldc + 2 * i + m % 3;
+            const int k = (2 * j + m / 3) * lay.ldc + 2 * i + m % 3;
             z[0][m] = ldv<LDG>(uc + k);
-            z[1][m] = ldv<LDG>(uc + n2c + k);
+            z[1][m] = ldv<LDG>(uc + lay.n2c + k);
         }
         const int o = orient(i, j, nc);
 #pragma unroll
@@ -384,20 +393,20 @@ __device__ __forceinline__ void prolong_cell(int i, int j, int nc, const T* __re
                     sx = fma(w, z[0][L], sx);
                     sy = fma(w, z[1][L], sy);
                 }
-                const size_t k = (size_t)Y * ldf + X;
+                const int k = Y * lay.ldf + X;
                 u[k] += sx;
-                u[n2f + k] += sy;
+                u[lay.n2f + k] += sy;
             }
     }
-    const int ldp = nc + 1, ldpf = nf + 1;
-    auto P = [&](int a, int b) { return ldv<LDG>(pc + (size_t)b * ldp + a); };
+    const int ldp = lay.ldpc, ldpf = lay.ldpf;
+    auto P = [&](int a, int b) { return ldv<LDG>(pc + (b * ldp + a)); };
     const T p00 = P(i, j);
-    p[(size_t)(2 * j) * ldpf + 2 * i] += p00;
-    if (i < nc) p[(size_t)(2 * j) * ldpf + 2 * i + 1] += T(0.5) * (p00 + P(i + 1, j));
-    if (j < nc) p[(size_t)(2 * j + 1) * ldpf + 2 * i] += T(0.5) * (p00 + P(i, j + 1));
+    p[(2 * j) * ldpf + 2 * i] += p00;
+    if (i < nc) p[(2 * j) * ldpf + 2 * i + 1] += T(0.5) * (p00 + P(i + 1, j));
+    if (j < nc) p[(2 * j + 1) * ldpf + 2 * i] += T(0.5) * (p00 + P(i, j + 1));
     if (i < nc && j < nc) {
         const T d = orient(i, j, nc) == 0 ? p00 + P(i + 1, j + 1) : P(i + 1, j) + P(i, j + 1);
-        p[(size_t)(2 * j + 1) * ldpf + 2 * i + 1] += T(0.5) * d;
+        p[(2 * j + 1) * ldpf + 2 * i + 1] += T(0.5) * d;
     }
 }
 
@@ -408,7 +417,7 @@ __global__ void __launch_bounds__(NT) k_prolong(int nc, const T* __restrict__ uc
     const int n = nc;
     CELL_INDEX
     if (!active) return;
-    prolong_cell<true>(i, j, nc, uc, pc, u, p);
+    prolong_cell<true>(i, j, nc, uc, pc, u, p, dense_layout(nc));
 }
 
 template <typename T>
