@@ -283,10 +283,14 @@ void record_step(stokes_handle* h) {
         // x += e, r -= A e (two-float residual, error-free float32 products), r32 = float(r)
         const int k = ev_begin(h);
         if (k >= 0) h->ev_resid++;
-        launch_ir_update_df(h->st, F.n, h->chi, h->clo, E.u, E.p, F.u, F.p, F.tu, F.tp, E.f, E.g, h->partial);
+        // the same pass leaves the partial sums of the zero-mean projection of x_p (second half)
+        const int nb = cells_blocks(F.n);
+        launch_ir_update_df(h->st, F.n, h->chi, h->clo, E.u, E.p, F.u, F.p, F.tu, F.tp, E.f, E.g, h->partial,
+                            h->partial + nb);
         ev_end(h, k);
-        launch_reduce(h->st, h->partial, cells_blocks(F.n), h->scal);
-        launch_pmean<double>(h->st, F.n, F.p, h->partial, h->scal + 1);
+        launch_reduce(h->st, h->partial, nb, h->scal);
+        launch_reduce(h->st, h->partial + nb, nb, h->scal + 1);
+        launch_psub<double>(h->st, F.n, F.p, h->scal + 1);
     } else {
         mg_cycle<double>(h, h->h64, h->L - 1);
         launch_pmean<double>(h->st, F.n, F.p, h->partial, h->scal + 1);
@@ -553,7 +557,7 @@ stokes_status stokes_setup(const stokes_params* prm, void* stream, stokes_handle
             if ((s = alloc_level(h->h32[k], k)) != STOKES_OK) return bail(s);
     }
     h->mass = make_mass<double>(h->fin().n);
-    h->npartial = cells_blocks(h->fin().n);
+    h->npartial = 2 * cells_blocks(h->fin().n);   // two sets of per-block partial sums (refinement update)
     if (cudaMalloc(&h->inv, 27 * 27 * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&h->partial, (size_t)h->npartial * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&h->scal, 8 * sizeof(double)) != cudaSuccess ||

@@ -157,6 +157,20 @@ __host__ __device__ __forceinline__ int orient(int si, int sj, int n) {
     return (si < h) != (sj < h);
 }
 
+// w_i = int psi_i = (number of triangles at vertex i) h^2 / 6: the pressure-mean weight (M_P 1)_i
+__device__ __forceinline__ double vertex_weight(int i, int j, int n) {
+    int cnt = 0;
+#pragma unroll
+    for (int SQ = 0; SQ < 4; ++SQ) {
+        const int si = i - (SQ & 1), sj = j - (SQ >> 1);
+        if (si < 0 || sj < 0 || si >= n || sj >= n) continue;
+        const int o = orient(si, sj, n), node = corner_node(SQ);
+        cnt += ((tri_mask(o, 0) >> node) & 1u) + ((tri_mask(o, 1) >> node) & 1u);
+    }
+    const double h = 1.0 / n;
+    return cnt * h * h / 6.0;
+}
+
 // stencil class (see stencil_pattern) of cell (i, j) of a level with N = n
 __host__ __device__ __forceinline__ int stencil_class(int i, int j, int n) {
     const int h = n >> 1;

@@ -520,19 +520,6 @@ void launch_schur_diag(cudaStream_t s, int n, const OpCoef<double>& c, T* sinv) 
 }
 
 // ------------------------------------------------------------------------------------------
-// w_i = int psi_i = (number of triangles at vertex i) h^2 / 6
-__device__ __forceinline__ double vertex_weight(int i, int j, int n) {
-    int cnt = 0;
-#pragma unroll
-    for (int SQ = 0; SQ < 4; ++SQ) {
-        const int si = i - (SQ & 1), sj = j - (SQ >> 1);
-        if (si < 0 || sj < 0 || si >= n || sj >= n) continue;
-        const int o = orient(si, sj, n), node = corner_node(SQ);
-        cnt += ((tri_mask(o, 0) >> node) & 1u) + ((tri_mask(o, 1) >> node) & 1u);
-    }
-    const double h = 1.0 / n;
-    return cnt * h * h / 6.0;
-}
 
 template <typename T>
 __global__ void __launch_bounds__(NT) k_pmean_partial(int n, const T* __restrict__ p, double* __restrict__ partial) {
@@ -578,6 +565,12 @@ void launch_pmean(cudaStream_t s, int n, T* p, double* partial, double* scalar) 
     launch_pdl(k_reduce, 1, 1024, 0, s, partial, grid.x * grid.y, scalar);
     launch_pdl(k_psub<T>, grid, blk, 0, s, n, p, scalar);
 }
+
+template <typename T>
+void launch_psub(cudaStream_t s, int n, T* p, const double* scalar) {
+    launch_pdl(k_psub<T>, cells_grid(n), dim3(BX, BY), 0, s, n, p, scalar);
+}
+template void launch_psub<double>(cudaStream_t, int, double*, const double*);
 
 // ------------------------------------------------------------------------------------------
 // load vectors (data f, g of Sec. 1 given by nodal values)

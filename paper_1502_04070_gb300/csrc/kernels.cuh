@@ -34,7 +34,10 @@ void launch_uzawa(cudaStream_t s, int n, const OpCoef<T>& c, T tau, T sigma, T* 
 //   partial sums of r.r.
 void launch_ir_update_df(cudaStream_t s, int n, const OpCoef<float>& chi, const OpCoef<float>& clo,
                          const float* eu, const float* ep, double* xu, double* xp, double* ru, double* rp,
-                         float* r32u, float* r32p, double* partial);
+                         float* r32u, float* r32p, double* partial, double* wpartial);
+// p -= *scalar on every vertex (the zero-mean projection once the weighted mean is reduced)
+template <typename T>
+void launch_psub(cudaStream_t s, int n, T* p, const double* scalar);
 void launch_residual_df(cudaStream_t s, int n, const OpCoef<double>& c, const double* u, const double* p,
                         const double* f, const double* g, double* ru, double* rp, float* r32u, float* r32p,
                         double* partial);

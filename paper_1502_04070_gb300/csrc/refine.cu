@@ -169,11 +169,12 @@ __global__ void __launch_bounds__(NT) k_ir_update_df(int n, const __grid_constan
                                                      double* __restrict__ xu, double* __restrict__ xp,
                                                      float2* __restrict__ ru, float2* __restrict__ rp,
                                                      float* __restrict__ r32u, float* __restrict__ r32p,
-                                                     double* __restrict__ partial) {
+                                                     double* __restrict__ partial, double* __restrict__ wpartial) {
     pdl_enter();
     CELL_INDEX
     const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
     float ss = 0.f;
+    double wp = 0.0;   // w_i x_p,i of the updated pressure (the zero-mean projection's numerator)
     if (active) {
         DFAcc a;
 #pragma unroll
@@ -213,7 +214,9 @@ __global__ void __launch_bounds__(NT) k_ir_update_df(int n, const __grid_constan
             }
         }
         const size_t vi = (size_t)j * (n + 1) + i;
-        xp[vi] += (double)ep[vi];
+        const double xpn = xp[vi] + (double)ep[vi];
+        xp[vi] = xpn;
+        wp = vertex_weight(i, j, n) * xpn;
         const float2 r = df_sub(rp[vi], a.bu);
         rp[vi] = r;
         r32p[vi] = r.x;
@@ -221,6 +224,9 @@ __global__ void __launch_bounds__(NT) k_ir_update_df(int n, const __grid_constan
     }
     const double t = block_sum2d((double)ss, tid);
     if (tid == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = t;
+    __syncthreads();   // block_sum2d's shared scratch is reused below
+    const double tw = block_sum2d(wp, tid);
+    if (tid == 0) wpartial[blockIdx.y * gridDim.x + blockIdx.x] = tw;
 }
 
 // true float64 residual r = F - A x (x, F float64), written as two-float r and float32 r32
@@ -270,9 +276,9 @@ __global__ void __launch_bounds__(NT) k_residual_df(int n, const __grid_constant
 
 void launch_ir_update_df(cudaStream_t s, int n, const OpCoef<float>& chi, const OpCoef<float>& clo,
                          const float* eu, const float* ep, double* xu, double* xp, double* ru, double* rp,
-                         float* r32u, float* r32p, double* partial) {
-    launch_pdl(k_ir_update_df, cells_grid(n), dim3(BX, BY), 0, s, n, chi, clo, eu, ep, xu, xp, reinterpret_cast<float2*>(ru),
-                                                          reinterpret_cast<float2*>(rp), r32u, r32p, partial);
+                         float* r32u, float* r32p, double* partial, double* wpartial) {
+    launch_pdl(k_ir_update_df, cells_grid(n), dim3(BX, BY), 0, s, n, chi, clo, eu, ep, xu, xp,
+               reinterpret_cast<float2*>(ru), reinterpret_cast<float2*>(rp), r32u, r32p, partial, wpartial);
 }
 
 void launch_residual_df(cudaStream_t s, int n, const OpCoef<double>& c, const double* u, const double* p,
