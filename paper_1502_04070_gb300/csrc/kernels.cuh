@@ -53,10 +53,6 @@ void launch_uzawa_pair(int variant, cudaStream_t s, int n, const OpCoef<float>& 
                        const float* u, const float* p, const float* f, const float* g, const float* sinv,
                        float* u_out, float* p_out);
 cudaError_t prepare_uzawa_pair();
-// The float32 three-kernel step with two vertically adjacent cells per thread (uzawa_twocell.cu);
-// updates (u, p) in place with (uh, dp) as scratch.
-void launch_uzawa_twocell(cudaStream_t s, int n, const OpCoef<float>& c, float tau, float sigma, float* u, float* p,
-                          const float* f, const float* g, const float* sinv, float* uh, float* dp);
 template <typename T>
 cudaError_t launch_uzawa_fused(cudaStream_t s, int n, const OpCoef<T>& c, T tau, T sigma, const T* u, const T* p,
                                const T* f, const T* g, const T* sinv, T* u_out, T* p_out);

@@ -166,11 +166,9 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 4 ? 2 : 1)) k_uzawa_fuse
 // 6: 8 x 8.  Fused step on component-pair tiles with packed FP32x2 arithmetic (uzawa_pair.cu):
 // 7: 28 cells wide, 8 warps, height chosen per level; 8: the same with 4 warps; 9: 28 x 8 cells,
 // 12 warps (one row of the u^{m-1/2} region per warp: shortest CTAs, for small levels).
-// 10: three-kernel step with two vertically adjacent cells per thread (uzawa_twocell.cu).
 constexpr int kFusedVariants = 4;
 constexpr int kPairVariant0 = 7;
-constexpr int kTwoCellVariant = 10;
-constexpr int kStepVariants = 11;
+constexpr int kStepVariants = 10;
 // per level k (N = 2^(k+1)): chosen variant; until tuned, the three-kernel step below N = 128 and the
 // 32 x 16 fused tile from N = 128 up
 static int g_tile_choice[32] = {5, 5, 5, 5, 5, 5, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0,
@@ -233,10 +231,6 @@ static bool launch_step_variant(int v, cudaStream_t s, int n, const OpCoef<float
     if (v < kFusedVariants) {
         launch_variant<float>(v, s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
         return true;
-    }
-    if (v == kTwoCellVariant) {
-        launch_uzawa_twocell(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
-        return false;
     }
     if (v >= kPairVariant0) {
         launch_uzawa_pair(v - kPairVariant0, s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
