@@ -82,8 +82,9 @@ __global__ void __launch_bounds__(NT) k_residual(int n, const __grid_constant__ 
     }
 }
 
+// float32: four CTAs per SM (64 registers; a few spilled) for more loads in flight
 template <typename T>
-__global__ void __launch_bounds__(NT) k_uzawa_u(int n, const __grid_constant__ OpCoef<T> c, T tau,
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 1) k_uzawa_u(int n, const __grid_constant__ OpCoef<T> c, T tau,
                                                 const T* __restrict__ u, const T* __restrict__ p,
                                                 const T* __restrict__ f, T* __restrict__ uh) {
     pdl_enter();
