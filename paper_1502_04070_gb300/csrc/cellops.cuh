@@ -353,6 +353,28 @@ __device__ __forceinline__ bool slot_unknown(const CellNodes& cn, int s) {
     const int tid = threadIdx.y * blockDim.x + threadIdx.x; \
     (void)tid;
 
+// Block sums of two doubles at once (one barrier); results valid in tid 0.
+__device__ __forceinline__ double2 block_sum2d_pair(double a, double b, int tid) {
+    __shared__ double2 red2[NT / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if ((tid & 31) == 0) red2[tid >> 5] = make_double2(a, b);
+    __syncthreads();
+    double2 s = make_double2(0.0, 0.0);
+    if (tid < 32) {
+        s = tid < NT / 32 ? red2[tid] : make_double2(0.0, 0.0);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s.x += __shfl_down_sync(0xffffffffu, s.x, o);
+            s.y += __shfl_down_sync(0xffffffffu, s.y, o);
+        }
+    }
+    return s;
+}
+
 // Block sum (thread-linear id tid) of one double; result valid in tid 0.
 __device__ __forceinline__ double block_sum2d(double v, int tid) {
     __shared__ double red[NT / 32];

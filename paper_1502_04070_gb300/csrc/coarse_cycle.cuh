@@ -90,17 +90,19 @@ __device__ __forceinline__ void cc_cell(int q, int n, int& i, int& j, int& cls) 
     cls = 2;
 }
 
-// Rows of a cell of any stencil class k, as rolled loops over the full 5 x 5 and 3 x 3 windows:
-// little code for the mid-line cells (the whole cycle of this kernel runs on one SM, whose
-// instruction cache it has to fit).
+// Rows of a cell of any stencil class k (known at run time) over the full 5 x 5 and 3 x 3 windows,
+// zero coefficients included: one body for the five mid-line classes, so that the code stays
+// within the instruction cache of the one SM that runs the whole cycle.  The loops are unrolled:
+// a mid-line warp works on every phase of every level, and a rolled loop of dependent loads made
+// it the slowest warp of each phase.
 template <bool DA, bool DBT, bool DB, bool DD>
-__device__ __noinline__ void cc_apply_rolled(int i, int j, int k, const OpCoef<float>& c, const float* ux,
+__device__ __noinline__ void cc_apply_dense(int i, int j, int k, const OpCoef<float>& c, const float* ux,
                                              const float* uy, int ld, const float* vp, int ldv, Acc<float>& a) {
 #pragma unroll
     for (int s = 0; s < 4; ++s) a.au[0][s] = a.au[1][s] = a.bt[0][s] = a.bt[1][s] = a.idg[s] = 0.f;
     a.bu = 0.f;
     if constexpr (DA || DB) {
-#pragma unroll 1
+#pragma unroll
         for (int w = 0; w < 25; ++w) {
             const int o = (2 * j + w / 5 - 2) * ld + 2 * i + w % 5 - 2;
             const float vx = ux[o], vy = uy[o];
@@ -115,7 +117,7 @@ __device__ __noinline__ void cc_apply_rolled(int i, int j, int k, const OpCoef<f
         }
     }
     if constexpr (DBT) {
-#pragma unroll 1
+#pragma unroll
         for (int v = 0; v < 9; ++v) {
             const float pv = vp[(j + v / 3 - 1) * ldv + i + v % 3 - 1];
 #pragma unroll
@@ -145,7 +147,7 @@ __device__ __forceinline__ void cc_apply(int q, const CCLevel& L, const OpCoef<f
         cell_apply_merged<DA, DBT, DB, DD, false, 1>(i, j, n, c, PViewU<float>{ux, L.ldu}, PViewU<float>{uy, L.ldu},
                                                      PViewU<float>{vp, L.ldv}, a);
     } else {
-        cc_apply_rolled<DA, DBT, DB, DD>(i, j, stencil_class(i, j, n), c, ux, uy, L.ldu, vp, L.ldv, a);
+        cc_apply_dense<DA, DBT, DB, DD>(i, j, stencil_class(i, j, n), c, ux, uy, L.ldu, vp, L.ldv, a);
     }
 }
 

@@ -222,11 +222,11 @@ __global__ void __launch_bounds__(NT) k_ir_update_df(int n, const __grid_constan
         r32p[vi] = r.x;
         ss = fmaf(r.x, r.x, ss);
     }
-    const double t = block_sum2d((double)ss, tid);
-    if (tid == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = t;
-    __syncthreads();   // block_sum2d's shared scratch is reused below
-    const double tw = block_sum2d(wp, tid);
-    if (tid == 0) wpartial[blockIdx.y * gridDim.x + blockIdx.x] = tw;
+    const double2 t = block_sum2d_pair((double)ss, wp, tid);
+    if (tid == 0) {
+        partial[blockIdx.y * gridDim.x + blockIdx.x] = t.x;
+        wpartial[blockIdx.y * gridDim.x + blockIdx.x] = t.y;
+    }
 }
 
 // true float64 residual r = F - A x (x, F float64), written as two-float r and float32 r32
