@@ -46,6 +46,10 @@ __device__ __forceinline__ void pdl_enter() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
+// Programmatic dependent launch is on unless the environment sets STOKES_MG_PDL=0 (read once per
+// process): with many independent solves in flight, CTAs launched early only wait on their SMs.
+bool pdl_enabled();
+
 template <typename... KArgs, typename... Args>
 inline void launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
     cudaLaunchConfig_t cfg = {};
@@ -57,7 +61,7 @@ inline void launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, 
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
     cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
 }
 

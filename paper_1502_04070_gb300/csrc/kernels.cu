@@ -6,6 +6,7 @@
 // meets one of the mid-lines x = 1/2, y = 1/2), with structurally-zero entries removed at compile
 // time.  Blocks whose cells all lie at least two cells inside the boundary read without any test.
 #include <cstdio>
+#include <cstdlib>
 
 #include "cellops.cuh"
 #include "kernels.cuh"
@@ -13,6 +14,14 @@
 namespace smg {
 
 int cells_blocks(int n) { return ((n + 1 + BX - 1) / BX) * ((n + 1 + BY - 1) / BY); }
+
+bool pdl_enabled() {
+    static const bool on = [] {
+        const char* e = std::getenv("STOKES_MG_PDL");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
 
 __constant__ double c_W2d[2][9][5][5];
 __constant__ float c_W2f[2][9][5][5];
