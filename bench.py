@@ -427,8 +427,12 @@ def run_ours(args, rank, world, local_rank):
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tpath):
         try:
+            # DRAM bytes per launch from an ncu capture, per float32 step variant of the finest level
+            # (the autotuner's choice can differ between runs); only while the kernel sources match
             tj = json.load(open(tpath))
             ent = tj.get(args.precision, {}).get(dom)
+            if ent and "variants" in ent:
+                ent = ent["variants"].get(str(variants.get("k=%d" % K_LEVEL)))
             if ent and ent.get("source_sha") == _kernel_source_sha():
                 traffic = ent["bytes_per_launch"]
         except Exception:
