@@ -3,7 +3,6 @@
 // A "view" maps P2-lattice coordinates (X, Y) (or vertex coordinates for pressure) to values; the
 // same row code reads global memory through the read-only path or a shared-memory tile.
 #pragma once
-#include <type_traits>
 #include <utility>
 
 #include "common.cuh"
@@ -102,35 +101,6 @@ struct GViewU {
 };
 template <typename T>
 __device__ __forceinline__ GViewU<T> gviewu(const T* p, int ld) { return GViewU<T>{p, ld}; }
-
-// The same unchecked reads, for a component array whose element (X, Y) has the parity of
-// PAR + X + Y within an 8- (float) or 16-byte (double) aligned allocation (the dense layout has
-// odd row and component strides): on every window row, two adjacent points that start on an even
-// element come in one vector load (row_pairs below).
-template <typename T, int PAR>
-struct GViewP {
-    static constexpr bool zero_filled = true;
-    static constexpr bool paired = true;
-    static constexpr int parity = PAR;
-    const T* p;
-    int ld;
-    __device__ __forceinline__ T operator()(int X, int Y) const { return __ldg(p + (Y * ld + X)); }
-    __device__ __forceinline__ T at(int si, int sj, int a, int b) const {
-        return __ldg(p + ((2 * sj + b) * ld + 2 * si + a));
-    }
-    __device__ __forceinline__ const T* row(int X, int Y) const { return p + (Y * ld + X); }
-};
-template <int PAR, typename T>
-__device__ __forceinline__ GViewP<T, PAR> gviewp(const T* p, int ld) { return GViewP<T, PAR>{p, ld}; }
-
-template <typename V, typename = void>
-struct paired_view : std::false_type {};
-template <typename V>
-struct paired_view<V, std::void_t<decltype(V::paired)>> : std::bool_constant<V::paired> {};
-
-template <typename T> struct Pair2;
-template <> struct Pair2<float> { using type = float2; };
-template <> struct Pair2<double> { using type = double2; };
 
 // True when every cell (i, j) of this block has m <= i, j <= n - m (block-uniform).  Margin 1: the
 // windows stay inside the arrays; margin 2: they also avoid the Dirichlet ring.
@@ -249,8 +219,8 @@ __host__ __device__ constexpr bool need_vwin(int C, int v) {
     return nz_MBT(C, 0, v) || nz_MBT(C, 1, v) || nz_MBT(C, 2, v) || nz_MBT(C, 3, v);
 }
 
-template <int C, bool DA, bool DB, bool MASK, int W, typename T, typename VU, typename VUY>
-__device__ __forceinline__ void win_load1(int i, int j, int n, const VU& ux, const VUY& uy, T (&wx)[25], T (&wy)[25]) {
+template <int C, bool DA, bool DB, bool MASK, int W, typename T, typename VU>
+__device__ __forceinline__ void win_load1(int i, int j, int n, const VU& ux, const VU& uy, T (&wx)[25], T (&wy)[25]) {
     if constexpr (need_win(C, DA, DB, W)) {
         constexpr int dx = W % 5 - 2, dy = W / 5 - 2;
         if constexpr (VU::zero_filled && !MASK) {
@@ -264,59 +234,10 @@ __device__ __forceinline__ void win_load1(int i, int j, int n, const VU& ux, con
         }
     }
 }
-template <int C, bool DA, bool DB, bool MASK, typename T, typename VU, typename VUY, int... W>
-__device__ __forceinline__ void win_load(int i, int j, int n, const VU& ux, const VUY& uy, T (&wx)[25], T (&wy)[25],
+template <int C, bool DA, bool DB, bool MASK, typename T, typename VU, int... W>
+__device__ __forceinline__ void win_load(int i, int j, int n, const VU& ux, const VU& uy, T (&wx)[25], T (&wy)[25],
                                          std::integer_sequence<int, W...>) {
     (win_load1<C, DA, DB, MASK, W>(i, j, n, ux, uy, wx, wy), ...);
-}
-
-// One window row DY of one component through a paired view: the points dx = -2..2 of row
-// Y = 2j + DY in vector loads where the pair starts on an even element.
-template <int C, bool DA, bool DB, int DY, typename T, typename V>
-__device__ __forceinline__ void row_pairs(int i, int j, const V& v, T (&w)[25]) {
-    using P = typename Pair2<T>::type;
-    constexpr int b = (DY + 2) * 5;
-    constexpr bool n0 = need_win(C, DA, DB, b), n1 = need_win(C, DA, DB, b + 1), n2 = need_win(C, DA, DB, b + 2),
-                   n3 = need_win(C, DA, DB, b + 3), n4 = need_win(C, DA, DB, b + 4);
-    const T* r = v.row(2 * i, 2 * j + DY);
-    if constexpr (((V::parity + DY) & 1) == 0) {   // pairs at dx = -2 and 0, single at 2
-        if constexpr (n0 || n1) {
-            const P q = __ldg(reinterpret_cast<const P*>(r - 2));
-            w[b] = q.x;
-            w[b + 1] = q.y;
-        }
-        if constexpr (n2 || n3) {
-            const P q = __ldg(reinterpret_cast<const P*>(r));
-            w[b + 2] = q.x;
-            w[b + 3] = q.y;
-        }
-        if constexpr (n4) w[b + 4] = __ldg(r + 2);
-    } else {                                        // single at dx = -2, pairs at -1 and 1
-        if constexpr (n0) w[b] = __ldg(r - 2);
-        if constexpr (n1 || n2) {
-            const P q = __ldg(reinterpret_cast<const P*>(r - 1));
-            w[b + 1] = q.x;
-            w[b + 2] = q.y;
-        }
-        if constexpr (n3 || n4) {
-            const P q = __ldg(reinterpret_cast<const P*>(r + 1));
-            w[b + 3] = q.x;
-            w[b + 4] = q.y;
-        }
-    }
-}
-template <int C, bool DA, bool DB, typename T, typename VU, typename VUY>
-__device__ __forceinline__ void win_load_paired(int i, int j, const VU& ux, const VUY& uy, T (&wx)[25], T (&wy)[25]) {
-    row_pairs<C, DA, DB, -2>(i, j, ux, wx);
-    row_pairs<C, DA, DB, -1>(i, j, ux, wx);
-    row_pairs<C, DA, DB, 0>(i, j, ux, wx);
-    row_pairs<C, DA, DB, 1>(i, j, ux, wx);
-    row_pairs<C, DA, DB, 2>(i, j, ux, wx);
-    row_pairs<C, DA, DB, -2>(i, j, uy, wy);
-    row_pairs<C, DA, DB, -1>(i, j, uy, wy);
-    row_pairs<C, DA, DB, 0>(i, j, uy, wy);
-    row_pairs<C, DA, DB, 1>(i, j, uy, wy);
-    row_pairs<C, DA, DB, 2>(i, j, uy, wy);
 }
 
 template <int C, int V, typename T, typename VP>
@@ -375,14 +296,11 @@ __device__ __forceinline__ T mb_row_i(const OpCoef<T>& c, const T (&wx)[25], con
     return s;
 }
 
-template <bool DA, bool DBT, bool DB, bool DD, bool MASK, int C, typename T, typename VU, typename VUY, typename VP>
-__device__ __forceinline__ void cell_apply_merged(int i, int j, int n, const OpCoef<T>& c, const VU& ux, const VUY& uy,
+template <bool DA, bool DBT, bool DB, bool DD, bool MASK, int C, typename T, typename VU, typename VP>
+__device__ __forceinline__ void cell_apply_merged(int i, int j, int n, const OpCoef<T>& c, const VU& ux, const VU& uy,
                                                   const VP& p, Acc<T>& a) {
     T wx[25], wy[25], pw[9];
-    if constexpr ((DA || DB) && paired_view<VU>::value && paired_view<VUY>::value)
-        win_load_paired<C, DA, DB>(i, j, ux, uy, wx, wy);
-    else if constexpr (DA || DB)
-        win_load<C, DA, DB, MASK>(i, j, n, ux, uy, wx, wy, std::make_integer_sequence<int, 25>{});
+    if constexpr (DA || DB) win_load<C, DA, DB, MASK>(i, j, n, ux, uy, wx, wy, std::make_integer_sequence<int, 25>{});
     if constexpr (DBT) vwin_load<C>(i, j, n, p, pw, std::make_integer_sequence<int, 9>{});
 #pragma unroll
     for (int s = 0; s < 4; ++s) a.au[0][s] = a.au[1][s] = a.bt[0][s] = a.bt[1][s] = a.idg[s] = T(0);
@@ -408,8 +326,8 @@ __device__ __forceinline__ void cell_apply_merged(int i, int j, int n, const OpC
 
 // Operator rows of cell (i, j) from the merged stencils of its class (branch uniform across a warp
 // except where the warp meets a mid-line).
-template <bool DA, bool DBT, bool DB, bool DD, bool MASK, typename T, typename VU, typename VUY, typename VP>
-__device__ __forceinline__ void cell_apply_auto(int i, int j, int n, const OpCoef<T>& c, const VU& ux, const VUY& uy,
+template <bool DA, bool DBT, bool DB, bool DD, bool MASK, typename T, typename VU, typename VP>
+__device__ __forceinline__ void cell_apply_auto(int i, int j, int n, const OpCoef<T>& c, const VU& ux, const VU& uy,
                                                 const VP& p, Acc<T>& a) {
     switch (stencil_class(i, j, n)) {
         case 0: cell_apply_merged<DA, DBT, DB, DD, MASK, 0>(i, j, n, c, ux, uy, p, a); break;

@@ -15,13 +15,6 @@ namespace smg {
 
 int cells_blocks(int n) { return ((n + 1 + BX - 1) / BX) * ((n + 1 + BY - 1) / BY); }
 
-// Paired window loads (GViewP) read two elements at once and need the array's base aligned to
-// two elements; the level arrays are, a caller's array may not be.
-template <typename T>
-static bool pairs_ok(const T* p) {
-    return (reinterpret_cast<uintptr_t>(p) % (2 * sizeof(T))) == 0;
-}
-
 bool pdl_enabled() {
     static const bool on = [] {
         const char* e = std::getenv("STOKES_MG_PDL");
@@ -53,17 +46,14 @@ __global__ void __launch_bounds__(NT) k_residual(int n, const __grid_constant__ 
                                                  const T* __restrict__ f, const T* __restrict__ g,
                                                  TO* __restrict__ ru, TO* __restrict__ rp,
                                                  double* __restrict__ partial, float* __restrict__ ru2,
-                                                 float* __restrict__ rp2, bool paired) {
+                                                 float* __restrict__ rp2) {
     pdl_enter();
     CELL_INDEX
     const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
     double ss = 0.0;
     if (active) {
         Acc<T> a;
-        if (block_interior(n, 2) && paired)
-            cell_apply_auto<true, true, true, false, false>(i, j, n, c, gviewp<0>(u, 2 * n + 1), gviewp<1>(u + n2, 2 * n + 1),
-                                                            gviewu(p, n + 1), a);
-        else if (block_interior(n, 2))
+        if (block_interior(n, 2))
             cell_apply_auto<true, true, true, false, false>(i, j, n, c, gviewu(u, 2 * n + 1), gviewu(u + n2, 2 * n + 1),
                                                             gviewu(p, n + 1), a);
         else
@@ -105,16 +95,13 @@ __global__ void __launch_bounds__(NT) k_residual(int n, const __grid_constant__ 
 template <typename T>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 1) k_uzawa_u(int n, const __grid_constant__ OpCoef<T> c, T tau,
                                                 const T* __restrict__ u, const T* __restrict__ p,
-                                                const T* __restrict__ f, T* __restrict__ uh, bool paired) {
+                                                const T* __restrict__ f, T* __restrict__ uh) {
     pdl_enter();
     CELL_INDEX
     if (!active) return;
     const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
     Acc<T> a;
-    if (block_interior(n, 2) && paired)
-        cell_apply_auto<true, true, false, true, false>(i, j, n, c, gviewp<0>(u, 2 * n + 1), gviewp<1>(u + n2, 2 * n + 1),
-                                                        gviewu(p, n + 1), a);
-    else if (block_interior(n, 2))
+    if (block_interior(n, 2))
         cell_apply_auto<true, true, false, true, false>(i, j, n, c, gviewu(u, 2 * n + 1), gviewu(u + n2, 2 * n + 1),
                                                         gviewu(p, n + 1), a);
     else
@@ -141,17 +128,13 @@ template <typename T>
 __global__ void __launch_bounds__(NT) k_uzawa_p(int n, const __grid_constant__ OpCoef<T> c, T sigma,
                                                 const T* __restrict__ uh, T* __restrict__ p,
                                                 const T* __restrict__ g, const T* __restrict__ sinv,
-                                                T* __restrict__ dp, bool paired) {
+                                                T* __restrict__ dp) {
     pdl_enter();
     CELL_INDEX
     if (!active) return;
     const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
     Acc<T> a;
-    if (block_interior(n, 1) && paired)
-        cell_apply_auto<false, false, true, false, false>(i, j, n, c, gviewp<0>(uh, 2 * n + 1),
-                                                          gviewp<1>(uh + n2, 2 * n + 1),
-                                                          gviewu((const T*)nullptr, n + 1), a);
-    else if (block_interior(n, 1))
+    if (block_interior(n, 1))
         cell_apply_auto<false, false, true, false, false>(i, j, n, c, gviewu(uh, 2 * n + 1), gviewu(uh + n2, 2 * n + 1),
                                                           gviewu((const T*)nullptr, n + 1), a);
     else
@@ -201,8 +184,8 @@ template <typename T>
 void launch_uzawa(cudaStream_t s, int n, const OpCoef<T>& c, T tau, T sigma, T* u, T* p, const T* f,
                   const T* g, const T* sinv, T* uh, T* dp, int bx, int by) {
     const dim3 blk(bx, by), grid((n + 1 + bx - 1) / bx, (n + 1 + by - 1) / by);
-    launch_pdl(k_uzawa_u<T>, grid, blk, 0, s, n, c, tau, u, p, f, uh, pairs_ok(u));
-    launch_pdl(k_uzawa_p<T>, grid, blk, 0, s, n, c, sigma, uh, p, g, sinv, dp, pairs_ok(uh));
+    launch_pdl(k_uzawa_u<T>, grid, blk, 0, s, n, c, tau, u, p, f, uh);
+    launch_pdl(k_uzawa_p<T>, grid, blk, 0, s, n, c, sigma, uh, p, g, sinv, dp);
     launch_pdl(k_uzawa_u2<T>, grid, blk, 0, s, n, c, tau, uh, dp, u);
 }
 
@@ -264,7 +247,7 @@ template <typename T>
 void launch_normal_eq(cudaStream_t s, int n, const OpCoef<T>& c, T tau, T* u, T* p, const T* f,
                       const T* g, const T* sinv, T* zu, T* zp) {
     const dim3 grid = cells_grid(n), blk(BX, BY);
-    launch_pdl(k_residual<T, T>, grid, blk, 0, s, n, c, u, p, f, g, zu, zp, nullptr, nullptr, nullptr, pairs_ok(u));
+    launch_pdl(k_residual<T, T>, grid, blk, 0, s, n, c, u, p, f, g, zu, zp, nullptr, nullptr, nullptr);
     launch_pdl(k_scale_L<T>, grid, blk, 0, s, n, c, zu, zp, sinv);
     launch_pdl(k_normal_update<T>, grid, blk, 0, s, n, c, tau, zu, zp, sinv, u, p);
 }
@@ -272,8 +255,7 @@ void launch_normal_eq(cudaStream_t s, int n, const OpCoef<T>& c, T tau, T* u, T*
 template <typename T, typename TO>
 void launch_residual(cudaStream_t s, int n, const OpCoef<T>& c, const T* u, const T* p, const T* f,
                      const T* g, TO* ru, TO* rp, double* partial, float* ru2, float* rp2) {
-    launch_pdl(k_residual<T, TO>, cells_grid(n), dim3(BX, BY), 0, s, n, c, u, p, f, g, ru, rp, partial, ru2, rp2,
-               pairs_ok(u));
+    launch_pdl(k_residual<T, TO>, cells_grid(n), dim3(BX, BY), 0, s, n, c, u, p, f, g, ru, rp, partial, ru2, rp2);
 }
 
 // ------------------------------------------------------------------------------------------
