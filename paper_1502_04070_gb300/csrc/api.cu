@@ -242,9 +242,7 @@ void mg_cycle(stokes_handle* h, std::vector<Level<T>>& H, int l) {
     T* rp = sw ? lv.p : lv.tp;
     Level<T>& cl = H[l - 1];
     launch_residual<T, T>(h->st, lv.n, lv.c, xu, xp, lv.f, lv.g, ru, rp, nullptr);
-    launch_restrict<T>(h->st, cl.n, ru, rp, cl.f, cl.g);
-    cudaMemsetAsync(cl.u, 0, 2 * cl.n2 * sizeof(T), h->st);
-    cudaMemsetAsync(cl.p, 0, cl.n1 * sizeof(T), h->st);
+    launch_restrict<T>(h->st, cl.n, ru, rp, cl.f, cl.g, cl.u, cl.p);   // and the coarse iterate := 0
     for (int r = 0; r < h->prm.gamma; ++r) mg_cycle(h, H, l - 1);
     launch_prolong_add<T>(h->st, cl.n, cl.u, cl.p, xu, xp);
     sw = smooth_level(h, lv, h->prm.nu_post, top, sw);

@@ -359,19 +359,34 @@ __device__ __forceinline__ void restrict_cell(int i, int j, int nc, const T* __r
     gc[j * lay.ldpc + i] = s + T(0.5) * half;
 }
 
+// With uc, pc given, the coarse iterate is also set to zero (the coarse correction starts from 0).
 template <typename T>
 __global__ void __launch_bounds__(NT) k_restrict(int nc, const T* __restrict__ ru, const T* __restrict__ rp,
-                                                 T* __restrict__ fc, T* __restrict__ gc) {
+                                                 T* __restrict__ fc, T* __restrict__ gc, T* __restrict__ uc,
+                                                 T* __restrict__ pc) {
     pdl_enter();
     const int n = nc;
     CELL_INDEX
     if (!active) return;
     restrict_cell<true>(i, j, nc, ru, rp, fc, gc, dense_layout(nc));
+    if (uc) {
+        const CellNodes cn = cell_nodes(i, j, nc);
+        const int ldc = 2 * nc + 1, n2c = ldc * ldc;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            if (!slot_exists(cn, s)) continue;
+            int X, Y;
+            slot_pos(i, j, s, X, Y);
+            uc[Y * ldc + X] = T(0);
+            uc[n2c + Y * ldc + X] = T(0);
+        }
+        pc[j * (nc + 1) + i] = T(0);
+    }
 }
 
 template <typename T>
-void launch_restrict(cudaStream_t s, int nc, const T* ru, const T* rp, T* fc, T* gc) {
-    launch_pdl(k_restrict<T>, cells_grid(nc), dim3(BX, BY), 0, s, nc, ru, rp, fc, gc);
+void launch_restrict(cudaStream_t s, int nc, const T* ru, const T* rp, T* fc, T* gc, T* uc, T* pc) {
+    launch_pdl(k_restrict<T>, cells_grid(nc), dim3(BX, BY), 0, s, nc, ru, rp, fc, gc, uc, pc);
 }
 
 // Prolongation (Sec. 3, canonical embedding): every fine point owned by coarse square (I, J) is
@@ -763,7 +778,7 @@ void launch_add_f32(cudaStream_t s, size_t count, const float* e, double* x) {
                                   const T*, T*, T*, int, int);                                                      \
     template void launch_normal_eq<T>(cudaStream_t, int, const OpCoef<T>&, T, T*, T*, const T*, const T*, \
                                       const T*, T*, T*);                                                  \
-    template void launch_restrict<T>(cudaStream_t, int, const T*, const T*, T*, T*);                      \
+    template void launch_restrict<T>(cudaStream_t, int, const T*, const T*, T*, T*, T*, T*);                      \
     template void launch_prolong_add<T>(cudaStream_t, int, const T*, const T*, T*, T*);                   \
     template void launch_coarse_solve<T>(cudaStream_t, const double*, const T*, const T*, T*, T*);        \
     template void launch_schur_diag<T>(cudaStream_t, int, const OpCoef<double>&, T*);                     \

@@ -77,7 +77,8 @@ void launch_normal_eq(cudaStream_t s, int n, const OpCoef<T>& c, T tau, T* u, T*
 
 // (fc, gc) = I^T (ru, rp): fine level n = 2 nc.
 template <typename T>
-void launch_restrict(cudaStream_t s, int nc, const T* ru, const T* rp, T* fc, T* gc);
+void launch_restrict(cudaStream_t s, int nc, const T* ru, const T* rp, T* fc, T* gc, T* uc = nullptr,
+                     T* pc = nullptr);   // uc, pc: optional coarse iterate set to zero
 
 // (u, p) += I (uc, pc)
 template <typename T>
