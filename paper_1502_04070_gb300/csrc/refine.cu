@@ -96,52 +96,108 @@ __device__ __forceinline__ void visit_df(int i, int j, int n, const OpCoef<float
 
 // The same rows from the merged stencils of class C (blocks off the mid-lines and at least two
 // cells inside the boundary: every window lies inside the arrays, every term is decided at compile
-// time).
-template <int C, int S, int K>
-__device__ __forceinline__ void ma_df(const OpCoef<float>& h, const OpCoef<float>& l, const float (&wx)[25],
-                                      const float (&wy)[25], DFAcc& a) {
-    if constexpr (nz_MA(C, S, K)) {
-        df_fma(a.au[0][S], h.MA[C][S][K], l.MA[C][S][K], wx[K]);
-        df_fma(a.au[1][S], h.MA[C][S][K], l.MA[C][S][K], wy[K]);
+// time), with the x and y components side by side in packed FP32x2 instructions: the velocity
+// block applies one coefficient to (e_x, e_y), B^T an (x, y) coefficient pair to (p, p), and B an
+// (x, y) pair to (e_x, e_y) whose two halves are summed at the end.  Each lane of every packed
+// instruction is a correctly rounded float operation, so TwoProduct and TwoSum stay exact.
+struct DFPairCoef {   // split float64 coefficients (hi + lo) as (x, y) pairs, classes 0 and 1
+    float2 MAh[2][4][25], MAl[2][4][25];
+    float2 MBTh[2][4][9], MBTl[2][4][9];
+    float2 MBh[2][25], MBl[2][25];
+};
+
+static DFPairCoef make_df_pairs(const OpCoef<float>& h, const OpCoef<float>& l) {
+    DFPairCoef q{};
+    for (int k = 0; k < 2; ++k) {
+        for (int s = 0; s < 4; ++s) {
+            for (int w = 0; w < 25; ++w) {
+                q.MAh[k][s][w] = make_float2(h.MA[k][s][w], h.MA[k][s][w]);
+                q.MAl[k][s][w] = make_float2(l.MA[k][s][w], l.MA[k][s][w]);
+            }
+            for (int v = 0; v < 9; ++v) {
+                q.MBTh[k][s][v] = make_float2(h.MBTx[k][s][v], h.MBTy[k][s][v]);
+                q.MBTl[k][s][v] = make_float2(l.MBTx[k][s][v], l.MBTy[k][s][v]);
+            }
+        }
+        for (int w = 0; w < 25; ++w) {
+            q.MBh[k][w] = make_float2(h.MBx[k][w], h.MBy[k][w]);
+            q.MBl[k][w] = make_float2(l.MBx[k][w], l.MBy[k][w]);
+        }
     }
+    return q;
+}
+
+struct DF2 {
+    float2 hi, lo;
+};
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+// s += (chi + clo) * v on both lanes (TwoProduct of chi * v, TwoSum into s.hi)
+__device__ __forceinline__ void df2_fma(DF2& s, float2 chi, float2 clo, float2 v) {
+    const float2 p = __fmul2_rn(chi, v);
+    const float2 pe = __ffma2_rn(chi, v, neg2(p));
+    const float2 t = __fadd2_rn(s.hi, p);
+    const float2 bb = __fadd2_rn(t, neg2(s.hi));
+    const float2 e = __fadd2_rn(__fadd2_rn(s.hi, neg2(__fadd2_rn(t, neg2(bb)))), __fadd2_rn(p, neg2(bb)));
+    s.hi = t;
+    s.lo = __fadd2_rn(s.lo, __fadd2_rn(e, __ffma2_rn(clo, v, pe)));
+}
+
+template <int C, int S, int K>
+__device__ __forceinline__ void ma_df2(const DFPairCoef& q, float2 v, DF2 (&au)[4]) {
+    if constexpr (nz_MA(C, S, K)) df2_fma(au[S], q.MAh[C][S][K], q.MAl[C][S][K], v);
 }
 template <int C, int K>
-__device__ __forceinline__ void win_df(const OpCoef<float>& h, const OpCoef<float>& l, const float (&wx)[25],
-                                       const float (&wy)[25], DFAcc& a) {
-    ma_df<C, 0, K>(h, l, wx, wy, a);
-    ma_df<C, 1, K>(h, l, wx, wy, a);
-    ma_df<C, 2, K>(h, l, wx, wy, a);
-    ma_df<C, 3, K>(h, l, wx, wy, a);
-    if constexpr (nz_MB(C, K)) {
-        df_fma(a.bu, h.MBx[C][K], l.MBx[C][K], wx[K]);
-        df_fma(a.bu, h.MBy[C][K], l.MBy[C][K], wy[K]);
+__device__ __forceinline__ void win_df2(const DFPairCoef& q, const float (&wx)[25], const float (&wy)[25],
+                                        DF2 (&au)[4], DF2& bu) {
+    if constexpr (need_win(C, true, true, K)) {
+        const float2 v = make_float2(wx[K], wy[K]);
+        ma_df2<C, 0, K>(q, v, au);
+        ma_df2<C, 1, K>(q, v, au);
+        ma_df2<C, 2, K>(q, v, au);
+        ma_df2<C, 3, K>(q, v, au);
+        if constexpr (nz_MB(C, K)) df2_fma(bu, q.MBh[C][K], q.MBl[C][K], v);
     }
 }
 template <int C, int S, int V>
-__device__ __forceinline__ void mbt_df(const OpCoef<float>& h, const OpCoef<float>& l, const float (&pw)[9], DFAcc& a) {
-    if constexpr (nz_MBT(C, S, V)) {
-        df_fma(a.au[0][S], h.MBTx[C][S][V], l.MBTx[C][S][V], pw[V]);
-        df_fma(a.au[1][S], h.MBTy[C][S][V], l.MBTy[C][S][V], pw[V]);
-    }
+__device__ __forceinline__ void mbt_df2(const DFPairCoef& q, float2 pv, DF2 (&au)[4]) {
+    if constexpr (nz_MBT(C, S, V)) df2_fma(au[S], q.MBTh[C][S][V], q.MBTl[C][S][V], pv);
 }
 template <int C, int V>
-__device__ __forceinline__ void vwin_df(const OpCoef<float>& h, const OpCoef<float>& l, const float (&pw)[9], DFAcc& a) {
-    mbt_df<C, 0, V>(h, l, pw, a);
-    mbt_df<C, 1, V>(h, l, pw, a);
-    mbt_df<C, 2, V>(h, l, pw, a);
-    mbt_df<C, 3, V>(h, l, pw, a);
+__device__ __forceinline__ void vwin_df2(const DFPairCoef& q, const float (&pw)[9], DF2 (&au)[4]) {
+    if constexpr (need_vwin(C, V)) {
+        const float2 pv = make_float2(pw[V], pw[V]);
+        mbt_df2<C, 0, V>(q, pv, au);
+        mbt_df2<C, 1, V>(q, pv, au);
+        mbt_df2<C, 2, V>(q, pv, au);
+        mbt_df2<C, 3, V>(q, pv, au);
+    }
 }
 template <int C, int... K, int... V>
-__device__ __forceinline__ void merged_df(int i, int j, int n, const OpCoef<float>& h, const OpCoef<float>& l,
-                                          const float* __restrict__ eu, const float* __restrict__ ep, DFAcc& a,
-                                          std::integer_sequence<int, K...>, std::integer_sequence<int, V...>) {
+__device__ __forceinline__ void merged_df(int i, int j, int n, const DFPairCoef& q, const float* __restrict__ eu,
+                                          const float* __restrict__ ep, DFAcc& a, std::integer_sequence<int, K...>,
+                                          std::integer_sequence<int, V...>) {
     const int n2 = (2 * n + 1) * (2 * n + 1);
     float wx[25], wy[25], pw[9];
     win_load<C, true, true, false>(i, j, n, gviewu(eu, 2 * n + 1), gviewu(eu + n2, 2 * n + 1), wx, wy,
                                    std::make_integer_sequence<int, 25>{});
     vwin_load<C>(i, j, n, gviewu(ep, n + 1), pw, std::make_integer_sequence<int, 9>{});
-    (win_df<C, K>(h, l, wx, wy, a), ...);
-    (vwin_df<C, V>(h, l, pw, a), ...);
+    DF2 au[4], bu;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) au[s] = DF2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    bu = DF2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    (win_df2<C, K>(q, wx, wy, au, bu), ...);
+    (vwin_df2<C, V>(q, pw, au), ...);
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        a.au[0][s] = DF{au[s].hi.x, au[s].lo.x};
+        a.au[1][s] = DF{au[s].hi.y, au[s].lo.y};
+    }
+    // B row: the x and y halves summed (TwoSum of the high parts)
+    const float t = __fadd_rn(bu.hi.x, bu.hi.y);
+    const float bb = __fsub_rn(t, bu.hi.x);
+    const float e = __fadd_rn(__fsub_rn(bu.hi.x, __fsub_rn(t, bb)), __fsub_rn(bu.hi.y, bb));
+    a.bu = DF{t, __fadd_rn(__fadd_rn(bu.lo.x, bu.lo.y), e)};
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -165,6 +221,7 @@ __device__ __forceinline__ float2 df_sub(float2 a, const DF& b) {
 
 __global__ void __launch_bounds__(NT) k_ir_update_df(int n, const __grid_constant__ OpCoef<float> ch,
                                                      const __grid_constant__ OpCoef<float> cl,
+                                                     const __grid_constant__ DFPairCoef cq,
                                                      const float* __restrict__ eu, const float* __restrict__ ep,
                                                      double* __restrict__ xu, double* __restrict__ xp,
                                                      float2* __restrict__ ru, float2* __restrict__ rp,
@@ -184,10 +241,10 @@ __global__ void __launch_bounds__(NT) k_ir_update_df(int n, const __grid_constan
         const bool single = (hh < bi0 || hh >= bi0 + (int)blockDim.x) && (hh < bj0 || hh >= bj0 + (int)blockDim.y);
         if (single && block_interior(n, 2)) {
             if (orient(bi0, bj0, n) == 0)
-                merged_df<0>(i, j, n, ch, cl, eu, ep, a, std::make_integer_sequence<int, 25>{},
+                merged_df<0>(i, j, n, cq, eu, ep, a, std::make_integer_sequence<int, 25>{},
                              std::make_integer_sequence<int, 9>{});
             else
-                merged_df<1>(i, j, n, ch, cl, eu, ep, a, std::make_integer_sequence<int, 25>{},
+                merged_df<1>(i, j, n, cq, eu, ep, a, std::make_integer_sequence<int, 25>{},
                              std::make_integer_sequence<int, 9>{});
         } else {
             visit_df<0>(i, j, n, ch, cl, eu, ep, a);
@@ -277,7 +334,7 @@ __global__ void __launch_bounds__(NT) k_residual_df(int n, const __grid_constant
 void launch_ir_update_df(cudaStream_t s, int n, const OpCoef<float>& chi, const OpCoef<float>& clo,
                          const float* eu, const float* ep, double* xu, double* xp, double* ru, double* rp,
                          float* r32u, float* r32p, double* partial, double* wpartial) {
-    launch_pdl(k_ir_update_df, cells_grid(n), dim3(BX, BY), 0, s, n, chi, clo, eu, ep, xu, xp,
+    launch_pdl(k_ir_update_df, cells_grid(n), dim3(BX, BY), 0, s, n, chi, clo, make_df_pairs(chi, clo), eu, ep, xu, xp,
                reinterpret_cast<float2*>(ru), reinterpret_cast<float2*>(rp), r32u, r32p, partial, wpartial);
 }
 
