@@ -173,15 +173,22 @@ __device__ __forceinline__ void vwin_df2(const DFPairCoef& q, const float (&pw)[
         mbt_df2<C, 3, V>(q, pv, au);
     }
 }
-template <int C, int... K, int... V>
+// CHECKED: blocks at the boundary (off the mid-lines) read with range tests and the Dirichlet mask
+template <int C, bool CHECKED, int... K, int... V>
 __device__ __forceinline__ void merged_df(int i, int j, int n, const DFPairCoef& q, const float* __restrict__ eu,
                                           const float* __restrict__ ep, DFAcc& a, std::integer_sequence<int, K...>,
                                           std::integer_sequence<int, V...>) {
     const int n2 = (2 * n + 1) * (2 * n + 1);
     float wx[25], wy[25], pw[9];
-    win_load<C, true, true, false>(i, j, n, gviewu(eu, 2 * n + 1), gviewu(eu + n2, 2 * n + 1), wx, wy,
-                                   std::make_integer_sequence<int, 25>{});
-    vwin_load<C>(i, j, n, gviewu(ep, n + 1), pw, std::make_integer_sequence<int, 9>{});
+    if constexpr (CHECKED) {
+        win_load<C, true, true, true>(i, j, n, gview(eu, 2 * n + 1), gview(eu + n2, 2 * n + 1), wx, wy,
+                                      std::make_integer_sequence<int, 25>{});
+        vwin_load<C>(i, j, n, gview(ep, n + 1), pw, std::make_integer_sequence<int, 9>{});
+    } else {
+        win_load<C, true, true, false>(i, j, n, gviewu(eu, 2 * n + 1), gviewu(eu + n2, 2 * n + 1), wx, wy,
+                                       std::make_integer_sequence<int, 25>{});
+        vwin_load<C>(i, j, n, gviewu(ep, n + 1), pw, std::make_integer_sequence<int, 9>{});
+    }
     DF2 au[4], bu;
 #pragma unroll
     for (int s = 0; s < 4; ++s) au[s] = DF2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
@@ -219,7 +226,7 @@ __device__ __forceinline__ float2 df_sub(float2 a, const DF& b) {
     return renorm(s, __fadd_rn(e, __fsub_rn(a.y, b.lo)));
 }
 
-__global__ void __launch_bounds__(NT) k_ir_update_df(int n, const __grid_constant__ OpCoef<float> ch,
+__global__ void __launch_bounds__(NT, 4) k_ir_update_df(int n, const __grid_constant__ OpCoef<float> ch,
                                                      const __grid_constant__ OpCoef<float> cl,
                                                      const __grid_constant__ DFPairCoef cq,
                                                      const float* __restrict__ eu, const float* __restrict__ ep,
@@ -239,13 +246,14 @@ __global__ void __launch_bounds__(NT) k_ir_update_df(int n, const __grid_constan
         a.bu = DF{0.f, 0.f};
         const int hh = n >> 1, bi0 = blockIdx.x * blockDim.x, bj0 = blockIdx.y * blockDim.y;
         const bool single = (hh < bi0 || hh >= bi0 + (int)blockDim.x) && (hh < bj0 || hh >= bj0 + (int)blockDim.y);
+        constexpr auto K25 = std::make_integer_sequence<int, 25>{};
+        constexpr auto V9 = std::make_integer_sequence<int, 9>{};
         if (single && block_interior(n, 2)) {
-            if (orient(bi0, bj0, n) == 0)
-                merged_df<0>(i, j, n, cq, eu, ep, a, std::make_integer_sequence<int, 25>{},
-                             std::make_integer_sequence<int, 9>{});
-            else
-                merged_df<1>(i, j, n, cq, eu, ep, a, std::make_integer_sequence<int, 25>{},
-                             std::make_integer_sequence<int, 9>{});
+            if (orient(bi0, bj0, n) == 0) merged_df<0, false>(i, j, n, cq, eu, ep, a, K25, V9);
+            else merged_df<1, false>(i, j, n, cq, eu, ep, a, K25, V9);
+        } else if (single) {
+            if (orient(bi0, bj0, n) == 0) merged_df<0, true>(i, j, n, cq, eu, ep, a, K25, V9);
+            else merged_df<1, true>(i, j, n, cq, eu, ep, a, K25, V9);
         } else {
             visit_df<0>(i, j, n, ch, cl, eu, ep, a);
             visit_df<1>(i, j, n, ch, cl, eu, ep, a);
