@@ -14,22 +14,24 @@ namespace smg {
 // the step count is below max_cycles and the residual is finite.
 __global__ void k_batch_check(cudaGraphConditionalHandle hnd, const double* __restrict__ scal, double tol2,
                               int max_cycles, int* __restrict__ count) {
-    pdl_enter();
+    pdl_wait();
     if (threadIdx.x != 0) return;
     const int c = *count + 1;
     *count = c;
     const double r2 = scal[0];
     const bool go = isfinite(r2) && r2 > tol2 * scal[2] && c < max_cycles;
     cudaGraphSetConditional(hnd, go ? 1u : 0u);
+    pdl_trigger();
 }
 
 __global__ void k_batch_store(const double* __restrict__ scal, const int* __restrict__ count,
                               double* __restrict__ out) {
-    pdl_enter();
+    pdl_wait();
     if (threadIdx.x != 0) return;
     out[0] = scal[0];
     out[1] = scal[2];
     out[2] = (double)*count;
+    pdl_trigger();
 }
 
 // Single solves: the same device-side loop, with a residual history and a divergence test.
@@ -37,7 +39,7 @@ __global__ void k_batch_store(const double* __restrict__ scal, const int* __rest
 // ictl: [0] step count, [1] consecutive growths.  hist[c] = r^2 after step c (c < cap).
 __global__ void k_solve_check(cudaGraphConditionalHandle hnd, const double* __restrict__ scal,
                               double* __restrict__ ctl, int* __restrict__ ictl, double* __restrict__ hist, int cap) {
-    pdl_enter();
+    pdl_wait();
     if (threadIdx.x != 0) return;
     const int c = ictl[0] + 1;
     ictl[0] = c;
@@ -48,6 +50,7 @@ __global__ void k_solve_check(cudaGraphConditionalHandle hnd, const double* __re
     ctl[2] = r2;
     const bool go = isfinite(r2) && r2 > ctl[0] * scal[2] && c < (int)ctl[1] && grow < 8;
     cudaGraphSetConditional(hnd, go ? 1u : 0u);
+    pdl_trigger();
 }
 
 void launch_solve_check(cudaStream_t s, cudaGraphConditionalHandle hnd, const double* scal, double* ctl, int* ictl,

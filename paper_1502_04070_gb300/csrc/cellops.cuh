@@ -38,14 +38,13 @@ struct Acc {
 };
 
 // Programmatic dependent launch: when the kernels of a cycle are launched with programmatic stream
-// serialisation (pdl_enabled), a kernel's CTAs can be scheduled while its predecessor drains; each
-// kernel first lets its own successor launch, then waits until every predecessor has completed and
-// its memory is visible, before it touches global memory.  Without the launch attribute both
-// instructions return at once.
-__device__ __forceinline__ void pdl_enter() {
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-}
+// serialisation (pdl_enabled), a kernel's CTAs can be scheduled before its predecessor has
+// finished.  Each kernel waits (pdl_wait) until every predecessor has completed and its memory is
+// visible before it touches global memory, and lets its successor launch (pdl_trigger) only at its
+// end, so that early-launched CTAs overlap the predecessor's tail instead of holding SM slots for
+// its whole run.  Without the launch attribute both instructions return at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // Programmatic dependent launch only if the environment sets STOKES_MG_PDL=1 (read once per
 // process).  Measured on GB300: off is faster, 0.74 against 0.77 ms per refinement step at

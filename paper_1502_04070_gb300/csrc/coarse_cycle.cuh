@@ -224,7 +224,7 @@ __device__ void cc_residual(const CCLevel& L, const OpCoef<float>& c) {
 }
 
 __global__ void __launch_bounds__(kCoarseThreads, 1) k_coarse_cycle(const __grid_constant__ CoarseCycleArgs A) {
-    pdl_enter();
+    pdl_wait();
     extern __shared__ __align__(16) float cc_smem[];
     // The operator coefficients of every level, copied from the parameter bank: the cycle indexes
     // levels at run time, and run-time-indexed parameter reads would each wait on the constant cache.
@@ -333,6 +333,7 @@ __global__ void __launch_bounds__(kCoarseThreads, 1) k_coarse_cycle(const __grid
         for (int q = threadIdx.x; q < (T.n + 1) * (T.n + 1); q += blockDim.x)
             A.p[q] = T.p[(q / (T.n + 1)) * T.ldv + q % (T.n + 1)];
     }
+    pdl_trigger();
 }
 
 cudaError_t prepare_coarse_cycle() {

@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(NT) k_residual(int n, const __grid_constant__ 
                                                  TO* __restrict__ ru, TO* __restrict__ rp,
                                                  double* __restrict__ partial, float* __restrict__ ru2,
                                                  float* __restrict__ rp2) {
-    pdl_enter();
+    pdl_wait();
     CELL_INDEX
     const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
     double ss = 0.0;
@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(NT) k_residual(int n, const __grid_constant__ 
         const double t = block_sum2d(ss, tid);
         if (tid == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = t;
     }
+    pdl_trigger();
 }
 
 // float32: four CTAs per SM (64 registers; a few spilled) for more loads in flight
@@ -96,7 +97,7 @@ template <typename T>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 1) k_uzawa_u(int n, const __grid_constant__ OpCoef<T> c, T tau,
                                                 const T* __restrict__ u, const T* __restrict__ p,
                                                 const T* __restrict__ f, T* __restrict__ uh) {
-    pdl_enter();
+    pdl_wait();
     CELL_INDEX
     if (!active) return;
     const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
@@ -122,6 +123,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 1) k_uzawa_u(int n, c
             uh[k] = unk ? u[k] + tau * (f[k] - a.au[comp][s] - a.bt[comp][s]) * a.idg[s] : T(0);
         }
     }
+    pdl_trigger();
 }
 
 template <typename T>
@@ -129,7 +131,7 @@ __global__ void __launch_bounds__(NT) k_uzawa_p(int n, const __grid_constant__ O
                                                 const T* __restrict__ uh, T* __restrict__ p,
                                                 const T* __restrict__ g, const T* __restrict__ sinv,
                                                 T* __restrict__ dp) {
-    pdl_enter();
+    pdl_wait();
     CELL_INDEX
     if (!active) return;
     const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
@@ -145,13 +147,14 @@ __global__ void __launch_bounds__(NT) k_uzawa_p(int n, const __grid_constant__ O
     const T d = sigma * sinv[vi] * (a.bu - g[vi]);
     p[vi] += d;
     dp[vi] = d;
+    pdl_trigger();
 }
 
 template <typename T>
 __global__ void __launch_bounds__(NT) k_uzawa_u2(int n, const __grid_constant__ OpCoef<T> c, T tau,
                                                  const T* __restrict__ uh, const T* __restrict__ dp,
                                                  T* __restrict__ u) {
-    pdl_enter();
+    pdl_wait();
     CELL_INDEX
     if (!active) return;
     const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
@@ -178,6 +181,7 @@ __global__ void __launch_bounds__(NT) k_uzawa_u2(int n, const __grid_constant__ 
             u[k] = unk ? uh[k] - tau * a.bt[comp][s] * a.idg[s] : T(0);
         }
     }
+    pdl_trigger();
 }
 
 template <typename T>
@@ -195,7 +199,7 @@ template <typename T>
 __global__ void __launch_bounds__(NT) k_scale_L(int n, const __grid_constant__ OpCoef<T> c,
                                                 T* __restrict__ zu, T* __restrict__ zp,
                                                 const T* __restrict__ sinv) {
-    pdl_enter();
+    pdl_wait();
     CELL_INDEX
     if (!active) return;
     const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
@@ -215,6 +219,7 @@ __global__ void __launch_bounds__(NT) k_scale_L(int n, const __grid_constant__ O
     }
     const size_t vi = (size_t)j * (n + 1) + i;
     zp[vi] *= sinv[vi];
+    pdl_trigger();
 }
 
 template <typename T>
@@ -222,7 +227,7 @@ __global__ void __launch_bounds__(NT) k_normal_update(int n, const __grid_consta
                                                       const T* __restrict__ zu, const T* __restrict__ zp,
                                                       const T* __restrict__ sinv, T* __restrict__ u,
                                                       T* __restrict__ p) {
-    pdl_enter();
+    pdl_wait();
     CELL_INDEX
     if (!active) return;
     const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
@@ -241,6 +246,7 @@ __global__ void __launch_bounds__(NT) k_normal_update(int n, const __grid_consta
     }
     const size_t vi = (size_t)j * (n + 1) + i;
     p[vi] += tau * sinv[vi] * a.bu;
+    pdl_trigger();
 }
 
 template <typename T>
@@ -364,7 +370,7 @@ template <typename T>
 __global__ void __launch_bounds__(NT) k_restrict(int nc, const T* __restrict__ ru, const T* __restrict__ rp,
                                                  T* __restrict__ fc, T* __restrict__ gc, T* __restrict__ uc,
                                                  T* __restrict__ pc) {
-    pdl_enter();
+    pdl_wait();
     const int n = nc;
     CELL_INDEX
     if (!active) return;
@@ -382,6 +388,7 @@ __global__ void __launch_bounds__(NT) k_restrict(int nc, const T* __restrict__ r
         }
         pc[j * (nc + 1) + i] = T(0);
     }
+    pdl_trigger();
 }
 
 template <typename T>
@@ -438,11 +445,12 @@ __device__ __forceinline__ void prolong_cell(int i, int j, int nc, const T* __re
 template <typename T>
 __global__ void __launch_bounds__(NT) k_prolong(int nc, const T* __restrict__ uc, const T* __restrict__ pc,
                                                 T* __restrict__ u, T* __restrict__ p) {
-    pdl_enter();
+    pdl_wait();
     const int n = nc;
     CELL_INDEX
     if (!active) return;
     prolong_cell<true>(i, j, nc, uc, pc, u, p, dense_layout(nc));
+    pdl_trigger();
 }
 
 template <typename T>
@@ -455,7 +463,7 @@ void launch_prolong_add(cudaStream_t s, int nc, const T* uc, const T* pc, T* u, 
 template <typename T>
 __global__ void k_coarse(const double* __restrict__ inv, const T* __restrict__ f, const T* __restrict__ g,
                          T* __restrict__ u, T* __restrict__ p) {
-    pdl_enter();
+    pdl_wait();
     __shared__ double b[27];
     const int t = threadIdx.x;
     auto vpos = [](int t, int& c, int& k) {
@@ -489,6 +497,7 @@ __global__ void k_coarse(const double* __restrict__ inv, const T* __restrict__ f
             p[t - 18] = (T)x;
         }
     }
+    pdl_trigger();
 }
 
 template <typename T>
@@ -548,24 +557,26 @@ void launch_schur_diag(cudaStream_t s, int n, const OpCoef<double>& c, T* sinv) 
 
 template <typename T>
 __global__ void __launch_bounds__(NT) k_pmean_partial(int n, const T* __restrict__ p, double* __restrict__ partial) {
-    pdl_enter();
+    pdl_wait();
     CELL_INDEX
     double v = 0.0;
     if (active) v = vertex_weight(i, j, n) * (double)p[(size_t)j * (n + 1) + i];
     const double t = block_sum2d(v, tid);
     if (tid == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = t;
+    pdl_trigger();
 }
 
 template <typename T>
 __global__ void __launch_bounds__(NT) k_psub(int n, T* __restrict__ p, const double* __restrict__ scalar) {
-    pdl_enter();
+    pdl_wait();
     CELL_INDEX
     if (!active) return;
     p[(size_t)j * (n + 1) + i] -= (T)(*scalar);   // sum_i w_i = |Omega| = 1
+    pdl_trigger();
 }
 
 __global__ void k_reduce(const double* __restrict__ partial, int count, double* __restrict__ out) {
-    pdl_enter();
+    pdl_wait();
     // fixed-order tree: deterministic for a given count
     __shared__ double red[1024];
     double s = 0.0;
@@ -577,6 +588,7 @@ __global__ void k_reduce(const double* __restrict__ partial, int count, double* 
         __syncthreads();
     }
     if (threadIdx.x == 0) out[0] = red[0];
+    pdl_trigger();
 }
 
 void launch_reduce(cudaStream_t s, const double* partial, int count, double* out) {

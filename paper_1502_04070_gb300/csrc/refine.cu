@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(NT, 4) k_ir_update_df(int n, const __grid_cons
                                                      float2* __restrict__ ru, float2* __restrict__ rp,
                                                      float* __restrict__ r32u, float* __restrict__ r32p,
                                                      double* __restrict__ partial, double* __restrict__ wpartial) {
-    pdl_enter();
+    pdl_wait();
     CELL_INDEX
     const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
     float ss = 0.f;
@@ -292,6 +292,7 @@ __global__ void __launch_bounds__(NT, 4) k_ir_update_df(int n, const __grid_cons
         partial[blockIdx.y * gridDim.x + blockIdx.x] = t.x;
         wpartial[blockIdx.y * gridDim.x + blockIdx.x] = t.y;
     }
+    pdl_trigger();
 }
 
 // true float64 residual r = F - A x (x, F float64), written as two-float r and float32 r32
@@ -301,7 +302,7 @@ __global__ void __launch_bounds__(NT) k_residual_df(int n, const __grid_constant
                                                     float2* __restrict__ ru, float2* __restrict__ rp,
                                                     float* __restrict__ r32u, float* __restrict__ r32p,
                                                     double* __restrict__ partial) {
-    pdl_enter();
+    pdl_wait();
     CELL_INDEX
     const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
     double ss = 0.0;
@@ -337,6 +338,7 @@ __global__ void __launch_bounds__(NT) k_residual_df(int n, const __grid_constant
     }
     const double t = block_sum2d(ss, tid);
     if (tid == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = t;
+    pdl_trigger();
 }
 
 void launch_ir_update_df(cudaStream_t s, int n, const OpCoef<float>& chi, const OpCoef<float>& clo,

@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 4 ? 2 : 1)) k_uzawa_fuse
                                                         const T* __restrict__ f, const T* __restrict__ g,
                                                         const T* __restrict__ sinv, T* __restrict__ u_out,
                                                         T* __restrict__ p_out) {
-    pdl_enter();
+    pdl_wait();
     using G = FusedTile<T, TX, TY>;
     constexpr int NTH = TX * TY;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -157,6 +157,7 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 4 ? 2 : 1)) k_uzawa_fuse
         u_out[n2 + k] = oy;
     }
     p_out[cj * (n + 1) + ci] = vp(ci, cj) + vd(ci, cj);
+    pdl_trigger();
 }
 
 // Step variants the autotuner chooses from, per level, for float32 (float64 uses the three-kernel

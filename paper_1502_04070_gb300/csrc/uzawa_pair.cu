@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(32 * NW, (NW > 8 ? 2 : NW > 4 ? 3 : 6))
                  float sigma, const float* __restrict__ u, const float* __restrict__ p, const float* __restrict__ f,
                  const float* __restrict__ g, const float* __restrict__ sinv, float* __restrict__ u_out,
                  float* __restrict__ p_out) {
-    pdl_enter();
+    pdl_wait();
     using G = PairTile;
     constexpr int TX = G::TX;
     const int UPL = G::upl(TY), HPL = G::hpl(TY);
@@ -399,6 +399,7 @@ __global__ void __launch_bounds__(32 * NW, (NW > 8 ? 2 : NW > 4 ? 3 : 6))
         }
         p_out[cj * (n + 1) + ci] = sP[(r + 3) * G::PW + lane + 3] + sD[(r + 1) * G::DW + lane + 1];
     }
+    pdl_trigger();
 }
 
 template <int NW>
