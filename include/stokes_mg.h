@@ -29,9 +29,9 @@
  * ERRORS: every call returns a stokes_status; no call aborts or exits the process.  After
  * STOKES_ERR_CUDA the handle should be destroyed.
  *
- * ENVIRONMENT: STOKES_MG_PDL=1 (read once per process) launches the cycle's kernels with
- * programmatic dependent launch (a kernel's CTAs may be scheduled while its predecessor drains);
- * the default is off, which measured faster.  Results do not depend on it.
+ * ENVIRONMENT: STOKES_MG_PDL=0 (read once per process) launches the cycle's kernels without
+ * programmatic dependent launch; by default a kernel's CTAs may be scheduled while the tail of
+ * its predecessor runs.  Results do not depend on it.
  */
 #ifndef STOKES_MG_H
 #define STOKES_MG_H

@@ -46,10 +46,11 @@ struct Acc {
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-// Programmatic dependent launch only if the environment sets STOKES_MG_PDL=1 (read once per
-// process).  Measured on GB300: off is faster, 0.74 against 0.77 ms per refinement step at
-// k = 8, and 90 against 130 ms for six concurrent solves, where CTAs launched early sit on SMs
-// waiting for their predecessors while other solves' work could run there.
+// Programmatic dependent launch unless the environment sets STOKES_MG_PDL=0 (read once per
+// process).  Measured on GB300 with the trigger at the end of each kernel: 0.705 against
+// 0.726 ms per refinement step at k = 8 and 84 against 86 ms for six concurrent solves; with the
+// trigger at the start (successors' CTAs waiting on SMs for the whole predecessor) it had cost
+// 130 against 90 ms.
 bool pdl_enabled();
 
 template <typename... KArgs, typename... Args>

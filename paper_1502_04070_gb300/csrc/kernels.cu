@@ -18,7 +18,7 @@ int cells_blocks(int n) { return ((n + 1 + BX - 1) / BX) * ((n + 1 + BY - 1) / B
 bool pdl_enabled() {
     static const bool on = [] {
         const char* e = std::getenv("STOKES_MG_PDL");
-        return e && e[0] == '1';
+        return !(e && e[0] == '0');
     }();
     return on;
 }
