@@ -54,7 +54,7 @@ def parse():
                     help="kernel modes: drive refinement steps from the host, one cycle graph per step, so that a "
                          "profiler lists every kernel (the device-side loop hides the loop body from it)")
     ap.add_argument("--variant", type=int, default=None,
-                    help="kernel modes: force this float32 Uzawa step variant (0-10) on every level")
+                    help="kernel modes: force this float32 Uzawa step variant (0-9) on every level")
     ap.add_argument("--variants", default=None,
                     help="kernel modes: float32 Uzawa step variant per level, 'k:v,k:v,...' (as the workload's "
                          "float32_step_variant_per_level reports them); levels not named are autotuned")

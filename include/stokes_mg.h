@@ -186,10 +186,10 @@ stokes_status stokes_residual_norm2_noalloc(int levels, double beta, const doubl
 stokes_status stokes_autotune(stokes_handle* h);
 /* The step variant currently used for a float32 level with `levels` levels (N = 2^levels), -1 if
  * out of range: 0-3 fused tiles 32x16, 32x8, 64x8, 16x16; 4-6 three-kernel step, blocks 32x8, 16x8, 8x8;
- * 7-10 fused step on component-pair tiles (packed FP32x2 arithmetic), 28 cells wide: 8 or 4 warps with the
- * tile height chosen per level, 12 warps on 8 rows, or 12 warps with the height chosen per level. */
+ * 7-9 fused step on component-pair tiles (packed FP32x2 arithmetic), 28 cells wide: 8 or 4 warps with the
+ * tile height chosen per level, or 12 warps on 8 rows. */
 int stokes_step_variant(int levels);
-/* Sets the step variant (0-10, as above) for float32 levels with `levels` levels (N = 2^levels),
+/* Sets the step variant (0-9, as above) for float32 levels with `levels` levels (N = 2^levels),
  * process-wide, and marks that size as tuned (stokes_autotune keeps it).  Takes effect for direct
  * smoothing calls (stokes_smooth_f32) and for cycle graphs captured afterwards; graphs a handle has
  * already captured keep their variant.  Not thread-safe against concurrent setup or capture.

@@ -47,8 +47,8 @@ void launch_residual_df(cudaStream_t s, int n, const OpCoef<double>& c, const do
 template <typename T>
 cudaError_t prepare_uzawa_fused();   // raises the kernel's shared-memory limit on the current device
 // The float32 step on component-pair tiles with packed FP32x2 arithmetic (uzawa_pair.cu), 28 cells
-// wide; variant 0: 8 warps, 1: 4 warps (tile height chosen per level), 2: 12 warps, 8 rows, 3: 12
-// warps, height chosen per level.  Reads (u, p), writes (u_out, p_out).
+// wide; variant 0: 8 warps, 1: 4 warps (tile height chosen per level), 2: 12 warps, 8 rows.  Reads
+// (u, p), writes (u_out, p_out).
 void launch_uzawa_pair(int variant, cudaStream_t s, int n, const OpCoef<float>& c, float tau, float sigma,
                        const float* u, const float* p, const float* f, const float* g, const float* sinv,
                        float* u_out, float* p_out);

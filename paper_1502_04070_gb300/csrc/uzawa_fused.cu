@@ -166,11 +166,10 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 4 ? 2 : 1)) k_uzawa_fuse
 // suits the small levels, whose few fused tiles are issue-bound) with blocks 4: 32 x 8, 5: 16 x 8,
 // 6: 8 x 8.  Fused step on component-pair tiles with packed FP32x2 arithmetic (uzawa_pair.cu):
 // 7: 28 cells wide, 8 warps, height chosen per level; 8: the same with 4 warps; 9: 28 x 8 cells,
-// 12 warps (one row of the u^{m-1/2} region per warp: shortest CTAs, for small levels); 10: 12
-// warps, height chosen per level.
+// 12 warps (one row of the u^{m-1/2} region per warp: shortest CTAs, for small levels).
 constexpr int kFusedVariants = 4;
 constexpr int kPairVariant0 = 7;
-constexpr int kStepVariants = 11;
+constexpr int kStepVariants = 10;
 // per level k (N = 2^(k+1)): chosen variant; until tuned, the three-kernel step below N = 128 and the
 // 32 x 16 fused tile from N = 128 up
 static int g_tile_choice[32] = {5, 5, 5, 5, 5, 5, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0,

@@ -470,8 +470,7 @@ void launch_uzawa_pair(int variant, cudaStream_t s, int n, const OpCoef<float>& 
                        float* u_out, float* p_out) {
     if (variant == 0) launch_pair_v<8>(s, n, 0, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
     else if (variant == 1) launch_pair_v<4>(s, n, 0, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
-    else if (variant == 2) launch_pair_v<12>(s, n, 8, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
-    else launch_pair_v<12>(s, n, 0, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
+    else launch_pair_v<12>(s, n, 8, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
 }
 
 }  // namespace smg
