@@ -212,20 +212,16 @@ __device__ __forceinline__ void cell_apply(int i, int j, int n, const T (&A)[2][
 // ---- merged node stencils: the rows of a cell's nodes summed over its four squares, per stencil
 // class (common.cuh).  Every structural-zero test below is a template argument (the class C), so
 // it is decided at compile time.
-// SM: the owned slots whose velocity rows are wanted (bit s for V, H, E, C; all four by default)
-__host__ __device__ constexpr bool need_win(int C, bool DA, bool DB, int w, unsigned SM = 0xFu) {
-    return (DA && (((SM & 1u) && nz_MA(C, 0, w)) || ((SM & 2u) && nz_MA(C, 1, w)) || ((SM & 4u) && nz_MA(C, 2, w)) ||
-                   ((SM & 8u) && nz_MA(C, 3, w)))) ||
-           (DB && nz_MB(C, w));
+__host__ __device__ constexpr bool need_win(int C, bool DA, bool DB, int w) {
+    return (DA && (nz_MA(C, 0, w) || nz_MA(C, 1, w) || nz_MA(C, 2, w) || nz_MA(C, 3, w))) || (DB && nz_MB(C, w));
 }
-__host__ __device__ constexpr bool need_vwin(int C, int v, unsigned SM = 0xFu) {
-    return ((SM & 1u) && nz_MBT(C, 0, v)) || ((SM & 2u) && nz_MBT(C, 1, v)) || ((SM & 4u) && nz_MBT(C, 2, v)) ||
-           ((SM & 8u) && nz_MBT(C, 3, v));
+__host__ __device__ constexpr bool need_vwin(int C, int v) {
+    return nz_MBT(C, 0, v) || nz_MBT(C, 1, v) || nz_MBT(C, 2, v) || nz_MBT(C, 3, v);
 }
 
-template <int C, bool DA, bool DB, bool MASK, int W, unsigned SM = 0xFu, typename T, typename VU>
+template <int C, bool DA, bool DB, bool MASK, int W, typename T, typename VU>
 __device__ __forceinline__ void win_load1(int i, int j, int n, const VU& ux, const VU& uy, T (&wx)[25], T (&wy)[25]) {
-    if constexpr (need_win(C, DA, DB, W, SM)) {
+    if constexpr (need_win(C, DA, DB, W)) {
         constexpr int dx = W % 5 - 2, dy = W / 5 - 2;
         if constexpr (VU::zero_filled && !MASK) {
             wx[W] = ux.at(i - 1, j - 1, dx + 2, dy + 2);
@@ -238,23 +234,23 @@ __device__ __forceinline__ void win_load1(int i, int j, int n, const VU& ux, con
         }
     }
 }
-template <int C, bool DA, bool DB, bool MASK, unsigned SM = 0xFu, typename T, typename VU, int... W>
+template <int C, bool DA, bool DB, bool MASK, typename T, typename VU, int... W>
 __device__ __forceinline__ void win_load(int i, int j, int n, const VU& ux, const VU& uy, T (&wx)[25], T (&wy)[25],
                                          std::integer_sequence<int, W...>) {
-    (win_load1<C, DA, DB, MASK, W, SM>(i, j, n, ux, uy, wx, wy), ...);
+    (win_load1<C, DA, DB, MASK, W>(i, j, n, ux, uy, wx, wy), ...);
 }
 
-template <int C, int V, unsigned SM = 0xFu, typename T, typename VP>
+template <int C, int V, typename T, typename VP>
 __device__ __forceinline__ void vwin_load1(int i, int j, int n, const VP& p, T (&pw)[9]) {
-    if constexpr (need_vwin(C, V, SM)) {
+    if constexpr (need_vwin(C, V)) {
         const int I = i + V % 3 - 1, J = j + V / 3 - 1;
         if constexpr (VP::zero_filled) pw[V] = p(I, J);
         else pw[V] = (I >= 0 && J >= 0 && I <= n && J <= n) ? p(I, J) : T(0);
     }
 }
-template <int C, unsigned SM = 0xFu, typename T, typename VP, int... V>
+template <int C, typename T, typename VP, int... V>
 __device__ __forceinline__ void vwin_load(int i, int j, int n, const VP& p, T (&pw)[9], std::integer_sequence<int, V...>) {
-    (vwin_load1<C, V, SM>(i, j, n, p, pw), ...);
+    (vwin_load1<C, V>(i, j, n, p, pw), ...);
 }
 
 template <int C, int S, int K, typename T>
@@ -300,29 +296,26 @@ __device__ __forceinline__ T mb_row_i(const OpCoef<T>& c, const T (&wx)[25], con
     return s;
 }
 
-// SM selects the owned slots whose velocity rows (A, B^T) are computed; the others stay zero.
-template <bool DA, bool DBT, bool DB, bool DD, bool MASK, int C, unsigned SM = 0xFu, typename T, typename VU,
-          typename VP>
+template <bool DA, bool DBT, bool DB, bool DD, bool MASK, int C, typename T, typename VU, typename VP>
 __device__ __forceinline__ void cell_apply_merged(int i, int j, int n, const OpCoef<T>& c, const VU& ux, const VU& uy,
                                                   const VP& p, Acc<T>& a) {
     T wx[25], wy[25], pw[9];
-    if constexpr (DA || DB)
-        win_load<C, DA, DB, MASK, SM>(i, j, n, ux, uy, wx, wy, std::make_integer_sequence<int, 25>{});
-    if constexpr (DBT) vwin_load<C, SM>(i, j, n, p, pw, std::make_integer_sequence<int, 9>{});
+    if constexpr (DA || DB) win_load<C, DA, DB, MASK>(i, j, n, ux, uy, wx, wy, std::make_integer_sequence<int, 25>{});
+    if constexpr (DBT) vwin_load<C>(i, j, n, p, pw, std::make_integer_sequence<int, 9>{});
 #pragma unroll
     for (int s = 0; s < 4; ++s) a.au[0][s] = a.au[1][s] = a.bt[0][s] = a.bt[1][s] = a.idg[s] = T(0);
     a.bu = T(0);
     if constexpr (DA) {
-        if constexpr (SM & 1u) { a.au[0][0] = ma_row<C, 0>(c, wx); a.au[1][0] = ma_row<C, 0>(c, wy); }
-        if constexpr (SM & 2u) { a.au[0][1] = ma_row<C, 1>(c, wx); a.au[1][1] = ma_row<C, 1>(c, wy); }
-        if constexpr (SM & 4u) { a.au[0][2] = ma_row<C, 2>(c, wx); a.au[1][2] = ma_row<C, 2>(c, wy); }
-        if constexpr (SM & 8u) { a.au[0][3] = ma_row<C, 3>(c, wx); a.au[1][3] = ma_row<C, 3>(c, wy); }
+        a.au[0][0] = ma_row<C, 0>(c, wx); a.au[1][0] = ma_row<C, 0>(c, wy);
+        a.au[0][1] = ma_row<C, 1>(c, wx); a.au[1][1] = ma_row<C, 1>(c, wy);
+        a.au[0][2] = ma_row<C, 2>(c, wx); a.au[1][2] = ma_row<C, 2>(c, wy);
+        a.au[0][3] = ma_row<C, 3>(c, wx); a.au[1][3] = ma_row<C, 3>(c, wy);
     }
     if constexpr (DBT) {
-        if constexpr (SM & 1u) { a.bt[0][0] = mbt_row<C, 0>(c.MBTx, pw); a.bt[1][0] = mbt_row<C, 0>(c.MBTy, pw); }
-        if constexpr (SM & 2u) { a.bt[0][1] = mbt_row<C, 1>(c.MBTx, pw); a.bt[1][1] = mbt_row<C, 1>(c.MBTy, pw); }
-        if constexpr (SM & 4u) { a.bt[0][2] = mbt_row<C, 2>(c.MBTx, pw); a.bt[1][2] = mbt_row<C, 2>(c.MBTy, pw); }
-        if constexpr (SM & 8u) { a.bt[0][3] = mbt_row<C, 3>(c.MBTx, pw); a.bt[1][3] = mbt_row<C, 3>(c.MBTy, pw); }
+        a.bt[0][0] = mbt_row<C, 0>(c.MBTx, pw); a.bt[1][0] = mbt_row<C, 0>(c.MBTy, pw);
+        a.bt[0][1] = mbt_row<C, 1>(c.MBTx, pw); a.bt[1][1] = mbt_row<C, 1>(c.MBTy, pw);
+        a.bt[0][2] = mbt_row<C, 2>(c.MBTx, pw); a.bt[1][2] = mbt_row<C, 2>(c.MBTy, pw);
+        a.bt[0][3] = mbt_row<C, 3>(c.MBTx, pw); a.bt[1][3] = mbt_row<C, 3>(c.MBTy, pw);
     }
     if constexpr (DD) {
 #pragma unroll

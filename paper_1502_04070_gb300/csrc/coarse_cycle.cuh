@@ -95,7 +95,7 @@ __device__ __forceinline__ void cc_cell(int q, int n, int& i, int& j, int& cls) 
 // within the instruction cache of the one SM that runs the whole cycle.  The loops are unrolled:
 // a mid-line warp works on every phase of every level, and a rolled loop of dependent loads made
 // it the slowest warp of each phase.
-template <bool DA, bool DBT, bool DB, bool DD, unsigned SM>
+template <bool DA, bool DBT, bool DB, bool DD>
 __device__ __noinline__ void cc_apply_dense(int i, int j, int k, const OpCoef<float>& c, const float* ux,
                                              const float* uy, int ld, const float* vp, int ldv, Acc<float>& a) {
 #pragma unroll
@@ -109,7 +109,6 @@ __device__ __noinline__ void cc_apply_dense(int i, int j, int k, const OpCoef<fl
             if constexpr (DA) {
 #pragma unroll
                 for (int s = 0; s < 4; ++s) {
-                    if (!((SM >> s) & 1u)) continue;
                     a.au[0][s] = fmaf(c.MA[k][s][w], vx, a.au[0][s]);
                     a.au[1][s] = fmaf(c.MA[k][s][w], vy, a.au[1][s]);
                 }
@@ -123,7 +122,6 @@ __device__ __noinline__ void cc_apply_dense(int i, int j, int k, const OpCoef<fl
             const float pv = vp[(j + v / 3 - 1) * ldv + i + v % 3 - 1];
 #pragma unroll
             for (int s = 0; s < 4; ++s) {
-                if (!((SM >> s) & 1u)) continue;
                 a.bt[0][s] = fmaf(c.MBTx[k][s][v], pv, a.bt[0][s]);
                 a.bt[1][s] = fmaf(c.MBTy[k][s][v], pv, a.bt[1][s]);
             }
@@ -135,104 +133,43 @@ __device__ __noinline__ void cc_apply_dense(int i, int j, int k, const OpCoef<fl
     }
 }
 
-// operator rows of work item q on a shared-memory level (velocity arrays ux, uy, vertex array vp),
-// the velocity rows of the owned slots in SM only
-template <bool DA, bool DBT, bool DB, bool DD, unsigned SM = 0xFu>
+// operator rows of work item q on a shared-memory level (velocity arrays ux, uy, vertex array vp)
+template <bool DA, bool DBT, bool DB, bool DD>
 __device__ __forceinline__ void cc_apply(int q, const CCLevel& L, const OpCoef<float>& c, const float* ux,
                                          const float* uy, const float* vp, int& i, int& j, Acc<float>& a) {
     int cls;
     const int n = L.n;
     cc_cell(q, n, i, j, cls);
     if (cls == 0) {
-        cell_apply_merged<DA, DBT, DB, DD, false, 0, SM>(i, j, n, c, PViewU<float>{ux, L.ldu},
-                                                         PViewU<float>{uy, L.ldu}, PViewU<float>{vp, L.ldv}, a);
+        cell_apply_merged<DA, DBT, DB, DD, false, 0>(i, j, n, c, PViewU<float>{ux, L.ldu}, PViewU<float>{uy, L.ldu},
+                                                     PViewU<float>{vp, L.ldv}, a);
     } else if (cls == 1) {
-        cell_apply_merged<DA, DBT, DB, DD, false, 1, SM>(i, j, n, c, PViewU<float>{ux, L.ldu},
-                                                         PViewU<float>{uy, L.ldu}, PViewU<float>{vp, L.ldv}, a);
+        cell_apply_merged<DA, DBT, DB, DD, false, 1>(i, j, n, c, PViewU<float>{ux, L.ldu}, PViewU<float>{uy, L.ldu},
+                                                     PViewU<float>{vp, L.ldv}, a);
     } else {
-        cc_apply_dense<DA, DBT, DB, DD, SM>(i, j, stencil_class(i, j, n), c, ux, uy, L.ldu, vp, L.ldv, a);
+        cc_apply_dense<DA, DBT, DB, DD>(i, j, stencil_class(i, j, n), c, ux, uy, L.ldu, vp, L.ldv, a);
     }
-}
-
-// On a level with at most half as many cells as threads, a cell's velocity rows are split between
-// two threads in different warps (slots V, H and slots E, C), which halves the longest dependent
-// chain of a phase; otherwise each thread takes whole cells.
-#define CC_CELLS(cells, BODY)                                                 \
-    if (2 * (cells) <= (int)blockDim.x) {                                     \
-        const int t_ = threadIdx.x;                                           \
-        if (t_ < (cells)) BODY(t_, 0x3u)                                      \
-        else if (t_ < 2 * (cells)) BODY(t_ - (cells), 0xCu)                   \
-    } else {                                                                  \
-        for (int q_ = threadIdx.x; q_ < (cells); q_ += blockDim.x) BODY(q_, 0xFu) \
-    }
-
-// Uzawa phase 1 on work item q: u^{m-1/2} of the slots in SM -> tu
-template <unsigned SM>
-__device__ __forceinline__ void cc_half_step(int q, const CCLevel& L, const OpCoef<float>& c, float tau) {
-    const int n = L.n, ld = L.ldu, n2 = L.n2u;
-    int i, j;
-    Acc<float> a;
-    cc_apply<true, true, false, true, SM>(q, L, c, L.u, L.u + n2, L.p, i, j, a);
-    const CellNodes cn = cell_nodes(i, j, n);
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-        if (!((SM >> s) & 1u) || !slot_exists(cn, s)) continue;
-        int X, Y;
-        slot_pos(i, j, s, X, Y);
-        const int k = Y * ld + X;
-        const bool unk = slot_unknown(cn, s);
-        L.tu[k] = unk ? L.u[k] + tau * (L.f[k] - a.au[0][s] - a.bt[0][s]) * a.idg[s] : 0.f;
-        L.tu[n2 + k] = unk ? L.u[n2 + k] + tau * (L.f[n2 + k] - a.au[1][s] - a.bt[1][s]) * a.idg[s] : 0.f;
-    }
-}
-// Uzawa phase 3 on work item q: u^{m} of the slots in SM
-template <unsigned SM>
-__device__ __forceinline__ void cc_correct(int q, const CCLevel& L, const OpCoef<float>& c, float tau) {
-    const int n = L.n, ld = L.ldu, n2 = L.n2u;
-    int i, j;
-    Acc<float> a;
-    cc_apply<false, true, false, true, SM>(q, L, c, L.tu, L.tu + n2, L.tp, i, j, a);
-    const CellNodes cn = cell_nodes(i, j, n);
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-        if (!((SM >> s) & 1u) || !slot_exists(cn, s)) continue;
-        int X, Y;
-        slot_pos(i, j, s, X, Y);
-        const int k = Y * ld + X;
-        const bool unk = slot_unknown(cn, s);
-        L.u[k] = unk ? L.tu[k] - tau * a.bt[0][s] * a.idg[s] : 0.f;
-        L.u[n2 + k] = unk ? L.tu[n2 + k] - tau * a.bt[1][s] * a.idg[s] : 0.f;
-    }
-}
-// residual on work item q: velocity residual of the slots in SM; the pressure residual goes with
-// the slots V, H
-template <unsigned SM>
-__device__ __forceinline__ void cc_resid(int q, const CCLevel& L, const OpCoef<float>& c) {
-    const int n = L.n, ld = L.ldu, n2 = L.n2u;
-    constexpr bool DB = (SM & 1u) != 0;
-    int i, j;
-    Acc<float> a;
-    cc_apply<true, true, DB, false, SM>(q, L, c, L.u, L.u + n2, L.p, i, j, a);
-    const CellNodes cn = cell_nodes(i, j, n);
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-        if (!((SM >> s) & 1u) || !slot_exists(cn, s)) continue;
-        int X, Y;
-        slot_pos(i, j, s, X, Y);
-        const int k = Y * ld + X;
-        const bool unk = slot_unknown(cn, s);
-        L.tu[k] = unk ? L.f[k] - a.au[0][s] - a.bt[0][s] : 0.f;
-        L.tu[n2 + k] = unk ? L.f[n2 + k] - a.au[1][s] - a.bt[1][s] : 0.f;
-    }
-    if constexpr (DB) L.tp[j * L.ldv + i] = L.g[j * L.ldv + i] - a.bu;
 }
 
 // one Uzawa step (Sec. 4) on a shared-memory level: u^{m-1/2} -> tu, dp -> tp, then u
 __device__ void cc_smooth(const CCLevel& L, const OpCoef<float>& c, float tau, float sigma) {
-    const int n = L.n, n2 = L.n2u, cells = (n + 1) * (n + 1);
-#define CC_HALF(q, sm) cc_half_step<sm>(q, L, c, tau);
-    CC_CELLS(cells, CC_HALF)
-#undef CC_HALF
+    const int n = L.n, ld = L.ldu, n2 = L.n2u, cells = (n + 1) * (n + 1);
+    for (int q = threadIdx.x; q < cells; q += blockDim.x) {
+        int i, j;
+        Acc<float> a;
+        cc_apply<true, true, false, true>(q, L, c, L.u, L.u + n2, L.p, i, j, a);
+        const CellNodes cn = cell_nodes(i, j, n);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            if (!slot_exists(cn, s)) continue;
+            int X, Y;
+            slot_pos(i, j, s, X, Y);
+            const int k = Y * ld + X;
+            const bool unk = slot_unknown(cn, s);
+            L.tu[k] = unk ? L.u[k] + tau * (L.f[k] - a.au[0][s] - a.bt[0][s]) * a.idg[s] : 0.f;
+            L.tu[n2 + k] = unk ? L.u[n2 + k] + tau * (L.f[n2 + k] - a.au[1][s] - a.bt[1][s]) * a.idg[s] : 0.f;
+        }
+    }
     __syncthreads();
     for (int q = threadIdx.x; q < cells; q += blockDim.x) {
         int i, j;
@@ -244,18 +181,45 @@ __device__ void cc_smooth(const CCLevel& L, const OpCoef<float>& c, float tau, f
         L.tp[v] = d;
     }
     __syncthreads();
-#define CC_CORR(q, sm) cc_correct<sm>(q, L, c, tau);
-    CC_CELLS(cells, CC_CORR)
-#undef CC_CORR
+    for (int q = threadIdx.x; q < cells; q += blockDim.x) {
+        int i, j;
+        Acc<float> a;
+        cc_apply<false, true, false, true>(q, L, c, L.tu, L.tu + n2, L.tp, i, j, a);
+        const CellNodes cn = cell_nodes(i, j, n);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            if (!slot_exists(cn, s)) continue;
+            int X, Y;
+            slot_pos(i, j, s, X, Y);
+            const int k = Y * ld + X;
+            const bool unk = slot_unknown(cn, s);
+            L.u[k] = unk ? L.tu[k] - tau * a.bt[0][s] * a.idg[s] : 0.f;
+            L.u[n2 + k] = unk ? L.tu[n2 + k] - tau * a.bt[1][s] * a.idg[s] : 0.f;
+        }
+    }
     __syncthreads();
 }
 
 // r = F - A x on a shared-memory level into (tu, tp)
 __device__ void cc_residual(const CCLevel& L, const OpCoef<float>& c) {
-    const int n = L.n, cells = (n + 1) * (n + 1);
-#define CC_RES(q, sm) cc_resid<sm>(q, L, c);
-    CC_CELLS(cells, CC_RES)
-#undef CC_RES
+    const int n = L.n, ld = L.ldu, n2 = L.n2u, cells = (n + 1) * (n + 1);
+    for (int q = threadIdx.x; q < cells; q += blockDim.x) {
+        int i, j;
+        Acc<float> a;
+        cc_apply<true, true, true, false>(q, L, c, L.u, L.u + n2, L.p, i, j, a);
+        const CellNodes cn = cell_nodes(i, j, n);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            if (!slot_exists(cn, s)) continue;
+            int X, Y;
+            slot_pos(i, j, s, X, Y);
+            const int k = Y * ld + X;
+            const bool unk = slot_unknown(cn, s);
+            L.tu[k] = unk ? L.f[k] - a.au[0][s] - a.bt[0][s] : 0.f;
+            L.tu[n2 + k] = unk ? L.f[n2 + k] - a.au[1][s] - a.bt[1][s] : 0.f;
+        }
+        L.tp[j * L.ldv + i] = L.g[j * L.ldv + i] - a.bu;
+    }
     __syncthreads();
 }
 
