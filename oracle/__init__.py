@@ -15,6 +15,8 @@ Modules:
                  preconditioner (eq. numintroduc), V/W cycles with an exact coarsest solve (Sec. 3),
                  solve loop, direct reference solve
     adjoint   -- gradients of a loss through the discrete solve (symmetric system)
+    experiments -- the numerical experiment of Sec. 5: cone-based exact solution, its L2
+                 projection, the error norm of eq. defMcL and the mean convergence rate
 
 Parity status: every function here is pinned by tests under tests/ against closed forms,
 invariants or brute force (see the test files); nothing is "parity unpinned".
