@@ -575,13 +575,19 @@ def run_batch(args, rank, world):
     return out
 
 
+# The sources that define and launch the float32 Uzawa-step kernels whose DRAM traffic
+# profiles/traffic.json records (the three-kernel step in kernels.cu, the pair tile in
+# uzawa_pair.cu, the variant table in uzawa_fused.cu, and every header they include).
+TRAFFIC_SOURCES = ("common.cuh", "cellops.cuh", "kernels.cuh", "kernels.cu", "coarse_cycle.cuh",
+                   "uzawa_fused.cu", "uzawa_pair.cu")
+
+
 def _kernel_source_sha():
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1502_04070_gb300", "csrc")
-    for nm in sorted(os.listdir(csrc)):
-        if nm.endswith((".cu", ".cuh", ".h", ".cpp")):
-            h.update(open(os.path.join(csrc, nm), "rb").read())
+    for nm in TRAFFIC_SOURCES:
+        h.update(open(os.path.join(csrc, nm), "rb").read())
     return h.hexdigest()[:16]
 
 
