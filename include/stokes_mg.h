@@ -149,6 +149,18 @@ stokes_status stokes_prolong_add(stokes_handle* h, const double* uc, const doubl
 stokes_status stokes_load_vectors(stokes_handle* h, const double* f_nodal, const double* g_nodal,
                                   int project_g, double* f, double* g);
 
+/* Right-hand side of one implicit Euler step of the time-dependent Stokes problem
+ *     u_t - Laplace u + grad p = f,  div u = g,  u = 0 on the boundary      (unit viscosity),
+ * whose step with length dt is the generalized Stokes system of Sec. 1 with beta = 1/dt (the
+ * handle's current beta; another viscosity is a rescaling the caller applies to beta, f and p):
+ *     f = (f_h + beta u_prev, phi_i) on interior P2 nodes,  g = (g_h, psi_i) with g_h shifted to
+ * zero mean, where f_nodal, g_nodal are the nodal data of the new time level (layouts and
+ * interpolants as in stokes_load_vectors) and u_prev the velocity of the previous level (layout of
+ * u, zero on the boundary).  The first call allocates one velocity-sized scratch array owned by
+ * the handle.  f and g must not alias f_nodal or g_nodal.  Asynchronous on the handle's stream. */
+stokes_status stokes_euler_rhs(stokes_handle* h, const double* u_prev, const double* f_nodal, const double* g_nodal,
+                               double* f, double* g);
+
 /* g <- g - (1^T g) w,  w = M_P 1 (w sums to 1): makes a pressure right-hand side orthogonal to the
  * constant pressure, the kernel of the matrix of eq. gen:bil:mv (Sec. 1: int g = 0).  Needed for
  * adjoint right-hand sides whose pressure part does not sum to zero.  In place, asynchronous. */

@@ -12,12 +12,14 @@ i.e. one generalized Stokes system (eq. stokes, Sec. 1) per step, whose discrete
 is the load vector of the nodal data f^{n+1} + beta u^n (the velocity load is linear in the
 nodal values: (f_h + beta u^n, phi_i) = M_U f + beta M_U u^n).  Reading where the paper is silent:
 unit viscosity (another viscosity is a rescaling of t, p and f by the caller) and the implicit
-Euler scheme.  Every step is solved exactly (sparse direct, zero-mean pressure as a border).
+Euler scheme.  Every step is solved exactly (sparse LU of the bordered system, factorised once
+per step length, zero-mean pressure as the border).
 """
 import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
 
 from . import fem
-from . import multigrid as mg
 
 
 def euler_rhs(disc: fem.Discretization, dt, u_prev_lat, f_nodal, g_nodal):
@@ -31,16 +33,27 @@ def implicit_euler(disc: fem.Discretization, dt, u0_lat, forcing, n_steps):
     """n_steps implicit Euler steps from the velocity u0 (lattice layout, zero on the boundary).
     forcing(n) -> (f_nodal, g_nodal) of step n = 1 .. n_steps.  Returns the list of unknown vectors
     x^1 .. x^n (velocity on the interior nodes, then pressure)."""
-    S = disc.system(1.0 / dt)
+    solve = step_solver(disc, dt)
     u = np.asarray(u0_lat, np.float64)
     out = []
     for n in range(1, n_steps + 1):
         fn, gn = forcing(n)
-        F = euler_rhs(disc, dt, u, fn, gn)
-        x = mg.direct_solve(S, disc, F)
+        x = solve(euler_rhs(disc, dt, u, fn, gn))
         out.append(x)
         u, _ = disc.from_vec(x)
     return out
+
+
+def step_solver(disc: fem.Discretization, dt):
+    """Exact solve of the step's system [[K + M/dt, B^T], [B, 0]] x = F with the zero-mean pressure
+    condition w^T p = 0 as a border row and column (w = M_P 1); the matrix is the same for every
+    step, so it is factorised once (sparse LU)."""
+    S = disc.system(1.0 / dt)
+    w = np.concatenate([np.zeros(disc.nu), disc.w])
+    Sb = sp.bmat([[S, sp.csr_matrix(w[:, None])], [sp.csr_matrix(w[None, :]), None]]).tocsc()
+    lu = spla.splu(Sb)
+    n = S.shape[0]
+    return lambda F: lu.solve(np.concatenate([F, [0.0]]))[:n]
 
 
 def energy_terms(disc: fem.Discretization, x_prev_u, x_u):

@@ -62,6 +62,7 @@ SIGNATURES = {
     "stokes_load_vectors": (_I, [_P, _P, _P, _I, _P, _P]),
     "stokes_mass_dot": (_I, [_P, _P, _P, ctypes.POINTER(_D)]),
     "stokes_make_consistent": (_I, [_P, _P]),
+    "stokes_euler_rhs": (_I, [_P, _P, _P, _P, _P, _P]),
     "stokes_residual_norm2_noalloc": (_I, [_I, _D, _P, _P, _P, _P, _P, _P]),
     "stokes_batch_setup": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(Params), _P, _I,
                                 ctypes.POINTER(_P)]),

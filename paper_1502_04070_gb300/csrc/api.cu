@@ -16,6 +16,11 @@
 #include "elements.h"
 #include "kernels.cuh"
 
+namespace smg {
+// timestep.cu: w = f + beta u over n values (the nodal data of an implicit Euler right-hand side)
+cudaError_t launch_euler_nodal(cudaStream_t st, size_t n, double beta, const double* f, const double* u, double* w);
+}  // namespace smg
+
 using namespace smg;
 
 namespace {
@@ -147,6 +152,7 @@ struct stokes_handle_t {
     int* ictl = nullptr;
     double* dhist = nullptr;                // residual^2 per step, device (kHistCap entries)
     double* hhist = nullptr;                // pinned mirror
+    double* euler_w = nullptr;              // nodal data of an implicit Euler right-hand side
     unsigned long long launches = 0;        // kernels launched by this handle (graph nodes included)
     // optional timing of the finest-level smoothing steps and of the float64 residual: event
     // pairs recorded inside the captured graph (cudaEventRecordExternal)
@@ -499,6 +505,7 @@ void stokes_destroy(stokes_handle* h) {
     if (h->ictl) cudaFree(h->ictl);
     if (h->dhist) cudaFree(h->dhist);
     if (h->hhist) cudaFreeHost(h->hhist);
+    if (h->euler_w) cudaFree(h->euler_w);
     for (auto e : h->ev) cudaEventDestroy(e);
     for (auto& l : h->h64) free_level(l);
     for (auto& l : h->h32) free_level(l);
@@ -805,6 +812,19 @@ stokes_status stokes_load_vectors(stokes_handle* h, const double* f_nodal, const
     if (!h || !f_nodal || !g_nodal || !f || !g) return STOKES_ERR_BAD_ARG;
     launch_load<double>(h->st, h->fin().n, h->mass, f_nodal, g_nodal, f, g, project_g, h->partial, h->scal + 4);
     h->launches += project_g ? 3 : 1;
+    CK(cudaGetLastError());
+    return STOKES_OK;
+}
+
+stokes_status stokes_euler_rhs(stokes_handle* h, const double* u_prev, const double* f_nodal, const double* g_nodal,
+                               double* f, double* g) {
+    if (!h || !u_prev || !f_nodal || !g_nodal || !f || !g) return STOKES_ERR_BAD_ARG;
+    const int n = h->fin().n;
+    const size_t nvel = 2 * (size_t)(2 * n + 1) * (2 * n + 1);
+    if (!h->euler_w) CK(cudaMalloc(&h->euler_w, nvel * sizeof(double)));
+    CK(launch_euler_nodal(h->st, nvel, h->prm.beta, f_nodal, u_prev, h->euler_w));
+    launch_load<double>(h->st, n, h->mass, h->euler_w, g_nodal, f, g, 1, h->partial, h->scal + 4);
+    h->launches += 4;
     CK(cudaGetLastError());
     return STOKES_OK;
 }

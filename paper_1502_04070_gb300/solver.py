@@ -199,6 +199,16 @@ class Solver:
     def kernel_launches(self):
         return int(self._lib.stokes_kernel_launches(self._h))
 
+    def euler_rhs(self, u_prev, f_nodal, g_nodal):
+        """Right-hand side (f, g) of one implicit Euler step with beta = 1/dt (stokes_euler_rhs):
+        the load vectors of the nodal data f_nodal + beta u_prev and g_nodal (shifted to zero mean)."""
+        f, g = self.zeros_u(), self.zeros_p()
+        B.check(self._lib.stokes_euler_rhs(self._h, self._chk(u_prev, self.shape_u, "u_prev"),
+                                           self._chk(f_nodal, self.shape_u, "f_nodal"),
+                                           self._chk(g_nodal, self.shape_p, "g_nodal"), _ptr(f), _ptr(g)),
+                "stokes_euler_rhs")
+        return f, g
+
     def make_consistent(self, g):
         """g <- g - (sum g) M_P 1 in place (pressure right-hand side orthogonal to constants)."""
         B.check(self._lib.stokes_make_consistent(self._h, self._chk(g, self.shape_p, "g")), "stokes_make_consistent")

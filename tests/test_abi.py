@@ -56,6 +56,15 @@ def test_setup_rejects_bad_arguments_without_touching_the_gpu():
     assert lib.stokes_setup(None, None, ctypes.byref(h)) == _binding.ERR_BAD_ARG
 
 
+def test_entry_points_reject_null_handles_without_touching_the_gpu():
+    from paper_1502_04070_gb300 import _binding
+    lib = _binding.load()
+    buf = ctypes.c_void_p(16)       # never dereferenced: the null handle is rejected first
+    assert lib.stokes_euler_rhs(None, buf, buf, buf, buf, buf) == _binding.ERR_BAD_ARG
+    assert lib.stokes_load_vectors(None, buf, buf, 1, buf, buf) == _binding.ERR_BAD_ARG
+    assert lib.stokes_cycle(None, buf, buf, buf, buf) == _binding.ERR_BAD_ARG
+
+
 def test_step_variant_selection_without_gpu():
     """The variant table is host state: out-of-range sizes and variants are rejected, a valid
     choice reads back."""
