@@ -18,6 +18,7 @@ Modules:
     experiments -- the numerical experiment of Sec. 5: cone-based exact solution, its L2
                  projection, the error norm of eq. defMcL and the mean convergence rate
     timestep  -- implicit Euler steps of the time-dependent Stokes problem (Sec. 1: beta = 1/dt)
+    lshape    -- the L-shaped (non-convex) domain: masked meshes, unknowns and transfers (Sec. 1)
 
 Parity status: every function here is pinned by tests under tests/ against closed forms,
 invariants or brute force (see the test files); nothing is "parity unpinned".

@@ -177,6 +177,7 @@ class Discretization:
         self.Mi = self.M[I][:, I].tocsr()
         self.Bi = sp.hstack([self.Bx[:, I], self.By[:, I]]).tocsr()   # (nv, 2 ni)
         self.w = np.asarray(self.MP.sum(axis=1)).ravel()             # w = M_P 1 = int psi_i
+        self.pnodes = np.arange(self.nv)                             # pressure unknowns: every vertex
 
     # sizes of the unknown vector x = [u_x (ni); u_y (ni); p (nv)]
     @property

@@ -65,4 +65,5 @@ def prolongation(coarse: fem.Discretization, fine: fem.Discretization):
     """I_{k-1}^k on the unknown vectors [u_x; u_y; p] (Dirichlet rows/columns dropped)."""
     P2, P1 = prolongation_full(coarse, fine)
     P2i = P2[fine.interior][:, coarse.interior]
-    return sp.block_diag([P2i, P2i, P1]).tocsr()
+    P1p = P1[fine.pnodes][:, coarse.pnodes]                    # pressure unknowns (all vertices on the square)
+    return sp.block_diag([P2i, P2i, P1p]).tocsr()
