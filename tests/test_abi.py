@@ -90,3 +90,10 @@ def test_product_path_fails_loudly_without_library(tmp_path):
             _binding.load(str(tmp_path / "missing.so"))
     finally:
         _binding._lib = saved
+
+
+def test_time_stepper_rejects_bad_step_without_gpu():
+    from paper_1502_04070_gb300.timestep import ImplicitEuler
+    for dt in (0.0, -1e-3, float("nan")):
+        with pytest.raises(ValueError):
+            ImplicitEuler(4, dt)
