@@ -140,6 +140,15 @@ def golden_cycles():
     return {r["beta"]: r["cycles"] for r in g["k8_sweep"]["runs"]}
 
 
+def oracle_cycles_by_beta():
+    """The oracle's float64 cycle counts to 1e-8 per beta (the written golden values, no oracle
+    call), keyed like cycles_per_beta; None if the file is missing."""
+    try:
+        return {str(float(b)): c for b, c in golden_cycles().items()}
+    except (OSError, KeyError, TypeError, ValueError):
+        return None
+
+
 # ------------------------------------------------------------------------------ CPU oracle
 def oracle_sample(n_cycles_per_beta=1, betas=(1.0,)):
     """Times the oracle (CPU float64 SciPy, as it stands) on a bounded sample of the workload:
@@ -513,7 +522,8 @@ def run_ours(args, rank, world, local_rank):
                 "config": {"workload": WORKLOAD, "precision": args.precision, "dof_per_solve": n_dof,
                            "solves_per_step": len(BETAS), "solves_per_s": len(BETAS) * args.steps * world / (ms / 1000),
                            "l2": "256 MB buffer written between steps (inside the timed region)",
-                           "cycles_per_beta": cycles, "mean_rate_per_beta": rates,
+                           "cycles_per_beta": cycles, "oracle_cycles_per_beta": oracle_cycles_by_beta(),
+                           "mean_rate_per_beta": rates,
                            "final_rel_residual_per_beta": final_rel,
                            "execution": "the six solves in one CUDA-graph launch (one device-side loop each)",
                            "float32_step_variant_per_level": variants},
