@@ -281,6 +281,24 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------ ours
+def job_throughput(units_per_rank_step, steps, world, ms):
+    """Whole-job rate (weak scaling): the units every rank processed in `steps` steps, divided by the
+    timed region in milliseconds (the maximum over ranks)."""
+    return units_per_rank_step * steps * world / (ms / 1000.0)
+
+
+def max_over_all_ranks(v, device):
+    """The maximum of a host number over the ranks of the default process group (all-reduce MAX of a
+    one-element float64 tensor on `device`); the number itself when no group is initialised."""
+    import torch
+    import torch.distributed as td
+    if not (td.is_available() and td.is_initialized()) or td.get_world_size() == 1:
+        return v
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -298,11 +316,7 @@ def run_ours(args, rank, world, local_rank):
             td.barrier()
 
     def max_over_ranks(v):
-        if not dist:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        td.all_reduce(t, op=td.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_all_ranks(v, "cuda")
 
     levels = K_LEVEL + 1
     fn_np, gn_np = workloads.random_nodal(K_LEVEL, 1 + rank)
@@ -360,7 +374,7 @@ def run_ours(args, rank, world, local_rank):
     ms = max_over_ranks(e0.elapsed_time(e1))
     launches = sweep.kernel_launches() - launches0
     n_dof = dofs(K_LEVEL)
-    value = nb * n_dof * args.steps * world / (ms / 1000.0)
+    value = job_throughput(nb * n_dof, args.steps, world, ms)
     cycles = {str(b): c for b, c in zip(BETAS, result["cycles"])}
     # mean rate per cycle of the relative residual (the start x = 0 has residual ||F||)
     rates = {str(b): round(r ** (1.0 / c), 4) for b, c, r in zip(BETAS, result["cycles"], result["rel"])}
