@@ -180,6 +180,24 @@ def direct_solve(S, disc: fem.Discretization, F):
     return spla.spsolve(Sb, np.concatenate([F, [0.0]]))[:n]
 
 
+def smoother_conditions(lvl: Level, tau=0.8, sigma=0.8):
+    """Diagnostic of the hypotheses of the smoothing analysis (Sec. 4, eq. def:tau:sigma):
+    tau^-1 Ahat >= A  and  sigma^-1 Shat >= tau B Ahat^-1 B^T, i.e.
+    lambda_max(Ahat^-1 A) <= 1/tau  and  lambda_max(Shat^-1 B Ahat^-1 B^T) <= 1/(sigma tau),
+    by dense symmetric eigenvalues of the diagonally scaled matrices (small levels only).
+    Returns the two largest eigenvalues and whether each condition holds."""
+    A = lvl.A.toarray()
+    d = 1.0 / np.sqrt(lvl.Ahat)
+    lam_a = np.linalg.eigvalsh(d[:, None] * A * d[None, :])[-1]
+    B = lvl.B.toarray()
+    St = B @ (B.T / lvl.Ahat[:, None])
+    e = 1.0 / np.sqrt(lvl.Shat)
+    St = 0.5 * (St + St.T)
+    lam_s = np.linalg.eigvalsh(e[:, None] * St * e[None, :])[-1]
+    return {"lambda_A": lam_a, "lambda_S": lam_s,
+            "A_condition": lam_a <= 1.0 / tau, "S_condition": lam_s <= 1.0 / (sigma * tau)}
+
+
 def contraction(hist):
     """Per-cycle factors q_i = ||r_i|| / ||r_{i-1}|| and their geometric mean (Sec. 5 mean rate)."""
     hist = np.asarray(hist)

@@ -157,3 +157,21 @@ def test_adjoint_vs_finite_differences(discs):
     eps = 1e-4 * beta
     fd = (L(F, beta + eps) - L(F, beta - eps)) / (2 * eps)
     assert abs(fd - gb) < 1e-6 * max(abs(fd), 1e-12)
+
+
+@pytest.mark.parametrize("beta", [0.0, 1e4, 1e8])
+def test_smoother_condition_diagnostic(discs, beta):
+    """The diagnostic of the smoothing hypotheses (Sec. 4): each largest eigenvalue of a diagonally
+    scaled SPD matrix lies between its mean diagonal, 1, and the Gershgorin bound max_i
+    sum_j |M_ij| / M_ii; with tau = sigma = 0.8 neither condition holds on this mesh (lambda_A
+    1.69-2.19 > 1.25, lambda_S 1.95 > 1.5625 at k = 3), as observed."""
+    H = mg.Hierarchy(4, beta, discs[:4])
+    lvl = H.finest
+    c = mg.smoother_conditions(lvl)
+    A = abs(lvl.A).toarray()
+    g_a = (A.sum(axis=1) / lvl.Ahat).max()
+    B = lvl.B.toarray()
+    St = abs(B @ (B.T / lvl.Ahat[:, None]))
+    g_s = (St.sum(axis=1) / lvl.Shat).max()
+    assert 1.0 <= c["lambda_A"] <= g_a and 1.0 <= c["lambda_S"] <= g_s
+    assert not c["A_condition"] and not c["S_condition"]
