@@ -149,6 +149,21 @@ stokes_status stokes_prolong_add(stokes_handle* h, const double* uc, const doubl
 stokes_status stokes_load_vectors(stokes_handle* h, const double* f_nodal, const double* g_nodal,
                                   int project_g, double* f, double* g);
 
+/* Host-only views of the operator tables the kernels use (no device work; callable without a GPU).
+ * stokes_stencil_class: the stencil class (0..6) of cell (i, j), 0 <= i, j <= N = 2^levels, by the
+ * orientations of its four squares (Sec. 5 mesh: 0 / 1 off the mid-lines, 2..6 on them).
+ * stokes_stencil_rows: for class cls of a level with N = 2^levels and the given beta, the rows of the
+ * matrix of eq. gen:bil:mv at the cell's four velocity nodes s = V (2i, 2j), H (2i+1, 2j),
+ * E (2i, 2j+1), C (2i+1, 2j+1), as written by the library:
+ *   ma[s*25 + (dy+2)*5 + dx+2]  = (K + beta M)(node s, lattice node (2i+dx, 2j+dy))   (caller array of 100)
+ *   mbtx[s*9 + (dj+1)*3 + di+1] = Bx(vertex (i+di, j+dj), node s), mbty likewise        (36 each)
+ *   mbx[(dy+2)*5 + dx+2]        = Bx(vertex (i, j), lattice node (2i+dx, 2j+dy)), mby likewise (25 each)
+ *   midg[s]                     = 1 / (K + beta M)(node s, node s)                       (4)
+ * with B_ij = (div phi_j, psi_i) split by component.  STOKES_ERR_BAD_ARG on out-of-range input. */
+stokes_status stokes_stencil_class(int levels, int i, int j, int* cls);
+stokes_status stokes_stencil_rows(int levels, double beta, int cls, double* ma, double* mbtx, double* mbty,
+                                  double* mbx, double* mby, double* midg);
+
 /* Right-hand side of one implicit Euler step of the time-dependent Stokes problem
  *     u_t - Laplace u + grad p = f,  div u = g,  u = 0 on the boundary      (unit viscosity),
  * whose step with length dt is the generalized Stokes system of Sec. 1 with beta = 1/dt (the

@@ -816,6 +816,29 @@ stokes_status stokes_load_vectors(stokes_handle* h, const double* f_nodal, const
     return STOKES_OK;
 }
 
+stokes_status stokes_stencil_class(int levels, int i, int j, int* cls) {
+    if (levels < 1 || levels > 13 || !cls) return STOKES_ERR_BAD_ARG;
+    const int n = 1 << levels;
+    if (i < 0 || j < 0 || i > n || j > n) return STOKES_ERR_BAD_ARG;
+    *cls = stencil_class(i, j, n);
+    return STOKES_OK;
+}
+
+stokes_status stokes_stencil_rows(int levels, double beta, int cls, double* ma, double* mbtx, double* mbty,
+                                  double* mbx, double* mby, double* midg) {
+    if (levels < 1 || levels > 13 || !(beta >= 0.0) || !std::isfinite(beta) || cls < 0 || cls >= kStencilClasses ||
+        !ma || !mbtx || !mbty || !mbx || !mby || !midg)
+        return STOKES_ERR_BAD_ARG;
+    const OpCoef<double> c = make_coef<double>(1 << levels, beta);
+    std::memcpy(ma, c.MA[cls], sizeof(c.MA[cls]));
+    std::memcpy(mbtx, c.MBTx[cls], sizeof(c.MBTx[cls]));
+    std::memcpy(mbty, c.MBTy[cls], sizeof(c.MBTy[cls]));
+    std::memcpy(mbx, c.MBx[cls], sizeof(c.MBx[cls]));
+    std::memcpy(mby, c.MBy[cls], sizeof(c.MBy[cls]));
+    std::memcpy(midg, c.MIdg[cls], sizeof(c.MIdg[cls]));
+    return STOKES_OK;
+}
+
 stokes_status stokes_euler_rhs(stokes_handle* h, const double* u_prev, const double* f_nodal, const double* g_nodal,
                                double* f, double* g) {
     if (!h || !u_prev || !f_nodal || !g_nodal || !f || !g) return STOKES_ERR_BAD_ARG;

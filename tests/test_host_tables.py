@@ -1,0 +1,124 @@
+"""Host logic of the CUDA library, checked without a GPU: the stencil class of every cell and the
+node-stencil rows the kernels apply (C-ABI stokes_stencil_class, stokes_stencil_rows) against the
+oracle's mesh and its assembled matrices of eq. gen:bil:mv.
+
+The class of a cell is read here from the oracle's triangle list: the orientation of each of its
+four squares is the direction of that square's diagonal edge ("/" = 0, "\\" = 1), and the four
+bits (square (i, j), (i-1, j), (i, j-1), (i-1, j-1)) name the class (0x0 -> 0, 0xF -> 1, the
+mid-line patterns 0x5, 0xA, 0x3, 0xC -> 2..5, the centre 0x6 -> 6)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from oracle import fem
+
+PATTERN_TO_CLASS = {0x0: 0, 0xF: 1, 0x5: 2, 0xA: 3, 0x3: 4, 0xC: 5, 0x6: 6}
+
+
+def square_orientations(m):
+    """orient[a, b] of the square with lower-left vertex (a/N, b/N), from the diagonal edges."""
+    n = m.n
+    orient = -np.ones((n, n), dtype=int)
+    P = m.verts[m.tris]                                   # P2-lattice coordinates, vertices even
+    for e0, e1 in ((0, 1), (1, 2), (2, 0)):
+        d = P[:, e1] - P[:, e0]
+        diag = (np.abs(d[:, 0]) == 2) & (np.abs(d[:, 1]) == 2)
+        lo = np.minimum(P[diag, e0], P[diag, e1]) // 2
+        orient[lo[:, 0], lo[:, 1]] = np.where(d[diag, 0] * d[diag, 1] > 0, 0, 1)
+    assert (orient >= 0).all()
+    return orient
+
+
+def cell_class(orient, i, j):
+    bits = orient[i, j] | (orient[i - 1, j] << 1) | (orient[i, j - 1] << 2) | (orient[i - 1, j - 1] << 3)
+    return PATTERN_TO_CLASS[int(bits)]
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1502_04070_gb300 import _binding
+    return _binding.load()
+
+
+@pytest.fixture(scope="module")
+def discs():
+    return fem.discretizations(5)
+
+
+@pytest.mark.parametrize("k", [2, 4])
+def test_stencil_classes_match_the_mesh(lib, discs, k):
+    m = discs[k].mesh
+    n = m.n
+    orient = square_orientations(m)
+    seen = set()
+    out = ctypes.c_int()
+    for i in range(1, n):
+        for j in range(1, n):
+            assert lib.stokes_stencil_class(k + 1, i, j, ctypes.byref(out)) == 0
+            c = cell_class(orient, i, j)
+            assert out.value == c, (i, j, out.value, c)
+            seen.add(c)
+    assert seen == set(range(7))
+
+
+@pytest.mark.parametrize("beta", [0.0, 7.5, 1e6])
+@pytest.mark.parametrize("k", [3, 4])
+def test_stencil_rows_match_the_assembled_matrices(lib, discs, k, beta):
+    d = discs[k]
+    n = d.n
+    A = (d.K + beta * d.M).tocsr()
+    Bx, By = d.Bx.tocsr(), d.By.tocsr()
+    BxT, ByT = Bx.T.tocsr(), By.T.tocsr()
+    lat = lambda X, Y: Y * (2 * n + 1) + X
+    vert = lambda a, b: b * (n + 1) + a
+    orient = square_orientations(d.mesh)
+    buf = {nm: np.zeros(sz) for nm, sz in (("ma", 100), ("mbtx", 36), ("mbty", 36), ("mbx", 25), ("mby", 25),
+                                           ("midg", 4))}
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    for cls in range(7):
+        assert lib.stokes_stencil_rows(k + 1, float(beta), cls, *(ptr(buf[nm]) for nm in
+                                       ("ma", "mbtx", "mbty", "mbx", "mby", "midg"))) == 0
+        cells = [(i, j) for i in range(2, n - 1) for j in range(2, n - 1) if cell_class(orient, i, j) == cls]
+        assert cells
+        for (i, j) in cells[:6]:
+            win = [(dx, dy) for dy in range(-2, 3) for dx in range(-2, 3)]
+            vwin = [(di, dj) for dj in range(-1, 2) for di in range(-1, 2)]
+            for s in range(4):
+                X, Y = 2 * i + (s & 1), 2 * j + (s >> 1)
+                row = A[lat(X, Y)].toarray().ravel()
+                scale = np.abs(row).max()
+                for w, (dx, dy) in enumerate(win):
+                    c = lat(2 * i + dx, 2 * j + dy)
+                    assert abs(buf["ma"][s * 25 + w] - row[c]) <= 1e-13 * scale, (cls, s, dx, dy)
+                    row[c] = 0.0
+                assert np.abs(row).max() == 0.0                       # no coupling outside the window
+                assert abs(buf["midg"][s] * A[lat(X, Y), lat(X, Y)] - 1.0) <= 1e-14
+                for name, BT in (("mbtx", BxT), ("mbty", ByT)):
+                    col = BT[lat(X, Y)].toarray().ravel()
+                    bscale = max(np.abs(col).max(), 1e-300)
+                    for w, (di, dj) in enumerate(vwin):
+                        v = vert(i + di, j + dj)
+                        assert abs(buf[name][s * 9 + w] - col[v]) <= 1e-13 * bscale, (name, cls, s, di, dj)
+                        col[v] = 0.0
+                    assert np.abs(col).max() == 0.0
+            for name, Bm in (("mbx", Bx), ("mby", By)):
+                row = Bm[vert(i, j)].toarray().ravel()
+                bscale = np.abs(row).max()
+                for w, (dx, dy) in enumerate(win):
+                    c = lat(2 * i + dx, 2 * j + dy)
+                    assert abs(buf[name][w] - row[c]) <= 1e-13 * bscale, (name, cls, dx, dy)
+                    row[c] = 0.0
+                assert np.abs(row).max() == 0.0
+
+
+def test_table_entry_points_reject_bad_arguments(lib):
+    out = ctypes.c_int()
+    a = np.zeros(100)
+    p = a.ctypes.data_as(ctypes.c_void_p)
+    assert lib.stokes_stencil_class(0, 1, 1, ctypes.byref(out)) != 0
+    assert lib.stokes_stencil_class(3, -1, 1, ctypes.byref(out)) != 0
+    assert lib.stokes_stencil_class(3, 1, 9, ctypes.byref(out)) != 0
+    assert lib.stokes_stencil_rows(3, 1.0, 7, p, p, p, p, p, p) != 0
+    assert lib.stokes_stencil_rows(3, -1.0, 0, p, p, p, p, p, p) != 0
+    assert lib.stokes_stencil_rows(3, 1.0, 0, None, p, p, p, p, p) != 0
