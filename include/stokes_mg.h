@@ -160,6 +160,16 @@ stokes_status stokes_load_vectors(stokes_handle* h, const double* f_nodal, const
  *   mbx[(dy+2)*5 + dx+2]        = Bx(vertex (i, j), lattice node (2i+dx, 2j+dy)), mby likewise (25 each)
  *   midg[s]                     = 1 / (K + beta M)(node s, node s)                       (4)
  * with B_ij = (div phi_j, psi_i) split by component.  STOKES_ERR_BAD_ARG on out-of-range input. */
+/* Host-only (no device work): the canonical P2 embedding weights of Sec. 3 that the transfer kernels
+ * use, w[((o*9 + L)*5 + fb)*5 + fa] = value of the local basis function L = 3*b + a (local lattice
+ * node (a, b) in {0,1,2}^2) of a coarse square of orientation o at its fine lattice point (fa, fb) in
+ * {0..4}^2 (caller array of 450); and the inverse of the level-0 system (N = 2) of eq. gen:bil:mv
+ * bordered with the zero-mean pressure condition, first 27 x 27 block, row-major, unknowns u_x at the
+ * interior lattice points (X, Y) in [1, 3]^2 (Y outer), then u_y, then p at the 3 x 3 vertices
+ * (caller array of 729).  STOKES_ERR_BAD_ARG on bad input or a singular system. */
+stokes_status stokes_transfer_weights(double* w);
+stokes_status stokes_coarse_inverse(double beta, double* inv);
+
 stokes_status stokes_stencil_class(int levels, int i, int j, int* cls);
 stokes_status stokes_stencil_rows(int levels, double beta, int cls, double* ma, double* mbtx, double* mbty,
                                   double* mbx, double* mby, double* midg);

@@ -839,6 +839,18 @@ stokes_status stokes_stencil_rows(int levels, double beta, int cls, double* ma, 
     return STOKES_OK;
 }
 
+stokes_status stokes_transfer_weights(double* w) {
+    if (!w) return STOKES_ERR_BAD_ARG;
+    const TransferWeights W = transfer_weights();
+    std::memcpy(w, &W.P2[0][0][0][0], sizeof(W.P2));
+    return STOKES_OK;
+}
+
+stokes_status stokes_coarse_inverse(double beta, double* inv) {
+    if (!inv || !(beta >= 0.0) || !std::isfinite(beta)) return STOKES_ERR_BAD_ARG;
+    return coarse_inverse(squares(), beta, inv) ? STOKES_OK : STOKES_ERR_BAD_ARG;
+}
+
 stokes_status stokes_euler_rhs(stokes_handle* h, const double* u_prev, const double* f_nodal, const double* g_nodal,
                                double* f, double* g) {
     if (!h || !u_prev || !f_nodal || !g_nodal || !f || !g) return STOKES_ERR_BAD_ARG;

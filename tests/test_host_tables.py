@@ -1,6 +1,8 @@
 """Host logic of the CUDA library, checked without a GPU: the stencil class of every cell and the
 node-stencil rows the kernels apply (C-ABI stokes_stencil_class, stokes_stencil_rows) against the
-oracle's mesh and its assembled matrices of eq. gen:bil:mv.
+oracle's mesh and its assembled matrices of eq. gen:bil:mv; the canonical embedding weights of the
+transfer kernels (stokes_transfer_weights) against the oracle's prolongation; and the level-0
+bordered inverse (stokes_coarse_inverse) against a dense inverse of the oracle's level-0 matrix.
 
 The class of a cell is read here from the oracle's triangle list: the orientation of each of its
 four squares is the direction of that square's diagonal edge ("/" = 0, "\\" = 1), and the four
@@ -122,3 +124,43 @@ def test_table_entry_points_reject_bad_arguments(lib):
     assert lib.stokes_stencil_rows(3, 1.0, 7, p, p, p, p, p, p) != 0
     assert lib.stokes_stencil_rows(3, -1.0, 0, p, p, p, p, p, p) != 0
     assert lib.stokes_stencil_rows(3, 1.0, 0, None, p, p, p, p, p) != 0
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_transfer_weights_equal_the_oracle_embedding(lib, discs, k):
+    """The embedding weights the transfer kernels apply (stokes_transfer_weights) equal the oracle's
+    prolongation (coarse basis functions evaluated at the fine nodes, Sec. 3) for every coarse
+    square, local node and fine lattice point of the square."""
+    from oracle import transfer
+    w = np.zeros(2 * 9 * 5 * 5)
+    assert lib.stokes_transfer_weights(w.ctypes.data_as(ctypes.c_void_p)) == 0
+    w = w.reshape(2, 9, 5, 5)
+    coarse, fine = discs[k], discs[k + 1]
+    P2, _ = transfer.prolongation_full(coarse, fine)
+    P2 = P2.toarray()
+    nc, nf = coarse.n, fine.n
+    orient = square_orientations(coarse.mesh)
+    for a in range(nc):
+        for b in range(nc):
+            o = orient[a, b]
+            for L in range(9):
+                cc = (2 * b + L // 3) * (2 * nc + 1) + 2 * a + L % 3
+                for fb in range(5):
+                    for fa in range(5):
+                        ff = (4 * b + fb) * (2 * nf + 1) + 4 * a + fa
+                        assert abs(P2[ff, cc] - w[o, L, fb, fa]) <= 1e-14, (a, b, L, fa, fb)
+
+
+@pytest.mark.parametrize("beta", [0.0, 1.0, 1e4])
+def test_coarse_inverse_equals_the_oracle_bordered_solve(lib, discs, beta):
+    """The level-0 inverse (host Gauss-Jordan, stokes_coarse_inverse) against a dense inverse of the
+    oracle's bordered level-0 matrix; the unknown orders coincide (interior u_x, u_y row-major,
+    then the vertex pressures)."""
+    from oracle import multigrid as mg
+    inv = np.zeros(27 * 27)
+    assert lib.stokes_coarse_inverse(float(beta), inv.ctypes.data_as(ctypes.c_void_p)) == 0
+    inv = inv.reshape(27, 27)
+    H = mg.Hierarchy(1, beta, discs[:1])
+    ref = np.linalg.inv(H.coarse_bordered)[:27, :27]
+    assert np.abs(inv - ref).max() <= 1e-10 * np.abs(ref).max()
+    assert lib.stokes_coarse_inverse(-1.0, inv.ctypes.data_as(ctypes.c_void_p)) != 0
