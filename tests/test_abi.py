@@ -97,3 +97,52 @@ def test_time_stepper_rejects_bad_step_without_gpu():
     for dt in (0.0, -1e-3, float("nan")):
         with pytest.raises(ValueError):
             ImplicitEuler(4, dt)
+
+
+def test_every_entry_point_rejects_bad_arguments_before_device_work():
+    """Failure handling (every call returns a status, nothing aborts): each entry point that takes a
+    handle rejects a null handle, and the handle-free ones reject out-of-range sizes, before any
+    CUDA call; destroy and the launch counters accept null."""
+    from paper_1502_04070_gb300 import _binding as B
+    lib = B.load()
+    buf = ctypes.c_void_p(16)                  # never dereferenced
+    d = ctypes.c_double()
+    bad = B.ERR_BAD_ARG
+    calls = {
+        "stokes_autotune": (None,),
+        "stokes_set_beta": (None, 1.0),
+        "stokes_sizes": (None, None, None, None, None),
+        "stokes_cycle": (None, buf, buf, buf, buf),
+        "stokes_solve": (None, buf, buf, buf, buf, 1e-8, 10, None, None),
+        "stokes_residual": (None, buf, buf, buf, buf, buf, buf),
+        "stokes_residual_norm": (None, buf, buf, buf, buf, ctypes.byref(d)),
+        "stokes_smooth": (None, buf, buf, buf, buf, 1),
+        "stokes_smooth_f32": (None, buf, buf, buf, buf, 1),
+        "stokes_restrict": (None, buf, buf, buf, buf),
+        "stokes_prolong_add": (None, buf, buf, buf, buf),
+        "stokes_load_vectors": (None, buf, buf, 1, buf, buf),
+        "stokes_euler_rhs": (None, buf, buf, buf, buf, buf),
+        "stokes_make_consistent": (None, buf),
+        "stokes_mass_dot": (None, buf, buf, ctypes.byref(d)),
+        "stokes_set_timing": (None, 1),
+        "stokes_get_timing": (None, None, None, None, None),
+        "stokes_residual_norm2_noalloc": (0, 1.0, buf, buf, buf, buf, ctypes.byref(d), None),
+        "stokes_batch_solve": (None, None, None, None, None, 1e-8, 10, None, None),
+        "stokes_transfer_weights": (None,),
+        "stokes_coarse_inverse": (0.0, None),
+    }
+    for name, args in calls.items():
+        assert getattr(lib, name)(*args) == bad, name
+    assert lib.stokes_residual_norm2_noalloc(30, 1.0, buf, buf, buf, buf, ctypes.byref(d), None) == bad
+    n = ctypes.c_int(1)
+    lv = (ctypes.c_int * 1)(3)
+    be = (ctypes.c_double * 1)(1.0)
+    out = ctypes.c_void_p()
+    prm = B.Params()
+    lib.stokes_default_params(ctypes.byref(prm), 3, 1.0)
+    assert lib.stokes_batch_setup(0, lv, be, ctypes.byref(prm), None, 0, ctypes.byref(out)) == bad
+    assert lib.stokes_batch_setup(n.value, None, be, ctypes.byref(prm), None, 0, ctypes.byref(out)) == bad
+    lib.stokes_destroy(None)
+    lib.stokes_batch_destroy(None)
+    assert lib.stokes_kernel_launches(None) == 0
+    assert lib.stokes_batch_kernel_launches(None) == 0
