@@ -189,14 +189,16 @@ def test_table3_uzawa_w_cycle(discs, tables, k):
         assert abs(n - t["n"][row][j]) <= band(t["n"][row][j]), (k, beta, n, t["n"][row][j])
 
 
-def test_table2_normal_equation_w_cycle(discs, tables):
-    """Table 2, k = 4: normal-equation smoother, tau = 0.35, W(3,3), six beta."""
+@pytest.mark.parametrize("k", [4, 5])
+def test_table2_normal_equation_w_cycle(discs, tables, k):
+    """Table 2: normal-equation smoother, tau = 0.35, W(3,3), six beta on level k."""
     t = tables["table2"]
+    row = t["k"].index(k)
     prm = mg.Params(gamma=2, smoother=mg.NORMAL_EQ, tau=0.35)
     for j, beta in enumerate(tables["betas"]):
-        n, q, errs, div = _oracle_rate(discs, 4, beta, prm, max_cycles=200)
+        n, q, errs, div = _oracle_rate(discs, k, beta, prm, max_cycles=200)
         assert not div
-        assert abs(n - t["n"][0][j]) <= band(t["n"][0][j]), (beta, n, t["n"][0][j])
+        assert abs(n - t["n"][row][j]) <= band(t["n"][row][j]), (k, beta, n, t["n"][row][j])
 
 
 def test_table1_smoothing_steps(discs, tables):
