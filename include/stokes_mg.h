@@ -167,6 +167,15 @@ stokes_status stokes_load_vectors(stokes_handle* h, const double* f_nodal, const
  * bordered with the zero-mean pressure condition, first 27 x 27 block, row-major, unknowns u_x at the
  * interior lattice points (X, Y) in [1, 3]^2 (Y outer), then u_y, then p at the 3 x 3 vertices
  * (caller array of 729).  STOKES_ERR_BAD_ARG on bad input or a singular system. */
+/* Host-only (no device work): tables for the L-shaped domain, the unit square without [1/2, 1]^2
+ * (Sec. 1: the method applies to non-convex domains).  For a pressure vertex on a re-entrant side
+ * of a level with N = 2^levels (levels >= 2): kind 0 = vertex (N/2, j), N/2 < j < N (side x = 1/2);
+ * kind 1 = vertex (i, N/2), N/2 < i < N (side y = 1/2); kind 2 = the corner (N/2, N/2).  Writes the
+ * vertex's B row over its 5 x 5 lattice window, mbx[(dy+2)*5 + dx+2] = Bx(vertex, lattice node
+ * (2i+dx, 2j+dy)) and mby likewise (25 each), summed over the squares around the vertex that lie in
+ * the L, and its pressure-mass weight w = (1, psi_vertex) over the L.  STOKES_ERR_BAD_ARG on bad
+ * input. */
+stokes_status stokes_lshape_vertex_rows(int levels, int kind, double* mbx, double* mby, double* w);
 stokes_status stokes_transfer_weights(double* w);
 stokes_status stokes_coarse_inverse(double beta, double* inv);
 

@@ -164,3 +164,40 @@ def test_coarse_inverse_equals_the_oracle_bordered_solve(lib, discs, beta):
     ref = np.linalg.inv(H.coarse_bordered)[:27, :27]
     assert np.abs(inv - ref).max() <= 1e-10 * np.abs(ref).max()
     assert lib.stokes_coarse_inverse(-1.0, inv.ctypes.data_as(ctypes.c_void_p)) != 0
+
+
+@pytest.mark.parametrize("j", [1, 2, 3])
+def test_lshape_reentrant_vertex_rows_equal_the_oracle(lib, j):
+    """L-shaped domain: the B rows and pressure-mass weights of the vertices on the re-entrant sides
+    (stokes_lshape_vertex_rows, summed over the squares inside the L) equal the rows of the
+    oracle's masked assembly (oracle/lshape.py) at every such vertex of L-level j."""
+    from oracle import lshape
+    d = lshape.discretizations(j + 1)[j]
+    n = d.n
+    levels = j + 2                                     # L-level j is the square's level j + 1
+    assert 2 ** levels == n
+    Bx, By = d.Bx.tocsr(), d.By.tocsr()
+    wfull = np.asarray(d.MPfull.sum(axis=1)).ravel()
+    lat = lambda X, Y: Y * (2 * n + 1) + X
+    h = n // 2
+    verts = {0: [(h, y) for y in range(h + 1, n)], 1: [(x, h) for x in range(h + 1, n)], 2: [(h, h)]}
+    mbx, mby, w = np.zeros(25), np.zeros(25), ctypes.c_double()
+    for kind, vs in verts.items():
+        assert lib.stokes_lshape_vertex_rows(levels, kind, mbx.ctypes.data_as(ctypes.c_void_p),
+                                             mby.ctypes.data_as(ctypes.c_void_p), ctypes.byref(w)) == 0
+        for (i, jj) in vs:
+            v = jj * (n + 1) + i
+            assert abs(w.value - wfull[v]) <= 1e-15, (kind, i, jj)
+            for name, Bm, tab in (("x", Bx, mbx), ("y", By, mby)):
+                row = Bm[v].toarray().ravel()
+                scale = np.abs(row).max()
+                for dy in range(-2, 3):
+                    for dx in range(-2, 3):
+                        X, Y = 2 * i + dx, 2 * jj + dy
+                        if 0 <= X <= 2 * n and 0 <= Y <= 2 * n:
+                            c = lat(X, Y)
+                            assert abs(tab[(dy + 2) * 5 + dx + 2] - row[c]) <= 1e-13 * scale, (kind, name, dx, dy)
+                            row[c] = 0.0
+                assert np.abs(row).max() == 0.0
+    assert lib.stokes_lshape_vertex_rows(1, 0, mbx.ctypes.data_as(ctypes.c_void_p),
+                                         mby.ctypes.data_as(ctypes.c_void_p), ctypes.byref(w)) != 0
