@@ -176,6 +176,11 @@ stokes_status stokes_load_vectors(stokes_handle* h, const double* f_nodal, const
  * the L, and its pressure-mass weight w = (1, psi_vertex) over the L.  STOKES_ERR_BAD_ARG on bad
  * input. */
 stokes_status stokes_lshape_vertex_rows(int levels, int kind, double* mbx, double* mby, double* w);
+/* Host-only: S_hat = diag(B Ahat^-1 B^T) (eq. numintroduc) on the L at the re-entrant vertices of a
+ * level with N = 2^levels, the sum over the velocity unknowns (nodes strictly inside the L) of the
+ * vertex's masked B row squared over diag A: s0[t] at (N/2, N/2 + 1 + t) and s1[t] at
+ * (N/2 + 1 + t, N/2), t = 0 .. N/2 - 2 (caller arrays of N/2 - 1), s2[0] at the corner. */
+stokes_status stokes_lshape_schur(int levels, double beta, double* s0, double* s1, double* s2);
 stokes_status stokes_transfer_weights(double* w);
 stokes_status stokes_coarse_inverse(double beta, double* inv);
 

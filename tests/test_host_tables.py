@@ -201,3 +201,29 @@ def test_lshape_reentrant_vertex_rows_equal_the_oracle(lib, j):
                 assert np.abs(row).max() == 0.0
     assert lib.stokes_lshape_vertex_rows(1, 0, mbx.ctypes.data_as(ctypes.c_void_p),
                                          mby.ctypes.data_as(ctypes.c_void_p), ctypes.byref(w)) != 0
+
+
+@pytest.mark.parametrize("beta", [0.0, 10.0, 1e6])
+@pytest.mark.parametrize("j", [1, 3])
+def test_lshape_reentrant_schur_diagonal_equals_the_oracle(lib, j, beta):
+    """L-shaped domain: S_hat = diag(B Ahat^-1 B^T) at the re-entrant vertices (stokes_lshape_schur)
+    equals the oracle's S_hat on the L (multigrid.Level over the masked discretization), including
+    the vertices next to the outer boundary where fewer velocity unknowns remain."""
+    from oracle import lshape
+    from oracle import multigrid as mg
+    ds = lshape.discretizations(j + 1)
+    d = ds[j]
+    n = d.n
+    H = mg.Hierarchy(j + 1, beta, ds)
+    shat = H.levels[j].Shat
+    pos = {int(v): k for k, v in enumerate(d.pnodes)}
+    h = n // 2
+    s0, s1, s2 = np.zeros(h - 1), np.zeros(h - 1), np.zeros(1)
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    assert lib.stokes_lshape_schur(j + 2, float(beta), ptr(s0), ptr(s1), ptr(s2)) == 0
+    for t in range(h - 1):
+        for got, (i, jj) in ((s0[t], (h, h + 1 + t)), (s1[t], (h + 1 + t, h))):
+            ref = shat[pos[jj * (n + 1) + i]]
+            assert abs(got - ref) <= 1e-12 * ref, (t, i, jj, got, ref)
+    ref = shat[pos[h * (n + 1) + h]]
+    assert abs(s2[0] - ref) <= 1e-12 * ref
