@@ -181,6 +181,12 @@ stokes_status stokes_lshape_vertex_rows(int levels, int kind, double* mbx, doubl
  * vertex's masked B row squared over diag A: s0[t] at (N/2, N/2 + 1 + t) and s1[t] at
  * (N/2 + 1 + t, N/2), t = 0 .. N/2 - 2 (caller arrays of N/2 - 1), s2[0] at the corner. */
 stokes_status stokes_lshape_schur(int levels, double beta, double* s0, double* s1, double* s2);
+/* Host-only: the inverse of level 0 of the L-shaped hierarchy (the square's N = 4 level without the
+ * upper-right quadrant) for eq. gen:bil:mv bordered with the zero-mean pressure condition, first
+ * block, row-major, unknowns u_x at the interior nodes of the L in lattice order (Y outer), then
+ * u_y, then p at the vertices of the L in lattice order; *nunk receives the size (87; caller array
+ * of 87 * 87).  STOKES_ERR_BAD_ARG on bad input or a singular system. */
+stokes_status stokes_lshape_coarse_inverse(double beta, double* inv, int* nunk);
 stokes_status stokes_transfer_weights(double* w);
 stokes_status stokes_coarse_inverse(double beta, double* inv);
 

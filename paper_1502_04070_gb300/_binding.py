@@ -66,6 +66,7 @@ SIGNATURES = {
     "stokes_transfer_weights": (_I, [_P]),
     "stokes_lshape_vertex_rows": (_I, [_I, _I, _P, _P, ctypes.POINTER(_D)]),
     "stokes_lshape_schur": (_I, [_I, _D, _P, _P, _P]),
+    "stokes_lshape_coarse_inverse": (_I, [_D, _P, ctypes.POINTER(_I)]),
     "stokes_coarse_inverse": (_I, [_D, _P]),
     "stokes_stencil_class": (_I, [_I, _I, _I, ctypes.POINTER(_I)]),
     "stokes_stencil_rows": (_I, [_I, _D, _I, _P, _P, _P, _P, _P, _P]),

@@ -8,6 +8,8 @@
 // the L only: this file computes those rows from the same square matrices as the square's tables.
 #include <cmath>
 #include <cstring>
+#include <utility>
+#include <vector>
 
 #include "../../include/stokes_mg.h"
 #include "common.cuh"
@@ -104,5 +106,82 @@ extern "C" stokes_status stokes_lshape_schur(int levels, double beta, double* s0
             out[kind][t] = s;
         }
     }
+    return STOKES_OK;
+}
+
+// Level 0 of the L-shaped hierarchy is the square's level with N = 4 without the upper-right
+// quadrant: the system of eq. gen:bil:mv over its 12 squares, Dirichlet velocity on the outer and
+// re-entrant sides, bordered with w = M_P 1 (zero-mean pressure), inverted by Gauss-Jordan
+// elimination with partial pivoting.  Unknowns: u_x at the interior nodes of the L in lattice order
+// (Y outer), then u_y, then p at the vertices of the L in lattice order.
+extern "C" stokes_status stokes_lshape_coarse_inverse(double beta, double* inv, int* nunk) {
+    if (!inv || !nunk || !(beta >= 0.0) || !std::isfinite(beta)) return STOKES_ERR_BAD_ARG;
+    const SquareMatrices& S = squares_l();
+    const int n = 4, m2 = 2 * n + 1, m1 = n + 1;
+    const double h = 1.0 / n;
+    auto kept = [&](int a, int b) { return !(a >= n / 2 && b >= n / 2); };
+    std::vector<int> vel(m2 * m2, -1), pre(m1 * m1, -1);
+    int ni = 0;
+    for (int Y = 0; Y < m2; ++Y)
+        for (int X = 0; X < m2; ++X)
+            if (l_interior(X, Y, n)) vel[Y * m2 + X] = ni++;
+    std::vector<char> inl(m1 * m1, 0);
+    for (int b = 0; b < n; ++b)
+        for (int a = 0; a < n; ++a)
+            if (kept(a, b))
+                for (int q = 0; q < 4; ++q) inl[(b + q / 2) * m1 + a + q % 2] = 1;
+    int np = 0;
+    for (int v = 0; v < m1 * m1; ++v)
+        if (inl[v]) pre[v] = 2 * ni + np++;
+    const int nu = 2 * ni + np, nb = nu + 1;
+    std::vector<double> M((size_t)nb * 2 * nb, 0.0);        // [A | I], row-major, width 2 nb
+    auto at = [&](int r, int c) -> double& { return M[(size_t)r * 2 * nb + c]; };
+    for (int b = 0; b < n; ++b)
+        for (int a = 0; a < n; ++a) {
+            if (!kept(a, b)) continue;
+            const int o = ((a < n / 2) != (b < n / 2)) ? 1 : 0;
+            int node[9];
+            for (int l = 0; l < 9; ++l) node[l] = vel[(2 * b + l / 3) * m2 + 2 * a + l % 3];
+            for (int l = 0; l < 9; ++l)
+                for (int k = 0; k < 9; ++k)
+                    if (node[l] >= 0 && node[k] >= 0) {
+                        const double v = S.K[o][l][k] + beta * h * h * S.M[o][l][k];
+                        at(node[l], node[k]) += v;
+                        at(ni + node[l], ni + node[k]) += v;
+                    }
+            for (int q = 0; q < 4; ++q) {
+                const int pr = pre[(b + q / 2) * m1 + a + q % 2];
+                for (int k = 0; k < 9; ++k) {
+                    if (node[k] < 0) continue;
+                    at(pr, node[k]) += h * S.Bx[o][q][k];
+                    at(node[k], pr) += h * S.Bx[o][q][k];
+                    at(pr, ni + node[k]) += h * S.By[o][q][k];
+                    at(ni + node[k], pr) += h * S.By[o][q][k];
+                }
+                for (int r = 0; r < 4; ++r) {
+                    at(pr, nu) += h * h * S.MP[o][q][r];
+                    at(nu, pr) += h * h * S.MP[o][q][r];
+                }
+            }
+        }
+    for (int i = 0; i < nb; ++i) at(i, nb + i) = 1.0;
+    for (int c = 0; c < nb; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < nb; ++r)
+            if (std::fabs(at(r, c)) > std::fabs(at(piv, c))) piv = r;
+        if (std::fabs(at(piv, c)) < 1e-300) return STOKES_ERR_BAD_ARG;
+        if (piv != c)
+            for (int k = 0; k < 2 * nb; ++k) std::swap(at(piv, k), at(c, k));
+        const double d = at(c, c);
+        for (int k = 0; k < 2 * nb; ++k) at(c, k) /= d;
+        for (int r = 0; r < nb; ++r)
+            if (r != c && at(r, c) != 0.0) {
+                const double f = at(r, c);
+                for (int k = 0; k < 2 * nb; ++k) at(r, k) -= f * at(c, k);
+            }
+    }
+    for (int i = 0; i < nu; ++i)
+        for (int k = 0; k < nu; ++k) inv[(size_t)i * nu + k] = at(i, nb + k);
+    *nunk = nu;
     return STOKES_OK;
 }

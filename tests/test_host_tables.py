@@ -227,3 +227,19 @@ def test_lshape_reentrant_schur_diagonal_equals_the_oracle(lib, j, beta):
             assert abs(got - ref) <= 1e-12 * ref, (t, i, jj, got, ref)
     ref = shat[pos[h * (n + 1) + h]]
     assert abs(s2[0] - ref) <= 1e-12 * ref
+
+
+@pytest.mark.parametrize("beta", [0.0, 1.0, 1e4])
+def test_lshape_coarse_inverse_equals_the_oracle(lib, beta):
+    """Level 0 of the L-shaped hierarchy: the host inverse (stokes_lshape_coarse_inverse) against a
+    dense inverse of the oracle's bordered level-0 matrix on the L (same unknown order)."""
+    from oracle import lshape
+    from oracle import multigrid as mg
+    d0 = lshape.discretizations(1)[0]
+    inv = np.zeros(87 * 87)
+    nunk = ctypes.c_int()
+    assert lib.stokes_lshape_coarse_inverse(float(beta), inv.ctypes.data_as(ctypes.c_void_p), ctypes.byref(nunk)) == 0
+    assert nunk.value == d0.ndof == 87
+    H = mg.Hierarchy(1, beta, [d0])
+    ref = np.linalg.inv(H.coarse_bordered)[:87, :87]
+    assert np.abs(inv.reshape(87, 87) - ref).max() <= 1e-10 * np.abs(ref).max()
