@@ -9,7 +9,8 @@
 * the Galerkin identity I^T A_j I = A_{j-1} of the masked transfers;
 * V- and W-cycles converge to the sparse direct solution;
 * Taylor-Hood orders 3, 2, 2 for a smooth manufactured solution vanishing on the whole boundary of
-  the L (stream function with double zeros on the re-entrant sides).
+  the L (stream function with double zeros on the re-entrant sides);
+* the square's canonical embedding restricted to the L's unknowns is the L's embedding.
 """
 import numpy as np
 import pytest
@@ -125,3 +126,31 @@ def test_manufactured_convergence_orders(ds):
     errs = np.array(errs)
     rates = np.log2(errs[:-1] / errs[1:])
     assert np.all(rates[-1] > np.array([2.7, 1.8, 1.7])), rates
+
+
+def test_square_transfers_restrict_to_the_l(ds):
+    """The L's canonical embedding (coarse L basis functions evaluated at the fine L nodes) equals
+    the square's embedding restricted to the L's unknowns: the transfer kernels of the square can
+    serve the L with a mask (a fine node of the L interpolates from coarse nodes of the L only)."""
+    from oracle import transfer
+    sq = fem.discretizations(5)
+    for j in (0, 1, 2):
+        Lc, Lf = ds[j], ds[j + 1]
+        Sc, Sf = sq[j + 1], sq[j + 2]
+        P_l = transfer.prolongation(Lc, Lf).toarray()
+        P2, P1 = transfer.prolongation_full(Sc, Sf)
+        P2, P1 = P2.toarray(), P1.toarray()
+        ref_u = P2[Lf.interior][:, Lc.interior]
+        ref_p = P1[Lf.pnodes][:, Lc.pnodes]
+        niF, niC = Lf.ni, Lc.ni
+        assert np.abs(P_l[:niF, :niC] - ref_u).max() < 1e-15
+        assert np.abs(P_l[niF:2 * niF, niC:2 * niC] - ref_u).max() < 1e-15
+        assert np.abs(P_l[2 * niF:, 2 * niC:] - ref_p).max() < 1e-15
+        # a fine node of the L draws on no coarse node strictly inside the removed quadrant (only on
+        # nodes of the closed L, whose re-entrant-side values are Dirichlet zeros), and a fine vertex
+        # of the L only on coarse vertices of the L
+        Xc, Yc = Sc.coords[:, 0], Sc.coords[:, 1]
+        used = np.abs(P2[Lf.interior]).sum(axis=0) > 0
+        assert not np.any(used & (Xc > Sc.n) & (Yc > Sc.n))
+        used_p = np.flatnonzero(np.abs(P1[Lf.pnodes]).sum(axis=0) > 0)
+        assert np.all(np.isin(used_p, Lc.pnodes))
