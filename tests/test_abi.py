@@ -146,3 +146,17 @@ def test_every_entry_point_rejects_bad_arguments_before_device_work():
     lib.stokes_batch_destroy(None)
     assert lib.stokes_kernel_launches(None) == 0
     assert lib.stokes_batch_kernel_launches(None) == 0
+
+
+def test_header_is_plain_c():
+    """include/stokes_mg.h is a C-ABI header: it compiles as C99 (no C++ or torch types)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            r = subprocess.run([cc, "-fsyntax-only", "-std=c99", "-Wall", "-Werror", "-x", "c",
+                                os.path.join(ROOT, "include", fn)], capture_output=True, text=True)
+            assert r.returncode == 0, r.stderr
