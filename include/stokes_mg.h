@@ -170,7 +170,8 @@ stokes_status stokes_load_vectors(stokes_handle* h, const double* f_nodal, const
 /* Host-only (no device work): tables for the L-shaped domain, the unit square without [1/2, 1]^2
  * (Sec. 1: the method applies to non-convex domains).  For a pressure vertex on a re-entrant side
  * of a level with N = 2^levels (levels >= 2): kind 0 = vertex (N/2, j), N/2 < j < N (side x = 1/2);
- * kind 1 = vertex (i, N/2), N/2 < i < N (side y = 1/2); kind 2 = the corner (N/2, N/2).  Writes the
+ * kind 1 = vertex (i, N/2), N/2 < i < N (side y = 1/2); kind 2 = the corner (N/2, N/2); kinds 3, 4 =
+ * the ends (N/2, N) and (N, N/2) of the two sides on the outer boundary.  Writes the
  * vertex's B row over its 5 x 5 lattice window, mbx[(dy+2)*5 + dx+2] = Bx(vertex, lattice node
  * (2i+dx, 2j+dy)) and mby likewise (25 each), summed over the squares around the vertex that lie in
  * the L, and its pressure-mass weight w = (1, psi_vertex) over the L.  STOKES_ERR_BAD_ARG on bad
@@ -179,7 +180,8 @@ stokes_status stokes_lshape_vertex_rows(int levels, int kind, double* mbx, doubl
 /* Host-only: S_hat = diag(B Ahat^-1 B^T) (eq. numintroduc) on the L at the re-entrant vertices of a
  * level with N = 2^levels, the sum over the velocity unknowns (nodes strictly inside the L) of the
  * vertex's masked B row squared over diag A: s0[t] at (N/2, N/2 + 1 + t) and s1[t] at
- * (N/2 + 1 + t, N/2), t = 0 .. N/2 - 2 (caller arrays of N/2 - 1), s2[0] at the corner. */
+ * (N/2 + 1 + t, N/2), t = 0 .. N/2 - 1 (the last entries are the ends on the outer boundary; caller
+ * arrays of N/2), s2[0] at the corner. */
 stokes_status stokes_lshape_schur(int levels, double beta, double* s0, double* s1, double* s2);
 /* Host-only: the inverse of level 0 of the L-shaped hierarchy (the square's N = 4 level without the
  * upper-right quadrant) for eq. gen:bil:mv bordered with the zero-mean pressure condition, first

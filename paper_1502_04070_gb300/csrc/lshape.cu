@@ -23,11 +23,14 @@ namespace {
 // is corner SQ of square SQ.  Squares in the removed quadrant, per kind of re-entrant vertex:
 //   kind 0, side x = 1/2 above the corner: SQ 0 and 2 (to the right);
 //   kind 1, side y = 1/2 right of the corner: SQ 0 and 1 (above);
-//   kind 2, the corner (1/2, 1/2): SQ 0.
+//   kind 2, the corner (1/2, 1/2): SQ 0;
+//   kind 3, the end (1/2, 1) of the side x = 1/2 on the outer boundary: SQ 0, 1 (outside) and 2;
+//   kind 4, the end (1, 1/2) of the side y = 1/2 on the outer boundary: SQ 0, 2 (outside) and 1.
 // The stencil classes of these cells (the mid-line cells above / right of the centre, and the
 // centre cell) give the orientation of every square.
-constexpr unsigned kRemoved[3] = {0x5u, 0x3u, 0x1u};
-constexpr int kClass[3] = {3, 5, 6};
+constexpr int kKinds = 5;
+constexpr unsigned kRemoved[kKinds] = {0x5u, 0x3u, 0x1u, 0x7u, 0x7u};
+constexpr int kClass[kKinds] = {3, 5, 6, 3, 5};
 
 // Velocity lattice node (X, Y) of the P2 lattice ([0, 2n]^2) strictly inside the L: off the outer
 // boundary and off the closed removed quadrant (whose edges are the re-entrant sides).
@@ -78,7 +81,7 @@ const SquareMatrices& squares_l() {
 }  // namespace
 
 extern "C" stokes_status stokes_lshape_vertex_rows(int levels, int kind, double* mbx, double* mby, double* w) {
-    if (levels < 2 || levels > 13 || kind < 0 || kind > 2 || !mbx || !mby || !w) return STOKES_ERR_BAD_ARG;
+    if (levels < 2 || levels > 13 || kind < 0 || kind >= kKinds || !mbx || !mby || !w) return STOKES_ERR_BAD_ARG;
     vertex_rows(squares_l(), 1 << levels, kind, mbx, mby, w);
     return STOKES_OK;
 }
@@ -88,13 +91,15 @@ extern "C" stokes_status stokes_lshape_schur(int levels, double beta, double* s0
         return STOKES_ERR_BAD_ARG;
     const SquareMatrices& S = squares_l();
     const int n = 1 << levels, hn = n / 2;
-    double* out[3] = {s0, s1, s2};
-    for (int kind = 0; kind < 3; ++kind) {
+    for (int kind = 0; kind < kKinds; ++kind) {
         double mbx[25], mby[25], w;
         vertex_rows(S, n, kind, mbx, mby, &w);
-        const int count = kind == 2 ? 1 : hn - 1;
-        for (int t = 0; t < count; ++t) {
-            const int i = kind == 1 ? hn + 1 + t : hn, j = kind == 0 ? hn + 1 + t : hn;
+        // kinds 0 / 1: t = 0 .. hn - 2 of s0 / s1; kinds 3 / 4: their last entry t = hn - 1
+        double* out = kind == 0 || kind == 3 ? s0 : kind == 1 || kind == 4 ? s1 : s2;
+        const int t0 = kind >= 3 ? hn - 1 : 0, count = kind == 2 ? 1 : kind >= 3 ? 1 : hn - 1;
+        for (int t = t0; t < t0 + count; ++t) {
+            const bool side_x = kind == 0 || kind == 3, side_y = kind == 1 || kind == 4;
+            const int i = side_y ? hn + 1 + t : hn, j = side_x ? hn + 1 + t : hn;
             double s = 0.0;
             for (int dy = -2; dy <= 2; ++dy)
                 for (int dx = -2; dx <= 2; ++dx) {
@@ -103,7 +108,7 @@ extern "C" stokes_status stokes_lshape_schur(int levels, double beta, double* s0
                     const double bx = mbx[(dy + 2) * 5 + dx + 2], by = mby[(dy + 2) * 5 + dx + 2];
                     s += (bx * bx + by * by) / a_diag(S, X, Y, n, beta);
                 }
-            out[kind][t] = s;
+            out[kind == 2 ? 0 : t] = s;
         }
     }
     return STOKES_OK;

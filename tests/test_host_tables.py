@@ -180,7 +180,8 @@ def test_lshape_reentrant_vertex_rows_equal_the_oracle(lib, j):
     wfull = np.asarray(d.MPfull.sum(axis=1)).ravel()
     lat = lambda X, Y: Y * (2 * n + 1) + X
     h = n // 2
-    verts = {0: [(h, y) for y in range(h + 1, n)], 1: [(x, h) for x in range(h + 1, n)], 2: [(h, h)]}
+    verts = {0: [(h, y) for y in range(h + 1, n)], 1: [(x, h) for x in range(h + 1, n)], 2: [(h, h)],
+             3: [(h, n)], 4: [(n, h)]}
     mbx, mby, w = np.zeros(25), np.zeros(25), ctypes.c_double()
     for kind, vs in verts.items():
         assert lib.stokes_lshape_vertex_rows(levels, kind, mbx.ctypes.data_as(ctypes.c_void_p),
@@ -218,10 +219,10 @@ def test_lshape_reentrant_schur_diagonal_equals_the_oracle(lib, j, beta):
     shat = H.levels[j].Shat
     pos = {int(v): k for k, v in enumerate(d.pnodes)}
     h = n // 2
-    s0, s1, s2 = np.zeros(h - 1), np.zeros(h - 1), np.zeros(1)
+    s0, s1, s2 = np.zeros(h), np.zeros(h), np.zeros(1)
     ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
     assert lib.stokes_lshape_schur(j + 2, float(beta), ptr(s0), ptr(s1), ptr(s2)) == 0
-    for t in range(h - 1):
+    for t in range(h):                                 # t = h - 1: the ends on the outer boundary
         for got, (i, jj) in ((s0[t], (h, h + 1 + t)), (s1[t], (h + 1 + t, h))):
             ref = shat[pos[jj * (n + 1) + i]]
             assert abs(got - ref) <= 1e-12 * ref, (t, i, jj, got, ref)
