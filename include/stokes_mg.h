@@ -160,6 +160,10 @@ stokes_status stokes_load_vectors(stokes_handle* h, const double* f_nodal, const
  *   mbx[(dy+2)*5 + dx+2]        = Bx(vertex (i, j), lattice node (2i+dx, 2j+dy)), mby likewise (25 each)
  *   midg[s]                     = 1 / (K + beta M)(node s, node s)                       (4)
  * with B_ij = (div phi_j, psi_i) split by component.  STOKES_ERR_BAD_ARG on out-of-range input. */
+stokes_status stokes_stencil_class(int levels, int i, int j, int* cls);
+stokes_status stokes_stencil_rows(int levels, double beta, int cls, double* ma, double* mbtx, double* mbty,
+                                  double* mbx, double* mby, double* midg);
+
 /* Host-only (no device work): the canonical P2 embedding weights of Sec. 3 that the transfer kernels
  * use, w[((o*9 + L)*5 + fb)*5 + fa] = value of the local basis function L = 3*b + a (local lattice
  * node (a, b) in {0,1,2}^2) of a coarse square of orientation o at its fine lattice point (fa, fb) in
@@ -167,6 +171,9 @@ stokes_status stokes_load_vectors(stokes_handle* h, const double* f_nodal, const
  * bordered with the zero-mean pressure condition, first 27 x 27 block, row-major, unknowns u_x at the
  * interior lattice points (X, Y) in [1, 3]^2 (Y outer), then u_y, then p at the 3 x 3 vertices
  * (caller array of 729).  STOKES_ERR_BAD_ARG on bad input or a singular system. */
+stokes_status stokes_transfer_weights(double* w);
+stokes_status stokes_coarse_inverse(double beta, double* inv);
+
 /* Host-only (no device work): tables for the L-shaped domain, the unit square without [1/2, 1]^2
  * (Sec. 1: the method applies to non-convex domains).  For a pressure vertex on a re-entrant side
  * of a level with N = 2^levels (levels >= 2): kind 0 = vertex (N/2, j), N/2 < j < N (side x = 1/2);
@@ -189,12 +196,6 @@ stokes_status stokes_lshape_schur(int levels, double beta, double* s0, double* s
  * u_y, then p at the vertices of the L in lattice order; *nunk receives the size (87; caller array
  * of 87 * 87).  STOKES_ERR_BAD_ARG on bad input or a singular system. */
 stokes_status stokes_lshape_coarse_inverse(double beta, double* inv, int* nunk);
-stokes_status stokes_transfer_weights(double* w);
-stokes_status stokes_coarse_inverse(double beta, double* inv);
-
-stokes_status stokes_stencil_class(int levels, int i, int j, int* cls);
-stokes_status stokes_stencil_rows(int levels, double beta, int cls, double* ma, double* mbtx, double* mbty,
-                                  double* mbx, double* mby, double* midg);
 
 /* Right-hand side of one implicit Euler step of the time-dependent Stokes problem
  *     u_t - Laplace u + grad p = f,  div u = g,  u = 0 on the boundary      (unit viscosity),
