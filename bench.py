@@ -1,17 +1,24 @@
 #!/usr/bin/env python
 """Benchmark: robust coupled multigrid solves of the generalized Stokes system on one GB300.
 
-Workload (one "step"): the robustness sweep at h = 1/512 (level k = 8, 2,356,227 unknowns):
-six solves, beta in {0, 1, 1e2, 1e4, 1e6, 1e8}, f and g with i.i.d. uniform[-1, 1] nodal values
-(seed 1 + rank, g shifted to zero mean), each from zero to 1e-8 relative residual (float64) with
-V(3,3) Uzawa cycles (tau = sigma = 0.8).  The six solves are independent and run concurrently in
-one CUDA-graph launch (each with its own device-side loop); the same solves one after another
-through the single-solve API are reported beside it.  The headline path is float32 cycles inside
-float64 iterative refinement (--precision mixed, default); the plain float64 multigrid is timed on
-the same workload for comparison.
+Headline workload (one "step"): one solve of the manufactured problem at h = 1/2048 (level k = 10,
+37,736,451 unknowns), beta = 1e4, u = curl(sin^2(pi x) sin^2(pi y)), p = cos(pi x) cos(pi y),
+from zero to 1e-8 relative residual (float64) with float32 V(3,3) Uzawa cycles (Sec. 4,
+tau = sigma = 0.8) inside float64 iterative refinement and a float64 coarse solve; the same solve
+with plain float64 multigrid is timed beside it (the speed-up at equal accuracy) and the two
+solutions are compared.
 
-Metric: unknowns solved per second (DoF/s) = 6 x 2,356,227 x steps x ranks / time.
-Multi-GPU: every rank solves its own sweep (independent problems, no collective on the data path):
+Also measured, as parsed keys of the same line:
+  sweep     -- the robustness sweep at h = 1/512 (k = 8), six beta in {0, 1, 1e2, 1e4, 1e6, 1e8},
+               f, g uniform[-1, 1] nodal (seed 1), six solves in one CUDA-graph launch, V and W
+               cycles, cycles per beta beside the oracle's;
+  levels    -- cycles to 1e-8 of the manufactured problem on k = 4..10 for V and W (h-robustness);
+  batch     -- 256 independent solves, k uniform in 4..8, beta log-uniform in [1e-2, 1e8], one launch;
+  small     -- h = 1/32 (k = 4), beta = 1, plain float64 V(3,3) to 1e-10: time per solve;
+  adjoint   -- h = 1/1024 (k = 9), beta = 1e3, L = 1/2 ||u - u_target||_M^2: forward + backward.
+
+Metric: unknowns solved per second (DoF/s) = unknowns x solves x ranks / time.
+Multi-GPU: every rank solves its own problems (independent, no collective on the data path):
 weak scaling.
 """
 import argparse
@@ -26,13 +33,18 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+K_HEAD = 10
+BETA_HEAD = 1e4
 BETAS = [0.0, 1.0, 1e2, 1e4, 1e6, 1e8]
-K_LEVEL = 8
+K_LEVEL = 8                      # the robustness sweep
 TOL = 1e-8
-METRIC = "DoF/s to 1e-8 relative residual (robustness sweep h=1/512, 6 beta values)"
-WORKLOAD = ("robustness sweep: unit square, Taylor-Hood P2-P1, h=1/512 (k=8, 2356227 DoF), "
-            "beta in {0,1,1e2,1e4,1e6,1e8}, f,g uniform[-1,1] nodal (seed 1, g zero-mean), "
-            "V(3,3) Uzawa tau=sigma=0.8, solve from 0 to 1e-8 relative residual")
+METRIC = "DoF/s to 1e-8 relative residual (h=1/2048 manufactured solution, mixed precision vs plain FP64 multigrid)"
+
+
+def workload_text(cycle):
+    return ("manufactured solution u=curl(sin^2(pi x) sin^2(pi y)), p=cos(pi x) cos(pi y): unit square, "
+            "Taylor-Hood P2-P1, h=1/2048 (k=10, 37736451 DoF), beta=1e4, %s(3,3) Uzawa cycles tau=sigma=0.8, "
+            "solve from 0 to 1e-8 relative residual" % cycle)
 
 
 def parse():
@@ -41,20 +53,20 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--cycle", default="V", choices=["V", "W"], help="cycle of the headline solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--fp64-steps", type=int, default=2, help="steps of the plain float64 comparison")
+    ap.add_argument("--fp64-steps", type=int, default=2, help="solves of the plain float64 comparison")
+    ap.add_argument("--only-head", action="store_true", help="skip the parsed secondary workloads")
     ap.add_argument("--kernel", default=None, choices=["uzawa_f32", "uzawa_f64", "residual_f64", "mixed_solve", "ir_steps"],
                     help="microbenchmark one kernel (for profiler captures) instead of the workload")
     ap.add_argument("--level", type=int, default=9)
-    ap.add_argument("--no-batch", action="store_true", help="skip the batched-solver measurement")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--host-loop", action="store_true",
                     help="kernel modes: drive refinement steps from the host, one cycle graph per step, so that a "
                          "profiler lists every kernel (the device-side loop hides the loop body from it)")
     ap.add_argument("--variant", type=int, default=None,
-                    help="kernel modes: force this float32 Uzawa step variant (0-9) on every level")
+                    help="kernel modes: force this float32 Uzawa step variant on every level")
     ap.add_argument("--variants", default=None,
                     help="kernel modes: float32 Uzawa step variant per level, 'k:v,k:v,...' (as the workload's "
                          "float32_step_variant_per_level reports them); levels not named are autotuned")
@@ -63,7 +75,6 @@ def parse():
 
 def run_kernel(args):
     """Runs one hot kernel alone on level --level with random data (profiler captures)."""
-    import numpy as np
     import torch
 
     from paper_1502_04070_gb300 import workloads
@@ -132,98 +143,91 @@ def dofs(k):
     return 2 * (2 * n - 1) ** 2 + (n + 1) ** 2
 
 
+def _golden(name):
+    with open(os.path.join(ROOT, "tests", "golden", name)) as fh:
+        return json.load(fh)
+
+
 def golden_cycles():
-    """Cycle counts to 1e-8 per beta, written by the oracle (tests/golden/make_sweep_golden.py)."""
-    path = os.path.join(ROOT, "tests", "golden", "sweep_k8.json")
-    with open(path) as fh:
-        g = json.load(fh)
-    return {r["beta"]: r["cycles"] for r in g["k8_sweep"]["runs"]}
+    """V(3,3) cycle counts to 1e-8 per beta of the sweep, written by the oracle
+    (tests/golden/make_sweep_golden.py)."""
+    return {r["beta"]: r["cycles"] for r in _golden("sweep_k8.json")["k8_sweep"]["runs"]}
 
 
-def oracle_cycles_by_beta():
-    """The oracle's float64 cycle counts to 1e-8 per beta (the written golden values, no oracle
+def oracle_sweep_cycles(gamma):
+    """The oracle's cycle counts to 1e-8 per beta of the sweep (the written golden values, no oracle
     call), keyed like cycles_per_beta; None if the file is missing."""
     try:
-        return {str(float(b)): c for b, c in golden_cycles().items()}
+        if gamma == 1:
+            return {str(float(b)): c for b, c in golden_cycles().items()}
+        runs = _golden("manufactured_k8.json")["k8_sweep_w"]["runs"]
+        return {str(float(r["beta"])): r["cycles"] for r in runs}
     except (OSError, KeyError, TypeError, ValueError):
         return None
 
 
+def oracle_manufactured_cycles(k, gamma):
+    """The oracle's cycles to 1e-8 on the manufactured problem (beta = 1e4) at level k, or None."""
+    try:
+        for r in _golden("manufactured_k8.json")["manufactured"]["runs"]:
+            if r["k"] == k and r["gamma"] == gamma:
+                return r["cycles"]
+    except (OSError, KeyError, TypeError, ValueError):
+        pass
+    return None
+
+
 # ------------------------------------------------------------------------------ CPU oracle
-def oracle_sample(n_cycles_per_beta=1, betas=(1.0,)):
-    """Times the oracle (CPU float64 SciPy, as it stands) on a bounded sample of the workload:
-    n_cycles_per_beta V-cycles per listed beta at k = 8; scaled to DoF/s with the oracle's own
-    cycle counts to 1e-8 for the full sweep.  Setup (assembly) is excluded and reported."""
+def oracle_sample(n_cycles, gamma, warmup=0):
+    """Times the oracle (CPU float64 SciPy, as it stands) on a bounded sample of the headline's
+    problem class: the manufactured problem with beta = 1e4 at k = 8, the largest level the oracle
+    assembles in seconds; n_cycles cycles from zero.  Returns the per-cycle times, the assembly time
+    and the oracle's own cycle count to 1e-8 at k = 8 (golden file)."""
     import numpy as np
 
     from oracle import fem
     from oracle import multigrid as mg
     from paper_1502_04070_gb300 import workloads
 
+    k = K_LEVEL
     t0 = time.perf_counter()
-    ds = fem.discretizations(K_LEVEL + 1)
-    d = ds[-1]
-    fn, gn = workloads.random_nodal(K_LEVEL, 1)
-    F = d.load(fn, gn, project_g=True)
-    hs = {b: mg.Hierarchy(K_LEVEL + 1, b, ds) for b in betas}
+    ds = fem.discretizations(k + 1)
+    fn, gn = workloads.manufactured_nodal(k, BETA_HEAD)
+    F = ds[-1].load(fn, gn, project_g=True)
+    H = mg.Hierarchy(k + 1, BETA_HEAD, ds)
     setup = time.perf_counter() - t0
-    per_cycle = {}
-    for b in betas:
-        x = np.zeros_like(F)
+    prm = mg.Params(gamma=gamma)
+    x = np.zeros_like(F)
+    for _ in range(warmup):
+        x = H.project_mean(k, H.cycle(k, x, F, prm))
+    times = []
+    for _ in range(n_cycles):
         t = time.perf_counter()
-        for _ in range(n_cycles_per_beta):
-            x = hs[b].project_mean(K_LEVEL, hs[b].cycle(K_LEVEL, x, F, mg.Params()))
-        per_cycle[b] = (time.perf_counter() - t) / n_cycles_per_beta
-    return per_cycle, setup
+        x = H.project_mean(k, H.cycle(k, x, F, prm))
+        times.append(time.perf_counter() - t)
+    return times, setup, oracle_manufactured_cycles(k, gamma)
 
 
-def oracle_dofs_per_s(per_cycle):
-    cyc = golden_cycles()
-    mean_cycle = statistics.mean(per_cycle.values())
-    total_time = sum(per_cycle.get(b, mean_cycle) * cyc[b] for b in BETAS)
-    return len(BETAS) * dofs(K_LEVEL) / total_time
+def oracle_rate(times, cycles):
+    """DoF/s of the oracle solving the k = 8 problem to 1e-8: unknowns / (per-cycle time x cycles)."""
+    return dofs(K_LEVEL) / (statistics.mean(times) * cycles)
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    from oracle import fem
-    from oracle import multigrid as mg
-    from paper_1502_04070_gb300 import workloads
-    import numpy as np
-
-    t0 = time.perf_counter()
-    ds = fem.discretizations(K_LEVEL + 1)
-    d = ds[-1]
-    fn, gn = workloads.random_nodal(K_LEVEL, 1)
-    F = d.load(fn, gn, project_g=True)
-    hs = {b: mg.Hierarchy(K_LEVEL + 1, b, ds) for b in BETAS}
-    setup = time.perf_counter() - t0
-    xs = {b: np.zeros_like(F) for b in BETAS}
-
-    def step(i):
-        b = BETAS[i % len(BETAS)]
-        t = time.perf_counter()
-        xs[b] = hs[b].project_mean(K_LEVEL, hs[b].cycle(K_LEVEL, xs[b], F, mg.Params()))
-        return b, time.perf_counter() - t
-
-    for i in range(args.warmup):
-        step(i)
-    times = {}
-    t = time.perf_counter()
-    for i in range(args.steps):
-        b, dt = step(args.warmup + i)
-        times.setdefault(b, []).append(dt)
-    wall = time.perf_counter() - t
-    per_cycle = {b: statistics.mean(v) for b, v in times.items()}
-    value = oracle_dofs_per_s(per_cycle)
-    sample = ("%d oracle V(3,3) cycles at k=8 (one per step, beta rotating over the sweep), scaled by "
-              "the oracle's own cycle counts to 1e-8 (tests/golden/sweep_k8.json); assembly %.1f s excluded"
-              % (args.steps, setup))
+    gamma = 2 if getattr(args, "cycle", "V") == "W" else 1
+    times, setup, cyc = oracle_sample(args.steps, gamma, warmup=args.warmup)
+    value = oracle_rate(times, cyc)
+    sample = ("%d oracle %s(3,3) cycles (one per step) of the same problem class at k=8 (h=1/512, 2356227 DoF, "
+              "the largest level the oracle assembles in seconds; beta=1e4, manufactured), rate = DoF / (mean "
+              "cycle time x the oracle's own %d cycles to 1e-8 at k=8, tests/golden/manufactured_k8.json); "
+              "SciPy CSR products on 1 core; assembly %.1f s excluded"
+              % (args.steps, "VW"[gamma - 1], cyc, setup))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * wall / max(args.steps, 1),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "data": "synthetic", "config": {"workload": workload_text("VW"[gamma - 1])},
             "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -299,6 +303,47 @@ def max_over_all_ranks(v, device):
     return float(t.item())
 
 
+def step_variants(levels):
+    from paper_1502_04070_gb300 import _binding as _B
+    return {"k=%d" % (l - 1): _B.load().stokes_step_variant(l) for l in range(2, levels + 1)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    return json.load(open(path)) if os.path.exists(path) else None
+
+
+# The sources that define and launch the float32 Uzawa-step kernels whose DRAM traffic
+# profiles/traffic.json records (the three-kernel step in kernels.cu, the tiles in uzawa_pair.cu and
+# uzawa_reg.cu, the variant table in uzawa_fused.cu, and every header they include).
+TRAFFIC_SOURCES = ("common.cuh", "cellops.cuh", "kernels.cuh", "kernels.cu", "coarse_cycle.cuh",
+                   "uzawa_fused.cu", "uzawa_pair.cu", "uzawa_reg.cu")
+
+
+def _kernel_source_sha():
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1502_04070_gb300", "csrc")
+    for nm in TRAFFIC_SOURCES:
+        p = os.path.join(csrc, nm)
+        if os.path.exists(p):
+            h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(level_key, variant):
+    """DRAM bytes per launch of the finest-level float32 Uzawa step from an ncu capture
+    (profiles/traffic.json), only while the kernel sources hash to the recorded value."""
+    try:
+        tj = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        ent = tj["mixed"]["uzawa_step_finest"][level_key]["variants"].get(str(variant))
+        if ent and ent.get("source_sha") == _kernel_source_sha():
+            return ent["bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -318,46 +363,32 @@ def run_ours(args, rank, world, local_rank):
     def max_over_ranks(v):
         return max_over_all_ranks(v, "cuda")
 
-    levels = K_LEVEL + 1
-    fn_np, gn_np = workloads.random_nodal(K_LEVEL, 1 + rank)
+    gamma = 2 if args.cycle == "W" else 1
+    levels = K_HEAD + 1
+    n_dof = dofs(K_HEAD)
+    fn_np, gn_np = workloads.manufactured_nodal(K_HEAD, BETA_HEAD)
     fn_h = torch.from_numpy(fn_np).pin_memory()
     gn_h = torch.from_numpy(gn_np).pin_memory()
     fn, gn = fn_h.cuda(), gn_h.cuda()
-
-    def make(prec):
-        return {b: Solver(levels, b, precision=prec) for b in BETAS}
-
-    solvers = make(args.precision)
-    S0 = solvers[BETAS[0]]
-    if args.precision == "mixed":
-        S0.autotune()     # float32 step variant per level (process-wide), before any graph capture
-    from paper_1502_04070_gb300 import _binding as _B
-    from paper_1502_04070_gb300.solver import BatchSolver
-    variants = {"k=%d" % (l - 1): _B.load().stokes_step_variant(l) for l in range(2, levels + 1)}
-    f, g = S0.load_vectors(fn, gn, project_g=True)
-    nb = len(BETAS)
+    S = Solver(levels, BETA_HEAD, precision="mixed", gamma=gamma)
+    S.autotune()                  # float32 step variant per level (process-wide), before any graph capture
+    variants = step_variants(levels)
+    f, g = S.load_vectors(fn, gn, project_g=True)
+    u, p = S.zeros_u(), S.zeros_p()
     flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")   # > 129 MB L2
+    state = {}
 
-    # The six solves of the sweep are independent: one graph launch runs them concurrently, each
-    # instance with its own device-side loop to 1e-8 (small levels of one instance overlap the
-    # others' work).
-    sweep = BatchSolver([levels] * nb, BETAS, precision=args.precision, autotune=args.precision == "mixed")
-    us = [torch.zeros(sweep.shapes(0)[0], dtype=torch.float64, device="cuda") for _ in BETAS]
-    ps = [torch.zeros(sweep.shapes(0)[1], dtype=torch.float64, device="cuda") for _ in BETAS]
-    result = {}
-
-    def sweep_step(B, fs, gs):
-        for u, p in zip(us, ps):
-            u.zero_()
-            p.zero_()
-        _, _, cyc, rel, st = B.solve(fs, gs, tol=TOL, max_cycles=100, us=us, ps=ps)
-        if st != 0 or max(rel) > TOL:
-            raise RuntimeError("sweep did not converge: status %d, residuals %r" % (st, rel))
-        result["cycles"], result["rel"] = cyc, rel
+    def solve_once(sv, ff, gg, uu, pp):
+        uu.zero_()
+        pp.zero_()
+        _, _, rep = sv.solve(ff, gg, tol=TOL, max_cycles=200, u=uu, p=pp)
+        if not rep.converged or rep.rel_residual > TOL:
+            raise RuntimeError("headline solve did not converge: %r" % (rep,))
+        state["rep"] = rep
 
     for _ in range(args.warmup):
-        sweep_step(sweep, [f] * nb, [g] * nb)
-    launches0 = sweep.kernel_launches()
+        solve_once(S, f, g, u, p)
+    launches0 = S.kernel_launches()
     clocks = ClockSampler(local_rank)
     clocks.start()
     barrier()
@@ -366,187 +397,218 @@ def run_ours(args, rank, world, local_rank):
     e0.record()
     for _ in range(args.steps):
         flush.fill_(1.0)
-        sweep_step(sweep, [f] * nb, [g] * nb)
+        solve_once(S, f, g, u, p)
     e1.record()
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
     ms = max_over_ranks(e0.elapsed_time(e1))
-    launches = sweep.kernel_launches() - launches0
-    n_dof = dofs(K_LEVEL)
-    value = job_throughput(nb * n_dof, args.steps, world, ms)
-    cycles = {str(b): c for b, c in zip(BETAS, result["cycles"])}
-    # mean rate per cycle of the relative residual (the start x = 0 has residual ||F||)
-    rates = {str(b): round(r ** (1.0 / c), 4) for b, c, r in zip(BETAS, result["cycles"], result["rel"])}
-    final_rel = {str(b): r for b, r in zip(BETAS, result["rel"])}
+    launches = S.kernel_launches() - launches0
+    value = job_throughput(n_dof, args.steps, world, ms)
+    rep = state["rep"]
 
-    # the same six solves one after another through the single-solve API (one solve in flight)
-    reports = {}
-
-    def step(sv):
-        for b in BETAS:
-            u = S0.zeros_u()
-            p = S0.zeros_p()
-            _, _, rep = sv[b].solve(f, g, tol=TOL, max_cycles=100, u=u, p=p)
-            if not rep.converged:
-                raise RuntimeError("beta=%g did not converge: %r" % (b, rep))
-            reports[b] = rep
-
-    step(solvers)
-    seq_steps = max(1, min(args.steps, 2))
-    torch.cuda.synchronize()
-    e0.record()
-    for _ in range(seq_steps):
-        flush.fill_(1.0)
-        step(solvers)
-    e1.record()
-    torch.cuda.synchronize()
-    seq_ms = max_over_ranks(e0.elapsed_time(e1)) / seq_steps
-    sequential = {"value": nb * n_dof * world / (seq_ms / 1000.0), "unit": "DoF/s", "ms_per_step": seq_ms,
-                  "steps": seq_steps, "cycles": {str(b): reports[b].cycles for b in BETAS}}
-
-    # kernel timings: a second timed pass over the same workload with CUDA event records inside
-    # the captured cycle (on the library's stream).  Event records cannot sit inside the device-side
-    # solve loop, so this pass drives the cycles from the host; the kernels are the same.
-    for s in solvers.values():
-        s.set_timing(True)
-    kern_steps = max(1, min(args.steps, 3))
+    # kernel timings: a second pass of the same solve with CUDA event records inside the captured
+    # cycle (on the library's stream); event records cannot sit inside the device-side solve loop, so
+    # this pass drives the refinement steps from the host; the kernels are the same
+    S.set_timing(True)
+    kern_steps = 2
     for _ in range(kern_steps):
         flush.fill_(1.0)
-        step(solvers)
-    sm_ms = sm_n = rs_ms = rs_n = 0.0
-    for s in solvers.values():
-        a, b_, c, d = s.timing()
-        sm_ms += a
-        sm_n += b_
-        rs_ms += c
-        rs_n += d
-        s.set_timing(False)
-    N = 2 ** (K_LEVEL + 1)
-    word = 4 if args.precision == "mixed" else 8
-    # Uzawa step on the finest level: read u (8N^2), f (8N^2), p, g, Shat^{-1} (N^2 each);
-    # write u (8N^2), p (N^2): 28 N^2 words
-    smooth_bytes = 28 * N * N * word
-    # outer step on the finest level.  fp64: the float64 residual reads x and F (18 N^2 words) and
-    # writes r (9 N^2).  mixed: the refinement update reads e (9 N^2 float32), x and r (float64),
+        solve_once(S, f, g, u, p)
+    sm_ms, sm_n, rs_ms, rs_n = S.timing()
+    S.set_timing(False)
+    N = 2 ** (K_HEAD + 1)
+    # Uzawa step on the finest level: read u (8N^2), f (8N^2), p, g, Shat^{-1} (N^2 each); write u (8N^2),
+    # p (N^2): 28 N^2 float32 words.  Refinement update: reads e (9 N^2 float32), x and r (float64),
     # writes x, r (float64) and r32 (float32): 9 N^2 (4 + 8 + 8 + 8 + 8 + 4) bytes
-    resid_name = "ir_update_finest" if args.precision == "mixed" else "residual_fp64_finest"
-    resid_bytes = 9 * N * N * 40 if args.precision == "mixed" else 27 * N * N * 8
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
-    hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
+    smooth_bytes = 28 * N * N * 4
+    resid_bytes = 9 * N * N * 40
+    pk = peaks()
+    hbm_peak = pk["hbm_gbs"] if pk else 6800.0
     sm_avg = sm_ms / max(sm_n, 1)
     rs_avg = rs_ms / max(rs_n, 1)
     kernels = {
         "uzawa_step_finest": {"ms_per_launch": sm_avg, "launches": int(sm_n), "total_ms": sm_ms,
                               "algorithmic_bytes": smooth_bytes,
-                              "achieved_gbs": smooth_bytes / (sm_avg * 1e6) if sm_avg > 0 else None},
-        resid_name: {"ms_per_launch": rs_avg, "launches": int(rs_n), "total_ms": rs_ms,
-                                 "algorithmic_bytes": resid_bytes,
-                                 "achieved_gbs": resid_bytes / (rs_avg * 1e6) if rs_avg > 0 else None},
+                              "achieved_gbs": smooth_bytes / (sm_avg * 1e6) if sm_avg > 0 else None,
+                              "variant": variants.get("k=%d" % K_HEAD)},
+        "ir_update_finest": {"ms_per_launch": rs_avg, "launches": int(rs_n), "total_ms": rs_ms,
+                             "algorithmic_bytes": resid_bytes,
+                             "achieved_gbs": resid_bytes / (rs_avg * 1e6) if rs_avg > 0 else None},
     }
     dom = max(kernels, key=lambda k: kernels[k]["total_ms"])
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
-        try:
-            # DRAM bytes per launch from an ncu capture, per float32 step variant of the finest level
-            # (the autotuner's choice can differ between runs); only while the kernel sources match
-            tj = json.load(open(tpath))
-            ent = tj.get(args.precision, {}).get(dom)
-            if ent and "variants" in ent:
-                ent = ent["variants"].get(str(variants.get("k=%d" % K_LEVEL)))
-            if ent and ent.get("source_sha") == _kernel_source_sha():
-                traffic = ent["bytes_per_launch"]
-        except Exception:
-            traffic = None
+    traffic = recorded_traffic("k=%d" % K_HEAD, variants.get("k=%d" % K_HEAD)) if dom == "uzawa_step_finest" else None
     roofline = {"bound": "hbm", "kernel": dom, "achieved": kernels[dom]["achieved_gbs"], "peak": hbm_peak,
                 "unit": "GB/s", "frac": (kernels[dom]["achieved_gbs"] or 0.0) / hbm_peak,
-                "traffic": traffic, "peak_source": "measured" if peaks else "fallback",
-                "note": "algorithmic bytes per launch / CUDA-event duration of the kernel, from a second timed "
-                        "pass of %d steps of the same workload with event records in the captured cycle" % kern_steps}
-
-    # ---------------------------------------------------------------- end to end (host buffers)
-    # per step: six copies of the nodal data host -> device, load vectors, the batched solve, six
-    # solutions device -> host
-    e2e_steps = max(1, min(args.steps, 3))
-    h2d = (fn_h.numel() + gn_h.numel()) * 8 * nb
-    d2h = (us[0].numel() + ps[0].numel()) * 8 * nb
-    u_host = [torch.empty(us[0].shape, dtype=torch.float64).pin_memory() for _ in BETAS]
-    p_host = [torch.empty(ps[0].shape, dtype=torch.float64).pin_memory() for _ in BETAS]
-    barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        fs, gs = [], []
-        for _b in BETAS:
-            fd = fn_h.to("cuda", non_blocking=True)
-            gd = gn_h.to("cuda", non_blocking=True)
-            ff, gg = S0.load_vectors(fd, gd, project_g=True)
-            fs.append(ff)
-            gs.append(gg)
-        sweep_step(sweep, fs, gs)
-        for i in range(nb):
-            u_host[i].copy_(us[i])
-            p_host[i].copy_(ps[i])
-    torch.cuda.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
-    e2e_value = nb * n_dof * e2e_steps * world / e2e_s
+                "traffic": traffic, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if pk else "fallback",
+                "note": "algorithmic bytes per launch / CUDA-event duration of the kernel at h=1/2048 (nothing stays "
+                        "in L2), from a second pass of %d solves with event records in the captured cycle" % kern_steps}
 
     # ---------------------------------------------------------------- plain float64 comparison
     fp64 = None
-    if args.precision == "mixed" and args.fp64_steps > 0:
-        sw64 = BatchSolver([levels] * nb, BETAS, precision="fp64", autotune=False)
-        sweep_step(sw64, [f] * nb, [g] * nb)   # warm-up (graph capture)
+    if args.fp64_steps > 0:
+        S64 = Solver(levels, BETA_HEAD, precision="fp64", gamma=gamma)
+        u64, p64 = S64.zeros_u(), S64.zeros_p()
+        solve_once(S64, f, g, u64, p64)               # warm-up (graph capture)
         torch.cuda.synchronize()
         e0.record()
         for _ in range(args.fp64_steps):
             flush.fill_(1.0)
-            sweep_step(sw64, [f] * nb, [g] * nb)
+            solve_once(S64, f, g, u64, p64)
         e1.record()
         torch.cuda.synchronize()
         dt = max_over_ranks(e0.elapsed_time(e1)) / 1000.0
-        v64 = nb * n_dof * args.fp64_steps * world / dt
-        fp64 = {"value": v64, "unit": "DoF/s", "ms_per_step": 1000 * dt / args.fp64_steps,
-                "cycles": {str(b): c for b, c in zip(BETAS, result["cycles"])},
-                "note": "the same six solves in one batched launch, float64 throughout",
-                "speedup_of_mixed": value / v64}
-        sw64.close()
+        rep64 = state["rep"]
+        v64 = n_dof * args.fp64_steps * world / dt
+        scale_u = float(u64.abs().max())
+        scale_p = float(p64.abs().max())
+        fp64 = {"value": v64, "unit": "DoF/s", "ms_per_solve": 1000 * dt / args.fp64_steps,
+                "cycles": rep64.cycles, "rel_residual": rep64.rel_residual,
+                "speedup_of_mixed": value / v64,
+                "mixed_vs_fp64_solution": {
+                    "max_rel_diff_u": float((u - u64).abs().max()) / scale_u,
+                    "max_rel_diff_p": float((p - p64).abs().max()) / scale_p,
+                    "note": "both solves stop at 1e-8 relative residual; the difference is bounded by the "
+                            "residual bound times the conditioning, not by float32 rounding"},
+                "note": "the same solve (same cycle, same tolerance) with float64 in every step"}
+        S64.close()
 
-    # ---------------------------------------------------------------- batched solves (one graph launch)
-    batch = None
-    if not args.no_batch:
-        batch = run_batch(args, rank, world)
+    # ---------------------------------------------------------------- end to end (host buffers)
+    # per step: nodal data host -> device, load vectors, the solve, the solution device -> host
+    e2e_steps = max(1, min(args.steps, 3))
+    h2d = (fn_h.numel() + gn_h.numel()) * 8
+    d2h = (u.numel() + p.numel()) * 8
+    u_host = torch.empty(u.shape, dtype=torch.float64).pin_memory()
+    p_host = torch.empty(p.shape, dtype=torch.float64).pin_memory()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        fd = fn_h.to("cuda", non_blocking=True)
+        gd = gn_h.to("cuda", non_blocking=True)
+        ff, gg = S.load_vectors(fd, gd, project_g=True)
+        solve_once(S, ff, gg, u, p)
+        u_host.copy_(u)
+        p_host.copy_(p)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_value = n_dof * e2e_steps * world / e2e_s
+
+    extra = {}
+    if not args.only_head:
+        extra["levels"] = run_levels(S, args)
+        extra["sweep"] = {"V": run_sweep(args, rank, world, 1, flush), "W": run_sweep(args, rank, world, 2, flush)}
+        extra["batch"] = run_batch(args, rank, world)
+        extra["small"] = run_small(args, world)
+        extra["adjoint"] = run_adjoint(args, world)
 
     # ---------------------------------------------------------------- CPU oracle baseline
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        per_cycle, setup = oracle_sample(n_cycles_per_beta=2, betas=(1.0,))
-        cpu = {"value": oracle_dofs_per_s(per_cycle), "unit": "DoF/s", "cores": 1, "kind": "oracle",
-               "sample": "2 oracle V(3,3) cycles at k=8, beta=1 (%.2f s each), scaled by the oracle's cycle "
-                         "counts to 1e-8 over the 6-beta sweep; SciPy CSR products run on 1 core; "
-                         "assembly %.1f s excluded; host has %d cores" % (per_cycle[1.0], setup, os.cpu_count())}
+        times, setup, cyc = oracle_sample(2, gamma)
+        cpu = {"value": oracle_rate(times, cyc), "unit": "DoF/s", "cores": 1, "kind": "oracle",
+               "sample": "2 oracle %s(3,3) cycles of the same problem class at k=8 (h=1/512, beta=1e4, manufactured; "
+                         "%.2f s each), rate = DoF / (cycle time x the oracle's own %d cycles to 1e-8 at k=8); "
+                         "SciPy CSR products run on 1 core; assembly %.1f s excluded; host has %d cores"
+                         % (args.cycle, statistics.mean(times), cyc, setup, os.cpu_count())}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32 cycles + f64 refinement" if args.precision == "mixed" else "f64",
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32 cycles + f64 refinement",
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD, "precision": args.precision, "dof_per_solve": n_dof,
-                           "solves_per_step": len(BETAS), "solves_per_s": len(BETAS) * args.steps * world / (ms / 1000),
-                           "l2": "256 MB buffer written between steps (inside the timed region)",
-                           "cycles_per_beta": cycles, "oracle_cycles_per_beta": oracle_cycles_by_beta(),
-                           "mean_rate_per_beta": rates,
-                           "final_rel_residual_per_beta": final_rel,
-                           "execution": "the six solves in one CUDA-graph launch (one device-side loop each)",
+                "config": {"workload": workload_text(args.cycle), "precision": "mixed", "dof_per_solve": n_dof,
+                           "solves_per_step": 1, "solves_per_s": args.steps * world / (ms / 1000),
+                           "l2": "inputs larger than L2 (the level-10 hierarchy holds about 1.5 GB) and a 256 MB "
+                                 "buffer written between steps (inside the timed region)",
+                           "cycles": rep.cycles, "oracle_cycles_k8": oracle_manufactured_cycles(K_LEVEL, gamma),
+                           "mean_rate": rep.mean_rate, "rel_residual": rep.rel_residual,
+                           "execution": "one CUDA-graph launch per solve (a device-side loop of refinement steps)",
                            "float32_step_variant_per_level": variants},
                 "roofline": roofline, "kernels": kernels, "clocks": clk,
                 "e2e": {"value": e2e_value, "unit": "DoF/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "steps": e2e_steps},
-                "gpu_launches": int(launches), "fp64_plain": fp64, "sequential_single_solves": sequential,
-                "batch": batch, "cpu_baseline": cpu}
+                "gpu_launches": int(launches), "fp64_plain": fp64, "cpu_baseline": cpu}
+        line.update(extra)
         print(json.dumps(line), flush=True)
+
+
+def run_levels(S_head, args):
+    """Cycles to 1e-8 of the manufactured problem (beta = 1e4) on k = 4..10 with V and W cycles in
+    mixed precision, beside the oracle's counts where it has them (k <= 8): the h-robustness of the
+    measured path."""
+    import torch
+
+    from paper_1502_04070_gb300 import workloads
+    from paper_1502_04070_gb300.solver import Solver
+    out = {}
+    for gamma in (1, 2):
+        row = {}
+        for k in range(4, K_HEAD + 1):
+            S = Solver(k + 1, BETA_HEAD, precision="mixed", gamma=gamma)
+            fn, gn = workloads.manufactured_nodal(k, BETA_HEAD)
+            f, g = S.load_vectors(torch.from_numpy(fn).cuda(), torch.from_numpy(gn).cuda(), project_g=True)
+            S.solve(f, g, tol=TOL, max_cycles=200)          # warm-up (graph capture)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            _, _, rep = S.solve(f, g, tol=TOL, max_cycles=200)
+            torch.cuda.synchronize()
+            row["k=%d" % k] = {"cycles": rep.cycles, "oracle_cycles": oracle_manufactured_cycles(k, gamma),
+                               "ms": 1000 * (time.perf_counter() - t), "mean_rate": round(rep.mean_rate, 4)}
+            S.close()
+        out["VW"[gamma - 1]] = row
+    return out
+
+
+def run_sweep(args, rank, world, gamma, flush):
+    """The robustness sweep (k = 8, six beta) in one batched CUDA-graph launch, V or W cycles."""
+    import torch
+
+    from paper_1502_04070_gb300 import workloads
+    from paper_1502_04070_gb300.solver import BatchSolver, Solver
+    levels = K_LEVEL + 1
+    fn_np, gn_np = workloads.random_nodal(K_LEVEL, 1 + rank)
+    L = Solver(levels, 1.0)
+    f, g = L.load_vectors(torch.from_numpy(fn_np).cuda(), torch.from_numpy(gn_np).cuda(), project_g=True)
+    nb = len(BETAS)
+    B = BatchSolver([levels] * nb, BETAS, precision="mixed", gamma=gamma, autotune=True)
+    us = [torch.zeros(B.shapes(0)[0], dtype=torch.float64, device="cuda") for _ in BETAS]
+    ps = [torch.zeros(B.shapes(0)[1], dtype=torch.float64, device="cuda") for _ in BETAS]
+    res = {}
+
+    def step():
+        for u, p in zip(us, ps):
+            u.zero_()
+            p.zero_()
+        _, _, cyc, rel, st = B.solve([f] * nb, [g] * nb, tol=TOL, max_cycles=200, us=us, ps=ps)
+        if st != 0 or max(rel) > TOL:
+            raise RuntimeError("sweep did not converge: status %d, residuals %r" % (st, rel))
+        res["cycles"], res["rel"] = cyc, rel
+
+    for _ in range(max(2, args.warmup)):
+        step()
+    steps = max(1, min(args.steps, 5))
+    launches0 = B.kernel_launches()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        flush.fill_(1.0)
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = max_over_all_ranks(e0.elapsed_time(e1), "cuda") / steps
+    out = {"value": nb * dofs(K_LEVEL) * world / (ms / 1000.0), "unit": "DoF/s", "ms_per_sweep": ms, "steps": steps,
+           "solves_per_s": nb * world / (ms / 1000.0),
+           "cycles_per_beta": {str(b): c for b, c in zip(BETAS, res["cycles"])},
+           "oracle_cycles_per_beta": oracle_sweep_cycles(gamma),
+           "mean_rate_per_beta": {str(b): round(r ** (1.0 / c), 4) for b, c, r in zip(BETAS, res["cycles"], res["rel"])},
+           "max_rel_residual": max(res["rel"]),
+           "gpu_launches_per_sweep": (B.kernel_launches() - launches0) // steps,
+           "execution": "the six solves (h=1/512, seed 1) in one CUDA-graph launch (one device-side loop each)"}
+    B.close()
+    L.close()
+    return out
 
 
 def run_batch(args, rank, world):
@@ -588,9 +650,9 @@ def run_batch(args, rank, world):
             raise RuntimeError("batched solve failed: status %d" % st)
     e1.record()
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / reps
+    ms = max_over_all_ranks(e0.elapsed_time(e1), "cuda") / reps
     total_dof = sum(dofs(k) for k in ks)
-    out = {"value": total_dof / (ms / 1000.0), "unit": "DoF/s", "solves_per_s": B.count / (ms / 1000.0),
+    out = {"value": total_dof * world / (ms / 1000.0), "unit": "DoF/s", "solves_per_s": B.count * world / (ms / 1000.0),
            "ms_per_batch": ms, "instances": B.count, "total_dof": total_dof, "levels_k": "4..8",
            "max_rel_residual": max(rel), "mean_steps": sum(cyc) / len(cyc), "max_steps": max(cyc),
            "setup_s": setup_s, "gpu_launches_per_batch": (B.kernel_launches() - launches0) // reps,
@@ -599,20 +661,80 @@ def run_batch(args, rank, world):
     return out
 
 
-# The sources that define and launch the float32 Uzawa-step kernels whose DRAM traffic
-# profiles/traffic.json records (the three-kernel step in kernels.cu, the pair tile in
-# uzawa_pair.cu, the variant table in uzawa_fused.cu, and every header they include).
-TRAFFIC_SOURCES = ("common.cuh", "cellops.cuh", "kernels.cuh", "kernels.cu", "coarse_cycle.cuh",
-                   "uzawa_fused.cu", "uzawa_pair.cu")
+def run_small(args, world):
+    """h = 1/32 (k = 4), beta = 1, f uniform[-1,1] nodal (seed 0), g = 0, plain float64 V(3,3) to 1e-10:
+    time per solve (latency-bound: 9,027 unknowns)."""
+    import torch
+
+    from paper_1502_04070_gb300 import workloads
+    from paper_1502_04070_gb300.solver import Solver
+    k = 4
+    S = Solver(k + 1, 1.0, precision="fp64")
+    fn, gn = workloads.random_nodal(k, 0, with_g=False)
+    f, g = S.load_vectors(torch.from_numpy(fn).cuda(), torch.from_numpy(gn).cuda(), project_g=True)
+    u, p = S.zeros_u(), S.zeros_p()
+    for _ in range(3):
+        u.zero_(), p.zero_()
+        S.solve(f, g, tol=1e-10, max_cycles=100, u=u, p=p)
+    reps = 20
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(reps):
+        u.zero_(), p.zero_()
+        _, _, rep = S.solve(f, g, tol=1e-10, max_cycles=100, u=u, p=p)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t) / reps
+    try:
+        gold = _golden("sweep_k8.json")["k4_plain"]["runs"][0]["cycles"]
+    except Exception:
+        gold = None
+    S.close()
+    return {"ms_per_solve": 1000 * dt, "solves_per_s": world / dt, "value": dofs(k) * world / dt, "unit": "DoF/s",
+            "cycles": rep.cycles, "oracle_cycles": gold, "rel_residual": rep.rel_residual,
+            "workload": "h=1/32 (k=4, 9027 DoF), beta=1, f uniform[-1,1] nodal (seed 0), g=0, float64 V(3,3) to 1e-10; "
+                        "wall time per solve including the host's convergence checks"}
 
 
-def _kernel_source_sha():
-    import hashlib
-    h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_1502_04070_gb300", "csrc")
-    for nm in TRAFFIC_SOURCES:
-        h.update(open(os.path.join(csrc, nm), "rb").read())
-    return h.hexdigest()[:16]
+def run_adjoint(args, world):
+    """h = 1/1024 (k = 9), beta = 1e3, L = 1/2 ||u - u_target||_M^2, u_target uniform[-1,1] nodal
+    (seed 5), f, g uniform[-1,1] nodal (seed 5): the forward solve and the adjoint backward solve through
+    torch.autograd (mixed precision, 1e-8), per forward + backward."""
+    import torch
+
+    from paper_1502_04070_gb300 import workloads
+    from paper_1502_04070_gb300.autograd import mass_half_norm2, stokes_solve
+    from paper_1502_04070_gb300.solver import Solver
+    k, beta = 9, 1e3
+    S = Solver(k + 1, beta, precision="mixed")
+    S.autotune()
+    fn, gn = workloads.random_nodal(k, 5)
+    ut, _ = workloads.random_nodal(k, 6)
+    f0, g0 = S.load_vectors(torch.from_numpy(fn).cuda(), torch.from_numpy(gn).cuda(), project_g=True)
+    utd = torch.from_numpy(ut).cuda()
+
+    def fwd_bwd():
+        f = f0.clone().requires_grad_(True)
+        g = g0.clone().requires_grad_(True)
+        b = torch.tensor(beta, dtype=torch.float64, device="cuda", requires_grad=True)
+        u, p = stokes_solve(f, g, b, S, tol=TOL, max_cycles=200)
+        L = mass_half_norm2(u - utd, S)
+        L.backward()
+        return float(L), float(b.grad)
+
+    fwd_bwd()
+    reps = 3
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(reps):
+        Lv, db = fwd_bwd()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t) / reps
+    S.close()
+    return {"ms_per_forward_backward": 1000 * dt, "value": 2 * dofs(k) * world / dt, "unit": "DoF/s",
+            "note": "two solves (forward and adjoint) of 9431043 unknowns per iteration, mixed precision to 1e-8; "
+                    "the gradients are checked against the oracle's adjoint and central differences in "
+                    "tests/test_gpu_adjoint.py",
+            "loss": Lv, "dL_dbeta": db}
 
 
 def main():

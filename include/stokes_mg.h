@@ -6,7 +6,7 @@
  * (Takacs, "A robust multigrid method for the time-dependent Stokes problem", SINUM 53(6), 2015:
  * problem statement Sec. 1, eq. stokes; variational form Sec. 2, eq. gen:bil; matrix form
  * eq. gen:bil:mv).  Discretisation: Taylor-Hood P2 velocity / P1 pressure on the unit square split
- * into 8 triangles around its centre (level 0) and refined uniformly k times (Sec. 5), so level k
+ * into 8 triangles around its centre (level 0) and refined uniformly k times (Sec. 6), so level k
  * has N = 2^(k+1) element legs per side.
  *
  * DATA LAYOUT (all arrays are caller-owned DEVICE memory of the current CUDA device, float64,
@@ -50,7 +50,8 @@ typedef enum stokes_status {
     STOKES_ERR_CUDA = 3,         /* a CUDA runtime call failed */
     STOKES_NOT_CONVERGED = 4,    /* solve reached max_cycles above tol (result still returned) */
     STOKES_DIVERGED = 5,         /* residual became NaN/Inf or grew in 8 consecutive cycles */
-    STOKES_ERR_TIMEOUT = 6       /* a bounded device-side wait gave up (batched persistent kernel) */
+    STOKES_ERR_TIMEOUT = 6       /* reserved for a bounded device-side wait that gives up; no call
+                                    returns it at present (no kernel of the library waits on a flag) */
 } stokes_status;
 
 typedef enum stokes_smoother {
@@ -66,10 +67,10 @@ typedef enum stokes_precision {
 typedef struct stokes_params {
     int levels;        /* number of grid levels; the finest is k = levels-1; 1 <= levels <= 13 */
     double beta;       /* >= 0 (Sec. 1 assumes beta > 0; beta = 0 is the stationary Stokes case) */
-    int nu_pre;        /* pre-smoothing steps  (Sec. 5 uses 3) */
-    int nu_post;       /* post-smoothing steps (Sec. 5 uses 3) */
-    double tau;        /* smoother damping tau   (Sec. 5: 0.8 Uzawa, 0.35 normal equation) */
-    double sigma;      /* Uzawa pressure damping (Sec. 5: 0.8) */
+    int nu_pre;        /* pre-smoothing steps  (Sec. 6 uses 3) */
+    int nu_post;       /* post-smoothing steps (Sec. 6 uses 3) */
+    double tau;        /* smoother damping tau   (Sec. 6: 0.8 Uzawa, 0.35 normal equation) */
+    double sigma;      /* Uzawa pressure damping (Sec. 6: 0.8) */
     int smoother;      /* stokes_smoother */
     int gamma;         /* 1 = V-cycle, 2 = W-cycle (Sec. 3) */
     int precision;     /* stokes_precision */
@@ -84,13 +85,13 @@ typedef struct stokes_handle_t stokes_handle;
 typedef struct stokes_report {
     int cycles;              /* cycles (FP64) or refinement steps (MIXED) performed */
     double rel_residual;     /* final ||F - A x||_2 / ||F||_2 over the unknowns (float64) */
-    double mean_rate;        /* geometric mean of the per-cycle residual reduction (Sec. 5 q) */
+    double mean_rate;        /* geometric mean of the per-cycle residual reduction (Sec. 6 q) */
     double initial_residual; /* ||F - A x0||_2 */
     double rhs_norm;         /* ||F||_2 */
 } stokes_report;
 
 /* Builds the level hierarchy (Sec. 2 nesting), the per-level diagonals Ahat = diag A_k and
- * Shat = diag(B_k Ahat^{-1} B_k^T) (Sec. 5, eq. numintroduc) and the level-0 factorisation
+ * Shat = diag(B_k Ahat^{-1} B_k^T) (Sec. 6, eq. numintroduc) and the level-0 factorisation
  * (Sec. 3: exact coarsest solve).  `stream` is a cudaStream_t (NULL = legacy default stream).
  * The library owns the handle and all internal buffers (cudaMalloc); free with stokes_destroy. */
 stokes_status stokes_setup(const stokes_params* prm, void* stream, stokes_handle** out);
@@ -131,9 +132,10 @@ stokes_status stokes_residual_norm(stokes_handle* h, const double* u, const doub
  * float64 arithmetic of the FP64 path.  Exposed for verification of the smoother alone. */
 stokes_status stokes_smooth(stokes_handle* h, double* u, double* p, const double* f, const double* g, int nu);
 
-/* nu steps of the float32 smoother used inside STOKES_MIXED refinement (the fused one-kernel Uzawa
- * step), on float32 arrays of the finest-level layouts; requires a STOKES_MIXED handle.  Exposed for
- * verification of the float32 path alone. */
+/* nu steps of the float32 smoother used inside STOKES_MIXED refinement, with the step variant
+ * currently set for the finest level (stokes_step_variant: a one-kernel tile, the three-kernel step
+ * or a pair tile), on float32 arrays of the finest-level layouts; requires a STOKES_MIXED handle.
+ * Exposed for verification of the float32 path alone. */
 stokes_status stokes_smooth_f32(stokes_handle* h, float* u, float* p, const float* f, const float* g, int nu);
 
 /* Canonical transfers (Sec. 3) between finest level k and level k-1 (requires levels >= 2):
@@ -151,7 +153,7 @@ stokes_status stokes_load_vectors(stokes_handle* h, const double* f_nodal, const
 
 /* Host-only views of the operator tables the kernels use (no device work; callable without a GPU).
  * stokes_stencil_class: the stencil class (0..6) of cell (i, j), 0 <= i, j <= N = 2^levels, by the
- * orientations of its four squares (Sec. 5 mesh: 0 / 1 off the mid-lines, 2..6 on them).
+ * orientations of its four squares (Sec. 6 mesh: 0 / 1 off the mid-lines, 2..6 on them).
  * stokes_stencil_rows: for class cls of a level with N = 2^levels and the given beta, the rows of the
  * matrix of eq. gen:bil:mv at the cell's four velocity nodes s = V (2i, 2j), H (2i+1, 2j),
  * E (2i, 2j+1), C (2i+1, 2j+1), as written by the library:
@@ -221,8 +223,9 @@ stokes_status stokes_mass_dot(stokes_handle* h, const double* a, const double* b
 
 /* ||F - A x||_2^2 of the finest level, like stokes_residual_norm, but without a handle and without
  * allocating any device memory.  The paper has no counterpart: this exists for callers that cannot
- * call cudaMalloc -- code that runs while a stream is being captured, code that lives inside a
- * fixed memory budget handed out by another framework, or code on a device that is already full.
+ * call cudaMalloc -- code that lives inside a fixed memory budget handed out by another framework
+ * (which owns the rest of the device), code on a device that is already full, or code that has no
+ * way to release memory later.
  *   levels, beta : as in stokes_params; levels <= 11 (N <= 2048), larger sizes return
  *                  STOKES_ERR_BAD_ARG before any GPU work
  *   u, p, f, g   : caller-owned device arrays with the layouts described at the top of this file
@@ -230,8 +233,9 @@ stokes_status stokes_mass_dot(stokes_handle* h, const double* a, const double* b
  *   stream       : cudaStream_t to run on (NULL = legacy default stream)
  * The per-block partial sums live in one fixed array inside the library (about 131 KB of device
  * memory on every GPU that loads the library, kept until the process exits).  The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress) and builds the host-side
- * element tables; make that first call before any stream capture.  Every call overwrites the whole
+ * device looks up that array's device address (cudaGetSymbolAddress); the first call in a process
+ * may also build the host-side element tables.  Make that first call before any stream capture.
+ * Every call overwrites the whole
  * part of the array it reads, so nothing needs clearing, but all calls share the one array: calls
  * whose GPU work overlaps (different streams or threads without ordering) race and give wrong
  * results. */

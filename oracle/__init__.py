@@ -7,7 +7,7 @@ CPU-baseline leg of ``bench.py`` may import it; the product path (the CUDA libra
 Python binding) never does, and the two share no code.
 
 Modules:
-    mesh      -- the 8-triangle coarse mesh of the unit square and uniform red refinement (Sec. 5)
+    mesh      -- the 8-triangle coarse mesh of the unit square and uniform red refinement (Sec. 6)
     fem       -- Taylor-Hood P2-P1 element matrices by exact polynomial integration, global
                  assembly of A = K + beta*M_U and B (Sec. 2, eq. gen:bil:mv)
     transfer  -- canonical prolongation (embedding) and restriction (its transpose) (Sec. 3)
@@ -15,7 +15,7 @@ Modules:
                  preconditioner (eq. numintroduc), V/W cycles with an exact coarsest solve (Sec. 3),
                  solve loop, direct reference solve
     adjoint   -- gradients of a loss through the discrete solve (symmetric system)
-    experiments -- the numerical experiment of Sec. 5: cone-based exact solution, its L2
+    experiments -- the numerical experiment of Sec. 6: cone-based exact solution, its L2
                  projection, the error norm of eq. defMcL and the mean convergence rate
     timestep  -- implicit Euler steps of the time-dependent Stokes problem (Sec. 1: beta = 1/dt)
     lshape    -- the L-shaped (non-convex) domain: masked meshes, unknowns and transfers (Sec. 1)

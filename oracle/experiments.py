@@ -1,10 +1,10 @@
-"""The numerical experiment of Sec. 5: the cone-based exact solution, its L2 projection x* into
+"""The numerical experiment of Sec. 6: the cone-based exact solution, its L2 projection x* into
 X_k, the error norm |||.|||_k of eq. defMcL and the mean convergence rate q.
 
 TEST INFRASTRUCTURE (part of the oracle package): only tests, the smoke check and the benchmark's
 CPU baseline may import it.
 
-Sec. 5 chooses f and g so that the discrete solution on level k is the L2 projection of
+Sec. 6 chooses f and g so that the discrete solution on level k is the L2 projection of
     u(x, y) = phi(x, y) (y - 1/2, 1/2 - x),   p(x, y) = phi(x, y),
     phi(x, y) = max{0, min{1, 2 - 4 r}},  r = |(x, y) - (1/2, 1/2)|,
 i.e. F_k = A_k x* with x* = (Pi_U u, Pi_P p).  The iteration starts from x^(0), stops at the first
@@ -31,13 +31,13 @@ EPS = 1e-9
 
 
 def cone(x, y):
-    """phi of Sec. 5: 1 for r <= 1/4, 2 - 4r for 1/4 <= r <= 1/2, 0 beyond."""
+    """phi of Sec. 6: 1 for r <= 1/4, 2 - 4r for 1/4 <= r <= 1/2, 0 beyond."""
     r = np.sqrt((x - 0.5) ** 2 + (y - 0.5) ** 2)
     return np.maximum(0.0, np.minimum(1.0, 2.0 - 4.0 * r))
 
 
 def cone_solution(x, y):
-    """(u_x, u_y, p) of the Sec. 5 experiment at points (x, y)."""
+    """(u_x, u_y, p) of the Sec. 6 experiment at points (x, y)."""
     ph = cone(x, y)
     return ph * (y - 0.5), ph * (0.5 - x), ph
 
@@ -160,7 +160,7 @@ def error_norm(disc: fem.Discretization, beta, e):
 
 
 def mean_rate(step, x0, xs, norm, eps=EPS, max_cycles=60, blowup=1e6):
-    """Sec. 5 protocol: iterate x <- step(x) from x0 until norm(x - xs) <= eps norm(x0 - xs).
+    """Sec. 6 protocol: iterate x <- step(x) from x0 until norm(x - xs) <= eps norm(x0 - xs).
     Returns (n, q, errors, divergent); errors[i] = norm(x^(i) - xs)."""
     x = x0.copy()
     errs = [norm(x - xs)]

@@ -1,11 +1,11 @@
-"""Mesh hierarchy of the numerical experiments (Sec. 5): unit square, 8 coarse triangles, red refinement.
+"""Mesh hierarchy of the numerical experiments (Sec. 6): unit square, 8 coarse triangles, red refinement.
 
-Reading of the missing figure (Sec. 5, Fig. 1): the coarsest mesh is the fan of 8 triangles
+Reading of the missing figure (Sec. 6, Fig. 1): the coarsest mesh is the fan of 8 triangles
 around the centre (1/2, 1/2) over the 3x3 vertex grid {0, 1/2, 1}^2.  It is the only split of
 that grid into 8 triangles in which every triangle has a vertex inside the domain (the centre),
 which the inf-sup condition of the Taylor-Hood pair requires (Sec. 2, after eq. cond:s).
 
-Each refinement step splits every triangle into four through its edge midpoints (Sec. 5).
+Each refinement step splits every triangle into four through its edge midpoints (Sec. 6).
 The mesh is built explicitly as a triangle list; no lattice formula is used to produce it.
 
 Coordinates are exact integers: on level k the P2 node lattice has spacing 1/(2N), N = 2^(k+1),
@@ -29,7 +29,7 @@ class Mesh:
 
 
 def coarse_mesh() -> Mesh:
-    """Level 0: fan of 8 triangles around the centre of the 3x3 vertex grid (Sec. 5)."""
+    """Level 0: fan of 8 triangles around the centre of the 3x3 vertex grid (Sec. 6)."""
     # P2 lattice of level 0 has spacing 1/4: vertex grid {0, 1/2, 1} -> {0, 2, 4}
     verts = np.array([(2 * x, 2 * y) for y in range(3) for x in range(3)], dtype=np.int64)
     centre = 4
@@ -54,7 +54,7 @@ def _orient_ccw(m: Mesh) -> None:
 
 
 def refine(m: Mesh) -> Mesh:
-    """Red refinement: every triangle is split into 4 by joining its edge midpoints (Sec. 5)."""
+    """Red refinement: every triangle is split into 4 by joining its edge midpoints (Sec. 6)."""
     verts = [tuple(2 * v) for v in m.verts]          # lattice spacing halves: coordinates double
     index = {v: i for i, v in enumerate(verts)}
 

@@ -10,9 +10,9 @@ Smoothers (Sec. 4):
                  p^{m}     = p^{m-1} - sigma Shat^{-1} (g - B u^{m-1/2})
                  u^{m}     = u^{m-1} + tau Ahat^{-1} (f - A u^{m-1} - B^T p^{m})
     normal equation:  x^{m} = x^{m-1} + tau L^{-1} A L^{-1} (F - A x^{m-1})
-with the practical preconditioner of Sec. 5 (eq. numintroduc):
+with the practical preconditioner of Sec. 6 (eq. numintroduc):
     Ahat = diag A_k,   Shat = diag(B_k Ahat^{-1} B_k^T),   L = diag(Ahat, Shat),
-    tau = sigma = 0.8 for Uzawa, tau = 0.35 for the normal equation (Sec. 5).
+    tau = sigma = 0.8 for Uzawa, tau = 0.35 for the normal equation (Sec. 6).
 Readings where the paper is silent:
   * post-smoothing uses the same smoother as pre-smoothing;
   * the pressure space is the full P1 nodal space; zero mean is imposed by the projection
@@ -199,7 +199,7 @@ def smoother_conditions(lvl: Level, tau=0.8, sigma=0.8):
 
 
 def contraction(hist):
-    """Per-cycle factors q_i = ||r_i|| / ||r_{i-1}|| and their geometric mean (Sec. 5 mean rate)."""
+    """Per-cycle factors q_i = ||r_i|| / ||r_{i-1}|| and their geometric mean (Sec. 6 mean rate)."""
     hist = np.asarray(hist)
     q = hist[1:] / hist[:-1]
     n = len(q)

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "../../include/stokes_mg.h"
+#include "coef.h"
 #include "elements.h"
 #include "kernels.cuh"
 
@@ -74,43 +75,6 @@ template <typename T>
 void free_level(Level<T>& L) {
     if (L.slab) cudaFree(L.slab);
     L.slab = nullptr;
-}
-
-const SquareMatrices& squares() {
-    static SquareMatrices S = square_matrices();
-    return S;
-}
-
-template <typename T>
-OpCoef<T> make_coef(int n, double beta) {
-    const SquareMatrices& S = squares();
-    const double h = 1.0 / n;
-    OpCoef<T> c;
-    for (int o = 0; o < 2; ++o) {
-        for (int l = 0; l < 9; ++l)
-            for (int m = 0; m < 9; ++m) c.A[o][l][m] = (T)(S.K[o][l][m] + beta * h * h * S.M[o][l][m]);
-        for (int q = 0; q < 4; ++q)
-            for (int m = 0; m < 9; ++m) {
-                c.Bx[o][q][m] = (T)(h * S.Bx[o][q][m]);
-                c.By[o][q][m] = (T)(h * S.By[o][q][m]);
-            }
-    }
-    fill_merged(c);
-    return c;
-}
-
-template <typename T>
-MassCoef<T> make_mass(int n) {
-    const SquareMatrices& S = squares();
-    const double h = 1.0 / n;
-    MassCoef<T> m;
-    for (int o = 0; o < 2; ++o) {
-        for (int l = 0; l < 9; ++l)
-            for (int k = 0; k < 9; ++k) m.M[o][l][k] = (T)(h * h * S.M[o][l][k]);
-        for (int q = 0; q < 4; ++q)
-            for (int r = 0; r < 4; ++r) m.MP[o][q][r] = (T)(h * h * S.MP[o][q][r]);
-    }
-    return m;
 }
 
 std::mutex g_dev_mu;
@@ -427,7 +391,7 @@ stokes_status rebuild_beta(stokes_handle* h) {
     }
     CK(cudaGetLastError());
     double inv[27 * 27];
-    if (!coarse_inverse(squares(), beta, inv)) return STOKES_ERR_BAD_ARG;
+    if (!coarse_inverse(square_tables(), beta, inv)) return STOKES_ERR_BAD_ARG;
     CK(cudaMemcpyAsync(h->inv, inv, sizeof(inv), cudaMemcpyHostToDevice, h->st));
     CK(cudaStreamSynchronize(h->st));
     if (h->step) {
@@ -848,7 +812,7 @@ stokes_status stokes_transfer_weights(double* w) {
 
 stokes_status stokes_coarse_inverse(double beta, double* inv) {
     if (!inv || !(beta >= 0.0) || !std::isfinite(beta)) return STOKES_ERR_BAD_ARG;
-    return coarse_inverse(squares(), beta, inv) ? STOKES_OK : STOKES_ERR_BAD_ARG;
+    return coarse_inverse(square_tables(), beta, inv) ? STOKES_OK : STOKES_ERR_BAD_ARG;
 }
 
 stokes_status stokes_euler_rhs(stokes_handle* h, const double* u_prev, const double* f_nodal, const double* g_nodal,

@@ -54,7 +54,7 @@ __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.lau
 bool pdl_enabled();
 
 template <typename... KArgs, typename... Args>
-inline void launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+inline cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;
@@ -65,7 +65,7 @@ inline void launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, 
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = pdl_enabled() ? 1 : 0;
-    cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+    return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
 }
 
 // Views map P2-lattice points to values.  A velocity view answers at(si, sj, a, b), the value at

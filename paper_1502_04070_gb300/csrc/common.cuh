@@ -1,6 +1,6 @@
 // common.cuh -- data structures and device helpers shared by the solver's kernels.
 //
-// Geometry (Sec. 5): level k of the unit square has N = 2^(k+1) squares per side; square (si, sj)
+// Geometry (Sec. 6): level k of the unit square has N = 2^(k+1) squares per side; square (si, sj)
 // covers [si/N, (si+1)/N] x [sj/N, (sj+1)/N] and is cut by one diagonal.  Refining the 8-triangle
 // coarse mesh (the fan around the centre) keeps the diagonal direction of each quadrant:
 //     orientation 0 ("/", from (0,0) to (1,1) of the square) in the SW and NE quadrants,

@@ -506,7 +506,7 @@ void launch_coarse_solve(cudaStream_t s, const double* inv, const T* f, const T*
 }
 
 // ------------------------------------------------------------------------------------------
-// Shat = diag(B Ahat^{-1} B^T), Ahat = diag A (Sec. 5, eq. numintroduc): for vertex (i, j),
+// Shat = diag(B Ahat^{-1} B^T), Ahat = diag A (Sec. 6, eq. numintroduc): for vertex (i, j),
 // sum over interior velocity nodes l and both components of B_{(i,j), l}^2 / A_{ll}.
 __device__ double diagA_at(int X, int Y, int n, const OpCoef<double>& c) {
     double d = 0.0;
@@ -591,8 +591,8 @@ __global__ void k_reduce(const double* __restrict__ partial, int count, double* 
     pdl_trigger();
 }
 
-void launch_reduce(cudaStream_t s, const double* partial, int count, double* out) {
-    launch_pdl(k_reduce, 1, 1024, 0, s, partial, count, out);
+cudaError_t launch_reduce(cudaStream_t s, const double* partial, int count, double* out) {
+    return launch_pdl(k_reduce, 1, 1024, 0, s, partial, count, out);
 }
 
 template <typename T>

@@ -96,8 +96,8 @@ void launch_schur_diag(cudaStream_t s, int n, const OpCoef<double>& c, T* sinv);
 template <typename T>
 void launch_pmean(cudaStream_t s, int n, T* p, double* partial, double* scalar);
 
-// out[0] = sum of partial[0..count)
-void launch_reduce(cudaStream_t s, const double* partial, int count, double* out);
+// out[0] = sum of partial[0..count); returns the launch's own status
+cudaError_t launch_reduce(cudaStream_t s, const double* partial, int count, double* out);
 
 // load vectors: f = M_U f_nodal (interior rows), g = M_P g_nodal, with optional zero-mean shift
 template <typename T>

@@ -40,7 +40,7 @@ bool l_interior(int X, int Y, int n) {
 }
 
 // Diagonal of A = K + beta M at an interior lattice node: the sum over the squares that contain it
-// (orientation 0 in the lower-left and upper-right quadrants, 1 in the other two, Sec. 5 mesh).
+// (orientation 0 in the lower-left and upper-right quadrants, 1 in the other two, Sec. 6 mesh).
 double a_diag(const SquareMatrices& S, int X, int Y, int n, double beta) {
     const double h = 1.0 / n;
     double s = 0.0;

@@ -1,18 +1,17 @@
 // noalloc.cu -- residual norm for callers that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc: code running inside a stream capture that must not
-// allocate, callers that own a fixed memory budget (an arena handed out by another framework,
-// or a device that is already full), or embedding code with no way to free memory later.  For
-// them this file offers stokes_residual_norm2_noalloc(), a handle-free variant of the residual
-// kernel whose only scratch (the per-block partial sums of the norm) lives in a file-scope
-// __device__ array of fixed size.  Each GPU that loads the library keeps that array (about 131 KB)
-// until the process exits.
+// Some callers cannot call cudaMalloc: code that works inside a fixed memory budget handed out by
+// another framework (an arena that owns the rest of the device), code on a device that is already
+// full, or embedding code with no way to release memory later.  For them this file offers
+// stokes_residual_norm2_noalloc(), a handle-free variant of the residual kernel whose only scratch
+// (the per-block partial sums of the norm) lives in a file-scope __device__ array of fixed size.
+// Each GPU that loads the library keeps that array (about 131 KB) until the process exits.
 #include <cmath>
 #include <mutex>
 
 #include "../../include/stokes_mg.h"
 #include "cellops.cuh"
-#include "elements.h"
+#include "coef.h"
 #include "kernels.cuh"
 
 namespace smg {
@@ -27,8 +26,6 @@ static __device__ __align__(256) double g_noalloc_partials[kNoAllocPartials];
 
 std::mutex g_noalloc_mu;
 double* g_noalloc_ptr[64] = {};          // device address of the array, per device (set-up once)
-SquareMatrices g_noalloc_sq;
-bool g_noalloc_sq_ready = false;
 
 // ||F - A x||^2 partial sums per block: the residual kernel without its output arrays
 __global__ void __launch_bounds__(NT) k_residual_sumsq(int n, const __grid_constant__ OpCoef<double> c,
@@ -78,12 +75,8 @@ extern "C" stokes_status stokes_residual_norm2_noalloc(int levels, double beta, 
     if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return STOKES_ERR_CUDA;
     double* scratch = nullptr;
     {
-        // set-up, once per device (and once per process for the host tables)
+        // set-up, once per device: the array's device address (host code cannot use the symbol itself)
         std::lock_guard<std::mutex> lk(g_noalloc_mu);
-        if (!g_noalloc_sq_ready) {
-            g_noalloc_sq = square_matrices();
-            g_noalloc_sq_ready = true;
-        }
         if (!g_noalloc_ptr[dev]) {
             void* ptr = nullptr;
             if (cudaGetSymbolAddress(&ptr, g_noalloc_partials) != cudaSuccess) return STOKES_ERR_CUDA;
@@ -92,20 +85,15 @@ extern "C" stokes_status stokes_residual_norm2_noalloc(int levels, double beta, 
         scratch = g_noalloc_ptr[dev];
     }
     const int n = 1 << levels;
-    const double h = 1.0 / n;
-    OpCoef<double> c;
-    for (int o = 0; o < 2; ++o) {
-        for (int l = 0; l < 9; ++l)
-            for (int m = 0; m < 9; ++m) c.A[o][l][m] = g_noalloc_sq.K[o][l][m] + beta * h * h * g_noalloc_sq.M[o][l][m];
-        for (int q = 0; q < 4; ++q)
-            for (int m = 0; m < 9; ++m) {
-                c.Bx[o][q][m] = h * g_noalloc_sq.Bx[o][q][m];
-                c.By[o][q][m] = h * g_noalloc_sq.By[o][q][m];
-            }
-    }
-    fill_merged(c);
+    const OpCoef<double> c = make_coef<double>(n, beta);
     cudaStream_t s = (cudaStream_t)stream;
-    k_residual_sumsq<<<cells_grid(n), dim3(BX, BY), 0, s>>>(n, c, u, p, f, g, scratch);
-    launch_reduce(s, scratch, cells_blocks(n), norm2);
-    return cudaGetLastError() == cudaSuccess ? STOKES_OK : STOKES_ERR_CUDA;
+    // each launch reports its own status (cudaLaunchKernelEx), so an error that the caller's earlier
+    // work left pending in the runtime is neither blamed on this call nor cleared by it
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = cells_grid(n);
+    cfg.blockDim = dim3(BX, BY);
+    cfg.stream = s;
+    if (cudaLaunchKernelEx(&cfg, k_residual_sumsq, n, c, u, p, f, g, scratch) != cudaSuccess) return STOKES_ERR_CUDA;
+    if (launch_reduce(s, scratch, cells_blocks(n), norm2) != cudaSuccess) return STOKES_ERR_CUDA;
+    return STOKES_OK;
 }

@@ -1,5 +1,5 @@
 """Writes tests/golden/replication_w33_k78.json with the oracle's (and only the oracle's) results
-for the experiment of Sec. 5 on levels k = 7 and 8: W(3,3) cycles with the Uzawa smoother
+for the experiment of Sec. 6 on levels k = 7 and 8: W(3,3) cycles with the Uzawa smoother
 (tau = sigma = 0.8) from x^(0) = 0 on the L2 projection x* of the cone solution, the error
 |||x^(i) - x*|||_k of eq. defMcL after every cycle until its reduction by 1e-9, and the mean rate
 q, for beta in {0, 1e2, 1e4, 1e6, 1e8, 1e10} (the columns of Tables 2 and 3).
@@ -24,7 +24,7 @@ BETAS = [0.0, 1e2, 1e4, 1e6, 1e8, 1e10]
 
 
 def main():
-    out = {"protocol": "Sec. 5: W(3,3), Uzawa tau = sigma = 0.8, x0 = 0, error norm of eq. defMcL with "
+    out = {"protocol": "Sec. 6: W(3,3), Uzawa tau = sigma = 0.8, x0 = 0, error norm of eq. defMcL with "
                        "h = sqrt(2)/N, stop at 1e-9 error reduction", "betas": BETAS, "levels": {}}
     for k in (7, 8):
         discs = fem.discretizations(k + 1)

@@ -240,7 +240,7 @@ def test_smoother_float32_every_variant(discs, Solver, k, variant):
 def test_mixed_cycle_variants(discs, Solver, k, nu_pre, nu_post, gamma):
     """W-cycles and odd smoothing counts (the float32 ping-pong ends in the scratch buffer) in the
     mixed path converge to the oracle's exact discrete solution.  (nu = 2+1 is not tested: like
-    2+2 in Sec. 5, Table 1, it diverges.)"""
+    2+2 in Sec. 6, Table 1, it diverges.)"""
     d = discs[k]
     fn, gn = workloads.random_nodal(k, 80 + k)
     S = Solver(k + 1, 10.0, precision="mixed", nu_pre=nu_pre, nu_post=nu_post, gamma=gamma)
@@ -253,7 +253,7 @@ def test_mixed_cycle_variants(discs, Solver, k, nu_pre, nu_post, gamma):
 
 
 def test_divergence_is_reported(Solver):
-    """Sec. 5, Table 1: the Uzawa smoother with nu = 1+1 diverges; the solver must stop with
+    """Sec. 6, Table 1: the Uzawa smoother with nu = 1+1 diverges; the solver must stop with
     STOKES_DIVERGED instead of running to max_cycles or raising."""
     from paper_1502_04070_gb300 import _binding
     k = 4

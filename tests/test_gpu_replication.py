@@ -1,4 +1,4 @@
-"""The experiment of Sec. 5 on the CUDA path: W(3,3) cycles with the Uzawa smoother from x^(0) = 0
+"""The experiment of Sec. 6 on the CUDA path: W(3,3) cycles with the Uzawa smoother from x^(0) = 0
 on F = A x*, x* the L2 projection of the cone solution, with the error measured after every cycle
 in the norm of eq. defMcL.  The oracle supplies x*, F and the norm; every cycle runs in the
 library (one stokes_cycle call per iteration).
@@ -7,7 +7,7 @@ library (one stokes_cycle call per iteration).
 * k = 7, 8: the float64 history equals the one the oracle wrote
   (tests/golden/replication_w33_k78.json, from tests/golden/make_replication_golden.py), and the
   iteration counts lie within the band around the paper's Table 3
-  (tests/golden/paper_tables_sec5.json) that the oracle's own counts meet on k = 4..6;
+  (tests/golden/paper_tables_sec6.json) that the oracle's own counts meet on k = 4..6;
 * k = 7, mixed precision (float32 W-cycles inside float64 refinement): the counts stay within
   one of the float64 ones and within the same band.
 """
@@ -26,7 +26,7 @@ from tests._gpu import dev, host
 pytestmark = pytest.mark.gpu
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-TABLES = json.load(open(os.path.join(HERE, "golden", "paper_tables_sec5.json")))
+TABLES = json.load(open(os.path.join(HERE, "golden", "paper_tables_sec6.json")))
 GOLD = json.load(open(os.path.join(HERE, "golden", "replication_w33_k78.json")))
 BETAS = TABLES["betas"]
 EPS = 1e-9
@@ -58,7 +58,7 @@ def _xstar(discs, projections, k):
 
 
 def gpu_errors(d, k, beta, xs, precision="fp64", max_cycles=60):
-    """The protocol of Sec. 5 with the library's cycle; returns (n, q, errors, divergent)."""
+    """The protocol of Sec. 6 with the library's cycle; returns (n, q, errors, divergent)."""
     from paper_1502_04070_gb300.solver import Solver
     F = d.system(beta) @ xs
     fu, gp = d.from_vec(F)

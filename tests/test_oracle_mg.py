@@ -40,7 +40,7 @@ def test_uzawa_step_equals_compact_form(discs, beta):
 
 
 def test_diagonals_definition(discs):
-    """Sec. 5 (eq. numintroduc): Shat = diag(B diag(A)^{-1} B^T), checked with dense algebra."""
+    """Sec. 6 (eq. numintroduc): Shat = diag(B diag(A)^{-1} B^T), checked with dense algebra."""
     H = mg.Hierarchy(3, 7.0, discs[:3])
     lvl = H.finest
     A = lvl.A.toarray()
@@ -120,7 +120,7 @@ def test_robust_contraction(discs):
 
 
 def test_table1_structure(discs):
-    """Sec. 5, Table 1 (k = 4): the Uzawa smoother diverges for nu = 1+1 and 2+2 and converges for
+    """Sec. 6, Table 1 (k = 4): the Uzawa smoother diverges for nu = 1+1 and 2+2 and converges for
     3+3; the normal-equation smoother (tau = 0.35) already converges for 1+1."""
     H = mg.Hierarchy(5, 1.0, discs)
     F = _rhs(H.discs[-1], 5)

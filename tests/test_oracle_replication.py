@@ -1,6 +1,6 @@
-"""The experiment of Sec. 5 in the oracle (oracle/experiments.py), pinned.
+"""The experiment of Sec. 6 in the oracle (oracle/experiments.py), pinned.
 
-* the fixture of the paper's printed Tables 1-3 (tests/golden/paper_tables_sec5.json) is
+* the fixture of the paper's printed Tables 1-3 (tests/golden/paper_tables_sec6.json) is
   consistent with the stated protocol (q^n <= 1e-9) and with the printed nu^(-1/2) row;
 * the quadrature rule, the load integrals of the cone solution and the L2 projection against
   closed forms (integrals over the disc written out by hand), exactness on P1 and the
@@ -22,7 +22,7 @@ from oracle import experiments as ex
 from oracle import fem
 from oracle import multigrid as mg
 
-GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "paper_tables_sec5.json")
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "paper_tables_sec6.json")
 
 
 @pytest.fixture(scope="module")
