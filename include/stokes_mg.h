@@ -243,7 +243,7 @@ stokes_status stokes_residual_norm2_noalloc(int levels, double beta, const doubl
                                             const double* f, const double* g, double* norm2, void* stream);
 
 /* Chooses, for every level of a STOKES_MIXED handle whose size has not been tuned in this process,
- * the fastest float32 Uzawa step variant (fused one-kernel tiles of several shapes, or the
+ * the fastest float32 Uzawa step variant (one-kernel tiles of several kinds and shapes, or the
  * three-kernel step with several block shapes) by timing each on the handle's buffers; the choice
  * is kept process-wide per level size.  Untuned levels use the three-kernel step below N = 128 and
  * the 32 x 16 fused tile above.  Synchronises the stream. */
@@ -251,9 +251,16 @@ stokes_status stokes_autotune(stokes_handle* h);
 /* The step variant currently used for a float32 level with `levels` levels (N = 2^levels), -1 if
  * out of range: 0-3 fused tiles 32x16, 32x8, 64x8, 16x16; 4-6 three-kernel step, blocks 32x8, 16x8, 8x8;
  * 7-9 fused step on component-pair tiles (packed FP32x2 arithmetic), 28 cells wide: 8 or 4 warps with the
- * tile height chosen per level, or 12 warps on 8 rows. */
+ * tile height chosen per level, or 12 warps on 8 rows; 10-11 fused step with the operator's coefficients
+ * in registers and asynchronous staging, 28 cells wide, 8 warps, tile height chosen per level for at least
+ * 2 or at least 4 resident CTAs per SM. */
 int stokes_step_variant(int levels);
-/* Sets the step variant (0-9, as above) for float32 levels with `levels` levels (N = 2^levels),
+/* Host-only (no device work): STOKES_OK if the merged stencils of the two orientation classes on a
+ * level with N = 2^levels and this beta have exactly the compile-time structure that step variants
+ * 10-11 assume (which coefficients vanish, which are equal, B and B^T entries +-b and +-b/2 for one
+ * b); STOKES_ERR_BAD_ARG otherwise (those variants then run the pair tile of variant 7 instead). */
+stokes_status stokes_step_tables_match(int levels, double beta);
+/* Sets the step variant (0-11, as above) for float32 levels with `levels` levels (N = 2^levels),
  * process-wide, and marks that size as tuned (stokes_autotune keeps it).  Takes effect for direct
  * smoothing calls (stokes_smooth_f32) and for cycle graphs captured afterwards; graphs a handle has
  * already captured keep their variant.  Not thread-safe against concurrent setup or capture.

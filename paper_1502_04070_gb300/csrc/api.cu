@@ -494,7 +494,8 @@ stokes_status stokes_setup(const stokes_params* prm, void* stream, stokes_handle
     stokes_status s = ensure_weights();
     if (s != STOKES_OK) return s;
     if (prepare_uzawa_fused<float>() != cudaSuccess || prepare_uzawa_fused<double>() != cudaSuccess ||
-        prepare_coarse_cycle() != cudaSuccess || prepare_uzawa_pair() != cudaSuccess)
+        prepare_coarse_cycle() != cudaSuccess || prepare_uzawa_pair() != cudaSuccess ||
+        prepare_uzawa_reg() != cudaSuccess)
         return STOKES_ERR_CUDA;
     stokes_handle* h = new stokes_handle_t();
     h->prm = P;
@@ -801,6 +802,11 @@ stokes_status stokes_stencil_rows(int levels, double beta, int cls, double* ma, 
     std::memcpy(mby, c.MBy[cls], sizeof(c.MBy[cls]));
     std::memcpy(midg, c.MIdg[cls], sizeof(c.MIdg[cls]));
     return STOKES_OK;
+}
+
+stokes_status stokes_step_tables_match(int levels, double beta) {
+    if (levels < 1 || levels > 13 || !(beta >= 0.0) || !std::isfinite(beta)) return STOKES_ERR_BAD_ARG;
+    return reg_tables_match(make_coef<float>(1 << levels, beta)) ? STOKES_OK : STOKES_ERR_BAD_ARG;
 }
 
 stokes_status stokes_transfer_weights(double* w) {

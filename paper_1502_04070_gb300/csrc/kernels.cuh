@@ -53,6 +53,16 @@ void launch_uzawa_pair(int variant, cudaStream_t s, int n, const OpCoef<float>& 
                        const float* u, const float* p, const float* f, const float* g, const float* sinv,
                        float* u_out, float* p_out);
 cudaError_t prepare_uzawa_pair();
+// The float32 step with the operator's coefficients in registers and asynchronous staging
+// (uzawa_reg.cu), 28 cells wide, 8 warps; variant 0: tile height for at least 2 CTAs per SM, 1: for at
+// least 4.  Returns false (and launches
+// nothing) if the level's coefficients do not have the compile-time structure the kernel assumes.
+bool launch_uzawa_reg(int variant, cudaStream_t s, int n, const OpCoef<float>& c, float tau, float sigma,
+                      const float* u, const float* p, const float* f, const float* g, const float* sinv,
+                      float* u_out, float* p_out);
+cudaError_t prepare_uzawa_reg();
+// Does the compile-time structure of the register tile match these coefficients?
+bool reg_tables_match(const OpCoef<float>& c);
 template <typename T>
 cudaError_t launch_uzawa_fused(cudaStream_t s, int n, const OpCoef<T>& c, T tau, T sigma, const T* u, const T* p,
                                const T* f, const T* g, const T* sinv, T* u_out, T* p_out);

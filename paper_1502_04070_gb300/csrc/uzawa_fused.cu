@@ -166,10 +166,13 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 4 ? 2 : 1)) k_uzawa_fuse
 // suits the small levels, whose few fused tiles are issue-bound) with blocks 4: 32 x 8, 5: 16 x 8,
 // 6: 8 x 8.  Fused step on component-pair tiles with packed FP32x2 arithmetic (uzawa_pair.cu):
 // 7: 28 cells wide, 8 warps, height chosen per level; 8: the same with 4 warps; 9: 28 x 8 cells,
-// 12 warps (one row of the u^{m-1/2} region per warp: shortest CTAs, for small levels).
+// 12 warps (one row of the u^{m-1/2} region per warp: shortest CTAs, for small levels).  Fused step
+// with the coefficients in registers and asynchronous staging (uzawa_reg.cu), 28 cells wide, 8 warps,
+// height chosen per level: 10: at least 2 CTAs per SM, 11: at least 4 (shorter tiles, 64 registers).
 constexpr int kFusedVariants = 4;
 constexpr int kPairVariant0 = 7;
-constexpr int kStepVariants = 10;
+constexpr int kRegVariant0 = 10;
+constexpr int kStepVariants = 12;
 // per level k (N = 2^(k+1)): chosen variant; until tuned, the three-kernel step below N = 128 and the
 // 32 x 16 fused tile from N = 128 up
 static int g_tile_choice[32] = {5, 5, 5, 5, 5, 5, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0,
@@ -231,6 +234,13 @@ static bool launch_step_variant(int v, cudaStream_t s, int n, const OpCoef<float
                                 float* p_out) {
     if (v < kFusedVariants) {
         launch_variant<float>(v, s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
+        return true;
+    }
+    if (v >= kRegVariant0) {
+        // the register tile checks the level's coefficients against its compile-time structure; if
+        // they do not match, the pair tile runs instead
+        if (!launch_uzawa_reg(v - kRegVariant0, s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out))
+            launch_uzawa_pair(0, s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
         return true;
     }
     if (v >= kPairVariant0) {

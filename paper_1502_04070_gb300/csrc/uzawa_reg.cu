@@ -1,0 +1,645 @@
+// uzawa_reg.cu -- the float32 Uzawa step (Sec. 4) in one kernel with the operator's coefficients
+// held in registers.
+//
+//   u^{m-1/2} = u^{m-1} + tau Ahat^{-1} (f - A u^{m-1} - B^T p^{m-1})
+//   dp        = sigma Shat^{-1} (B u^{m-1/2} - g),      p^{m} = p^{m-1} + dp
+//   u^{m}     = u^{m-1/2} - tau Ahat^{-1} B^T dp
+//
+// Away from the two mid-lines every cell has the stencils of its quadrant's orientation class, and
+// these stencils are far sparser and more regular than their structural pattern: the four velocity
+// rows of a cell (V, H, E, C) have 17 + 9 + 9 + 7 nonzero coefficients (for every beta and h: K has
+// the zero couplings of the P2 stiffness on right isosceles triangles, M those of the P2 mass), which
+// take only eight distinct values per class (the mesh's point and diagonal symmetries and A = A^T);
+// the vertex row of B^T vanishes, and every entry of B and B^T is +-b or +-b/2 for one b ~ h.  The
+// kernel therefore keeps the eight A values as (a, a) pairs in sixteen registers, applies each A
+// term with one packed FP32x2 FMA on the (u_x, u_y) pair, and forms B u and B^T p as sums with the
+// literal weights +-1, +-1/2, scaled once by b.  The structure is a compile-time table (below),
+// checked against the level's assembled coefficients on the host before every launch
+// (make_reg_coef).
+//
+// Data movement: a CTA owns a 28 x ty tile of cells and stages, with asynchronous 4-byte copies
+// (cp.async, zero-filled off the domain), u with a three-cell halo as (u_x, u_y) pairs split by the
+// parity of the lattice column, p with the same halo, f on the tile plus two cells, and g, Shat^{-1}
+// on the tile plus one vertex.  u^{m-1/2} overwrites f in place (each value read and written by the
+// same thread) and dp overwrites g.  Tiles whose u^{m-1/2} region meets a mid-line take the general
+// per-cell rows of cellops.cuh on the same shared tiles.
+#include <algorithm>
+#include <cmath>
+
+#include "cellops.cuh"
+#include "kernels.cuh"
+#include "tiles.cuh"
+
+namespace smg {
+namespace {
+
+// ---------------------------------------------------------------------------------------------
+// Structure of the merged stencils of the orientation classes 0 and 1 (common.cuh), by window
+// point w = (dy + 2) * 5 + dx + 2 of the 5 x 5 lattice window around the cell's vertex (2i, 2j)
+// and owned node s (0 V, 1 H, 2 E, 3 C):
+//   kGid[cls][s][w]  group of the A coefficient (-1: zero); every group holds one value
+//   kBx / kBy[cls][w]  the vertex's B row in units of b/2 (values 0, +-1, +-2)
+//   kBTx / kBTy[cls][s][v]  the B^T rows over the 3 x 3 vertex window v = (dj + 1) * 3 + di + 1,
+//                           in units of b/2
+constexpr int kGroups = 8;
+constexpr int kGidDiagV = 4, kGidDiagE = 7;   // groups of the diagonal of the V row and of the H, E, C rows
+constexpr signed char kGid[2][4][25] = {
+    {{0, 1, 2, -1, -1, 1, -1, 3, 1, -1, 2, 3, 4, 3, 2, -1, 1, 3, -1, 1, -1, -1, 2, 1, 0},
+     {-1, -1, 1, -1, -1, -1, -1, 5, 6, -1, -1, -1, 3, 7, 3, -1, -1, -1, 6, 5, -1, -1, -1, -1, 1},
+     {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, 1, 5, 3, -1, -1, -1, 6, 7, 6, -1, -1, -1, 3, 5, 1},
+     {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, 6, 1, -1, -1, 6, 7, 6, -1, -1, 1, 6, -1}},
+    {{-1, -1, 0, 1, 2, -1, 1, 3, -1, 1, 0, 3, 4, 3, 0, 1, -1, 3, 1, -1, 2, 1, 0, -1, -1},
+     {-1, -1, -1, -1, 1, -1, -1, -1, 5, 6, -1, -1, 3, 7, 3, -1, -1, 6, 5, -1, -1, -1, 1, -1, -1},
+     {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, 3, 6, 1, -1, 5, 7, 5, -1, 1, 6, 3, -1, -1},
+     {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, 1, 5, -1, -1, -1, 5, 7, 5, -1, -1, -1, 5, 1}}};
+constexpr signed char kBx[2][25] = {
+    {0, 0, 0, 0, 0, -1, -1, 1, 1, 0, 0, -2, 0, 2, 0, 0, -1, -1, 1, 1, 0, 0, 0, 0, 0},
+    {0, 0, 0, 0, 0, 0, -1, -1, 1, 1, 0, -2, 0, 2, 0, -1, -1, 1, 1, 0, 0, 0, 0, 0, 0}};
+constexpr signed char kBy[2][25] = {
+    {0, -1, 0, 0, 0, 0, -1, -2, -1, 0, 0, 1, 0, -1, 0, 0, 1, 2, 1, 0, 0, 0, 0, 1, 0},
+    {0, 0, 0, -1, 0, 0, -1, -2, -1, 0, 0, -1, 0, 1, 0, 0, 1, 2, 1, 0, 0, 1, 0, 0, 0}};
+constexpr signed char kBTx[2][4][9] = {
+    {{0, 0, 0, 0, 0, 0, 0, 0, 0}, {0, 0, 0, 0, 2, -2, 0, 0, 0}, {0, 0, 0, 1, -1, 0, 0, 1, -1}, {0, 0, 0, 0, 1, -1, 0, 1, -1}},
+    {{0, 0, 0, 0, 0, 0, 0, 0, 0}, {0, 0, 0, 0, 2, -2, 0, 0, 0}, {0, 0, 0, 0, 1, -1, 1, -1, 0}, {0, 0, 0, 0, 1, -1, 0, 1, -1}}};
+constexpr signed char kBTy[2][4][9] = {
+    {{0, 0, 0, 0, 0, 0, 0, 0, 0}, {0, 1, 0, 0, -1, 1, 0, 0, -1}, {0, 0, 0, 0, 2, 0, 0, -2, 0}, {0, 0, 0, 0, 1, 1, 0, -1, -1}},
+    {{0, 0, 0, 0, 0, 0, 0, 0, 0}, {0, 0, 1, 0, 1, -1, 0, -1, 0}, {0, 0, 0, 0, 2, 0, 0, -2, 0}, {0, 0, 0, 0, 1, 1, 0, -1, -1}}};
+
+__host__ __device__ constexpr bool a_win(int C, int w) {
+    return kGid[C][0][w] >= 0 || kGid[C][1][w] >= 0 || kGid[C][2][w] >= 0 || kGid[C][3][w] >= 0;
+}
+__host__ __device__ constexpr bool bt_vwin(int C, int v) {
+    for (int s = 0; s < 4; ++s)
+        if (kBTx[C][s][v] != 0 || kBTy[C][s][v] != 0) return true;
+    return false;
+}
+
+}  // namespace
+
+// Values of the structure above for one level (host-built by make_reg_coef)
+struct RegCoef {
+    float2 a[2][kGroups];   // A group values as (a, a) pairs, per class
+    float ti[2][2];         // tau / diag A: [class][0 = V row, 1 = H, E, C rows]
+    float b;                // B = (b / 2) x (the integer tables)
+};
+
+// Fills q from the level's merged stencils and checks that they have exactly the compile-time
+// structure (zeros, equal groups, B entries +-b, +-b/2); false if not (the caller then uses
+// another step variant).
+static bool make_reg_coef(const OpCoef<float>& c, float tau, RegCoef& q) {
+    double amax = 0.0, bmax = 0.0;
+    for (int C = 0; C < 2; ++C) {
+        for (int s = 0; s < 4; ++s)
+            for (int w = 0; w < 25; ++w) amax = std::max(amax, std::fabs((double)c.MA[C][s][w]));
+        for (int w = 0; w < 25; ++w) bmax = std::max({bmax, std::fabs((double)c.MBx[C][w]), std::fabs((double)c.MBy[C][w])});
+    }
+    if (!(amax > 0.0) || !(bmax > 0.0)) return false;
+    const double b = bmax;
+    for (int C = 0; C < 2; ++C) {
+        bool set[kGroups] = {};
+        for (int s = 0; s < 4; ++s)
+            for (int w = 0; w < 25; ++w) {
+                const double v = c.MA[C][s][w];
+                const int gid = kGid[C][s][w];
+                if (gid < 0) {
+                    if (std::fabs(v) > 1e-6 * amax) return false;
+                    continue;
+                }
+                if (!set[gid]) {
+                    q.a[C][gid] = make_float2((float)v, (float)v);
+                    set[gid] = true;
+                } else if (std::fabs(v - (double)q.a[C][gid].x) > 1e-6 * std::fabs(v) + 1e-7 * amax) {
+                    return false;
+                }
+            }
+        for (int g = 0; g < kGroups; ++g)
+            if (!set[g]) return false;
+        for (int w = 0; w < 25; ++w)
+            if (std::fabs(c.MBx[C][w] - 0.5 * b * kBx[C][w]) > 1e-6 * b ||
+                std::fabs(c.MBy[C][w] - 0.5 * b * kBy[C][w]) > 1e-6 * b)
+                return false;
+        for (int s = 0; s < 4; ++s)
+            for (int v = 0; v < 9; ++v)
+                if (std::fabs(c.MBTx[C][s][v] - 0.5 * b * kBTx[C][s][v]) > 1e-6 * b ||
+                    std::fabs(c.MBTy[C][s][v] - 0.5 * b * kBTy[C][s][v]) > 1e-6 * b)
+                    return false;
+        // the diagonal groups are the stored inverse diagonals
+        if (std::fabs(1.0 / q.a[C][kGidDiagV].x - c.MIdg[C][0]) > 1e-6 * std::fabs(c.MIdg[C][0])) return false;
+        for (int s = 1; s < 4; ++s)
+            if (std::fabs(1.0 / q.a[C][kGidDiagE].x - c.MIdg[C][s]) > 1e-6 * std::fabs(c.MIdg[C][s])) return false;
+        q.ti[C][0] = tau * c.MIdg[C][0];
+        q.ti[C][1] = tau * c.MIdg[C][1];
+    }
+    q.b = (float)b;
+    return true;
+}
+
+bool reg_tables_match(const OpCoef<float>& c) {
+    RegCoef q;
+    return make_reg_coef(c, 1.0f, q);
+}
+
+namespace {
+
+struct RegTile {
+    static constexpr int TX = 28;
+    static_assert(TX + 4 == 32, "one warp covers a row of the u^{m-1/2} region");
+    static constexpr int UWH = TX + 6;   // u: cells [i0-3, i0+TX+3); float2 per parity-plane row
+    static constexpr int PW = TX + 6;    // p: vertices [i0-3, i0+TX+3)
+    static constexpr int FW = TX + 4;    // f, u^{m-1/2}: cells [i0-2, i0+TX+2), one plane per node type
+    static constexpr int DW = TX + 2;    // g, Shat^{-1}, dp: vertices [i0-1, i0+TX+1)
+    // planes are padded to 8 float2 modulo 16 so that two planes start 16 banks apart: a warp that
+    // stages 16 consecutive lattice points (both components) writes 32 distinct banks
+    __host__ __device__ static constexpr int pad8(int m) { return m + ((8 - m % 16) + 16) % 16; }
+    __host__ __device__ static constexpr int upl(int ty) { return pad8(UWH * 2 * (ty + 6)); }   // float2 per u plane
+    __host__ __device__ static constexpr int fpl(int ty) { return pad8(FW * (ty + 4)); }        // float2 per f plane
+    __host__ __device__ static constexpr int dsz(int ty) { return DW * (ty + 2); }
+    __host__ __device__ static constexpr size_t bytes(int ty) {
+        return 8 * (size_t)(2 * upl(ty) + 4 * fpl(ty)) + 4 * (size_t)(PW * (ty + 6) + 2 * dsz(ty));
+    }
+};
+constexpr int kRegMaxRows = 24;
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+// 4-byte asynchronous copy global -> shared, zero-filled when !valid (the source is then not read)
+__device__ __forceinline__ void cp4(void* dst, const float* src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_commit_wait() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// One component of the f / u^{m-1/2} tile (four planes by node type, FW float2 per row); lattice
+// coordinates are absolute, the region starts at cell (xc0, yc0).
+struct QuadLat {
+    static constexpr bool zero_filled = true;
+    const float2* p;
+    int pl, xc0, yc0;
+    bool ycomp;
+    __device__ __forceinline__ float operator()(int X, int Y) const {
+        const int dx = X - 2 * xc0, dy = Y - 2 * yc0;
+        const float2 e = p[((dx & 1) + 2 * (dy & 1)) * pl + (dy >> 1) * RegTile::FW + (dx >> 1)];
+        return ycomp ? e.y : e.x;
+    }
+    __device__ __forceinline__ float at(int si, int sj, int a, int b) const { return (*this)(2 * si + a, 2 * sj + b); }
+};
+// one component of the u tile (two planes by column parity, as in uzawa_pair.cu)
+struct ULat {
+    static constexpr bool zero_filled = true;
+    const float2* p;
+    int pl, xh0, y0;
+    bool ycomp;
+    __device__ __forceinline__ float at(int si, int sj, int a, int b) const {
+        const float2 e = p[(a & 1) * pl + (2 * sj + b - y0) * RegTile::UWH + (si - xh0) + (a >> 1)];
+        return ycomp ? e.y : e.x;
+    }
+    __device__ __forceinline__ float operator()(int X, int Y) const {
+        const int dx = X - 2 * xh0;
+        const float2 e = p[(dx & 1) * pl + (Y - y0) * RegTile::UWH + (dx >> 1)];
+        return ycomp ? e.y : e.x;
+    }
+};
+
+// acc += (k / 2) v with a compile-time k in {0, +-1, +-2}
+template <int K>
+__device__ __forceinline__ void addk(float& acc, float v) {
+    if constexpr (K == 2) acc += v;
+    else if constexpr (K == -2) acc -= v;
+    else if constexpr (K == 1) acc = fmaf(0.5f, v, acc);
+    else if constexpr (K == -1) acc = fmaf(-0.5f, v, acc);
+}
+
+// ---- phase 1, fast path: A rows over the u window, B^T rows over the p window
+template <int C, int W>
+__device__ __forceinline__ void a_term(const float2 (&a)[kGroups], const float2* t0, const float2* t1, float2 (&au)[4],
+                                       float2 (&ctr)[4]) {
+    if constexpr (a_win(C, W)) {
+        constexpr int dx = W % 5 - 2, dy = W / 5 - 2;
+        constexpr int g0 = kGid[C][0][W], g1 = kGid[C][1][W], g2 = kGid[C][2][W], g3 = kGid[C][3][W];
+        const float2 w = ((dx & 1) ? t1 : t0)[dy * RegTile::UWH + (dx >> 1)];
+        if constexpr (g0 >= 0) au[0] = __ffma2_rn(a[g0], w, au[0]);
+        if constexpr (g1 >= 0) au[1] = __ffma2_rn(a[g1], w, au[1]);
+        if constexpr (g2 >= 0) au[2] = __ffma2_rn(a[g2], w, au[2]);
+        if constexpr (g3 >= 0) au[3] = __ffma2_rn(a[g3], w, au[3]);
+        if constexpr (W == 12) ctr[0] = w;
+        if constexpr (W == 13) ctr[1] = w;
+        if constexpr (W == 17) ctr[2] = w;
+        if constexpr (W == 18) ctr[3] = w;
+    }
+}
+template <int C, int... W>
+__device__ __forceinline__ void a_rows(const float2 (&a)[kGroups], const float2* t0, const float2* t1, float2 (&au)[4],
+                                       float2 (&ctr)[4], std::integer_sequence<int, W...>) {
+    (a_term<C, W>(a, t0, t1, au, ctr), ...);
+}
+// B^T rows of the H, E, C nodes (the V row is zero) over a 3 x 3 vertex window at sp[b], row pitch LD
+template <int C, int LD, int V>
+__device__ __forceinline__ void bt_term(const float* sp, float2 (&bt)[4]) {
+    if constexpr (bt_vwin(C, V)) {
+        const float v = sp[(V / 3 - 1) * LD + V % 3 - 1];
+        addk<kBTx[C][1][V]>(bt[1].x, v);
+        addk<kBTy[C][1][V]>(bt[1].y, v);
+        addk<kBTx[C][2][V]>(bt[2].x, v);
+        addk<kBTy[C][2][V]>(bt[2].y, v);
+        addk<kBTx[C][3][V]>(bt[3].x, v);
+        addk<kBTy[C][3][V]>(bt[3].y, v);
+    }
+}
+template <int C, int LD, int... V>
+__device__ __forceinline__ void bt_rows(const float* sp, float2 (&bt)[4], std::integer_sequence<int, V...>) {
+    (bt_term<C, LD, V>(sp, bt), ...);
+}
+// B row of a vertex over the u^{m-1/2} window: f0 points at the vertex's node in plane 0
+template <int C, int W>
+__device__ __forceinline__ void b_term(const float2* f0, int fpl, float& acc) {
+    if constexpr (kBx[C][W] != 0 || kBy[C][W] != 0) {
+        constexpr int dx = W % 5 - 2, dy = W / 5 - 2;
+        constexpr int plane = (dx & 1) + 2 * (dy & 1);
+        const float2 w = f0[plane * fpl + (dy >> 1) * RegTile::FW + (dx >> 1)];
+        addk<kBx[C][W]>(acc, w.x);
+        addk<kBy[C][W]>(acc, w.y);
+    }
+}
+template <int C, int... W>
+__device__ __forceinline__ float b_row(const float2* f0, int fpl, std::integer_sequence<int, W...>) {
+    float acc = 0.f;
+    (b_term<C, W>(f0, fpl, acc), ...);
+    return acc;
+}
+
+template <int C>
+__device__ __forceinline__ void load_coef(const RegCoef& q, float2 (&a)[kGroups]) {
+#pragma unroll
+    for (int g = 0; g < kGroups; ++g) {
+        a[g] = q.a[C][g];
+        // keep the values in registers (the compiler may not rematerialise them from the constant bank)
+        asm("" : "+f"(a[g].x), "+f"(a[g].y));
+    }
+}
+
+template <int C, bool INNER>
+__device__ __forceinline__ void phase1_fast(const RegCoef& q, const float2* sU, int UPL, const float* sP, float2* sF,
+                                           int FPL, int TY, int NW, int warp, int lane, int i0, int j0, int n) {
+    float2 a[kGroups];
+    load_coef<C>(q, a);
+    const float ti0 = q.ti[C][0], ti1 = q.ti[C][1];
+    const float2 mb = f2(-q.b, -q.b);
+    for (int r = warp; r < TY + 4; r += NW) {
+        const float2* t0 = sU + 2 * (r + 1) * RegTile::UWH + lane + 1;
+        const float2* t1 = t0 + UPL;
+        float2 au[4], ctr[4], bt[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) au[s] = ctr[s] = bt[s] = f2(0.f, 0.f);
+        a_rows<C>(a, t0, t1, au, ctr, std::make_integer_sequence<int, 25>{});
+        bt_rows<C, RegTile::PW>(sP + (r + 1) * RegTile::PW + lane + 1, bt, std::make_integer_sequence<int, 9>{});
+        // only unknowns keep their value (interior tiles hold nothing else)
+        bool unk[4] = {true, true, true, true};
+        if constexpr (!INNER) {
+            const int ci = i0 - 2 + lane, cj = j0 - 2 + r;
+            const bool ci_in = ci > 0 && ci < n, cj_in = cj > 0 && cj < n;
+            const bool ci_h = ci >= 0 && ci < n, cj_h = cj >= 0 && cj < n;
+            unk[0] = ci_in && cj_in;
+            unk[1] = ci_h && cj_in;
+            unk[2] = ci_in && cj_h;
+            unk[3] = ci_h && cj_h;
+        }
+        float2* fr = sF + r * RegTile::FW + lane;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const float2 fs = fr[s * FPL];
+            const float ti = s == 0 ? ti0 : ti1;
+            // u^{m-1/2} = u + ti (f - A u - b (B^T p / b)); the V row of B^T is zero
+            float2 t = f2(fs.x - au[s].x, fs.y - au[s].y);
+            if (s > 0) t = __ffma2_rn(mb, bt[s], t);
+            const float2 h = __ffma2_rn(f2(ti, ti), t, ctr[s]);
+            if constexpr (INNER) fr[s * FPL] = h;
+            else fr[s * FPL] = unk[s] ? h : f2(0.f, 0.f);
+        }
+    }
+}
+
+template <int C>
+__device__ __forceinline__ void phase2_fast(const RegCoef& q, const float2* sF, int FPL, float* sG, const float* sS,
+                                            float sigma, int TY, int NW, int warp, int lane) {
+    const float b = q.b;
+    for (int r = warp; r < TY + 2; r += NW) {
+        if (lane >= RegTile::DW) break;
+        const float2* f0 = sF + (r + 1) * RegTile::FW + lane + 1;
+        const float acc = b_row<C>(f0, FPL, std::make_integer_sequence<int, 25>{});
+        const int k = r * RegTile::DW + lane;
+        // Shat^{-1} is zero-filled off the domain, so dp = 0 there
+        sG[k] = sigma * sS[k] * fmaf(b, acc, -sG[k]);
+    }
+}
+
+template <int C, bool INNER>
+__device__ __forceinline__ void phase3_fast(const RegCoef& q, const float2* sF, int FPL, const float* sG,
+                                            const float* sP, int TY, int NW, int warp, int lane, int i0, int j0,
+                                            int n, float* __restrict__ u_out, float* __restrict__ p_out) {
+    const float nb1 = -q.ti[C][1] * q.b;
+    const int ld = 2 * n + 1, n2 = ld * ld;
+    for (int r = warp; r < TY; r += NW) {
+        if (lane >= RegTile::TX) break;
+        const int ci = i0 + lane, cj = j0 + r;
+        if (!INNER && (ci > n || cj > n)) continue;
+        float2 bt[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) bt[s] = f2(0.f, 0.f);
+        bt_rows<C, RegTile::DW>(sG + (r + 1) * RegTile::DW + lane + 1, bt, std::make_integer_sequence<int, 9>{});
+        const float2* hr = sF + (r + 2) * RegTile::FW + lane + 2;
+        float2 o[4];
+        o[0] = hr[0];
+#pragma unroll
+        for (int s = 1; s < 4; ++s) o[s] = __ffma2_rn(f2(nb1, nb1), bt[s], hr[s * FPL]);
+        if constexpr (INNER) {
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                const int k = (2 * cj + (s >> 1)) * ld + 2 * ci + (s & 1);
+                u_out[k] = o[s].x;
+                u_out[n2 + k] = o[s].y;
+            }
+        } else {
+            const CellNodes cn = cell_nodes(ci, cj, n);
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                if (!slot_exists(cn, s)) continue;
+                const int k = (2 * cj + (s >> 1)) * ld + 2 * ci + (s & 1);
+                const bool uk = slot_unknown(cn, s);
+                u_out[k] = uk ? o[s].x : 0.f;
+                u_out[n2 + k] = uk ? o[s].y : 0.f;
+            }
+        }
+        p_out[cj * (n + 1) + ci] = sP[(r + 3) * RegTile::PW + lane + 3] + sG[(r + 1) * RegTile::DW + lane + 1];
+    }
+}
+
+template <int NW, int MINB>
+__global__ void __launch_bounds__(32 * NW, MINB)
+    k_uzawa_reg(int n, int TY, TileOrder ord, const __grid_constant__ OpCoef<float> c, const __grid_constant__ RegCoef q,
+                float tau, float sigma, const float* __restrict__ u, const float* __restrict__ p,
+                const float* __restrict__ f, const float* __restrict__ g, const float* __restrict__ sinv,
+                float* __restrict__ u_out, float* __restrict__ p_out) {
+    pdl_wait();
+    using G = RegTile;
+    constexpr int TX = G::TX;
+    const int UPL = G::upl(TY), FPL = G::fpl(TY), DSZ = G::dsz(TY);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* sU = reinterpret_cast<float2*>(smem_raw);
+    float2* sF = sU + 2 * UPL;
+    float* sP = reinterpret_cast<float*>(sF + 4 * FPL);
+    float* sG = sP + G::PW * (TY + 6);
+    float* sS = sG + DSZ;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int tc, tr;
+    ord.tile(blockIdx.x, tc, tr);
+    const int i0 = tc * TX, j0 = tr * TY;
+    const int ld = 2 * n + 1, n2 = ld * ld, h = n >> 1;
+    const bool fast = (h < i0 - 2 || h >= i0 + TX + 2) && (h < j0 - 2 || h >= j0 + TY + 2);
+    const bool inner = fast && i0 >= 4 && j0 >= 4 && i0 + TX + 3 <= n && j0 + TY + 3 <= n;
+    const int cls = orient(i0, j0, n);
+
+    // ---- asynchronous staging.  Lane l copies component l >> 4 of lattice point 16 q + (l & 15) of a row:
+    // one instruction moves 16 consecutive points with both components (two 64-byte global segments,
+    // 32 distinct shared banks).  Interior tiles copy without any test, at fixed offsets from one
+    // address per row; the others zero-fill what lies off the domain (u also on its boundary).
+    {
+        const int cx = lane >> 4, px = lane & 15;
+        // u: lattice columns X0 + x, x in [0, 68), rows Y0 + y, y in [0, 2 (TY + 6)); column x goes to plane
+        // x & 1, plane column x >> 1
+        const int X0 = 2 * (i0 - 3), Y0 = 2 * (j0 - 3);
+        float* du = reinterpret_cast<float*>(sU + (px & 1) * UPL + (px >> 1)) + cx;
+        const float* gu = u + cx * n2 + X0 + px;
+        for (int y = warp; y < 2 * (TY + 6); y += NW) {
+            const int Y = Y0 + y;
+            float* d = du + 2 * y * G::UWH;
+            if (inner) {
+                const float* src = gu + Y * ld;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) cp4(d + 16 * t, src + 16 * t, true);
+                if (px < 4) cp4(d + 64, src + 64, true);
+            } else {
+#pragma unroll
+                for (int t = 0; t < 5; ++t) {
+                    if (t == 4 && px >= 4) break;
+                    const bool ok = interior2(X0 + px + 16 * t, Y, n);
+                    cp4(d + 16 * t, ok ? gu + Y * ld + 16 * t : u, ok);
+                }
+            }
+        }
+        // f: the u^{m-1/2} region, lattice columns XF + x, x in [0, 64), rows YF + y; node type
+        // (x & 1) + 2 (y & 1), cell (x >> 1, y >> 1)
+        const int XF = 2 * (i0 - 2), YF = 2 * (j0 - 2);
+        float* dfb = reinterpret_cast<float*>(sF + (px & 1) * FPL + (px >> 1)) + cx;
+        const float* gf = f + cx * n2 + XF + px;
+        for (int y = warp; y < 2 * (TY + 4); y += NW) {
+            const int Y = YF + y;
+            float* d = dfb + 2 * ((y & 1) * 2 * FPL + (y >> 1) * G::FW);
+            if (inner) {
+                const float* src = gf + Y * ld;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) cp4(d + 16 * t, src + 16 * t, true);
+            } else {
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int X = XF + px + 16 * t;
+                    const bool ok = X >= 0 && Y >= 0 && X <= 2 * n && Y <= 2 * n;
+                    cp4(d + 16 * t, ok ? gf + Y * ld + 16 * t : f, ok);
+                }
+            }
+        }
+        // p: vertices (i0 - 3 + x, j0 - 3 + y), x in [0, 34)
+        for (int y = warp; y < TY + 6; y += NW) {
+            const int J = j0 - 3 + y;
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                if (t == 1 && lane >= 2) break;
+                const int x = lane + 32 * t, I = i0 - 3 + x;
+                const bool ok = inner || (I >= 0 && J >= 0 && I <= n && J <= n);
+                cp4(sP + y * G::PW + x, ok ? p + J * (n + 1) + I : p, ok);
+            }
+        }
+        // g, Shat^{-1}: vertices (i0 - 1 + x, j0 - 1 + y), x in [0, 30)
+        for (int y = warp; y < TY + 2; y += NW) {
+            if (lane >= G::DW) break;
+            const int J = j0 - 1 + y, I = i0 - 1 + lane;
+            const bool ok = inner || (I >= 0 && J >= 0 && I <= n && J <= n);
+            const int k = ok ? J * (n + 1) + I : 0;
+            cp4(sG + y * G::DW + lane, g + k, ok);
+            cp4(sS + y * G::DW + lane, sinv + k, ok);
+        }
+        cp_commit_wait();
+    }
+    __syncthreads();
+
+    const ULat vux{sU, UPL, i0 - 3, 2 * (j0 - 3), false};
+    const ULat vuy{sU, UPL, i0 - 3, 2 * (j0 - 3), true};
+    const SVert<float, G::PW> vp{sP, i0 - 3, j0 - 3};
+    const QuadLat vhx{sF, FPL, i0 - 2, j0 - 2, false};
+    const QuadLat vhy{sF, FPL, i0 - 2, j0 - 2, true};
+
+    // ---- u^{m-1/2} on cells (i0 - 2 + lane, j0 - 2 + r), written over f
+    if (fast) {
+        if (inner) {
+            if (cls == 0) phase1_fast<0, true>(q, sU, UPL, sP, sF, FPL, TY, NW, warp, lane, i0, j0, n);
+            else phase1_fast<1, true>(q, sU, UPL, sP, sF, FPL, TY, NW, warp, lane, i0, j0, n);
+        } else {
+            if (cls == 0) phase1_fast<0, false>(q, sU, UPL, sP, sF, FPL, TY, NW, warp, lane, i0, j0, n);
+            else phase1_fast<1, false>(q, sU, UPL, sP, sF, FPL, TY, NW, warp, lane, i0, j0, n);
+        }
+    } else {
+        for (int r = warp; r < TY + 4; r += NW) {
+            const int ci = i0 - 2 + lane, cj = j0 - 2 + r;
+            float2 hv[4];
+#pragma unroll
+            for (int s = 0; s < 4; ++s) hv[s] = f2(0.f, 0.f);
+            float2* fr = sF + r * G::FW + lane;
+            if (ci >= 0 && cj >= 0 && ci <= n && cj <= n) {
+                Acc<float> a;
+                cell_apply_auto<true, true, false, true, false>(ci, cj, n, c, vux, vuy, vp, a);
+                const CellNodes cn = cell_nodes(ci, cj, n);
+#pragma unroll
+                for (int s = 0; s < 4; ++s) {
+                    if (!slot_unknown(cn, s)) continue;
+                    const float2 fs = fr[s * FPL];
+                    const float w = tau * a.idg[s];
+                    hv[s] = f2(vux.at(ci, cj, s & 1, s >> 1) + w * (fs.x - a.au[0][s] - a.bt[0][s]),
+                               vuy.at(ci, cj, s & 1, s >> 1) + w * (fs.y - a.au[1][s] - a.bt[1][s]));
+                }
+            }
+#pragma unroll
+            for (int s = 0; s < 4; ++s) fr[s * FPL] = hv[s];
+        }
+    }
+    __syncthreads();
+
+    // ---- dp on vertices (i0 - 1 + lane, j0 - 1 + r), written over g
+    if (fast) {
+        if (cls == 0) phase2_fast<0>(q, sF, FPL, sG, sS, sigma, TY, NW, warp, lane);
+        else phase2_fast<1>(q, sF, FPL, sG, sS, sigma, TY, NW, warp, lane);
+    } else {
+        for (int r = warp; r < TY + 2; r += NW) {
+            if (lane >= G::DW) break;
+            const int vi = i0 - 1 + lane, vj = j0 - 1 + r;
+            float d = 0.f;
+            if (vi >= 0 && vj >= 0 && vi <= n && vj <= n) {
+                Acc<float> a;
+                cell_apply_auto<false, false, true, false, false>(vi, vj, n, c, vhx, vhy, vp, a);
+                const int k = r * G::DW + lane;
+                d = sigma * sS[k] * (a.bu - sG[k]);
+            }
+            sG[r * G::DW + lane] = d;
+        }
+    }
+    __syncthreads();
+
+    // ---- new (u, p) on the owned cells (i0 + lane, j0 + r)
+    if (fast) {
+        if (inner) {
+            if (cls == 0) phase3_fast<0, true>(q, sF, FPL, sG, sP, TY, NW, warp, lane, i0, j0, n, u_out, p_out);
+            else phase3_fast<1, true>(q, sF, FPL, sG, sP, TY, NW, warp, lane, i0, j0, n, u_out, p_out);
+        } else {
+            if (cls == 0) phase3_fast<0, false>(q, sF, FPL, sG, sP, TY, NW, warp, lane, i0, j0, n, u_out, p_out);
+            else phase3_fast<1, false>(q, sF, FPL, sG, sP, TY, NW, warp, lane, i0, j0, n, u_out, p_out);
+        }
+    } else {
+        const SVert<float, G::DW> vd{sG, i0 - 1, j0 - 1};
+        for (int r = warp; r < TY; r += NW) {
+            if (lane >= TX) break;
+            const int ci = i0 + lane, cj = j0 + r;
+            if (ci > n || cj > n) continue;
+            Acc<float> a;
+            cell_apply_auto<false, true, false, true, false>(ci, cj, n, c, vhx, vhy, vd, a);
+            const CellNodes cn = cell_nodes(ci, cj, n);
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                if (!slot_exists(cn, s)) continue;
+                const int k = (2 * cj + (s >> 1)) * ld + 2 * ci + (s & 1);
+                float ox = 0.f, oy = 0.f;
+                if (slot_unknown(cn, s)) {
+                    const float w = tau * a.idg[s];
+                    ox = vhx.at(ci, cj, s & 1, s >> 1) - w * a.bt[0][s];
+                    oy = vhy.at(ci, cj, s & 1, s >> 1) - w * a.bt[1][s];
+                }
+                u_out[k] = ox;
+                u_out[n2 + k] = oy;
+            }
+            p_out[cj * (n + 1) + ci] = sP[(r + 3) * G::PW + lane + 3] + sG[(r + 1) * G::DW + lane + 1];
+        }
+    }
+    pdl_trigger();
+}
+
+template <int NW, int MINB>
+cudaError_t reg_smem_attr() {
+    return cudaFuncSetAttribute(k_uzawa_reg<NW, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)RegTile::bytes(kRegMaxRows));
+}
+
+// Rows per tile for level size n: the least work on the busiest SM, (tiles per SM, rounded up) x
+// (work of one tile, about ty + 4 rows of the u^{m-1/2} region), among the tile heights that keep
+// at least MINB CTAs resident per SM.
+template <int NW, int MINB>
+int reg_rows(int n) {
+    static int cache[32] = {};
+    const int lv = 31 - __builtin_clz((unsigned)n);
+    int& r = cache[lv & 31];
+    if (r) return r;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    sms = std::max(sms, 1);
+    const int cols = (n + 1 + RegTile::TX - 1) / RegTile::TX;
+    double best = 1e300;
+    int best_ty = 12;
+    for (int ty = 4; ty <= kRegMaxRows; ++ty) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_uzawa_reg<NW, MINB>, 32 * NW,
+                                                          RegTile::bytes(ty)) != cudaSuccess || per_sm < MINB)
+            continue;
+        const long tiles = (long)cols * ((n + 1 + ty - 1) / ty);
+        const double cost = (double)((tiles + sms - 1) / sms) * (ty + 4);
+        if (cost < best) {
+            best = cost;
+            best_ty = ty;
+        }
+    }
+    cudaGetLastError();
+    r = best_ty;
+    return r;
+}
+
+template <int NW, int MINB>
+bool launch_reg_v(cudaStream_t s, int n, const OpCoef<float>& c, float tau, float sigma, const float* u, const float* p,
+                  const float* f, const float* g, const float* sinv, float* u_out, float* p_out) {
+    RegCoef q;
+    if (!make_reg_coef(c, tau, q)) return false;
+    const int ty = reg_rows<NW, MINB>(n);
+    TileOrder ord;
+    ord.cols = (n + 1 + RegTile::TX - 1) / RegTile::TX;
+    ord.rows = (n + 1 + ty - 1) / ty;
+    mid_band(n / 2, RegTile::TX, ord.cols, ord.c0, ord.nc);
+    mid_band(n / 2, ty, ord.rows, ord.r0, ord.nr);
+    launch_pdl(k_uzawa_reg<NW, MINB>, dim3(ord.cols * ord.rows), dim3(32 * NW), RegTile::bytes(ty), s, n, ty, ord, c, q, tau,
+               sigma, u, p, f, g, sinv, u_out, p_out);
+    return true;
+}
+
+}  // namespace
+
+cudaError_t prepare_uzawa_reg() {
+    cudaError_t e = reg_smem_attr<8, 2>();
+    if (e == cudaSuccess) e = reg_smem_attr<8, 4>();
+    return e;
+}
+
+bool launch_uzawa_reg(int variant, cudaStream_t s, int n, const OpCoef<float>& c, float tau, float sigma,
+                      const float* u, const float* p, const float* f, const float* g, const float* sinv,
+                      float* u_out, float* p_out) {
+    if (variant == 0) return launch_reg_v<8, 2>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
+    return launch_reg_v<8, 4>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
+}
+
+}  // namespace smg

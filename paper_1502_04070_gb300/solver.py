@@ -229,7 +229,7 @@ class Solver:
 def step_variant(levels):
     """Float32 Uzawa step variant used for levels with N = 2^levels (0-3 fused tiles 32x16, 32x8,
     64x8, 16x16; 4-6 three-kernel step with blocks 32x8, 16x8, 8x8; 7-9 fused step on
-    component-pair tiles, 28 cells wide)."""
+    component-pair tiles, 28 cells wide; 10-11 fused step with the coefficients in registers)."""
     return int(B.load().stokes_step_variant(int(levels)))
 
 

@@ -72,7 +72,7 @@ def test_step_variant_selection_without_gpu():
     lib = _binding.load()
     assert lib.stokes_set_step_variant(1, 0) == _binding.ERR_BAD_ARG
     assert lib.stokes_set_step_variant(32, 0) == _binding.ERR_BAD_ARG
-    assert lib.stokes_set_step_variant(5, 10) == _binding.ERR_BAD_ARG
+    assert lib.stokes_set_step_variant(5, 12) == _binding.ERR_BAD_ARG
     assert lib.stokes_set_step_variant(5, -1) == _binding.ERR_BAD_ARG
     assert lib.stokes_step_variant(1) == -1
     old = lib.stokes_step_variant(5)

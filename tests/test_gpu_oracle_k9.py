@@ -51,8 +51,9 @@ def test_k9_mixed_solve_residual_by_oracle(level):
 
 
 def _variants():
-    # the pair tiles and the three-kernel step (the autotuner's candidates that win at k >= 8)
-    return [4, 7, 8]
+    # the three-kernel step, the pair tiles and the register-coefficient tiles (the autotuner's
+    # candidates that win at k >= 8)
+    return [4, 7, 8, 10, 11]
 
 
 @pytest.mark.parametrize("variant", [None] + _variants())

@@ -204,10 +204,11 @@ def test_smoother_float32_fused(discs, Solver, k, beta, nu):
 
 
 @pytest.mark.parametrize("k", [3, 5, 6])
-@pytest.mark.parametrize("variant", range(10))
+@pytest.mark.parametrize("variant", range(12))
 def test_smoother_float32_every_variant(discs, Solver, k, variant):
     """Every float32 step variant the autotuner may choose (four fused tile shapes, the three-kernel
-    step with three block shapes, the component-pair tiles in three shapes) gives the oracle's three
+    step with three block shapes, the component-pair tiles in three shapes, the register-coefficient
+    tiles in two) gives the oracle's three
     Uzawa steps at a size whose cells do not fill the last tile or block (N + 1 = 2^(k+1) + 1 per
     side); at k = 6 the pair tiles take both their interior and their general path.  Bound as
     above (2e-5)."""

@@ -126,6 +126,19 @@ def test_table_entry_points_reject_bad_arguments(lib):
     assert lib.stokes_stencil_rows(3, 1.0, 0, None, p, p, p, p, p) != 0
 
 
+@pytest.mark.parametrize("levels", range(1, 14))
+def test_register_tile_structure_holds_on_every_level(lib, levels):
+    """The register-coefficient Uzawa tiles (step variants 10-11) hard-code which coefficients of the
+    merged stencils of the two orientation classes vanish, which are equal (eight values for the
+    42 nonzero A terms of a cell), and that every B and B^T entry is +-b or +-b/2.  The host check of
+    that structure against the stencils the library builds (the rows pinned to the oracle's
+    assembled matrices above) passes for every level and for beta from 0 to 1e12."""
+    for beta in (0.0, 1e-3, 1.0, 37.0, 1e4, 1e8, 1e12):
+        assert lib.stokes_step_tables_match(levels, beta) == 0, (levels, beta)
+    assert lib.stokes_step_tables_match(0, 1.0) != 0
+    assert lib.stokes_step_tables_match(3, -1.0) != 0
+
+
 @pytest.mark.parametrize("k", [1, 2, 3])
 def test_transfer_weights_equal_the_oracle_embedding(lib, discs, k):
     """The embedding weights the transfer kernels apply (stokes_transfer_weights) equal the oracle's
