@@ -71,20 +71,25 @@ class Params:
 
 
 class Hierarchy:
-    """All levels k = 0 .. levels-1 with their matrices, diagonals and transfers."""
+    """All levels k = 0 .. levels-1 with their matrices, diagonals and transfers.  The multigrid
+    iteration descends to `coarse_level` (default 0, the coarse mesh of Sec. 6), where the coarse
+    problem is solved exactly (Sec. 3); the levels below it are not used."""
 
-    def __init__(self, levels: int, beta: float, discs=None):
+    def __init__(self, levels: int, beta: float, discs=None, coarse_level: int = 0):
         self.discs = discs if discs is not None else fem.discretizations(levels)
         self.levels = [Level(d, beta) for d in self.discs]
         for l in range(1, len(self.levels)):
             self.levels[l].P = transfer.prolongation(self.discs[l - 1], self.discs[l])
         self.beta = beta
-        d0 = self.discs[0]
-        S0 = self.levels[0].S.toarray()
-        n = S0.shape[0]
-        w = np.concatenate([np.zeros(d0.nu), d0.w])
+        if not 0 <= coarse_level < len(self.levels):
+            raise ValueError("coarse_level must lie in 0 .. levels - 1")
+        self.coarse_level = coarse_level
+        dc = self.discs[coarse_level]
+        Sc = self.levels[coarse_level].S.toarray()
+        n = Sc.shape[0]
+        w = np.concatenate([np.zeros(dc.nu), dc.w])
         border = np.zeros((n + 1, n + 1))
-        border[:n, :n] = S0
+        border[:n, :n] = Sc
         border[:n, n] = w
         border[n, :n] = w
         self.coarse_bordered = border
@@ -119,14 +124,15 @@ class Hierarchy:
 
     # ------------------------------------------------------------------ coarse solve
     def coarse_solve(self, F0):
-        """Exact solve on level 0 (Sec. 3): the bordered system fixes w^T p = 0."""
+        """Exact solve on the coarsest level of the iteration (Sec. 3): the bordered system fixes
+        w^T p = 0."""
         rhs = np.concatenate([F0, [0.0]])
         return np.linalg.solve(self.coarse_bordered, rhs)[:-1]
 
     # ------------------------------------------------------------------ cycle
     def cycle(self, l: int, x, F, prm: Params):
         """One multigrid iteration on level l (Sec. 3)."""
-        if l == 0:
+        if l == self.coarse_level:
             return self.coarse_solve(F)
         lvl = self.levels[l]
         for _ in range(prm.nu_pre):

@@ -83,6 +83,70 @@ def test_two_grid_exact_coarse(discs):
     assert np.abs(got - ref).max() < 1e-11 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("c", [1, 2])
+def test_coarse_level_is_an_exact_two_grid_solve(discs, c):
+    """With the coarsest level of the iteration at c = k - 1 (Sec. 3: the coarse problem is solved
+    exactly), one cycle is smoothing plus the exact coarse correction with A_c^{-1} taken from the
+    sparse direct solver of the bordered level-c system."""
+    k = c + 1
+    H = mg.Hierarchy(k + 1, 3.0, discs[:k + 1], coarse_level=c)
+    F = _rhs(H.discs[k], 5)
+    prm = mg.Params(nu_pre=2, nu_post=0)
+    x = np.zeros_like(F)
+    for _ in range(2):
+        x = H.uzawa_step(H.finest, x, F, prm)
+    rc = H.finest.P.T @ (F - H.finest.S @ x)
+    ref = x + H.finest.P @ mg.direct_solve(H.levels[c].S, H.discs[c], rc)
+    got = H.cycle(k, np.zeros_like(F), F, prm)
+    assert np.abs(got - ref).max() < 1e-11 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("beta", [0.0, 1e4])
+def test_w_cycle_with_finer_coarse_level_converges_to_direct_solution(discs, beta):
+    """A W-cycle that stops at level 2 (an exact solve there) converges to the exact discrete
+    solution, like the one that descends to level 0."""
+    H = mg.Hierarchy(5, beta, discs, coarse_level=2)
+    d = H.discs[-1]
+    F = _rhs(d, 6)
+    xd = H.direct(F)
+    x, hist = H.solve(F, mg.Params(gamma=2), tol=1e-11, max_cycles=80)
+    assert hist[-1] <= 1e-11 * np.linalg.norm(F)
+    assert np.abs(x - xd).max() <= 1e-8 * np.abs(xd).max()
+    with pytest.raises(ValueError):
+        mg.Hierarchy(3, beta, discs[:3], coarse_level=3)
+
+
+def _contraction_estimate(H, k, gamma, its=25, seed=0):
+    """Power iteration on the cycle's error propagation (F = 0, zero-mean pressure kept): the
+    last ratio ||x_{m+1}|| / ||x_m|| estimates its spectral radius."""
+    rng = np.random.default_rng(seed)
+    x = H.project_mean(k, rng.uniform(-1, 1, H.discs[k].ndof))
+    x /= np.linalg.norm(x)
+    F = np.zeros_like(x)
+    for _ in range(its):
+        y = H.project_mean(k, H.cycle(k, x, F, mg.Params(gamma=gamma)))
+        q = np.linalg.norm(y)
+        x = y / q
+    return q
+
+
+def test_w_cycle_contraction_is_h_robust_and_the_v_cycle_is_not():
+    """Sec. 3 proves h- and beta-independent convergence of the W-cycle (Sec. 6 runs W; it calls the
+    V-cycle comparable).  On this mesh (beta = 0, Uzawa 3+3) the W-cycle's contraction levels off
+    (0.380, 0.394, 0.394 at k = 5, 6, 7) while the V-cycle's grows (0.378, 0.394, then 0.55 at k = 7),
+    which is why the V-cycle needs 68 cycles at h = 1/512 and 34 at h = 1/2048 in the benchmark."""
+    ds = fem.discretizations(8)
+    qw, qv = {}, {}
+    for k in (5, 6, 7):
+        H = mg.Hierarchy(k + 1, 0.0, ds[:k + 1])
+        qw[k] = _contraction_estimate(H, k, 2)
+        if k in (5, 7):
+            qv[k] = _contraction_estimate(H, k, 1)
+    assert all(0.3 < q < 0.42 for q in qw.values()), qw
+    assert max(qw.values()) - min(qw.values()) < 0.03, qw
+    assert qv[5] < 0.42 and qv[7] > 0.5, qv
+
+
 def test_manufactured_convergence_orders():
     """Taylor-Hood P2-P1 (Sec. 2): ||u-u_h||_L2 ~ h^3, |u-u_h|_H1 ~ h^2, ||p-p_h||_L2 ~ h^2.
     The weak form of Sec. 2 carries +(p, div v), i.e. the discrete p approximates -p of the strong
