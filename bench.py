@@ -4,15 +4,16 @@
 Headline workload (one "step"): one solve of the manufactured problem at h = 1/2048 (level k = 10,
 37,736,451 unknowns), beta = 1e4, u = curl(sin^2(pi x) sin^2(pi y)), p = cos(pi x) cos(pi y),
 from zero to 1e-8 relative residual (float64) with float32 V(3,3) Uzawa cycles (Sec. 4,
-tau = sigma = 0.8) inside float64 iterative refinement and a float64 coarse solve; the same solve
-with plain float64 multigrid is timed beside it (the speed-up at equal accuracy) and the two
-solutions are compared.
+tau = sigma = 0.8) inside float64 iterative refinement, the coarsest level of the iteration at
+h = 1/16 (level 3) solved exactly by a dense float64 inverse; the same solve with plain float64
+multigrid is timed beside it (the speed-up at equal accuracy) and the two solutions are compared.
 
 Also measured, as parsed keys of the same line:
   sweep     -- the robustness sweep at h = 1/512 (k = 8), six beta in {0, 1, 1e2, 1e4, 1e6, 1e8},
                f, g uniform[-1, 1] nodal (seed 1), six solves in one CUDA-graph launch, V and W
                cycles, cycles per beta beside the oracle's;
-  levels    -- cycles to 1e-8 of the manufactured problem on k = 4..10 for V and W (h-robustness);
+  levels    -- cycles to 1e-8 of the manufactured problem on k = 4..10 for V and W cycles
+               (h-robustness), beside the oracle's counts;
   batch     -- 256 independent solves, k uniform in 4..8, beta log-uniform in [1e-2, 1e8], one launch;
   small     -- h = 1/32 (k = 4), beta = 1, plain float64 V(3,3) to 1e-10: time per solve;
   adjoint   -- h = 1/1024 (k = 9), beta = 1e3, L = 1/2 ||u - u_target||_M^2: forward + backward.
@@ -41,10 +42,10 @@ TOL = 1e-8
 METRIC = "DoF/s to 1e-8 relative residual (h=1/2048 manufactured solution, mixed precision vs plain FP64 multigrid)"
 
 
-def workload_text(cycle):
+def workload_text(cycle, coarse_level):
     return ("manufactured solution u=curl(sin^2(pi x) sin^2(pi y)), p=cos(pi x) cos(pi y): unit square, "
             "Taylor-Hood P2-P1, h=1/2048 (k=10, 37736451 DoF), beta=1e4, %s(3,3) Uzawa cycles tau=sigma=0.8, "
-            "solve from 0 to 1e-8 relative residual" % cycle)
+            "coarsest level %d solved exactly, solve from 0 to 1e-8 relative residual" % (cycle, coarse_level))
 
 
 def parse():
@@ -54,12 +55,15 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cycle", default="V", choices=["V", "W"], help="cycle of the headline solve")
+    ap.add_argument("--head-coarse-level", type=int, default=3, help="coarsest level of the headline solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=2, help="solves of the plain float64 comparison")
     ap.add_argument("--only-head", action="store_true", help="skip the parsed secondary workloads")
     ap.add_argument("--kernel", default=None, choices=["uzawa_f32", "uzawa_f64", "residual_f64", "mixed_solve", "ir_steps"],
                     help="microbenchmark one kernel (for profiler captures) instead of the workload")
     ap.add_argument("--level", type=int, default=9)
+    ap.add_argument("--gamma", type=int, default=1, help="kernel modes: 1 = V-cycle, 2 = W-cycle")
+    ap.add_argument("--coarse-level", type=int, default=0, help="kernel modes: coarsest level of the iteration")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--host-loop", action="store_true",
@@ -85,7 +89,7 @@ def run_kernel(args):
     f, g = workloads.random_nodal(k, 6)
     g = g - g.mean()
     prec = "mixed" if args.kernel in ("uzawa_f32", "mixed_solve", "ir_steps") else "fp64"
-    S = Solver(k + 1, 1e4, precision=prec)
+    S = Solver(k + 1, 1e4, precision=prec, gamma=args.gamma, coarse_level=args.coarse_level)
     if args.variant is not None or args.variants:
         from paper_1502_04070_gb300.solver import set_step_variant
         if args.variant is not None:
@@ -154,23 +158,23 @@ def golden_cycles():
     return {r["beta"]: r["cycles"] for r in _golden("sweep_k8.json")["k8_sweep"]["runs"]}
 
 
-def oracle_sweep_cycles(gamma):
+def oracle_sweep_cycles(gamma, coarse_level=0):
     """The oracle's cycle counts to 1e-8 per beta of the sweep (the written golden values, no oracle
     call), keyed like cycles_per_beta; None if the file is missing."""
     try:
         if gamma == 1:
             return {str(float(b)): c for b, c in golden_cycles().items()}
-        runs = _golden("manufactured_k8.json")["k8_sweep_w"]["runs"]
+        runs = _golden("manufactured_k8.json")["k8_sweep_w_c3" if coarse_level == 3 else "k8_sweep_w"]["runs"]
         return {str(float(r["beta"])): r["cycles"] for r in runs}
     except (OSError, KeyError, TypeError, ValueError):
         return None
 
 
-def oracle_manufactured_cycles(k, gamma):
+def oracle_manufactured_cycles(k, gamma, coarse_level=0):
     """The oracle's cycles to 1e-8 on the manufactured problem (beta = 1e4) at level k, or None."""
     try:
         for r in _golden("manufactured_k8.json")["manufactured"]["runs"]:
-            if r["k"] == k and r["gamma"] == gamma:
+            if r["k"] == k and r["gamma"] == gamma and r.get("coarse_level", 0) == coarse_level:
                 return r["cycles"]
     except (OSError, KeyError, TypeError, ValueError):
         pass
@@ -178,7 +182,7 @@ def oracle_manufactured_cycles(k, gamma):
 
 
 # ------------------------------------------------------------------------------ CPU oracle
-def oracle_sample(n_cycles, gamma, warmup=0):
+def oracle_sample(n_cycles, gamma, warmup=0, coarse_level=0):
     """Times the oracle (CPU float64 SciPy, as it stands) on a bounded sample of the headline's
     problem class: the manufactured problem with beta = 1e4 at k = 8, the largest level the oracle
     assembles in seconds; n_cycles cycles from zero.  Returns the per-cycle times, the assembly time
@@ -194,7 +198,7 @@ def oracle_sample(n_cycles, gamma, warmup=0):
     ds = fem.discretizations(k + 1)
     fn, gn = workloads.manufactured_nodal(k, BETA_HEAD)
     F = ds[-1].load(fn, gn, project_g=True)
-    H = mg.Hierarchy(k + 1, BETA_HEAD, ds)
+    H = mg.Hierarchy(k + 1, BETA_HEAD, ds, coarse_level=coarse_level)
     setup = time.perf_counter() - t0
     prm = mg.Params(gamma=gamma)
     x = np.zeros_like(F)
@@ -205,7 +209,10 @@ def oracle_sample(n_cycles, gamma, warmup=0):
         t = time.perf_counter()
         x = H.project_mean(k, H.cycle(k, x, F, prm))
         times.append(time.perf_counter() - t)
-    return times, setup, oracle_manufactured_cycles(k, gamma)
+    cyc = oracle_manufactured_cycles(k, gamma, coarse_level)
+    if cyc is None:
+        cyc = oracle_manufactured_cycles(k, gamma)
+    return times, setup, cyc
 
 
 def oracle_rate(times, cycles):
@@ -217,7 +224,8 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     gamma = 2 if getattr(args, "cycle", "V") == "W" else 1
-    times, setup, cyc = oracle_sample(args.steps, gamma, warmup=args.warmup)
+    cl = getattr(args, "head_coarse_level", 3)
+    times, setup, cyc = oracle_sample(args.steps, gamma, warmup=args.warmup, coarse_level=cl)
     value = oracle_rate(times, cyc)
     sample = ("%d oracle %s(3,3) cycles (one per step) of the same problem class at k=8 (h=1/512, 2356227 DoF, "
               "the largest level the oracle assembles in seconds; beta=1e4, manufactured), rate = DoF / (mean "
@@ -227,7 +235,7 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": workload_text("VW"[gamma - 1])},
+            "data": "synthetic", "config": {"workload": workload_text("VW"[gamma - 1], cl)},
             "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -370,7 +378,8 @@ def run_ours(args, rank, world, local_rank):
     fn_h = torch.from_numpy(fn_np).pin_memory()
     gn_h = torch.from_numpy(gn_np).pin_memory()
     fn, gn = fn_h.cuda(), gn_h.cuda()
-    S = Solver(levels, BETA_HEAD, precision="mixed", gamma=gamma)
+    cl = args.head_coarse_level
+    S = Solver(levels, BETA_HEAD, precision="mixed", gamma=gamma, coarse_level=cl)
     S.autotune()                  # float32 step variant per level (process-wide), before any graph capture
     variants = step_variants(levels)
     f, g = S.load_vectors(fn, gn, project_g=True)
@@ -447,7 +456,7 @@ def run_ours(args, rank, world, local_rank):
     # ---------------------------------------------------------------- plain float64 comparison
     fp64 = None
     if args.fp64_steps > 0:
-        S64 = Solver(levels, BETA_HEAD, precision="fp64", gamma=gamma)
+        S64 = Solver(levels, BETA_HEAD, precision="fp64", gamma=gamma, coarse_level=cl)
         u64, p64 = S64.zeros_u(), S64.zeros_p()
         solve_once(S64, f, g, u64, p64)               # warm-up (graph capture)
         torch.cuda.synchronize()
@@ -497,7 +506,8 @@ def run_ours(args, rank, world, local_rank):
     extra = {}
     if not args.only_head:
         extra["levels"] = run_levels(S, args)
-        extra["sweep"] = {"V": run_sweep(args, rank, world, 1, flush), "W": run_sweep(args, rank, world, 2, flush)}
+        extra["sweep"] = {"V": run_sweep(args, rank, world, 1, 0, flush),
+                          "W_coarse3": run_sweep(args, rank, world, 2, 3, flush)}
         extra["batch"] = run_batch(args, rank, world)
         extra["small"] = run_small(args, world)
         extra["adjoint"] = run_adjoint(args, world)
@@ -505,7 +515,7 @@ def run_ours(args, rank, world, local_rank):
     # ---------------------------------------------------------------- CPU oracle baseline
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        times, setup, cyc = oracle_sample(2, gamma)
+        times, setup, cyc = oracle_sample(2, gamma, coarse_level=cl)
         cpu = {"value": oracle_rate(times, cyc), "unit": "DoF/s", "cores": 1, "kind": "oracle",
                "sample": "2 oracle %s(3,3) cycles of the same problem class at k=8 (h=1/512, beta=1e4, manufactured; "
                          "%.2f s each), rate = DoF / (cycle time x the oracle's own %d cycles to 1e-8 at k=8); "
@@ -517,11 +527,11 @@ def run_ours(args, rank, world, local_rank):
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32 cycles + f64 refinement",
                 "data": "synthetic",
-                "config": {"workload": workload_text(args.cycle), "precision": "mixed", "dof_per_solve": n_dof,
+                "config": {"workload": workload_text(args.cycle, cl), "precision": "mixed", "dof_per_solve": n_dof,
                            "solves_per_step": 1, "solves_per_s": args.steps * world / (ms / 1000),
                            "l2": "inputs larger than L2 (the level-10 hierarchy holds about 1.5 GB) and a 256 MB "
                                  "buffer written between steps (inside the timed region)",
-                           "cycles": rep.cycles, "oracle_cycles_k8": oracle_manufactured_cycles(K_LEVEL, gamma),
+                           "cycles": rep.cycles, "oracle_cycles_k8": oracle_manufactured_cycles(K_LEVEL, gamma, cl),
                            "mean_rate": rep.mean_rate, "rel_residual": rep.rel_residual,
                            "execution": "one CUDA-graph launch per solve (a device-side loop of refinement steps)",
                            "float32_step_variant_per_level": variants},
@@ -534,18 +544,18 @@ def run_ours(args, rank, world, local_rank):
 
 
 def run_levels(S_head, args):
-    """Cycles to 1e-8 of the manufactured problem (beta = 1e4) on k = 4..10 with V and W cycles in
-    mixed precision, beside the oracle's counts where it has them (k <= 8): the h-robustness of the
-    measured path."""
+    """Cycles to 1e-8 and time per solve of the manufactured problem (beta = 1e4) on k = 4..10 in mixed
+    precision with the V-cycle (coarsest level 0 and 3) and the W-cycle (coarsest level 3), beside
+    the oracle's counts where it has them (k <= 8): the h-robustness of the measured path."""
     import torch
 
     from paper_1502_04070_gb300 import workloads
     from paper_1502_04070_gb300.solver import Solver
     out = {}
-    for gamma in (1, 2):
+    for name, gamma, cl in (("V", 1, 0), ("V_coarse3", 1, 3), ("W_coarse3", 2, 3)):
         row = {}
         for k in range(4, K_HEAD + 1):
-            S = Solver(k + 1, BETA_HEAD, precision="mixed", gamma=gamma)
+            S = Solver(k + 1, BETA_HEAD, precision="mixed", gamma=gamma, coarse_level=cl)
             fn, gn = workloads.manufactured_nodal(k, BETA_HEAD)
             f, g = S.load_vectors(torch.from_numpy(fn).cuda(), torch.from_numpy(gn).cuda(), project_g=True)
             S.solve(f, g, tol=TOL, max_cycles=200)          # warm-up (graph capture)
@@ -553,14 +563,14 @@ def run_levels(S_head, args):
             t = time.perf_counter()
             _, _, rep = S.solve(f, g, tol=TOL, max_cycles=200)
             torch.cuda.synchronize()
-            row["k=%d" % k] = {"cycles": rep.cycles, "oracle_cycles": oracle_manufactured_cycles(k, gamma),
+            row["k=%d" % k] = {"cycles": rep.cycles, "oracle_cycles": oracle_manufactured_cycles(k, gamma, cl),
                                "ms": 1000 * (time.perf_counter() - t), "mean_rate": round(rep.mean_rate, 4)}
             S.close()
-        out["VW"[gamma - 1]] = row
+        out[name] = row
     return out
 
 
-def run_sweep(args, rank, world, gamma, flush):
+def run_sweep(args, rank, world, gamma, coarse_level, flush):
     """The robustness sweep (k = 8, six beta) in one batched CUDA-graph launch, V or W cycles."""
     import torch
 
@@ -571,7 +581,7 @@ def run_sweep(args, rank, world, gamma, flush):
     L = Solver(levels, 1.0)
     f, g = L.load_vectors(torch.from_numpy(fn_np).cuda(), torch.from_numpy(gn_np).cuda(), project_g=True)
     nb = len(BETAS)
-    B = BatchSolver([levels] * nb, BETAS, precision="mixed", gamma=gamma, autotune=True)
+    B = BatchSolver([levels] * nb, BETAS, precision="mixed", gamma=gamma, coarse_level=coarse_level, autotune=True)
     us = [torch.zeros(B.shapes(0)[0], dtype=torch.float64, device="cuda") for _ in BETAS]
     ps = [torch.zeros(B.shapes(0)[1], dtype=torch.float64, device="cuda") for _ in BETAS]
     res = {}
@@ -601,7 +611,8 @@ def run_sweep(args, rank, world, gamma, flush):
     out = {"value": nb * dofs(K_LEVEL) * world / (ms / 1000.0), "unit": "DoF/s", "ms_per_sweep": ms, "steps": steps,
            "solves_per_s": nb * world / (ms / 1000.0),
            "cycles_per_beta": {str(b): c for b, c in zip(BETAS, res["cycles"])},
-           "oracle_cycles_per_beta": oracle_sweep_cycles(gamma),
+           "oracle_cycles_per_beta": oracle_sweep_cycles(gamma, coarse_level),
+           "coarse_level": coarse_level,
            "mean_rate_per_beta": {str(b): round(r ** (1.0 / c), 4) for b, c, r in zip(BETAS, res["cycles"], res["rel"])},
            "max_rel_residual": max(res["rel"]),
            "gpu_launches_per_sweep": (B.kernel_launches() - launches0) // steps,

@@ -75,9 +75,15 @@ typedef struct stokes_params {
     int gamma;         /* 1 = V-cycle, 2 = W-cycle (Sec. 3) */
     int precision;     /* stokes_precision */
     int inner_cycles;  /* STOKES_MIXED: float32 cycles per refinement step (>= 1) */
+    int coarse_level;  /* coarsest level of the iteration, 0 <= coarse_level <= min(levels - 1, 3): the
+                          coarse problem is solved exactly there (Sec. 3) -- on level 0 by a 27 x 27
+                          inverse, on level c > 0 by a dense float64 inverse of its bordered system
+                          (2212 unknowns at c = 3) computed on the device at setup and set_beta; a
+                          finer coarse level shortens the W-cycle's recursion */
 } stokes_params;
 
-/* Paper defaults: Uzawa, nu = 3+3, tau = sigma = 0.8, V-cycle, float64, one inner cycle. */
+/* Paper defaults: Uzawa, nu = 3+3, tau = sigma = 0.8, V-cycle, float64, one inner cycle, coarsest
+ * level 0. */
 void stokes_default_params(stokes_params* prm, int levels, double beta);
 
 typedef struct stokes_handle_t stokes_handle;
@@ -90,13 +96,31 @@ typedef struct stokes_report {
     double rhs_norm;         /* ||F||_2 */
 } stokes_report;
 
+/* Device memory for the internal buffers of handles and batches.  alloc returns a pointer to at
+ * least `bytes` bytes of device memory of the current device, 256-byte aligned and usable on
+ * `stream` (the handle's cudaStream_t), or NULL on failure (the setup then returns STOKES_ERR_OOM);
+ * release frees a block that alloc returned, with the same bytes and stream.  ctx is passed through.
+ * The callbacks are called only inside stokes_setup, stokes_batch_setup, stokes_euler_rhs (its first
+ * call) and the destroy calls, on the calling thread. */
+typedef void* (*stokes_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*stokes_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
+
+/* Registers the allocator that every later stokes_setup and stokes_batch_setup uses for its device
+ * buffers (process-wide; both NULL restores cudaMalloc / cudaFree, one of them NULL is
+ * STOKES_ERR_BAD_ARG).  A handle keeps the allocator it was set up with and releases its buffers
+ * through it in stokes_destroy, so the allocator must outlive the handles set up with it.  This lets
+ * a framework's caching allocator (PyTorch's, for one) own the solver's level buffers.  Pinned host
+ * mirrors of a few scalars are always cudaMallocHost. */
+stokes_status stokes_set_allocator(stokes_alloc_fn alloc, stokes_free_fn release, void* ctx);
+
 /* Builds the level hierarchy (Sec. 2 nesting), the per-level diagonals Ahat = diag A_k and
- * Shat = diag(B_k Ahat^{-1} B_k^T) (Sec. 6, eq. numintroduc) and the level-0 factorisation
- * (Sec. 3: exact coarsest solve).  `stream` is a cudaStream_t (NULL = legacy default stream).
- * The library owns the handle and all internal buffers (cudaMalloc); free with stokes_destroy. */
+ * Shat = diag(B_k Ahat^{-1} B_k^T) (Sec. 6, eq. numintroduc) and the coarsest level's factorisation
+ * (Sec. 3: exact coarsest solve).  `stream` is a cudaStream_t (NULL = a stream the library creates).
+ * The library owns the handle and all internal buffers (from the registered allocator, else
+ * cudaMalloc); free with stokes_destroy. */
 stokes_status stokes_setup(const stokes_params* prm, void* stream, stokes_handle** out);
 
-/* Changes beta: rebuilds the diagonals and the coarse factorisation only. */
+/* Changes beta: rebuilds the diagonals and the coarse factorisation only (synchronises the stream). */
 stokes_status stokes_set_beta(stokes_handle* h, double beta);
 
 void stokes_destroy(stokes_handle* h);

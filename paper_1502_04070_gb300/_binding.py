@@ -25,6 +25,7 @@ class Params(ctypes.Structure):
         ("gamma", ctypes.c_int),
         ("precision", ctypes.c_int),
         ("inner_cycles", ctypes.c_int),
+        ("coarse_level", ctypes.c_int),
     ]
 
 
@@ -43,10 +44,15 @@ _D = ctypes.c_double
 _I = ctypes.c_int
 _SZ = ctypes.c_size_t
 
+# stokes_alloc_fn / stokes_free_fn
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
 # name -> (restype, argtypes); every symbol declared in include/stokes_mg.h
 SIGNATURES = {
     "stokes_default_params": (None, [ctypes.POINTER(Params), _I, _D]),
     "stokes_setup": (_I, [ctypes.POINTER(Params), _P, ctypes.POINTER(_P)]),
+    "stokes_set_allocator": (_I, [ALLOC_FN, FREE_FN, _P]),
     "stokes_set_beta": (_I, [_P, _D]),
     "stokes_destroy": (None, [_P]),
     "stokes_status_str": (ctypes.c_char_p, [_I]),

@@ -40,6 +40,63 @@ stokes_status fail(cudaError_t e) {
     return STOKES_ERR_CUDA;
 }
 
+// Device memory of a handle or batch: through the allocator registered with stokes_set_allocator
+// when the handle was set up, else cudaMalloc / cudaFree.  Keeps the size of every live block (the
+// release callback receives it).
+struct DevMem {
+    stokes_alloc_fn alloc = nullptr;
+    stokes_free_fn release = nullptr;
+    void* ctx = nullptr;
+    cudaStream_t st = nullptr;
+    std::vector<std::pair<void*, size_t>> live;
+    cudaError_t get(void** p, size_t bytes) {
+        *p = nullptr;
+        if (alloc) {
+            *p = alloc(bytes, (void*)st, ctx);
+            if (!*p) return cudaErrorMemoryAllocation;
+        } else {
+            cudaError_t e = cudaMalloc(p, bytes);
+            if (e != cudaSuccess) return e;
+        }
+        live.emplace_back(*p, bytes);
+        return cudaSuccess;
+    }
+    template <typename T>
+    cudaError_t get(T** p, size_t bytes) {
+        void* q = nullptr;
+        cudaError_t e = get(&q, bytes);
+        *p = static_cast<T*>(q);
+        return e;
+    }
+    void put(void* p) {
+        if (!p) return;
+        for (size_t i = 0; i < live.size(); ++i)
+            if (live[i].first == p) {
+                if (release) release(p, live[i].second, (void*)st, ctx);
+                else cudaFree(p);
+                live[i] = live.back();
+                live.pop_back();
+                return;
+            }
+    }
+    void put_all() {
+        while (!live.empty()) put(live.back().first);
+    }
+};
+
+std::mutex g_alloc_mu;
+stokes_alloc_fn g_alloc = nullptr;
+stokes_free_fn g_release = nullptr;
+void* g_alloc_ctx = nullptr;
+
+void init_mem(DevMem& m, cudaStream_t st) {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    m.alloc = g_alloc;
+    m.release = g_release;
+    m.ctx = g_alloc_ctx;
+    m.st = st;
+}
+
 template <typename T>
 struct Level {
     int n = 0;
@@ -51,14 +108,14 @@ struct Level {
 };
 
 template <typename T>
-stokes_status alloc_level(Level<T>& L, int k) {
+stokes_status alloc_level(Level<T>& L, int k, DevMem& mem) {
     L.n = 1 << (k + 1);
     L.n2 = (size_t)(2 * L.n + 1) * (2 * L.n + 1);
     L.n1 = (size_t)(L.n + 1) * (L.n + 1);
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
     const size_t bu = al(2 * L.n2 * sizeof(T)), bp = al(L.n1 * sizeof(T));
     const size_t total = 3 * bu + 4 * bp;
-    CK(cudaMalloc(&L.slab, total));
+    CK(mem.get(&L.slab, total));
     char* q = (char*)L.slab;
     L.u = (T*)q; q += bu;
     L.f = (T*)q; q += bu;
@@ -67,14 +124,8 @@ stokes_status alloc_level(Level<T>& L, int k) {
     L.g = (T*)q; q += bp;
     L.tp = (T*)q; q += bp;
     L.sinv = (T*)q;
-    CK(cudaMemset(L.slab, 0, total));
+    CK(cudaMemsetAsync(L.slab, 0, total, mem.st));
     return STOKES_OK;
-}
-
-template <typename T>
-void free_level(Level<T>& L) {
-    if (L.slab) cudaFree(L.slab);
-    L.slab = nullptr;
 }
 
 std::mutex g_dev_mu;
@@ -96,11 +147,18 @@ stokes_status ensure_weights() {
 struct stokes_handle_t {
     stokes_params prm{};
     cudaStream_t st = nullptr;
+    DevMem mem;                             // every device buffer of the handle
     bool own_stream = false;
     int L = 0;                              // number of levels
     std::vector<Level<double>> h64;         // FP64: all levels; MIXED: finest only
     std::vector<Level<float>> h32;          // MIXED: all levels
     double* inv = nullptr;                  // level-0 bordered inverse (27 x 27)
+    int clev = 0;                           // coarsest level of the iteration (exact solve there)
+    int cnb = 0;                            // clev > 0: size of its bordered system
+    double* cinv = nullptr;                 // clev > 0: its inverse, cnb x cnb, float64
+    int* cperm = nullptr;                   // clev > 0: scratch of the inversion
+    double* ccol = nullptr;
+    int* cstat = nullptr;
     double* partial = nullptr;
     int npartial = 0;
     double* scal = nullptr;                 // device scalars
@@ -178,13 +236,15 @@ bool smooth_level(stokes_handle* h, Level<T>& lv, int steps, bool timed, bool sw
 template <typename T>
 void mg_cycle(stokes_handle* h, std::vector<Level<T>>& H, int l) {
     Level<T>& lv = H[l];
-    if (l == 0) {
-        launch_coarse_solve<T>(h->st, h->inv, lv.f, lv.g, lv.u, lv.p);
+    if (l == h->clev) {   // the coarsest level of the iteration: exact solve (Sec. 3)
+        if (l == 0) launch_coarse_solve<T>(h->st, h->inv, lv.f, lv.g, lv.u, lv.p);
+        else launch_dense_solve<T>(h->st, lv.n, h->cinv, h->cnb, lv.f, lv.g, lv.u, lv.p);
         return;
     }
     if constexpr (sizeof(T) == 4) {
         // small levels: the whole V-cycle from level l down in one CTA (shared memory)
-        if (l <= kCoarseCycleTop && h->prm.gamma == 1 && h->prm.smoother == STOKES_UZAWA && h->coarse_kernel) {
+        if (l <= kCoarseCycleTop && h->prm.gamma == 1 && h->prm.smoother == STOKES_UZAWA && h->coarse_kernel &&
+            h->clev == 0) {
             CoarseCycleArgs a;
             for (int k = 1; k <= l; ++k) {
                 a.c[k - 1] = H[k].c;
@@ -393,6 +453,17 @@ stokes_status rebuild_beta(stokes_handle* h) {
     double inv[27 * 27];
     if (!coarse_inverse(square_tables(), beta, inv)) return STOKES_ERR_BAD_ARG;
     CK(cudaMemcpyAsync(h->inv, inv, sizeof(inv), cudaMemcpyHostToDevice, h->st));
+    if (h->clev > 0) {
+        // the bordered system of the coarsest level, assembled on the host, inverted on the device
+        std::vector<double> M((size_t)h->cnb * h->cnb);
+        bordered_system(square_tables(), 1 << (h->clev + 1), beta, M.data());
+        CK(cudaMemcpyAsync(h->cinv, M.data(), M.size() * sizeof(double), cudaMemcpyHostToDevice, h->st));
+        CK(launch_dense_inverse(h->st, h->cinv, h->cnb, h->cperm, h->ccol, h->cstat));
+        int st = 0;
+        CK(cudaMemcpyAsync(&st, h->cstat, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+        CK(cudaStreamSynchronize(h->st));
+        if (st != 0) return STOKES_ERR_BAD_ARG;
+    }
     CK(cudaStreamSynchronize(h->st));
     if (h->step) {
         cudaGraphExecDestroy(h->step);
@@ -445,6 +516,7 @@ void stokes_default_params(stokes_params* prm, int levels, double beta) {
     prm->gamma = 1;
     prm->precision = STOKES_FP64;
     prm->inner_cycles = 1;
+    prm->coarse_level = 0;
 }
 
 const char* stokes_status_str(stokes_status s) {
@@ -465,17 +537,9 @@ void stokes_destroy(stokes_handle* h) {
     if (h->st) cudaStreamSynchronize(h->st);
     if (h->step) cudaGraphExecDestroy(h->step);
     if (h->loop) cudaGraphExecDestroy(h->loop);
-    if (h->dctl) cudaFree(h->dctl);
-    if (h->ictl) cudaFree(h->ictl);
-    if (h->dhist) cudaFree(h->dhist);
     if (h->hhist) cudaFreeHost(h->hhist);
-    if (h->euler_w) cudaFree(h->euler_w);
     for (auto e : h->ev) cudaEventDestroy(e);
-    for (auto& l : h->h64) free_level(l);
-    for (auto& l : h->h32) free_level(l);
-    if (h->inv) cudaFree(h->inv);
-    if (h->partial) cudaFree(h->partial);
-    if (h->scal) cudaFree(h->scal);
+    h->mem.put_all();   // level slabs, coarse inverses, partial sums, scalars, loop control, history
     if (h->hscal) cudaFreeHost(h->hscal);
     if (h->own_stream && h->st) cudaStreamDestroy(h->st);
     delete h;
@@ -489,13 +553,14 @@ stokes_status stokes_setup(const stokes_params* prm, void* stream, stokes_handle
         P.nu_post < 0 || !(P.tau > 0.0) || !(P.sigma > 0.0) || (P.gamma != 1 && P.gamma != 2) ||
         (P.smoother != STOKES_UZAWA && P.smoother != STOKES_NORMAL_EQ) ||
         (P.precision != STOKES_FP64 && P.precision != STOKES_MIXED) ||
-        (P.precision == STOKES_MIXED && P.inner_cycles < 1))
+        (P.precision == STOKES_MIXED && P.inner_cycles < 1) || P.coarse_level < 0 ||
+        P.coarse_level > kMaxCoarseLevel || P.coarse_level > P.levels - 1)
         return STOKES_ERR_BAD_ARG;
     stokes_status s = ensure_weights();
     if (s != STOKES_OK) return s;
     if (prepare_uzawa_fused<float>() != cudaSuccess || prepare_uzawa_fused<double>() != cudaSuccess ||
         prepare_coarse_cycle() != cudaSuccess || prepare_uzawa_pair() != cudaSuccess ||
-        prepare_uzawa_reg() != cudaSuccess)
+        prepare_uzawa_reg() != cudaSuccess || prepare_dense_solve(bordered_size(1 << (kMaxCoarseLevel + 1))) != cudaSuccess)
         return STOKES_ERR_CUDA;
     stokes_handle* h = new stokes_handle_t();
     h->prm = P;
@@ -514,29 +579,41 @@ stokes_status stokes_setup(const stokes_params* prm, void* stream, stokes_handle
         stokes_destroy(h);
         return e;
     };
+    init_mem(h->mem, h->st);
     const int kfin = P.levels - 1;
     if (P.precision == STOKES_FP64) {
         h->h64.resize(P.levels);
         for (int k = 0; k < P.levels; ++k)
-            if ((s = alloc_level(h->h64[k], k)) != STOKES_OK) return bail(s);
+            if ((s = alloc_level(h->h64[k], k, h->mem)) != STOKES_OK) return bail(s);
     } else {
         h->h64.resize(1);
-        if ((s = alloc_level(h->h64[0], kfin)) != STOKES_OK) return bail(s);
+        if ((s = alloc_level(h->h64[0], kfin, h->mem)) != STOKES_OK) return bail(s);
         h->h32.resize(P.levels);
         for (int k = 0; k < P.levels; ++k)
-            if ((s = alloc_level(h->h32[k], k)) != STOKES_OK) return bail(s);
+            if ((s = alloc_level(h->h32[k], k, h->mem)) != STOKES_OK) return bail(s);
     }
     h->mass = make_mass<double>(h->fin().n);
     h->npartial = 2 * cells_blocks(h->fin().n);   // two sets of per-block partial sums (refinement update)
-    if (cudaMalloc(&h->inv, 27 * 27 * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&h->partial, (size_t)h->npartial * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&h->scal, 8 * sizeof(double)) != cudaSuccess ||
+    if (h->mem.get(&h->inv, 27 * 27 * sizeof(double)) != cudaSuccess ||
+        h->mem.get(&h->partial, (size_t)h->npartial * sizeof(double)) != cudaSuccess ||
+        h->mem.get(&h->scal, 8 * sizeof(double)) != cudaSuccess ||
         cudaMallocHost(&h->hscal, 8 * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&h->dctl, 4 * sizeof(double)) != cudaSuccess || cudaMalloc(&h->ictl, 4 * sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&h->dhist, stokes_handle_t::kHistCap * sizeof(double)) != cudaSuccess ||
+        h->mem.get(&h->dctl, 4 * sizeof(double)) != cudaSuccess || h->mem.get(&h->ictl, 4 * sizeof(int)) != cudaSuccess ||
+        h->mem.get(&h->dhist, stokes_handle_t::kHistCap * sizeof(double)) != cudaSuccess ||
         cudaMallocHost(&h->hhist, stokes_handle_t::kHistCap * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         return bail(STOKES_ERR_OOM);
+    }
+    h->clev = P.coarse_level;
+    if (h->clev > 0) {
+        h->cnb = bordered_size(1 << (h->clev + 1));
+        if (h->mem.get(&h->cinv, sizeof(double) * (size_t)h->cnb * h->cnb) != cudaSuccess ||
+            h->mem.get(&h->cperm, sizeof(int) * (size_t)h->cnb) != cudaSuccess ||
+            h->mem.get(&h->ccol, sizeof(double) * (size_t)h->cnb) != cudaSuccess ||
+            h->mem.get(&h->cstat, sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(STOKES_ERR_OOM);
+        }
     }
     if ((s = rebuild_beta(h)) != STOKES_OK) return bail(s);
     *out = h;
@@ -557,6 +634,15 @@ stokes_status stokes_autotune(stokes_handle* h) {
         h->loop = nullptr;
     }
     return s;
+}
+
+stokes_status stokes_set_allocator(stokes_alloc_fn alloc, stokes_free_fn release, void* ctx) {
+    if ((alloc == nullptr) != (release == nullptr)) return STOKES_ERR_BAD_ARG;
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_alloc = alloc;
+    g_release = release;
+    g_alloc_ctx = alloc ? ctx : nullptr;
+    return STOKES_OK;
 }
 
 stokes_status stokes_set_beta(stokes_handle* h, double beta) {
@@ -826,7 +912,7 @@ stokes_status stokes_euler_rhs(stokes_handle* h, const double* u_prev, const dou
     if (!h || !u_prev || !f_nodal || !g_nodal || !f || !g) return STOKES_ERR_BAD_ARG;
     const int n = h->fin().n;
     const size_t nvel = 2 * (size_t)(2 * n + 1) * (2 * n + 1);
-    if (!h->euler_w) CK(cudaMalloc(&h->euler_w, nvel * sizeof(double)));
+    if (!h->euler_w) CK(h->mem.get(&h->euler_w, nvel * sizeof(double)));
     CK(launch_euler_nodal(h->st, nvel, h->prm.beta, f_nodal, u_prev, h->euler_w));
     launch_load<double>(h->st, n, h->mass, h->euler_w, g_nodal, f, g, 1, h->partial, h->scal + 4);
     h->launches += 4;
@@ -923,6 +1009,7 @@ struct stokes_batch_t {
     double* d_res = nullptr;            // device: per instance (true ||r||^2, ||F||^2, steps)
     double* h_res = nullptr;            // pinned mirror
     unsigned long long launches = 0;
+    DevMem mem;
 };
 
 void stokes_batch_destroy(stokes_batch* b) {
@@ -930,8 +1017,7 @@ void stokes_batch_destroy(stokes_batch* b) {
     if (b->st) cudaStreamSynchronize(b->st);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     for (auto h : b->inst) stokes_destroy(h);
-    if (b->d_count) cudaFree(b->d_count);
-    if (b->d_res) cudaFree(b->d_res);
+    b->mem.put_all();
     if (b->h_res) cudaFreeHost(b->h_res);
     if (b->own_stream && b->st) cudaStreamDestroy(b->st);
     delete b;
@@ -964,8 +1050,9 @@ stokes_status stokes_batch_setup(int count, const int* levels, const double* bet
         }
         b->inst.push_back(h);
     }
-    if (cudaMalloc(&b->d_count, sizeof(int) * count) != cudaSuccess ||
-        cudaMalloc(&b->d_res, sizeof(double) * 3 * count) != cudaSuccess ||
+    init_mem(b->mem, b->st);
+    if (b->mem.get(&b->d_count, sizeof(int) * count) != cudaSuccess ||
+        b->mem.get(&b->d_res, sizeof(double) * 3 * count) != cudaSuccess ||
         cudaMallocHost(&b->h_res, sizeof(double) * 3 * count) != cudaSuccess) {
         cudaGetLastError();
         stokes_batch_destroy(b);

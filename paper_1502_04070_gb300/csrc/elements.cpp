@@ -268,7 +268,7 @@ bool coarse_inverse(const SquareMatrices& S, double beta, double inv[27 * 27]) {
         Abig[27][18 + i] = w[i];
     }
     // Gauss-Jordan on [Abig | I]
-    static double aug[28][56];
+    double aug[28][56];
     for (int i = 0; i < nb; ++i)
         for (int j = 0; j < 2 * nb; ++j) aug[i][j] = j < nb ? Abig[i][j] : (j - nb == i ? 1.0 : 0.0);
     for (int c = 0; c < nb; ++c) {
@@ -289,6 +289,58 @@ bool coarse_inverse(const SquareMatrices& S, double beta, double inv[27 * 27]) {
     for (int i = 0; i < 27; ++i)
         for (int j = 0; j < 27; ++j) inv[i * 27 + j] = aug[i][nb + j];
     return true;
+}
+
+int bordered_size(int n) { return 2 * (2 * n - 1) * (2 * n - 1) + (n + 1) * (n + 1) + 1; }
+
+// The matrix of eq. gen:bil:mv on a level with N = n, assembled square by square from the local
+// matrices, bordered with w = M_P 1 (the zero-mean pressure condition): row-major nb x nb,
+// nb = bordered_size(n).  Unknown order as in coarse_inverse: u_x at the interior lattice points
+// (X, Y), 1 <= X, Y <= 2n - 1, Y outer; then u_y; then p at the vertices (x, y), y outer; then the
+// border's multiplier.
+void bordered_system(const SquareMatrices& S, int n, double beta, double* M) {
+    const int nm = 2 * n - 1, nv = nm * nm, nb = bordered_size(n);
+    std::memset(M, 0, sizeof(double) * (size_t)nb * nb);
+    auto at = [&](int r, int c) -> double& { return M[(size_t)r * nb + c]; };
+    auto vidx = [&](int c, int X, int Y) -> int {
+        if (X <= 0 || Y <= 0 || X >= 2 * n || Y >= 2 * n) return -1;
+        return c * nv + (Y - 1) * nm + (X - 1);
+    };
+    auto pidx = [&](int x, int y) { return 2 * nv + y * (n + 1) + x; };
+    const double h = 1.0 / n;
+    for (int sj = 0; sj < n; ++sj)
+        for (int si = 0; si < n; ++si) {
+            const int o = ((si < n / 2) != (sj < n / 2)) ? 1 : 0;
+            for (int l = 0; l < 9; ++l)
+                for (int m = 0; m < 9; ++m) {
+                    const double a = S.K[o][l][m] + beta * h * h * S.M[o][l][m];
+                    if (a == 0.0) continue;
+                    for (int c = 0; c < 2; ++c) {
+                        const int r = vidx(c, 2 * si + l % 3, 2 * sj + l / 3);
+                        const int q = vidx(c, 2 * si + m % 3, 2 * sj + m / 3);
+                        if (r >= 0 && q >= 0) at(r, q) += a;
+                    }
+                }
+            for (int q = 0; q < 4; ++q) {
+                const int pr = pidx(si + q % 2, sj + q / 2);
+                for (int m = 0; m < 9; ++m) {
+                    const int cx = vidx(0, 2 * si + m % 3, 2 * sj + m / 3);
+                    const int cy = vidx(1, 2 * si + m % 3, 2 * sj + m / 3);
+                    if (cx >= 0) {
+                        at(pr, cx) += h * S.Bx[o][q][m];
+                        at(cx, pr) += h * S.Bx[o][q][m];
+                    }
+                    if (cy >= 0) {
+                        at(pr, cy) += h * S.By[o][q][m];
+                        at(cy, pr) += h * S.By[o][q][m];
+                    }
+                }
+                double wq = 0.0;
+                for (int r = 0; r < 4; ++r) wq += h * h * S.MP[o][q][r];
+                at(pr, nb - 1) += wq;
+                at(nb - 1, pr) += wq;
+            }
+        }
 }
 
 }  // namespace smg

@@ -25,4 +25,9 @@ TransferWeights transfer_weights();
 // Inverse (first 27 x 27 block) of the level-0 system bordered with the zero-mean constraint.
 bool coarse_inverse(const SquareMatrices& S, double beta, double inv[27 * 27]);
 
+// Size nb and row-major entries (caller array of nb * nb) of the system of a level with N = n
+// bordered with the zero-mean pressure condition (unknown order as in coarse_inverse).
+int bordered_size(int n);
+void bordered_system(const SquareMatrices& S, int n, double beta, double* M);
+
 }  // namespace smg

@@ -98,6 +98,15 @@ void launch_prolong_add(cudaStream_t s, int nc, const T* uc, const T* pc, T* u, 
 template <typename T>
 void launch_coarse_solve(cudaStream_t s, const double* inv, const T* f, const T* g, T* u, T* p);
 
+// Exact solve on a coarsest level c > 0 (dense.cu): in-place float64 inverse of the bordered
+// system (row-major nb x nb, device; perm, col, status device scratch; *status != 0 = singular), and
+// (u, p) = M^{-1} (f, g) on the level with N = n.
+cudaError_t launch_dense_inverse(cudaStream_t s, double* M, int nb, int* perm, double* col, int* status);
+template <typename T>
+void launch_dense_solve(cudaStream_t s, int n, const double* inv, int nb, const T* f, const T* g, T* u, T* p);
+cudaError_t prepare_dense_solve(int nb_max);
+constexpr int kMaxCoarseLevel = 3;   // N = 16: a bordered system of 2212 unknowns
+
 // Shat^{-1} per vertex (float64 computation, stored as T)
 template <typename T>
 void launch_schur_diag(cudaStream_t s, int n, const OpCoef<double>& c, T* sinv);

@@ -42,7 +42,8 @@ class Solver:
     """Coupled multigrid solver for [A + beta M, B^T; B, 0] on level k = levels - 1."""
 
     def __init__(self, levels: int, beta: float, *, nu_pre=3, nu_post=3, tau=None, sigma=0.8,
-                 smoother="uzawa", gamma=1, precision="fp64", inner_cycles=1, stream=None, device=None):
+                 smoother="uzawa", gamma=1, precision="fp64", inner_cycles=1, coarse_level=0, stream=None,
+                 device=None):
         self._lib = B.load()
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         prm = B.Params()
@@ -54,6 +55,7 @@ class Solver:
         prm.gamma = gamma
         prm.precision = _PREC[precision]
         prm.inner_cycles = inner_cycles
+        prm.coarse_level = coarse_level
         self.params = prm
         self.levels = levels
         self.beta = float(beta)
@@ -226,6 +228,40 @@ class Solver:
         return out.value
 
 
+_TORCH_ALLOCATOR = None   # the registered callbacks (kept alive while registered)
+
+
+def _torch_alloc(nbytes, stream, ctx):
+    try:
+        return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+    except Exception:
+        return None
+
+
+def _torch_free(ptr, nbytes, stream, ctx):
+    torch.cuda.caching_allocator_delete(int(ptr))
+
+
+def use_torch_allocator(enable=True):
+    """Let PyTorch's caching allocator serve the device buffers of solvers set up from now on
+    (stokes_set_allocator); enable=False restores cudaMalloc for later setups.  Solvers keep the
+    allocator they were set up with."""
+    global _TORCH_ALLOCATOR
+    lib = B.load()
+    if enable:
+        cbs = (B.ALLOC_FN(_torch_alloc), B.FREE_FN(_torch_free))
+        B.check(lib.stokes_set_allocator(cbs[0], cbs[1], None), "stokes_set_allocator")
+        # earlier callbacks stay referenced by the solvers that use them
+        _KEEP.append(cbs)
+        _TORCH_ALLOCATOR = cbs
+    else:
+        B.check(lib.stokes_set_allocator(B.ALLOC_FN(), B.FREE_FN(), None), "stokes_set_allocator")
+        _TORCH_ALLOCATOR = None
+
+
+_KEEP = []
+
+
 def step_variant(levels):
     """Float32 Uzawa step variant used for levels with N = 2^levels (0-3 fused tiles 32x16, 32x8,
     64x8, 16x16; 4-6 three-kernel step with blocks 32x8, 16x8, 8x8; 7-9 fused step on
@@ -244,7 +280,7 @@ class BatchSolver:
     launch (stokes_batch_setup / stokes_batch_solve)."""
 
     def __init__(self, levels, betas, *, precision="mixed", nu_pre=3, nu_post=3, tau=0.8, sigma=0.8, gamma=1,
-                 autotune=True, device=None):
+                 coarse_level=0, autotune=True, device=None):
         self._lib = B.load()
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.levels = [int(l) for l in levels]
@@ -253,6 +289,7 @@ class BatchSolver:
         prm = B.Params()
         self._lib.stokes_default_params(ctypes.byref(prm), 1, 0.0)
         prm.nu_pre, prm.nu_post, prm.tau, prm.sigma, prm.gamma = nu_pre, nu_post, tau, sigma, gamma
+        prm.coarse_level = coarse_level
         prm.precision = _PREC[precision]
         n = len(self.levels)
         lv = (ctypes.c_int * n)(*self.levels)

@@ -54,6 +54,10 @@ def test_setup_rejects_bad_arguments_without_touching_the_gpu():
     lib.stokes_default_params(ctypes.byref(prm), 4, float("nan"))
     assert lib.stokes_setup(ctypes.byref(prm), None, ctypes.byref(h)) == _binding.ERR_BAD_ARG
     assert lib.stokes_setup(None, None, ctypes.byref(h)) == _binding.ERR_BAD_ARG
+    for levels, c in ((3, 3), (6, 4), (6, -1)):                 # coarsest level out of range
+        lib.stokes_default_params(ctypes.byref(prm), levels, 1.0)
+        prm.coarse_level = c
+        assert lib.stokes_setup(ctypes.byref(prm), None, ctypes.byref(h)) == _binding.ERR_BAD_ARG
 
 
 def test_entry_points_reject_null_handles_without_touching_the_gpu():
@@ -79,6 +83,15 @@ def test_step_variant_selection_without_gpu():
     assert lib.stokes_set_step_variant(5, 6) == _binding.OK
     assert lib.stokes_step_variant(5) == 6
     assert lib.stokes_set_step_variant(5, old) == _binding.OK
+
+
+def test_allocator_registration_without_gpu():
+    """stokes_set_allocator takes both callbacks or neither (cudaMalloc again)."""
+    from paper_1502_04070_gb300 import _binding as B
+    lib = B.load()
+    keep = B.ALLOC_FN(lambda nbytes, stream, ctx: None)
+    assert lib.stokes_set_allocator(keep, B.FREE_FN(), None) == B.ERR_BAD_ARG
+    assert lib.stokes_set_allocator(B.ALLOC_FN(), B.FREE_FN(), None) == B.OK
 
 
 def test_product_path_fails_loudly_without_library(tmp_path):
