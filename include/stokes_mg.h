@@ -235,6 +235,20 @@ stokes_status stokes_lshape_coarse_inverse(double beta, double* inv, int* nunk);
 stokes_status stokes_euler_rhs(stokes_handle* h, const double* u_prev, const double* f_nodal, const double* g_nodal,
                                double* f, double* g);
 
+/* A sequence of `steps` implicit Euler steps (as in stokes_euler_rhs, beta = 1/dt the handle's beta)
+ * in ONE CUDA-graph launch.  For n = 0 .. steps-1: the right-hand side of the step from the nodal data
+ * f_nodal[n], g_nodal[n] of the new time level and the current velocity, then multigrid cycles from the
+ * current (u, p) (a warm start) in a device-side loop until the TRUE float64 relative residual
+ * ||F - A x|| / ||F|| <= tol or max_cycles cycles.  u, p (device, layouts above) hold the initial state
+ * and receive the state after the last step; f_nodal, g_nodal are host arrays of `steps` device
+ * pointers (repeat a pointer for constant forcing).  cycles, rel_residual (caller-owned host arrays of
+ * `steps`, may be NULL) receive each step's cycle count and final relative residual.  The graph is kept
+ * and replayed while the pointers, tol and max_cycles are the same.  Returns STOKES_NOT_CONVERGED if
+ * some step missed tol (the trajectory is still written).  Synchronises the stream. */
+stokes_status stokes_euler_run(stokes_handle* h, double* u, double* p, const double* const* f_nodal,
+                               const double* const* g_nodal, int steps, double tol, int max_cycles, int* cycles,
+                               double* rel_residual);
+
 /* g <- g - (1^T g) w,  w = M_P 1 (w sums to 1): makes a pressure right-hand side orthogonal to the
  * constant pressure, the kernel of the matrix of eq. gen:bil:mv (Sec. 1: int g = 0).  Needed for
  * adjoint right-hand sides whose pressure part does not sum to zero.  In place, asynchronous. */
@@ -313,6 +327,15 @@ stokes_status stokes_batch_solve(stokes_batch* b, double* const* u, double* cons
                                  const double* const* g, double tol, int max_cycles, int* cycles,
                                  double* rel_residual);
 void stokes_batch_destroy(stokes_batch* b);
+/* Independent implicit Euler trajectories, one per instance of the batch (instance i: its own level
+ * and beta = 1/dt_i), each a chain of `steps` steps as in stokes_euler_run, all instances concurrent in
+ * one CUDA-graph launch.  u, p: host arrays of `count` device pointers (state in, state out);
+ * f_nodal, g_nodal: host arrays of count * steps device pointers, instance-major (entry i * steps + n
+ * is step n of instance i); cycles, rel_residual (may be NULL): host arrays of count * steps, likewise.
+ * Returns STOKES_NOT_CONVERGED if some step of some instance missed tol.  Synchronises the stream. */
+stokes_status stokes_batch_euler_run(stokes_batch* b, double* const* u, double* const* p, const double* const* f_nodal,
+                                     const double* const* g_nodal, int steps, double tol, int max_cycles, int* cycles,
+                                     double* rel_residual);
 /* Kernels executed by stokes_batch_solve calls so far (loop bodies counted per executed step). */
 unsigned long long stokes_batch_kernel_launches(const stokes_batch* b);
 

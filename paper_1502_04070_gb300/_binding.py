@@ -82,6 +82,10 @@ SIGNATURES = {
     "stokes_batch_solve": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
                                 _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "stokes_batch_destroy": (None, [_P]),
+    "stokes_euler_run": (_I, [_P, _P, _P, ctypes.POINTER(_P), ctypes.POINTER(_P), _I, _D, _I, ctypes.POINTER(_I),
+                              ctypes.POINTER(_D)]),
+    "stokes_batch_euler_run": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                    _I, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "stokes_batch_kernel_launches": (ctypes.c_ulonglong, [_P]),
     "stokes_autotune": (_I, [_P]),
     "stokes_step_variant": (_I, [_I]),

@@ -175,6 +175,13 @@ struct stokes_handle_t {
     double* dhist = nullptr;                // residual^2 per step, device (kHistCap entries)
     double* hhist = nullptr;                // pinned mirror
     double* euler_w = nullptr;              // nodal data of an implicit Euler right-hand side
+    cudaGraphExec_t euler = nullptr;        // a sequence of implicit Euler steps (stokes_euler_run)
+    std::vector<const void*> euler_key;     // pointers (and so steps) it was built for
+    double euler_tol = -1.0;                // tol and max_cycles it was built for
+    int euler_max = -1;
+    int* d_ecount = nullptr;                // device: cycles per step
+    double* d_eres = nullptr;               // device: per step (true ||r||^2, ||F||^2, cycles)
+    int euler_kernels = 0, euler_body = 0;  // kernels outside / inside the loop bodies
     unsigned long long launches = 0;        // kernels launched by this handle (graph nodes included)
     // optional timing of the finest-level smoothing steps and of the float64 residual: event
     // pairs recorded inside the captured graph (cudaEventRecordExternal)
@@ -473,6 +480,10 @@ stokes_status rebuild_beta(stokes_handle* h) {
         cudaGraphExecDestroy(h->loop);
         h->loop = nullptr;
     }
+    if (h->euler) {
+        cudaGraphExecDestroy(h->euler);
+        h->euler = nullptr;
+    }
     return STOKES_OK;
 }
 
@@ -537,6 +548,7 @@ void stokes_destroy(stokes_handle* h) {
     if (h->st) cudaStreamSynchronize(h->st);
     if (h->step) cudaGraphExecDestroy(h->step);
     if (h->loop) cudaGraphExecDestroy(h->loop);
+    if (h->euler) cudaGraphExecDestroy(h->euler);
     if (h->hhist) cudaFreeHost(h->hhist);
     for (auto e : h->ev) cudaEventDestroy(e);
     h->mem.put_all();   // level slabs, coarse inverses, partial sums, scalars, loop control, history
@@ -632,6 +644,10 @@ stokes_status stokes_autotune(stokes_handle* h) {
     if (s == STOKES_OK && h->loop) {
         cudaGraphExecDestroy(h->loop);
         h->loop = nullptr;
+    }
+    if (s == STOKES_OK && h->euler) {
+        cudaGraphExecDestroy(h->euler);
+        h->euler = nullptr;
     }
     return s;
 }
@@ -1191,5 +1207,219 @@ stokes_status stokes_batch_solve(stokes_batch* b, double* const* u, double* cons
 }
 
 unsigned long long stokes_batch_kernel_launches(const stokes_batch* b) { return b ? b->launches : 0ull; }
+
+// ----------------------------------------------------------------------------------- time stepping
+
+static int graph_kernels(cudaGraph_t gr) {
+    size_t nn = 0;
+    cudaGraphGetNodes(gr, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    cudaGraphGetNodes(gr, nodes.data(), &nn);
+    int k = 0;
+    for (auto nd : nodes) {
+        cudaGraphNodeType ty;
+        if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++k;
+    }
+    return k;
+}
+
+// Appends to `top`, after *dep (null: no dependency), the implicit Euler steps of handle h (Sec. 1:
+// the step of length dt is the generalized Stokes system with beta = 1/dt, the handle's beta): (u, p)
+// is copied into the handle's finest arrays; per step n the right-hand side is formed from the nodal
+// data f_nodal[n] + beta u and g_nodal[n] (load vectors, g shifted to zero mean), ||F||^2 and the
+// true residual are computed, a conditional WHILE node runs cycles (body: one cycle, or one
+// refinement step followed by the true float64 residual; then the device-side test of the relative
+// residual against tol and of max_cycles), and the step's true ||r||^2, ||F||^2 and cycle count go to
+// res[3 n .. 3 n + 2]; finally (u, p) is written back.  *kernels counts the kernels outside the loop
+// bodies, *body those of one loop iteration.
+static cudaError_t add_euler_chain(cudaGraph_t top, cudaGraphNode_t* dep, stokes_handle* h, double* u, double* p,
+                                   const double* const* f_nodal, const double* const* g_nodal, int steps,
+                                   double tol, int max_cycles, int* count, double* res, int* kernels, int* body) {
+    cudaStream_t st = h->st;
+    Level<double>& F = h->fin();
+    const size_t nvel = 2 * F.n2;
+    const bool timing = h->timing;
+    h->timing = false;
+    cudaError_t e = cudaSuccess;
+    auto child = [&](auto&& record) -> cudaError_t {
+        cudaGraph_t g = nullptr;
+        cudaError_t r = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (r != cudaSuccess) return r;
+        record();
+        if ((r = cudaStreamEndCapture(st, &g)) != cudaSuccess) return r;
+        *kernels += graph_kernels(g);
+        cudaGraphNode_t nd;
+        r = cudaGraphAddChildGraphNode(&nd, top, *dep ? dep : nullptr, *dep ? 1 : 0, g);
+        cudaGraphDestroy(g);
+        if (r == cudaSuccess) *dep = nd;
+        return r;
+    };
+    e = child([&] {
+        cudaMemcpyAsync(F.u, u, nvel * sizeof(double), cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(F.p, p, F.n1 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    });
+    for (int n = 0; n < steps && e == cudaSuccess; ++n) {
+        e = child([&] {
+            launch_euler_nodal(st, nvel, h->prm.beta, f_nodal[n], F.u, h->euler_w);
+            launch_load<double>(st, F.n, h->mass, h->euler_w, g_nodal[n], F.f, F.g, 1, h->partial, h->scal + 4);
+            launch_rhs_norm(st, F.n, F.f, F.g, h->partial);
+            launch_reduce(st, h->partial, cells_blocks(F.n), h->scal + 2);
+            residual_norm_fin(h);
+            cudaMemsetAsync(count + n, 0, sizeof(int), st);
+        });
+        if (e != cudaSuccess) break;
+        cudaGraphConditionalHandle hnd;
+        if ((e = cudaGraphConditionalHandleCreate(&hnd, top, 1, cudaGraphCondAssignDefault)) != cudaSuccess) break;
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = hnd;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t nc;
+        if ((e = cudaGraphAddNode(&nc, top, dep, nullptr, 1, &cp)) != cudaSuccess) break;
+        cudaGraph_t bg = cp.conditional.phGraph_out[0];
+        if ((e = cudaStreamBeginCaptureToGraph(st, bg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+            cudaSuccess)
+            break;
+        record_step(h);
+        if (h->mixed()) residual_norm_fin(h);   // the test uses the true residual, not the updated one
+        launch_batch_check(st, hnd, h->scal, tol * tol, max_cycles, count + n);
+        if ((e = cudaStreamEndCapture(st, &bg)) != cudaSuccess) break;
+        *body = graph_kernels(bg);
+        *dep = nc;
+        e = child([&] { launch_batch_store(st, h->scal, count + n, res + 3 * n); });
+    }
+    if (e == cudaSuccess)
+        e = child([&] {
+            cudaMemcpyAsync(u, F.u, nvel * sizeof(double), cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(p, F.p, F.n1 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+        });
+    h->timing = timing;
+    return e;
+}
+
+// reads back the per-step results of an Euler graph; OK, or NOT_CONVERGED if a step missed tol
+static stokes_status euler_results(const std::vector<double>& res, int steps, double tol, int* cycles,
+                                   double* rel_residual, unsigned long long* total_cycles) {
+    stokes_status out = STOKES_OK;
+    for (int n = 0; n < steps; ++n) {
+        const double r = std::sqrt(res[3 * n]), nF = std::sqrt(res[3 * n + 1]);
+        const int c = (int)res[3 * n + 2];
+        *total_cycles += (unsigned long long)c;
+        if (cycles) cycles[n] = c;
+        const double rel = nF > 0 ? r / nF : r;
+        if (rel_residual) rel_residual[n] = rel;
+        if (!(rel <= tol)) out = STOKES_NOT_CONVERGED;
+    }
+    return out;
+}
+
+stokes_status stokes_euler_run(stokes_handle* h, double* u, double* p, const double* const* f_nodal,
+                               const double* const* g_nodal, int steps, double tol, int max_cycles, int* cycles,
+                               double* rel_residual) {
+    if (!h || !u || !p || !f_nodal || !g_nodal || steps < 1 || !(tol > 0.0) || max_cycles < 1) return STOKES_ERR_BAD_ARG;
+    std::vector<const void*> key = {u, p};
+    for (int n = 0; n < steps; ++n) {
+        if (!f_nodal[n] || !g_nodal[n]) return STOKES_ERR_BAD_ARG;
+        key.push_back(f_nodal[n]);
+        key.push_back(g_nodal[n]);
+    }
+    Level<double>& F = h->fin();
+    if (!h->euler_w) CK(h->mem.get(&h->euler_w, 2 * F.n2 * sizeof(double)));
+    if (!h->euler || key != h->euler_key || tol != h->euler_tol || max_cycles != h->euler_max) {
+        if (h->euler) {
+            cudaGraphExecDestroy(h->euler);
+            h->euler = nullptr;
+        }
+        CK(cudaStreamSynchronize(h->st));
+        h->mem.put(h->d_ecount);
+        h->mem.put(h->d_eres);
+        h->d_ecount = nullptr;
+        h->d_eres = nullptr;
+        CK(h->mem.get(&h->d_ecount, sizeof(int) * (size_t)steps));
+        CK(h->mem.get(&h->d_eres, sizeof(double) * 3 * (size_t)steps));
+        cudaGraph_t top = nullptr;
+        CK(cudaGraphCreate(&top, 0));
+        cudaGraphNode_t dep = nullptr;
+        h->euler_kernels = h->euler_body = 0;
+        cudaError_t e = add_euler_chain(top, &dep, h, u, p, f_nodal, g_nodal, steps, tol, max_cycles, h->d_ecount,
+                                        h->d_eres, &h->euler_kernels, &h->euler_body);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&h->euler, top, 0);
+        cudaGraphDestroy(top);
+        if (e != cudaSuccess) {
+            h->euler = nullptr;
+            return fail(e);
+        }
+        h->euler_key = key;
+        h->euler_tol = tol;
+        h->euler_max = max_cycles;
+    }
+    CK(cudaGraphLaunch(h->euler, h->st));
+    std::vector<double> res(3 * (size_t)steps);
+    CK(cudaMemcpyAsync(res.data(), h->d_eres, res.size() * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    unsigned long long total = 0;
+    const stokes_status out = euler_results(res, steps, tol, cycles, rel_residual, &total);
+    h->launches += (unsigned long long)h->euler_kernels + total * (unsigned long long)h->euler_body;
+    return out;
+}
+
+stokes_status stokes_batch_euler_run(stokes_batch* b, double* const* u, double* const* p,
+                                     const double* const* f_nodal, const double* const* g_nodal, int steps,
+                                     double tol, int max_cycles, int* cycles, double* rel_residual) {
+    if (!b || !u || !p || !f_nodal || !g_nodal || steps < 1 || !(tol > 0.0) || max_cycles < 1)
+        return STOKES_ERR_BAD_ARG;
+    const int count = b->count;
+    for (int i = 0; i < count; ++i) {
+        if (!u[i] || !p[i]) return STOKES_ERR_BAD_ARG;
+        for (int n = 0; n < steps; ++n)
+            if (!f_nodal[(size_t)i * steps + n] || !g_nodal[(size_t)i * steps + n]) return STOKES_ERR_BAD_ARG;
+    }
+    // one graph per call: every instance's chain of steps is an independent branch
+    std::vector<int*> dcount(count, nullptr);
+    std::vector<double*> dres(count, nullptr);
+    cudaGraph_t top = nullptr;
+    CK(cudaGraphCreate(&top, 0));
+    cudaError_t e = cudaSuccess;
+    std::vector<int> kern(count, 0), body(count, 0);
+    for (int i = 0; i < count && e == cudaSuccess; ++i) {
+        stokes_handle* h = b->inst[i];
+        Level<double>& F = h->fin();
+        if (!h->euler_w && (e = h->mem.get(&h->euler_w, 2 * F.n2 * sizeof(double))) != cudaSuccess) break;
+        if ((e = b->mem.get(&dcount[i], sizeof(int) * (size_t)steps)) != cudaSuccess) break;
+        if ((e = b->mem.get(&dres[i], sizeof(double) * 3 * (size_t)steps)) != cudaSuccess) break;
+        // the instance's stream is the batch's stream: the branches are captured one after another
+        cudaGraphNode_t dep = nullptr;
+        e = add_euler_chain(top, &dep, h, u[i], p[i], f_nodal + (size_t)i * steps, g_nodal + (size_t)i * steps, steps,
+                            tol, max_cycles, dcount[i], dres[i], &kern[i], &body[i]);
+    }
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, top, 0);
+    cudaGraphDestroy(top);
+    stokes_status out = STOKES_OK;
+    if (e == cudaSuccess) e = cudaGraphLaunch(exec, b->st);
+    std::vector<double> res(3 * (size_t)steps);
+    for (int i = 0; i < count && e == cudaSuccess; ++i) {
+        if ((e = cudaMemcpyAsync(res.data(), dres[i], res.size() * sizeof(double), cudaMemcpyDeviceToHost, b->st)) !=
+                cudaSuccess ||
+            (e = cudaStreamSynchronize(b->st)) != cudaSuccess)
+            break;
+        unsigned long long total = 0;
+        const stokes_status si = euler_results(res, steps, tol, cycles ? cycles + (size_t)i * steps : nullptr,
+                                               rel_residual ? rel_residual + (size_t)i * steps : nullptr, &total);
+        if (si != STOKES_OK) out = si;
+        b->launches += (unsigned long long)kern[i] + total * (unsigned long long)body[i];
+    }
+    if (exec) {
+        cudaStreamSynchronize(b->st);
+        cudaGraphExecDestroy(exec);
+    }
+    for (int i = 0; i < count; ++i) {
+        b->mem.put(dcount[i]);
+        b->mem.put(dres[i]);
+    }
+    if (e != cudaSuccess) return fail(e);
+    return out;
+}
 
 }  // extern "C"

@@ -3,8 +3,8 @@ residual histories to 1e-8 relative residual (Uzawa smoother, Sec. 4, tau = sigm
 zero start):
 
 * the manufactured problem (u = curl(sin^2(pi x) sin^2(pi y)), p = cos(pi x) cos(pi y), beta = 1e4)
-  on levels k = 4..8 with the V-cycle and the W-cycle (Sec. 3: gamma = 1, 2), and with the W-cycle
-  whose coarsest level is 3 (exact solve there);
+  on levels k = 4..8 with the V-cycle and the W-cycle (Sec. 3: gamma = 1, 2), each with the coarsest
+  level 0 and 3 (exact solve there);
 * the robustness sweep of h = 1/512 (k = 8, beta in {0, 1, 1e2, 1e4, 1e6, 1e8}, f and g uniform[-1,1]
   nodal, seed 1, g zero-mean) with the W-cycle, coarsest level 0 and 3 (the V-cycle counts are in
   sweep_k8.json).
@@ -50,7 +50,7 @@ if __name__ == "__main__":
         F = ds[-1].load(fn, gn, project_g=True)
         for gamma in (1, 2):
             man.append(solve(ds, 1e4, F, gamma))
-        man.append(solve(ds, 1e4, F, 2, coarse_level=3))
+            man.append(solve(ds, 1e4, F, gamma, coarse_level=3))
     fn, gn = workloads.random_nodal(8, 1)
     F = ds_all[-1].load(fn, gn, project_g=True)
     sweep = [solve(ds_all, b, F, 2) for b in BETAS]

@@ -140,3 +140,76 @@ def test_warm_start_needs_fewer_cycles():
         assert sum(warm[1:]) <= 0.7 * sum(cold[1:]), (warm, cold)
     finally:
         te.close()
+
+
+@pytest.mark.parametrize("precision,tol,bound", [("fp64", 1e-12, 1e-8), ("mixed", 1e-10, 1e-6)])
+def test_graph_run_matches_oracle_and_host_steps(discs, precision, tol, bound):
+    """The five steps of the trajectory test (k = 5, dt = 1e-2) as one CUDA-graph launch
+    (stokes_euler_run): the last level matches the oracle's exact steps within the same bounds,
+    every step meets its tolerance in the true float64 residual, and each step takes the cycles of
+    the same step driven from the host (within one: the graph stops on the true residual after every
+    cycle, the host loop on the refinement's updated one, confirmed at the end)."""
+    from paper_1502_04070_gb300.timestep import ImplicitEuler
+    k, steps, dt = 5, 5, 1e-2
+    d = discs[k]
+    u0 = _velocity(d, 21)
+    forcing = _forcing(k, 22)
+    ref = _reference(d, dt, u0, forcing, steps)
+    te = ImplicitEuler(k + 1, dt, precision=precision, tol=tol, max_cycles=200)
+    try:
+        data = [tuple(dev(a) for a in forcing(n)) for n in range(1, steps + 1)]
+        u, p = dev(u0), te.solver.zeros_p()
+        cyc, rel = te.run_graph(u, p, [a for a, _ in data], [b for _, b in data])
+        assert len(cyc) == steps and all(r <= tol for r in rel), rel
+        x = d.to_vec(host(u), host(p))
+        assert np.abs(x - ref[-1]).max() <= bound * np.abs(ref[-1]).max()
+        u2, p2 = dev(u0), te.solver.zeros_p()
+        reps = [te.step(u2, p2, a, b) for a, b in data]
+        assert all(abs(c - max(1, r.cycles)) <= 1 for c, r in zip(cyc, reps)), (cyc, [r.cycles for r in reps])
+        # a second launch of the same graph from the same start gives the same trajectory
+        u3, p3 = dev(u0), te.solver.zeros_p()
+        cyc3, _ = te.run_graph(u3, p3, [a for a, _ in data], [b for _, b in data])
+        assert cyc3 == cyc and float((u3 - u).abs().max()) == 0.0
+    finally:
+        te.close()
+
+
+def test_batched_trajectories_match_single_runs(discs):
+    """Three independent trajectories (k = 3, 4, 5 with dt = 1e-2, 1e-3, 1e-4), four steps each, in one
+    launch (stokes_batch_euler_run): each equals its own single-trajectory graph run (the same kernels
+    on the same data) and the k = 5 one the oracle's exact steps."""
+    from paper_1502_04070_gb300.timestep import BatchImplicitEuler, ImplicitEuler
+    ks, dts, steps = [3, 4, 5], [1e-2, 1e-3, 1e-4], 4
+    datas, u0s = [], []
+    for i, k in enumerate(ks):
+        d = discs[k]
+        u0s.append(_velocity(d, 51 + i))
+        fo = _forcing(k, 61 + i)
+        datas.append([tuple(dev(a) for a in fo(n)) for n in range(1, steps + 1)])
+    be = BatchImplicitEuler([k + 1 for k in ks], dts, precision="fp64", tol=1e-12, max_cycles=200)
+    try:
+        us = [dev(u0) for u0 in u0s]
+        ps = [torch_zeros_p(k) for k in ks]
+        cyc, rel = be.run(us, ps, [[a for a, _ in dd] for dd in datas], [[b for _, b in dd] for dd in datas])
+        assert all(r <= 1e-12 for row in rel for r in row)
+        for i, k in enumerate(ks):
+            te = ImplicitEuler(k + 1, dts[i], precision="fp64", tol=1e-12, max_cycles=200)
+            try:
+                u, p = dev(u0s[i]), te.solver.zeros_p()
+                c1, _ = te.run_graph(u, p, [a for a, _ in datas[i]], [b for _, b in datas[i]])
+                assert c1 == cyc[i]
+                assert float((u - us[i]).abs().max()) <= 1e-14 * float(u.abs().max())
+            finally:
+                te.close()
+        d = discs[5]
+        ref = ts.implicit_euler(d, dts[2], u0s[2], _forcing(5, 63), steps)
+        x = d.to_vec(host(us[2]), host(ps[2]))
+        assert np.abs(x - ref[-1]).max() <= 1e-8 * np.abs(ref[-1]).max()
+    finally:
+        be.close()
+
+
+def torch_zeros_p(k):
+    import torch
+    n = 2 ** (k + 1)
+    return torch.zeros((n + 1, n + 1), dtype=torch.float64, device="cuda")
