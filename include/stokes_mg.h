@@ -59,6 +59,11 @@ typedef enum stokes_smoother {
     STOKES_NORMAL_EQ = 1         /* preconditioned normal-equation smoother, Sec. 4 (tau = 0.35) */
 } stokes_smoother;
 
+typedef enum stokes_domain {
+    STOKES_UNIT_SQUARE = 0,      /* the unit square of Sec. 6 */
+    STOKES_L_SHAPE = 1           /* the unit square without [1/2, 1]^2 (a non-convex domain, Sec. 1) */
+} stokes_domain;
+
 typedef enum stokes_precision {
     STOKES_FP64 = 0,             /* every level and every step in float64 */
     STOKES_MIXED = 1             /* float32 cycles inside float64 iterative refinement */
@@ -80,6 +85,15 @@ typedef struct stokes_params {
                           inverse, on level c > 0 by a dense float64 inverse of its bordered system
                           (2212 unknowns at c = 3) computed on the device at setup and set_beta; a
                           finer coarse level shortens the W-cycle's recursion */
+    int domain;        /* stokes_domain.  STOKES_L_SHAPE keeps the square's lattice and layouts: the
+                          L's level j is the square's level j + 1 with the velocity nodes in the closed
+                          removed quadrant (the re-entrant sides x = 1/2, y >= 1/2 and y = 1/2,
+                          x >= 1/2 and beyond) Dirichlet nodes and the vertices strictly inside it not
+                          unknowns; entries of u, p, f, g there are ignored on input and zero on output,
+                          and the zero-mean pressure is over the L.  It needs STOKES_FP64, the Uzawa
+                          smoother, coarse_level = 1 (the L's level 0) and levels >= 2; load vectors,
+                          Euler right-hand sides and mass products are square-only (they return
+                          STOKES_ERR_BAD_ARG on an L handle) */
 } stokes_params;
 
 /* Paper defaults: Uzawa, nu = 3+3, tau = sigma = 0.8, V-cycle, float64, one inner cycle, coarsest

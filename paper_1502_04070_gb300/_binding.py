@@ -10,6 +10,7 @@ from . import build as _build
 
 OK, ERR_BAD_ARG, ERR_OOM, ERR_CUDA, NOT_CONVERGED, DIVERGED, ERR_TIMEOUT = range(7)
 UZAWA, NORMAL_EQ = 0, 1
+UNIT_SQUARE, L_SHAPE = 0, 1
 FP64, MIXED = 0, 1
 
 
@@ -26,6 +27,7 @@ class Params(ctypes.Structure):
         ("precision", ctypes.c_int),
         ("inner_cycles", ctypes.c_int),
         ("coarse_level", ctypes.c_int),
+        ("domain", ctypes.c_int),
     ]
 
 

@@ -153,6 +153,7 @@ struct stokes_handle_t {
     std::vector<Level<double>> h64;         // FP64: all levels; MIXED: finest only
     std::vector<Level<float>> h32;          // MIXED: all levels
     double* inv = nullptr;                  // level-0 bordered inverse (27 x 27)
+    int dom = kDomSquare;                   // the domain: kDomSquare, or kDomL (common.cuh)
     int clev = 0;                           // coarsest level of the iteration (exact solve there)
     int cnb = 0;                            // clev > 0: size of its bordered system
     double* cinv = nullptr;                 // clev > 0: its inverse, cnb x cnb, float64
@@ -231,7 +232,7 @@ bool smooth_level(stokes_handle* h, Level<T>& lv, int steps, bool timed, bool sw
                                          lv.sinv, ou, op))
                 sw = !sw;
         } else {
-            launch_uzawa<T>(h->st, lv.n, lv.c, (T)P.tau, (T)P.sigma, xu, xp, lv.f, lv.g, lv.sinv, ou, op);
+            launch_uzawa<T>(h->st, lv.n, lv.c, (T)P.tau, (T)P.sigma, xu, xp, lv.f, lv.g, lv.sinv, ou, op, 32, 8, h->dom);
         }
         ev_end(h, k);
     }
@@ -278,10 +279,10 @@ void mg_cycle(stokes_handle* h, std::vector<Level<T>>& H, int l) {
     T* ru = sw ? lv.u : lv.tu;
     T* rp = sw ? lv.p : lv.tp;
     Level<T>& cl = H[l - 1];
-    launch_residual<T, T>(h->st, lv.n, lv.c, xu, xp, lv.f, lv.g, ru, rp, nullptr);
-    launch_restrict<T>(h->st, cl.n, ru, rp, cl.f, cl.g, cl.u, cl.p);   // and the coarse iterate := 0
+    launch_residual<T, T>(h->st, lv.n, lv.c, xu, xp, lv.f, lv.g, ru, rp, nullptr, nullptr, nullptr, h->dom);
+    launch_restrict<T>(h->st, cl.n, ru, rp, cl.f, cl.g, cl.u, cl.p, h->dom);   // and the coarse iterate := 0
     for (int r = 0; r < h->prm.gamma; ++r) mg_cycle(h, H, l - 1);
-    launch_prolong_add<T>(h->st, cl.n, cl.u, cl.p, xu, xp);
+    launch_prolong_add<T>(h->st, cl.n, cl.u, cl.p, xu, xp, h->dom);
     sw = smooth_level(h, lv, h->prm.nu_post, top, sw);
     if (sw) {   // odd number of ping-pong steps: bring the iterate back to (u, p)
         cudaMemcpyAsync(lv.u, lv.tu, 2 * lv.n2 * sizeof(T), cudaMemcpyDeviceToDevice, h->st);
@@ -301,7 +302,8 @@ void residual_norm_fin(stokes_handle* h, bool timed = false) {
         Level<float>& E = h->h32.back();
         launch_residual_df(h->st, F.n, F.c, F.u, F.p, F.f, F.g, F.tu, F.tp, E.f, E.g, h->partial);
     } else {
-        launch_residual<double, double>(h->st, F.n, F.c, F.u, F.p, F.f, F.g, F.tu, F.tp, h->partial);
+        launch_residual<double, double>(h->st, F.n, F.c, F.u, F.p, F.f, F.g, F.tu, F.tp, h->partial, nullptr, nullptr,
+                                        h->dom);
     }
     ev_end(h, k);
     launch_reduce(h->st, h->partial, cells_blocks(F.n), h->scal);
@@ -328,7 +330,7 @@ void record_step(stokes_handle* h) {
         launch_psub<double>(h->st, F.n, F.p, h->scal + 1);
     } else {
         mg_cycle<double>(h, h->h64, h->L - 1);
-        launch_pmean<double>(h->st, F.n, F.p, h->partial, h->scal + 1);
+        launch_pmean<double>(h->st, F.n, F.p, h->partial, h->scal + 1, h->dom);
         residual_norm_fin(h, true);
     }
 }
@@ -439,7 +441,7 @@ stokes_status rebuild_beta(stokes_handle* h) {
     const double beta = h->prm.beta;
     for (auto& lv : h->h64) {
         lv.c = make_coef<double>(lv.n, beta);
-        launch_schur_diag<double>(h->st, lv.n, lv.c, lv.sinv);
+        launch_schur_diag<double>(h->st, lv.n, lv.c, lv.sinv, h->dom);
     }
     for (auto& lv : h->h32) {
         lv.c = make_coef<float>(lv.n, beta);
@@ -463,7 +465,8 @@ stokes_status rebuild_beta(stokes_handle* h) {
     if (h->clev > 0) {
         // the bordered system of the coarsest level, assembled on the host, inverted on the device
         std::vector<double> M((size_t)h->cnb * h->cnb);
-        bordered_system(square_tables(), 1 << (h->clev + 1), beta, M.data());
+        if (h->dom == kDomL) lshape_bordered_system(beta, M.data());   // the L's level 0 (square level 1)
+        else bordered_system(square_tables(), 1 << (h->clev + 1), beta, M.data());
         CK(cudaMemcpyAsync(h->cinv, M.data(), M.size() * sizeof(double), cudaMemcpyHostToDevice, h->st));
         CK(launch_dense_inverse(h->st, h->cinv, h->cnb, h->cperm, h->ccol, h->cstat));
         int st = 0;
@@ -493,6 +496,11 @@ stokes_status copy_in(stokes_handle* h, const double* u, const double* p, const 
     CK(cudaMemcpyAsync(F.p, p, F.n1 * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
     CK(cudaMemcpyAsync(F.f, f, 2 * F.n2 * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
     CK(cudaMemcpyAsync(F.g, g, F.n1 * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    if (h->dom == kDomL) {   // entries outside the L are ignored: they are zero from here on
+        launch_mask_l(h->st, F.n, F.u, F.p);
+        launch_mask_l(h->st, F.n, F.f, F.g);
+        h->launches += 2;
+    }
     return STOKES_OK;
 }
 
@@ -528,6 +536,7 @@ void stokes_default_params(stokes_params* prm, int levels, double beta) {
     prm->precision = STOKES_FP64;
     prm->inner_cycles = 1;
     prm->coarse_level = 0;
+    prm->domain = STOKES_UNIT_SQUARE;
 }
 
 const char* stokes_status_str(stokes_status s) {
@@ -566,7 +575,12 @@ stokes_status stokes_setup(const stokes_params* prm, void* stream, stokes_handle
         (P.smoother != STOKES_UZAWA && P.smoother != STOKES_NORMAL_EQ) ||
         (P.precision != STOKES_FP64 && P.precision != STOKES_MIXED) ||
         (P.precision == STOKES_MIXED && P.inner_cycles < 1) || P.coarse_level < 0 ||
-        P.coarse_level > kMaxCoarseLevel || P.coarse_level > P.levels - 1)
+        P.coarse_level > kMaxCoarseLevel || P.coarse_level > P.levels - 1 ||
+        (P.domain != STOKES_UNIT_SQUARE && P.domain != STOKES_L_SHAPE))
+        return STOKES_ERR_BAD_ARG;
+    // the L-shaped domain: float64 Uzawa cycles, coarsest level 1 (the L's level 0)
+    if (P.domain == STOKES_L_SHAPE && (P.precision != STOKES_FP64 || P.smoother != STOKES_UZAWA ||
+                                       P.coarse_level != 1 || P.levels < 2))
         return STOKES_ERR_BAD_ARG;
     stokes_status s = ensure_weights();
     if (s != STOKES_OK) return s;
@@ -592,6 +606,7 @@ stokes_status stokes_setup(const stokes_params* prm, void* stream, stokes_handle
         return e;
     };
     init_mem(h->mem, h->st);
+    h->dom = P.domain == STOKES_L_SHAPE ? kDomL : kDomSquare;
     const int kfin = P.levels - 1;
     if (P.precision == STOKES_FP64) {
         h->h64.resize(P.levels);
@@ -808,7 +823,7 @@ stokes_status stokes_residual(stokes_handle* h, const double* u, const double* p
                               const double* g, double* ru, double* rp) {
     if (!h || !u || !p || !f || !g || !ru || !rp) return STOKES_ERR_BAD_ARG;
     Level<double>& F = h->fin();
-    launch_residual<double, double>(h->st, F.n, F.c, u, p, f, g, ru, rp, nullptr);
+    launch_residual<double, double>(h->st, F.n, F.c, u, p, f, g, ru, rp, nullptr, nullptr, nullptr, h->dom);
     h->launches += 1;
     CK(cudaGetLastError());
     return STOKES_OK;
@@ -818,7 +833,7 @@ stokes_status stokes_residual_norm(stokes_handle* h, const double* u, const doub
                                    const double* g, double* norm) {
     if (!h || !u || !p || !f || !g || !norm) return STOKES_ERR_BAD_ARG;
     Level<double>& F = h->fin();
-    launch_residual<double, double>(h->st, F.n, F.c, u, p, f, g, F.tu, F.tp, h->partial);
+    launch_residual<double, double>(h->st, F.n, F.c, u, p, f, g, F.tu, F.tp, h->partial, nullptr, nullptr, h->dom);
     launch_reduce(h->st, h->partial, cells_blocks(F.n), h->scal + 3);
     h->launches += 2;
     double v;
@@ -860,7 +875,7 @@ stokes_status stokes_smooth_f32(stokes_handle* h, float* u, float* p, const floa
 
 stokes_status stokes_restrict(stokes_handle* h, const double* fu, const double* fp, double* fc, double* gc) {
     if (!h || !fu || !fp || !fc || !gc || h->L < 2) return STOKES_ERR_BAD_ARG;
-    launch_restrict<double>(h->st, h->fin().n / 2, fu, fp, fc, gc);
+    launch_restrict<double>(h->st, h->fin().n / 2, fu, fp, fc, gc, nullptr, nullptr, h->dom);
     h->launches += 1;
     CK(cudaGetLastError());
     return STOKES_OK;
@@ -868,7 +883,7 @@ stokes_status stokes_restrict(stokes_handle* h, const double* fu, const double* 
 
 stokes_status stokes_prolong_add(stokes_handle* h, const double* uc, const double* pc, double* uf, double* pf) {
     if (!h || !uc || !pc || !uf || !pf || h->L < 2) return STOKES_ERR_BAD_ARG;
-    launch_prolong_add<double>(h->st, h->fin().n / 2, uc, pc, uf, pf);
+    launch_prolong_add<double>(h->st, h->fin().n / 2, uc, pc, uf, pf, h->dom);
     h->launches += 1;
     CK(cudaGetLastError());
     return STOKES_OK;
@@ -876,7 +891,7 @@ stokes_status stokes_prolong_add(stokes_handle* h, const double* uc, const doubl
 
 stokes_status stokes_load_vectors(stokes_handle* h, const double* f_nodal, const double* g_nodal, int project_g,
                                   double* f, double* g) {
-    if (!h || !f_nodal || !g_nodal || !f || !g) return STOKES_ERR_BAD_ARG;
+    if (!h || !f_nodal || !g_nodal || !f || !g || h->dom != kDomSquare) return STOKES_ERR_BAD_ARG;
     launch_load<double>(h->st, h->fin().n, h->mass, f_nodal, g_nodal, f, g, project_g, h->partial, h->scal + 4);
     h->launches += project_g ? 3 : 1;
     CK(cudaGetLastError());
@@ -925,7 +940,7 @@ stokes_status stokes_coarse_inverse(double beta, double* inv) {
 
 stokes_status stokes_euler_rhs(stokes_handle* h, const double* u_prev, const double* f_nodal, const double* g_nodal,
                                double* f, double* g) {
-    if (!h || !u_prev || !f_nodal || !g_nodal || !f || !g) return STOKES_ERR_BAD_ARG;
+    if (!h || !u_prev || !f_nodal || !g_nodal || !f || !g || h->dom != kDomSquare) return STOKES_ERR_BAD_ARG;
     const int n = h->fin().n;
     const size_t nvel = 2 * (size_t)(2 * n + 1) * (2 * n + 1);
     if (!h->euler_w) CK(h->mem.get(&h->euler_w, nvel * sizeof(double)));
@@ -937,7 +952,7 @@ stokes_status stokes_euler_rhs(stokes_handle* h, const double* u_prev, const dou
 }
 
 stokes_status stokes_make_consistent(stokes_handle* h, double* g) {
-    if (!h || !g) return STOKES_ERR_BAD_ARG;
+    if (!h || !g || h->dom != kDomSquare) return STOKES_ERR_BAD_ARG;
     launch_make_consistent(h->st, h->fin().n, g, h->partial, h->scal + 6);
     h->launches += 3;
     CK(cudaGetLastError());
@@ -945,7 +960,7 @@ stokes_status stokes_make_consistent(stokes_handle* h, double* g) {
 }
 
 stokes_status stokes_mass_dot(stokes_handle* h, const double* a, const double* b, double* dot) {
-    if (!h || !a || !b || !dot) return STOKES_ERR_BAD_ARG;
+    if (!h || !a || !b || !dot || h->dom != kDomSquare) return STOKES_ERR_BAD_ARG;
     const int n = h->fin().n;
     launch_mass_dot(h->st, n, h->mass, a, b, h->partial);
     launch_reduce(h->st, h->partial, cells_blocks(n), h->scal + 5);

@@ -247,6 +247,39 @@ __device__ __forceinline__ CellNodes cell_nodes(int i, int j, int n) {
     return c;
 }
 
+// The L-shaped domain (the unit square without its upper-right quadrant [1/2, 1]^2) on the square's
+// lattice: velocity nodes in the closed removed quadrant (lattice X >= N and Y >= N, its edges being
+// the re-entrant sides) are Dirichlet nodes, and vertices strictly inside it (i > N/2, j > N/2) are
+// not pressure unknowns.  Every other node keeps the square's rows: all triangles around a velocity
+// node strictly inside the L lie in the L.
+enum : int { kDomSquare = 0, kDomL = 1 };
+__host__ __device__ __forceinline__ bool l_masked_node(int X, int Y, int n) { return X >= n && Y >= n; }
+__host__ __device__ __forceinline__ bool l_masked_vertex(int i, int j, int n) { return 2 * i > n && 2 * j > n; }
+__device__ __forceinline__ CellNodes cell_nodes_dom(int i, int j, int n, int dom) {
+    CellNodes c = cell_nodes(i, j, n);
+    if (dom == kDomL) {
+        c.v = c.v && !l_masked_node(2 * i, 2 * j, n);
+        c.h = c.h && !l_masked_node(2 * i + 1, 2 * j, n);
+        c.e = c.e && !l_masked_node(2 * i, 2 * j + 1, n);
+        c.c = c.c && !l_masked_node(2 * i + 1, 2 * j + 1, n);
+    }
+    return c;
+}
+// w_i = int_Omega psi_i for the square or the L (squares in the removed quadrant do not count)
+__device__ __forceinline__ double vertex_weight_dom(int i, int j, int n, int dom) {
+    int cnt = 0;
+#pragma unroll
+    for (int SQ = 0; SQ < 4; ++SQ) {
+        const int si = i - (SQ & 1), sj = j - (SQ >> 1);
+        if (si < 0 || sj < 0 || si >= n || sj >= n) continue;
+        if (dom == kDomL && 2 * si >= n && 2 * sj >= n) continue;
+        const int o = orient(si, sj, n), node = corner_node(SQ);
+        cnt += ((tri_mask(o, 0) >> node) & 1u) + ((tri_mask(o, 1) >> node) & 1u);
+    }
+    const double h = 1.0 / n;
+    return cnt * h * h / 6.0;
+}
+
 template <typename T> struct Vec2;
 template <> struct Vec2<float> { using type = float2; };
 template <> struct Vec2<double> { using type = double2; };

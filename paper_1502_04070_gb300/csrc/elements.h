@@ -29,5 +29,8 @@ bool coarse_inverse(const SquareMatrices& S, double beta, double inv[27 * 27]);
 // bordered with the zero-mean pressure condition (unknown order as in coarse_inverse).
 int bordered_size(int n);
 void bordered_system(const SquareMatrices& S, int n, double beta, double* M);
+// Level 0 of the L-shaped hierarchy (the square's level with N = 4 without its upper-right quadrant)
+// in the same order and size (n = 4), with identity rows at the square's unknowns outside the L.
+void lshape_bordered_system(double beta, double* M);
 
 }  // namespace smg

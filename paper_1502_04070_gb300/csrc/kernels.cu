@@ -5,6 +5,7 @@
 // the cell's stencil class (the orientations of its four squares; warp-uniform except where a warp
 // meets one of the mid-lines x = 1/2, y = 1/2), with structurally-zero entries removed at compile
 // time.  Blocks whose cells all lie at least two cells inside the boundary read without any test.
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 
@@ -46,7 +47,7 @@ __global__ void __launch_bounds__(NT) k_residual(int n, const __grid_constant__ 
                                                  const T* __restrict__ f, const T* __restrict__ g,
                                                  TO* __restrict__ ru, TO* __restrict__ rp,
                                                  double* __restrict__ partial, float* __restrict__ ru2,
-                                                 float* __restrict__ rp2) {
+                                                 float* __restrict__ rp2, int dom) {
     pdl_wait();
     CELL_INDEX
     const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
@@ -59,7 +60,7 @@ __global__ void __launch_bounds__(NT) k_residual(int n, const __grid_constant__ 
         else
             cell_apply_auto<true, true, true, false, true>(i, j, n, c, gview(u, 2 * n + 1), gview(u + n2, 2 * n + 1),
                                                            gview(p, n + 1), a);
-        const CellNodes cn = cell_nodes(i, j, n);
+        const CellNodes cn = cell_nodes_dom(i, j, n, dom);
         const int ld = 2 * n + 1;
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
@@ -80,7 +81,7 @@ __global__ void __launch_bounds__(NT) k_residual(int n, const __grid_constant__ 
             }
         }
         const size_t vi = (size_t)j * (n + 1) + i;
-        const T r = g[vi] - a.bu;
+        const T r = (dom == kDomL && l_masked_vertex(i, j, n)) ? T(0) : g[vi] - a.bu;
         rp[vi] = (TO)r;
         if (rp2) rp2[vi] = (float)r;
         ss += (double)r * (double)r;
@@ -96,7 +97,7 @@ __global__ void __launch_bounds__(NT) k_residual(int n, const __grid_constant__ 
 template <typename T>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 1) k_uzawa_u(int n, const __grid_constant__ OpCoef<T> c, T tau,
                                                 const T* __restrict__ u, const T* __restrict__ p,
-                                                const T* __restrict__ f, T* __restrict__ uh) {
+                                                const T* __restrict__ f, T* __restrict__ uh, int dom) {
     pdl_wait();
     CELL_INDEX
     if (!active) return;
@@ -108,7 +109,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 1) k_uzawa_u(int n, c
     else
         cell_apply_auto<true, true, false, true, true>(i, j, n, c, gview(u, 2 * n + 1), gview(u + n2, 2 * n + 1),
                                                        gview(p, n + 1), a);
-    const CellNodes cn = cell_nodes(i, j, n);
+    const CellNodes cn = cell_nodes_dom(i, j, n, dom);
     const int ld = 2 * n + 1;
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
@@ -153,7 +154,7 @@ __global__ void __launch_bounds__(NT) k_uzawa_p(int n, const __grid_constant__ O
 template <typename T>
 __global__ void __launch_bounds__(NT) k_uzawa_u2(int n, const __grid_constant__ OpCoef<T> c, T tau,
                                                  const T* __restrict__ uh, const T* __restrict__ dp,
-                                                 T* __restrict__ u) {
+                                                 T* __restrict__ u, int dom) {
     pdl_wait();
     CELL_INDEX
     if (!active) return;
@@ -165,7 +166,7 @@ __global__ void __launch_bounds__(NT) k_uzawa_u2(int n, const __grid_constant__ 
     else
         cell_apply_auto<false, true, false, true, false>(i, j, n, c, gview((const T*)nullptr, 2 * n + 1),
                                                          gview((const T*)nullptr, 2 * n + 1), gview(dp, n + 1), a);
-    const CellNodes cn = cell_nodes(i, j, n);
+    const CellNodes cn = cell_nodes_dom(i, j, n, dom);
     const int ld = 2 * n + 1;
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
@@ -186,11 +187,12 @@ __global__ void __launch_bounds__(NT) k_uzawa_u2(int n, const __grid_constant__ 
 
 template <typename T>
 void launch_uzawa(cudaStream_t s, int n, const OpCoef<T>& c, T tau, T sigma, T* u, T* p, const T* f,
-                  const T* g, const T* sinv, T* uh, T* dp, int bx, int by) {
+                  const T* g, const T* sinv, T* uh, T* dp, int bx, int by, int dom) {
     const dim3 blk(bx, by), grid((n + 1 + bx - 1) / bx, (n + 1 + by - 1) / by);
-    launch_pdl(k_uzawa_u<T>, grid, blk, 0, s, n, c, tau, u, p, f, uh);
+    launch_pdl(k_uzawa_u<T>, grid, blk, 0, s, n, c, tau, u, p, f, uh, dom);
+    // dp = 0 where Shat^{-1} = 0: on the L the vertices outside it
     launch_pdl(k_uzawa_p<T>, grid, blk, 0, s, n, c, sigma, uh, p, g, sinv, dp);
-    launch_pdl(k_uzawa_u2<T>, grid, blk, 0, s, n, c, tau, uh, dp, u);
+    launch_pdl(k_uzawa_u2<T>, grid, blk, 0, s, n, c, tau, uh, dp, u, dom);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -253,15 +255,15 @@ template <typename T>
 void launch_normal_eq(cudaStream_t s, int n, const OpCoef<T>& c, T tau, T* u, T* p, const T* f,
                       const T* g, const T* sinv, T* zu, T* zp) {
     const dim3 grid = cells_grid(n), blk(BX, BY);
-    launch_pdl(k_residual<T, T>, grid, blk, 0, s, n, c, u, p, f, g, zu, zp, nullptr, nullptr, nullptr);
+    launch_pdl(k_residual<T, T>, grid, blk, 0, s, n, c, u, p, f, g, zu, zp, nullptr, nullptr, nullptr, (int)kDomSquare);
     launch_pdl(k_scale_L<T>, grid, blk, 0, s, n, c, zu, zp, sinv);
     launch_pdl(k_normal_update<T>, grid, blk, 0, s, n, c, tau, zu, zp, sinv, u, p);
 }
 
 template <typename T, typename TO>
 void launch_residual(cudaStream_t s, int n, const OpCoef<T>& c, const T* u, const T* p, const T* f,
-                     const T* g, TO* ru, TO* rp, double* partial, float* ru2, float* rp2) {
-    launch_pdl(k_residual<T, TO>, cells_grid(n), dim3(BX, BY), 0, s, n, c, u, p, f, g, ru, rp, partial, ru2, rp2);
+                     const T* g, TO* ru, TO* rp, double* partial, float* ru2, float* rp2, int dom) {
+    launch_pdl(k_residual<T, TO>, cells_grid(n), dim3(BX, BY), 0, s, n, c, u, p, f, g, ru, rp, partial, ru2, rp2, dom);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -326,7 +328,8 @@ __device__ __forceinline__ void restrict_visit(int I, int J, int nc, const T* __
 // coarse cell (i, j) of level nc: its owned coarse velocity nodes and vertex
 template <bool LDG, typename T>
 __device__ __forceinline__ void restrict_cell(int i, int j, int nc, const T* __restrict__ ru, const T* __restrict__ rp,
-                                              T* __restrict__ fc, T* __restrict__ gc, const XferLayout& lay) {
+                                              T* __restrict__ fc, T* __restrict__ gc, const XferLayout& lay,
+                                              int dom = kDomSquare) {
     T acc[2][4];
 #pragma unroll
     for (int s = 0; s < 4; ++s) acc[0][s] = acc[1][s] = T(0);
@@ -334,7 +337,7 @@ __device__ __forceinline__ void restrict_cell(int i, int j, int nc, const T* __r
     restrict_visit<1, LDG>(i, j, nc, ru, acc, lay);
     restrict_visit<2, LDG>(i, j, nc, ru, acc, lay);
     restrict_visit<3, LDG>(i, j, nc, ru, acc, lay);
-    const CellNodes cn = cell_nodes(i, j, nc);
+    const CellNodes cn = cell_nodes_dom(i, j, nc, dom);
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
         if (!slot_exists(cn, s)) continue;
@@ -362,19 +365,19 @@ __device__ __forceinline__ void restrict_cell(int i, int j, int nc, const T* __r
     if (x > 0 && y > 0 && orient(i - 1, j - 1, nc) == 0) half += rp[(y - 1) * ldf + x - 1];
     if (x < nf && y > 0 && orient(i, j - 1, nc) == 1) half += rp[(y - 1) * ldf + x + 1];
     if (x > 0 && y < nf && orient(i - 1, j, nc) == 1) half += rp[(y + 1) * ldf + x - 1];
-    gc[j * lay.ldpc + i] = s + T(0.5) * half;
+    gc[j * lay.ldpc + i] = (dom == kDomL && l_masked_vertex(i, j, nc)) ? T(0) : s + T(0.5) * half;
 }
 
 // With uc, pc given, the coarse iterate is also set to zero (the coarse correction starts from 0).
 template <typename T>
 __global__ void __launch_bounds__(NT) k_restrict(int nc, const T* __restrict__ ru, const T* __restrict__ rp,
                                                  T* __restrict__ fc, T* __restrict__ gc, T* __restrict__ uc,
-                                                 T* __restrict__ pc) {
+                                                 T* __restrict__ pc, int dom) {
     pdl_wait();
     const int n = nc;
     CELL_INDEX
     if (!active) return;
-    restrict_cell<true>(i, j, nc, ru, rp, fc, gc, dense_layout(nc));
+    restrict_cell<true>(i, j, nc, ru, rp, fc, gc, dense_layout(nc), dom);
     if (uc) {
         const CellNodes cn = cell_nodes(i, j, nc);
         const int ldc = 2 * nc + 1, n2c = ldc * ldc;
@@ -392,8 +395,8 @@ __global__ void __launch_bounds__(NT) k_restrict(int nc, const T* __restrict__ r
 }
 
 template <typename T>
-void launch_restrict(cudaStream_t s, int nc, const T* ru, const T* rp, T* fc, T* gc, T* uc, T* pc) {
-    launch_pdl(k_restrict<T>, cells_grid(nc), dim3(BX, BY), 0, s, nc, ru, rp, fc, gc, uc, pc);
+void launch_restrict(cudaStream_t s, int nc, const T* ru, const T* rp, T* fc, T* gc, T* uc, T* pc, int dom) {
+    launch_pdl(k_restrict<T>, cells_grid(nc), dim3(BX, BY), 0, s, nc, ru, rp, fc, gc, uc, pc, dom);
 }
 
 // Prolongation (Sec. 3, canonical embedding): every fine point owned by coarse square (I, J) is
@@ -401,7 +404,8 @@ void launch_restrict(cudaStream_t s, int nc, const T* ru, const T* rp, T* fc, T*
 // averages along coarse edges.
 template <bool LDG, typename T>
 __device__ __forceinline__ void prolong_cell(int i, int j, int nc, const T* __restrict__ uc, const T* __restrict__ pc,
-                                             T* __restrict__ u, T* __restrict__ p, const XferLayout& lay) {
+                                             T* __restrict__ u, T* __restrict__ p, const XferLayout& lay,
+                                             int dom = kDomSquare) {
     const int nf = 2 * nc;
     if (i < nc && j < nc) {
         T z[2][9];
@@ -417,7 +421,7 @@ __device__ __forceinline__ void prolong_cell(int i, int j, int nc, const T* __re
 #pragma unroll
             for (int fa = 0; fa < 4; ++fa) {
                 const int X = 4 * i + fa, Y = 4 * j + fb;
-                if (!interior2(X, Y, nf)) continue;
+                if (!interior2(X, Y, nf) || (dom == kDomL && l_masked_node(X, Y, nf))) continue;
                 T sx = T(0), sy = T(0);
 #pragma unroll
                 for (int L = 0; L < 9; ++L) {
@@ -433,10 +437,12 @@ __device__ __forceinline__ void prolong_cell(int i, int j, int nc, const T* __re
     const int ldp = lay.ldpc, ldpf = lay.ldpf;
     auto P = [&](int a, int b) { return ldv<LDG>(pc + (b * ldp + a)); };
     const T p00 = P(i, j);
-    p[(2 * j) * ldpf + 2 * i] += p00;
-    if (i < nc) p[(2 * j) * ldpf + 2 * i + 1] += T(0.5) * (p00 + P(i + 1, j));
-    if (j < nc) p[(2 * j + 1) * ldpf + 2 * i] += T(0.5) * (p00 + P(i, j + 1));
-    if (i < nc && j < nc) {
+    // on the L, fine vertices strictly inside the removed quadrant keep their zero
+    auto live = [&](int x, int y) { return !(dom == kDomL && l_masked_vertex(x, y, nf)); };
+    if (live(2 * i, 2 * j)) p[(2 * j) * ldpf + 2 * i] += p00;
+    if (i < nc && live(2 * i + 1, 2 * j)) p[(2 * j) * ldpf + 2 * i + 1] += T(0.5) * (p00 + P(i + 1, j));
+    if (j < nc && live(2 * i, 2 * j + 1)) p[(2 * j + 1) * ldpf + 2 * i] += T(0.5) * (p00 + P(i, j + 1));
+    if (i < nc && j < nc && live(2 * i + 1, 2 * j + 1)) {
         const T d = orient(i, j, nc) == 0 ? p00 + P(i + 1, j + 1) : P(i + 1, j) + P(i, j + 1);
         p[(2 * j + 1) * ldpf + 2 * i + 1] += T(0.5) * d;
     }
@@ -444,18 +450,18 @@ __device__ __forceinline__ void prolong_cell(int i, int j, int nc, const T* __re
 
 template <typename T>
 __global__ void __launch_bounds__(NT) k_prolong(int nc, const T* __restrict__ uc, const T* __restrict__ pc,
-                                                T* __restrict__ u, T* __restrict__ p) {
+                                                T* __restrict__ u, T* __restrict__ p, int dom) {
     pdl_wait();
     const int n = nc;
     CELL_INDEX
     if (!active) return;
-    prolong_cell<true>(i, j, nc, uc, pc, u, p, dense_layout(nc));
+    prolong_cell<true>(i, j, nc, uc, pc, u, p, dense_layout(nc), dom);
     pdl_trigger();
 }
 
 template <typename T>
-void launch_prolong_add(cudaStream_t s, int nc, const T* uc, const T* pc, T* u, T* p) {
-    launch_pdl(k_prolong<T>, cells_grid(nc), dim3(BX, BY), 0, s, nc, uc, pc, u, p);
+void launch_prolong_add(cudaStream_t s, int nc, const T* uc, const T* pc, T* u, T* p, int dom) {
+    launch_pdl(k_prolong<T>, cells_grid(nc), dim3(BX, BY), 0, s, nc, uc, pc, u, p, dom);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -521,10 +527,17 @@ __device__ double diagA_at(int X, int Y, int n, const OpCoef<double>& c) {
     return d;
 }
 
+// On the L the sum runs over the L's velocity unknowns only (their B coefficients are the square's:
+// all squares around such a node lie in the L), and Shat^{-1} = 0 at vertices outside the L.
 template <typename T>
-__global__ void __launch_bounds__(NT) k_schur(int n, const __grid_constant__ OpCoef<double> c, T* __restrict__ sinv) {
+__global__ void __launch_bounds__(NT) k_schur(int n, const __grid_constant__ OpCoef<double> c, T* __restrict__ sinv,
+                                              int dom) {
     CELL_INDEX
     if (!active) return;
+    if (dom == kDomL && l_masked_vertex(i, j, n)) {
+        sinv[(size_t)j * (n + 1) + i] = T(0);
+        return;
+    }
     double bx[5][5], by[5][5];
     for (int b = 0; b < 5; ++b)
         for (int a = 0; a < 5; ++a) bx[b][a] = by[b][a] = 0.0;
@@ -542,36 +555,42 @@ __global__ void __launch_bounds__(NT) k_schur(int n, const __grid_constant__ OpC
     for (int py = 0; py < 5; ++py)
         for (int px = 0; px < 5; ++px) {
             const int X = 2 * i - 2 + px, Y = 2 * j - 2 + py;
-            if (!interior2(X, Y, n)) continue;
+            if (!interior2(X, Y, n) || (dom == kDomL && l_masked_node(X, Y, n))) continue;
             s += (bx[py][px] * bx[py][px] + by[py][px] * by[py][px]) / diagA_at(X, Y, n, c);
         }
     sinv[(size_t)j * (n + 1) + i] = (T)(1.0 / s);
 }
 
 template <typename T>
-void launch_schur_diag(cudaStream_t s, int n, const OpCoef<double>& c, T* sinv) {
-    k_schur<T><<<cells_grid(n), dim3(BX, BY), 0, s>>>(n, c, sinv);
+void launch_schur_diag(cudaStream_t s, int n, const OpCoef<double>& c, T* sinv, int dom) {
+    k_schur<T><<<cells_grid(n), dim3(BX, BY), 0, s>>>(n, c, sinv, dom);
 }
 
 // ------------------------------------------------------------------------------------------
 
 template <typename T>
-__global__ void __launch_bounds__(NT) k_pmean_partial(int n, const T* __restrict__ p, double* __restrict__ partial) {
+__global__ void __launch_bounds__(NT) k_pmean_partial(int n, const T* __restrict__ p, double* __restrict__ partial,
+                                                      int dom) {
     pdl_wait();
     CELL_INDEX
     double v = 0.0;
-    if (active) v = vertex_weight(i, j, n) * (double)p[(size_t)j * (n + 1) + i];
+    if (active) v = vertex_weight_dom(i, j, n, dom) * (double)p[(size_t)j * (n + 1) + i];
     const double t = block_sum2d(v, tid);
     if (tid == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = t;
     pdl_trigger();
 }
 
+// p -= (w^T p) / |Omega| at the pressure unknowns; |Omega| = sum_i w_i = 1 (square) or 3/4 (L)
 template <typename T>
-__global__ void __launch_bounds__(NT) k_psub(int n, T* __restrict__ p, const double* __restrict__ scalar) {
+__global__ void __launch_bounds__(NT) k_psub(int n, T* __restrict__ p, const double* __restrict__ scalar, int dom) {
     pdl_wait();
     CELL_INDEX
     if (!active) return;
-    p[(size_t)j * (n + 1) + i] -= (T)(*scalar);   // sum_i w_i = |Omega| = 1
+    if (dom == kDomL) {
+        if (!l_masked_vertex(i, j, n)) p[(size_t)j * (n + 1) + i] -= (T)(*scalar / 0.75);
+    } else {
+        p[(size_t)j * (n + 1) + i] -= (T)(*scalar);
+    }
     pdl_trigger();
 }
 
@@ -596,16 +615,16 @@ cudaError_t launch_reduce(cudaStream_t s, const double* partial, int count, doub
 }
 
 template <typename T>
-void launch_pmean(cudaStream_t s, int n, T* p, double* partial, double* scalar) {
+void launch_pmean(cudaStream_t s, int n, T* p, double* partial, double* scalar, int dom) {
     const dim3 grid = cells_grid(n), blk(BX, BY);
-    launch_pdl(k_pmean_partial<T>, grid, blk, 0, s, n, p, partial);
+    launch_pdl(k_pmean_partial<T>, grid, blk, 0, s, n, p, partial, dom);
     launch_pdl(k_reduce, 1, 1024, 0, s, partial, grid.x * grid.y, scalar);
-    launch_pdl(k_psub<T>, grid, blk, 0, s, n, p, scalar);
+    launch_pdl(k_psub<T>, grid, blk, 0, s, n, p, scalar, dom);
 }
 
 template <typename T>
 void launch_psub(cudaStream_t s, int n, T* p, const double* scalar) {
-    launch_pdl(k_psub<T>, cells_grid(n), dim3(BX, BY), 0, s, n, p, scalar);
+    launch_pdl(k_psub<T>, cells_grid(n), dim3(BX, BY), 0, s, n, p, scalar, (int)kDomSquare);
 }
 template void launch_psub<double>(cudaStream_t, int, double*, const double*);
 
@@ -782,30 +801,51 @@ void launch_add_f32(cudaStream_t s, size_t count, const float* e, double* x) {
     k_add_f32<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(count, e, x);
 }
 
+// On the L: zero the entries of velocity arrays at nodes outside the L's unknowns' closure (the closed
+// removed quadrant) and of vertex arrays at vertices strictly inside it; either pointer pair may be null.
+__global__ void k_mask_l(int n, double* __restrict__ u, double* __restrict__ p) {
+    const int ld = 2 * n + 1, n2 = ld * ld;
+    const int stride = gridDim.x * blockDim.x;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n2; k += stride) {
+        const int X = k % ld, Y = k / ld;
+        if (l_masked_node(X, Y, n) && u) {
+            u[k] = 0.0;
+            u[n2 + k] = 0.0;
+        }
+        if (p && X <= n && Y <= n && l_masked_vertex(X, Y, n)) p[Y * (n + 1) + X] = 0.0;
+    }
+}
+
+void launch_mask_l(cudaStream_t s, int n, double* u, double* p) {
+    const int ld = 2 * n + 1;
+    const int blocks = std::min((ld * ld + 255) / 256, 4096);
+    k_mask_l<<<blocks, 256, 0, s>>>(n, u, p);
+}
+
 #include "coarse_cycle.cuh"
 
 // ------------------------------------------------------------------------------------------
 #define INST(T)                                                                                         \
     template void launch_uzawa<T>(cudaStream_t, int, const OpCoef<T>&, T, T, T*, T*, const T*, const T*, \
-                                  const T*, T*, T*, int, int);                                                      \
+                                  const T*, T*, T*, int, int, int);                                                 \
     template void launch_normal_eq<T>(cudaStream_t, int, const OpCoef<T>&, T, T*, T*, const T*, const T*, \
                                       const T*, T*, T*);                                                  \
-    template void launch_restrict<T>(cudaStream_t, int, const T*, const T*, T*, T*, T*, T*);                      \
-    template void launch_prolong_add<T>(cudaStream_t, int, const T*, const T*, T*, T*);                   \
+    template void launch_restrict<T>(cudaStream_t, int, const T*, const T*, T*, T*, T*, T*, int);                 \
+    template void launch_prolong_add<T>(cudaStream_t, int, const T*, const T*, T*, T*, int);              \
     template void launch_coarse_solve<T>(cudaStream_t, const double*, const T*, const T*, T*, T*);        \
-    template void launch_schur_diag<T>(cudaStream_t, int, const OpCoef<double>&, T*);                     \
-    template void launch_pmean<T>(cudaStream_t, int, T*, double*, double*);                               \
+    template void launch_schur_diag<T>(cudaStream_t, int, const OpCoef<double>&, T*, int);                \
+    template void launch_pmean<T>(cudaStream_t, int, T*, double*, double*, int);                          \
     template void launch_load<T>(cudaStream_t, int, const MassCoef<T>&, const T*, const T*, T*, T*, int,  \
                                  double*, double*);
 INST(float)
 INST(double)
 template void launch_residual<double, double>(cudaStream_t, int, const OpCoef<double>&, const double*,
                                               const double*, const double*, const double*, double*, double*,
-                                              double*, float*, float*);
+                                              double*, float*, float*, int);
 template void launch_residual<float, float>(cudaStream_t, int, const OpCoef<float>&, const float*, const float*,
-                                            const float*, const float*, float*, float*, double*, float*, float*);
+                                            const float*, const float*, float*, float*, double*, float*, float*, int);
 template void launch_residual<double, float>(cudaStream_t, int, const OpCoef<double>&, const double*,
                                              const double*, const double*, const double*, float*, float*,
-                                             double*, float*, float*);
+                                             double*, float*, float*, int);
 
 }  // namespace smg

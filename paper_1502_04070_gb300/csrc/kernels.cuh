@@ -15,9 +15,11 @@ cudaError_t upload_transfer_weights(const double* P2 /* [2][9][5][5] */);
 
 // r = F - A x with per-block partial sums of r.r (over unknowns) in `partial` (may be null) and an
 // optional float32 copy of r in (ru2, rp2).
+// dom: kDomSquare or kDomL (common.cuh: on the L, the nodes outside it are not unknowns)
 template <typename T, typename TO>
 void launch_residual(cudaStream_t s, int n, const OpCoef<T>& c, const T* u, const T* p, const T* f,
-                     const T* g, TO* ru, TO* rp, double* partial, float* ru2 = nullptr, float* rp2 = nullptr);
+                     const T* g, TO* ru, TO* rp, double* partial, float* ru2 = nullptr, float* rp2 = nullptr,
+                     int dom = kDomSquare);
 
 
 // Uzawa step (Sec. 4), three kernels:
@@ -26,7 +28,7 @@ void launch_residual(cudaStream_t s, int n, const OpCoef<T>& c, const T* u, cons
 //   u  = uh - tau Ahat^{-1} B^T dp
 template <typename T>
 void launch_uzawa(cudaStream_t s, int n, const OpCoef<T>& c, T tau, T sigma, T* u, T* p, const T* f,
-                  const T* g, const T* sinv, T* uh, T* dp, int bx = 32, int by = 8);
+                  const T* g, const T* sinv, T* uh, T* dp, int bx = 32, int by = 8, int dom = kDomSquare);
 
 // Refinement update (see refine.cu): float32 correction e, float64 iterate x, residual r stored as
 // (hi, lo) float pairs in the 8-byte slots of a float64 array:
@@ -88,15 +90,19 @@ void launch_normal_eq(cudaStream_t s, int n, const OpCoef<T>& c, T tau, T* u, T*
 // (fc, gc) = I^T (ru, rp): fine level n = 2 nc.
 template <typename T>
 void launch_restrict(cudaStream_t s, int nc, const T* ru, const T* rp, T* fc, T* gc, T* uc = nullptr,
-                     T* pc = nullptr);   // uc, pc: optional coarse iterate set to zero
+                     T* pc = nullptr, int dom = kDomSquare);   // uc, pc: optional coarse iterate set to zero
 
 // (u, p) += I (uc, pc)
 template <typename T>
-void launch_prolong_add(cudaStream_t s, int nc, const T* uc, const T* pc, T* u, T* p);
+void launch_prolong_add(cudaStream_t s, int nc, const T* uc, const T* pc, T* u, T* p, int dom = kDomSquare);
 
 // level-0 exact solve with the bordered inverse (27 x 27, float64)
 template <typename T>
 void launch_coarse_solve(cudaStream_t s, const double* inv, const T* f, const T* g, T* u, T* p);
+
+// The L-shaped domain: zero the entries outside the L (velocity: the closed removed quadrant; vertices:
+// strictly inside it) of a float64 velocity array u and / or vertex array p (either may be null).
+void launch_mask_l(cudaStream_t s, int n, double* u, double* p);
 
 // Exact solve on a coarsest level c > 0 (dense.cu): in-place float64 inverse of the bordered
 // system (row-major nb x nb, device; perm, col, status device scratch; *status != 0 = singular), and
@@ -109,11 +115,11 @@ constexpr int kMaxCoarseLevel = 3;   // N = 16: a bordered system of 2212 unknow
 
 // Shat^{-1} per vertex (float64 computation, stored as T)
 template <typename T>
-void launch_schur_diag(cudaStream_t s, int n, const OpCoef<double>& c, T* sinv);
+void launch_schur_diag(cudaStream_t s, int n, const OpCoef<double>& c, T* sinv, int dom = kDomSquare);
 
 // p <- p - sum_i w_i p_i  (w = M_P 1, sum w = 1): partial sums then subtraction
 template <typename T>
-void launch_pmean(cudaStream_t s, int n, T* p, double* partial, double* scalar);
+void launch_pmean(cudaStream_t s, int n, T* p, double* partial, double* scalar, int dom = kDomSquare);
 
 // out[0] = sum of partial[0..count); returns the launch's own status
 cudaError_t launch_reduce(cudaStream_t s, const double* partial, int count, double* out);

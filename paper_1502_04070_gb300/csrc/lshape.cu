@@ -80,6 +80,70 @@ const SquareMatrices& squares_l() {
 
 }  // namespace
 
+namespace smg {
+
+// Level 0 of the L-shaped hierarchy (the square's level with N = 4 without the upper-right quadrant)
+// in the square's unknown order of bordered_system (size bordered_size(4) = 124): the system of
+// eq. gen:bil:mv over the 12 squares of the L, the L's pressure weights in the border, and identity
+// rows and columns at the square's unknowns that are not the L's (velocity nodes on the re-entrant
+// sides or in the removed quadrant, vertices strictly inside it), so that the solution is zero there
+// when the right-hand side is.
+void lshape_bordered_system(double beta, double* M) {
+    const SquareMatrices& S = squares_l();
+    const int n = 4, nm = 2 * n - 1, nv = nm * nm, nb = bordered_size(n);
+    const double h = 1.0 / n;
+    std::memset(M, 0, sizeof(double) * (size_t)nb * nb);
+    auto at = [&](int r, int c) -> double& { return M[(size_t)r * nb + c]; };
+    auto vidx = [&](int c, int X, int Y) -> int {
+        if (!l_interior(X, Y, n)) return -1;
+        return c * nv + (Y - 1) * nm + (X - 1);
+    };
+    auto pidx = [&](int x, int y) { return 2 * nv + y * (n + 1) + x; };
+    for (int b = 0; b < n; ++b)
+        for (int a = 0; a < n; ++a) {
+            if (a >= n / 2 && b >= n / 2) continue;                    // the removed quadrant
+            const int o = ((a < n / 2) != (b < n / 2)) ? 1 : 0;
+            for (int l = 0; l < 9; ++l)
+                for (int m = 0; m < 9; ++m) {
+                    const double v = S.K[o][l][m] + beta * h * h * S.M[o][l][m];
+                    for (int c = 0; c < 2; ++c) {
+                        const int r = vidx(c, 2 * a + l % 3, 2 * b + l / 3), q = vidx(c, 2 * a + m % 3, 2 * b + m / 3);
+                        if (r >= 0 && q >= 0) at(r, q) += v;
+                    }
+                }
+            for (int q = 0; q < 4; ++q) {
+                const int pr = pidx(a + q % 2, b + q / 2);
+                for (int m = 0; m < 9; ++m) {
+                    const int cx = vidx(0, 2 * a + m % 3, 2 * b + m / 3), cy = vidx(1, 2 * a + m % 3, 2 * b + m / 3);
+                    if (cx >= 0) {
+                        at(pr, cx) += h * S.Bx[o][q][m];
+                        at(cx, pr) += h * S.Bx[o][q][m];
+                    }
+                    if (cy >= 0) {
+                        at(pr, cy) += h * S.By[o][q][m];
+                        at(cy, pr) += h * S.By[o][q][m];
+                    }
+                }
+                double wq = 0.0;
+                for (int r = 0; r < 4; ++r) wq += h * h * S.MP[o][q][r];
+                at(pr, nb - 1) += wq;
+                at(nb - 1, pr) += wq;
+            }
+        }
+    for (int c = 0; c < 2; ++c)
+        for (int Y = 1; Y < 2 * n; ++Y)
+            for (int X = 1; X < 2 * n; ++X)
+                if (!l_interior(X, Y, n)) {
+                    const int r = c * nv + (Y - 1) * nm + (X - 1);
+                    at(r, r) = 1.0;
+                }
+    for (int y = 0; y <= n; ++y)
+        for (int x = 0; x <= n; ++x)
+            if (2 * x > n && 2 * y > n) at(pidx(x, y), pidx(x, y)) = 1.0;
+}
+
+}  // namespace smg
+
 extern "C" stokes_status stokes_lshape_vertex_rows(int levels, int kind, double* mbx, double* mby, double* w) {
     if (levels < 2 || levels > 13 || kind < 0 || kind >= kKinds || !mbx || !mby || !w) return STOKES_ERR_BAD_ARG;
     vertex_rows(squares_l(), 1 << levels, kind, mbx, mby, w);

@@ -14,6 +14,7 @@ from . import _binding as B
 
 _SMOOTHERS = {"uzawa": B.UZAWA, "normal": B.NORMAL_EQ}
 _PREC = {"fp64": B.FP64, "mixed": B.MIXED}
+_DOMAINS = {"square": B.UNIT_SQUARE, "lshape": B.L_SHAPE}
 
 
 class Report:
@@ -42,8 +43,8 @@ class Solver:
     """Coupled multigrid solver for [A + beta M, B^T; B, 0] on level k = levels - 1."""
 
     def __init__(self, levels: int, beta: float, *, nu_pre=3, nu_post=3, tau=None, sigma=0.8,
-                 smoother="uzawa", gamma=1, precision="fp64", inner_cycles=1, coarse_level=0, stream=None,
-                 device=None):
+                 smoother="uzawa", gamma=1, precision="fp64", inner_cycles=1, coarse_level=0, domain="square",
+                 stream=None, device=None):
         self._lib = B.load()
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         prm = B.Params()
@@ -56,6 +57,7 @@ class Solver:
         prm.precision = _PREC[precision]
         prm.inner_cycles = inner_cycles
         prm.coarse_level = coarse_level
+        prm.domain = _DOMAINS[domain]
         self.params = prm
         self.levels = levels
         self.beta = float(beta)
