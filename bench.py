@@ -16,7 +16,13 @@ Also measured, as parsed keys of the same line:
                (h-robustness), beside the oracle's counts;
   batch     -- 256 independent solves, k uniform in 4..8, beta log-uniform in [1e-2, 1e8], one launch;
   small     -- h = 1/32 (k = 4), beta = 1, plain float64 V(3,3) to 1e-10: time per solve;
-  adjoint   -- h = 1/1024 (k = 9), beta = 1e3, L = 1/2 ||u - u_target||_M^2: forward + backward.
+  adjoint   -- h = 1/1024 (k = 9), beta = 1e3, L = 1/2 ||u - u_target||_M^2: forward + backward;
+  timestep  -- implicit Euler steps at h = 1/512 (beta = 1/dt): host-driven steps, the same steps as
+               one CUDA-graph launch, and 8 trajectories with their own step lengths in one launch;
+  lshape    -- the L-shaped domain (square without [1/2, 1]^2) at h = 1/512, float64 V and W cycles.
+
+--oracle-batch N times the oracle (CPU) on N instances of the batch workload across all host cores
+(a process pool, one instance per task) and prints that one JSON line instead.
 
 Metric: unknowns solved per second (DoF/s) = unknowns x solves x ranks / time.
 Multi-GPU: every rank solves its own problems (independent, no collective on the data path):
@@ -59,6 +65,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=2, help="solves of the plain float64 comparison")
     ap.add_argument("--only-head", action="store_true", help="skip the parsed secondary workloads")
+    ap.add_argument("--oracle-batch", type=int, default=0,
+                    help="time the oracle on this many batch instances across all host cores, then exit")
     ap.add_argument("--kernel", default=None, choices=["uzawa_f32", "uzawa_f64", "residual_f64", "mixed_solve", "ir_steps"],
                     help="microbenchmark one kernel (for profiler captures) instead of the workload")
     ap.add_argument("--level", type=int, default=9)
@@ -511,6 +519,8 @@ def run_ours(args, rank, world, local_rank):
         extra["batch"] = run_batch(args, rank, world)
         extra["small"] = run_small(args, world)
         extra["adjoint"] = run_adjoint(args, world)
+        extra["timestep"] = run_timestep(args, world)
+        extra["lshape"] = run_lshape(args, world)
 
     # ---------------------------------------------------------------- CPU oracle baseline
     cpu = None
@@ -748,8 +758,159 @@ def run_adjoint(args, world):
             "loss": Lv, "dL_dbeta": db}
 
 
+def run_timestep(args, world):
+    """Implicit Euler steps of the time-dependent Stokes problem (Sec. 1: beta = 1/dt) at h = 1/512
+    (k = 8), dt = 1e-3, forcing f, g uniform[-1, 1] nodal (seed 7) varying slowly in time, from u = 0,
+    mixed precision to 1e-8: 10 host-driven steps, the same 10 steps as one CUDA-graph launch
+    (stokes_euler_run), and 8 independent trajectories (dt = 1e-4 .. 1e-1) of 10 steps in one launch
+    (stokes_batch_euler_run)."""
+    import torch
+
+    from paper_1502_04070_gb300 import workloads
+    from paper_1502_04070_gb300.timestep import BatchImplicitEuler, ImplicitEuler
+    k, dt, steps = K_LEVEL, 1e-3, 10
+    f0, g0 = workloads.random_nodal(k, 7, with_g=True)
+    fs = [torch.from_numpy(f0 * (1.0 + 0.1 * math_sin(n))).cuda() for n in range(1, steps + 1)]
+    gs = [torch.from_numpy(g0 * math_cos(0.3 * n)).cuda() for n in range(1, steps + 1)]
+    te = ImplicitEuler(k + 1, dt, precision="mixed", tol=TOL, max_cycles=200)
+    te.solver.autotune()
+    u, p = te.solver.zeros_u(), te.solver.zeros_p()
+    te.run_graph(u, p, fs, gs)                             # warm-up: builds the graph
+    u.zero_(), p.zero_()
+    for a, b in zip(fs, gs):                                # warm-up of the host-driven path
+        te.step(u, p, a, b)
+    torch.cuda.synchronize()
+    u.zero_(), p.zero_()
+    t = time.perf_counter()
+    host_cycles = [te.step(u, p, a, b).cycles for a, b in zip(fs, gs)]
+    torch.cuda.synchronize()
+    t_host = time.perf_counter() - t
+    u.zero_(), p.zero_()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    graph_cycles, rel = te.run_graph(u, p, fs, gs)
+    torch.cuda.synchronize()
+    t_graph = time.perf_counter() - t
+    te.close()
+    dts = [10.0 ** (-4 + 3 * i / 7) for i in range(8)]
+    be = BatchImplicitEuler([k + 1] * 8, dts, precision="mixed", tol=TOL, max_cycles=200)
+    us = [torch.zeros_like(fs[0]) for _ in dts]
+    ps = [torch.zeros_like(gs[0]) for _ in dts]
+    be.run(us, ps, [fs] * 8, [gs] * 8)                     # warm-up
+    for a, b in zip(us, ps):
+        a.zero_(), b.zero_()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    bcyc, _ = be.run(us, ps, [fs] * 8, [gs] * 8)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t
+    be.close()
+    n_dof = dofs(k)
+    return {"workload": "implicit Euler, h=1/512 (k=8), dt=1e-3, f,g uniform[-1,1] nodal (seed 7) varying in time, "
+                        "from u=0, mixed precision to 1e-8, 10 steps",
+            "host_steps": {"ms": 1000 * t_host, "cycles": host_cycles, "value": steps * n_dof * world / t_host,
+                           "unit": "DoF/s"},
+            "graph": {"ms": 1000 * t_graph, "cycles": graph_cycles, "value": steps * n_dof * world / t_graph,
+                      "unit": "DoF/s", "max_rel_residual": max(rel)},
+            "batch_8_trajectories": {"ms": 1000 * t_batch, "dt": dts, "cycles_per_step": bcyc,
+                                     "value": 8 * steps * n_dof * world / t_batch, "unit": "DoF/s"}}
+
+
+def math_sin(x):
+    import math
+    return math.sin(x)
+
+
+def math_cos(x):
+    import math
+    return math.cos(x)
+
+
+def run_lshape(args, world):
+    """The L-shaped domain at h = 1/512 of the square's lattice (L-level 7), beta = 1e2, f, g uniform
+    [-1, 1] on the L's unknowns (seed 9, sum g = 0), float64 V(3,3) and W(3,3) to 1e-8 from zero."""
+    import numpy as np
+    import torch
+
+    from paper_1502_04070_gb300.solver import Solver
+    k = K_LEVEL
+    n = 2 ** (k + 1)
+    rng = np.random.default_rng(9)
+    f = rng.uniform(-1, 1, (2, 2 * n + 1, 2 * n + 1))
+    g = rng.uniform(-1, 1, (n + 1, n + 1))
+    X = np.arange(2 * n + 1)
+    out_u = (X[None, :] >= n) & (X[:, None] >= n)
+    f[:, out_u] = 0.0
+    f[:, 0, :] = f[:, -1, :] = f[:, :, 0] = f[:, :, -1] = 0.0
+    f[:, n, n:] = f[:, n:, n] = 0.0
+    V = np.arange(n + 1)
+    out_p = (2 * V[None, :] > n) & (2 * V[:, None] > n)
+    g[out_p] = 0.0
+    g[~out_p] -= g[~out_p].mean()
+    ndof = int(2 * np.count_nonzero(f[0]) + np.count_nonzero(~out_p))
+    fd, gd = torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda()
+    out = {"workload": "L-shaped domain (unit square without [1/2,1]^2), lattice h=1/512, beta=1e2, f,g "
+                       "uniform[-1,1] on the L's unknowns (seed 9), float64, solve from 0 to 1e-8",
+           "unknowns": ndof}
+    for name, gamma in (("V", 1), ("W", 2)):
+        S = Solver(k + 1, 1e2, precision="fp64", gamma=gamma, coarse_level=1, domain="lshape")
+        S.solve(fd, gd, tol=TOL, max_cycles=200)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        _, _, rep = S.solve(fd, gd, tol=TOL, max_cycles=200)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        out[name] = {"cycles": rep.cycles, "mean_rate": round(rep.mean_rate, 4), "ms": 1000 * dt,
+                     "value": ndof * world / dt, "unit": "DoF/s", "rel_residual": rep.rel_residual}
+        S.close()
+    return out
+
+
+def _oracle_batch_task(item):
+    """One instance of the batch workload solved by the oracle (runs in a worker process)."""
+    k, beta, seed = item
+    import numpy as np
+
+    from oracle import fem
+    from oracle import multigrid as mg
+    from paper_1502_04070_gb300 import workloads
+    ds = fem.discretizations(k + 1)
+    fn, gn = workloads.random_nodal(k, seed)
+    F = ds[-1].load(fn, gn, project_g=True)
+    H = mg.Hierarchy(k + 1, beta, ds)
+    t = time.perf_counter()
+    x, hist = H.solve(F, mg.Params(), tol=TOL, max_cycles=200)
+    return time.perf_counter() - t, len(hist) - 1, dofs(k)
+
+
+def run_oracle_batch(args):
+    """The batch workload's first args.oracle_batch instances (levels uniform in 4..8, seed 3) solved
+    by the oracle, one instance per task of a process pool over all host cores (spawned workers, so
+    that no CUDA state is forked); solve time excludes each instance's assembly."""
+    import multiprocessing as mp
+
+    from paper_1502_04070_gb300 import workloads
+    ks, betas, seeds = workloads.batch_spec(args.batch_count, 3, k_min=4, k_max=8)
+    items = list(zip(ks, betas, seeds))[:args.oracle_batch]
+    cores = os.cpu_count()
+    t = time.perf_counter()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_batch_task, items, chunksize=1)
+    wall = time.perf_counter() - t
+    solve_s = sum(r[0] for r in res)
+    total_dof = sum(r[2] for r in res)
+    print(json.dumps({"oracle_batch": {"instances": len(items), "cores": cores, "wall_s": wall,
+                                       "solve_s_summed": solve_s, "value_wall": total_dof / wall,
+                                       "value_solve_only_per_core": total_dof / solve_s, "unit": "DoF/s",
+                                       "cycles": [r[1] for r in res], "note": "wall time includes assembly in "
+                                       "the workers; value_solve_only_per_core excludes it"}}), flush=True)
+
+
 def main():
     args = parse()
+    if args.oracle_batch:
+        run_oracle_batch(args)
+        return
     if args.kernel:
         from paper_1502_04070_gb300 import build as _b
         _b.build()
