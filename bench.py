@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--level", type=int, default=9)
     ap.add_argument("--gamma", type=int, default=1, help="kernel modes: 1 = V-cycle, 2 = W-cycle")
     ap.add_argument("--coarse-level", type=int, default=0, help="kernel modes: coarsest level of the iteration")
+    ap.add_argument("--tma-level", type=int, default=0,
+                    help="kernel modes: lowest planar float32 level (0: the library default; 14: none)")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--host-loop", action="store_true",
@@ -97,7 +99,8 @@ def run_kernel(args):
     f, g = workloads.random_nodal(k, 6)
     g = g - g.mean()
     prec = "mixed" if args.kernel in ("uzawa_f32", "mixed_solve", "ir_steps") else "fp64"
-    S = Solver(k + 1, 1e4, precision=prec, gamma=args.gamma, coarse_level=args.coarse_level)
+    S = Solver(k + 1, 1e4, precision=prec, gamma=args.gamma, coarse_level=args.coarse_level,
+               tma_level=args.tma_level)
     if args.variant is not None or args.variants:
         from paper_1502_04070_gb300.solver import set_step_variant
         if args.variant is not None:

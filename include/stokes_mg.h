@@ -94,6 +94,16 @@ typedef struct stokes_params {
                           smoother, coarse_level = 1 (the L's level 0) and levels >= 2; load vectors,
                           Euler right-hand sides and mass products are square-only (they return
                           STOKES_ERR_BAD_ARG on an L handle) */
+    int tma_level;     /* STOKES_MIXED with the Uzawa smoother on the unit square: the float32 levels
+                          k >= tma_level are held in a padded layout whose rows start on 16-byte
+                          boundaries and smoothed by a one-kernel step whose tiles arrive by
+                          tensor-memory-access box copies (the other levels as set by
+                          stokes_set_step_variant).  0 selects the default (level 6, N = 128); otherwise
+                          tma_level >= 5, and a value above the finest level keeps every level on the
+                          other variants.  Internal layout only: every array a caller passes keeps the
+                          layout above.  The step needs the register tile's coefficient structure
+                          (stokes_step_tables_match): setup and set_beta return STOKES_ERR_BAD_ARG for
+                          a beta without it on such a level */
 } stokes_params;
 
 /* Paper defaults: Uzawa, nu = 3+3, tau = sigma = 0.8, V-cycle, float64, one inner cycle, coarsest

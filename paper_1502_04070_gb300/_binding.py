@@ -28,6 +28,7 @@ class Params(ctypes.Structure):
         ("inner_cycles", ctypes.c_int),
         ("coarse_level", ctypes.c_int),
         ("domain", ctypes.c_int),
+        ("tma_level", ctypes.c_int),
     ]
 
 

@@ -100,7 +100,8 @@ void init_mem(DevMem& m, cudaStream_t st) {
 template <typename T>
 struct Level {
     int n = 0;
-    size_t n2 = 0, n1 = 0;   // (2n+1)^2 and (n+1)^2
+    size_t n2 = 0, n1 = 0;   // (2n+1)^2 and (n+1)^2; planar: half the velocity array and the vertex array
+    bool planar = false;     // float32 level in the planar layout (common.cuh), smoothed by the TMA step
     T *u = nullptr, *p = nullptr, *f = nullptr, *g = nullptr;
     T *tu = nullptr, *tp = nullptr, *sinv = nullptr;
     void* slab = nullptr;
@@ -108,10 +109,11 @@ struct Level {
 };
 
 template <typename T>
-stokes_status alloc_level(Level<T>& L, int k, DevMem& mem) {
+stokes_status alloc_level(Level<T>& L, int k, DevMem& mem, bool planar = false) {
     L.n = 1 << (k + 1);
-    L.n2 = (size_t)(2 * L.n + 1) * (2 * L.n + 1);
-    L.n1 = (size_t)(L.n + 1) * (L.n + 1);
+    L.planar = planar;
+    L.n2 = planar ? pl_ucount(L.n) / 2 : (size_t)(2 * L.n + 1) * (2 * L.n + 1);
+    L.n1 = planar ? pl_pcount(L.n) : (size_t)(L.n + 1) * (L.n + 1);
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
     const size_t bu = al(2 * L.n2 * sizeof(T)), bp = al(L.n1 * sizeof(T));
     const size_t total = 3 * bu + 4 * bp;
@@ -167,6 +169,8 @@ struct stokes_handle_t {
     MassCoef<double> mass{};
     OpCoef<float> chi{}, clo{};             // MIXED: finest float64 coefficients split hi + lo
     bool coarse_kernel = true;              // float32 levels <= 4 in one shared-memory kernel
+    bool launch_failed = false;             // a step variant refused to launch (reported by the next call)
+    bool has_planar = false;                // some float32 level is planar
     cudaGraphExec_t step = nullptr;         // one cycle + projection + residual norm
     int step_kernels = 0;                   // kernel nodes in `step`
     cudaGraphExec_t loop = nullptr;         // WHILE(not converged) { step; device-side test }
@@ -210,6 +214,21 @@ void ev_end(stokes_handle* h, int k) {
     if (k >= 0) cudaEventRecordWithFlags(h->ev[2 * k + 1], h->st, cudaEventRecordExternal);
 }
 
+// The status a call reports once its work is done: STOKES_ERR_CUDA if a step variant refused to
+// launch (recorded while launching or capturing), STOKES_ERR_TIMEOUT if a CTA of the planar levels'
+// step gave up waiting for its tiles (a device-wide flag, cleared by the read), else st.
+stokes_status take_launch_failure(stokes_handle* h, stokes_status st = STOKES_OK) {
+    if (h->launch_failed) {
+        h->launch_failed = false;
+        return STOKES_ERR_CUDA;
+    }
+    if (h->has_planar) {
+        CK(cudaStreamSynchronize(h->st));
+        if (uzawa_tma_timeouts()) return STOKES_ERR_TIMEOUT;
+    }
+    return st;
+}
+
 // nu smoothing steps on level lv.  The state is in (u, p) when `sw` is false and in (tu, tp)
 // when true; returns where it is afterwards.  The fused float32 Uzawa kernel writes the other
 // buffer pair (ping-pong); the float64 and normal-equation steps work in place and use the other
@@ -228,9 +247,16 @@ bool smooth_level(stokes_handle* h, Level<T>& lv, int steps, bool timed, bool sw
         if (P.smoother == STOKES_NORMAL_EQ) {
             launch_normal_eq<T>(h->st, lv.n, lv.c, (T)P.tau, xu, xp, lv.f, lv.g, lv.sinv, ou, op);
         } else if constexpr (sizeof(T) == 4) {
-            if (f32 && launch_uzawa_auto(h->st, lv.n, lv.c, (float)P.tau, (float)P.sigma, xu, xp, lv.f, lv.g,
-                                         lv.sinv, ou, op))
+            if (lv.planar) {
+                if (launch_uzawa_tma(h->st, lv.n, lv.c, (float)P.tau, (float)P.sigma, xu, xp, lv.f, lv.g, lv.sinv, ou,
+                                     op))
+                    sw = !sw;
+                else
+                    h->launch_failed = true;
+            } else if (f32 && launch_uzawa_auto(h->st, lv.n, lv.c, (float)P.tau, (float)P.sigma, xu, xp, lv.f, lv.g,
+                                                lv.sinv, ou, op)) {
                 sw = !sw;
+            }
         } else {
             launch_uzawa<T>(h->st, lv.n, lv.c, (T)P.tau, (T)P.sigma, xu, xp, lv.f, lv.g, lv.sinv, ou, op, 32, 8, h->dom);
         }
@@ -279,10 +305,20 @@ void mg_cycle(stokes_handle* h, std::vector<Level<T>>& H, int l) {
     T* ru = sw ? lv.u : lv.tu;
     T* rp = sw ? lv.p : lv.tp;
     Level<T>& cl = H[l - 1];
-    launch_residual<T, T>(h->st, lv.n, lv.c, xu, xp, lv.f, lv.g, ru, rp, nullptr, nullptr, nullptr, h->dom);
-    launch_restrict<T>(h->st, cl.n, ru, rp, cl.f, cl.g, cl.u, cl.p, h->dom);   // and the coarse iterate := 0
-    for (int r = 0; r < h->prm.gamma; ++r) mg_cycle(h, H, l - 1);
-    launch_prolong_add<T>(h->st, cl.n, cl.u, cl.p, xu, xp, h->dom);
+    if constexpr (sizeof(T) == 4) {
+        if (lv.planar) {
+            launch_residual_planar(h->st, lv.n, lv.c, xu, xp, lv.f, lv.g, ru, rp);
+            launch_restrict_planar(h->st, cl.n, cl.planar, ru, rp, cl.f, cl.g, cl.u, cl.p);
+            for (int r = 0; r < h->prm.gamma; ++r) mg_cycle(h, H, l - 1);
+            launch_prolong_add_planar(h->st, cl.n, cl.planar, cl.u, cl.p, xu, xp);
+        }
+    }
+    if (!lv.planar) {
+        launch_residual<T, T>(h->st, lv.n, lv.c, xu, xp, lv.f, lv.g, ru, rp, nullptr, nullptr, nullptr, h->dom);
+        launch_restrict<T>(h->st, cl.n, ru, rp, cl.f, cl.g, cl.u, cl.p, h->dom);   // and the coarse iterate := 0
+        for (int r = 0; r < h->prm.gamma; ++r) mg_cycle(h, H, l - 1);
+        launch_prolong_add<T>(h->st, cl.n, cl.u, cl.p, xu, xp, h->dom);
+    }
     sw = smooth_level(h, lv, h->prm.nu_post, top, sw);
     if (sw) {   // odd number of ping-pong steps: bring the iterate back to (u, p)
         cudaMemcpyAsync(lv.u, lv.tu, 2 * lv.n2 * sizeof(T), cudaMemcpyDeviceToDevice, h->st);
@@ -300,7 +336,7 @@ void residual_norm_fin(stokes_handle* h, bool timed = false) {
     if (h->mixed()) {
         // x in float64; r kept as two floats for the refinement updates, r32 = its float32 value
         Level<float>& E = h->h32.back();
-        launch_residual_df(h->st, F.n, F.c, F.u, F.p, F.f, F.g, F.tu, F.tp, E.f, E.g, h->partial);
+        launch_residual_df(h->st, F.n, F.c, F.u, F.p, F.f, F.g, F.tu, F.tp, E.f, E.g, h->partial, E.planar);
     } else {
         launch_residual<double, double>(h->st, F.n, F.c, F.u, F.p, F.f, F.g, F.tu, F.tp, h->partial, nullptr, nullptr,
                                         h->dom);
@@ -323,7 +359,7 @@ void record_step(stokes_handle* h) {
         // the same pass leaves the partial sums of the zero-mean projection of x_p (second half)
         const int nb = cells_blocks(F.n);
         launch_ir_update_df(h->st, F.n, h->chi, h->clo, E.u, E.p, F.u, F.p, F.tu, F.tp, E.f, E.g, h->partial,
-                            h->partial + nb);
+                            h->partial + nb, E.planar);
         ev_end(h, k);
         launch_reduce(h->st, h->partial, nb, h->scal);
         launch_reduce(h->st, h->partial + nb, nb, h->scal + 1);
@@ -445,7 +481,10 @@ stokes_status rebuild_beta(stokes_handle* h) {
     }
     for (auto& lv : h->h32) {
         lv.c = make_coef<float>(lv.n, beta);
-        launch_schur_diag<float>(h->st, lv.n, make_coef<double>(lv.n, beta), lv.sinv);
+        // planar levels run only the register-tile step, which needs its coefficient structure
+        if (lv.planar && !reg_tables_match(lv.c)) return STOKES_ERR_BAD_ARG;
+        launch_schur_diag<float>(h->st, lv.n, make_coef<double>(lv.n, beta), lv.sinv, kDomSquare,
+                                 lv.planar ? pl_vpitch(lv.n) : 0);
     }
     if (h->mixed()) {
         const OpCoef<double>& c = h->fin().c;
@@ -576,7 +615,7 @@ stokes_status stokes_setup(const stokes_params* prm, void* stream, stokes_handle
         (P.precision != STOKES_FP64 && P.precision != STOKES_MIXED) ||
         (P.precision == STOKES_MIXED && P.inner_cycles < 1) || P.coarse_level < 0 ||
         P.coarse_level > kMaxCoarseLevel || P.coarse_level > P.levels - 1 ||
-        (P.domain != STOKES_UNIT_SQUARE && P.domain != STOKES_L_SHAPE))
+        (P.domain != STOKES_UNIT_SQUARE && P.domain != STOKES_L_SHAPE) || (P.tma_level != 0 && P.tma_level < 5))
         return STOKES_ERR_BAD_ARG;
     // the L-shaped domain: float64 Uzawa cycles, coarsest level 1 (the L's level 0)
     if (P.domain == STOKES_L_SHAPE && (P.precision != STOKES_FP64 || P.smoother != STOKES_UZAWA ||
@@ -616,8 +655,11 @@ stokes_status stokes_setup(const stokes_params* prm, void* stream, stokes_handle
         h->h64.resize(1);
         if ((s = alloc_level(h->h64[0], kfin, h->mem)) != STOKES_OK) return bail(s);
         h->h32.resize(P.levels);
+        const int tlev = P.tma_level > 0 ? P.tma_level : kDefaultTmaLevel;
+        const bool tma = P.smoother == STOKES_UZAWA && P.domain == STOKES_UNIT_SQUARE && uzawa_tma_available();
         for (int k = 0; k < P.levels; ++k)
-            if ((s = alloc_level(h->h32[k], k, h->mem)) != STOKES_OK) return bail(s);
+            if ((s = alloc_level(h->h32[k], k, h->mem, tma && k >= tlev)) != STOKES_OK) return bail(s);
+        h->has_planar = tma && tlev < P.levels;
     }
     h->mass = make_mass<double>(h->fin().n);
     h->npartial = 2 * cells_blocks(h->fin().n);   // two sets of per-block partial sums (refinement update)
@@ -703,7 +745,7 @@ stokes_status stokes_cycle(stokes_handle* h, double* u, double* p, const double*
     if ((s = build_graph(h)) != STOKES_OK) return s;
     stokes_status s2 = launch_step(h);
     if (s2 != STOKES_OK) return s2;
-    return copy_out(h, u, p);
+    return take_launch_failure(h, copy_out(h, u, p));
 }
 
 stokes_status stokes_solve(stokes_handle* h, double* u, double* p, const double* f, const double* g,
@@ -816,7 +858,7 @@ stokes_status stokes_solve(stokes_handle* h, double* u, double* p, const double*
         rep->rel_residual = nF > 0 ? r / nF : r;
         rep->mean_rate = cycles > 0 && r0 > 0 ? std::pow(r / r0, 1.0 / cycles) : 0.0;
     }
-    return result;
+    return take_launch_failure(h, result);
 }
 
 stokes_status stokes_residual(stokes_handle* h, const double* u, const double* p, const double* f,
@@ -859,6 +901,16 @@ stokes_status stokes_smooth(stokes_handle* h, double* u, double* p, const double
 stokes_status stokes_smooth_f32(stokes_handle* h, float* u, float* p, const float* f, const float* g, int nu) {
     if (!h || !u || !p || !f || !g || nu < 0 || !h->mixed()) return STOKES_ERR_BAD_ARG;
     Level<float> lv = h->h32.back();   // coefficients, diagonals and ping-pong partners of the finest level
+    if (lv.planar) {
+        // the caller's compact arrays into the level's own planar buffers, and the result back
+        launch_to_planar(h->st, lv.n, u, p, lv.u, lv.p);
+        launch_to_planar(h->st, lv.n, f, g, lv.f, lv.g);
+        const bool sw = smooth_level<float>(h, lv, nu, false, false);
+        launch_from_planar(h->st, lv.n, sw ? lv.tu : lv.u, sw ? lv.tp : lv.p, u, p);
+        h->launches += (unsigned long long)nu + 3;
+        CK(cudaGetLastError());
+        return take_launch_failure(h);
+    }
     lv.u = u;
     lv.p = p;
     lv.f = const_cast<float*>(f);
@@ -870,7 +922,7 @@ stokes_status stokes_smooth_f32(stokes_handle* h, float* u, float* p, const floa
     }
     h->launches += (unsigned long long)nu;
     CK(cudaGetLastError());
-    return STOKES_OK;
+    return take_launch_failure(h);
 }
 
 stokes_status stokes_restrict(stokes_handle* h, const double* fu, const double* fp, double* fc, double* gc) {
@@ -1006,7 +1058,7 @@ static stokes_status autotune_levels(stokes_handle* h, cudaStream_t st) {
     if (!h->mixed() || h->prm.smoother != STOKES_UZAWA) return STOKES_OK;
     for (int l = 1; l < (int)h->h32.size(); ++l) {
         Level<float>& lv = h->h32[l];
-        if (uzawa_tuned(lv.n)) continue;
+        if (lv.planar || uzawa_tuned(lv.n)) continue;   // planar levels have one step kernel
         cudaError_t e = autotune_uzawa_fused(st, lv.n, lv.c, (float)h->prm.tau, (float)h->prm.sigma, lv.u, lv.p, lv.f,
                                              lv.g, lv.sinv, lv.tu, lv.tp, nullptr, nullptr);
         if (e != cudaSuccess) return fail(e);
@@ -1218,6 +1270,7 @@ stokes_status stokes_batch_solve(stokes_batch* b, double* const* u, double* cons
         if (cycles) cycles[i] = total;
         if (rel_residual) rel_residual[i] = nF > 0 ? r / nF : r;
     }
+    for (int i = 0; i < b->count; ++i) result = take_launch_failure(b->inst[i], result);
     return result;
 }
 
@@ -1376,7 +1429,7 @@ stokes_status stokes_euler_run(stokes_handle* h, double* u, double* p, const dou
     unsigned long long total = 0;
     const stokes_status out = euler_results(res, steps, tol, cycles, rel_residual, &total);
     h->launches += (unsigned long long)h->euler_kernels + total * (unsigned long long)h->euler_body;
-    return out;
+    return take_launch_failure(h, out);
 }
 
 stokes_status stokes_batch_euler_run(stokes_batch* b, double* const* u, double* const* p,
@@ -1434,6 +1487,7 @@ stokes_status stokes_batch_euler_run(stokes_batch* b, double* const* u, double* 
         b->mem.put(dres[i]);
     }
     if (e != cudaSuccess) return fail(e);
+    for (int i = 0; i < count; ++i) out = take_launch_failure(b->inst[i], out);
     return out;
 }
 

@@ -102,6 +102,27 @@ struct GViewU {
 template <typename T>
 __device__ __forceinline__ GViewU<T> gviewu(const T* p, int ld) { return GViewU<T>{p, ld}; }
 
+// One component of a planar float32 velocity array (common.cuh, pl_u), through the read-only path:
+// p is the array plus the component (0 or 1), rs and ps the row and plane strides in floats.
+// ZF as for GViewU (true only where every window lies inside the lattice and off the ring).
+template <bool ZF>
+struct GViewP {
+    static constexpr bool zero_filled = ZF;
+    const float* p;
+    int rs, ps;
+    __device__ __forceinline__ float operator()(int X, int Y) const {
+        return __ldg(p + ((X & 1) * ps + Y * rs + (X >> 1) * 2));
+    }
+    __device__ __forceinline__ float at(int si, int sj, int a, int b) const {
+        return __ldg(p + ((a & 1) * ps + (2 * sj + b) * rs + 2 * (si + (a >> 1))));
+    }
+};
+template <bool ZF>
+__device__ __forceinline__ GViewP<ZF> gviewp(const float* u, int n, int comp) {
+    const int rs = 2 * pl_pitch(n);
+    return GViewP<ZF>{u + comp, rs, rs * pl_rows(n)};
+}
+
 // True when every cell (i, j) of this block has m <= i, j <= n - m (block-uniform).  Margin 1: the
 // windows stay inside the arrays; margin 2: they also avoid the Dirichlet ring.
 __device__ __forceinline__ bool block_interior(int n, int m) {

@@ -280,6 +280,26 @@ __device__ __forceinline__ double vertex_weight_dom(int i, int j, int n, int dom
     return cnt * h * h / 6.0;
 }
 
+// Planar float32 layout of the large float32 levels (the velocity arrays of the refinement's inner
+// cycles, staged by the tensor-memory-access engine, which needs 16-byte row pitches):
+//   velocity: (u_x, u_y) pairs side by side, in two planes by the parity of the lattice column X;
+//             plane a holds the points X = 2 q + a, row Y at pair q; pl_rows(n) = 2N + 2 rows per
+//             plane (row 2N + 1 is padding) of pl_pitch(n) = N + 2 pairs (q = N + 1, and q = N of
+//             plane 1, are padding), so every row starts on a 16-byte boundary;
+//   vertex arrays: rows of pl_vpitch(n) = N + 1 rounded up to 4 floats.
+// Padding and the Dirichlet boundary nodes of every velocity array hold zero (the arrays are zeroed
+// when allocated, and kernels write the boundary nodes as zero and never write the padding), so a
+// tile of either plane, or of the four node-type planes, is one box copy with no masking.
+__host__ __device__ __forceinline__ int pl_pitch(int n) { return (n + 2) & ~1; }
+__host__ __device__ __forceinline__ int pl_rows(int n) { return 2 * n + 2; }
+__host__ __device__ __forceinline__ int pl_vpitch(int n) { return (n + 4) & ~3; }
+__host__ __device__ __forceinline__ size_t pl_ucount(int n) { return (size_t)4 * pl_rows(n) * pl_pitch(n); }   // floats
+__host__ __device__ __forceinline__ size_t pl_pcount(int n) { return (size_t)(n + 1) * pl_vpitch(n); }
+// float index of u_x at lattice point (X, Y); u_y follows it
+__host__ __device__ __forceinline__ int pl_u(int n, int X, int Y) {
+    return (((X & 1) * pl_rows(n) + Y) * pl_pitch(n) + (X >> 1)) * 2;
+}
+
 template <typename T> struct Vec2;
 template <> struct Vec2<float> { using type = float2; };
 template <> struct Vec2<double> { using type = double2; };

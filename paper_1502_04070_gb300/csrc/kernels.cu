@@ -40,26 +40,38 @@ cudaError_t upload_transfer_weights(const double* P2) {
 }
 
 // ------------------------------------------------------------------------------------------
-// r = F - A x  (eq. gen:bil:mv), optional sum of squares
-template <typename T, typename TO>
+// r = F - A x  (eq. gen:bil:mv), optional sum of squares.  PL: float32 arrays in the planar layout
+// (common.cuh; then ru2, rp2 are null).
+template <typename T, typename TO, bool PL>
 __global__ void __launch_bounds__(NT) k_residual(int n, const __grid_constant__ OpCoef<T> c,
                                                  const T* __restrict__ u, const T* __restrict__ p,
                                                  const T* __restrict__ f, const T* __restrict__ g,
                                                  TO* __restrict__ ru, TO* __restrict__ rp,
                                                  double* __restrict__ partial, float* __restrict__ ru2,
                                                  float* __restrict__ rp2, int dom) {
+    static_assert(!PL || (sizeof(T) == 4 && sizeof(TO) == 4), "the planar layout is float32 only");
     pdl_wait();
     CELL_INDEX
     const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
+    const int vld = PL ? pl_vpitch(n) : n + 1;
     double ss = 0.0;
     if (active) {
         Acc<T> a;
-        if (block_interior(n, 2))
-            cell_apply_auto<true, true, true, false, false>(i, j, n, c, gviewu(u, 2 * n + 1), gviewu(u + n2, 2 * n + 1),
-                                                            gviewu(p, n + 1), a);
-        else
-            cell_apply_auto<true, true, true, false, true>(i, j, n, c, gview(u, 2 * n + 1), gview(u + n2, 2 * n + 1),
-                                                           gview(p, n + 1), a);
+        if constexpr (PL) {
+            if (block_interior(n, 2))
+                cell_apply_auto<true, true, true, false, false>(i, j, n, c, gviewp<true>(u, n, 0), gviewp<true>(u, n, 1),
+                                                                gviewu(p, vld), a);
+            else
+                cell_apply_auto<true, true, true, false, true>(i, j, n, c, gviewp<false>(u, n, 0), gviewp<false>(u, n, 1),
+                                                               gview(p, vld), a);
+        } else {
+            if (block_interior(n, 2))
+                cell_apply_auto<true, true, true, false, false>(i, j, n, c, gviewu(u, 2 * n + 1),
+                                                                gviewu(u + n2, 2 * n + 1), gviewu(p, n + 1), a);
+            else
+                cell_apply_auto<true, true, true, false, true>(i, j, n, c, gview(u, 2 * n + 1), gview(u + n2, 2 * n + 1),
+                                                               gview(p, n + 1), a);
+        }
         const CellNodes cn = cell_nodes_dom(i, j, n, dom);
         const int ld = 2 * n + 1;
 #pragma unroll
@@ -67,23 +79,24 @@ __global__ void __launch_bounds__(NT) k_residual(int n, const __grid_constant__ 
             if (!slot_exists(cn, s)) continue;
             int X, Y;
             slot_pos(i, j, s, X, Y);
-            const size_t idx = (size_t)Y * ld + X;
+            const size_t idx = PL ? (size_t)pl_u(n, X, Y) : (size_t)Y * ld + X;
 #pragma unroll
             for (int comp = 0; comp < 2; ++comp) {
+                const size_t k = PL ? idx + comp : comp * n2 + idx;
                 TO r = TO(0);
                 if (slot_unknown(cn, s)) {
-                    const T rr = f[comp * n2 + idx] - a.au[comp][s] - a.bt[comp][s];
+                    const T rr = f[k] - a.au[comp][s] - a.bt[comp][s];
                     r = (TO)rr;
                     ss += (double)rr * (double)rr;
                 }
-                ru[comp * n2 + idx] = r;
-                if (ru2) ru2[comp * n2 + idx] = (float)r;
+                ru[k] = r;
+                if (!PL && ru2) ru2[k] = (float)r;
             }
         }
-        const size_t vi = (size_t)j * (n + 1) + i;
+        const size_t vi = (size_t)j * vld + i;
         const T r = (dom == kDomL && l_masked_vertex(i, j, n)) ? T(0) : g[vi] - a.bu;
         rp[vi] = (TO)r;
-        if (rp2) rp2[vi] = (float)r;
+        if (!PL && rp2) rp2[vi] = (float)r;
         ss += (double)r * (double)r;
     }
     if (partial) {
@@ -255,7 +268,8 @@ template <typename T>
 void launch_normal_eq(cudaStream_t s, int n, const OpCoef<T>& c, T tau, T* u, T* p, const T* f,
                       const T* g, const T* sinv, T* zu, T* zp) {
     const dim3 grid = cells_grid(n), blk(BX, BY);
-    launch_pdl(k_residual<T, T>, grid, blk, 0, s, n, c, u, p, f, g, zu, zp, nullptr, nullptr, nullptr, (int)kDomSquare);
+    launch_pdl(k_residual<T, T, false>, grid, blk, 0, s, n, c, u, p, f, g, zu, zp, nullptr, nullptr, nullptr,
+               (int)kDomSquare);
     launch_pdl(k_scale_L<T>, grid, blk, 0, s, n, c, zu, zp, sinv);
     launch_pdl(k_normal_update<T>, grid, blk, 0, s, n, c, tau, zu, zp, sinv, u, p);
 }
@@ -263,7 +277,14 @@ void launch_normal_eq(cudaStream_t s, int n, const OpCoef<T>& c, T tau, T* u, T*
 template <typename T, typename TO>
 void launch_residual(cudaStream_t s, int n, const OpCoef<T>& c, const T* u, const T* p, const T* f,
                      const T* g, TO* ru, TO* rp, double* partial, float* ru2, float* rp2, int dom) {
-    launch_pdl(k_residual<T, TO>, cells_grid(n), dim3(BX, BY), 0, s, n, c, u, p, f, g, ru, rp, partial, ru2, rp2, dom);
+    launch_pdl(k_residual<T, TO, false>, cells_grid(n), dim3(BX, BY), 0, s, n, c, u, p, f, g, ru, rp, partial, ru2, rp2,
+               dom);
+}
+
+void launch_residual_planar(cudaStream_t s, int n, const OpCoef<float>& c, const float* u, const float* p,
+                            const float* f, const float* g, float* ru, float* rp) {
+    launch_pdl(k_residual<float, float, true>, cells_grid(n), dim3(BX, BY), 0, s, n, c, u, p, f, g, ru, rp,
+               (double*)nullptr, (float*)nullptr, (float*)nullptr, (int)kDomSquare);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -295,19 +316,45 @@ __device__ __forceinline__ T ldv(const T* p) {
 }
 
 // Strides of the arrays a transfer reads and writes, each pointer at the array's (0, 0) entry:
-// the dense level arrays (dense_layout), or the padded shared-memory arrays of the coarse cycle.
+// the dense level arrays (dense_layout), the padded shared-memory arrays of the coarse cycle, or
+// float32 levels in the planar layout (template flags PF / PC of the fine / coarse level; there the
+// row stride is in floats, the component stride is 1 and psf / psc is the parity-plane stride).
 struct XferLayout {
     int ldf, n2f;   // fine velocity: row stride, component stride
     int ldpf;       // fine vertex array: row stride
     int ldc, n2c;   // coarse velocity
     int ldpc;       // coarse vertex array
+    int psf = 0, psc = 0;
 };
 __host__ __device__ __forceinline__ XferLayout dense_layout(int nc) {
     const int ldf = 4 * nc + 1, ldc = 2 * nc + 1;
     return XferLayout{ldf, ldf * ldf, 2 * nc + 1, ldc, ldc * ldc, nc + 1};
 }
+__host__ __device__ __forceinline__ XferLayout xfer_layout(int nc, bool pf, bool pc) {
+    XferLayout l = dense_layout(nc);
+    if (pf) {
+        const int nf = 2 * nc;
+        l.ldf = 2 * pl_pitch(nf);
+        l.n2f = 1;
+        l.ldpf = pl_vpitch(nf);
+        l.psf = l.ldf * pl_rows(nf);
+    }
+    if (pc) {
+        l.ldc = 2 * pl_pitch(nc);
+        l.n2c = 1;
+        l.ldpc = pl_vpitch(nc);
+        l.psc = l.ldc * pl_rows(nc);
+    }
+    return l;
+}
+// offset of lattice point (X, Y), component 0, in a velocity array of row stride ld (plane stride ps)
+template <bool PLN>
+__host__ __device__ __forceinline__ int lat_at(int X, int Y, int ld, int ps) {
+    if constexpr (PLN) return (X & 1) * ps + Y * ld + (X >> 1) * 2;
+    else return Y * ld + X;
+}
 
-template <int SQ, bool LDG, typename T>
+template <int SQ, bool LDG, bool PF, typename T>
 __device__ __forceinline__ void restrict_visit(int I, int J, int nc, const T* __restrict__ ru, T (&acc)[2][4],
                                                const XferLayout& lay) {
     const int SI = I - (SQ & 1), SJ = J - (SQ >> 1);
@@ -317,7 +364,7 @@ __device__ __forceinline__ void restrict_visit(int I, int J, int nc, const T* __
     for (int fb = 0; fb < 4; ++fb)
 #pragma unroll
         for (int fa = 0; fa < 4; ++fa) {
-            const int k = (4 * SJ + fb) * lay.ldf + 4 * SI + fa;
+            const int k = lat_at<PF>(4 * SI + fa, 4 * SJ + fb, lay.ldf, lay.psf);
             v[0][fb][fa] = ldv<LDG>(ru + k);
             v[1][fb][fa] = ldv<LDG>(ru + lay.n2f + k);
         }
@@ -326,24 +373,24 @@ __device__ __forceinline__ void restrict_visit(int I, int J, int nc, const T* __
 }
 
 // coarse cell (i, j) of level nc: its owned coarse velocity nodes and vertex
-template <bool LDG, typename T>
+template <bool LDG, typename T, bool PF = false, bool PC = false>
 __device__ __forceinline__ void restrict_cell(int i, int j, int nc, const T* __restrict__ ru, const T* __restrict__ rp,
                                               T* __restrict__ fc, T* __restrict__ gc, const XferLayout& lay,
                                               int dom = kDomSquare) {
     T acc[2][4];
 #pragma unroll
     for (int s = 0; s < 4; ++s) acc[0][s] = acc[1][s] = T(0);
-    restrict_visit<0, LDG>(i, j, nc, ru, acc, lay);
-    restrict_visit<1, LDG>(i, j, nc, ru, acc, lay);
-    restrict_visit<2, LDG>(i, j, nc, ru, acc, lay);
-    restrict_visit<3, LDG>(i, j, nc, ru, acc, lay);
+    restrict_visit<0, LDG, PF>(i, j, nc, ru, acc, lay);
+    restrict_visit<1, LDG, PF>(i, j, nc, ru, acc, lay);
+    restrict_visit<2, LDG, PF>(i, j, nc, ru, acc, lay);
+    restrict_visit<3, LDG, PF>(i, j, nc, ru, acc, lay);
     const CellNodes cn = cell_nodes_dom(i, j, nc, dom);
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
         if (!slot_exists(cn, s)) continue;
         int X, Y;
         slot_pos(i, j, s, X, Y);
-        const int k = Y * lay.ldc + X;
+        const int k = lat_at<PC>(X, Y, lay.ldc, lay.psc);
         const bool unk = slot_unknown(cn, s);
         fc[k] = unk ? acc[0][s] : T(0);
         fc[lay.n2c + k] = unk ? acc[1][s] : T(0);
@@ -369,7 +416,8 @@ __device__ __forceinline__ void restrict_cell(int i, int j, int nc, const T* __r
 }
 
 // With uc, pc given, the coarse iterate is also set to zero (the coarse correction starts from 0).
-template <typename T>
+// PF / PC: the fine / coarse level is a float32 level in the planar layout.
+template <typename T, bool PF, bool PC>
 __global__ void __launch_bounds__(NT) k_restrict(int nc, const T* __restrict__ ru, const T* __restrict__ rp,
                                                  T* __restrict__ fc, T* __restrict__ gc, T* __restrict__ uc,
                                                  T* __restrict__ pc, int dom) {
@@ -377,32 +425,43 @@ __global__ void __launch_bounds__(NT) k_restrict(int nc, const T* __restrict__ r
     const int n = nc;
     CELL_INDEX
     if (!active) return;
-    restrict_cell<true>(i, j, nc, ru, rp, fc, gc, dense_layout(nc), dom);
+    const XferLayout lay = xfer_layout(nc, PF, PC);
+    restrict_cell<true, T, PF, PC>(i, j, nc, ru, rp, fc, gc, lay, dom);
     if (uc) {
         const CellNodes cn = cell_nodes(i, j, nc);
-        const int ldc = 2 * nc + 1, n2c = ldc * ldc;
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
             if (!slot_exists(cn, s)) continue;
             int X, Y;
             slot_pos(i, j, s, X, Y);
-            uc[Y * ldc + X] = T(0);
-            uc[n2c + Y * ldc + X] = T(0);
+            const int k = lat_at<PC>(X, Y, lay.ldc, lay.psc);
+            uc[k] = T(0);
+            uc[lay.n2c + k] = T(0);
         }
-        pc[j * (nc + 1) + i] = T(0);
+        pc[j * lay.ldpc + i] = T(0);
     }
     pdl_trigger();
 }
 
 template <typename T>
 void launch_restrict(cudaStream_t s, int nc, const T* ru, const T* rp, T* fc, T* gc, T* uc, T* pc, int dom) {
-    launch_pdl(k_restrict<T>, cells_grid(nc), dim3(BX, BY), 0, s, nc, ru, rp, fc, gc, uc, pc, dom);
+    launch_pdl(k_restrict<T, false, false>, cells_grid(nc), dim3(BX, BY), 0, s, nc, ru, rp, fc, gc, uc, pc, dom);
+}
+
+void launch_restrict_planar(cudaStream_t s, int nc, bool pc_planar, const float* ru, const float* rp, float* fc,
+                            float* gc, float* uc, float* pc) {
+    if (pc_planar)
+        launch_pdl(k_restrict<float, true, true>, cells_grid(nc), dim3(BX, BY), 0, s, nc, ru, rp, fc, gc, uc, pc,
+                   (int)kDomSquare);
+    else
+        launch_pdl(k_restrict<float, true, false>, cells_grid(nc), dim3(BX, BY), 0, s, nc, ru, rp, fc, gc, uc, pc,
+                   (int)kDomSquare);
 }
 
 // Prolongation (Sec. 3, canonical embedding): every fine point owned by coarse square (I, J) is
 // the coarse P2 function of that square evaluated there; P1 values are vertex injection and
 // averages along coarse edges.
-template <bool LDG, typename T>
+template <bool LDG, typename T, bool PF = false, bool PC = false>
 __device__ __forceinline__ void prolong_cell(int i, int j, int nc, const T* __restrict__ uc, const T* __restrict__ pc,
                                              T* __restrict__ u, T* __restrict__ p, const XferLayout& lay,
                                              int dom = kDomSquare) {
@@ -411,7 +470,7 @@ __device__ __forceinline__ void prolong_cell(int i, int j, int nc, const T* __re
         T z[2][9];
 #pragma unroll
         for (int m = 0; m < 9; ++m) {
-            const int k = (2 * j + m / 3) * lay.ldc + 2 * i + m % 3;
+            const int k = lat_at<PC>(2 * i + m % 3, 2 * j + m / 3, lay.ldc, lay.psc);
             z[0][m] = ldv<LDG>(uc + k);
             z[1][m] = ldv<LDG>(uc + lay.n2c + k);
         }
@@ -429,7 +488,7 @@ __device__ __forceinline__ void prolong_cell(int i, int j, int nc, const T* __re
                     sx = fma(w, z[0][L], sx);
                     sy = fma(w, z[1][L], sy);
                 }
-                const int k = Y * lay.ldf + X;
+                const int k = lat_at<PF>(X, Y, lay.ldf, lay.psf);
                 u[k] += sx;
                 u[lay.n2f + k] += sy;
             }
@@ -448,20 +507,28 @@ __device__ __forceinline__ void prolong_cell(int i, int j, int nc, const T* __re
     }
 }
 
-template <typename T>
+template <typename T, bool PF, bool PC>
 __global__ void __launch_bounds__(NT) k_prolong(int nc, const T* __restrict__ uc, const T* __restrict__ pc,
                                                 T* __restrict__ u, T* __restrict__ p, int dom) {
     pdl_wait();
     const int n = nc;
     CELL_INDEX
     if (!active) return;
-    prolong_cell<true>(i, j, nc, uc, pc, u, p, dense_layout(nc), dom);
+    prolong_cell<true, T, PF, PC>(i, j, nc, uc, pc, u, p, xfer_layout(nc, PF, PC), dom);
     pdl_trigger();
 }
 
 template <typename T>
 void launch_prolong_add(cudaStream_t s, int nc, const T* uc, const T* pc, T* u, T* p, int dom) {
-    launch_pdl(k_prolong<T>, cells_grid(nc), dim3(BX, BY), 0, s, nc, uc, pc, u, p, dom);
+    launch_pdl(k_prolong<T, false, false>, cells_grid(nc), dim3(BX, BY), 0, s, nc, uc, pc, u, p, dom);
+}
+
+void launch_prolong_add_planar(cudaStream_t s, int nc, bool pc_planar, const float* uc, const float* pc, float* u,
+                               float* p) {
+    if (pc_planar)
+        launch_pdl(k_prolong<float, true, true>, cells_grid(nc), dim3(BX, BY), 0, s, nc, uc, pc, u, p, (int)kDomSquare);
+    else
+        launch_pdl(k_prolong<float, true, false>, cells_grid(nc), dim3(BX, BY), 0, s, nc, uc, pc, u, p, (int)kDomSquare);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -531,11 +598,11 @@ __device__ double diagA_at(int X, int Y, int n, const OpCoef<double>& c) {
 // all squares around such a node lie in the L), and Shat^{-1} = 0 at vertices outside the L.
 template <typename T>
 __global__ void __launch_bounds__(NT) k_schur(int n, const __grid_constant__ OpCoef<double> c, T* __restrict__ sinv,
-                                              int dom) {
+                                              int dom, int vld) {
     CELL_INDEX
     if (!active) return;
     if (dom == kDomL && l_masked_vertex(i, j, n)) {
-        sinv[(size_t)j * (n + 1) + i] = T(0);
+        sinv[(size_t)j * vld + i] = T(0);
         return;
     }
     double bx[5][5], by[5][5];
@@ -558,12 +625,12 @@ __global__ void __launch_bounds__(NT) k_schur(int n, const __grid_constant__ OpC
             if (!interior2(X, Y, n) || (dom == kDomL && l_masked_node(X, Y, n))) continue;
             s += (bx[py][px] * bx[py][px] + by[py][px] * by[py][px]) / diagA_at(X, Y, n, c);
         }
-    sinv[(size_t)j * (n + 1) + i] = (T)(1.0 / s);
+    sinv[(size_t)j * vld + i] = (T)(1.0 / s);
 }
 
 template <typename T>
-void launch_schur_diag(cudaStream_t s, int n, const OpCoef<double>& c, T* sinv, int dom) {
-    k_schur<T><<<cells_grid(n), dim3(BX, BY), 0, s>>>(n, c, sinv, dom);
+void launch_schur_diag(cudaStream_t s, int n, const OpCoef<double>& c, T* sinv, int dom, int vld) {
+    k_schur<T><<<cells_grid(n), dim3(BX, BY), 0, s>>>(n, c, sinv, dom, vld > 0 ? vld : n + 1);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -801,6 +868,49 @@ void launch_add_f32(cudaStream_t s, size_t count, const float* e, double* x) {
     k_add_f32<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(count, e, x);
 }
 
+// compact (2N+1)^2 x 2 / (N+1)^2 float32 state <-> the planar layout (common.cuh)
+__global__ void k_to_planar(int n, const float* __restrict__ u, const float* __restrict__ p, float* __restrict__ pu,
+                            float* __restrict__ pp) {
+    const int ld = 2 * n + 1, n2 = ld * ld, P = pl_pitch(n), RP = pl_rows(n), vp = pl_vpitch(n);
+    const int slots = 2 * RP * P, verts = (n + 1) * vp;
+    const int stride = gridDim.x * blockDim.x;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < slots; k += stride) {
+        const int q = k % P, Y = (k / P) % RP, X = 2 * q + k / (P * RP);
+        float2 v = make_float2(0.f, 0.f);
+        if (interior2(X, Y, n)) v = make_float2(u[Y * ld + X], u[n2 + Y * ld + X]);
+        reinterpret_cast<float2*>(pu)[k] = v;
+    }
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < verts; k += stride) {
+        const int i = k % vp, j = k / vp;
+        pp[k] = i <= n ? p[j * (n + 1) + i] : 0.f;
+    }
+}
+
+__global__ void k_from_planar(int n, const float* __restrict__ pu, const float* __restrict__ pp, float* __restrict__ u,
+                              float* __restrict__ p) {
+    const int ld = 2 * n + 1, n2 = ld * ld, vp = pl_vpitch(n);
+    const int stride = gridDim.x * blockDim.x;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n2; k += stride) {
+        const int X = k % ld, Y = k / ld, o = pl_u(n, X, Y);
+        u[k] = pu[o];
+        u[n2 + k] = pu[o + 1];
+    }
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < (n + 1) * (n + 1); k += stride) {
+        const int i = k % (n + 1), j = k / (n + 1);
+        p[k] = pp[j * vp + i];
+    }
+}
+
+void launch_to_planar(cudaStream_t s, int n, const float* u, const float* p, float* pu, float* pp) {
+    const int work = 2 * pl_rows(n) * pl_pitch(n);
+    k_to_planar<<<std::min((work + 255) / 256, 4096), 256, 0, s>>>(n, u, p, pu, pp);
+}
+
+void launch_from_planar(cudaStream_t s, int n, const float* pu, const float* pp, float* u, float* p) {
+    const int work = (2 * n + 1) * (2 * n + 1);
+    k_from_planar<<<std::min((work + 255) / 256, 4096), 256, 0, s>>>(n, pu, pp, u, p);
+}
+
 // On the L: zero the entries of velocity arrays at nodes outside the L's unknowns' closure (the closed
 // removed quadrant) and of vertex arrays at vertices strictly inside it; either pointer pair may be null.
 __global__ void k_mask_l(int n, double* __restrict__ u, double* __restrict__ p) {
@@ -833,7 +943,7 @@ void launch_mask_l(cudaStream_t s, int n, double* u, double* p) {
     template void launch_restrict<T>(cudaStream_t, int, const T*, const T*, T*, T*, T*, T*, int);                 \
     template void launch_prolong_add<T>(cudaStream_t, int, const T*, const T*, T*, T*, int);              \
     template void launch_coarse_solve<T>(cudaStream_t, const double*, const T*, const T*, T*, T*);        \
-    template void launch_schur_diag<T>(cudaStream_t, int, const OpCoef<double>&, T*, int);                \
+    template void launch_schur_diag<T>(cudaStream_t, int, const OpCoef<double>&, T*, int, int);           \
     template void launch_pmean<T>(cudaStream_t, int, T*, double*, double*, int);                          \
     template void launch_load<T>(cudaStream_t, int, const MassCoef<T>&, const T*, const T*, T*, T*, int,  \
                                  double*, double*);

@@ -33,16 +33,16 @@ void launch_uzawa(cudaStream_t s, int n, const OpCoef<T>& c, T tau, T sigma, T* 
 // Refinement update (see refine.cu): float32 correction e, float64 iterate x, residual r stored as
 // (hi, lo) float pairs in the 8-byte slots of a float64 array:
 //   x += e,  r -= A e  (error-free float32 products, ~2^-48 relative),  r32 = float(r),
-//   partial sums of r.r.
+//   partial sums of r.r; planar: e and r32 in the planar float32 layout (common.cuh).
 void launch_ir_update_df(cudaStream_t s, int n, const OpCoef<float>& chi, const OpCoef<float>& clo,
                          const float* eu, const float* ep, double* xu, double* xp, double* ru, double* rp,
-                         float* r32u, float* r32p, double* partial, double* wpartial);
+                         float* r32u, float* r32p, double* partial, double* wpartial, bool planar = false);
 // p -= *scalar on every vertex (the zero-mean projection once the weighted mean is reduced)
 template <typename T>
 void launch_psub(cudaStream_t s, int n, T* p, const double* scalar);
 void launch_residual_df(cudaStream_t s, int n, const OpCoef<double>& c, const double* u, const double* p,
                         const double* f, const double* g, double* ru, double* rp, float* r32u, float* r32p,
-                        double* partial);
+                        double* partial, bool planar = false);   // planar: (r32u, r32p) in the planar layout
 
 // The same Uzawa step fused into one kernel with shared-memory halos: reads (u, p), writes
 // (u_out, p_out) (distinct buffers).
@@ -63,6 +63,16 @@ bool launch_uzawa_reg(int variant, cudaStream_t s, int n, const OpCoef<float>& c
                       const float* u, const float* p, const float* f, const float* g, const float* sinv,
                       float* u_out, float* p_out);
 cudaError_t prepare_uzawa_reg();
+// The same step on a float32 level in the planar layout (common.cuh), its tiles staged by
+// tensor-memory-access box copies; false (nothing launched) if the coefficients lack the register
+// tile's structure or the driver offers no tensor-map encoder.  uzawa_tma_available: the encoder is
+// there.  uzawa_tma_timeouts: nonzero if a CTA of the kernel gave up waiting (about a second) for
+// its tiles since the last call; clears the flag (synchronises with the device).
+constexpr int kDefaultTmaLevel = 6;   // lowest level held planar unless stokes_params.tma_level says otherwise
+bool launch_uzawa_tma(cudaStream_t s, int n, const OpCoef<float>& c, float tau, float sigma, const float* u,
+                      const float* p, const float* f, const float* g, const float* sinv, float* u_out, float* p_out);
+bool uzawa_tma_available();
+unsigned uzawa_tma_timeouts();
 // Does the compile-time structure of the register tile match these coefficients?
 bool reg_tables_match(const OpCoef<float>& c);
 template <typename T>
@@ -96,6 +106,19 @@ void launch_restrict(cudaStream_t s, int nc, const T* ru, const T* rp, T* fc, T*
 template <typename T>
 void launch_prolong_add(cudaStream_t s, int nc, const T* uc, const T* pc, T* u, T* p, int dom = kDomSquare);
 
+// Float32 levels in the planar layout (common.cuh): the residual of a planar level, and the transfers
+// between a planar fine level (N = 2 nc) and its coarse level, planar or not (pc_planar).
+void launch_residual_planar(cudaStream_t s, int n, const OpCoef<float>& c, const float* u, const float* p,
+                            const float* f, const float* g, float* ru, float* rp);
+void launch_restrict_planar(cudaStream_t s, int nc, bool pc_planar, const float* ru, const float* rp, float* fc,
+                            float* gc, float* uc, float* pc);
+void launch_prolong_add_planar(cudaStream_t s, int nc, bool pc_planar, const float* uc, const float* pc, float* u,
+                               float* p);
+// compact <-> planar copies of a float32 level state (u: velocity, p: vertex array); to_planar writes
+// zero at the boundary nodes and the padding of the planar velocity array
+void launch_to_planar(cudaStream_t s, int n, const float* u, const float* p, float* pu, float* pp);
+void launch_from_planar(cudaStream_t s, int n, const float* pu, const float* pp, float* u, float* p);
+
 // level-0 exact solve with the bordered inverse (27 x 27, float64)
 template <typename T>
 void launch_coarse_solve(cudaStream_t s, const double* inv, const T* f, const T* g, T* u, T* p);
@@ -113,9 +136,9 @@ void launch_dense_solve(cudaStream_t s, int n, const double* inv, int nb, const 
 cudaError_t prepare_dense_solve(int nb_max);
 constexpr int kMaxCoarseLevel = 3;   // N = 16: a bordered system of 2212 unknowns
 
-// Shat^{-1} per vertex (float64 computation, stored as T)
+// Shat^{-1} per vertex (float64 computation, stored as T), rows of vld entries (0: N + 1)
 template <typename T>
-void launch_schur_diag(cudaStream_t s, int n, const OpCoef<double>& c, T* sinv, int dom = kDomSquare);
+void launch_schur_diag(cudaStream_t s, int n, const OpCoef<double>& c, T* sinv, int dom = kDomSquare, int vld = 0);
 
 // p <- p - sum_i w_i p_i  (w = M_P 1, sum w = 1): partial sums then subtraction
 template <typename T>

@@ -75,16 +75,23 @@ __device__ __forceinline__ void sq_b_df(const OpCoef<float>& h, const OpCoef<flo
         }
 }
 
-template <int SQ>
+// PL: the float32 correction e is in the planar layout (common.cuh)
+template <int SQ, bool PL>
 __device__ __forceinline__ void visit_df(int i, int j, int n, const OpCoef<float>& h, const OpCoef<float>& l,
                                          const float* __restrict__ eu, const float* __restrict__ ep, DFAcc& a) {
     const int si = i - (SQ & 1), sj = j - (SQ >> 1);
     if (si < 0 || sj < 0 || si >= n || sj >= n) return;
     const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
     float vx[9], vy[9], pq[4];
-    load_sq<true>(gview(eu, 2 * n + 1), n, si, sj, vx);
-    load_sq<true>(gview(eu + n2, 2 * n + 1), n, si, sj, vy);
-    load_sq_p(gview(ep, n + 1), si, sj, pq);
+    if constexpr (PL) {
+        load_sq<true>(gviewp<false>(eu, n, 0), n, si, sj, vx);
+        load_sq<true>(gviewp<false>(eu, n, 1), n, si, sj, vy);
+        load_sq_p(gview(ep, pl_vpitch(n)), si, sj, pq);
+    } else {
+        load_sq<true>(gview(eu, 2 * n + 1), n, si, sj, vx);
+        load_sq<true>(gview(eu + n2, 2 * n + 1), n, si, sj, vy);
+        load_sq_p(gview(ep, n + 1), si, sj, pq);
+    }
     if (orient(si, sj, n)) {
         sq_rows_df<1, SQ, 0>(h, l, vx, vy, pq, a);
         sq_b_df<1, SQ>(h, l, vx, vy, a);
@@ -174,13 +181,21 @@ __device__ __forceinline__ void vwin_df2(const DFPairCoef& q, const float (&pw)[
     }
 }
 // CHECKED: blocks at the boundary (off the mid-lines) read with range tests and the Dirichlet mask
-template <int C, bool CHECKED, int... K, int... V>
+template <int C, bool CHECKED, bool PL, int... K, int... V>
 __device__ __forceinline__ void merged_df(int i, int j, int n, const DFPairCoef& q, const float* __restrict__ eu,
                                           const float* __restrict__ ep, DFAcc& a, std::integer_sequence<int, K...>,
                                           std::integer_sequence<int, V...>) {
     const int n2 = (2 * n + 1) * (2 * n + 1);
     float wx[25], wy[25], pw[9];
-    if constexpr (CHECKED) {
+    if constexpr (PL && CHECKED) {
+        win_load<C, true, true, true>(i, j, n, gviewp<false>(eu, n, 0), gviewp<false>(eu, n, 1), wx, wy,
+                                      std::make_integer_sequence<int, 25>{});
+        vwin_load<C>(i, j, n, gview(ep, pl_vpitch(n)), pw, std::make_integer_sequence<int, 9>{});
+    } else if constexpr (PL) {
+        win_load<C, true, true, false>(i, j, n, gviewp<true>(eu, n, 0), gviewp<true>(eu, n, 1), wx, wy,
+                                       std::make_integer_sequence<int, 25>{});
+        vwin_load<C>(i, j, n, gviewu(ep, pl_vpitch(n)), pw, std::make_integer_sequence<int, 9>{});
+    } else if constexpr (CHECKED) {
         win_load<C, true, true, true>(i, j, n, gview(eu, 2 * n + 1), gview(eu + n2, 2 * n + 1), wx, wy,
                                       std::make_integer_sequence<int, 25>{});
         vwin_load<C>(i, j, n, gview(ep, n + 1), pw, std::make_integer_sequence<int, 9>{});
@@ -226,6 +241,7 @@ __device__ __forceinline__ float2 df_sub(float2 a, const DF& b) {
     return renorm(s, __fadd_rn(e, __fsub_rn(a.y, b.lo)));
 }
 
+template <bool PL>
 __global__ void __launch_bounds__(NT, 4) k_ir_update_df(int n, const __grid_constant__ OpCoef<float> ch,
                                                      const __grid_constant__ OpCoef<float> cl,
                                                      const __grid_constant__ DFPairCoef cq,
@@ -249,16 +265,16 @@ __global__ void __launch_bounds__(NT, 4) k_ir_update_df(int n, const __grid_cons
         constexpr auto K25 = std::make_integer_sequence<int, 25>{};
         constexpr auto V9 = std::make_integer_sequence<int, 9>{};
         if (single && block_interior(n, 2)) {
-            if (orient(bi0, bj0, n) == 0) merged_df<0, false>(i, j, n, cq, eu, ep, a, K25, V9);
-            else merged_df<1, false>(i, j, n, cq, eu, ep, a, K25, V9);
+            if (orient(bi0, bj0, n) == 0) merged_df<0, false, PL>(i, j, n, cq, eu, ep, a, K25, V9);
+            else merged_df<1, false, PL>(i, j, n, cq, eu, ep, a, K25, V9);
         } else if (single) {
-            if (orient(bi0, bj0, n) == 0) merged_df<0, true>(i, j, n, cq, eu, ep, a, K25, V9);
-            else merged_df<1, true>(i, j, n, cq, eu, ep, a, K25, V9);
+            if (orient(bi0, bj0, n) == 0) merged_df<0, true, PL>(i, j, n, cq, eu, ep, a, K25, V9);
+            else merged_df<1, true, PL>(i, j, n, cq, eu, ep, a, K25, V9);
         } else {
-            visit_df<0>(i, j, n, ch, cl, eu, ep, a);
-            visit_df<1>(i, j, n, ch, cl, eu, ep, a);
-            visit_df<2>(i, j, n, ch, cl, eu, ep, a);
-            visit_df<3>(i, j, n, ch, cl, eu, ep, a);
+            visit_df<0, PL>(i, j, n, ch, cl, eu, ep, a);
+            visit_df<1, PL>(i, j, n, ch, cl, eu, ep, a);
+            visit_df<2, PL>(i, j, n, ch, cl, eu, ep, a);
+            visit_df<3, PL>(i, j, n, ch, cl, eu, ep, a);
         }
         const CellNodes cn = cell_nodes(i, j, n);
         const int ld = 2 * n + 1;
@@ -268,23 +284,24 @@ __global__ void __launch_bounds__(NT, 4) k_ir_update_df(int n, const __grid_cons
             int X, Y;
             slot_pos(i, j, s, X, Y);
             const size_t idx = (size_t)Y * ld + X;
+            const size_t i32 = PL ? (size_t)pl_u(n, X, Y) : idx;   // the float32 arrays' index
 #pragma unroll
             for (int comp = 0; comp < 2; ++comp) {
-                const size_t k = comp * n2 + idx;
-                xu[k] += (double)eu[k];
+                const size_t k = comp * n2 + idx, k32 = PL ? i32 + comp : k;
+                xu[k] += (double)eu[k32];
                 const float2 r = df_sub(ru[k], a.au[comp][s]);
                 ru[k] = r;
-                r32u[k] = r.x;
+                r32u[k32] = r.x;
                 ss = fmaf(r.x, r.x, ss);
             }
         }
-        const size_t vi = (size_t)j * (n + 1) + i;
-        const double xpn = xp[vi] + (double)ep[vi];
+        const size_t vi = (size_t)j * (n + 1) + i, vi32 = PL ? (size_t)j * pl_vpitch(n) + i : vi;
+        const double xpn = xp[vi] + (double)ep[vi32];
         xp[vi] = xpn;
         wp = vertex_weight(i, j, n) * xpn;
         const float2 r = df_sub(rp[vi], a.bu);
         rp[vi] = r;
-        r32p[vi] = r.x;
+        r32p[vi32] = r.x;
         ss = fmaf(r.x, r.x, ss);
     }
     const double2 t = block_sum2d_pair((double)ss, wp, tid);
@@ -295,7 +312,9 @@ __global__ void __launch_bounds__(NT, 4) k_ir_update_df(int n, const __grid_cons
     pdl_trigger();
 }
 
-// true float64 residual r = F - A x (x, F float64), written as two-float r and float32 r32
+// true float64 residual r = F - A x (x, F float64), written as two-float r and float32 r32 (PL: r32
+// in the planar layout)
+template <bool PL>
 __global__ void __launch_bounds__(NT) k_residual_df(int n, const __grid_constant__ OpCoef<double> c,
                                                     const double* __restrict__ u, const double* __restrict__ p,
                                                     const double* __restrict__ f, const double* __restrict__ g,
@@ -318,6 +337,7 @@ __global__ void __launch_bounds__(NT) k_residual_df(int n, const __grid_constant
             int X, Y;
             slot_pos(i, j, s, X, Y);
             const size_t idx = (size_t)Y * ld + X;
+            const size_t i32 = PL ? (size_t)pl_u(n, X, Y) : idx;
 #pragma unroll
             for (int comp = 0; comp < 2; ++comp) {
                 const size_t k = comp * n2 + idx;
@@ -325,7 +345,7 @@ __global__ void __launch_bounds__(NT) k_residual_df(int n, const __grid_constant
                 if (slot_unknown(cn, s)) r = f[k] - a.au[comp][s] - a.bt[comp][s];
                 const float hi = (float)r;
                 ru[k] = make_float2(hi, (float)(r - (double)hi));
-                r32u[k] = hi;
+                r32u[PL ? i32 + comp : k] = hi;
                 ss += r * r;
             }
         }
@@ -333,7 +353,7 @@ __global__ void __launch_bounds__(NT) k_residual_df(int n, const __grid_constant
         const double r = g[vi] - a.bu;
         const float hi = (float)r;
         rp[vi] = make_float2(hi, (float)(r - (double)hi));
-        r32p[vi] = hi;
+        r32p[PL ? (size_t)j * pl_vpitch(n) + i : vi] = hi;
         ss += r * r;
     }
     const double t = block_sum2d(ss, tid);
@@ -343,16 +363,17 @@ __global__ void __launch_bounds__(NT) k_residual_df(int n, const __grid_constant
 
 void launch_ir_update_df(cudaStream_t s, int n, const OpCoef<float>& chi, const OpCoef<float>& clo,
                          const float* eu, const float* ep, double* xu, double* xp, double* ru, double* rp,
-                         float* r32u, float* r32p, double* partial, double* wpartial) {
-    launch_pdl(k_ir_update_df, cells_grid(n), dim3(BX, BY), 0, s, n, chi, clo, make_df_pairs(chi, clo), eu, ep, xu, xp,
-               reinterpret_cast<float2*>(ru), reinterpret_cast<float2*>(rp), r32u, r32p, partial, wpartial);
+                         float* r32u, float* r32p, double* partial, double* wpartial, bool planar) {
+    launch_pdl(planar ? k_ir_update_df<true> : k_ir_update_df<false>, cells_grid(n), dim3(BX, BY), 0, s, n, chi, clo,
+               make_df_pairs(chi, clo), eu, ep, xu, xp, reinterpret_cast<float2*>(ru), reinterpret_cast<float2*>(rp), r32u,
+               r32p, partial, wpartial);
 }
 
 void launch_residual_df(cudaStream_t s, int n, const OpCoef<double>& c, const double* u, const double* p,
                         const double* f, const double* g, double* ru, double* rp, float* r32u, float* r32p,
-                        double* partial) {
-    launch_pdl(k_residual_df, cells_grid(n), dim3(BX, BY), 0, s, n, c, u, p, f, g, reinterpret_cast<float2*>(ru),
-                                                         reinterpret_cast<float2*>(rp), r32u, r32p, partial);
+                        double* partial, bool planar) {
+    launch_pdl(planar ? k_residual_df<true> : k_residual_df<false>, cells_grid(n), dim3(BX, BY), 0, s, n, c, u, p, f,
+               g, reinterpret_cast<float2*>(ru), reinterpret_cast<float2*>(rp), r32u, r32p, partial);
 }
 
 }  // namespace smg

@@ -25,6 +25,9 @@
 // per-cell rows of cellops.cuh on the same shared tiles.
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
+
+#include <cuda.h>
 
 #include "cellops.cuh"
 #include "kernels.cuh"
@@ -141,13 +144,20 @@ bool reg_tables_match(const OpCoef<float>& c) {
 
 namespace {
 
-struct RegTile {
+// Shared-memory tile geometry.  A CTA owns cells [i0, i0 + TX) x [j0, j0 + ty).  The u tile holds
+// cells from i0 - UX (two planes by column parity, UWH (u_x, u_y) pairs per lattice row, rows from
+// 2 (j0 - 3)); the f / u^{m-1/2} tile cells [i0 - 2, i0 + TX + 2) x [j0 - 2, j0 + ty + 2) (four planes
+// by node type, FW pairs per row); the p tile vertices from (i0 - PX, j0 - 3), PW per row; the g,
+// Shat^{-1} and dp tiles vertices from (i0 - DX, j0 - 1), DW per row, of which DN are computed.
+struct RegTile {   // staged by 4-byte asynchronous copies from the compact float32 layout
     static constexpr int TX = 28;
     static_assert(TX + 4 == 32, "one warp covers a row of the u^{m-1/2} region");
+    static constexpr int UX = 3, PX = 3, DX = 1;
     static constexpr int UWH = TX + 6;   // u: cells [i0-3, i0+TX+3); float2 per parity-plane row
     static constexpr int PW = TX + 6;    // p: vertices [i0-3, i0+TX+3)
     static constexpr int FW = TX + 4;    // f, u^{m-1/2}: cells [i0-2, i0+TX+2), one plane per node type
     static constexpr int DW = TX + 2;    // g, Shat^{-1}, dp: vertices [i0-1, i0+TX+1)
+    static constexpr int DN = TX + 2;
     // planes are padded to 8 float2 modulo 16 so that two planes start 16 banks apart: a warp that
     // stages 16 consecutive lattice points (both components) writes 32 distinct banks
     __host__ __device__ static constexpr int pad8(int m) { return m + ((8 - m % 16) + 16) % 16; }
@@ -156,6 +166,34 @@ struct RegTile {
     __host__ __device__ static constexpr int dsz(int ty) { return DW * (ty + 2); }
     __host__ __device__ static constexpr size_t bytes(int ty) {
         return 8 * (size_t)(2 * upl(ty) + 4 * fpl(ty)) + 4 * (size_t)(PW * (ty + 6) + 2 * dsz(ty));
+    }
+};
+
+// The same tile staged by the tensor-memory-access engine from the planar float32 layout: each tile
+// is one box copy, so rows start on 16-byte boundaries (the u and vertex tiles start one cell or
+// vertex further left, at a multiple of 4) and planes are dense.  Buffers are 128-byte aligned after
+// a 128-byte slot for the mbarrier.
+struct TmaTile {
+    static constexpr int TX = 28;
+    static constexpr int UX = 4, PX = 4, DX = 4;
+    static constexpr int UWH = 36;       // u: pairs [i0-4, i0+32)
+    static constexpr int PW = 36;        // p: vertices [i0-4, i0+32)
+    static constexpr int FW = TX + 4;
+    static constexpr int DW = 36;        // g, Shat^{-1}, dp: vertices [i0-4, i0+32)
+    static constexpr int DN = TX + 2;
+    __host__ __device__ static constexpr int upl(int ty) { return UWH * 2 * (ty + 6); }
+    __host__ __device__ static constexpr int fpl(int ty) { return FW * (ty + 4); }
+    __host__ __device__ static constexpr int dsz(int ty) { return DW * (ty + 2); }
+    __host__ __device__ static constexpr size_t a128(size_t b) { return (b + 127) / 128 * 128; }
+    __host__ __device__ static constexpr size_t off_f(int ty) { return 128 + a128(8 * (size_t)(2 * upl(ty))); }
+    __host__ __device__ static constexpr size_t off_p(int ty) { return off_f(ty) + a128(8 * (size_t)(4 * fpl(ty))); }
+    __host__ __device__ static constexpr size_t off_g(int ty) { return off_p(ty) + a128(4 * (size_t)(PW * (ty + 6))); }
+    __host__ __device__ static constexpr size_t off_s(int ty) { return off_g(ty) + a128(4 * (size_t)dsz(ty)); }
+    // dynamic shared memory per CTA (plus 128 bytes to align the base)
+    __host__ __device__ static constexpr size_t bytes(int ty) { return off_s(ty) + a128(4 * (size_t)dsz(ty)) + 128; }
+    // bytes the copies of one tile deliver
+    __host__ __device__ static constexpr unsigned tx_bytes(int ty) {
+        return (unsigned)(8 * (2 * upl(ty) + 4 * fpl(ty)) + 4 * (PW * (ty + 6) + 2 * dsz(ty)));
     }
 };
 constexpr int kRegMaxRows = 24;
@@ -174,6 +212,7 @@ __device__ __forceinline__ void cp_commit_wait() {
 
 // One component of the f / u^{m-1/2} tile (four planes by node type, FW float2 per row); lattice
 // coordinates are absolute, the region starts at cell (xc0, yc0).
+template <class G>
 struct QuadLat {
     static constexpr bool zero_filled = true;
     const float2* p;
@@ -181,24 +220,25 @@ struct QuadLat {
     bool ycomp;
     __device__ __forceinline__ float operator()(int X, int Y) const {
         const int dx = X - 2 * xc0, dy = Y - 2 * yc0;
-        const float2 e = p[((dx & 1) + 2 * (dy & 1)) * pl + (dy >> 1) * RegTile::FW + (dx >> 1)];
+        const float2 e = p[((dx & 1) + 2 * (dy & 1)) * pl + (dy >> 1) * G::FW + (dx >> 1)];
         return ycomp ? e.y : e.x;
     }
     __device__ __forceinline__ float at(int si, int sj, int a, int b) const { return (*this)(2 * si + a, 2 * sj + b); }
 };
 // one component of the u tile (two planes by column parity, as in uzawa_pair.cu)
+template <class G>
 struct ULat {
     static constexpr bool zero_filled = true;
     const float2* p;
     int pl, xh0, y0;
     bool ycomp;
     __device__ __forceinline__ float at(int si, int sj, int a, int b) const {
-        const float2 e = p[(a & 1) * pl + (2 * sj + b - y0) * RegTile::UWH + (si - xh0) + (a >> 1)];
+        const float2 e = p[(a & 1) * pl + (2 * sj + b - y0) * G::UWH + (si - xh0) + (a >> 1)];
         return ycomp ? e.y : e.x;
     }
     __device__ __forceinline__ float operator()(int X, int Y) const {
         const int dx = X - 2 * xh0;
-        const float2 e = p[(dx & 1) * pl + (Y - y0) * RegTile::UWH + (dx >> 1)];
+        const float2 e = p[(dx & 1) * pl + (Y - y0) * G::UWH + (dx >> 1)];
         return ycomp ? e.y : e.x;
     }
 };
@@ -213,13 +253,13 @@ __device__ __forceinline__ void addk(float& acc, float v) {
 }
 
 // ---- phase 1, fast path: A rows over the u window, B^T rows over the p window
-template <int C, int W>
+template <int C, int UWH, int W>
 __device__ __forceinline__ void a_term(const float2 (&a)[kGroups], const float2* t0, const float2* t1, float2 (&au)[4],
                                        float2 (&ctr)[4]) {
     if constexpr (a_win(C, W)) {
         constexpr int dx = W % 5 - 2, dy = W / 5 - 2;
         constexpr int g0 = kGid[C][0][W], g1 = kGid[C][1][W], g2 = kGid[C][2][W], g3 = kGid[C][3][W];
-        const float2 w = ((dx & 1) ? t1 : t0)[dy * RegTile::UWH + (dx >> 1)];
+        const float2 w = ((dx & 1) ? t1 : t0)[dy * UWH + (dx >> 1)];
         if constexpr (g0 >= 0) au[0] = __ffma2_rn(a[g0], w, au[0]);
         if constexpr (g1 >= 0) au[1] = __ffma2_rn(a[g1], w, au[1]);
         if constexpr (g2 >= 0) au[2] = __ffma2_rn(a[g2], w, au[2]);
@@ -230,10 +270,10 @@ __device__ __forceinline__ void a_term(const float2 (&a)[kGroups], const float2*
         if constexpr (W == 18) ctr[3] = w;
     }
 }
-template <int C, int... W>
+template <int C, int UWH, int... W>
 __device__ __forceinline__ void a_rows(const float2 (&a)[kGroups], const float2* t0, const float2* t1, float2 (&au)[4],
                                        float2 (&ctr)[4], std::integer_sequence<int, W...>) {
-    (a_term<C, W>(a, t0, t1, au, ctr), ...);
+    (a_term<C, UWH, W>(a, t0, t1, au, ctr), ...);
 }
 // B^T rows of the H, E, C nodes (the V row is zero) over a 3 x 3 vertex window at sp[b], row pitch LD
 template <int C, int LD, int V>
@@ -253,20 +293,20 @@ __device__ __forceinline__ void bt_rows(const float* sp, float2 (&bt)[4], std::i
     (bt_term<C, LD, V>(sp, bt), ...);
 }
 // B row of a vertex over the u^{m-1/2} window: f0 points at the vertex's node in plane 0
-template <int C, int W>
+template <int C, int FW, int W>
 __device__ __forceinline__ void b_term(const float2* f0, int fpl, float& acc) {
     if constexpr (kBx[C][W] != 0 || kBy[C][W] != 0) {
         constexpr int dx = W % 5 - 2, dy = W / 5 - 2;
         constexpr int plane = (dx & 1) + 2 * (dy & 1);
-        const float2 w = f0[plane * fpl + (dy >> 1) * RegTile::FW + (dx >> 1)];
+        const float2 w = f0[plane * fpl + (dy >> 1) * FW + (dx >> 1)];
         addk<kBx[C][W]>(acc, w.x);
         addk<kBy[C][W]>(acc, w.y);
     }
 }
-template <int C, int... W>
+template <int C, int FW, int... W>
 __device__ __forceinline__ float b_row(const float2* f0, int fpl, std::integer_sequence<int, W...>) {
     float acc = 0.f;
-    (b_term<C, W>(f0, fpl, acc), ...);
+    (b_term<C, FW, W>(f0, fpl, acc), ...);
     return acc;
 }
 
@@ -280,7 +320,7 @@ __device__ __forceinline__ void load_coef(const RegCoef& q, float2 (&a)[kGroups]
     }
 }
 
-template <int C, bool INNER>
+template <class G, int C, bool INNER>
 __device__ __forceinline__ void phase1_fast(const RegCoef& q, const float2* sU, int UPL, const float* sP, float2* sF,
                                            int FPL, int TY, int NW, int warp, int lane, int i0, int j0, int n) {
     float2 a[kGroups];
@@ -288,13 +328,13 @@ __device__ __forceinline__ void phase1_fast(const RegCoef& q, const float2* sU, 
     const float ti0 = q.ti[C][0], ti1 = q.ti[C][1];
     const float2 mb = f2(-q.b, -q.b);
     for (int r = warp; r < TY + 4; r += NW) {
-        const float2* t0 = sU + 2 * (r + 1) * RegTile::UWH + lane + 1;
+        const float2* t0 = sU + 2 * (r + 1) * G::UWH + lane + G::UX - 2;
         const float2* t1 = t0 + UPL;
         float2 au[4], ctr[4], bt[4];
 #pragma unroll
         for (int s = 0; s < 4; ++s) au[s] = ctr[s] = bt[s] = f2(0.f, 0.f);
-        a_rows<C>(a, t0, t1, au, ctr, std::make_integer_sequence<int, 25>{});
-        bt_rows<C, RegTile::PW>(sP + (r + 1) * RegTile::PW + lane + 1, bt, std::make_integer_sequence<int, 9>{});
+        a_rows<C, G::UWH>(a, t0, t1, au, ctr, std::make_integer_sequence<int, 25>{});
+        bt_rows<C, G::PW>(sP + (r + 1) * G::PW + lane + G::PX - 2, bt, std::make_integer_sequence<int, 9>{});
         // only unknowns keep their value (interior tiles hold nothing else)
         bool unk[4] = {true, true, true, true};
         if constexpr (!INNER) {
@@ -306,7 +346,7 @@ __device__ __forceinline__ void phase1_fast(const RegCoef& q, const float2* sU, 
             unk[2] = ci_in && cj_h;
             unk[3] = ci_h && cj_h;
         }
-        float2* fr = sF + r * RegTile::FW + lane;
+        float2* fr = sF + r * G::FW + lane;
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
             const float2 fs = fr[s * FPL];
@@ -321,58 +361,176 @@ __device__ __forceinline__ void phase1_fast(const RegCoef& q, const float2* sU, 
     }
 }
 
-template <int C>
+template <class G, int C>
 __device__ __forceinline__ void phase2_fast(const RegCoef& q, const float2* sF, int FPL, float* sG, const float* sS,
                                             float sigma, int TY, int NW, int warp, int lane) {
     const float b = q.b;
     for (int r = warp; r < TY + 2; r += NW) {
-        if (lane >= RegTile::DW) break;
-        const float2* f0 = sF + (r + 1) * RegTile::FW + lane + 1;
-        const float acc = b_row<C>(f0, FPL, std::make_integer_sequence<int, 25>{});
-        const int k = r * RegTile::DW + lane;
+        if (lane >= G::DN) break;
+        const float2* f0 = sF + (r + 1) * G::FW + lane + 1;
+        const float acc = b_row<C, G::FW>(f0, FPL, std::make_integer_sequence<int, 25>{});
+        const int k = r * G::DW + lane + G::DX - 1;
         // Shat^{-1} is zero-filled off the domain, so dp = 0 there
         sG[k] = sigma * sS[k] * fmaf(b, acc, -sG[k]);
     }
 }
 
-template <int C, bool INNER>
+// Where a cell's new values go: the compact float32 lattice (PLO false) or the planar layout
+template <bool PLO>
+__device__ __forceinline__ void store_node(float* __restrict__ u_out, int n, int X, int Y, float2 v) {
+    if constexpr (PLO) {
+        *reinterpret_cast<float2*>(u_out + pl_u(n, X, Y)) = v;
+    } else {
+        const int ld = 2 * n + 1, k = Y * ld + X;
+        u_out[k] = v.x;
+        u_out[ld * ld + k] = v.y;
+    }
+}
+template <bool PLO>
+__device__ __forceinline__ int vert_at(int n, int i, int j) {
+    return j * (PLO ? pl_vpitch(n) : n + 1) + i;
+}
+
+template <class G, bool PLO, int C, bool INNER>
 __device__ __forceinline__ void phase3_fast(const RegCoef& q, const float2* sF, int FPL, const float* sG,
                                             const float* sP, int TY, int NW, int warp, int lane, int i0, int j0,
                                             int n, float* __restrict__ u_out, float* __restrict__ p_out) {
     const float nb1 = -q.ti[C][1] * q.b;
-    const int ld = 2 * n + 1, n2 = ld * ld;
     for (int r = warp; r < TY; r += NW) {
-        if (lane >= RegTile::TX) break;
+        if (lane >= G::TX) break;
         const int ci = i0 + lane, cj = j0 + r;
         if (!INNER && (ci > n || cj > n)) continue;
         float2 bt[4];
 #pragma unroll
         for (int s = 0; s < 4; ++s) bt[s] = f2(0.f, 0.f);
-        bt_rows<C, RegTile::DW>(sG + (r + 1) * RegTile::DW + lane + 1, bt, std::make_integer_sequence<int, 9>{});
-        const float2* hr = sF + (r + 2) * RegTile::FW + lane + 2;
+        bt_rows<C, G::DW>(sG + (r + 1) * G::DW + lane + G::DX, bt, std::make_integer_sequence<int, 9>{});
+        const float2* hr = sF + (r + 2) * G::FW + lane + 2;
         float2 o[4];
         o[0] = hr[0];
 #pragma unroll
         for (int s = 1; s < 4; ++s) o[s] = __ffma2_rn(f2(nb1, nb1), bt[s], hr[s * FPL]);
         if constexpr (INNER) {
 #pragma unroll
-            for (int s = 0; s < 4; ++s) {
-                const int k = (2 * cj + (s >> 1)) * ld + 2 * ci + (s & 1);
-                u_out[k] = o[s].x;
-                u_out[n2 + k] = o[s].y;
-            }
+            for (int s = 0; s < 4; ++s) store_node<PLO>(u_out, n, 2 * ci + (s & 1), 2 * cj + (s >> 1), o[s]);
         } else {
             const CellNodes cn = cell_nodes(ci, cj, n);
 #pragma unroll
             for (int s = 0; s < 4; ++s) {
                 if (!slot_exists(cn, s)) continue;
-                const int k = (2 * cj + (s >> 1)) * ld + 2 * ci + (s & 1);
-                const bool uk = slot_unknown(cn, s);
-                u_out[k] = uk ? o[s].x : 0.f;
-                u_out[n2 + k] = uk ? o[s].y : 0.f;
+                store_node<PLO>(u_out, n, 2 * ci + (s & 1), 2 * cj + (s >> 1),
+                                slot_unknown(cn, s) ? o[s] : f2(0.f, 0.f));
             }
         }
-        p_out[cj * (n + 1) + ci] = sP[(r + 3) * RegTile::PW + lane + 3] + sG[(r + 1) * RegTile::DW + lane + 1];
+        p_out[vert_at<PLO>(n, ci, cj)] = sP[(r + 3) * G::PW + lane + G::PX] + sG[(r + 1) * G::DW + lane + G::DX];
+    }
+}
+
+// The three phases of the step on the staged tiles (sU, sP, sF = f, sG = g, sS = Shat^{-1}); writes
+// the new state of the CTA's cells to (u_out, p_out).
+template <class G, bool PLO, int NW>
+__device__ __forceinline__ void reg_phases(int n, int TY, int i0, int j0, const OpCoef<float>& c, const RegCoef& q,
+                                           float tau, float sigma, const float2* sU, float2* sF, const float* sP,
+                                           float* sG, const float* sS, float* __restrict__ u_out,
+                                           float* __restrict__ p_out) {
+    constexpr int TX = G::TX;
+    const int UPL = G::upl(TY), FPL = G::fpl(TY);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int h = n >> 1;
+    const bool fast = (h < i0 - 2 || h >= i0 + TX + 2) && (h < j0 - 2 || h >= j0 + TY + 2);
+    const bool inner = fast && i0 >= 4 && j0 >= 4 && i0 + TX + 3 <= n && j0 + TY + 3 <= n;
+    const int cls = orient(i0, j0, n);
+
+    const ULat<G> vux{sU, UPL, i0 - G::UX, 2 * (j0 - 3), false};
+    const ULat<G> vuy{sU, UPL, i0 - G::UX, 2 * (j0 - 3), true};
+    const SVert<float, G::PW> vp{sP, i0 - G::PX, j0 - 3};
+    const QuadLat<G> vhx{sF, FPL, i0 - 2, j0 - 2, false};
+    const QuadLat<G> vhy{sF, FPL, i0 - 2, j0 - 2, true};
+
+    // ---- u^{m-1/2} on cells (i0 - 2 + lane, j0 - 2 + r), written over f
+    if (fast) {
+        if (inner) {
+            if (cls == 0) phase1_fast<G, 0, true>(q, sU, UPL, sP, sF, FPL, TY, NW, warp, lane, i0, j0, n);
+            else phase1_fast<G, 1, true>(q, sU, UPL, sP, sF, FPL, TY, NW, warp, lane, i0, j0, n);
+        } else {
+            if (cls == 0) phase1_fast<G, 0, false>(q, sU, UPL, sP, sF, FPL, TY, NW, warp, lane, i0, j0, n);
+            else phase1_fast<G, 1, false>(q, sU, UPL, sP, sF, FPL, TY, NW, warp, lane, i0, j0, n);
+        }
+    } else {
+        for (int r = warp; r < TY + 4; r += NW) {
+            const int ci = i0 - 2 + lane, cj = j0 - 2 + r;
+            float2 hv[4];
+#pragma unroll
+            for (int s = 0; s < 4; ++s) hv[s] = f2(0.f, 0.f);
+            float2* fr = sF + r * G::FW + lane;
+            if (ci >= 0 && cj >= 0 && ci <= n && cj <= n) {
+                Acc<float> a;
+                cell_apply_auto<true, true, false, true, false>(ci, cj, n, c, vux, vuy, vp, a);
+                const CellNodes cn = cell_nodes(ci, cj, n);
+#pragma unroll
+                for (int s = 0; s < 4; ++s) {
+                    if (!slot_unknown(cn, s)) continue;
+                    const float2 fs = fr[s * FPL];
+                    const float w = tau * a.idg[s];
+                    hv[s] = f2(vux.at(ci, cj, s & 1, s >> 1) + w * (fs.x - a.au[0][s] - a.bt[0][s]),
+                               vuy.at(ci, cj, s & 1, s >> 1) + w * (fs.y - a.au[1][s] - a.bt[1][s]));
+                }
+            }
+#pragma unroll
+            for (int s = 0; s < 4; ++s) fr[s * FPL] = hv[s];
+        }
+    }
+    __syncthreads();
+
+    // ---- dp on vertices (i0 - 1 + lane, j0 - 1 + r), written over g
+    if (fast) {
+        if (cls == 0) phase2_fast<G, 0>(q, sF, FPL, sG, sS, sigma, TY, NW, warp, lane);
+        else phase2_fast<G, 1>(q, sF, FPL, sG, sS, sigma, TY, NW, warp, lane);
+    } else {
+        for (int r = warp; r < TY + 2; r += NW) {
+            if (lane >= G::DN) break;
+            const int vi = i0 - 1 + lane, vj = j0 - 1 + r;
+            const int k = r * G::DW + lane + G::DX - 1;
+            float d = 0.f;
+            if (vi >= 0 && vj >= 0 && vi <= n && vj <= n) {
+                Acc<float> a;
+                cell_apply_auto<false, false, true, false, false>(vi, vj, n, c, vhx, vhy, vp, a);
+                d = sigma * sS[k] * (a.bu - sG[k]);
+            }
+            sG[k] = d;
+        }
+    }
+    __syncthreads();
+
+    // ---- new (u, p) on the owned cells (i0 + lane, j0 + r)
+    if (fast) {
+        if (inner) {
+            if (cls == 0) phase3_fast<G, PLO, 0, true>(q, sF, FPL, sG, sP, TY, NW, warp, lane, i0, j0, n, u_out, p_out);
+            else phase3_fast<G, PLO, 1, true>(q, sF, FPL, sG, sP, TY, NW, warp, lane, i0, j0, n, u_out, p_out);
+        } else {
+            if (cls == 0) phase3_fast<G, PLO, 0, false>(q, sF, FPL, sG, sP, TY, NW, warp, lane, i0, j0, n, u_out, p_out);
+            else phase3_fast<G, PLO, 1, false>(q, sF, FPL, sG, sP, TY, NW, warp, lane, i0, j0, n, u_out, p_out);
+        }
+    } else {
+        const SVert<float, G::DW> vd{sG, i0 - G::DX, j0 - 1};
+        for (int r = warp; r < TY; r += NW) {
+            if (lane >= TX) break;
+            const int ci = i0 + lane, cj = j0 + r;
+            if (ci > n || cj > n) continue;
+            Acc<float> a;
+            cell_apply_auto<false, true, false, true, false>(ci, cj, n, c, vhx, vhy, vd, a);
+            const CellNodes cn = cell_nodes(ci, cj, n);
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                if (!slot_exists(cn, s)) continue;
+                float2 o = f2(0.f, 0.f);
+                if (slot_unknown(cn, s)) {
+                    const float w = tau * a.idg[s];
+                    o = f2(vhx.at(ci, cj, s & 1, s >> 1) - w * a.bt[0][s], vhy.at(ci, cj, s & 1, s >> 1) - w * a.bt[1][s]);
+                }
+                store_node<PLO>(u_out, n, 2 * ci + (s & 1), 2 * cj + (s >> 1), o);
+            }
+            p_out[vert_at<PLO>(n, ci, cj)] = sP[(r + 3) * G::PW + lane + G::PX] + sG[(r + 1) * G::DW + lane + G::DX];
+        }
     }
 }
 
@@ -399,7 +557,6 @@ __global__ void __launch_bounds__(32 * NW, MINB)
     const int ld = 2 * n + 1, n2 = ld * ld, h = n >> 1;
     const bool fast = (h < i0 - 2 || h >= i0 + TX + 2) && (h < j0 - 2 || h >= j0 + TY + 2);
     const bool inner = fast && i0 >= 4 && j0 >= 4 && i0 + TX + 3 <= n && j0 + TY + 3 <= n;
-    const int cls = orient(i0, j0, n);
 
     // ---- asynchronous staging.  Lane l copies component l >> 4 of lattice point 16 q + (l & 15) of a row:
     // one instruction moves 16 consecutive points with both components (two 64-byte global segments,
@@ -474,101 +631,100 @@ __global__ void __launch_bounds__(32 * NW, MINB)
     }
     __syncthreads();
 
-    const ULat vux{sU, UPL, i0 - 3, 2 * (j0 - 3), false};
-    const ULat vuy{sU, UPL, i0 - 3, 2 * (j0 - 3), true};
-    const SVert<float, G::PW> vp{sP, i0 - 3, j0 - 3};
-    const QuadLat vhx{sF, FPL, i0 - 2, j0 - 2, false};
-    const QuadLat vhy{sF, FPL, i0 - 2, j0 - 2, true};
 
-    // ---- u^{m-1/2} on cells (i0 - 2 + lane, j0 - 2 + r), written over f
-    if (fast) {
-        if (inner) {
-            if (cls == 0) phase1_fast<0, true>(q, sU, UPL, sP, sF, FPL, TY, NW, warp, lane, i0, j0, n);
-            else phase1_fast<1, true>(q, sU, UPL, sP, sF, FPL, TY, NW, warp, lane, i0, j0, n);
-        } else {
-            if (cls == 0) phase1_fast<0, false>(q, sU, UPL, sP, sF, FPL, TY, NW, warp, lane, i0, j0, n);
-            else phase1_fast<1, false>(q, sU, UPL, sP, sF, FPL, TY, NW, warp, lane, i0, j0, n);
-        }
-    } else {
-        for (int r = warp; r < TY + 4; r += NW) {
-            const int ci = i0 - 2 + lane, cj = j0 - 2 + r;
-            float2 hv[4];
-#pragma unroll
-            for (int s = 0; s < 4; ++s) hv[s] = f2(0.f, 0.f);
-            float2* fr = sF + r * G::FW + lane;
-            if (ci >= 0 && cj >= 0 && ci <= n && cj <= n) {
-                Acc<float> a;
-                cell_apply_auto<true, true, false, true, false>(ci, cj, n, c, vux, vuy, vp, a);
-                const CellNodes cn = cell_nodes(ci, cj, n);
-#pragma unroll
-                for (int s = 0; s < 4; ++s) {
-                    if (!slot_unknown(cn, s)) continue;
-                    const float2 fs = fr[s * FPL];
-                    const float w = tau * a.idg[s];
-                    hv[s] = f2(vux.at(ci, cj, s & 1, s >> 1) + w * (fs.x - a.au[0][s] - a.bt[0][s]),
-                               vuy.at(ci, cj, s & 1, s >> 1) + w * (fs.y - a.au[1][s] - a.bt[1][s]));
-                }
-            }
-#pragma unroll
-            for (int s = 0; s < 4; ++s) fr[s * FPL] = hv[s];
-        }
+    reg_phases<G, false, NW>(n, TY, i0, j0, c, q, tau, sigma, sU, sF, sP, sG, sS, u_out, p_out);
+    pdl_trigger();
+}
+
+// ---------------------------------------------------------------------------------------------
+// The step on planar float32 levels: the five input tiles arrive by tensor-memory-access box copies
+// (cp.async.bulk.tensor into the CTA's own shared memory, completion counted on one mbarrier), so
+// staging issues no per-thread load instructions; zero fill outside the arrays and the layout's
+// zero boundary and padding replace the masking of the asynchronous-copy path.
+
+struct TmaMaps {
+    CUtensorMap u;        // velocity, 3-d: (2 pl_pitch floats, pl_rows rows, 2 parity planes)
+    CUtensorMap f0, f1;   // right-hand side at even / odd rows, 3-d: (floats, cell rows, parity planes)
+    CUtensorMap p, g, s;  // vertex arrays, 2-d: (pl_vpitch floats, N + 1 rows)
+};
+
+// Set (never cleared by the kernels) when a CTA gave up waiting for its tiles; read and cleared by
+// uzawa_tma_timeouts().
+__device__ unsigned g_tma_timeout = 0;
+
+constexpr long long kTmaWaitCycles = 2000000000LL;   // about one second at the GPU's clock
+
+__device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait on phase `parity` of the mbarrier at shared address bar; false after about a second
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
+    const long long t0 = clock64();
+    while (!mbar_try(bar, parity))
+        if (clock64() - t0 > kTmaWaitCycles) return false;
+    return true;
+}
+__device__ __forceinline__ void tma_2d(unsigned dst, const CUtensorMap* map, int x, int y, unsigned bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(dst), "l"(map), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tma_3d(unsigned dst, const CUtensorMap* map, int x, int y, int z, unsigned bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(dst), "l"(map), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+
+template <int NW, int MINB>
+__global__ void __launch_bounds__(32 * NW, MINB)
+    k_uzawa_tma(int n, int TY, TileOrder ord, const __grid_constant__ OpCoef<float> c, const __grid_constant__ RegCoef q,
+                float tau, float sigma, const __grid_constant__ TmaMaps maps, float* __restrict__ u_out,
+                float* __restrict__ p_out) {
+    using G = TmaTile;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    float2* sU = reinterpret_cast<float2*>(base + 128);
+    float2* sF = reinterpret_cast<float2*>(base + G::off_f(TY));
+    float* sP = reinterpret_cast<float*>(base + G::off_p(TY));
+    float* sG = reinterpret_cast<float*>(base + G::off_g(TY));
+    float* sS = reinterpret_cast<float*>(base + G::off_s(TY));
+    const unsigned bar = (unsigned)__cvta_generic_to_shared(base);
+    int tc, tr;
+    ord.tile(blockIdx.x, tc, tr);
+    const int i0 = tc * G::TX, j0 = tr * TY;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-
-    // ---- dp on vertices (i0 - 1 + lane, j0 - 1 + r), written over g
-    if (fast) {
-        if (cls == 0) phase2_fast<0>(q, sF, FPL, sG, sS, sigma, TY, NW, warp, lane);
-        else phase2_fast<1>(q, sF, FPL, sG, sS, sigma, TY, NW, warp, lane);
-    } else {
-        for (int r = warp; r < TY + 2; r += NW) {
-            if (lane >= G::DW) break;
-            const int vi = i0 - 1 + lane, vj = j0 - 1 + r;
-            float d = 0.f;
-            if (vi >= 0 && vj >= 0 && vi <= n && vj <= n) {
-                Acc<float> a;
-                cell_apply_auto<false, false, true, false, false>(vi, vj, n, c, vhx, vhy, vp, a);
-                const int k = r * G::DW + lane;
-                d = sigma * sS[k] * (a.bu - sG[k]);
-            }
-            sG[r * G::DW + lane] = d;
-        }
+    pdl_wait();   // the inputs are the previous kernel's outputs
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(G::tx_bytes(TY)) : "memory");
+        const unsigned du = (unsigned)__cvta_generic_to_shared(sU), df = (unsigned)__cvta_generic_to_shared(sF);
+        tma_3d(du, &maps.u, 2 * (i0 - G::UX), 2 * (j0 - 3), 0, bar);
+        tma_3d(df, &maps.f0, 2 * (i0 - 2), j0 - 2, 0, bar);
+        tma_3d(df + 8 * 2 * G::fpl(TY), &maps.f1, 2 * (i0 - 2), j0 - 2, 0, bar);
+        tma_2d((unsigned)__cvta_generic_to_shared(sP), &maps.p, i0 - G::PX, j0 - 3, bar);
+        tma_2d((unsigned)__cvta_generic_to_shared(sG), &maps.g, i0 - G::DX, j0 - 1, bar);
+        tma_2d((unsigned)__cvta_generic_to_shared(sS), &maps.s, i0 - G::DX, j0 - 1, bar);
     }
-    __syncthreads();
-
-    // ---- new (u, p) on the owned cells (i0 + lane, j0 + r)
-    if (fast) {
-        if (inner) {
-            if (cls == 0) phase3_fast<0, true>(q, sF, FPL, sG, sP, TY, NW, warp, lane, i0, j0, n, u_out, p_out);
-            else phase3_fast<1, true>(q, sF, FPL, sG, sP, TY, NW, warp, lane, i0, j0, n, u_out, p_out);
-        } else {
-            if (cls == 0) phase3_fast<0, false>(q, sF, FPL, sG, sP, TY, NW, warp, lane, i0, j0, n, u_out, p_out);
-            else phase3_fast<1, false>(q, sF, FPL, sG, sP, TY, NW, warp, lane, i0, j0, n, u_out, p_out);
+    const bool ok = mbar_wait_bounded(bar, 0);
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) {
+            atomicOr(&g_tma_timeout, 1u);
+            mbar_wait_bounded(bar, 0);   // once more, for copies still in flight into this CTA's memory
         }
-    } else {
-        const SVert<float, G::DW> vd{sG, i0 - 1, j0 - 1};
-        for (int r = warp; r < TY; r += NW) {
-            if (lane >= TX) break;
-            const int ci = i0 + lane, cj = j0 + r;
-            if (ci > n || cj > n) continue;
-            Acc<float> a;
-            cell_apply_auto<false, true, false, true, false>(ci, cj, n, c, vhx, vhy, vd, a);
-            const CellNodes cn = cell_nodes(ci, cj, n);
-#pragma unroll
-            for (int s = 0; s < 4; ++s) {
-                if (!slot_exists(cn, s)) continue;
-                const int k = (2 * cj + (s >> 1)) * ld + 2 * ci + (s & 1);
-                float ox = 0.f, oy = 0.f;
-                if (slot_unknown(cn, s)) {
-                    const float w = tau * a.idg[s];
-                    ox = vhx.at(ci, cj, s & 1, s >> 1) - w * a.bt[0][s];
-                    oy = vhy.at(ci, cj, s & 1, s >> 1) - w * a.bt[1][s];
-                }
-                u_out[k] = ox;
-                u_out[n2 + k] = oy;
-            }
-            p_out[cj * (n + 1) + ci] = sP[(r + 3) * G::PW + lane + 3] + sG[(r + 1) * G::DW + lane + 1];
-        }
+        return;
     }
+    reg_phases<G, true, NW>(n, TY, i0, j0, c, q, tau, sigma, sU, sF, sP, sG, sS, u_out, p_out);
     pdl_trigger();
 }
 
@@ -577,13 +733,17 @@ cudaError_t reg_smem_attr() {
     return cudaFuncSetAttribute(k_uzawa_reg<NW, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)RegTile::bytes(kRegMaxRows));
 }
+template <int NW, int MINB>
+cudaError_t tma_smem_attr() {
+    return cudaFuncSetAttribute(k_uzawa_tma<NW, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)TmaTile::bytes(kRegMaxRows));
+}
 
 // Rows per tile for level size n: the least work on the busiest SM, (tiles per SM, rounded up) x
 // (work of one tile, about ty + 4 rows of the u^{m-1/2} region), among the tile heights that keep
-// at least MINB CTAs resident per SM.
-template <int NW, int MINB>
-int reg_rows(int n) {
-    static int cache[32] = {};
+// at least MINB CTAs of kernel k (dynamic shared memory bytes(ty)) resident per SM.
+template <class G, class K>
+int tile_rows(int n, K k, int nthreads, int minb, int* cache) {
     const int lv = 31 - __builtin_clz((unsigned)n);
     int& r = cache[lv & 31];
     if (r) return r;
@@ -591,13 +751,13 @@ int reg_rows(int n) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     sms = std::max(sms, 1);
-    const int cols = (n + 1 + RegTile::TX - 1) / RegTile::TX;
+    const int cols = (n + 1 + G::TX - 1) / G::TX;
     double best = 1e300;
     int best_ty = 12;
     for (int ty = 4; ty <= kRegMaxRows; ++ty) {
         int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_uzawa_reg<NW, MINB>, 32 * NW,
-                                                          RegTile::bytes(ty)) != cudaSuccess || per_sm < MINB)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, nthreads, G::bytes(ty)) != cudaSuccess ||
+            per_sm < minb)
             continue;
         const long tiles = (long)cols * ((n + 1 + ty - 1) / ty);
         const double cost = (double)((tiles + sms - 1) / sms) * (ty + 4);
@@ -612,18 +772,93 @@ int reg_rows(int n) {
 }
 
 template <int NW, int MINB>
+int reg_rows(int n) {
+    static int cache[32] = {};
+    return tile_rows<RegTile>(n, k_uzawa_reg<NW, MINB>, 32 * NW, MINB, cache);
+}
+template <int NW, int MINB>
+int tma_rows(int n) {
+    static int cache[32] = {};
+    return tile_rows<TmaTile>(n, k_uzawa_tma<NW, MINB>, 32 * NW, MINB, cache);
+}
+
+template <class G>
+TileOrder tile_order(int n, int ty) {
+    TileOrder ord;
+    ord.cols = (n + 1 + G::TX - 1) / G::TX;
+    ord.rows = (n + 1 + ty - 1) / ty;
+    mid_band(n / 2, G::TX, ord.cols, ord.c0, ord.nc);
+    mid_band(n / 2, ty, ord.rows, ord.r0, ord.nr);
+    return ord;
+}
+
+template <int NW, int MINB>
 bool launch_reg_v(cudaStream_t s, int n, const OpCoef<float>& c, float tau, float sigma, const float* u, const float* p,
                   const float* f, const float* g, const float* sinv, float* u_out, float* p_out) {
     RegCoef q;
     if (!make_reg_coef(c, tau, q)) return false;
     const int ty = reg_rows<NW, MINB>(n);
-    TileOrder ord;
-    ord.cols = (n + 1 + RegTile::TX - 1) / RegTile::TX;
-    ord.rows = (n + 1 + ty - 1) / ty;
-    mid_band(n / 2, RegTile::TX, ord.cols, ord.c0, ord.nc);
-    mid_band(n / 2, ty, ord.rows, ord.r0, ord.nr);
+    const TileOrder ord = tile_order<RegTile>(n, ty);
     launch_pdl(k_uzawa_reg<NW, MINB>, dim3(ord.cols * ord.rows), dim3(32 * NW), RegTile::bytes(ty), s, n, ty, ord, c, q, tau,
                sigma, u, p, f, g, sinv, u_out, p_out);
+    return true;
+}
+
+// cuTensorMapEncodeTiled, from the driver through the runtime's entry-point query (no link to the
+// driver library)
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+    static const EncodeTiledFn fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult qr{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &qr) != cudaSuccess ||
+            qr != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        cudaGetLastError();
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
+// float32 box map over `rank` dimensions (strides in bytes for dimensions 1..rank-1), zero fill
+bool encode_box(CUtensorMap& m, const float* base, cuuint32_t rank, const cuuint64_t* dims, const cuuint64_t* strides,
+                const cuuint32_t* box) {
+    const cuuint32_t es[3] = {1, 1, 1};
+    return encode_tiled()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, const_cast<float*>(base), dims, strides, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The tile maps of a planar level with N = n, tile height ty
+bool make_tma_maps(int n, int ty, const float* u, const float* p, const float* f, const float* g, const float* sinv,
+                   TmaMaps& m) {
+    if (!encode_tiled()) return false;
+    const cuuint64_t P = (cuuint64_t)pl_pitch(n), RP = (cuuint64_t)pl_rows(n), VP = (cuuint64_t)pl_vpitch(n);
+    const cuuint64_t rows = (cuuint64_t)n + 1;
+    const cuuint64_t ud[3] = {2 * P, RP, 2}, us[2] = {8 * P, 8 * P * RP};
+    const cuuint32_t ub[3] = {2 * TmaTile::UWH, (cuuint32_t)(2 * (ty + 6)), 2};
+    const cuuint64_t fd[3] = {2 * P, rows, 2}, fs[2] = {16 * P, 8 * P * RP};
+    const cuuint32_t fb[3] = {2 * TmaTile::FW, (cuuint32_t)(ty + 4), 2};
+    const cuuint64_t vd[2] = {VP, rows}, vs[1] = {4 * VP};
+    const cuuint32_t pb[2] = {TmaTile::PW, (cuuint32_t)(ty + 6)}, gb[2] = {TmaTile::DW, (cuuint32_t)(ty + 2)};
+    return encode_box(m.u, u, 3, ud, us, ub) && encode_box(m.f0, f, 3, fd, fs, fb) &&
+           encode_box(m.f1, f + 2 * P, 3, fd, fs, fb) && encode_box(m.p, p, 2, vd, vs, pb) &&
+           encode_box(m.g, g, 2, vd, vs, gb) && encode_box(m.s, sinv, 2, vd, vs, gb);
+}
+
+template <int NW, int MINB>
+bool launch_tma_v(cudaStream_t s, int n, const OpCoef<float>& c, float tau, float sigma, const float* u, const float* p,
+                  const float* f, const float* g, const float* sinv, float* u_out, float* p_out) {
+    RegCoef q;
+    if (!make_reg_coef(c, tau, q)) return false;
+    const int ty = tma_rows<NW, MINB>(n);
+    TmaMaps m;
+    if (!make_tma_maps(n, ty, u, p, f, g, sinv, m)) return false;
+    const TileOrder ord = tile_order<TmaTile>(n, ty);
+    launch_pdl(k_uzawa_tma<NW, MINB>, dim3(ord.cols * ord.rows), dim3(32 * NW), TmaTile::bytes(ty), s, n, ty, ord, c, q,
+               tau, sigma, m, u_out, p_out);
     return true;
 }
 
@@ -632,6 +867,7 @@ bool launch_reg_v(cudaStream_t s, int n, const OpCoef<float>& c, float tau, floa
 cudaError_t prepare_uzawa_reg() {
     cudaError_t e = reg_smem_attr<8, 2>();
     if (e == cudaSuccess) e = reg_smem_attr<8, 4>();
+    if (e == cudaSuccess) e = tma_smem_attr<8, 3>();
     return e;
 }
 
@@ -640,6 +876,21 @@ bool launch_uzawa_reg(int variant, cudaStream_t s, int n, const OpCoef<float>& c
                       float* u_out, float* p_out) {
     if (variant == 0) return launch_reg_v<8, 2>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
     return launch_reg_v<8, 4>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
+}
+
+bool launch_uzawa_tma(cudaStream_t s, int n, const OpCoef<float>& c, float tau, float sigma, const float* u,
+                      const float* p, const float* f, const float* g, const float* sinv, float* u_out, float* p_out) {
+    return launch_tma_v<8, 3>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
+}
+
+bool uzawa_tma_available() { return encode_tiled() != nullptr; }
+
+unsigned uzawa_tma_timeouts() {
+    unsigned v = 0;
+    const unsigned zero = 0;
+    if (cudaMemcpyFromSymbol(&v, g_tma_timeout, sizeof v) != cudaSuccess) return 0;
+    if (v) cudaMemcpyToSymbol(g_tma_timeout, &zero, sizeof zero);
+    return v;
 }
 
 }  // namespace smg

@@ -221,7 +221,7 @@ def test_smoother_float32_every_variant(discs, Solver, k, variant):
     F = d.to_vec(f, g)
     for _ in range(3):
         x = H.uzawa_step(H.finest, x, F, mg.Params())
-    S = Solver(k + 1, beta, precision="mixed")
+    S = Solver(k + 1, beta, precision="mixed", tma_level=14)   # every level on the compact variants
     t = lambda a: dev(a).float().contiguous()
     tu, tp = t(u), t(p)
     old = step_variant(k + 1)

@@ -1,0 +1,122 @@
+"""Planar float32 levels (stokes_params.tma_level): the float32 layout whose rows start on 16-byte
+boundaries, and the one-kernel Uzawa step (Sec. 4) whose input tiles arrive by tensor-memory-access
+box copies, against the oracle:
+
+* nu float32 steps on a planar finest level equal the oracle's three-line steps within 2e-5 of the
+  largest entry (float32 rounding of row sums of a few dozen terms) at k = 5, 6 (N + 1 = 2^(k+1) + 1
+  cells per side fill no tile: ragged tiles at both ends, both mid-line bands, tiles whose boxes
+  reach outside the arrays on every side) and several beta (k = 9: tests/test_gpu_oracle_k9.py);
+* mixed-precision V and W cycles with planar levels from 5 up (so a planar level restricts to a
+  compact one) converge to the oracle's direct solution with the oracle's cycle count (within one),
+  with coarsest level 0 and 3;
+* a planar hierarchy and an all-compact one solve the same problem in the same number of steps.
+"""
+import numpy as np
+import pytest
+
+from oracle import fem
+from oracle import multigrid as mg
+from paper_1502_04070_gb300 import workloads
+from tests._gpu import dev, host, rel_err
+
+pytestmark = pytest.mark.gpu
+
+KMAX = 6
+
+
+@pytest.fixture(scope="module")
+def discs():
+    return fem.discretizations(KMAX + 1)
+
+
+def _state(k, seed):
+    u, p = workloads.random_state(k, seed)
+    f, g = workloads.random_nodal(k, seed + 1000)
+    return u, p, f, g - g.mean()
+
+
+@pytest.mark.parametrize("k", [5, 6])
+@pytest.mark.parametrize("beta", [0.0, 1e2, 1e8])
+@pytest.mark.parametrize("nu", [1, 3])
+def test_planar_step_by_oracle(discs, k, beta, nu):
+    from paper_1502_04070_gb300.solver import Solver
+    H = mg.Hierarchy(k + 1, beta, discs[:k + 1])
+    d = H.discs[-1]
+    u, p, f, g = _state(k, 300 + k)
+    # the oracle from the same float32-rounded inputs, in float64
+    r32 = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    x = d.to_vec(r32(u), r32(p))
+    F = d.to_vec(r32(f), r32(g))
+    for _ in range(nu):
+        x = H.uzawa_step(H.finest, x, F, mg.Params())
+    S = Solver(k + 1, beta, precision="mixed", tma_level=5)
+    t = lambda a: dev(a).float().contiguous()
+    tu, tp = t(u), t(p)
+    S.smooth_f32(tu, tp, t(f), t(g), nu)
+    uo, po = d.from_vec(x)
+    got = np.concatenate([host(tu.double()).ravel(), host(tp.double()).ravel()])
+    ref = np.concatenate([uo.ravel(), po.ravel()])
+    assert rel_err(got, ref) < 2e-5, rel_err(got, ref)
+    S.close()
+
+
+def test_planar_step_zeroes_the_boundary(discs):
+    """Boundary velocity nodes come back zero whatever the caller's arrays hold there (the planar
+    copy of the state is zero on the Dirichlet ring)."""
+    from paper_1502_04070_gb300.solver import Solver
+    k = 5
+    u, p, f, g = _state(k, 77)
+    u = u.copy()
+    u[:, 0, :] = 1.0
+    u[:, :, -1] = -2.0
+    S = Solver(k + 1, 1e2, precision="mixed", tma_level=5)
+    tu = dev(u).float().contiguous()
+    tp = dev(p).float().contiguous()
+    S.smooth_f32(tu, tp, dev(f).float().contiguous(), dev(g).float().contiguous(), 1)
+    out = host(tu)
+    assert np.all(out[:, 0, :] == 0) and np.all(out[:, -1, :] == 0)
+    assert np.all(out[:, :, 0] == 0) and np.all(out[:, :, -1] == 0)
+    S.close()
+
+
+_DIRECT = {}
+
+
+@pytest.mark.parametrize("gamma,coarse_level", [(1, 0), (2, 0), (2, 3), (1, 3)])
+def test_planar_mixed_solve_by_oracle(discs, gamma, coarse_level):
+    """k = 5 with levels 5 and up planar: the finest level restricts to a compact level."""
+    from paper_1502_04070_gb300.solver import Solver
+    k, beta = 5, 1e2
+    d = discs[k]
+    H = mg.Hierarchy(k + 1, beta, discs[:k + 1], coarse_level=coarse_level)
+    fn, gn = workloads.random_nodal(k, 90 + k)
+    F = d.load(fn, gn, project_g=True)
+    _, hist = H.solve(F, mg.Params(gamma=gamma), tol=1e-8, max_cycles=100)
+    if k not in _DIRECT:
+        _DIRECT[k] = H.direct(F)   # the finest system's solution: the same for every coarsest level
+    xd = _DIRECT[k]
+    S = Solver(k + 1, beta, precision="mixed", gamma=gamma, coarse_level=coarse_level, tma_level=5)
+    f, g = S.load_vectors(dev(fn), dev(gn), project_g=True)
+    u, p, rep = S.solve(f, g, tol=1e-8, max_cycles=100)
+    assert rep.converged, rep
+    assert abs(rep.cycles - (len(hist) - 1)) <= 1, (rep.cycles, len(hist) - 1)
+    assert rel_err(d.to_vec(host(u), host(p)), xd) < 1e-6
+    S.close()
+
+
+def test_planar_and_compact_hierarchies_agree(discs):
+    """k = 7 (N = 256), manufactured-style random data: the solve with levels 5..7 planar and the
+    solve with every level compact take the same steps, and both meet the tolerance in float64."""
+    from paper_1502_04070_gb300.solver import Solver
+    k, beta = 7, 1e4
+    fn, gn = workloads.random_nodal(k, 5)
+    out = {}
+    for tl in (5, 14):
+        S = Solver(k + 1, beta, precision="mixed", tma_level=tl)
+        f, g = S.load_vectors(dev(fn), dev(gn), project_g=True)
+        u, p, rep = S.solve(f, g, tol=1e-8, max_cycles=100)
+        assert rep.converged and rep.rel_residual <= 1e-8, rep
+        out[tl] = (rep.cycles, np.concatenate([host(u).ravel(), host(p).ravel()]))
+        S.close()
+    assert abs(out[5][0] - out[14][0]) <= 1, (out[5][0], out[14][0])
+    assert rel_err(out[5][1], out[14][1]) < 1e-6
