@@ -74,6 +74,7 @@ def parse():
     ap.add_argument("--coarse-level", type=int, default=0, help="kernel modes: coarsest level of the iteration")
     ap.add_argument("--tma-level", type=int, default=0,
                     help="kernel modes: lowest planar float32 level (0: the library default; 14: none)")
+    ap.add_argument("--planar-variant", type=int, default=None, help="kernel modes: force this planar step variant")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--host-loop", action="store_true",
@@ -109,6 +110,10 @@ def run_kernel(args):
         for item in (args.variants.split(",") if args.variants else []):
             kl, v = item.split(":")
             set_step_variant(int(kl) + 1, int(v))
+    if args.planar_variant is not None:
+        from paper_1502_04070_gb300.solver import set_planar_step_variant
+        for l in range(2, k + 2):
+            set_planar_step_variant(l, args.planar_variant)
     if args.host_loop:
         S.set_timing(True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -306,8 +306,8 @@ stokes_status stokes_residual_norm2_noalloc(int levels, double beta, const doubl
 
 /* Chooses, for every level of a STOKES_MIXED handle whose size has not been tuned in this process,
  * the fastest float32 Uzawa step variant (one-kernel tiles of several kinds and shapes, or the
- * three-kernel step with several block shapes) by timing each on the handle's buffers; the choice
- * is kept process-wide per level size.  Untuned levels use the three-kernel step below N = 128 and
+ * three-kernel step with several block shapes; on planar levels the planar step variants) by timing
+ * each on the handle's buffers; the choice is kept process-wide per level size.  Untuned levels use the three-kernel step below N = 128 and
  * the 32 x 16 fused tile above.  Synchronises the stream. */
 stokes_status stokes_autotune(stokes_handle* h);
 /* The step variant currently used for a float32 level with `levels` levels (N = 2^levels), -1 if
@@ -328,6 +328,14 @@ stokes_status stokes_step_tables_match(int levels, double beta);
  * already captured keep their variant.  Not thread-safe against concurrent setup or capture.
  * Returns STOKES_ERR_BAD_ARG for levels outside 2..31 or an unknown variant. */
 stokes_status stokes_set_step_variant(int levels, int variant);
+/* The same for the planar float32 levels (stokes_params.tma_level), whose step stages its tiles by
+ * tensor-memory-access box copies, one tile per CTA of 8 warps: 0 tile height for 3 resident CTAs per
+ * SM, 2 for 4 (fewer registers, shorter tiles); 1 and 3 the same, each CTA also prefetching into L2
+ * the tiles of a tile one wave of resident CTAs ahead.
+ * stokes_autotune times them on the handle's planar levels; untuned sizes use 0.  Same scope and
+ * rules as stokes_set_step_variant; -1 / STOKES_ERR_BAD_ARG out of range. */
+int stokes_planar_step_variant(int levels);
+stokes_status stokes_set_planar_step_variant(int levels, int variant);
 
 /* ---- batches: many independent solves (right-hand sides, beta values, mesh levels) in one launch.
  * stokes_batch_setup builds `count` solvers; instance i has levels[i] levels and beta betas[i], the

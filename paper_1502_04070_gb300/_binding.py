@@ -93,6 +93,8 @@ SIGNATURES = {
     "stokes_autotune": (_I, [_P]),
     "stokes_step_variant": (_I, [_I]),
     "stokes_set_step_variant": (_I, [_I, _I]),
+    "stokes_planar_step_variant": (_I, [_I]),
+    "stokes_set_planar_step_variant": (_I, [_I, _I]),
     "stokes_step_tables_match": (_I, [_I, _D]),
     "stokes_set_timing": (_I, [_P, _I]),
     "stokes_get_timing": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D),

@@ -1058,9 +1058,11 @@ static stokes_status autotune_levels(stokes_handle* h, cudaStream_t st) {
     if (!h->mixed() || h->prm.smoother != STOKES_UZAWA) return STOKES_OK;
     for (int l = 1; l < (int)h->h32.size(); ++l) {
         Level<float>& lv = h->h32[l];
-        if (lv.planar || uzawa_tuned(lv.n)) continue;   // planar levels have one step kernel
-        cudaError_t e = autotune_uzawa_fused(st, lv.n, lv.c, (float)h->prm.tau, (float)h->prm.sigma, lv.u, lv.p, lv.f,
-                                             lv.g, lv.sinv, lv.tu, lv.tp, nullptr, nullptr);
+        if (lv.planar ? tma_tuned(lv.n) : uzawa_tuned(lv.n)) continue;
+        cudaError_t e = lv.planar ? autotune_uzawa_tma(st, lv.n, lv.c, (float)h->prm.tau, (float)h->prm.sigma, lv.u, lv.p,
+                                                       lv.f, lv.g, lv.sinv, lv.tu, lv.tp)
+                                  : autotune_uzawa_fused(st, lv.n, lv.c, (float)h->prm.tau, (float)h->prm.sigma, lv.u,
+                                                         lv.p, lv.f, lv.g, lv.sinv, lv.tu, lv.tp, nullptr, nullptr);
         if (e != cudaSuccess) return fail(e);
         cudaMemsetAsync(lv.u, 0, 2 * lv.n2 * sizeof(float), st);
         cudaMemsetAsync(lv.p, 0, lv.n1 * sizeof(float), st);
@@ -1075,6 +1077,13 @@ int stokes_step_variant(int levels) { return levels >= 2 && levels <= 31 ? uzawa
 
 stokes_status stokes_set_step_variant(int levels, int variant) {
     if (levels < 2 || levels > 31 || !set_uzawa_choice(1 << levels, variant)) return STOKES_ERR_BAD_ARG;
+    return STOKES_OK;
+}
+
+int stokes_planar_step_variant(int levels) { return levels >= 2 && levels <= 31 ? tma_choice(1 << levels) : -1; }
+
+stokes_status stokes_set_planar_step_variant(int levels, int variant) {
+    if (levels < 2 || levels > 31 || !set_tma_choice(1 << levels, variant)) return STOKES_ERR_BAD_ARG;
     return STOKES_OK;
 }
 

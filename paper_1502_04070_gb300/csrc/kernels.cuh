@@ -72,6 +72,20 @@ constexpr int kDefaultTmaLevel = 6;   // lowest level held planar unless stokes_
 bool launch_uzawa_tma(cudaStream_t s, int n, const OpCoef<float>& c, float tau, float sigma, const float* u,
                       const float* p, const float* f, const float* g, const float* sinv, float* u_out, float* p_out);
 bool uzawa_tma_available();
+// Variants of the planar step, one tile per CTA of 8 warps: 0 tile height for 3 CTAs per SM (80
+// registers), 2 for 4 CTAs per SM (64 registers); 1, 3 the same, each CTA also prefetching into L2
+// the tiles of the tile one wave of resident CTAs ahead.  launch_uzawa_tma runs the variant chosen
+// for level size n (0 until autotune_uzawa_tma or set_tma_choice).
+constexpr int kTmaVariants = 4;
+bool launch_uzawa_tma_variant(int variant, cudaStream_t s, int n, const OpCoef<float>& c, float tau, float sigma,
+                              const float* u, const float* p, const float* f, const float* g, const float* sinv,
+                              float* u_out, float* p_out);
+int tma_choice(int n);
+bool tma_tuned(int n);
+bool set_tma_choice(int n, int v);
+// times every planar variant on these planar buffers (contents overwritten) and keeps the fastest
+cudaError_t autotune_uzawa_tma(cudaStream_t s, int n, const OpCoef<float>& c, float tau, float sigma, float* u,
+                               float* p, const float* f, const float* g, const float* sinv, float* u_out, float* p_out);
 unsigned uzawa_tma_timeouts();
 // Does the compile-time structure of the register tile match these coefficients?
 bool reg_tables_match(const OpCoef<float>& c);

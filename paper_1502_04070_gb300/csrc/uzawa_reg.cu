@@ -683,11 +683,31 @@ __device__ __forceinline__ void tma_3d(unsigned dst, const CUtensorMap* map, int
         : "memory");
 }
 
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int x, int y) {
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(map), "r"(x), "r"(y) : "memory");
+}
+__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap* map, int x, int y, int z) {
+    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(map), "r"(x), "r"(y), "r"(z)
+                 : "memory");
+}
+// the five tiles of the tile at (i0, j0) into L2, for the CTA that will take that tile later
+__device__ __forceinline__ void tma_prefetch_tile(int TY, int i0, int j0, const TmaMaps& maps) {
+    using G = TmaTile;
+    tma_prefetch_3d(&maps.u, 2 * (i0 - G::UX), 2 * (j0 - 3), 0);
+    tma_prefetch_3d(&maps.f0, 2 * (i0 - 2), j0 - 2, 0);
+    tma_prefetch_3d(&maps.f1, 2 * (i0 - 2), j0 - 2, 0);
+    tma_prefetch_2d(&maps.p, i0 - G::PX, j0 - 3);
+    tma_prefetch_2d(&maps.g, i0 - G::DX, j0 - 1);
+    tma_prefetch_2d(&maps.s, i0 - G::DX, j0 - 1);
+}
+
+// pf > 0: also prefetch into L2 the tiles of tile blockIdx.x + pf (about one wave of resident CTAs
+// ahead), so that the CTA that takes it finds its tiles in L2
 template <int NW, int MINB>
 __global__ void __launch_bounds__(32 * NW, MINB)
     k_uzawa_tma(int n, int TY, TileOrder ord, const __grid_constant__ OpCoef<float> c, const __grid_constant__ RegCoef q,
                 float tau, float sigma, const __grid_constant__ TmaMaps maps, float* __restrict__ u_out,
-                float* __restrict__ p_out) {
+                float* __restrict__ p_out, int pf) {
     using G = TmaTile;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
@@ -715,6 +735,12 @@ __global__ void __launch_bounds__(32 * NW, MINB)
         tma_2d((unsigned)__cvta_generic_to_shared(sP), &maps.p, i0 - G::PX, j0 - 3, bar);
         tma_2d((unsigned)__cvta_generic_to_shared(sG), &maps.g, i0 - G::DX, j0 - 1, bar);
         tma_2d((unsigned)__cvta_generic_to_shared(sS), &maps.s, i0 - G::DX, j0 - 1, bar);
+        const int ahead = (int)blockIdx.x + pf;
+        if (pf > 0 && ahead < (int)gridDim.x) {
+            int ac, ar;
+            ord.tile(ahead, ac, ar);
+            tma_prefetch_tile(TY, ac * G::TX, ar * TY, maps);
+        }
     }
     const bool ok = mbar_wait_bounded(bar, 0);
     if (__syncthreads_or(!ok)) {
@@ -741,7 +767,7 @@ cudaError_t tma_smem_attr() {
 
 // Rows per tile for level size n: the least work on the busiest SM, (tiles per SM, rounded up) x
 // (work of one tile, about ty + 4 rows of the u^{m-1/2} region), among the tile heights that keep
-// at least MINB CTAs of kernel k (dynamic shared memory bytes(ty)) resident per SM.
+// at least MINB CTAs of kernel k (dynamic shared memory G::bytes(ty)) resident per SM.
 template <class G, class K>
 int tile_rows(int n, K k, int nthreads, int minb, int* cache) {
     const int lv = 31 - __builtin_clz((unsigned)n);
@@ -781,7 +807,6 @@ int tma_rows(int n) {
     static int cache[32] = {};
     return tile_rows<TmaTile>(n, k_uzawa_tma<NW, MINB>, 32 * NW, MINB, cache);
 }
-
 template <class G>
 TileOrder tile_order(int n, int ty) {
     TileOrder ord;
@@ -850,15 +875,26 @@ bool make_tma_maps(int n, int ty, const float* u, const float* p, const float* f
 
 template <int NW, int MINB>
 bool launch_tma_v(cudaStream_t s, int n, const OpCoef<float>& c, float tau, float sigma, const float* u, const float* p,
-                  const float* f, const float* g, const float* sinv, float* u_out, float* p_out) {
+                  const float* f, const float* g, const float* sinv, float* u_out, float* p_out, bool prefetch) {
     RegCoef q;
     if (!make_reg_coef(c, tau, q)) return false;
     const int ty = tma_rows<NW, MINB>(n);
     TmaMaps m;
     if (!make_tma_maps(n, ty, u, p, f, g, sinv, m)) return false;
     const TileOrder ord = tile_order<TmaTile>(n, ty);
+    int pf = 0;
+    if (prefetch) {   // one wave of resident CTAs ahead
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_uzawa_tma<NW, MINB>, 32 * NW, TmaTile::bytes(ty)) !=
+            cudaSuccess)
+            per_sm = MINB;
+        cudaGetLastError();
+        pf = std::max(1, sms) * std::max(1, per_sm);
+    }
     launch_pdl(k_uzawa_tma<NW, MINB>, dim3(ord.cols * ord.rows), dim3(32 * NW), TmaTile::bytes(ty), s, n, ty, ord, c, q,
-               tau, sigma, m, u_out, p_out);
+               tau, sigma, m, u_out, p_out, pf);
     return true;
 }
 
@@ -868,6 +904,7 @@ cudaError_t prepare_uzawa_reg() {
     cudaError_t e = reg_smem_attr<8, 2>();
     if (e == cudaSuccess) e = reg_smem_attr<8, 4>();
     if (e == cudaSuccess) e = tma_smem_attr<8, 3>();
+    if (e == cudaSuccess) e = tma_smem_attr<8, 4>();
     return e;
 }
 
@@ -878,9 +915,73 @@ bool launch_uzawa_reg(int variant, cudaStream_t s, int n, const OpCoef<float>& c
     return launch_reg_v<8, 4>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
 }
 
+namespace {
+int g_tma_choice[32] = {};     // planar step variant per level size (log2 N)
+bool g_tma_tuned[32] = {};
+int lvl(int n) { return (31 - __builtin_clz((unsigned)n)) & 31; }
+}  // namespace
+
+bool launch_uzawa_tma_variant(int variant, cudaStream_t s, int n, const OpCoef<float>& c, float tau, float sigma,
+                              const float* u, const float* p, const float* f, const float* g, const float* sinv,
+                              float* u_out, float* p_out) {
+    switch (variant) {
+        case 1: return launch_tma_v<8, 3>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out, true);
+        case 2: return launch_tma_v<8, 4>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out, false);
+        case 3: return launch_tma_v<8, 4>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out, true);
+        default: return launch_tma_v<8, 3>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out, false);
+    }
+}
+
 bool launch_uzawa_tma(cudaStream_t s, int n, const OpCoef<float>& c, float tau, float sigma, const float* u,
                       const float* p, const float* f, const float* g, const float* sinv, float* u_out, float* p_out) {
-    return launch_tma_v<8, 3>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
+    return launch_uzawa_tma_variant(g_tma_choice[lvl(n)], s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
+}
+
+int tma_choice(int n) { return g_tma_choice[lvl(n)]; }
+bool tma_tuned(int n) { return g_tma_tuned[lvl(n)]; }
+bool set_tma_choice(int n, int v) {
+    if (v < 0 || v >= kTmaVariants) return false;
+    g_tma_choice[lvl(n)] = v;
+    g_tma_tuned[lvl(n)] = true;
+    return true;
+}
+
+cudaError_t autotune_uzawa_tma(cudaStream_t s, int n, const OpCoef<float>& c, float tau, float sigma, float* u,
+                               float* p, const float* f, const float* g, const float* sinv, float* u_out, float* p_out) {
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return cudaErrorUnknown;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cudaErrorUnknown;
+    }
+    const int reps = n >= 512 ? 5 : 20;
+    int best = 0;
+    float bms = 1e30f;
+    cudaError_t err = cudaSuccess;
+    for (int v = 0; v < kTmaVariants && err == cudaSuccess; ++v) {
+        if (!launch_uzawa_tma_variant(v, s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out)) continue;   // warm-up
+        bool sw = true;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps; ++r) {
+            launch_uzawa_tma_variant(v, s, n, c, tau, sigma, sw ? u_out : u, sw ? p_out : p, f, g, sinv, sw ? u : u_out,
+                                     sw ? p : p_out);
+            sw = !sw;
+        }
+        cudaEventRecord(e1, s);
+        if ((err = cudaEventSynchronize(e1)) != cudaSuccess) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms / reps < bms) {
+            bms = ms / reps;
+            best = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != cudaSuccess) return err;
+    g_tma_choice[lvl(n)] = best;
+    g_tma_tuned[lvl(n)] = true;
+    return cudaGetLastError();
 }
 
 bool uzawa_tma_available() { return encode_tiled() != nullptr; }

@@ -278,6 +278,17 @@ def set_step_variant(levels, variant):
     B.check(B.load().stokes_set_step_variant(int(levels), int(variant)), "stokes_set_step_variant")
 
 
+def planar_step_variant(levels):
+    """Step variant used for planar float32 levels with N = 2^levels (0 one tile per CTA; 1, 2
+    persistent CTAs with two tile buffers, 8 or 16 warps)."""
+    return int(B.load().stokes_planar_step_variant(int(levels)))
+
+
+def set_planar_step_variant(levels, variant):
+    """Forces the planar step variant for levels with N = 2^levels (process-wide)."""
+    B.check(B.load().stokes_set_planar_step_variant(int(levels), int(variant)), "stokes_set_planar_step_variant")
+
+
 class BatchSolver:
     """Many independent solves (levels, beta per instance) run to convergence in one CUDA-graph
     launch (stokes_batch_setup / stokes_batch_solve)."""

@@ -37,9 +37,11 @@ def _state(k, seed):
 
 @pytest.mark.parametrize("k", [5, 6])
 @pytest.mark.parametrize("beta", [0.0, 1e2, 1e8])
-@pytest.mark.parametrize("nu", [1, 3])
-def test_planar_step_by_oracle(discs, k, beta, nu):
-    from paper_1502_04070_gb300.solver import Solver
+@pytest.mark.parametrize("nu,variant", [(1, 0), (3, 0), (3, 1), (3, 2), (3, 3)])
+def test_planar_step_by_oracle(discs, k, beta, nu, variant):
+    """Every planar step variant: tiles for 3 or 4 resident CTAs per SM, with and without the L2
+    prefetch of a later tile."""
+    from paper_1502_04070_gb300.solver import Solver, planar_step_variant, set_planar_step_variant
     H = mg.Hierarchy(k + 1, beta, discs[:k + 1])
     d = H.discs[-1]
     u, p, f, g = _state(k, 300 + k)
@@ -52,7 +54,12 @@ def test_planar_step_by_oracle(discs, k, beta, nu):
     S = Solver(k + 1, beta, precision="mixed", tma_level=5)
     t = lambda a: dev(a).float().contiguous()
     tu, tp = t(u), t(p)
-    S.smooth_f32(tu, tp, t(f), t(g), nu)
+    old = planar_step_variant(k + 1)
+    set_planar_step_variant(k + 1, variant)
+    try:
+        S.smooth_f32(tu, tp, t(f), t(g), nu)
+    finally:
+        set_planar_step_variant(k + 1, old)
     uo, po = d.from_vec(x)
     got = np.concatenate([host(tu.double()).ravel(), host(tp.double()).ravel()])
     ref = np.concatenate([uo.ravel(), po.ravel()])
@@ -82,10 +89,10 @@ def test_planar_step_zeroes_the_boundary(discs):
 _DIRECT = {}
 
 
-@pytest.mark.parametrize("gamma,coarse_level", [(1, 0), (2, 0), (2, 3), (1, 3)])
-def test_planar_mixed_solve_by_oracle(discs, gamma, coarse_level):
+@pytest.mark.parametrize("gamma,coarse_level,variant", [(1, 0, 0), (2, 0, 1), (2, 3, 2), (1, 3, 3)])
+def test_planar_mixed_solve_by_oracle(discs, gamma, coarse_level, variant):
     """k = 5 with levels 5 and up planar: the finest level restricts to a compact level."""
-    from paper_1502_04070_gb300.solver import Solver
+    from paper_1502_04070_gb300.solver import Solver, planar_step_variant, set_planar_step_variant
     k, beta = 5, 1e2
     d = discs[k]
     H = mg.Hierarchy(k + 1, beta, discs[:k + 1], coarse_level=coarse_level)
@@ -95,9 +102,14 @@ def test_planar_mixed_solve_by_oracle(discs, gamma, coarse_level):
     if k not in _DIRECT:
         _DIRECT[k] = H.direct(F)   # the finest system's solution: the same for every coarsest level
     xd = _DIRECT[k]
-    S = Solver(k + 1, beta, precision="mixed", gamma=gamma, coarse_level=coarse_level, tma_level=5)
-    f, g = S.load_vectors(dev(fn), dev(gn), project_g=True)
-    u, p, rep = S.solve(f, g, tol=1e-8, max_cycles=100)
+    old = planar_step_variant(k + 1)
+    set_planar_step_variant(k + 1, variant)
+    try:
+        S = Solver(k + 1, beta, precision="mixed", gamma=gamma, coarse_level=coarse_level, tma_level=5)
+        f, g = S.load_vectors(dev(fn), dev(gn), project_g=True)
+        u, p, rep = S.solve(f, g, tol=1e-8, max_cycles=100)
+    finally:
+        set_planar_step_variant(k + 1, old)
     assert rep.converged, rep
     assert abs(rep.cycles - (len(hist) - 1)) <= 1, (rep.cycles, len(hist) - 1)
     assert rel_err(d.to_vec(host(u), host(p)), xd) < 1e-6
