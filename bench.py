@@ -83,7 +83,7 @@ def parse():
     ap.add_argument("--variant", type=int, default=None,
                     help="kernel modes: force this float32 Uzawa step variant on every level")
     ap.add_argument("--variants", default=None,
-                    help="kernel modes: float32 Uzawa step variant per level, 'k:v,k:v,...' (as the workload's "
+                    help="kernel modes: float32 Uzawa step variant per level, 'k:v,k:tma:v,...' (as the workload's "
                          "float32_step_variant_per_level reports them); levels not named are autotuned")
     return ap.parse_args()
 
@@ -107,9 +107,13 @@ def run_kernel(args):
         if args.variant is not None:
             for l in range(2, k + 2):
                 set_step_variant(l, args.variant)
+        from paper_1502_04070_gb300.solver import set_planar_step_variant
         for item in (args.variants.split(",") if args.variants else []):
-            kl, v = item.split(":")
-            set_step_variant(int(kl) + 1, int(v))
+            kl, v = item.split(":", 1)
+            if v.startswith("tma:"):
+                set_planar_step_variant(int(kl) + 1, int(v[4:]))
+            else:
+                set_step_variant(int(kl) + 1, int(v))
     if args.planar_variant is not None:
         from paper_1502_04070_gb300.solver import set_planar_step_variant
         for l in range(2, k + 2):
@@ -327,9 +331,16 @@ def max_over_all_ranks(v, device):
     return float(t.item())
 
 
-def step_variants(levels):
+TMA_LEVEL = 6   # the library's default lowest planar float32 level (stokes_params.tma_level = 0)
+
+
+def step_variants(levels, tma_level=TMA_LEVEL):
+    """Float32 Uzawa step variant per level: an int for compact levels, "tma:<v>" for planar levels
+    (the step staged by tensor-memory-access copies, planar variant v)."""
     from paper_1502_04070_gb300 import _binding as _B
-    return {"k=%d" % (l - 1): _B.load().stokes_step_variant(l) for l in range(2, levels + 1)}
+    lib = _B.load()
+    return {"k=%d" % (l - 1): ("tma:%d" % lib.stokes_planar_step_variant(l)) if l - 1 >= tma_level
+            else lib.stokes_step_variant(l) for l in range(2, levels + 1)}
 
 
 def peaks():
@@ -341,7 +352,7 @@ def peaks():
 # profiles/traffic.json records (the three-kernel step in kernels.cu, the tiles in uzawa_pair.cu and
 # uzawa_reg.cu, the variant table in uzawa_fused.cu, and every header they include).
 TRAFFIC_SOURCES = ("common.cuh", "cellops.cuh", "kernels.cuh", "kernels.cu", "coarse_cycle.cuh",
-                   "uzawa_fused.cu", "uzawa_pair.cu", "uzawa_reg.cu")
+                   "uzawa_fused.cu", "uzawa_pair.cu", "uzawa_reg.cu", "tiles.cuh")
 
 
 def _kernel_source_sha():
