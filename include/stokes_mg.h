@@ -185,6 +185,15 @@ stokes_status stokes_smooth(stokes_handle* h, double* u, double* p, const double
  * or a pair tile), on float32 arrays of the finest-level layouts; requires a STOKES_MIXED handle.
  * Exposed for verification of the float32 path alone. */
 stokes_status stokes_smooth_f32(stokes_handle* h, float* u, float* p, const float* f, const float* g, int nu);
+/* Verification of the float32 transfer path (Sec. 3): (fc, gc) = I^T (F - A x) from the finest level of
+ * a STOKES_MIXED handle to the level below, float32, on the caller's arrays in the layout above
+ * (u, f: 2 (2N+1)^2, p, g: (N+1)^2 of the finest level; fc: 2 (N+1)^2, gc: (N/2+1)^2).  On a planar
+ * finest level (stokes_params.tma_level) this is the kernel the cycles run, defect and restriction in
+ * one pass over tiles staged by tensor-memory-access copies; the caller's arrays are copied into the
+ * handle's finest and coarse float32 buffers (their contents are overwritten).  Asynchronous on the
+ * handle's stream.  STOKES_ERR_BAD_ARG for a float64 handle or levels < 2. */
+stokes_status stokes_residual_restrict_f32(stokes_handle* h, const float* u, const float* p, const float* f,
+                                           const float* g, float* fc, float* gc);
 
 /* Canonical transfers (Sec. 3) between finest level k and level k-1 (requires levels >= 2):
  * restriction  (fc, gc) = I_k^{k-1} (fu, fp)   with coarse layouts of level k-1,

@@ -66,6 +66,7 @@ SIGNATURES = {
     "stokes_residual_norm": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(_D)]),
     "stokes_smooth": (_I, [_P, _P, _P, _P, _P, _I]),
     "stokes_smooth_f32": (_I, [_P, _P, _P, _P, _P, _I]),
+    "stokes_residual_restrict_f32": (_I, [_P, _P, _P, _P, _P, _P, _P]),
     "stokes_restrict": (_I, [_P, _P, _P, _P, _P]),
     "stokes_prolong_add": (_I, [_P, _P, _P, _P, _P]),
     "stokes_load_vectors": (_I, [_P, _P, _P, _I, _P, _P]),

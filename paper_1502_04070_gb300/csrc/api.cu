@@ -307,8 +307,11 @@ void mg_cycle(stokes_handle* h, std::vector<Level<T>>& H, int l) {
     Level<T>& cl = H[l - 1];
     if constexpr (sizeof(T) == 4) {
         if (lv.planar) {
-            launch_residual_planar(h->st, lv.n, lv.c, xu, xp, lv.f, lv.g, ru, rp);
-            launch_restrict_planar(h->st, cl.n, cl.planar, ru, rp, cl.f, cl.g, cl.u, cl.p);
+            // the defect and its restriction in one kernel on the staged tiles (the defect stays on chip)
+            if (!launch_restrict_tma(h->st, lv.n, cl.planar, lv.c, xu, xp, lv.f, lv.g, cl.f, cl.g, cl.u, cl.p)) {
+                launch_residual_planar(h->st, lv.n, lv.c, xu, xp, lv.f, lv.g, ru, rp);
+                launch_restrict_planar(h->st, cl.n, cl.planar, ru, rp, cl.f, cl.g, cl.u, cl.p);
+            }
             for (int r = 0; r < h->prm.gamma; ++r) mg_cycle(h, H, l - 1);
             launch_prolong_add_planar(h->st, cl.n, cl.planar, cl.u, cl.p, xu, xp);
         }
@@ -921,6 +924,32 @@ stokes_status stokes_smooth_f32(stokes_handle* h, float* u, float* p, const floa
         CK(cudaMemcpyAsync(p, lv.tp, lv.n1 * sizeof(float), cudaMemcpyDeviceToDevice, h->st));
     }
     h->launches += (unsigned long long)nu;
+    CK(cudaGetLastError());
+    return take_launch_failure(h);
+}
+
+stokes_status stokes_residual_restrict_f32(stokes_handle* h, const float* u, const float* p, const float* f,
+                                           const float* g, float* fc, float* gc) {
+    if (!h || !u || !p || !f || !g || !fc || !gc || !h->mixed() || h->L < 2) return STOKES_ERR_BAD_ARG;
+    Level<float>& lv = h->h32.back();
+    Level<float>& cl = h->h32[h->L - 2];
+    if (lv.planar) {
+        launch_to_planar(h->st, lv.n, u, p, lv.u, lv.p);
+        launch_to_planar(h->st, lv.n, f, g, lv.f, lv.g);
+        if (!launch_restrict_tma(h->st, lv.n, cl.planar, lv.c, lv.u, lv.p, lv.f, lv.g, cl.f, cl.g, cl.u, cl.p))
+            return STOKES_ERR_CUDA;
+        if (cl.planar) {
+            launch_from_planar(h->st, cl.n, cl.f, cl.g, fc, gc);
+        } else {
+            CK(cudaMemcpyAsync(fc, cl.f, 2 * cl.n2 * sizeof(float), cudaMemcpyDeviceToDevice, h->st));
+            CK(cudaMemcpyAsync(gc, cl.g, cl.n1 * sizeof(float), cudaMemcpyDeviceToDevice, h->st));
+        }
+        h->launches += 4;
+    } else {
+        launch_residual<float, float>(h->st, lv.n, lv.c, u, p, f, g, lv.tu, lv.tp, nullptr);
+        launch_restrict<float>(h->st, cl.n, lv.tu, lv.tp, fc, gc);
+        h->launches += 2;
+    }
     CK(cudaGetLastError());
     return take_launch_failure(h);
 }

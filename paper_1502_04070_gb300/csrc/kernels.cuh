@@ -80,6 +80,12 @@ constexpr int kTmaVariants = 4;
 bool launch_uzawa_tma_variant(int variant, cudaStream_t s, int n, const OpCoef<float>& c, float tau, float sigma,
                               const float* u, const float* p, const float* f, const float* g, const float* sinv,
                               float* u_out, float* p_out);
+// r = F - A x on a planar level (N = n) and its restriction (fc, gc) = I^T r to the coarse level
+// (planar or not: pc_planar), with the coarse iterate (uc, pc) set to zero, in one kernel on the
+// tiles of the planar step; the fine defect stays in shared memory.  False (nothing launched) as
+// for launch_uzawa_tma.
+bool launch_restrict_tma(cudaStream_t s, int n, bool pc_planar, const OpCoef<float>& c, const float* u, const float* p,
+                         const float* f, const float* g, float* fc, float* gc, float* uc, float* pc);
 int tma_choice(int n);
 bool tma_tuned(int n);
 bool set_tma_choice(int n, int v);

@@ -30,6 +30,7 @@
 #include <cuda.h>
 
 #include "cellops.cuh"
+#include "elements.h"
 #include "kernels.cuh"
 #include "tiles.cuh"
 
@@ -754,6 +755,237 @@ __global__ void __launch_bounds__(32 * NW, MINB)
     pdl_trigger();
 }
 
+// ---------------------------------------------------------------------------------------------
+// Residual and restriction of a planar level in one kernel (Sec. 3: the coarse right-hand side is
+// the transposed canonical embedding of the fine defect).  A CTA stages the tiles of k_uzawa_tma
+// (the g tile one row lower, no Shat^{-1}), forms the defect r = F - A x on fine cells and vertices
+// [i0 - 2, i0 + TX) x [j0 - 2, j0 + ty) in shared memory (r_u over f, r_p over g), and restricts it
+// to its own coarse cells [i0 / 2, i0 / 2 + TX / 2) x [j0 / 2, j0 / 2 + ty / 2): every fine point that
+// a coarse basis function of those cells reaches lies in that region.  The fine defect never goes to
+// global memory.  The coarse iterate of those cells is set to zero (the coarse correction starts
+// from 0).
+
+// The canonical embedding weights of the restriction, [orientation][coarse local node][fb][fa]
+struct RestrictWeights {
+    float w[2][9][4][4];
+};
+
+// B row of a vertex over the u tile (two column-parity planes, as a_term reads them)
+template <int C, int UWH, int W>
+__device__ __forceinline__ void bu_term(const float2* t0, const float2* t1, float& acc) {
+    if constexpr (kBx[C][W] != 0 || kBy[C][W] != 0) {
+        constexpr int dx = W % 5 - 2, dy = W / 5 - 2;
+        const float2 w = ((dx & 1) ? t1 : t0)[dy * UWH + (dx >> 1)];
+        addk<kBx[C][W]>(acc, w.x);
+        addk<kBy[C][W]>(acc, w.y);
+    }
+}
+template <int C, int UWH, int... W>
+__device__ __forceinline__ float bu_row(const float2* t0, const float2* t1, std::integer_sequence<int, W...>) {
+    float acc = 0.f;
+    (bu_term<C, UWH, W>(t0, t1, acc), ...);
+    return acc;
+}
+
+// the defect on cells and vertices (i0 - 2 + lane, j0 - 2 + r), r < TY + 2, fast path (class C)
+template <class G, int C>
+__device__ __forceinline__ void defect_fast(const RegCoef& q, const float2* sU, int UPL, const float* sP, float2* sF,
+                                           int FPL, float* sG, int TY, int NW, int warp, int lane, int i0, int j0,
+                                           int n) {
+    float2 a[kGroups];
+    load_coef<C>(q, a);
+    const float2 mb = f2(-q.b, -q.b);
+    const float hb = q.b;
+    for (int r = warp; r < TY + 2; r += NW) {
+        const float2* t0 = sU + 2 * (r + 1) * G::UWH + lane + G::UX - 2;
+        const float2* t1 = t0 + UPL;
+        float2 au[4], ctr[4], bt[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) au[s] = ctr[s] = bt[s] = f2(0.f, 0.f);
+        a_rows<C, G::UWH>(a, t0, t1, au, ctr, std::make_integer_sequence<int, 25>{});
+        bt_rows<C, G::PW>(sP + (r + 1) * G::PW + lane + G::PX - 2, bt, std::make_integer_sequence<int, 9>{});
+        const float bu = hb * bu_row<C, G::UWH>(t0, t1, std::make_integer_sequence<int, 25>{});
+        const int ci = i0 - 2 + lane, cj = j0 - 2 + r;
+        const bool ci_in = ci > 0 && ci < n, cj_in = cj > 0 && cj < n;
+        const bool ci_h = ci >= 0 && ci < n, cj_h = cj >= 0 && cj < n;
+        const bool unk[4] = {ci_in && cj_in, ci_h && cj_in, ci_in && cj_h, ci_h && cj_h};
+        float2* fr = sF + r * G::FW + lane;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const float2 fs = fr[s * FPL];
+            float2 t = f2(fs.x - au[s].x, fs.y - au[s].y);
+            if (s > 0) t = __ffma2_rn(mb, bt[s], t);
+            fr[s * FPL] = unk[s] ? t : f2(0.f, 0.f);
+        }
+        if (lane < G::DN) {
+            const int k = r * G::DW + lane + G::DX - 2;
+            const bool live = ci >= 0 && cj >= 0 && ci <= n && cj <= n;
+            sG[k] = live ? sG[k] - bu : 0.f;
+        }
+    }
+}
+
+// coarse cell (I, J) of level nc: the restricted defect at its owned nodes and vertex, from the
+// fine defect tiles (r_u over the node-type planes of sF, origin cell (xc0, yc0); r_p in sG, origin
+// vertex (xv0, yv0), DW per row)
+template <class G, int SQ>
+__device__ __forceinline__ void restrict_sq(const RestrictWeights& wt, int I, int J, int nc, const float2* sF, int FPL,
+                                            int xc0, int yc0, float2 (&acc)[4]) {
+    const int SI = I - (SQ & 1), SJ = J - (SQ >> 1);
+    if (SI < 0 || SJ < 0 || SI >= nc || SJ >= nc) return;
+    const int o = orient(SI, SJ, nc);
+    float2 v[4][4];
+#pragma unroll
+    for (int fb = 0; fb < 4; ++fb)
+#pragma unroll
+        for (int fa = 0; fa < 4; ++fa)
+            v[fb][fa] = sF[((fa & 1) + 2 * (fb & 1)) * FPL + (2 * SJ + (fb >> 1) - yc0) * G::FW + 2 * SI + (fa >> 1) - xc0];
+#pragma unroll
+    for (int R = 0; R < sq_nrows(SQ); ++R) {
+        const int L = sq_row(SQ, R), s = sq_slot(SQ, R);
+#pragma unroll
+        for (int fb = 0; fb < 4; ++fb)
+#pragma unroll
+            for (int fa = 0; fa < 4; ++fa) {
+                const float w = wt.w[o][L][fb][fa];
+                acc[s] = __ffma2_rn(f2(w, w), v[fb][fa], acc[s]);
+            }
+    }
+}
+
+template <int NW, int MINB, bool PC>
+__global__ void __launch_bounds__(32 * NW, MINB)
+    k_restrict_tma(int n, int TY, TileOrder ord, const __grid_constant__ OpCoef<float> c,
+                   const __grid_constant__ RegCoef q, const __grid_constant__ RestrictWeights wt,
+                   const __grid_constant__ TmaMaps maps, float* __restrict__ fc, float* __restrict__ gc,
+                   float* __restrict__ uc, float* __restrict__ pc) {
+    using G = TmaTile;
+    constexpr int TX = G::TX;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    float2* sU = reinterpret_cast<float2*>(base + 128);
+    float2* sF = reinterpret_cast<float2*>(base + G::off_f(TY));
+    float* sP = reinterpret_cast<float*>(base + G::off_p(TY));
+    float* sG = reinterpret_cast<float*>(base + G::off_g(TY));
+    const unsigned bar = (unsigned)__cvta_generic_to_shared(base);
+    const int UPL = G::upl(TY), FPL = G::fpl(TY);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int tc, tr;
+    ord.tile(blockIdx.x, tc, tr);
+    const int i0 = tc * TX, j0 = tr * TY;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    pdl_wait();
+    if (threadIdx.x == 0) {
+        const unsigned bytes = G::tx_bytes(TY) - 4u * (unsigned)G::dsz(TY);   // no Shat^{-1} tile
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+        const unsigned du = (unsigned)__cvta_generic_to_shared(sU), df = (unsigned)__cvta_generic_to_shared(sF);
+        tma_3d(du, &maps.u, 2 * (i0 - G::UX), 2 * (j0 - 3), 0, bar);
+        tma_3d(df, &maps.f0, 2 * (i0 - 2), j0 - 2, 0, bar);
+        tma_3d(df + 8 * 2 * FPL, &maps.f1, 2 * (i0 - 2), j0 - 2, 0, bar);
+        tma_2d((unsigned)__cvta_generic_to_shared(sP), &maps.p, i0 - G::PX, j0 - 3, bar);
+        tma_2d((unsigned)__cvta_generic_to_shared(sG), &maps.g, i0 - G::DX, j0 - 2, bar);
+    }
+    const bool ok = mbar_wait_bounded(bar, 0);
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) {
+            atomicOr(&g_tma_timeout, 1u);
+            mbar_wait_bounded(bar, 0);
+        }
+        return;
+    }
+    // ---- the fine defect on cells and vertices [i0 - 2, i0 + TX) x [j0 - 2, j0 + TY)
+    const int h = n >> 1;
+    const bool fast = (h < i0 - 2 || h >= i0 + TX) && (h < j0 - 2 || h >= j0 + TY);
+    if (fast) {
+        if (orient(i0, j0, n) == 0) defect_fast<G, 0>(q, sU, UPL, sP, sF, FPL, sG, TY, NW, warp, lane, i0, j0, n);
+        else defect_fast<G, 1>(q, sU, UPL, sP, sF, FPL, sG, TY, NW, warp, lane, i0, j0, n);
+    } else {
+        const ULat<G> vux{sU, UPL, i0 - G::UX, 2 * (j0 - 3), false};
+        const ULat<G> vuy{sU, UPL, i0 - G::UX, 2 * (j0 - 3), true};
+        const SVert<float, G::PW> vp{sP, i0 - G::PX, j0 - 3};
+        for (int r = warp; r < TY + 2; r += NW) {
+            const int ci = i0 - 2 + lane, cj = j0 - 2 + r;
+            const bool live = ci >= 0 && cj >= 0 && ci <= n && cj <= n;
+            float2 rv[4];
+#pragma unroll
+            for (int s = 0; s < 4; ++s) rv[s] = f2(0.f, 0.f);
+            float rpv = 0.f;
+            float2* fr = sF + r * G::FW + lane;
+            const int k = r * G::DW + lane + G::DX - 2;
+            if (live) {
+                Acc<float> a;
+                cell_apply_auto<true, true, true, false, false>(ci, cj, n, c, vux, vuy, vp, a);
+                const CellNodes cn = cell_nodes(ci, cj, n);
+#pragma unroll
+                for (int s = 0; s < 4; ++s) {
+                    if (!slot_unknown(cn, s)) continue;
+                    const float2 fs = fr[s * FPL];
+                    rv[s] = f2(fs.x - a.au[0][s] - a.bt[0][s], fs.y - a.au[1][s] - a.bt[1][s]);
+                }
+                if (lane < G::DN) rpv = sG[k] - a.bu;
+            }
+#pragma unroll
+            for (int s = 0; s < 4; ++s) fr[s * FPL] = rv[s];
+            if (lane < G::DN) sG[k] = rpv;
+        }
+    }
+    __syncthreads();
+    // ---- restriction to the coarse cells (I, J) of this tile
+    const int nc = n >> 1;
+    for (int t = threadIdx.x; t < (TX / 2) * (TY / 2); t += 32 * NW) {
+        const int I = i0 / 2 + t % (TX / 2), J = j0 / 2 + t / (TX / 2);
+        if (I > nc || J > nc) continue;
+        float2 acc[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) acc[s] = f2(0.f, 0.f);
+        restrict_sq<G, 0>(wt, I, J, nc, sF, FPL, i0 - 2, j0 - 2, acc);
+        restrict_sq<G, 1>(wt, I, J, nc, sF, FPL, i0 - 2, j0 - 2, acc);
+        restrict_sq<G, 2>(wt, I, J, nc, sF, FPL, i0 - 2, j0 - 2, acc);
+        restrict_sq<G, 3>(wt, I, J, nc, sF, FPL, i0 - 2, j0 - 2, acc);
+        const CellNodes cn = cell_nodes(I, J, nc);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            if (!slot_exists(cn, s)) continue;
+            const int X = 2 * I + (s & 1), Y = 2 * J + (s >> 1);
+            const float2 v = slot_unknown(cn, s) ? acc[s] : f2(0.f, 0.f);
+            if constexpr (PC) {
+                const int o = pl_u(nc, X, Y);
+                *reinterpret_cast<float2*>(fc + o) = v;
+                *reinterpret_cast<float2*>(uc + o) = f2(0.f, 0.f);
+            } else {
+                const int ld = 2 * nc + 1, o = Y * ld + X;
+                fc[o] = v.x;
+                fc[ld * ld + o] = v.y;
+                uc[o] = 0.f;
+                uc[ld * ld + o] = 0.f;
+            }
+        }
+        // P1: the fine vertex (2I, 2J), and halves of the fine vertices halfway along the coarse
+        // edges through it (horizontal, vertical, and the diagonal of each square whose cut passes
+        // through it)
+        const int nf = n, x = 2 * I, y = 2 * J;
+        auto R = [&](int xx, int yy) { return sG[(yy - (j0 - 2)) * G::DW + xx - (i0 - G::DX)]; };
+        const float sv = R(x, y);
+        float half = 0.f;
+        if (x > 0) half += R(x - 1, y);
+        if (x < nf) half += R(x + 1, y);
+        if (y > 0) half += R(x, y - 1);
+        if (y < nf) half += R(x, y + 1);
+        if (x < nf && y < nf && orient(I, J, nc) == 0) half += R(x + 1, y + 1);
+        if (x > 0 && y > 0 && orient(I - 1, J - 1, nc) == 0) half += R(x - 1, y - 1);
+        if (x < nf && y > 0 && orient(I, J - 1, nc) == 1) half += R(x + 1, y - 1);
+        if (x > 0 && y < nf && orient(I - 1, J, nc) == 1) half += R(x - 1, y + 1);
+        const int vi = PC ? J * pl_vpitch(nc) + I : J * (nc + 1) + I;
+        gc[vi] = fmaf(0.5f, half, sv);
+        pc[vi] = 0.f;
+    }
+    pdl_trigger();
+}
+
 template <int NW, int MINB>
 cudaError_t reg_smem_attr() {
     return cudaFuncSetAttribute(k_uzawa_reg<NW, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -795,6 +1027,12 @@ int tile_rows(int n, K k, int nthreads, int minb, int* cache) {
     cudaGetLastError();
     r = best_ty;
     return r;
+}
+
+template <bool PC>
+cudaError_t rt_smem_attr() {
+    return cudaFuncSetAttribute(k_restrict_tma<8, 3, PC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)TmaTile::bytes(kRegMaxRows));
 }
 
 template <int NW, int MINB>
@@ -898,13 +1136,48 @@ bool launch_tma_v(cudaStream_t s, int n, const OpCoef<float>& c, float tau, floa
     return true;
 }
 
+const RestrictWeights& restrict_weights() {
+    static const RestrictWeights w = [] {
+        RestrictWeights r{};
+        const TransferWeights t = transfer_weights();
+        for (int o = 0; o < 2; ++o)
+            for (int L = 0; L < 9; ++L)
+                for (int fb = 0; fb < 4; ++fb)
+                    for (int fa = 0; fa < 4; ++fa) r.w[o][L][fb][fa] = (float)t.P2[o][L][fb][fa];
+        return r;
+    }();
+    return w;
+}
+
+template <bool PC>
+bool launch_rt(cudaStream_t s, int n, const OpCoef<float>& c, const float* u, const float* p, const float* f,
+               const float* g, float* fc, float* gc, float* uc, float* pc) {
+    RegCoef q;
+    if (!make_reg_coef(c, 1.0f, q)) return false;
+    const int ty = std::max(4, tma_rows<8, 3>(n) & ~1);   // even: whole coarse cells per tile
+    TmaMaps m;
+    if (!make_tma_maps(n, ty, u, p, f, g, g, m)) return false;   // no Shat^{-1} tile (its map is unused)
+    const TileOrder ord = tile_order<TmaTile>(n, ty);
+    launch_pdl(k_restrict_tma<8, 3, PC>, dim3(ord.cols * ord.rows), dim3(256), TmaTile::bytes(ty), s, n, ty, ord, c, q,
+               restrict_weights(), m, fc, gc, uc, pc);
+    return true;
+}
+
 }  // namespace
+
+bool launch_restrict_tma(cudaStream_t s, int n, bool pc_planar, const OpCoef<float>& c, const float* u, const float* p,
+                         const float* f, const float* g, float* fc, float* gc, float* uc, float* pc) {
+    return pc_planar ? launch_rt<true>(s, n, c, u, p, f, g, fc, gc, uc, pc)
+                     : launch_rt<false>(s, n, c, u, p, f, g, fc, gc, uc, pc);
+}
 
 cudaError_t prepare_uzawa_reg() {
     cudaError_t e = reg_smem_attr<8, 2>();
     if (e == cudaSuccess) e = reg_smem_attr<8, 4>();
     if (e == cudaSuccess) e = tma_smem_attr<8, 3>();
     if (e == cudaSuccess) e = tma_smem_attr<8, 4>();
+    if (e == cudaSuccess) e = rt_smem_attr<true>();
+    if (e == cudaSuccess) e = rt_smem_attr<false>();
     return e;
 }
 

@@ -167,6 +167,18 @@ class Solver:
         B.check(self._lib.stokes_smooth_f32(self._h, _ptr(u), _ptr(p), _ptr(f), _ptr(g), int(nu)), "stokes_smooth_f32")
         return u, p
 
+    def residual_restrict_f32(self, u, p, f, g):
+        """float32 I^T (F - A x) from the finest level to the next (the inner cycle's transfer)."""
+        for t, sh, nm in ((u, self.shape_u, "u"), (p, self.shape_p, "p"), (f, self.shape_u, "f"), (g, self.shape_p, "g")):
+            if t.dtype != torch.float32 or tuple(t.shape) != tuple(sh) or not t.is_contiguous() or t.device != self.device:
+                raise ValueError("%s must be a contiguous float32 tensor of shape %s" % (nm, sh))
+        su, sp = self._coarse_shapes()
+        fc = torch.zeros(su, dtype=torch.float32, device=self.device)
+        gc = torch.zeros(sp, dtype=torch.float32, device=self.device)
+        B.check(self._lib.stokes_residual_restrict_f32(self._h, _ptr(u), _ptr(p), _ptr(f), _ptr(g), _ptr(fc), _ptr(gc)),
+                "stokes_residual_restrict_f32")
+        return fc, gc
+
     def _coarse_shapes(self):
         nc = self.N // 2
         return (2, 2 * nc + 1, 2 * nc + 1), (nc + 1, nc + 1)

@@ -132,3 +132,30 @@ def test_planar_and_compact_hierarchies_agree(discs):
         S.close()
     assert abs(out[5][0] - out[14][0]) <= 1, (out[5][0], out[14][0])
     assert rel_err(out[5][1], out[14][1]) < 1e-6
+
+
+@pytest.mark.parametrize("k", [5, 6])
+@pytest.mark.parametrize("beta", [0.0, 1e4])
+@pytest.mark.parametrize("tma_level", [5, 14])
+def test_defect_restriction_by_oracle(discs, k, beta, tma_level):
+    """I^T (F - S x) in float32 from the finest level to the next, against the oracle's assembled S
+    and prolongation P (float64, from the same float32-rounded inputs); on a planar finest level
+    (tma_level = 5) defect and restriction run in one kernel on staged tiles, with the coarse level
+    planar (k = 6) or compact (k = 5); tma_level = 14 is the compact two-kernel path.  Bound as for
+    the smoother (2e-5 of the largest entry)."""
+    from oracle import transfer
+    from paper_1502_04070_gb300.solver import Solver
+    c, d = discs[k - 1], discs[k]
+    P = transfer.prolongation(c, d)
+    u, p, f, g = _state(k, 500 + k)
+    r32 = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    x = d.to_vec(r32(u), r32(p))
+    F = d.to_vec(r32(f), r32(g))
+    ref = P.T @ (F - d.system(beta) @ x)
+    fo, go = c.from_vec(ref)
+    S = Solver(k + 1, beta, precision="mixed", tma_level=tma_level)
+    t = lambda a: dev(a).float().contiguous()
+    fc, gc = S.residual_restrict_f32(t(u), t(p), t(f), t(g))
+    got = np.concatenate([host(fc.double()).ravel(), host(gc.double()).ravel()])
+    assert rel_err(got, np.concatenate([fo.ravel(), go.ravel()])) < 2e-5
+    S.close()
