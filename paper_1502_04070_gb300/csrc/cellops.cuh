@@ -403,6 +403,35 @@ __device__ __forceinline__ double2 block_sum2d_pair(double a, double b, int tid)
     return s;
 }
 
+// Block sums of a float (summed in float: a sum of squares for a convergence test) and a double
+// (one barrier); results valid in tid 0.  Keeps the second sum off the float64 pipe.
+__device__ __forceinline__ double2 block_sum2_fd(float a, double b, int tid) {
+    __shared__ float redf[NT / 32];
+    __shared__ double redd[NT / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if ((tid & 31) == 0) {
+        redf[tid >> 5] = a;
+        redd[tid >> 5] = b;
+    }
+    __syncthreads();
+    float sa = 0.f;
+    double sb = 0.0;
+    if (tid < 32) {
+        sa = tid < NT / 32 ? redf[tid] : 0.f;
+        sb = tid < NT / 32 ? redd[tid] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sa += __shfl_down_sync(0xffffffffu, sa, o);
+            sb += __shfl_down_sync(0xffffffffu, sb, o);
+        }
+    }
+    return make_double2((double)sa, sb);
+}
+
 // Block sum (thread-linear id tid) of one double; result valid in tid 0.
 __device__ __forceinline__ double block_sum2d(double v, int tid) {
     __shared__ double red[NT / 32];

@@ -157,8 +157,8 @@ __host__ __device__ __forceinline__ int orient(int si, int sj, int n) {
     return (si < h) != (sj < h);
 }
 
-// w_i = int psi_i = (number of triangles at vertex i) h^2 / 6: the pressure-mean weight (M_P 1)_i
-__device__ __forceinline__ double vertex_weight(int i, int j, int n) {
+// number of triangles at vertex (i, j) of a level with N = n (0 outside the level)
+__device__ __forceinline__ int vertex_triangles(int i, int j, int n) {
     int cnt = 0;
 #pragma unroll
     for (int SQ = 0; SQ < 4; ++SQ) {
@@ -167,8 +167,13 @@ __device__ __forceinline__ double vertex_weight(int i, int j, int n) {
         const int o = orient(si, sj, n), node = corner_node(SQ);
         cnt += ((tri_mask(o, 0) >> node) & 1u) + ((tri_mask(o, 1) >> node) & 1u);
     }
+    return cnt;
+}
+
+// w_i = int psi_i = (number of triangles at vertex i) h^2 / 6: the pressure-mean weight (M_P 1)_i
+__device__ __forceinline__ double vertex_weight(int i, int j, int n) {
     const double h = 1.0 / n;
-    return cnt * h * h / 6.0;
+    return vertex_triangles(i, j, n) * h * h / 6.0;
 }
 
 // stencil class (see stencil_pattern) of cell (i, j) of a level with N = n

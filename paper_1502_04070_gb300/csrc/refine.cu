@@ -181,6 +181,26 @@ __device__ __forceinline__ void vwin_df2(const DFPairCoef& q, const float (&pw)[
     }
 }
 // CHECKED: blocks at the boundary (off the mid-lines) read with range tests and the Dirichlet mask
+// Window point W of cell (i, j) from a planar float32 velocity array (both components in one 8-byte
+// load; every window point inside the arrays)
+template <int C, int W>
+__device__ __forceinline__ void win_pair1(int i, int j, const float* __restrict__ eu, int rs, int ps, float (&wx)[25],
+                                          float (&wy)[25]) {
+    if constexpr (need_win(C, true, true, W)) {
+        constexpr int dx = W % 5 - 2, dy = W / 5 - 2;
+        const float2 v = __ldg(reinterpret_cast<const float2*>(eu + (dx & 1) * ps + (2 * j + dy) * rs +
+                                                               2 * (i + (dx >> 1))));
+        wx[W] = v.x;
+        wy[W] = v.y;
+    }
+}
+template <int C, int... W>
+__device__ __forceinline__ void win_pairs(int i, int j, int n, const float* __restrict__ eu, float (&wx)[25],
+                                          float (&wy)[25], std::integer_sequence<int, W...>) {
+    const int rs = 2 * pl_pitch(n), ps = rs * pl_rows(n);
+    (win_pair1<C, W>(i, j, eu, rs, ps, wx, wy), ...);
+}
+
 template <int C, bool CHECKED, bool PL, int... K, int... V>
 __device__ __forceinline__ void merged_df(int i, int j, int n, const DFPairCoef& q, const float* __restrict__ eu,
                                           const float* __restrict__ ep, DFAcc& a, std::integer_sequence<int, K...>,
@@ -192,8 +212,7 @@ __device__ __forceinline__ void merged_df(int i, int j, int n, const DFPairCoef&
                                       std::make_integer_sequence<int, 25>{});
         vwin_load<C>(i, j, n, gview(ep, pl_vpitch(n)), pw, std::make_integer_sequence<int, 9>{});
     } else if constexpr (PL) {
-        win_load<C, true, true, false>(i, j, n, gviewp<true>(eu, n, 0), gviewp<true>(eu, n, 1), wx, wy,
-                                       std::make_integer_sequence<int, 25>{});
+        win_pairs<C>(i, j, n, eu, wx, wy, std::make_integer_sequence<int, 25>{});
         vwin_load<C>(i, j, n, gviewu(ep, pl_vpitch(n)), pw, std::make_integer_sequence<int, 9>{});
     } else if constexpr (CHECKED) {
         win_load<C, true, true, true>(i, j, n, gview(eu, 2 * n + 1), gview(eu + n2, 2 * n + 1), wx, wy,
@@ -249,12 +268,15 @@ __global__ void __launch_bounds__(NT, 4) k_ir_update_df(int n, const __grid_cons
                                                      double* __restrict__ xu, double* __restrict__ xp,
                                                      float2* __restrict__ ru, float2* __restrict__ rp,
                                                      float* __restrict__ r32u, float* __restrict__ r32p,
-                                                     double* __restrict__ partial, double* __restrict__ wpartial) {
+                                                     double* __restrict__ partial, double* __restrict__ wpartial,
+                                                     double wscale) {
     pdl_wait();
     CELL_INDEX
     const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
     float ss = 0.f;
-    double wp = 0.0;   // w_i x_p,i of the updated pressure (the zero-mean projection's numerator)
+    // (triangles at vertex i) x_p,i of the updated pressure; times wscale = h^2 / 6 per block, the
+    // zero-mean projection's numerator sum_i w_i x_p,i (float64 work kept to the additions)
+    double wp = 0.0;
     if (active) {
         DFAcc a;
 #pragma unroll
@@ -298,16 +320,16 @@ __global__ void __launch_bounds__(NT, 4) k_ir_update_df(int n, const __grid_cons
         const size_t vi = (size_t)j * (n + 1) + i, vi32 = PL ? (size_t)j * pl_vpitch(n) + i : vi;
         const double xpn = xp[vi] + (double)ep[vi32];
         xp[vi] = xpn;
-        wp = vertex_weight(i, j, n) * xpn;
+        wp = (double)vertex_triangles(i, j, n) * xpn;
         const float2 r = df_sub(rp[vi], a.bu);
         rp[vi] = r;
         r32p[vi32] = r.x;
         ss = fmaf(r.x, r.x, ss);
     }
-    const double2 t = block_sum2d_pair((double)ss, wp, tid);
+    const double2 t = block_sum2_fd(ss, wp, tid);
     if (tid == 0) {
         partial[blockIdx.y * gridDim.x + blockIdx.x] = t.x;
-        wpartial[blockIdx.y * gridDim.x + blockIdx.x] = t.y;
+        wpartial[blockIdx.y * gridDim.x + blockIdx.x] = t.y * wscale;
     }
     pdl_trigger();
 }
@@ -366,7 +388,7 @@ void launch_ir_update_df(cudaStream_t s, int n, const OpCoef<float>& chi, const 
                          float* r32u, float* r32p, double* partial, double* wpartial, bool planar) {
     launch_pdl(planar ? k_ir_update_df<true> : k_ir_update_df<false>, cells_grid(n), dim3(BX, BY), 0, s, n, chi, clo,
                make_df_pairs(chi, clo), eu, ep, xu, xp, reinterpret_cast<float2*>(ru), reinterpret_cast<float2*>(rp), r32u,
-               r32p, partial, wpartial);
+               r32p, partial, wpartial, 1.0 / (6.0 * (double)n * (double)n));
 }
 
 void launch_residual_df(cudaStream_t s, int n, const OpCoef<double>& c, const double* u, const double* p,
