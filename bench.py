@@ -75,6 +75,8 @@ def parse():
     ap.add_argument("--tma-level", type=int, default=0,
                     help="kernel modes: lowest planar float32 level (0: the library default; 14: none)")
     ap.add_argument("--planar-variant", type=int, default=None, help="kernel modes: force this planar step variant")
+    ap.add_argument("--coop-level", type=int, default=0,
+                    help="kernel modes: highest level of the cooperative small-level cycle (0: off)")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--host-loop", action="store_true",
@@ -101,7 +103,7 @@ def run_kernel(args):
     g = g - g.mean()
     prec = "mixed" if args.kernel in ("uzawa_f32", "mixed_solve", "ir_steps") else "fp64"
     S = Solver(k + 1, 1e4, precision=prec, gamma=args.gamma, coarse_level=args.coarse_level,
-               tma_level=args.tma_level)
+               tma_level=args.tma_level, coop_level=args.coop_level)
     if args.variant is not None or args.variants:
         from paper_1502_04070_gb300.solver import set_step_variant
         if args.variant is not None:

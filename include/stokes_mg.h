@@ -104,6 +104,12 @@ typedef struct stokes_params {
                           layout above.  The step needs the register tile's coefficient structure
                           (stokes_step_tables_match): setup and set_beta return STOKES_ERR_BAD_ARG for
                           a beta without it on such a level */
+    int coop_level;    /* STOKES_MIXED with the Uzawa smoother on the unit square: a visit of a float32
+                          level l <= coop_level (and above the coarsest level, below tma_level) runs the
+                          whole V- or W-cycle from l down, the coarsest solve included, as ONE
+                          cooperative launch whose phases meet at grid barriers, instead of one launch
+                          per phase.  0 or -1: off (the default; on a GB300 a phase of that launch
+                          costs about as much as a launch of its own); at most 6 */
 } stokes_params;
 
 /* Paper defaults: Uzawa, nu = 3+3, tau = sigma = 0.8, V-cycle, float64, one inner cycle, coarsest

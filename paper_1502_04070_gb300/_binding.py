@@ -29,6 +29,7 @@ class Params(ctypes.Structure):
         ("coarse_level", ctypes.c_int),
         ("domain", ctypes.c_int),
         ("tma_level", ctypes.c_int),
+        ("coop_level", ctypes.c_int),
     ]
 
 

@@ -171,6 +171,9 @@ struct stokes_handle_t {
     bool coarse_kernel = true;              // float32 levels <= 4 in one shared-memory kernel
     bool launch_failed = false;             // a step variant refused to launch (reported by the next call)
     bool has_planar = false;                // some float32 level is planar
+    int small_top = -1;                     // float32 levels clev+1..small_top: one cooperative launch per visit
+    OpCoef<float>* dcoef = nullptr;         // device copies of the float32 operators of levels 0..small_top
+    unsigned* dbar = nullptr;               // grid-barrier counter of that launch
     cudaGraphExec_t step = nullptr;         // one cycle + projection + residual norm
     int step_kernels = 0;                   // kernel nodes in `step`
     cudaGraphExec_t loop = nullptr;         // WHILE(not converged) { step; device-side test }
@@ -276,6 +279,35 @@ void mg_cycle(stokes_handle* h, std::vector<Level<T>>& H, int l) {
         return;
     }
     if constexpr (sizeof(T) == 4) {
+        // small levels: the whole V- or W-cycle from level l down in one cooperative launch
+        if (l <= h->small_top && l > h->clev) {
+            SmallCycleHost sh{};
+            for (int k = h->clev; k <= l; ++k) {
+                Level<float>& L = H[k];
+                sh.u[k] = L.u;
+                sh.p[k] = L.p;
+                sh.f[k] = L.f;
+                sh.g[k] = L.g;
+                sh.tu[k] = L.tu;
+                sh.tp[k] = L.tp;
+                sh.sinv[k] = L.sinv;
+                sh.coef_host[k] = &L.c;
+            }
+            sh.coef_dev = h->dcoef;
+            sh.inv0 = h->inv;
+            sh.cinv = h->cinv;
+            sh.cnb = h->cnb;
+            sh.bar = h->dbar;
+            sh.tau = (float)h->prm.tau;
+            sh.sigma = (float)h->prm.sigma;
+            sh.nu_pre = h->prm.nu_pre;
+            sh.nu_post = h->prm.nu_post;
+            sh.gamma = h->prm.gamma;
+            sh.top = l;
+            sh.clev = h->clev;
+            if (launch_small_cycle(h->st, sh) != cudaSuccess) h->launch_failed = true;
+            return;
+        }
         // small levels: the whole V-cycle from level l down in one CTA (shared memory)
         if (l <= kCoarseCycleTop && h->prm.gamma == 1 && h->prm.smoother == STOKES_UZAWA && h->coarse_kernel &&
             h->clev == 0) {
@@ -484,6 +516,9 @@ stokes_status rebuild_beta(stokes_handle* h) {
     }
     for (auto& lv : h->h32) {
         lv.c = make_coef<float>(lv.n, beta);
+        const int k = (int)(&lv - h->h32.data());
+        if (k <= h->small_top)   // the cooperative cycle's copy (the host structure stays in the handle)
+            CK(cudaMemcpyAsync(h->dcoef + k, &lv.c, sizeof(OpCoef<float>), cudaMemcpyHostToDevice, h->st));
         // planar levels run only the register-tile step, which needs its coefficient structure
         if (lv.planar && !reg_tables_match(lv.c)) return STOKES_ERR_BAD_ARG;
         launch_schur_diag<float>(h->st, lv.n, make_coef<double>(lv.n, beta), lv.sinv, kDomSquare,
@@ -618,7 +653,8 @@ stokes_status stokes_setup(const stokes_params* prm, void* stream, stokes_handle
         (P.precision != STOKES_FP64 && P.precision != STOKES_MIXED) ||
         (P.precision == STOKES_MIXED && P.inner_cycles < 1) || P.coarse_level < 0 ||
         P.coarse_level > kMaxCoarseLevel || P.coarse_level > P.levels - 1 ||
-        (P.domain != STOKES_UNIT_SQUARE && P.domain != STOKES_L_SHAPE) || (P.tma_level != 0 && P.tma_level < 5))
+        (P.domain != STOKES_UNIT_SQUARE && P.domain != STOKES_L_SHAPE) || (P.tma_level != 0 && P.tma_level < 5) ||
+        P.coop_level < -1 || P.coop_level > kSmallCycleTop)
         return STOKES_ERR_BAD_ARG;
     // the L-shaped domain: float64 Uzawa cycles, coarsest level 1 (the L's level 0)
     if (P.domain == STOKES_L_SHAPE && (P.precision != STOKES_FP64 || P.smoother != STOKES_UZAWA ||
@@ -663,6 +699,19 @@ stokes_status stokes_setup(const stokes_params* prm, void* stream, stokes_handle
         for (int k = 0; k < P.levels; ++k)
             if ((s = alloc_level(h->h32[k], k, h->mem, tma && k >= tlev)) != STOKES_OK) return bail(s);
         h->has_planar = tma && tlev < P.levels;
+        // the cooperative small-level cycle: compact float32 levels up to coop_level, above the coarsest
+        if (P.coop_level > 0 && P.smoother == STOKES_UZAWA && P.domain == STOKES_UNIT_SQUARE) {
+            int top = P.coop_level;
+            top = std::min(std::min(top, (int)kSmallCycleTop), std::min(P.levels - 1, tma ? tlev - 1 : (int)kSmallCycleTop));
+            if (top > P.coarse_level) {
+                h->small_top = top;
+                if (h->mem.get(&h->dcoef, sizeof(OpCoef<float>) * (size_t)(top + 1)) != cudaSuccess ||
+                    h->mem.get(&h->dbar, sizeof(unsigned)) != cudaSuccess) {
+                    cudaGetLastError();
+                    return bail(STOKES_ERR_OOM);
+                }
+            }
+        }
     }
     h->mass = make_mass<double>(h->fin().n);
     h->npartial = 2 * cells_blocks(h->fin().n);   // two sets of per-block partial sums (refinement update)

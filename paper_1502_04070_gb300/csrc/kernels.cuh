@@ -86,6 +86,29 @@ bool launch_uzawa_tma_variant(int variant, cudaStream_t s, int n, const OpCoef<f
 // for launch_uzawa_tma.
 bool launch_restrict_tma(cudaStream_t s, int n, bool pc_planar, const OpCoef<float>& c, const float* u, const float* p,
                          const float* f, const float* g, float* fc, float* gc, float* uc, float* pc);
+// The float32 V- or W-cycle from level `top` (compact layout, top <= kSmallCycleTop) down to the
+// coarsest level clev of the iteration, with its exact solve, in ONE cooperative launch (uzawa_reg.cu):
+// every CTA resident, phases separated by grid barriers whose waits are bounded (about a second; a
+// timeout sets the flag uzawa_tma_timeouts() reports).  On entry (u, p) of `top` hold its iterate and
+// (f, g) its right-hand side; on exit (u, p) hold the iterate after the cycle.  Arrays per level
+// (index = level, N = 2^(level + 1)); coef_host: the levels' operators (host), coef_dev: the same on the
+// device; inv0: the level-0 bordered inverse (clev = 0), cinv / cnb: the level-clev one (clev > 0);
+// bar: one device word, cleared by the launch (stream-ordered) and used by the barriers.
+constexpr int kSmallCycleTop = 6;
+struct SmallCycleHost {
+    float *u[kSmallCycleTop + 1], *p[kSmallCycleTop + 1], *f[kSmallCycleTop + 1], *g[kSmallCycleTop + 1];
+    float *tu[kSmallCycleTop + 1], *tp[kSmallCycleTop + 1];
+    const float* sinv[kSmallCycleTop + 1];
+    const OpCoef<float>* coef_host[kSmallCycleTop + 1];
+    const OpCoef<float>* coef_dev;
+    const double* inv0;
+    const double* cinv;
+    int cnb;
+    unsigned* bar;
+    float tau, sigma;
+    int nu_pre, nu_post, gamma, top, clev;
+};
+cudaError_t launch_small_cycle(cudaStream_t s, const SmallCycleHost& h);
 int tma_choice(int n);
 bool tma_tuned(int n);
 bool set_tma_choice(int n, int v);

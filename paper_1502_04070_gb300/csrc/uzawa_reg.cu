@@ -853,50 +853,19 @@ __device__ __forceinline__ void restrict_sq(const RestrictWeights& wt, int I, in
     }
 }
 
-template <int NW, int MINB, bool PC>
-__global__ void __launch_bounds__(32 * NW, MINB)
-    k_restrict_tma(int n, int TY, TileOrder ord, const __grid_constant__ OpCoef<float> c,
-                   const __grid_constant__ RegCoef q, const __grid_constant__ RestrictWeights wt,
-                   const __grid_constant__ TmaMaps maps, float* __restrict__ fc, float* __restrict__ gc,
-                   float* __restrict__ uc, float* __restrict__ pc) {
-    using G = TmaTile;
+// The defect on fine cells and vertices [i0 - 2, i0 + TX) x [j0 - 2, j0 + TY) of the staged tiles
+// (r_u over sF, r_p over sG, whose tile starts at vertex row j0 - 2) and its restriction to the
+// coarse cells [i0 / 2, i0 / 2 + TX / 2) x [j0 / 2, j0 / 2 + TY / 2) of level n / 2 (planar: PC), with
+// the coarse iterate of those cells set to zero.  All threads of the CTA take part.
+template <class G, int NW, bool PC>
+__device__ __forceinline__ void defect_restrict(int n, int TY, int i0, int j0, const OpCoef<float>& c, const RegCoef& q,
+                                                const RestrictWeights& wt, const float2* sU, float2* sF,
+                                                const float* sP, float* sG, float* __restrict__ fc,
+                                                float* __restrict__ gc, float* __restrict__ uc,
+                                                float* __restrict__ pc) {
     constexpr int TX = G::TX;
-    extern __shared__ unsigned char smem_raw[];
-    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    float2* sU = reinterpret_cast<float2*>(base + 128);
-    float2* sF = reinterpret_cast<float2*>(base + G::off_f(TY));
-    float* sP = reinterpret_cast<float*>(base + G::off_p(TY));
-    float* sG = reinterpret_cast<float*>(base + G::off_g(TY));
-    const unsigned bar = (unsigned)__cvta_generic_to_shared(base);
     const int UPL = G::upl(TY), FPL = G::fpl(TY);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int tc, tr;
-    ord.tile(blockIdx.x, tc, tr);
-    const int i0 = tc * TX, j0 = tr * TY;
-    if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    pdl_wait();
-    if (threadIdx.x == 0) {
-        const unsigned bytes = G::tx_bytes(TY) - 4u * (unsigned)G::dsz(TY);   // no Shat^{-1} tile
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-        const unsigned du = (unsigned)__cvta_generic_to_shared(sU), df = (unsigned)__cvta_generic_to_shared(sF);
-        tma_3d(du, &maps.u, 2 * (i0 - G::UX), 2 * (j0 - 3), 0, bar);
-        tma_3d(df, &maps.f0, 2 * (i0 - 2), j0 - 2, 0, bar);
-        tma_3d(df + 8 * 2 * FPL, &maps.f1, 2 * (i0 - 2), j0 - 2, 0, bar);
-        tma_2d((unsigned)__cvta_generic_to_shared(sP), &maps.p, i0 - G::PX, j0 - 3, bar);
-        tma_2d((unsigned)__cvta_generic_to_shared(sG), &maps.g, i0 - G::DX, j0 - 2, bar);
-    }
-    const bool ok = mbar_wait_bounded(bar, 0);
-    if (__syncthreads_or(!ok)) {
-        if (threadIdx.x == 0) {
-            atomicOr(&g_tma_timeout, 1u);
-            mbar_wait_bounded(bar, 0);
-        }
-        return;
-    }
     // ---- the fine defect on cells and vertices [i0 - 2, i0 + TX) x [j0 - 2, j0 + TY)
     const int h = n >> 1;
     const bool fast = (h < i0 - 2 || h >= i0 + TX) && (h < j0 - 2 || h >= j0 + TY);
@@ -983,7 +952,390 @@ __global__ void __launch_bounds__(32 * NW, MINB)
         gc[vi] = fmaf(0.5f, half, sv);
         pc[vi] = 0.f;
     }
+}
+
+template <int NW, int MINB, bool PC>
+__global__ void __launch_bounds__(32 * NW, MINB)
+    k_restrict_tma(int n, int TY, TileOrder ord, const __grid_constant__ OpCoef<float> c,
+                   const __grid_constant__ RegCoef q, const __grid_constant__ RestrictWeights wt,
+                   const __grid_constant__ TmaMaps maps, float* __restrict__ fc, float* __restrict__ gc,
+                   float* __restrict__ uc, float* __restrict__ pc) {
+    using G = TmaTile;
+    constexpr int TX = G::TX;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    float2* sU = reinterpret_cast<float2*>(base + 128);
+    float2* sF = reinterpret_cast<float2*>(base + G::off_f(TY));
+    float* sP = reinterpret_cast<float*>(base + G::off_p(TY));
+    float* sG = reinterpret_cast<float*>(base + G::off_g(TY));
+    const unsigned bar = (unsigned)__cvta_generic_to_shared(base);
+    const int FPL = G::fpl(TY);
+    int tc, tr;
+    ord.tile(blockIdx.x, tc, tr);
+    const int i0 = tc * TX, j0 = tr * TY;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    pdl_wait();
+    if (threadIdx.x == 0) {
+        const unsigned bytes = G::tx_bytes(TY) - 4u * (unsigned)G::dsz(TY);   // no Shat^{-1} tile
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+        const unsigned du = (unsigned)__cvta_generic_to_shared(sU), df = (unsigned)__cvta_generic_to_shared(sF);
+        tma_3d(du, &maps.u, 2 * (i0 - G::UX), 2 * (j0 - 3), 0, bar);
+        tma_3d(df, &maps.f0, 2 * (i0 - 2), j0 - 2, 0, bar);
+        tma_3d(df + 8 * 2 * FPL, &maps.f1, 2 * (i0 - 2), j0 - 2, 0, bar);
+        tma_2d((unsigned)__cvta_generic_to_shared(sP), &maps.p, i0 - G::PX, j0 - 3, bar);
+        tma_2d((unsigned)__cvta_generic_to_shared(sG), &maps.g, i0 - G::DX, j0 - 2, bar);
+    }
+    const bool ok = mbar_wait_bounded(bar, 0);
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) {
+            atomicOr(&g_tma_timeout, 1u);
+            mbar_wait_bounded(bar, 0);
+        }
+        return;
+    }
+    defect_restrict<G, NW, PC>(n, TY, i0, j0, c, q, wt, sU, sF, sP, sG, fc, gc, uc, pc);
     pdl_trigger();
+}
+
+// ---------------------------------------------------------------------------------------------
+// The float32 cycle below a small level in ONE cooperative launch.  On levels with N <= 128 a
+// multigrid phase is a few thousand cells, and launching one kernel per phase costs far more than
+// the arithmetic (a W-cycle visits level l 2^(k - l) times).  Here every CTA of a cooperative grid
+// (all resident at once) walks the phases of the whole V- or W-cycle from level `top` down to the
+// coarsest level of the iteration, doing its share of each phase's tiles and meeting the others at a
+// grid barrier between phases (a counter in global memory, bounded waits).  A phase is: one Uzawa
+// step (the register tile of k_uzawa_tma on tiles staged by plain loads from the compact layout),
+// defect + restriction (defect_restrict), prolongation + correction, or the exact coarsest solve.
+// Values written in one phase are read in the next through L2 (__ldcg), never through the read-only
+// or L1 caches.
+
+constexpr int kSmallTop = 6;              // highest level the cooperative cycle takes (N = 128)
+constexpr int kSmallTY = 12;              // tile height (even: whole coarse cells per tile)
+constexpr int kSmallNW = 8;               // warps per CTA
+constexpr int kSmallMaxNb = 2212;         // largest bordered coarse system (coarsest level 3)
+
+struct SmallLevelArgs {
+    float *u, *p, *f, *g, *tu, *tp;
+    const float* sinv;
+};
+struct SmallCycleArgs {
+    SmallLevelArgs L[kSmallTop + 1];      // index = level (N = 2^(level + 1)), compact float32 layout
+    RegCoef q[kSmallTop + 1];
+    const OpCoef<float>* coef;            // device copies of the levels' operators, index = level
+    RestrictWeights wt;
+    const double* inv0;                   // level-0 bordered inverse (27 x 27), coarsest level 0
+    const double* cinv;                   // coarsest level c > 0: its bordered inverse, cnb x cnb
+    int cnb;
+    unsigned* bar;                        // barrier counter, zero at launch
+    float tau, sigma;
+    int nu_pre, nu_post, gamma, top, clev;
+};
+
+// Grid barrier number k (k = 1, 2, ...): every CTA adds one to the counter and waits until it
+// reaches k x gridDim.x (the counter only grows during a launch).  The wait gives up after about a
+// second (g_tma_timeout is set, false is returned).
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned k) {
+    __syncthreads();
+    bool ok = true;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(bar, 1u);
+        const unsigned target = k * gridDim.x;
+        const long long t0 = clock64();
+        // poll with relaxed loads (an acquire load per poll would invalidate the L1 each time); one
+        // fence after the wait orders this CTA's later reads after the other CTAs' writes
+        while (true) {
+            unsigned v;
+            asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+            if (v >= target) break;
+            if (clock64() - t0 > kTmaWaitCycles) {
+                atomicOr(&g_tma_timeout, 1u);
+                ok = false;
+                break;
+            }
+            __nanosleep(32);
+        }
+        __threadfence();
+    }
+    return __syncthreads_and(ok);
+}
+
+// Stages the tiles of TmaTile geometry for tile (i0, j0) of a compact float32 level with N = n from
+// global memory through L2: u (zero off the interior lattice), f, p, g (vertex rows from gy0) and,
+// if sinv is given, Shat^{-1}; zero outside the arrays.
+__device__ void stage_compact(int n, int TY, int i0, int j0, int gy0, const float* u, const float* p, const float* f,
+                              const float* g, const float* sinv, float2* sU, float2* sF, float* sP, float* sG,
+                              float* sS) {
+    using G = TmaTile;
+    constexpr int B = 4;   // elements per thread and round: their loads are all in flight together
+    const int ld = 2 * n + 1, n2 = ld * ld;
+    const int nt = blockDim.x;
+    // u: two parity planes of 2 (TY + 6) rows of UWH pairs, lattice X = 2 (i0 - UX) + 2 x + plane
+    const int un = 2 * 2 * (TY + 6) * G::UWH;
+    for (int t0 = threadIdx.x; t0 < un; t0 += B * nt) {
+        float2 v[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int t = t0 + b * nt;
+            const int x = t % G::UWH, y = (t / G::UWH) % (2 * (TY + 6)), pl = t / (G::UWH * 2 * (TY + 6));
+            const int X = 2 * (i0 - G::UX) + 2 * x + pl, Y = 2 * (j0 - 3) + y;
+            v[b] = (t < un && interior2(X, Y, n)) ? make_float2(__ldcg(u + Y * ld + X), __ldcg(u + n2 + Y * ld + X))
+                                                  : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int b = 0; b < B; ++b)
+            if (t0 + b * nt < un) sU[t0 + b * nt] = v[b];
+    }
+    // f: four node-type planes of TY + 4 cell rows of FW pairs
+    const int fn = 4 * (TY + 4) * G::FW;
+    for (int t0 = threadIdx.x; t0 < fn; t0 += B * nt) {
+        float2 v[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int t = t0 + b * nt;
+            const int x = t % G::FW, r = (t / G::FW) % (TY + 4), pl = t / (G::FW * (TY + 4));
+            const int X = 2 * (i0 - 2 + x) + (pl & 1), Y = 2 * (j0 - 2 + r) + (pl >> 1);
+            v[b] = (t < fn && X >= 0 && Y >= 0 && X <= 2 * n && Y <= 2 * n)
+                       ? make_float2(__ldcg(f + Y * ld + X), __ldcg(f + n2 + Y * ld + X))
+                       : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int b = 0; b < B; ++b)
+            if (t0 + b * nt < fn) sF[t0 + b * nt] = v[b];
+    }
+    const int pn = (TY + 6) * G::PW, dn = (TY + 2) * G::DW;
+    for (int t0 = threadIdx.x; t0 < pn; t0 += B * nt) {
+        float v[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int t = t0 + b * nt;
+            const int I = i0 - G::PX + t % G::PW, J = j0 - 3 + t / G::PW;
+            v[b] = (t < pn && I >= 0 && J >= 0 && I <= n && J <= n) ? __ldcg(p + J * (n + 1) + I) : 0.f;
+        }
+#pragma unroll
+        for (int b = 0; b < B; ++b)
+            if (t0 + b * nt < pn) sP[t0 + b * nt] = v[b];
+    }
+    for (int t0 = threadIdx.x; t0 < dn; t0 += B * nt) {
+        float vg[B], vs[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int t = t0 + b * nt;
+            const int I = i0 - G::DX + t % G::DW, J = gy0 + t / G::DW;
+            const bool in = t < dn && I >= 0 && J >= 0 && I <= n && J <= n;
+            vg[b] = in ? __ldcg(g + J * (n + 1) + I) : 0.f;
+            vs[b] = (in && sinv) ? __ldcg(sinv + J * (n + 1) + I) : 0.f;
+        }
+#pragma unroll
+        for (int b = 0; b < B; ++b)
+            if (t0 + b * nt < dn) {
+                sG[t0 + b * nt] = vg[b];
+                if (sinv) sS[t0 + b * nt] = vs[b];
+            }
+    }
+}
+
+// (u, p) += I (uc, pc) on the fine cells owned by coarse cell (i, j), compact layouts
+__device__ void small_prolong_cell(int i, int j, int nc, const RestrictWeights& wt, const float* uc, const float* pc,
+                                   float* u, float* p) {
+    const int nf = 2 * nc, ldc = 2 * nc + 1, n2c = ldc * ldc, ldf = 2 * nf + 1, n2f = ldf * ldf;
+    if (i < nc && j < nc) {
+        float zx[9], zy[9];
+#pragma unroll
+        for (int m = 0; m < 9; ++m) {
+            const int k = (2 * j + m / 3) * ldc + 2 * i + m % 3;
+            zx[m] = __ldcg(uc + k);
+            zy[m] = __ldcg(uc + n2c + k);
+        }
+        const int o = orient(i, j, nc);
+#pragma unroll
+        for (int fb = 0; fb < 4; ++fb)
+#pragma unroll
+            for (int fa = 0; fa < 4; ++fa) {
+                const int X = 4 * i + fa, Y = 4 * j + fb;
+                if (!interior2(X, Y, nf)) continue;
+                float sx = 0.f, sy = 0.f;
+#pragma unroll
+                for (int L = 0; L < 9; ++L) {
+                    const float w = wt.w[o][L][fb][fa];
+                    sx = fmaf(w, zx[L], sx);
+                    sy = fmaf(w, zy[L], sy);
+                }
+                const int k = Y * ldf + X;
+                u[k] = __ldcg(u + k) + sx;
+                u[n2f + k] = __ldcg(u + n2f + k) + sy;
+            }
+    }
+    auto P = [&](int a, int b) { return __ldcg(pc + b * (nc + 1) + a); };
+    auto add = [&](int x, int y, float v) { p[y * (nf + 1) + x] = __ldcg(p + y * (nf + 1) + x) + v; };
+    const float p00 = P(i, j);
+    add(2 * i, 2 * j, p00);
+    if (i < nc) add(2 * i + 1, 2 * j, 0.5f * (p00 + P(i + 1, j)));
+    if (j < nc) add(2 * i, 2 * j + 1, 0.5f * (p00 + P(i, j + 1)));
+    if (i < nc && j < nc) add(2 * i + 1, 2 * j + 1, 0.5f * (orient(i, j, nc) == 0 ? p00 + P(i + 1, j + 1) : P(i + 1, j) + P(i, j + 1)));
+}
+
+// The exact solve on the coarsest level c of the iteration into its (u, p): c = 0 with the 27 x 27
+// bordered inverse, c > 0 with the dense bordered inverse (rows over every warp of the grid, the
+// right-hand side gathered into each CTA's shared memory F).
+__device__ void small_coarse_solve(const SmallCycleArgs& A, double* F) {
+    const SmallLevelArgs& Z = A.L[A.clev];
+    const int n = 2 << A.clev, ld = 2 * n + 1, n2 = ld * ld, nm = 2 * n - 1, nv = nm * nm;
+    const int nunk = A.clev == 0 ? 27 : A.cnb - 1;
+    const double* inv = A.clev == 0 ? A.inv0 : A.cinv;
+    const int stride = A.clev == 0 ? 27 : A.cnb;
+    for (int t = threadIdx.x; t < nunk; t += blockDim.x) {
+        double v;
+        if (t < 2 * nv) {
+            const int c = t / nv, r = t - c * nv;
+            v = (double)__ldcg(Z.f + c * n2 + (r / nm + 1) * ld + r % nm + 1);
+        } else {
+            v = (double)__ldcg(Z.g + (t - 2 * nv));
+        }
+        F[t] = v;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    for (int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < nunk; row += nwarps) {
+        const double* r = inv + (size_t)row * stride;
+        double acc = 0.0;
+#pragma unroll 8
+        for (int j = lane; j < nunk; j += 32) acc = fma(__ldg(r + j), F[j], acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) {
+            if (row < 2 * nv) {
+                const int c = row / nv, q = row - c * nv;
+                Z.u[c * n2 + (q / nm + 1) * ld + q % nm + 1] = (float)acc;
+            } else {
+                Z.p[row - 2 * nv] = (float)acc;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(32 * kSmallNW, 1) k_small_cycle(const __grid_constant__ SmallCycleArgs A) {
+    using G = TmaTile;
+    constexpr int TY = kSmallTY;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    float2* sU = reinterpret_cast<float2*>(base + 128);
+    float2* sF = reinterpret_cast<float2*>(base + G::off_f(TY));
+    float* sP = reinterpret_cast<float*>(base + G::off_p(TY));
+    float* sG = reinterpret_cast<float*>(base + G::off_g(TY));
+    float* sS = reinterpret_cast<float*>(base + G::off_s(TY));
+    double* sRhs = reinterpret_cast<double*>(base + G::bytes(TY));            // coarsest right-hand side
+    OpCoef<float>* sc = reinterpret_cast<OpCoef<float>*>(sRhs + kSmallMaxNb);  // levels clev + 1 .. top
+    const int nlev = A.top - A.clev;
+    {
+        const float* src = reinterpret_cast<const float*>(A.coef + A.clev + 1);
+        float* dst = reinterpret_cast<float*>(sc);
+        const int words = nlev * (int)(sizeof(OpCoef<float>) / sizeof(float));
+        for (int t = threadIdx.x; t < words; t += blockDim.x) dst[t] = __ldg(src + t);
+    }
+    __syncthreads();
+    unsigned k = 0;                // grid barriers passed
+    bool sw[kSmallTop + 1] = {};   // level state in (tu, tp) instead of (u, p)
+    int cnt[kSmallTop + 1] = {};   // coarse corrections still to do at a level
+    int l = A.top;
+    bool enter = true;
+    auto tiles = [&](int n, int& cols) {
+        cols = (n + 1 + G::TX - 1) / G::TX;
+        return cols * ((n + 1 + TY - 1) / TY);
+    };
+    auto smooth = [&](int lv) {   // one Uzawa step on level lv, ping-pong
+        const SmallLevelArgs& L = A.L[lv];
+        const int n = 2 << lv;
+        const float* xu = sw[lv] ? L.tu : L.u;
+        const float* xp = sw[lv] ? L.tp : L.p;
+        float* ou = sw[lv] ? L.u : L.tu;
+        float* op = sw[lv] ? L.p : L.tp;
+        int cols;
+        const int nt = tiles(n, cols);
+        for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+            const int i0 = (t % cols) * G::TX, j0 = (t / cols) * TY;
+            stage_compact(n, TY, i0, j0, j0 - 1, xu, xp, L.f, L.g, L.sinv, sU, sF, sP, sG, sS);
+            __syncthreads();
+            reg_phases<G, false, kSmallNW>(n, TY, i0, j0, sc[lv - A.clev - 1], A.q[lv], A.tau, A.sigma, sU, sF, sP, sG,
+                                           sS, ou, op);
+            __syncthreads();
+        }
+        sw[lv] = !sw[lv];
+        return grid_barrier(A.bar, ++k);
+    };
+    while (true) {
+        if (enter) {
+            if (l == A.clev) {
+                small_coarse_solve(A, sRhs);
+                sw[l] = false;
+                if (!grid_barrier(A.bar, ++k)) return;
+                enter = false;
+                continue;
+            }
+            for (int m = 0; m < A.nu_pre; ++m)
+                if (!smooth(l)) return;
+            {   // defect and restriction into level l - 1, whose iterate starts from zero
+                const SmallLevelArgs& L = A.L[l];
+                const SmallLevelArgs& C = A.L[l - 1];
+                const int n = 2 << l;
+                int cols;
+                const int nt = tiles(n, cols);
+                for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+                    const int i0 = (t % cols) * G::TX, j0 = (t / cols) * TY;
+                    stage_compact(n, TY, i0, j0, j0 - 2, sw[l] ? L.tu : L.u, sw[l] ? L.tp : L.p, L.f, L.g, nullptr, sU,
+                                  sF, sP, sG, sS);
+                    __syncthreads();
+                    defect_restrict<G, kSmallNW, false>(n, TY, i0, j0, sc[l - A.clev - 1], A.q[l], A.wt, sU, sF, sP, sG,
+                                                        C.f, C.g, C.u, C.p);
+                    __syncthreads();
+                }
+                sw[l - 1] = false;
+                if (!grid_barrier(A.bar, ++k)) return;
+            }
+            cnt[l] = A.gamma;
+            --l;
+        } else {
+            if (l == A.top) break;
+            const int pl = l + 1;
+            if (--cnt[pl] > 0) {   // the W-cycle's next coarse correction, from the current coarse iterate
+                l = pl - 1;
+                enter = true;
+                continue;
+            }
+            {   // prolongation and correction
+                const SmallLevelArgs& C = A.L[l];
+                const SmallLevelArgs& L = A.L[pl];
+                const int nc = 2 << l, cells = (nc + 1) * (nc + 1);
+                const float* uc = sw[l] ? C.tu : C.u;
+                const float* pc = sw[l] ? C.tp : C.p;
+                float* uf = sw[pl] ? L.tu : L.u;
+                float* pf = sw[pl] ? L.tp : L.p;
+                for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < cells; q += gridDim.x * blockDim.x)
+                    small_prolong_cell(q % (nc + 1), q / (nc + 1), nc, A.wt, uc, pc, uf, pf);
+                if (!grid_barrier(A.bar, ++k)) return;
+            }
+            for (int m = 0; m < A.nu_post; ++m)
+                if (!smooth(pl)) return;
+            l = pl;
+        }
+    }
+    if (sw[A.top]) {   // odd number of steps on the top level: its state back to (u, p)
+        const SmallLevelArgs& L = A.L[A.top];
+        const int n = 2 << A.top, nu = 2 * (2 * n + 1) * (2 * n + 1), np = (n + 1) * (n + 1);
+        for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nu; q += gridDim.x * blockDim.x) L.u[q] = __ldcg(L.tu + q);
+        for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < np; q += gridDim.x * blockDim.x) L.p[q] = __ldcg(L.tp + q);
+    }
+}
+
+// dynamic shared memory: the tiles, the coarsest right-hand side, nlev levels' operators, and the
+// slack that aligns the base to 128 bytes
+size_t small_cycle_smem(int nlev) {
+    return TmaTile::bytes(kSmallTY) + sizeof(double) * kSmallMaxNb + sizeof(OpCoef<float>) * (size_t)nlev + 128;
 }
 
 template <int NW, int MINB>
@@ -1163,7 +1515,54 @@ bool launch_rt(cudaStream_t s, int n, const OpCoef<float>& c, const float* u, co
     return true;
 }
 
+cudaError_t small_smem_attr() {
+    return cudaFuncSetAttribute(k_small_cycle, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)small_cycle_smem(kSmallTop));
+}
+
 }  // namespace
+
+cudaError_t launch_small_cycle(cudaStream_t s, const SmallCycleHost& h) {
+    if (h.top < 1 || h.top > kSmallTop || h.clev < 0 || h.clev >= h.top || h.cnb > kSmallMaxNb) return cudaErrorInvalidValue;
+    SmallCycleArgs A{};
+    for (int l = h.clev; l <= h.top; ++l) {
+        A.L[l] = SmallLevelArgs{h.u[l], h.p[l], h.f[l], h.g[l], h.tu[l], h.tp[l], h.sinv[l]};
+        if (l > h.clev && !make_reg_coef(*h.coef_host[l], h.tau, A.q[l])) return cudaErrorInvalidValue;
+    }
+    A.coef = h.coef_dev;
+    A.wt = restrict_weights();
+    A.inv0 = h.inv0;
+    A.cinv = h.cinv;
+    A.cnb = h.cnb;
+    A.bar = h.bar;
+    A.tau = h.tau;
+    A.sigma = h.sigma;
+    A.nu_pre = h.nu_pre;
+    A.nu_post = h.nu_post;
+    A.gamma = h.gamma;
+    A.top = h.top;
+    A.clev = h.clev;
+    const size_t smem = small_cycle_smem(h.top - h.clev);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_small_cycle, 32 * kSmallNW, smem);
+    if (e != cudaSuccess) return e;
+    // every SM: the tile phases use at most `tiles` CTAs, the coarsest solve's rows all of them
+    const int grid = std::max(1, sms * per_sm);
+    if ((e = cudaMemsetAsync(h.bar, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(32 * kSmallNW);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;   // every CTA resident: the grid barriers complete
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_small_cycle, A);
+}
 
 bool launch_restrict_tma(cudaStream_t s, int n, bool pc_planar, const OpCoef<float>& c, const float* u, const float* p,
                          const float* f, const float* g, float* fc, float* gc, float* uc, float* pc) {
@@ -1178,6 +1577,7 @@ cudaError_t prepare_uzawa_reg() {
     if (e == cudaSuccess) e = tma_smem_attr<8, 4>();
     if (e == cudaSuccess) e = rt_smem_attr<true>();
     if (e == cudaSuccess) e = rt_smem_attr<false>();
+    if (e == cudaSuccess) e = small_smem_attr();
     return e;
 }
 

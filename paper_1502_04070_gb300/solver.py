@@ -44,7 +44,7 @@ class Solver:
 
     def __init__(self, levels: int, beta: float, *, nu_pre=3, nu_post=3, tau=None, sigma=0.8,
                  smoother="uzawa", gamma=1, precision="fp64", inner_cycles=1, coarse_level=0, domain="square",
-                 tma_level=0, stream=None, device=None):
+                 tma_level=0, coop_level=0, stream=None, device=None):
         self._lib = B.load()
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         prm = B.Params()
@@ -59,6 +59,7 @@ class Solver:
         prm.coarse_level = coarse_level
         prm.domain = _DOMAINS[domain]
         prm.tma_level = tma_level
+        prm.coop_level = coop_level
         self.params = prm
         self.levels = levels
         self.beta = float(beta)
@@ -306,7 +307,7 @@ class BatchSolver:
     launch (stokes_batch_setup / stokes_batch_solve)."""
 
     def __init__(self, levels, betas, *, precision="mixed", nu_pre=3, nu_post=3, tau=0.8, sigma=0.8, gamma=1,
-                 coarse_level=0, tma_level=0, autotune=True, device=None):
+                 coarse_level=0, tma_level=0, coop_level=0, autotune=True, device=None):
         self._lib = B.load()
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.levels = [int(l) for l in levels]
@@ -317,6 +318,7 @@ class BatchSolver:
         prm.nu_pre, prm.nu_post, prm.tau, prm.sigma, prm.gamma = nu_pre, nu_post, tau, sigma, gamma
         prm.coarse_level = coarse_level
         prm.tma_level = tma_level
+        prm.coop_level = coop_level
         prm.precision = _PREC[precision]
         n = len(self.levels)
         lv = (ctypes.c_int * n)(*self.levels)
