@@ -48,10 +48,11 @@ TOL = 1e-8
 METRIC = "DoF/s to 1e-8 relative residual (h=1/2048 manufactured solution, mixed precision vs plain FP64 multigrid)"
 
 
-def workload_text(cycle, coarse_level):
+def workload_text(cycle, coarse_level, inner=1):
     return ("manufactured solution u=curl(sin^2(pi x) sin^2(pi y)), p=cos(pi x) cos(pi y): unit square, "
             "Taylor-Hood P2-P1, h=1/2048 (k=10, 37736451 DoF), beta=1e4, %s(3,3) Uzawa cycles tau=sigma=0.8, "
-            "coarsest level %d solved exactly, solve from 0 to 1e-8 relative residual" % (cycle, coarse_level))
+            "coarsest level %d solved exactly, %d float32 cycle%s per float64 refinement step, solve from 0 to 1e-8 "
+            "relative residual" % (cycle, coarse_level, inner, "" if inner == 1 else "s"))
 
 
 def parse():
@@ -62,6 +63,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cycle", default="V", choices=["V", "W"], help="cycle of the headline solve")
     ap.add_argument("--head-coarse-level", type=int, default=3, help="coarsest level of the headline solve")
+    ap.add_argument("--head-inner-cycles", type=int, default=2,
+                    help="float32 cycles per float64 refinement step of the headline solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=2, help="solves of the plain float64 comparison")
     ap.add_argument("--only-head", action="store_true", help="skip the parsed secondary workloads")
@@ -257,7 +260,7 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": workload_text("VW"[gamma - 1], cl)},
+            "data": "synthetic", "config": {"workload": workload_text("VW"[gamma - 1], cl, args.head_inner_cycles)},
             "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -408,7 +411,7 @@ def run_ours(args, rank, world, local_rank):
     gn_h = torch.from_numpy(gn_np).pin_memory()
     fn, gn = fn_h.cuda(), gn_h.cuda()
     cl = args.head_coarse_level
-    S = Solver(levels, BETA_HEAD, precision="mixed", gamma=gamma, coarse_level=cl)
+    S = Solver(levels, BETA_HEAD, precision="mixed", gamma=gamma, coarse_level=cl, inner_cycles=args.head_inner_cycles)
     S.autotune()                  # float32 step variant per level (process-wide), before any graph capture
     variants = step_variants(levels)
     f, g = S.load_vectors(fn, gn, project_g=True)
@@ -558,7 +561,8 @@ def run_ours(args, rank, world, local_rank):
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32 cycles + f64 refinement",
                 "data": "synthetic",
-                "config": {"workload": workload_text(args.cycle, cl), "precision": "mixed", "dof_per_solve": n_dof,
+                "config": {"workload": workload_text(args.cycle, cl, args.head_inner_cycles), "precision": "mixed",
+                           "dof_per_solve": n_dof,
                            "solves_per_step": 1, "solves_per_s": args.steps * world / (ms / 1000),
                            "l2": "inputs larger than L2 (the level-10 hierarchy holds about 1.5 GB) and a 256 MB "
                                  "buffer written between steps (inside the timed region)",
