@@ -346,7 +346,8 @@ stokes_status stokes_set_step_variant(int levels, int variant);
 /* The same for the planar float32 levels (stokes_params.tma_level), whose step stages its tiles by
  * tensor-memory-access box copies, one tile per CTA of 8 warps: 0 tile height for 3 resident CTAs per
  * SM, 2 for 4 (fewer registers, shorter tiles); 1 and 3 the same, each CTA also prefetching into L2
- * the tiles of a tile one wave of resident CTAs ahead.
+ * the tiles of a tile one wave of resident CTAs ahead; 4 and 5 two cell rows per warp pass (window
+ * rows shared by the two loaded once), 2 or 3 CTAs per SM, with the prefetch.
  * stokes_autotune times them on the handle's planar levels; untuned sizes use 0.  Same scope and
  * rules as stokes_set_step_variant; -1 / STOKES_ERR_BAD_ARG out of range. */
 int stokes_planar_step_variant(int levels);

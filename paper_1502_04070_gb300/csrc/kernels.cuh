@@ -74,9 +74,11 @@ bool launch_uzawa_tma(cudaStream_t s, int n, const OpCoef<float>& c, float tau, 
 bool uzawa_tma_available();
 // Variants of the planar step, one tile per CTA of 8 warps: 0 tile height for 3 CTAs per SM (80
 // registers), 2 for 4 CTAs per SM (64 registers); 1, 3 the same, each CTA also prefetching into L2
-// the tiles of the tile one wave of resident CTAs ahead.  launch_uzawa_tma runs the variant chosen
-// for level size n (0 until autotune_uzawa_tma or set_tma_choice).
-constexpr int kTmaVariants = 4;
+// the tiles of the tile one wave of resident CTAs ahead; 4, 5 two rows per warp pass (the shared
+// window rows loaded once; even tile heights), 2 or 3 CTAs per SM, with the prefetch.
+// launch_uzawa_tma runs the variant chosen for level size n (0 until autotune_uzawa_tma or
+// set_tma_choice).
+constexpr int kTmaVariants = 6;
 bool launch_uzawa_tma_variant(int variant, cudaStream_t s, int n, const OpCoef<float>& c, float tau, float sigma,
                               const float* u, const float* p, const float* f, const float* g, const float* sinv,
                               float* u_out, float* p_out);

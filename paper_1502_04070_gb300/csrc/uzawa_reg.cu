@@ -426,9 +426,205 @@ __device__ __forceinline__ void phase3_fast(const RegCoef& q, const float2* sF, 
     }
 }
 
+// ---- the same phases two cell (or vertex) rows at a time: the windows of rows r and r + 1 overlap
+// in three of their five lattice rows (two of three vertex rows), so each shared value they share is
+// loaded once for both (fewer shared-memory wavefronts per cell).  Needs an even tile height.
+
+// the A group terms of window point W applied to the value w
+template <int C, int W>
+__device__ __forceinline__ void a_apply(const float2 (&a)[kGroups], float2 w, float2 (&au)[4], float2 (&ctr)[4]) {
+    constexpr int g0 = kGid[C][0][W], g1 = kGid[C][1][W], g2 = kGid[C][2][W], g3 = kGid[C][3][W];
+    if constexpr (g0 >= 0) au[0] = __ffma2_rn(a[g0], w, au[0]);
+    if constexpr (g1 >= 0) au[1] = __ffma2_rn(a[g1], w, au[1]);
+    if constexpr (g2 >= 0) au[2] = __ffma2_rn(a[g2], w, au[2]);
+    if constexpr (g3 >= 0) au[3] = __ffma2_rn(a[g3], w, au[3]);
+    if constexpr (W == 12) ctr[0] = w;
+    if constexpr (W == 13) ctr[1] = w;
+    if constexpr (W == 17) ctr[2] = w;
+    if constexpr (W == 18) ctr[3] = w;
+}
+// lattice point at row offset R (-2..4 from row r's centre) and column offset DX: window point
+// (R + 2) * 5 + DX + 2 of row r (A) and R * 5 + DX + 2 of row r + 1 (B)
+template <int C, int UWH, int I>
+__device__ __forceinline__ void a_pair_term(const float2 (&a)[kGroups], const float2* t0, const float2* t1,
+                                            float2 (&auA)[4], float2 (&ctrA)[4], float2 (&auB)[4],
+                                            float2 (&ctrB)[4]) {
+    constexpr int R = I / 5 - 2, DX = I % 5 - 2;
+    constexpr int WA = (R + 2) * 5 + DX + 2, WB = R * 5 + DX + 2;
+    constexpr bool useA = R <= 2 && a_win(C, WA), useB = R >= 0 && a_win(C, WB);
+    if constexpr (useA || useB) {
+        const float2 w = ((DX & 1) ? t1 : t0)[R * UWH + (DX >> 1)];
+        if constexpr (useA) a_apply<C, (useA ? WA : 0)>(a, w, auA, ctrA);
+        if constexpr (useB) a_apply<C, (useB ? WB : 0)>(a, w, auB, ctrB);
+    }
+}
+template <int C, int UWH, int... I>
+__device__ __forceinline__ void a_pair_rows(const float2 (&a)[kGroups], const float2* t0, const float2* t1,
+                                            float2 (&auA)[4], float2 (&ctrA)[4], float2 (&auB)[4], float2 (&ctrB)[4],
+                                            std::integer_sequence<int, I...>) {
+    (a_pair_term<C, UWH, I>(a, t0, t1, auA, ctrA, auB, ctrB), ...);
+}
+// B^T rows of the H, E, C nodes of window point V applied to the vertex value v
+template <int C, int V>
+__device__ __forceinline__ void bt_apply(float v, float2 (&bt)[4]) {
+    addk<kBTx[C][1][V]>(bt[1].x, v);
+    addk<kBTy[C][1][V]>(bt[1].y, v);
+    addk<kBTx[C][2][V]>(bt[2].x, v);
+    addk<kBTy[C][2][V]>(bt[2].y, v);
+    addk<kBTx[C][3][V]>(bt[3].x, v);
+    addk<kBTy[C][3][V]>(bt[3].y, v);
+}
+// vertex at row offset RV (-1..2 from row r's centre vertex) and column offset DV
+template <int C, int LD, int I>
+__device__ __forceinline__ void bt_pair_term(const float* sp, float2 (&btA)[4], float2 (&btB)[4]) {
+    constexpr int RV = I / 3 - 1, DV = I % 3 - 1;
+    constexpr int VA = (RV + 1) * 3 + DV + 1, VB = RV * 3 + DV + 1;
+    constexpr bool useA = RV <= 1 && bt_vwin(C, VA), useB = RV >= 0 && bt_vwin(C, VB);
+    if constexpr (useA || useB) {
+        const float v = sp[RV * LD + DV];
+        if constexpr (useA) bt_apply<C, (useA ? VA : 0)>(v, btA);
+        if constexpr (useB) bt_apply<C, (useB ? VB : 0)>(v, btB);
+    }
+}
+template <int C, int LD, int... I>
+__device__ __forceinline__ void bt_pair_rows(const float* sp, float2 (&btA)[4], float2 (&btB)[4],
+                                             std::integer_sequence<int, I...>) {
+    (bt_pair_term<C, LD, I>(sp, btA, btB), ...);
+}
+// B row of the vertices of rows r (A) and r + 1 (B) over the u^{m-1/2} planes
+template <int C, int FW, int I>
+__device__ __forceinline__ void b_pair_term(const float2* f0, int fpl, float& accA, float& accB) {
+    constexpr int R = I / 5 - 2, DX = I % 5 - 2;
+    constexpr int WA = (R + 2) * 5 + DX + 2, WB = R * 5 + DX + 2;
+    constexpr bool useA = R <= 2 && (kBx[C][R <= 2 ? WA : 0] != 0 || kBy[C][R <= 2 ? WA : 0] != 0);
+    constexpr bool useB = R >= 0 && (kBx[C][R >= 0 ? WB : 0] != 0 || kBy[C][R >= 0 ? WB : 0] != 0);
+    if constexpr (useA || useB) {
+        constexpr int plane = (DX & 1) + 2 * (R & 1);
+        const float2 w = f0[plane * fpl + (R >> 1) * FW + (DX >> 1)];
+        if constexpr (useA) {
+            addk<kBx[C][useA ? WA : 0]>(accA, w.x);
+            addk<kBy[C][useA ? WA : 0]>(accA, w.y);
+        }
+        if constexpr (useB) {
+            addk<kBx[C][useB ? WB : 0]>(accB, w.x);
+            addk<kBy[C][useB ? WB : 0]>(accB, w.y);
+        }
+    }
+}
+template <int C, int FW, int... I>
+__device__ __forceinline__ void b_pair_rows(const float2* f0, int fpl, float& accA, float& accB,
+                                            std::integer_sequence<int, I...>) {
+    (b_pair_term<C, FW, I>(f0, fpl, accA, accB), ...);
+}
+
+// u^{m-1/2} of the cells of row r from their A and B^T rows (written over f)
+template <class G, bool INNER>
+__device__ __forceinline__ void u_half_row(const float2 (&au)[4], const float2 (&ctr)[4], const float2 (&bt)[4],
+                                           float ti0, float ti1, float2 mb, float2* sF, int FPL, int r, int lane,
+                                           int i0, int j0, int n) {
+    bool unk[4] = {true, true, true, true};
+    if constexpr (!INNER) {
+        const int ci = i0 - 2 + lane, cj = j0 - 2 + r;
+        const bool ci_in = ci > 0 && ci < n, cj_in = cj > 0 && cj < n;
+        const bool ci_h = ci >= 0 && ci < n, cj_h = cj >= 0 && cj < n;
+        unk[0] = ci_in && cj_in;
+        unk[1] = ci_h && cj_in;
+        unk[2] = ci_in && cj_h;
+        unk[3] = ci_h && cj_h;
+    }
+    float2* fr = sF + r * G::FW + lane;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        const float2 fs = fr[s * FPL];
+        const float ti = s == 0 ? ti0 : ti1;
+        float2 t = f2(fs.x - au[s].x, fs.y - au[s].y);
+        if (s > 0) t = __ffma2_rn(mb, bt[s], t);
+        const float2 h = __ffma2_rn(f2(ti, ti), t, ctr[s]);
+        if constexpr (INNER) fr[s * FPL] = h;
+        else fr[s * FPL] = unk[s] ? h : f2(0.f, 0.f);
+    }
+}
+
+template <class G, int C, bool INNER>
+__device__ __forceinline__ void phase1_pair(const RegCoef& q, const float2* sU, int UPL, const float* sP, float2* sF,
+                                           int FPL, int TY, int NW, int warp, int lane, int i0, int j0, int n) {
+    float2 a[kGroups];
+    load_coef<C>(q, a);
+    const float ti0 = q.ti[C][0], ti1 = q.ti[C][1];
+    const float2 mb = f2(-q.b, -q.b);
+    for (int r = 2 * warp; r < TY + 4; r += 2 * NW) {
+        const float2* t0 = sU + 2 * (r + 1) * G::UWH + lane + G::UX - 2;
+        const float2* t1 = t0 + UPL;
+        float2 auA[4], ctrA[4], btA[4], auB[4], ctrB[4], btB[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) auA[s] = ctrA[s] = btA[s] = auB[s] = ctrB[s] = btB[s] = f2(0.f, 0.f);
+        a_pair_rows<C, G::UWH>(a, t0, t1, auA, ctrA, auB, ctrB, std::make_integer_sequence<int, 35>{});
+        bt_pair_rows<C, G::PW>(sP + (r + 1) * G::PW + lane + G::PX - 2, btA, btB, std::make_integer_sequence<int, 12>{});
+        u_half_row<G, INNER>(auA, ctrA, btA, ti0, ti1, mb, sF, FPL, r, lane, i0, j0, n);
+        u_half_row<G, INNER>(auB, ctrB, btB, ti0, ti1, mb, sF, FPL, r + 1, lane, i0, j0, n);
+    }
+}
+
+template <class G, int C>
+__device__ __forceinline__ void phase2_pair(const RegCoef& q, const float2* sF, int FPL, float* sG, const float* sS,
+                                            float sigma, int TY, int NW, int warp, int lane) {
+    const float b = q.b;
+    for (int r = 2 * warp; r < TY + 2; r += 2 * NW) {
+        if (lane >= G::DN) break;
+        const float2* f0 = sF + (r + 1) * G::FW + lane + 1;
+        float accA = 0.f, accB = 0.f;
+        b_pair_rows<C, G::FW>(f0, FPL, accA, accB, std::make_integer_sequence<int, 35>{});
+        const int k = r * G::DW + lane + G::DX - 1;
+        sG[k] = sigma * sS[k] * fmaf(b, accA, -sG[k]);
+        sG[k + G::DW] = sigma * sS[k + G::DW] * fmaf(b, accB, -sG[k + G::DW]);
+    }
+}
+
+// the new (u, p) of the cells of row r from their B^T dp rows
+template <class G, bool PLO, bool INNER>
+__device__ __forceinline__ void uzawa_out_row(const float2 (&bt)[4], float nb1, const float2* sF, int FPL,
+                                              const float* sG, const float* sP, int r, int lane, int i0, int j0,
+                                              int n, float* __restrict__ u_out, float* __restrict__ p_out) {
+    const int ci = i0 + lane, cj = j0 + r;
+    if (!INNER && (ci > n || cj > n)) return;
+    const float2* hr = sF + (r + 2) * G::FW + lane + 2;
+    float2 o[4];
+    o[0] = hr[0];
+#pragma unroll
+    for (int s = 1; s < 4; ++s) o[s] = __ffma2_rn(f2(nb1, nb1), bt[s], hr[s * FPL]);
+    if constexpr (INNER) {
+#pragma unroll
+        for (int s = 0; s < 4; ++s) store_node<PLO>(u_out, n, 2 * ci + (s & 1), 2 * cj + (s >> 1), o[s]);
+    } else {
+        const CellNodes cn = cell_nodes(ci, cj, n);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            if (!slot_exists(cn, s)) continue;
+            store_node<PLO>(u_out, n, 2 * ci + (s & 1), 2 * cj + (s >> 1), slot_unknown(cn, s) ? o[s] : f2(0.f, 0.f));
+        }
+    }
+    p_out[vert_at<PLO>(n, ci, cj)] = sP[(r + 3) * G::PW + lane + G::PX] + sG[(r + 1) * G::DW + lane + G::DX];
+}
+
+template <class G, bool PLO, int C, bool INNER>
+__device__ __forceinline__ void phase3_pair(const RegCoef& q, const float2* sF, int FPL, const float* sG,
+                                            const float* sP, int TY, int NW, int warp, int lane, int i0, int j0,
+                                            int n, float* __restrict__ u_out, float* __restrict__ p_out) {
+    const float nb1 = -q.ti[C][1] * q.b;
+    for (int r = 2 * warp; r < TY; r += 2 * NW) {
+        if (lane >= G::TX) break;
+        float2 btA[4], btB[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) btA[s] = btB[s] = f2(0.f, 0.f);
+        bt_pair_rows<C, G::DW>(sG + (r + 1) * G::DW + lane + G::DX, btA, btB, std::make_integer_sequence<int, 12>{});
+        uzawa_out_row<G, PLO, INNER>(btA, nb1, sF, FPL, sG, sP, r, lane, i0, j0, n, u_out, p_out);
+        uzawa_out_row<G, PLO, INNER>(btB, nb1, sF, FPL, sG, sP, r + 1, lane, i0, j0, n, u_out, p_out);
+    }
+}
+
 // The three phases of the step on the staged tiles (sU, sP, sF = f, sG = g, sS = Shat^{-1}); writes
 // the new state of the CTA's cells to (u_out, p_out).
-template <class G, bool PLO, int NW>
+template <class G, bool PLO, int NW, bool PAIR = false>
 __device__ __forceinline__ void reg_phases(int n, int TY, int i0, int j0, const OpCoef<float>& c, const RegCoef& q,
                                            float tau, float sigma, const float2* sU, float2* sF, const float* sP,
                                            float* sG, const float* sS, float* __restrict__ u_out,
@@ -448,7 +644,15 @@ __device__ __forceinline__ void reg_phases(int n, int TY, int i0, int j0, const 
     const QuadLat<G> vhy{sF, FPL, i0 - 2, j0 - 2, true};
 
     // ---- u^{m-1/2} on cells (i0 - 2 + lane, j0 - 2 + r), written over f
-    if (fast) {
+    if (fast && PAIR) {
+        if (inner) {
+            if (cls == 0) phase1_pair<G, 0, true>(q, sU, UPL, sP, sF, FPL, TY, NW, warp, lane, i0, j0, n);
+            else phase1_pair<G, 1, true>(q, sU, UPL, sP, sF, FPL, TY, NW, warp, lane, i0, j0, n);
+        } else {
+            if (cls == 0) phase1_pair<G, 0, false>(q, sU, UPL, sP, sF, FPL, TY, NW, warp, lane, i0, j0, n);
+            else phase1_pair<G, 1, false>(q, sU, UPL, sP, sF, FPL, TY, NW, warp, lane, i0, j0, n);
+        }
+    } else if (fast) {
         if (inner) {
             if (cls == 0) phase1_fast<G, 0, true>(q, sU, UPL, sP, sF, FPL, TY, NW, warp, lane, i0, j0, n);
             else phase1_fast<G, 1, true>(q, sU, UPL, sP, sF, FPL, TY, NW, warp, lane, i0, j0, n);
@@ -483,7 +687,10 @@ __device__ __forceinline__ void reg_phases(int n, int TY, int i0, int j0, const 
     __syncthreads();
 
     // ---- dp on vertices (i0 - 1 + lane, j0 - 1 + r), written over g
-    if (fast) {
+    if (fast && PAIR) {
+        if (cls == 0) phase2_pair<G, 0>(q, sF, FPL, sG, sS, sigma, TY, NW, warp, lane);
+        else phase2_pair<G, 1>(q, sF, FPL, sG, sS, sigma, TY, NW, warp, lane);
+    } else if (fast) {
         if (cls == 0) phase2_fast<G, 0>(q, sF, FPL, sG, sS, sigma, TY, NW, warp, lane);
         else phase2_fast<G, 1>(q, sF, FPL, sG, sS, sigma, TY, NW, warp, lane);
     } else {
@@ -503,7 +710,15 @@ __device__ __forceinline__ void reg_phases(int n, int TY, int i0, int j0, const 
     __syncthreads();
 
     // ---- new (u, p) on the owned cells (i0 + lane, j0 + r)
-    if (fast) {
+    if (fast && PAIR) {
+        if (inner) {
+            if (cls == 0) phase3_pair<G, PLO, 0, true>(q, sF, FPL, sG, sP, TY, NW, warp, lane, i0, j0, n, u_out, p_out);
+            else phase3_pair<G, PLO, 1, true>(q, sF, FPL, sG, sP, TY, NW, warp, lane, i0, j0, n, u_out, p_out);
+        } else {
+            if (cls == 0) phase3_pair<G, PLO, 0, false>(q, sF, FPL, sG, sP, TY, NW, warp, lane, i0, j0, n, u_out, p_out);
+            else phase3_pair<G, PLO, 1, false>(q, sF, FPL, sG, sP, TY, NW, warp, lane, i0, j0, n, u_out, p_out);
+        }
+    } else if (fast) {
         if (inner) {
             if (cls == 0) phase3_fast<G, PLO, 0, true>(q, sF, FPL, sG, sP, TY, NW, warp, lane, i0, j0, n, u_out, p_out);
             else phase3_fast<G, PLO, 1, true>(q, sF, FPL, sG, sP, TY, NW, warp, lane, i0, j0, n, u_out, p_out);
@@ -704,7 +919,7 @@ __device__ __forceinline__ void tma_prefetch_tile(int TY, int i0, int j0, const 
 
 // pf > 0: also prefetch into L2 the tiles of tile blockIdx.x + pf (about one wave of resident CTAs
 // ahead), so that the CTA that takes it finds its tiles in L2
-template <int NW, int MINB>
+template <int NW, int MINB, bool PAIR = false>
 __global__ void __launch_bounds__(32 * NW, MINB)
     k_uzawa_tma(int n, int TY, TileOrder ord, const __grid_constant__ OpCoef<float> c, const __grid_constant__ RegCoef q,
                 float tau, float sigma, const __grid_constant__ TmaMaps maps, float* __restrict__ u_out,
@@ -751,7 +966,7 @@ __global__ void __launch_bounds__(32 * NW, MINB)
         }
         return;
     }
-    reg_phases<G, true, NW>(n, TY, i0, j0, c, q, tau, sigma, sU, sF, sP, sG, sS, u_out, p_out);
+    reg_phases<G, true, NW, PAIR>(n, TY, i0, j0, c, q, tau, sigma, sU, sF, sP, sG, sS, u_out, p_out);
     pdl_trigger();
 }
 
@@ -1343,9 +1558,9 @@ cudaError_t reg_smem_attr() {
     return cudaFuncSetAttribute(k_uzawa_reg<NW, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)RegTile::bytes(kRegMaxRows));
 }
-template <int NW, int MINB>
+template <int NW, int MINB, bool PAIR = false>
 cudaError_t tma_smem_attr() {
-    return cudaFuncSetAttribute(k_uzawa_tma<NW, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_uzawa_tma<NW, MINB, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)TmaTile::bytes(kRegMaxRows));
 }
 
@@ -1353,7 +1568,7 @@ cudaError_t tma_smem_attr() {
 // (work of one tile, about ty + 4 rows of the u^{m-1/2} region), among the tile heights that keep
 // at least MINB CTAs of kernel k (dynamic shared memory G::bytes(ty)) resident per SM.
 template <class G, class K>
-int tile_rows(int n, K k, int nthreads, int minb, int* cache) {
+int tile_rows(int n, K k, int nthreads, int minb, int* cache, bool even = false) {
     const int lv = 31 - __builtin_clz((unsigned)n);
     int& r = cache[lv & 31];
     if (r) return r;
@@ -1364,7 +1579,7 @@ int tile_rows(int n, K k, int nthreads, int minb, int* cache) {
     const int cols = (n + 1 + G::TX - 1) / G::TX;
     double best = 1e300;
     int best_ty = 12;
-    for (int ty = 4; ty <= kRegMaxRows; ++ty) {
+    for (int ty = 4; ty <= kRegMaxRows; ty += even ? 2 : 1) {
         int per_sm = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, nthreads, G::bytes(ty)) != cudaSuccess ||
             per_sm < minb)
@@ -1392,10 +1607,10 @@ int reg_rows(int n) {
     static int cache[32] = {};
     return tile_rows<RegTile>(n, k_uzawa_reg<NW, MINB>, 32 * NW, MINB, cache);
 }
-template <int NW, int MINB>
+template <int NW, int MINB, bool PAIR = false>
 int tma_rows(int n) {
     static int cache[32] = {};
-    return tile_rows<TmaTile>(n, k_uzawa_tma<NW, MINB>, 32 * NW, MINB, cache);
+    return tile_rows<TmaTile>(n, k_uzawa_tma<NW, MINB, PAIR>, 32 * NW, MINB, cache, PAIR);
 }
 template <class G>
 TileOrder tile_order(int n, int ty) {
@@ -1463,12 +1678,12 @@ bool make_tma_maps(int n, int ty, const float* u, const float* p, const float* f
            encode_box(m.g, g, 2, vd, vs, gb) && encode_box(m.s, sinv, 2, vd, vs, gb);
 }
 
-template <int NW, int MINB>
+template <int NW, int MINB, bool PAIR = false>
 bool launch_tma_v(cudaStream_t s, int n, const OpCoef<float>& c, float tau, float sigma, const float* u, const float* p,
                   const float* f, const float* g, const float* sinv, float* u_out, float* p_out, bool prefetch) {
     RegCoef q;
     if (!make_reg_coef(c, tau, q)) return false;
-    const int ty = tma_rows<NW, MINB>(n);
+    const int ty = tma_rows<NW, MINB, PAIR>(n);
     TmaMaps m;
     if (!make_tma_maps(n, ty, u, p, f, g, sinv, m)) return false;
     const TileOrder ord = tile_order<TmaTile>(n, ty);
@@ -1477,14 +1692,14 @@ bool launch_tma_v(cudaStream_t s, int n, const OpCoef<float>& c, float tau, floa
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_uzawa_tma<NW, MINB>, 32 * NW, TmaTile::bytes(ty)) !=
-            cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_uzawa_tma<NW, MINB, PAIR>, 32 * NW,
+                                                          TmaTile::bytes(ty)) != cudaSuccess)
             per_sm = MINB;
         cudaGetLastError();
         pf = std::max(1, sms) * std::max(1, per_sm);
     }
-    launch_pdl(k_uzawa_tma<NW, MINB>, dim3(ord.cols * ord.rows), dim3(32 * NW), TmaTile::bytes(ty), s, n, ty, ord, c, q,
-               tau, sigma, m, u_out, p_out, pf);
+    launch_pdl(k_uzawa_tma<NW, MINB, PAIR>, dim3(ord.cols * ord.rows), dim3(32 * NW), TmaTile::bytes(ty), s, n, ty, ord, c,
+               q, tau, sigma, m, u_out, p_out, pf);
     return true;
 }
 
@@ -1575,6 +1790,8 @@ cudaError_t prepare_uzawa_reg() {
     if (e == cudaSuccess) e = reg_smem_attr<8, 4>();
     if (e == cudaSuccess) e = tma_smem_attr<8, 3>();
     if (e == cudaSuccess) e = tma_smem_attr<8, 4>();
+    if (e == cudaSuccess) e = tma_smem_attr<8, 2, true>();
+    if (e == cudaSuccess) e = tma_smem_attr<8, 3, true>();
     if (e == cudaSuccess) e = rt_smem_attr<true>();
     if (e == cudaSuccess) e = rt_smem_attr<false>();
     if (e == cudaSuccess) e = small_smem_attr();
@@ -1601,6 +1818,8 @@ bool launch_uzawa_tma_variant(int variant, cudaStream_t s, int n, const OpCoef<f
         case 1: return launch_tma_v<8, 3>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out, true);
         case 2: return launch_tma_v<8, 4>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out, false);
         case 3: return launch_tma_v<8, 4>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out, true);
+        case 4: return launch_tma_v<8, 2, true>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out, true);
+        case 5: return launch_tma_v<8, 3, true>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out, true);
         default: return launch_tma_v<8, 3>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out, false);
     }
 }

@@ -89,7 +89,7 @@ def test_step_variant_selection_without_gpu():
     assert lib.stokes_set_step_variant(32, 0) == _binding.ERR_BAD_ARG
     assert lib.stokes_set_step_variant(5, 12) == _binding.ERR_BAD_ARG
     assert lib.stokes_set_step_variant(5, -1) == _binding.ERR_BAD_ARG
-    assert lib.stokes_set_planar_step_variant(5, 4) == _binding.ERR_BAD_ARG
+    assert lib.stokes_set_planar_step_variant(5, 6) == _binding.ERR_BAD_ARG
     assert lib.stokes_set_planar_step_variant(1, 0) == _binding.ERR_BAD_ARG
     assert lib.stokes_planar_step_variant(40) == -1
     assert lib.stokes_step_variant(1) == -1

@@ -37,10 +37,10 @@ def _state(k, seed):
 
 @pytest.mark.parametrize("k", [5, 6])
 @pytest.mark.parametrize("beta", [0.0, 1e2, 1e8])
-@pytest.mark.parametrize("nu,variant", [(1, 0), (3, 0), (3, 1), (3, 2), (3, 3)])
+@pytest.mark.parametrize("nu,variant", [(1, 0), (3, 0), (3, 1), (3, 2), (3, 3), (1, 4), (3, 4), (3, 5)])
 def test_planar_step_by_oracle(discs, k, beta, nu, variant):
     """Every planar step variant: tiles for 3 or 4 resident CTAs per SM, with and without the L2
-    prefetch of a later tile."""
+    prefetch of a later tile, and two cell rows per warp pass."""
     from paper_1502_04070_gb300.solver import Solver, planar_step_variant, set_planar_step_variant
     H = mg.Hierarchy(k + 1, beta, discs[:k + 1])
     d = H.discs[-1]
@@ -89,7 +89,7 @@ def test_planar_step_zeroes_the_boundary(discs):
 _DIRECT = {}
 
 
-@pytest.mark.parametrize("gamma,coarse_level,variant", [(1, 0, 0), (2, 0, 1), (2, 3, 2), (1, 3, 3)])
+@pytest.mark.parametrize("gamma,coarse_level,variant", [(1, 0, 0), (2, 0, 1), (2, 3, 2), (1, 3, 3), (1, 0, 4), (2, 3, 5)])
 def test_planar_mixed_solve_by_oracle(discs, gamma, coarse_level, variant):
     """k = 5 with levels 5 and up planar: the finest level restricts to a compact level."""
     from paper_1502_04070_gb300.solver import Solver, planar_step_variant, set_planar_step_variant
