@@ -12,6 +12,8 @@
 #include <mutex>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/stokes_mg.h"
 #include "coef.h"
 #include "elements.h"
@@ -23,6 +25,17 @@ cudaError_t launch_euler_nodal(cudaStream_t st, size_t n, double beta, const dou
 }  // namespace smg
 
 using namespace smg;
+
+namespace {
+
+// A named range around each public call that launches work, for timeline profilers (NVTX: header-only,
+// no cost unless a profiler is attached).
+struct ApiRange {
+    explicit ApiRange(const char* name) { nvtxRangePushA(name); }
+    ~ApiRange() { nvtxRangePop(); }
+};
+
+}  // namespace
 
 namespace {
 
@@ -644,6 +657,7 @@ void stokes_destroy(stokes_handle* h) {
 }
 
 stokes_status stokes_setup(const stokes_params* prm, void* stream, stokes_handle** out) {
+    ApiRange nvtx_range("stokes_setup");
     if (!prm || !out) return STOKES_ERR_BAD_ARG;
     *out = nullptr;
     const stokes_params& P = *prm;
@@ -744,6 +758,7 @@ stokes_status stokes_setup(const stokes_params* prm, void* stream, stokes_handle
 static stokes_status autotune_levels(stokes_handle* h, cudaStream_t st);
 
 stokes_status stokes_autotune(stokes_handle* h) {
+    ApiRange nvtx_range("stokes_autotune");
     if (!h) return STOKES_ERR_BAD_ARG;
     stokes_status s = autotune_levels(h, h->st);
     if (s == STOKES_OK && h->step) {   // the captured cycle holds the old choices
@@ -771,6 +786,7 @@ stokes_status stokes_set_allocator(stokes_alloc_fn alloc, stokes_free_fn release
 }
 
 stokes_status stokes_set_beta(stokes_handle* h, double beta) {
+    ApiRange nvtx_range("stokes_set_beta");
     if (!h || !(beta >= 0.0) || !std::isfinite(beta)) return STOKES_ERR_BAD_ARG;
     h->prm.beta = beta;
     return rebuild_beta(h);
@@ -787,6 +803,7 @@ stokes_status stokes_sizes(const stokes_handle* h, int* N, size_t* n_vel, size_t
 }
 
 stokes_status stokes_cycle(stokes_handle* h, double* u, double* p, const double* f, const double* g) {
+    ApiRange nvtx_range("stokes_cycle");
     if (!h || !u || !p || !f || !g) return STOKES_ERR_BAD_ARG;
     stokes_status s;
     if ((s = copy_in(h, u, p, f, g)) != STOKES_OK) return s;
@@ -802,6 +819,7 @@ stokes_status stokes_cycle(stokes_handle* h, double* u, double* p, const double*
 
 stokes_status stokes_solve(stokes_handle* h, double* u, double* p, const double* f, const double* g,
                            double tol, int max_cycles, stokes_report* rep, double* history) {
+    ApiRange nvtx_range("stokes_solve");
     if (!h || !u || !p || !f || !g || max_cycles < 0 || !(tol >= 0.0)) return STOKES_ERR_BAD_ARG;
     stokes_status s;
     if ((s = copy_in(h, u, p, f, g)) != STOKES_OK) return s;
@@ -951,6 +969,7 @@ stokes_status stokes_smooth(stokes_handle* h, double* u, double* p, const double
 }
 
 stokes_status stokes_smooth_f32(stokes_handle* h, float* u, float* p, const float* f, const float* g, int nu) {
+    ApiRange nvtx_range("stokes_smooth_f32");
     if (!h || !u || !p || !f || !g || nu < 0 || !h->mixed()) return STOKES_ERR_BAD_ARG;
     Level<float> lv = h->h32.back();   // coefficients, diagonals and ping-pong partners of the finest level
     if (lv.planar) {
@@ -979,6 +998,7 @@ stokes_status stokes_smooth_f32(stokes_handle* h, float* u, float* p, const floa
 
 stokes_status stokes_residual_restrict_f32(stokes_handle* h, const float* u, const float* p, const float* f,
                                            const float* g, float* fc, float* gc) {
+    ApiRange nvtx_range("stokes_residual_restrict_f32");
     if (!h || !u || !p || !f || !g || !fc || !gc || !h->mixed() || h->L < 2) return STOKES_ERR_BAD_ARG;
     Level<float>& lv = h->h32.back();
     Level<float>& cl = h->h32[h->L - 2];
@@ -1195,6 +1215,7 @@ void stokes_batch_destroy(stokes_batch* b) {
 
 stokes_status stokes_batch_setup(int count, const int* levels, const double* betas, const stokes_params* base,
                                  void* stream, int autotune, stokes_batch** out) {
+    ApiRange nvtx_range("stokes_batch_setup");
     if (count < 1 || !levels || !betas || !base || !out) return STOKES_ERR_BAD_ARG;
     *out = nullptr;
     stokes_batch* b = new stokes_batch_t();
@@ -1319,6 +1340,7 @@ static stokes_status batch_build(stokes_batch* b, double* const* u, double* cons
 stokes_status stokes_batch_solve(stokes_batch* b, double* const* u, double* const* p, const double* const* f,
                                  const double* const* g, double tol, int max_cycles, int* cycles,
                                  double* rel_residual) {
+    ApiRange nvtx_range("stokes_batch_solve");
     if (!b || !u || !p || !f || !g || !(tol > 0.0) || max_cycles < 1) return STOKES_ERR_BAD_ARG;
     std::vector<const void*> key;
     for (int i = 0; i < b->count; ++i) {
@@ -1472,6 +1494,7 @@ static stokes_status euler_results(const std::vector<double>& res, int steps, do
 stokes_status stokes_euler_run(stokes_handle* h, double* u, double* p, const double* const* f_nodal,
                                const double* const* g_nodal, int steps, double tol, int max_cycles, int* cycles,
                                double* rel_residual) {
+    ApiRange nvtx_range("stokes_euler_run");
     if (!h || !u || !p || !f_nodal || !g_nodal || steps < 1 || !(tol > 0.0) || max_cycles < 1) return STOKES_ERR_BAD_ARG;
     std::vector<const void*> key = {u, p};
     for (int n = 0; n < steps; ++n) {
@@ -1522,6 +1545,7 @@ stokes_status stokes_euler_run(stokes_handle* h, double* u, double* p, const dou
 stokes_status stokes_batch_euler_run(stokes_batch* b, double* const* u, double* const* p,
                                      const double* const* f_nodal, const double* const* g_nodal, int steps,
                                      double tol, int max_cycles, int* cycles, double* rel_residual) {
+    ApiRange nvtx_range("stokes_batch_euler_run");
     if (!b || !u || !p || !f_nodal || !g_nodal || steps < 1 || !(tol > 0.0) || max_cycles < 1)
         return STOKES_ERR_BAD_ARG;
     const int count = b->count;
