@@ -521,16 +521,25 @@ def run_ours(args, rank, world, local_rank):
     d2h = (u.numel() + p.numel()) * 8
     u_host = torch.empty(u.shape, dtype=torch.float64).pin_memory()
     p_host = torch.empty(p.shape, dtype=torch.float64).pin_memory()
+    # device buffers of the nodal data and the load vectors, reused by every step (as a serving loop
+    # would); one untimed step first
+    fd, gd = torch.empty_like(fn_h, device="cuda"), torch.empty_like(gn_h, device="cuda")
+    ff, gg = S.zeros_u(), S.zeros_p()
+
+    def e2e_step():
+        fd.copy_(fn_h, non_blocking=True)
+        gd.copy_(gn_h, non_blocking=True)
+        S.load_vectors(fd, gd, project_g=True, out=(ff, gg))
+        solve_once(S, ff, gg, u, p)
+        u_host.copy_(u)
+        p_host.copy_(p)
+
+    e2e_step()
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        fd = fn_h.to("cuda", non_blocking=True)
-        gd = gn_h.to("cuda", non_blocking=True)
-        ff, gg = S.load_vectors(fd, gd, project_g=True)
-        solve_once(S, ff, gg, u, p)
-        u_host.copy_(u)
-        p_host.copy_(p)
+        e2e_step()
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0)
     e2e_value = n_dof * e2e_steps * world / e2e_s

@@ -114,8 +114,14 @@ class Solver:
         B.check(self._lib.stokes_set_beta(self._h, float(beta)), "stokes_set_beta")
         self.beta = float(beta)
 
-    def load_vectors(self, f_nodal, g_nodal, project_g=True):
-        f, g = self.zeros_u(), self.zeros_p()
+    def load_vectors(self, f_nodal, g_nodal, project_g=True, out=None):
+        """Load vectors (f, g) of nodal data; out = (f, g) writes into given float64 tensors."""
+        if out is None:
+            f, g = self.zeros_u(), self.zeros_p()
+        else:
+            f, g = out
+            self._chk(f, self.shape_u, "f")
+            self._chk(g, self.shape_p, "g")
         B.check(self._lib.stokes_load_vectors(self._h, self._chk(f_nodal, self.shape_u, "f_nodal"),
                                               self._chk(g_nodal, self.shape_p, "g_nodal"), int(project_g),
                                               _ptr(f), _ptr(g)), "stokes_load_vectors")
