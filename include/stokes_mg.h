@@ -50,8 +50,10 @@ typedef enum stokes_status {
     STOKES_ERR_CUDA = 3,         /* a CUDA runtime call failed */
     STOKES_NOT_CONVERGED = 4,    /* solve reached max_cycles above tol (result still returned) */
     STOKES_DIVERGED = 5,         /* residual became NaN/Inf or grew in 8 consecutive cycles */
-    STOKES_ERR_TIMEOUT = 6       /* reserved for a bounded device-side wait that gives up; no call
-                                    returns it at present (no kernel of the library waits on a flag) */
+    STOKES_ERR_TIMEOUT = 6       /* a bounded device-side wait gave up (about a second): the tile
+                                    copies of the planar levels' kernels, or a grid barrier of the
+                                    cooperative small-level cycle; reported by the next solve, cycle,
+                                    float32 smoothing or batch call after it; results are not valid */
 } stokes_status;
 
 typedef enum stokes_smoother {
