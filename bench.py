@@ -19,7 +19,8 @@ Also measured, as parsed keys of the same line:
   adjoint   -- h = 1/1024 (k = 9), beta = 1e3, L = 1/2 ||u - u_target||_M^2: forward + backward;
   timestep  -- implicit Euler steps at h = 1/512 (beta = 1/dt): host-driven steps, the same steps as
                one CUDA-graph launch, and 8 trajectories with their own step lengths in one launch;
-  lshape    -- the L-shaped domain (square without [1/2, 1]^2) at h = 1/512, float64 V and W cycles.
+  lshape    -- the L-shaped domain (square without [1/2, 1]^2) at h = 1/512, float64 V and W cycles,
+               mixed-precision V-cycles.
 
 --oracle-batch N times the oracle (CPU) on N instances of the batch workload across all host cores
 (a process pool, one instance per task) and prints that one JSON line instead.
@@ -862,7 +863,8 @@ def math_cos(x):
 
 def run_lshape(args, world):
     """The L-shaped domain at h = 1/512 of the square's lattice (L-level 7), beta = 1e2, f, g uniform
-    [-1, 1] on the L's unknowns (seed 9, sum g = 0), float64 V(3,3) and W(3,3) to 1e-8 from zero."""
+    [-1, 1] on the L's unknowns (seed 9, sum g = 0), float64 V(3,3) and W(3,3) to 1e-8 from zero, and
+    V(3,3) in mixed precision (float32 cycles inside float64 refinement) to the same tolerance."""
     import numpy as np
     import torch
 
@@ -884,10 +886,11 @@ def run_lshape(args, world):
     ndof = int(2 * np.count_nonzero(f[0]) + np.count_nonzero(~out_p))
     fd, gd = torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda()
     out = {"workload": "L-shaped domain (unit square without [1/2,1]^2), lattice h=1/512, beta=1e2, f,g "
-                       "uniform[-1,1] on the L's unknowns (seed 9), float64, solve from 0 to 1e-8",
+                       "uniform[-1,1] on the L's unknowns (seed 9), solve from 0 to 1e-8 (float64 V, W; "
+                       "mixed-precision V)",
            "unknowns": ndof}
-    for name, gamma in (("V", 1), ("W", 2)):
-        S = Solver(k + 1, 1e2, precision="fp64", gamma=gamma, coarse_level=1, domain="lshape")
+    for name, gamma, prec in (("V", 1, "fp64"), ("W", 2, "fp64"), ("V_mixed", 1, "mixed")):
+        S = Solver(k + 1, 1e2, precision=prec, gamma=gamma, coarse_level=1, domain="lshape")
         S.solve(fd, gd, tol=TOL, max_cycles=200)
         torch.cuda.synchronize()
         t = time.perf_counter()

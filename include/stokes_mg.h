@@ -92,8 +92,9 @@ typedef struct stokes_params {
                           removed quadrant (the re-entrant sides x = 1/2, y >= 1/2 and y = 1/2,
                           x >= 1/2 and beyond) Dirichlet nodes and the vertices strictly inside it not
                           unknowns; entries of u, p, f, g there are ignored on input and zero on output,
-                          and the zero-mean pressure is over the L.  It needs STOKES_FP64, the Uzawa
-                          smoother, coarse_level = 1 (the L's level 0) and levels >= 2; load vectors,
+                          and the zero-mean pressure is over the L.  It needs the Uzawa smoother,
+                          coarse_level = 1 (the L's level 0) and levels >= 2; with STOKES_MIXED its
+                          float32 levels keep the compact layout and the per-phase step; load vectors,
                           Euler right-hand sides and mass products are square-only (they return
                           STOKES_ERR_BAD_ARG on an L handle) */
     int tma_level;     /* STOKES_MIXED with the Uzawa smoother on the unit square: the float32 levels

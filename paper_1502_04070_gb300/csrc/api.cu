@@ -263,7 +263,10 @@ bool smooth_level(stokes_handle* h, Level<T>& lv, int steps, bool timed, bool sw
         if (P.smoother == STOKES_NORMAL_EQ) {
             launch_normal_eq<T>(h->st, lv.n, lv.c, (T)P.tau, xu, xp, lv.f, lv.g, lv.sinv, ou, op);
         } else if constexpr (sizeof(T) == 4) {
-            if (lv.planar) {
+            if (h->dom == kDomL) {   // the L: the per-phase kernels (in place), the removed quadrant kept zero
+                launch_uzawa<float>(h->st, lv.n, lv.c, (float)P.tau, (float)P.sigma, xu, xp, lv.f, lv.g, lv.sinv, ou, op,
+                                    32, 8, h->dom);
+            } else if (lv.planar) {
                 if (launch_uzawa_tma(h->st, lv.n, lv.c, (float)P.tau, (float)P.sigma, xu, xp, lv.f, lv.g, lv.sinv, ou,
                                      op))
                     sw = !sw;
@@ -384,7 +387,7 @@ void residual_norm_fin(stokes_handle* h, bool timed = false) {
     if (h->mixed()) {
         // x in float64; r kept as two floats for the refinement updates, r32 = its float32 value
         Level<float>& E = h->h32.back();
-        launch_residual_df(h->st, F.n, F.c, F.u, F.p, F.f, F.g, F.tu, F.tp, E.f, E.g, h->partial, E.planar);
+        launch_residual_df(h->st, F.n, F.c, F.u, F.p, F.f, F.g, F.tu, F.tp, E.f, E.g, h->partial, E.planar, h->dom);
     } else {
         launch_residual<double, double>(h->st, F.n, F.c, F.u, F.p, F.f, F.g, F.tu, F.tp, h->partial, nullptr, nullptr,
                                         h->dom);
@@ -407,11 +410,11 @@ void record_step(stokes_handle* h) {
         // the same pass leaves the partial sums of the zero-mean projection of x_p (second half)
         const int nb = cells_blocks(F.n);
         launch_ir_update_df(h->st, F.n, h->chi, h->clo, E.u, E.p, F.u, F.p, F.tu, F.tp, E.f, E.g, h->partial,
-                            h->partial + nb, E.planar);
+                            h->partial + nb, E.planar, h->dom);
         ev_end(h, k);
         launch_reduce(h->st, h->partial, nb, h->scal);
         launch_reduce(h->st, h->partial + nb, nb, h->scal + 1);
-        launch_psub<double>(h->st, F.n, F.p, h->scal + 1);
+        launch_psub<double>(h->st, F.n, F.p, h->scal + 1, h->dom);
     } else {
         mg_cycle<double>(h, h->h64, h->L - 1);
         launch_pmean<double>(h->st, F.n, F.p, h->partial, h->scal + 1, h->dom);
@@ -534,7 +537,7 @@ stokes_status rebuild_beta(stokes_handle* h) {
             CK(cudaMemcpyAsync(h->dcoef + k, &lv.c, sizeof(OpCoef<float>), cudaMemcpyHostToDevice, h->st));
         // planar levels run only the register-tile step, which needs its coefficient structure
         if (lv.planar && !reg_tables_match(lv.c)) return STOKES_ERR_BAD_ARG;
-        launch_schur_diag<float>(h->st, lv.n, make_coef<double>(lv.n, beta), lv.sinv, kDomSquare,
+        launch_schur_diag<float>(h->st, lv.n, make_coef<double>(lv.n, beta), lv.sinv, h->dom,
                                  lv.planar ? pl_vpitch(lv.n) : 0);
     }
     if (h->mixed()) {
@@ -670,9 +673,9 @@ stokes_status stokes_setup(const stokes_params* prm, void* stream, stokes_handle
         (P.domain != STOKES_UNIT_SQUARE && P.domain != STOKES_L_SHAPE) || (P.tma_level != 0 && P.tma_level < 5) ||
         P.coop_level < -1 || P.coop_level > kSmallCycleTop)
         return STOKES_ERR_BAD_ARG;
-    // the L-shaped domain: float64 Uzawa cycles, coarsest level 1 (the L's level 0)
-    if (P.domain == STOKES_L_SHAPE && (P.precision != STOKES_FP64 || P.smoother != STOKES_UZAWA ||
-                                       P.coarse_level != 1 || P.levels < 2))
+    // the L-shaped domain: Uzawa cycles (float64, or float32 inside float64 refinement), coarsest
+    // level 1 (the L's level 0)
+    if (P.domain == STOKES_L_SHAPE && (P.smoother != STOKES_UZAWA || P.coarse_level != 1 || P.levels < 2))
         return STOKES_ERR_BAD_ARG;
     stokes_status s = ensure_weights();
     if (s != STOKES_OK) return s;
@@ -1153,7 +1156,8 @@ unsigned long long stokes_kernel_launches(const stokes_handle* h) { return h ? h
 // Times the float32 Uzawa step variants on each not-yet-tuned level of h's float32 hierarchy
 // (process-wide choice per level size) and leaves the buffers zero as a fresh handle has them.
 static stokes_status autotune_levels(stokes_handle* h, cudaStream_t st) {
-    if (!h->mixed() || h->prm.smoother != STOKES_UZAWA) return STOKES_OK;
+    // the L's float32 levels run the per-phase step only: nothing to choose
+    if (!h->mixed() || h->prm.smoother != STOKES_UZAWA || h->dom != kDomSquare) return STOKES_OK;
     for (int l = 1; l < (int)h->h32.size(); ++l) {
         Level<float>& lv = h->h32[l];
         if (lv.planar ? tma_tuned(lv.n) : uzawa_tuned(lv.n)) continue;

@@ -270,19 +270,24 @@ __device__ __forceinline__ CellNodes cell_nodes_dom(int i, int j, int n, int dom
     }
     return c;
 }
-// w_i = int_Omega psi_i for the square or the L (squares in the removed quadrant do not count)
-__device__ __forceinline__ double vertex_weight_dom(int i, int j, int n, int dom) {
+// number of triangles at vertex (i, j) on the square or the L (squares of the removed quadrant do
+// not count)
+__device__ __forceinline__ int vertex_triangles_dom(int i, int j, int n, int dom) {
+    if (dom != kDomL) return vertex_triangles(i, j, n);
     int cnt = 0;
 #pragma unroll
     for (int SQ = 0; SQ < 4; ++SQ) {
         const int si = i - (SQ & 1), sj = j - (SQ >> 1);
-        if (si < 0 || sj < 0 || si >= n || sj >= n) continue;
-        if (dom == kDomL && 2 * si >= n && 2 * sj >= n) continue;
+        if (si < 0 || sj < 0 || si >= n || sj >= n || (2 * si >= n && 2 * sj >= n)) continue;
         const int o = orient(si, sj, n), node = corner_node(SQ);
         cnt += ((tri_mask(o, 0) >> node) & 1u) + ((tri_mask(o, 1) >> node) & 1u);
     }
+    return cnt;
+}
+// w_i = int_Omega psi_i for the square or the L
+__device__ __forceinline__ double vertex_weight_dom(int i, int j, int n, int dom) {
     const double h = 1.0 / n;
-    return cnt * h * h / 6.0;
+    return vertex_triangles_dom(i, j, n, dom) * h * h / 6.0;
 }
 
 // Planar float32 layout of the large float32 levels (the velocity arrays of the refinement's inner

@@ -690,10 +690,10 @@ void launch_pmean(cudaStream_t s, int n, T* p, double* partial, double* scalar, 
 }
 
 template <typename T>
-void launch_psub(cudaStream_t s, int n, T* p, const double* scalar) {
-    launch_pdl(k_psub<T>, cells_grid(n), dim3(BX, BY), 0, s, n, p, scalar, (int)kDomSquare);
+void launch_psub(cudaStream_t s, int n, T* p, const double* scalar, int dom) {
+    launch_pdl(k_psub<T>, cells_grid(n), dim3(BX, BY), 0, s, n, p, scalar, dom);
 }
-template void launch_psub<double>(cudaStream_t, int, double*, const double*);
+template void launch_psub<double>(cudaStream_t, int, double*, const double*, int);
 
 // ------------------------------------------------------------------------------------------
 // load vectors (data f, g of Sec. 1 given by nodal values)

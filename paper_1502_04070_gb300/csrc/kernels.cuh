@@ -33,16 +33,20 @@ void launch_uzawa(cudaStream_t s, int n, const OpCoef<T>& c, T tau, T sigma, T* 
 // Refinement update (see refine.cu): float32 correction e, float64 iterate x, residual r stored as
 // (hi, lo) float pairs in the 8-byte slots of a float64 array:
 //   x += e,  r -= A e  (error-free float32 products, ~2^-48 relative),  r32 = float(r),
-//   partial sums of r.r; planar: e and r32 in the planar float32 layout (common.cuh).
+//   partial sums of r.r; planar: e and r32 in the planar float32 layout (common.cuh); dom = kDomL:
+//   the L's unknowns and pressure-mean weights (the nodes outside it keep zero).
 void launch_ir_update_df(cudaStream_t s, int n, const OpCoef<float>& chi, const OpCoef<float>& clo,
                          const float* eu, const float* ep, double* xu, double* xp, double* ru, double* rp,
-                         float* r32u, float* r32p, double* partial, double* wpartial, bool planar = false);
-// p -= *scalar on every vertex (the zero-mean projection once the weighted mean is reduced)
+                         float* r32u, float* r32p, double* partial, double* wpartial, bool planar = false,
+                         int dom = kDomSquare);
+// p -= *scalar on every vertex (the zero-mean projection once the integral of p is reduced); on the
+// L (dom = kDomL) p -= *scalar / (3/4) at the L's vertices
 template <typename T>
-void launch_psub(cudaStream_t s, int n, T* p, const double* scalar);
+void launch_psub(cudaStream_t s, int n, T* p, const double* scalar, int dom = kDomSquare);
 void launch_residual_df(cudaStream_t s, int n, const OpCoef<double>& c, const double* u, const double* p,
                         const double* f, const double* g, double* ru, double* rp, float* r32u, float* r32p,
-                        double* partial, bool planar = false);   // planar: (r32u, r32p) in the planar layout
+                        double* partial, bool planar = false,   // planar: (r32u, r32p) in the planar layout
+                        int dom = kDomSquare);                   // kDomL: the L's unknowns only
 
 // The same Uzawa step fused into one kernel with shared-memory halos: reads (u, p), writes
 // (u_out, p_out) (distinct buffers).

@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(NT, 4) k_ir_update_df(int n, const __grid_cons
                                                      float2* __restrict__ ru, float2* __restrict__ rp,
                                                      float* __restrict__ r32u, float* __restrict__ r32p,
                                                      double* __restrict__ partial, double* __restrict__ wpartial,
-                                                     double wscale) {
+                                                     double wscale, int dom) {
     pdl_wait();
     CELL_INDEX
     const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(NT, 4) k_ir_update_df(int n, const __grid_cons
             visit_df<2, PL>(i, j, n, ch, cl, eu, ep, a);
             visit_df<3, PL>(i, j, n, ch, cl, eu, ep, a);
         }
-        const CellNodes cn = cell_nodes(i, j, n);
+        const CellNodes cn = cell_nodes_dom(i, j, n, dom);
         const int ld = 2 * n + 1;
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
@@ -318,13 +318,15 @@ __global__ void __launch_bounds__(NT, 4) k_ir_update_df(int n, const __grid_cons
             }
         }
         const size_t vi = (size_t)j * (n + 1) + i, vi32 = PL ? (size_t)j * pl_vpitch(n) + i : vi;
-        const double xpn = xp[vi] + (double)ep[vi32];
-        xp[vi] = xpn;
-        wp = (double)vertex_triangles(i, j, n) * xpn;
-        const float2 r = df_sub(rp[vi], a.bu);
-        rp[vi] = r;
-        r32p[vi32] = r.x;
-        ss = fmaf(r.x, r.x, ss);
+        if (!(dom == kDomL && l_masked_vertex(i, j, n))) {   // vertices outside the L keep zero
+            const double xpn = xp[vi] + (double)ep[vi32];
+            xp[vi] = xpn;
+            wp = (double)vertex_triangles_dom(i, j, n, dom) * xpn;
+            const float2 r = df_sub(rp[vi], a.bu);
+            rp[vi] = r;
+            r32p[vi32] = r.x;
+            ss = fmaf(r.x, r.x, ss);
+        }
     }
     const double2 t = block_sum2_fd(ss, wp, tid);
     if (tid == 0) {
@@ -342,7 +344,7 @@ __global__ void __launch_bounds__(NT) k_residual_df(int n, const __grid_constant
                                                     const double* __restrict__ f, const double* __restrict__ g,
                                                     float2* __restrict__ ru, float2* __restrict__ rp,
                                                     float* __restrict__ r32u, float* __restrict__ r32p,
-                                                    double* __restrict__ partial) {
+                                                    double* __restrict__ partial, int dom) {
     pdl_wait();
     CELL_INDEX
     const size_t n2 = (size_t)(2 * n + 1) * (2 * n + 1);
@@ -351,7 +353,7 @@ __global__ void __launch_bounds__(NT) k_residual_df(int n, const __grid_constant
         Acc<double> a;
         cell_apply_auto<true, true, true, false, true>(i, j, n, c, gview(u, 2 * n + 1), gview(u + n2, 2 * n + 1),
                                                   gview(p, n + 1), a);
-        const CellNodes cn = cell_nodes(i, j, n);
+        const CellNodes cn = cell_nodes_dom(i, j, n, dom);
         const int ld = 2 * n + 1;
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
@@ -372,7 +374,7 @@ __global__ void __launch_bounds__(NT) k_residual_df(int n, const __grid_constant
             }
         }
         const size_t vi = (size_t)j * (n + 1) + i;
-        const double r = g[vi] - a.bu;
+        const double r = (dom == kDomL && l_masked_vertex(i, j, n)) ? 0.0 : g[vi] - a.bu;
         const float hi = (float)r;
         rp[vi] = make_float2(hi, (float)(r - (double)hi));
         r32p[PL ? (size_t)j * pl_vpitch(n) + i : vi] = hi;
@@ -385,17 +387,17 @@ __global__ void __launch_bounds__(NT) k_residual_df(int n, const __grid_constant
 
 void launch_ir_update_df(cudaStream_t s, int n, const OpCoef<float>& chi, const OpCoef<float>& clo,
                          const float* eu, const float* ep, double* xu, double* xp, double* ru, double* rp,
-                         float* r32u, float* r32p, double* partial, double* wpartial, bool planar) {
+                         float* r32u, float* r32p, double* partial, double* wpartial, bool planar, int dom) {
     launch_pdl(planar ? k_ir_update_df<true> : k_ir_update_df<false>, cells_grid(n), dim3(BX, BY), 0, s, n, chi, clo,
                make_df_pairs(chi, clo), eu, ep, xu, xp, reinterpret_cast<float2*>(ru), reinterpret_cast<float2*>(rp), r32u,
-               r32p, partial, wpartial, 1.0 / (6.0 * (double)n * (double)n));
+               r32p, partial, wpartial, 1.0 / (6.0 * (double)n * (double)n), dom);
 }
 
 void launch_residual_df(cudaStream_t s, int n, const OpCoef<double>& c, const double* u, const double* p,
                         const double* f, const double* g, double* ru, double* rp, float* r32u, float* r32p,
-                        double* partial, bool planar) {
+                        double* partial, bool planar, int dom) {
     launch_pdl(planar ? k_residual_df<true> : k_residual_df<false>, cells_grid(n), dim3(BX, BY), 0, s, n, c, u, p, f,
-               g, reinterpret_cast<float2*>(ru), reinterpret_cast<float2*>(rp), r32u, r32p, partial);
+               g, reinterpret_cast<float2*>(ru), reinterpret_cast<float2*>(rp), r32u, r32p, partial, dom);
 }
 
 }  // namespace smg

@@ -62,9 +62,8 @@ def test_setup_rejects_bad_arguments_without_touching_the_gpu():
         lib.stokes_default_params(ctypes.byref(prm), 6, 1.0)
         prm.precision, prm.tma_level = _binding.MIXED, t
         assert lib.stokes_setup(ctypes.byref(prm), None, ctypes.byref(h)) == _binding.ERR_BAD_ARG, t
-    # the L-shaped domain needs float64 Uzawa cycles with coarsest level 1
-    for field, value in (("coarse_level", 0), ("precision", _binding.MIXED), ("smoother", _binding.NORMAL_EQ),
-                         ("domain", 2)):
+    # the L-shaped domain needs Uzawa cycles with coarsest level 1
+    for field, value in (("coarse_level", 0), ("coarse_level", 2), ("smoother", _binding.NORMAL_EQ), ("domain", 2)):
         lib.stokes_default_params(ctypes.byref(prm), 5, 1.0)
         prm.domain, prm.coarse_level = _binding.L_SHAPE, 1
         setattr(prm, field, value)

@@ -6,7 +6,9 @@ element, at L-levels j = 1..4 (square levels 2..5, N = 8..64 squares per side):
 * the residual F - S x of eq. gen:bil:mv (1e-12, relative to the largest entry);
 * one Uzawa smoothing step (Sec. 4) with the L's diagonals Ahat, Shat (1e-12);
 * whole V and W cycles with the exact solve on the L's level 0 and the zero-mean pressure over the
-  L (1e-10), and solves against the oracle's sparse direct solution.
+  L (1e-10), and solves against the oracle's sparse direct solution;
+* float32 cycles inside float64 refinement (STOKES_MIXED): the first step against one oracle cycle
+  (1e-5) and solves against the direct solution (1e-8).
 Entries outside the L are zero in every result.
 """
 import numpy as np
@@ -112,4 +114,45 @@ def test_solve_reaches_the_direct_solution(ds, gamma, beta):
     assert rep.converged and abs(rep.cycles - (len(hist) - 1)) <= 1, (rep.cycles, len(hist) - 1)
     assert rel_err(d.to_vec(host(u), host(p)), xd) < 1e-8
     assert abs(d.w @ host(p).ravel()[d.pnodes]) < 1e-12 * np.abs(host(p)).max()
+    S.close()
+
+
+@pytest.mark.parametrize("gamma", [1, 2])
+def test_mixed_first_step_is_one_cycle(ds, gamma):
+    """STOKES_MIXED on the L, j = 3: one refinement step from zero is one float32 cycle of the L
+    (Sec. 3) added to the float64 iterate, then the zero-mean projection over the L: the oracle's
+    float64 cycle to float32 accuracy, zero outside the L."""
+    j, beta = 3, 1e4
+    d = ds[j]
+    H = mg.Hierarchy(j + 1, beta, ds[:j + 1])
+    _, _, f, g, _, F = _masked_state(d, 50 + gamma)
+    x = H.project_mean(j, H.cycle(j, np.zeros(d.ndof), F, mg.Params(gamma=gamma)))
+    S = _solver(j, beta, gamma=gamma, precision="mixed")
+    u, p, rep = S.solve(dev(f), dev(g), tol=1e-30, max_cycles=1)
+    got_u, got_p = host(u), host(p)
+    assert rep.cycles == 1 and not rep.converged
+    assert _outside_is_zero(d, got_u, got_p)
+    assert rel_err(d.to_vec(got_u, got_p), x) < 1e-5
+    S.close()
+
+
+@pytest.mark.parametrize("j", [3, 4])
+@pytest.mark.parametrize("gamma", [1, 2])
+@pytest.mark.parametrize("beta", [0.0, 1e4])
+def test_mixed_solve_reaches_the_direct_solution(ds, j, gamma, beta):
+    """STOKES_MIXED on the L: float32 cycles inside float64 iterative refinement reach the oracle's
+    sparse direct solution to float64 accuracy (1e-11 relative residual), in the oracle's float64
+    cycle count within two, with zero entries outside the L and a zero pressure mean over the L."""
+    d = ds[j]
+    H = mg.Hierarchy(j + 1, beta, ds[:j + 1])
+    _, _, f, g, _, F = _masked_state(d, 60 + j)
+    xo, hist = H.solve(F, mg.Params(gamma=gamma), tol=1e-11, max_cycles=100)
+    xd = H.direct(F)
+    S = _solver(j, beta, gamma=gamma, precision="mixed")
+    u, p, rep = S.solve(dev(f), dev(g), tol=1e-11, max_cycles=100)
+    got_u, got_p = host(u), host(p)
+    assert rep.converged and abs(rep.cycles - (len(hist) - 1)) <= 2, (rep.cycles, len(hist) - 1)
+    assert _outside_is_zero(d, got_u, got_p)
+    assert rel_err(d.to_vec(got_u, got_p), xd) < 1e-8
+    assert abs(d.w @ got_p.ravel()[d.pnodes]) < 1e-12 * np.abs(got_p).max()
     S.close()
