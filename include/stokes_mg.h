@@ -31,7 +31,10 @@
  *
  * ENVIRONMENT: STOKES_MG_PDL=0 (read once per process) launches the cycle's kernels without
  * programmatic dependent launch; by default a kernel's CTAs may be scheduled while the tail of
- * its predecessor runs.  Results do not depend on it.
+ * its predecessor runs.  Results do not depend on it.  STOKES_MG_FUSE_PROLONG=0 (read once per
+ * process) prolongates on the planar float32 levels with a separate kernel; by default the
+ * coarse-grid correction is added to the staged tiles of the first post-smoothing step (results
+ * differ in float32 rounding only).
  */
 #ifndef STOKES_MG_H
 #define STOKES_MG_H
@@ -393,10 +396,14 @@ unsigned long long stokes_batch_kernel_launches(const stokes_batch* b);
 /* Timing of the hot kernels inside the captured cycle: with enable != 0, the cycle graph is
  * rebuilt with CUDA event records (cudaEventRecordExternal) around every finest-level smoothing
  * step and around the float64 finest-level residual, and stokes_solve accumulates their durations
- * (milliseconds, counts) until the next stokes_set_timing call, which also resets the totals. */
+ * (milliseconds, counts) until the next stokes_set_timing call, which also resets the totals.
+ * stokes_get_timing_fused: the finest-level smoothing steps that also add the coarse-grid
+ * correction to their staged tiles (the first post-smoothing step of a planar level, Sec. 3),
+ * which stokes_get_timing's smoothing totals leave out.  Any output pointer may be NULL. */
 stokes_status stokes_set_timing(stokes_handle* h, int enable);
 stokes_status stokes_get_timing(const stokes_handle* h, double* smooth_ms, long long* smooth_count,
                                 double* resid_ms, long long* resid_count);
+stokes_status stokes_get_timing_fused(const stokes_handle* h, double* ms, long long* count);
 
 /* Number of CUDA kernels this handle has launched so far (kernel nodes of replayed graphs
  * included); for accounting in benchmarks. */

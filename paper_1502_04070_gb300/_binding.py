@@ -101,6 +101,7 @@ SIGNATURES = {
     "stokes_set_timing": (_I, [_P, _I]),
     "stokes_get_timing": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D),
                                ctypes.POINTER(ctypes.c_longlong)]),
+    "stokes_get_timing_fused": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong)]),
     "stokes_kernel_launches": (ctypes.c_ulonglong, [_P]),
 }
 

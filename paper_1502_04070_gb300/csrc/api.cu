@@ -185,6 +185,7 @@ struct stokes_handle_t {
     bool launch_failed = false;             // a step variant refused to launch (reported by the next call)
     bool has_planar = false;                // some float32 level is planar
     int small_top = -1;                     // float32 levels clev+1..small_top: one cooperative launch per visit
+    bool fuse_prolong = false;              // planar levels: x += P x_c inside the first post-smoothing step
     OpCoef<float>* dcoef = nullptr;         // device copies of the float32 operators of levels 0..small_top
     unsigned* dbar = nullptr;               // grid-barrier counter of that launch
     cudaGraphExec_t step = nullptr;         // one cycle + projection + residual norm
@@ -210,8 +211,11 @@ struct stokes_handle_t {
     std::vector<cudaEvent_t> ev;            // pairs: [2i] start, [2i+1] end
     int ev_smooth = 0, ev_resid = 0;        // pairs used by one graph launch
     int ev_cursor = 0;                      // pair index while capturing
+    std::vector<unsigned char> ev_kind;     // per pair: kEvSmooth, kEvFused or kEvResid
     double t_smooth = 0.0, t_resid = 0.0;   // accumulated milliseconds
     long long n_smooth = 0, n_resid = 0;    // accumulated launches (groups)
+    double t_fused = 0.0;                   // smoothing steps that also add the coarse-grid correction
+    long long n_fused = 0;
 
     static constexpr int kHistCap = 4096;
     Level<double>& fin() { return h64.back(); }
@@ -220,9 +224,11 @@ struct stokes_handle_t {
 
 namespace {
 
-int ev_begin(stokes_handle* h) {
+enum : unsigned char { kEvSmooth = 0, kEvFused = 1, kEvResid = 2 };
+int ev_begin(stokes_handle* h, unsigned char kind) {
     if (!h->timing || h->ev_cursor * 2 + 1 >= (int)h->ev.size()) return -1;
     const int k = h->ev_cursor++;
+    h->ev_kind[k] = kind;
     cudaEventRecordWithFlags(h->ev[2 * k], h->st, cudaEventRecordExternal);
     return k;
 }
@@ -248,13 +254,15 @@ stokes_status take_launch_failure(stokes_handle* h, stokes_status st = STOKES_OK
 // nu smoothing steps on level lv.  The state is in (u, p) when `sw` is false and in (tu, tp)
 // when true; returns where it is afterwards.  The fused float32 Uzawa kernel writes the other
 // buffer pair (ping-pong); the float64 and normal-equation steps work in place and use the other
-// pair as scratch.
+// pair as scratch.  With `coarse` given (a planar level), the first step adds the coarse-grid
+// correction P x_c of that coarse level to its staged tiles before it smooths.
 template <typename T>
-bool smooth_level(stokes_handle* h, Level<T>& lv, int steps, bool timed, bool sw) {
+bool smooth_level(stokes_handle* h, Level<T>& lv, int steps, bool timed, bool sw, const Level<T>* coarse = nullptr) {
     const stokes_params& P = h->prm;
     const bool f32 = sizeof(T) == 4 && P.smoother == STOKES_UZAWA;
     for (int s = 0; s < steps; ++s) {
-        const int k = timed ? ev_begin(h) : -1;
+        const bool fused = coarse && s == 0 && lv.planar;
+        const int k = timed ? ev_begin(h, fused ? kEvFused : kEvSmooth) : -1;
         if (k >= 0) h->ev_smooth++;
         T* xu = sw ? lv.tu : lv.u;
         T* xp = sw ? lv.tp : lv.p;
@@ -267,8 +275,10 @@ bool smooth_level(stokes_handle* h, Level<T>& lv, int steps, bool timed, bool sw
                 launch_uzawa<float>(h->st, lv.n, lv.c, (float)P.tau, (float)P.sigma, xu, xp, lv.f, lv.g, lv.sinv, ou, op,
                                     32, 8, h->dom);
             } else if (lv.planar) {
+                CoarseCorrection cc;
+                if (coarse && s == 0) cc = CoarseCorrection{coarse->u, coarse->p, coarse->planar};
                 if (launch_uzawa_tma(h->st, lv.n, lv.c, (float)P.tau, (float)P.sigma, xu, xp, lv.f, lv.g, lv.sinv, ou,
-                                     op))
+                                     op, cc))
                     sw = !sw;
                 else
                     h->launch_failed = true;
@@ -348,6 +358,7 @@ void mg_cycle(stokes_handle* h, std::vector<Level<T>>& H, int l) {
     }
     const bool top = l == (int)H.size() - 1;
     bool sw = smooth_level(h, lv, h->prm.nu_pre, top, false);
+    const Level<T>* fused_coarse = nullptr;   // the coarse-grid correction goes into the first post-smoothing step
     T* xu = sw ? lv.tu : lv.u;
     T* xp = sw ? lv.tp : lv.p;
     T* ru = sw ? lv.u : lv.tu;
@@ -361,7 +372,8 @@ void mg_cycle(stokes_handle* h, std::vector<Level<T>>& H, int l) {
                 launch_restrict_planar(h->st, cl.n, cl.planar, ru, rp, cl.f, cl.g, cl.u, cl.p);
             }
             for (int r = 0; r < h->prm.gamma; ++r) mg_cycle(h, H, l - 1);
-            launch_prolong_add_planar(h->st, cl.n, cl.planar, cl.u, cl.p, xu, xp);
+            if (h->fuse_prolong && h->prm.nu_post > 0) fused_coarse = &cl;
+            else launch_prolong_add_planar(h->st, cl.n, cl.planar, cl.u, cl.p, xu, xp);
         }
     }
     if (!lv.planar) {
@@ -370,7 +382,7 @@ void mg_cycle(stokes_handle* h, std::vector<Level<T>>& H, int l) {
         for (int r = 0; r < h->prm.gamma; ++r) mg_cycle(h, H, l - 1);
         launch_prolong_add<T>(h->st, cl.n, cl.u, cl.p, xu, xp, h->dom);
     }
-    sw = smooth_level(h, lv, h->prm.nu_post, top, sw);
+    sw = smooth_level(h, lv, h->prm.nu_post, top, sw, fused_coarse);
     if (sw) {   // odd number of ping-pong steps: bring the iterate back to (u, p)
         cudaMemcpyAsync(lv.u, lv.tu, 2 * lv.n2 * sizeof(T), cudaMemcpyDeviceToDevice, h->st);
         cudaMemcpyAsync(lv.p, lv.tp, lv.n1 * sizeof(T), cudaMemcpyDeviceToDevice, h->st);
@@ -382,7 +394,7 @@ void mg_cycle(stokes_handle* h, std::vector<Level<T>>& H, int l) {
 // the right-hand side of the next correction problem.
 void residual_norm_fin(stokes_handle* h, bool timed = false) {
     Level<double>& F = h->fin();
-    const int k = timed ? ev_begin(h) : -1;
+    const int k = timed ? ev_begin(h, kEvResid) : -1;
     if (k >= 0) h->ev_resid++;
     if (h->mixed()) {
         // x in float64; r kept as two floats for the refinement updates, r32 = its float32 value
@@ -405,7 +417,7 @@ void record_step(stokes_handle* h) {
         cudaMemsetAsync(E.p, 0, E.n1 * sizeof(float), h->st);
         for (int c = 0; c < h->prm.inner_cycles; ++c) mg_cycle<float>(h, h->h32, h->L - 1);
         // x += e, r -= A e (two-float residual, error-free float32 products), r32 = float(r)
-        const int k = ev_begin(h);
+        const int k = ev_begin(h, kEvResid);
         if (k >= 0) h->ev_resid++;
         // the same pass leaves the partial sums of the zero-mean projection of x_p (second half)
         const int nb = cells_blocks(F.n);
@@ -506,17 +518,18 @@ stokes_status launch_step(stokes_handle* h) {
 // after the stream is synchronised: add the event intervals of the last graph launch
 void collect_timing(stokes_handle* h) {
     if (!h->timing) return;
-    int k = 0;
-    for (int i = 0; i < h->ev_smooth + h->ev_resid; ++i, ++k) {
+    for (int k = 0; k < h->ev_smooth + h->ev_resid; ++k) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, h->ev[2 * k], h->ev[2 * k + 1]) != cudaSuccess) {
             cudaGetLastError();
             continue;
         }
-        // capture order: smoothing steps of the cycle first, the residual last
-        if (i < h->ev_smooth) {
+        if (h->ev_kind[k] == kEvSmooth) {
             h->t_smooth += ms;
             h->n_smooth++;
+        } else if (h->ev_kind[k] == kEvFused) {
+            h->t_fused += ms;
+            h->n_fused++;
         } else {
             h->t_resid += ms;
             h->n_resid++;
@@ -716,6 +729,7 @@ stokes_status stokes_setup(const stokes_params* prm, void* stream, stokes_handle
         for (int k = 0; k < P.levels; ++k)
             if ((s = alloc_level(h->h32[k], k, h->mem, tma && k >= tlev)) != STOKES_OK) return bail(s);
         h->has_planar = tma && tlev < P.levels;
+        h->fuse_prolong = h->has_planar && fuse_prolong_enabled() && uzawa_tma_embed_available();
         // the cooperative small-level cycle: compact float32 levels up to coop_level, above the coarsest
         if (P.coop_level > 0 && P.smoother == STOKES_UZAWA && P.domain == STOKES_UNIT_SQUARE) {
             int top = P.coop_level;
@@ -1127,6 +1141,7 @@ stokes_status stokes_set_timing(stokes_handle* h, int enable) {
     if (on && h->ev.empty()) {
         const int pairs = (h->prm.nu_pre + h->prm.nu_post) * (h->mixed() ? h->prm.inner_cycles : 1) + 1;
         h->ev.resize(2 * pairs);
+        h->ev_kind.assign(pairs, kEvSmooth);
         for (auto& e : h->ev) CK(cudaEventCreate(&e));
     }
     if (on != h->timing && h->step) {
@@ -1134,8 +1149,8 @@ stokes_status stokes_set_timing(stokes_handle* h, int enable) {
         h->step = nullptr;
     }
     h->timing = on;
-    h->t_smooth = h->t_resid = 0.0;
-    h->n_smooth = h->n_resid = 0;
+    h->t_smooth = h->t_resid = h->t_fused = 0.0;
+    h->n_smooth = h->n_resid = h->n_fused = 0;
     return STOKES_OK;
 }
 
@@ -1146,6 +1161,13 @@ stokes_status stokes_get_timing(const stokes_handle* h, double* smooth_ms, long 
     if (smooth_count) *smooth_count = h->n_smooth;
     if (resid_ms) *resid_ms = h->t_resid;
     if (resid_count) *resid_count = h->n_resid;
+    return STOKES_OK;
+}
+
+stokes_status stokes_get_timing_fused(const stokes_handle* h, double* ms, long long* count) {
+    if (!h) return STOKES_ERR_BAD_ARG;
+    if (ms) *ms = h->t_fused;
+    if (count) *count = h->n_fused;
     return STOKES_OK;
 }
 

@@ -24,6 +24,14 @@ bool pdl_enabled() {
     return on;
 }
 
+bool fuse_prolong_enabled() {
+    static const bool on = [] {
+        const char* e = std::getenv("STOKES_MG_FUSE_PROLONG");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
+
 __constant__ double c_W2d[2][9][5][5];
 __constant__ float c_W2f[2][9][5][5];
 

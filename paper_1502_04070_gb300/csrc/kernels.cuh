@@ -73,9 +73,24 @@ cudaError_t prepare_uzawa_reg();
 // there.  uzawa_tma_timeouts: nonzero if a CTA of the kernel gave up waiting (about a second) for
 // its tiles since the last call; clears the flag (synchronises with the device).
 constexpr int kDefaultTmaLevel = 6;   // lowest level held planar unless stokes_params.tma_level says otherwise
+// With u given, the step starts from x + P x_c, x_c = (u, p) the iterate of the coarse level N / 2
+// (planar or compact): the coarse-grid correction of Sec. 3 added to the staged tiles in shared
+// memory (the separate prolongation kernel and its pass over the fine state are saved).
+struct CoarseCorrection {
+    const float* u = nullptr;
+    const float* p = nullptr;
+    bool planar = false;
+};
 bool launch_uzawa_tma(cudaStream_t s, int n, const OpCoef<float>& c, float tau, float sigma, const float* u,
-                      const float* p, const float* f, const float* g, const float* sinv, float* u_out, float* p_out);
+                      const float* p, const float* f, const float* g, const float* sinv, float* u_out, float* p_out,
+                      const CoarseCorrection& cc = CoarseCorrection{});
 bool uzawa_tma_available();
+// the fused correction can be used: the tensor-map encoder is there and the kernel's compile-time
+// embedding table equals the host element code's transfer weights
+bool uzawa_tma_embed_available();
+// false when the environment sets STOKES_MG_FUSE_PROLONG=0 (read once per process): the planar
+// levels then prolongate with the separate kernel
+bool fuse_prolong_enabled();
 // Variants of the planar step, one tile per CTA of 8 warps: 0 tile height for 3 CTAs per SM (80
 // registers), 2 for 4 CTAs per SM (64 registers); 1, 3 the same, each CTA also prefetching into L2
 // the tiles of the tile one wave of resident CTAs ahead; 4, 5 two rows per warp pass (the shared
@@ -85,7 +100,7 @@ bool uzawa_tma_available();
 constexpr int kTmaVariants = 6;
 bool launch_uzawa_tma_variant(int variant, cudaStream_t s, int n, const OpCoef<float>& c, float tau, float sigma,
                               const float* u, const float* p, const float* f, const float* g, const float* sinv,
-                              float* u_out, float* p_out);
+                              float* u_out, float* p_out, const CoarseCorrection& cc = CoarseCorrection{});
 // r = F - A x on a planar level (N = n) and its restriction (fc, gc) = I^T r to the coarse level
 // (planar or not: pc_planar), with the coarse iterate (uc, pc) set to zero, in one kernel on the
 // tiles of the planar step; the fine defect stays in shared memory.  False (nothing launched) as

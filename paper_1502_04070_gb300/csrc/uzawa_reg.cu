@@ -917,13 +917,233 @@ __device__ __forceinline__ void tma_prefetch_tile(int TY, int i0, int j0, const 
     tma_prefetch_2d(&maps.s, i0 - G::DX, j0 - 1);
 }
 
+// ---- the coarse-grid correction x += P x_c (Sec. 3, the canonical embedding) on the staged u and
+// p tiles of the first post-smoothing step: every fine lattice point of the u tile and every fine
+// vertex of the p tile gets the coarse P2 / P1 function of the coarse square that owns it, added in
+// shared memory, so the corrected state is never written to global memory and read back.
+
+// the two triangles of a coarse square of orientation o (the split of tri_mask), vertices in coarse
+// lattice units (0 or 2)
+struct EmbedTri {
+    int x[3], y[3];
+};
+__host__ __device__ constexpr EmbedTri embed_tri(int o, int t) {
+    return o == 0 ? (t == 0 ? EmbedTri{{0, 2, 2}, {0, 0, 2}} : EmbedTri{{0, 2, 0}, {0, 2, 2}})
+                  : (t == 0 ? EmbedTri{{0, 2, 0}, {0, 0, 2}} : EmbedTri{{2, 2, 0}, {0, 2, 2}});
+}
+// Value at the fine lattice point (fa / 2, fb / 2), fa, fb in [0, 4), of the coarse P2 basis
+// function of local node L (lattice offset (L % 3, L / 3)): in the triangle that holds the point,
+// with barycentric coordinates l, l_i (2 l_i - 1) at vertex i and 4 l_j l_k at the midpoint of the
+// edge (j, k); zero where L is no node of that triangle.  Evaluated at compile time.
+__host__ __device__ constexpr double embed_weight(int o, int L, int fa, int fb) {
+    const double px = 0.5 * fa, py = 0.5 * fb;
+    const int lx = L % 3, ly = L / 3;
+    for (int t = 0; t < 2; ++t) {
+        const EmbedTri T = embed_tri(o, t);
+        const double twoA = (T.x[1] - T.x[0]) * (T.y[2] - T.y[0]) - (T.x[2] - T.x[0]) * (T.y[1] - T.y[0]);
+        double l[3] = {0.0, 0.0, 0.0};
+        bool inside = true;
+        for (int i = 0; i < 3; ++i) {
+            const int j = (i + 1) % 3, k = (i + 2) % 3;
+            l[i] = ((T.x[j] - px) * (T.y[k] - py) - (T.x[k] - px) * (T.y[j] - py)) / twoA;
+            if (l[i] < 0.0) inside = false;
+        }
+        if (!inside) continue;
+        for (int i = 0; i < 3; ++i)
+            if (T.x[i] == lx && T.y[i] == ly) return l[i] * (2.0 * l[i] - 1.0);
+        for (int i = 0; i < 3; ++i) {
+            const int j = (i + 1) % 3, k = (i + 2) % 3;
+            if (T.x[j] + T.x[k] == 2 * lx && T.y[j] + T.y[k] == 2 * ly) return 4.0 * l[j] * l[k];
+        }
+        return 0.0;
+    }
+    return 0.0;
+}
+__host__ __device__ constexpr bool embed_partition_of_unity() {
+    for (int o = 0; o < 2; ++o)
+        for (int f = 0; f < 16; ++f) {
+            double s = 0.0;
+            for (int L = 0; L < 9; ++L) s += embed_weight(o, L, f % 4, f / 4);
+            if (s != 1.0) return false;
+        }
+    return true;
+}
+static_assert(embed_partition_of_unity(), "the coarse basis functions sum to one at every fine point");
+static_assert(embed_weight(0, 0, 1, 0) == 0.375 && embed_weight(0, 1, 1, 0) == 0.75 && embed_weight(0, 2, 1, 0) == -0.125,
+              "on a coarse edge the embedding is the quadratic through its three nodes");
+static_assert(embed_weight(1, 4, 2, 2) == 1.0 && embed_weight(0, 3, 2, 2) == 0.0, "a coarse node keeps its value");
+
+template <int O, int FA, int FB, int L>
+__device__ __forceinline__ void embed_term(const float2 (&z)[9], float2& acc) {
+    constexpr float w = (float)embed_weight(O, L, FA, FB);
+    if constexpr (w == 1.0f) acc = f2(acc.x + z[L].x, acc.y + z[L].y);
+    else if constexpr (w != 0.0f) acc = __ffma2_rn(f2(w, w), z[L], acc);
+}
+// fine point P = FB * 4 + FA of a coarse square added to its u-tile entry (plane FA & 1, row FB,
+// pair FA / 2 from the square's corner at offset `base` of plane 0) if bit P of `mask` is set
+template <class G, int O, int P, int... L>
+__device__ __forceinline__ void embed_point(const float2 (&z)[9], float2* sU, int base, int UPL, unsigned mask,
+                                            std::integer_sequence<int, L...>) {
+    constexpr int FA = P % 4, FB = P / 4;
+    if (!((mask >> P) & 1u)) return;
+    float2* d = sU + base + (FA & 1) * UPL + FB * G::UWH + (FA >> 1);
+    float2 acc = *d;
+    (embed_term<O, FA, FB, L>(z, acc), ...);
+    *d = acc;
+}
+template <class G, int O, int... P>
+__device__ __forceinline__ void embed_square(const float2 (&z)[9], float2* sU, int base, int UPL, unsigned mask,
+                                             std::integer_sequence<int, P...>) {
+    (embed_point<G, O, P>(z, sU, base, UPL, mask, std::make_integer_sequence<int, 9>{}), ...);
+}
+// the same for a square whose 16 points all lie in the tile and inside the level: the 16 tile
+// entries are read first, corrected, then written (no per-point tests); b0, b1 = the square's
+// corner in the two column-parity planes
+template <class G, int P>
+__device__ __forceinline__ float2* embed_at(float2* b0, float2* b1) {
+    return ((P % 4) & 1 ? b1 : b0) + (P / 4) * G::UWH + ((P % 4) >> 1);
+}
+template <int O, int P, int... L>
+__device__ __forceinline__ void embed_fma(const float2 (&z)[9], float2& v, std::integer_sequence<int, L...>) {
+    (embed_term<O, P % 4, P / 4, L>(z, v), ...);
+}
+template <class G, int O, int P0, int... P>
+__device__ __forceinline__ void embed_chunk(const float2 (&z)[9], float2* b0, float2* b1, std::integer_sequence<int, P...>) {
+    float2 v[sizeof...(P)];
+    ((v[P] = *embed_at<G, P0 + P>(b0, b1)), ...);
+    (embed_fma<O, P0 + P>(z, v[P], std::make_integer_sequence<int, 9>{}), ...);
+    ((*embed_at<G, P0 + P>(b0, b1) = v[P]), ...);
+}
+// CH points at a time (16, or 8 where registers are scarce)
+template <class G, int O, int CH>
+__device__ __forceinline__ void embed_square_full(const float2 (&z)[9], float2* b0, float2* b1) {
+    static_assert(CH == 8 || CH == 16, "whole rows of points");
+    embed_chunk<G, O, 0>(z, b0, b1, std::make_integer_sequence<int, CH>{});
+    if constexpr (CH == 8) embed_chunk<G, O, 8>(z, b0, b1, std::make_integer_sequence<int, 8>{});
+}
+
+// One coarse square's share of the correction: its nine P2 values and the P1 values at its four
+// corners (those of the level), loaded before the tiles arrive.
+struct EmbedJob {
+    float2 z[9];
+    float p00, p10, p01, p11;
+    int I, J;   // I < 0: no work
+};
+
+// The coarse squares [i0 / 2 - 2, i0 / 2 + 16) x [J0, J1] of the CTA at (i0, j0) own every fine
+// lattice point of its u tile (pairs from cell i0 - UX, rows from 2 (j0 - 3)) and every fine vertex of
+// its p tile (from (i0 - PX, j0 - 3)); job t is square (I0 + t % 18, J0 + t / 18).
+template <class G>
+struct EmbedGrid {
+    static constexpr int NI = G::UWH / 2;
+    static_assert(G::UX == 4 && G::PX == 4 && G::UWH % 2 == 0 && G::PW == G::UWH, "tile origin at an even cell");
+    int I0, J0, count;
+    __device__ __forceinline__ EmbedGrid(int TY, int i0, int j0) {
+        I0 = (i0 >> 1) - 2;                   // i0 is even
+        J0 = (2 * j0 + 2) / 4 - 2;            // floor((2 j0 - 6) / 4) for j0 >= 0
+        count = NI * ((2 * j0 + 2 * TY + 5) / 4 - J0 + 1);
+    }
+};
+
+// Tile height of the launches that add the correction: at most 18 x 14 coarse squares, so that each
+// of the 256 threads has one square at most (a second square for a few threads left the other
+// warps waiting on them).
+constexpr int kEmbedMaxRows = 20;
+constexpr int embed_max_squares(int ty) {   // over tile origins j0 of either parity
+    const int even = (2 * ty + 5) / 4 + 3, odd = (2 * ty + 7) / 4 + 2;
+    return EmbedGrid<TmaTile>::NI * (even > odd ? even : odd);
+}
+static_assert(embed_max_squares(kEmbedMaxRows) <= 256, "one coarse square per thread");
+
+// coarse iterate (uc, pc) of level nc, planar when pcp
+__device__ __forceinline__ void embed_load(EmbedJob& jb, int t, const EmbedGrid<TmaTile>& eg, int nc,
+                                           const float* __restrict__ uc, const float* __restrict__ pc, bool pcp) {
+    constexpr int NI = EmbedGrid<TmaTile>::NI;
+    const int I = eg.I0 + t % NI, J = eg.J0 + t / NI;
+    jb.I = -1;
+    if (t >= eg.count || I < 0 || J < 0 || I > nc || J > nc) return;
+    jb.I = I;
+    jb.J = J;
+    const int ldc = 2 * nc + 1, vld = pcp ? pl_vpitch(nc) : nc + 1;
+    if (I < nc && J < nc) {
+        if (pcp) {   // pair I (+1) of rows 2J .. 2J + 2 of the two column-parity planes
+            const float2* r0 = reinterpret_cast<const float2*>(uc + pl_u(nc, 2 * I, 2 * J));
+            const int rp = pl_pitch(nc), pp = pl_rows(nc) * pl_pitch(nc);
+#pragma unroll
+            for (int m = 0; m < 9; ++m) jb.z[m] = __ldg(r0 + (m % 3 & 1) * pp + (m / 3) * rp + (m % 3 >> 1));
+        } else {
+            const float* r0 = uc + (2 * J) * ldc + 2 * I;
+#pragma unroll
+            for (int m = 0; m < 9; ++m) {
+                const int k = (m / 3) * ldc + m % 3;
+                jb.z[m] = f2(__ldg(r0 + k), __ldg(r0 + ldc * ldc + k));
+            }
+        }
+    }
+    jb.p00 = __ldg(pc + J * vld + I);
+    jb.p10 = I < nc ? __ldg(pc + J * vld + I + 1) : 0.f;
+    jb.p01 = J < nc ? __ldg(pc + (J + 1) * vld + I) : 0.f;
+    jb.p11 = I < nc && J < nc ? __ldg(pc + (J + 1) * vld + I + 1) : 0.f;
+}
+
+// the job's fine points added to the tiles: the lattice points strictly inside the level and the
+// tile's rows, and the vertices of the level inside the p tile
+template <class G, int CH>
+__device__ __forceinline__ void embed_apply(const EmbedJob& jb, int n, int TY, int i0, int j0, float2* sU, float* sP) {
+    if (jb.I < 0) return;
+    const int nc = n >> 1, I = jb.I, J = jb.J, UPL = G::upl(TY);
+    const int pxlo = i0 - G::PX, pylo = j0 - 3;
+    // rows [2J, 2J + 2) of vertices (and so [4J, 4J + 4) of lattice points) inside the tiles, and the
+    // square strictly inside the level: every point of it is corrected
+    if (I > 0 && J > 0 && I < nc && J < nc && 2 * J >= pylo && 2 * J + 2 <= pylo + TY + 6) {
+        const int base = (4 * J - 2 * pylo) * G::UWH + ((4 * I - 2 * (i0 - G::UX)) >> 1);
+        const int o = orient(I, J, nc);
+        if (o == 0) embed_square_full<G, 0, CH>(jb.z, sU + base, sU + base + UPL);
+        else embed_square_full<G, 1, CH>(jb.z, sU + base, sU + base + UPL);
+        float* q = sP + (2 * J - pylo) * G::PW + (2 * I - pxlo);
+        q[0] += jb.p00;
+        q[1] += 0.5f * (jb.p00 + jb.p10);
+        q[G::PW] += 0.5f * (jb.p00 + jb.p01);
+        q[G::PW + 1] += 0.5f * (o == 0 ? jb.p00 + jb.p11 : jb.p10 + jb.p01);
+        return;
+    }
+    if (I < nc && J < nc) {
+        const int xlo = 2 * (i0 - G::UX), ylo = 2 * (j0 - 3), yhi = ylo + 2 * (TY + 6);
+        unsigned cols = 0u, mask = 0u;
+#pragma unroll
+        for (int fa = 0; fa < 4; ++fa) {   // the tile holds every column of its squares
+            const int X = 4 * I + fa;
+            if (X > 0 && X < 2 * n) cols |= 1u << fa;
+        }
+#pragma unroll
+        for (int fb = 0; fb < 4; ++fb) {
+            const int Y = 4 * J + fb;
+            if (Y >= ylo && Y < yhi && Y > 0 && Y < 2 * n) mask |= cols << (4 * fb);
+        }
+        const int base = (4 * J - ylo) * G::UWH + ((4 * I - xlo) >> 1);
+        constexpr auto P16 = std::make_integer_sequence<int, 16>{};
+        if (orient(I, J, nc) == 0) embed_square<G, 0>(jb.z, sU, base, UPL, mask, P16);
+        else embed_square<G, 1>(jb.z, sU, base, UPL, mask, P16);
+    }
+    // P1: injection at the coarse vertex, averages halfway along the coarse edges from it
+    auto addp = [&](int x, int y, float v) {
+        if (x < pxlo || x >= pxlo + G::PW || y < pylo || y >= pylo + TY + 6 || x > n || y > n) return;
+        sP[(y - pylo) * G::PW + (x - pxlo)] += v;
+    };
+    addp(2 * I, 2 * J, jb.p00);
+    if (I < nc) addp(2 * I + 1, 2 * J, 0.5f * (jb.p00 + jb.p10));
+    if (J < nc) addp(2 * I, 2 * J + 1, 0.5f * (jb.p00 + jb.p01));
+    if (I < nc && J < nc)
+        addp(2 * I + 1, 2 * J + 1, 0.5f * (orient(I, J, nc) == 0 ? jb.p00 + jb.p11 : jb.p10 + jb.p01));
+}
+
 // pf > 0: also prefetch into L2 the tiles of tile blockIdx.x + pf (about one wave of resident CTAs
 // ahead), so that the CTA that takes it finds its tiles in L2
 template <int NW, int MINB, bool PAIR = false>
 __global__ void __launch_bounds__(32 * NW, MINB)
     k_uzawa_tma(int n, int TY, TileOrder ord, const __grid_constant__ OpCoef<float> c, const __grid_constant__ RegCoef q,
                 float tau, float sigma, const __grid_constant__ TmaMaps maps, float* __restrict__ u_out,
-                float* __restrict__ p_out, int pf) {
+                float* __restrict__ p_out, int pf, const float* __restrict__ uc, const float* __restrict__ pc, int pcp) {
     using G = TmaTile;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
@@ -958,6 +1178,11 @@ __global__ void __launch_bounds__(32 * NW, MINB)
             tma_prefetch_tile(TY, ac * G::TX, ar * TY, maps);
         }
     }
+    // uc, pc given: the step starts from x + P x_c; each thread loads the coarse values of its
+    // square while the tiles are in flight
+    const EmbedGrid<G> eg(TY, i0, j0);
+    EmbedJob jb;
+    if (uc) embed_load(jb, threadIdx.x, eg, n >> 1, uc, pc, pcp != 0);
     const bool ok = mbar_wait_bounded(bar, 0);
     if (__syncthreads_or(!ok)) {
         if (threadIdx.x == 0) {
@@ -965,6 +1190,15 @@ __global__ void __launch_bounds__(32 * NW, MINB)
             mbar_wait_bounded(bar, 0);   // once more, for copies still in flight into this CTA's memory
         }
         return;
+    }
+    if (uc) {
+        constexpr int CH = MINB >= 4 ? 8 : 16;   // points corrected at a time (registers)
+        embed_apply<G, CH>(jb, n, TY, i0, j0, sU, sP);
+        for (int t = threadIdx.x + 32 * NW; t < eg.count; t += 32 * NW) {   // tiles above kEmbedMaxRows only
+            embed_load(jb, t, eg, n >> 1, uc, pc, pcp != 0);
+            embed_apply<G, CH>(jb, n, TY, i0, j0, sU, sP);
+        }
+        __syncthreads();
     }
     reg_phases<G, true, NW, PAIR>(n, TY, i0, j0, c, q, tau, sigma, sU, sF, sP, sG, sS, u_out, p_out);
     pdl_trigger();
@@ -1680,10 +1914,12 @@ bool make_tma_maps(int n, int ty, const float* u, const float* p, const float* f
 
 template <int NW, int MINB, bool PAIR = false>
 bool launch_tma_v(cudaStream_t s, int n, const OpCoef<float>& c, float tau, float sigma, const float* u, const float* p,
-                  const float* f, const float* g, const float* sinv, float* u_out, float* p_out, bool prefetch) {
+                  const float* f, const float* g, const float* sinv, float* u_out, float* p_out, bool prefetch,
+                  const CoarseCorrection& cc) {
     RegCoef q;
     if (!make_reg_coef(c, tau, q)) return false;
-    const int ty = tma_rows<NW, MINB, PAIR>(n);
+    int ty = tma_rows<NW, MINB, PAIR>(n);
+    if (cc.u) ty = std::min(ty, kEmbedMaxRows);
     TmaMaps m;
     if (!make_tma_maps(n, ty, u, p, f, g, sinv, m)) return false;
     const TileOrder ord = tile_order<TmaTile>(n, ty);
@@ -1699,8 +1935,22 @@ bool launch_tma_v(cudaStream_t s, int n, const OpCoef<float>& c, float tau, floa
         pf = std::max(1, sms) * std::max(1, per_sm);
     }
     launch_pdl(k_uzawa_tma<NW, MINB, PAIR>, dim3(ord.cols * ord.rows), dim3(32 * NW), TmaTile::bytes(ty), s, n, ty, ord, c,
-               q, tau, sigma, m, u_out, p_out, pf);
+               q, tau, sigma, m, u_out, p_out, pf, cc.u, cc.p, cc.planar ? 1 : 0);
     return true;
+}
+
+// the compile-time embedding table equals the host element code's transfer weights
+bool embed_table_matches() {
+    static const bool ok = [] {
+        const TransferWeights t = transfer_weights();
+        for (int o = 0; o < 2; ++o)
+            for (int L = 0; L < 9; ++L)
+                for (int fb = 0; fb < 4; ++fb)
+                    for (int fa = 0; fa < 4; ++fa)
+                        if (std::fabs(t.P2[o][L][fb][fa] - embed_weight(o, L, fa, fb)) > 1e-14) return false;
+        return true;
+    }();
+    return ok;
 }
 
 const RestrictWeights& restrict_weights() {
@@ -1813,21 +2063,25 @@ int lvl(int n) { return (31 - __builtin_clz((unsigned)n)) & 31; }
 
 bool launch_uzawa_tma_variant(int variant, cudaStream_t s, int n, const OpCoef<float>& c, float tau, float sigma,
                               const float* u, const float* p, const float* f, const float* g, const float* sinv,
-                              float* u_out, float* p_out) {
+                              float* u_out, float* p_out, const CoarseCorrection& cc) {
+    if (cc.u && (!cc.p || !embed_table_matches())) return false;
     switch (variant) {
-        case 1: return launch_tma_v<8, 3>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out, true);
-        case 2: return launch_tma_v<8, 4>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out, false);
-        case 3: return launch_tma_v<8, 4>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out, true);
-        case 4: return launch_tma_v<8, 2, true>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out, true);
-        case 5: return launch_tma_v<8, 3, true>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out, true);
-        default: return launch_tma_v<8, 3>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out, false);
+        case 1: return launch_tma_v<8, 3>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out, true, cc);
+        case 2: return launch_tma_v<8, 4>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out, false, cc);
+        case 3: return launch_tma_v<8, 4>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out, true, cc);
+        case 4: return launch_tma_v<8, 2, true>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out, true, cc);
+        case 5: return launch_tma_v<8, 3, true>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out, true, cc);
+        default: return launch_tma_v<8, 3>(s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out, false, cc);
     }
 }
 
 bool launch_uzawa_tma(cudaStream_t s, int n, const OpCoef<float>& c, float tau, float sigma, const float* u,
-                      const float* p, const float* f, const float* g, const float* sinv, float* u_out, float* p_out) {
-    return launch_uzawa_tma_variant(g_tma_choice[lvl(n)], s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out);
+                      const float* p, const float* f, const float* g, const float* sinv, float* u_out, float* p_out,
+                      const CoarseCorrection& cc) {
+    return launch_uzawa_tma_variant(g_tma_choice[lvl(n)], s, n, c, tau, sigma, u, p, f, g, sinv, u_out, p_out, cc);
 }
+
+bool uzawa_tma_embed_available() { return uzawa_tma_available() && embed_table_matches(); }
 
 int tma_choice(int n) { return g_tma_choice[lvl(n)]; }
 bool tma_tuned(int n) { return g_tma_tuned[lvl(n)]; }

@@ -220,6 +220,14 @@ class Solver:
                                             ctypes.byref(rc)), "stokes_get_timing")
         return sm.value, sc.value, rm.value, rc.value
 
+    def timing_fused(self):
+        """(ms total, steps) of the finest-level smoothing steps that also add the coarse-grid
+        correction (the first post-smoothing step of a planar level) since set_timing."""
+        ms, cnt = ctypes.c_double(), ctypes.c_longlong()
+        B.check(self._lib.stokes_get_timing_fused(self._h, ctypes.byref(ms), ctypes.byref(cnt)),
+                "stokes_get_timing_fused")
+        return ms.value, cnt.value
+
     def kernel_launches(self):
         return int(self._lib.stokes_kernel_launches(self._h))
 

@@ -152,6 +152,7 @@ def test_every_entry_point_rejects_bad_arguments_before_device_work():
         "stokes_mass_dot": (None, buf, buf, ctypes.byref(d)),
         "stokes_set_timing": (None, 1),
         "stokes_get_timing": (None, None, None, None, None),
+        "stokes_get_timing_fused": (None, None, None),
         "stokes_residual_norm2_noalloc": (0, 1.0, buf, buf, buf, buf, ctypes.byref(d), None),
         "stokes_batch_solve": (None, None, None, None, None, 1e-8, 10, None, None),
         "stokes_transfer_weights": (None,),

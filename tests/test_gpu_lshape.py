@@ -1,7 +1,7 @@
 """The L-shaped domain on the CUDA path (stokes_params.domain = STOKES_L_SHAPE: the square's lattice
 with the closed upper-right quadrant masked; Sec. 1: the method applies to non-convex domains)
 against the oracle's L (oracle/lshape.py: the kept triangles assembled on their own), element by
-element, at L-levels j = 1..4 (square levels 2..5, N = 8..64 squares per side):
+element, at L-levels j = 1..5 (square levels 2..6, N = 8..128 squares per side):
 
 * the residual F - S x of eq. gen:bil:mv (1e-12, relative to the largest entry);
 * one Uzawa smoothing step (Sec. 4) with the L's diagonals Ahat, Shat (1e-12);
@@ -20,7 +20,7 @@ from tests._gpu import dev, host, rel_err
 
 pytestmark = pytest.mark.gpu
 
-JMAX = 4
+JMAX = 5
 
 
 @pytest.fixture(scope="module")
@@ -49,7 +49,7 @@ def _outside_is_zero(d, u, p):
     return np.abs(u - xi[0]).max() == 0.0 and np.abs(p - xi[1]).max() == 0.0
 
 
-@pytest.mark.parametrize("j", [1, 2, 3, 4])
+@pytest.mark.parametrize("j", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("beta", [0.0, 1e4])
 def test_residual(ds, j, beta):
     d = ds[j]
@@ -63,7 +63,7 @@ def test_residual(ds, j, beta):
     S.close()
 
 
-@pytest.mark.parametrize("j", [1, 3])
+@pytest.mark.parametrize("j", [1, 3, 5])
 @pytest.mark.parametrize("beta", [1.0, 1e6])
 def test_uzawa_step(ds, j, beta):
     d = ds[j]
@@ -79,7 +79,7 @@ def test_uzawa_step(ds, j, beta):
     S.close()
 
 
-@pytest.mark.parametrize("j", [1, 2, 4])
+@pytest.mark.parametrize("j", [1, 2, 4, 5])
 @pytest.mark.parametrize("gamma", [1, 2])
 @pytest.mark.parametrize("beta", [1.0, 1e6])
 def test_cycle(ds, j, gamma, beta):

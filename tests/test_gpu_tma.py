@@ -116,6 +116,39 @@ def test_planar_mixed_solve_by_oracle(discs, gamma, coarse_level, variant):
     S.close()
 
 
+@pytest.mark.parametrize("k,gamma,coarse_level,nu,variant", [(6, 1, 0, (3, 3), 0), (6, 2, 3, (3, 3), 5),
+                                                          (6, 2, 0, (2, 1), 1), (5, 1, 3, (3, 3), 4),
+                                                          (6, 1, 3, (3, 0), 2)])
+def test_planar_first_refinement_step_is_one_cycle(discs, k, gamma, coarse_level, nu, variant):
+    """One refinement step from zero with planar levels from 5 up is one float32 cycle (Sec. 3) and
+    the zero-mean projection: the oracle's float64 cycle within 1e-5 of the largest entry.  With
+    nu_post > 0 the coarse-grid correction of every planar level is added to the staged tiles of its
+    first post-smoothing step (coarse level planar at k = 6, compact below); nu_post = 0 takes the
+    separate prolongation kernel."""
+    from paper_1502_04070_gb300.solver import Solver, planar_step_variant, set_planar_step_variant
+    beta = 1e2
+    d = discs[k]
+    H = mg.Hierarchy(k + 1, beta, discs[:k + 1], coarse_level=coarse_level)
+    fn, gn = workloads.random_nodal(k, 70 + k)
+    F = d.load(fn, gn, project_g=True)
+    prm = mg.Params(gamma=gamma, nu_pre=nu[0], nu_post=nu[1])
+    x = H.project_mean(k, H.cycle(k, np.zeros(d.ndof), F, prm))
+    olds = {lv: planar_step_variant(lv + 1) for lv in range(5, k + 1)}
+    for lv in olds:
+        set_planar_step_variant(lv + 1, variant)
+    try:
+        S = Solver(k + 1, beta, precision="mixed", gamma=gamma, coarse_level=coarse_level, tma_level=5,
+                   nu_pre=nu[0], nu_post=nu[1])
+        f, g = S.load_vectors(dev(fn), dev(gn), project_g=True)
+        u, p, rep = S.solve(f, g, tol=1e-30, max_cycles=1)
+    finally:
+        for lv, v in olds.items():
+            set_planar_step_variant(lv + 1, v)
+    assert rep.cycles == 1
+    assert rel_err(d.to_vec(host(u), host(p)), x) < 1e-5
+    S.close()
+
+
 def test_planar_and_compact_hierarchies_agree(discs):
     """k = 7 (N = 256), manufactured-style random data: the solve with levels 5..7 planar and the
     solve with every level compact take the same steps, and both meet the tolerance in float64."""
