@@ -243,6 +243,12 @@ stokes_status stokes_stencil_rows(int levels, double beta, int cls, double* ma, 
  * interior lattice points (X, Y) in [1, 3]^2 (Y outer), then u_y, then p at the 3 x 3 vertices
  * (caller array of 729).  STOKES_ERR_BAD_ARG on bad input or a singular system. */
 stokes_status stokes_transfer_weights(double* w);
+/* Host-only: the embedding weights compiled into the planar float32 smoothing kernel, which adds
+ * the coarse-grid correction P x_c (Sec. 3) to the tiles of a planar level's first post-smoothing
+ * step: w[((o * 9 + L) * 4 + fb) * 4 + fa] for orientation o, coarse local node L and the fine
+ * lattice points (fa, fb) in {0..3}^2 that a coarse square owns (caller array of 288).
+ * STOKES_ERR_BAD_ARG if w is NULL. */
+stokes_status stokes_embed_weights(double* w);
 stokes_status stokes_coarse_inverse(double beta, double* inv);
 
 /* Host-only (no device work): tables for the L-shaped domain, the unit square without [1/2, 1]^2

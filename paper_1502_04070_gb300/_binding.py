@@ -102,6 +102,7 @@ SIGNATURES = {
     "stokes_get_timing": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D),
                                ctypes.POINTER(ctypes.c_longlong)]),
     "stokes_get_timing_fused": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong)]),
+    "stokes_embed_weights": (_I, [_P]),
     "stokes_kernel_launches": (ctypes.c_ulonglong, [_P]),
 }
 

@@ -1100,6 +1100,12 @@ stokes_status stokes_transfer_weights(double* w) {
     return STOKES_OK;
 }
 
+stokes_status stokes_embed_weights(double* w) {
+    if (!w) return STOKES_ERR_BAD_ARG;
+    embed_weights_table(w);
+    return STOKES_OK;
+}
+
 stokes_status stokes_coarse_inverse(double beta, double* inv) {
     if (!inv || !(beta >= 0.0) || !std::isfinite(beta)) return STOKES_ERR_BAD_ARG;
     return coarse_inverse(square_tables(), beta, inv) ? STOKES_OK : STOKES_ERR_BAD_ARG;

@@ -88,6 +88,8 @@ bool uzawa_tma_available();
 // the fused correction can be used: the tensor-map encoder is there and the kernel's compile-time
 // embedding table equals the host element code's transfer weights
 bool uzawa_tma_embed_available();
+// that compile-time table, w[((o * 9 + L) * 4 + fb) * 4 + fa] (host only)
+void embed_weights_table(double* w);
 // false when the environment sets STOKES_MG_FUSE_PROLONG=0 (read once per process): the planar
 // levels then prolongate with the separate kernel
 bool fuse_prolong_enabled();

@@ -2083,6 +2083,13 @@ bool launch_uzawa_tma(cudaStream_t s, int n, const OpCoef<float>& c, float tau, 
 
 bool uzawa_tma_embed_available() { return uzawa_tma_available() && embed_table_matches(); }
 
+void embed_weights_table(double* w) {
+    for (int o = 0; o < 2; ++o)
+        for (int L = 0; L < 9; ++L)
+            for (int fb = 0; fb < 4; ++fb)
+                for (int fa = 0; fa < 4; ++fa) w[((o * 9 + L) * 4 + fb) * 4 + fa] = embed_weight(o, L, fa, fb);
+}
+
 int tma_choice(int n) { return g_tma_choice[lvl(n)]; }
 bool tma_tuned(int n) { return g_tma_tuned[lvl(n)]; }
 bool set_tma_choice(int n, int v) {

@@ -156,6 +156,7 @@ def test_every_entry_point_rejects_bad_arguments_before_device_work():
         "stokes_residual_norm2_noalloc": (0, 1.0, buf, buf, buf, buf, ctypes.byref(d), None),
         "stokes_batch_solve": (None, None, None, None, None, 1e-8, 10, None, None),
         "stokes_transfer_weights": (None,),
+        "stokes_embed_weights": (None,),
         "stokes_coarse_inverse": (0.0, None),
     }
     for name, args in calls.items():

@@ -1,7 +1,8 @@
 """Host logic of the CUDA library, checked without a GPU: the stencil class of every cell and the
 node-stencil rows the kernels apply (C-ABI stokes_stencil_class, stokes_stencil_rows) against the
 oracle's mesh and its assembled matrices of eq. gen:bil:mv; the canonical embedding weights of the
-transfer kernels (stokes_transfer_weights) against the oracle's prolongation; and the level-0
+transfer kernels (stokes_transfer_weights) and of the coarse-grid correction compiled into the
+planar smoothing kernel (stokes_embed_weights) against the oracle's prolongation; and the level-0
 bordered inverse (stokes_coarse_inverse) against a dense inverse of the oracle's level-0 matrix.
 
 The class of a cell is read here from the oracle's triangle list: the orientation of each of its
@@ -137,6 +138,30 @@ def test_register_tile_structure_holds_on_every_level(lib, levels):
         assert lib.stokes_step_tables_match(levels, beta) == 0, (levels, beta)
     assert lib.stokes_step_tables_match(0, 1.0) != 0
     assert lib.stokes_step_tables_match(3, -1.0) != 0
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_fused_correction_table_equals_the_oracle_embedding(lib, discs, k):
+    """The embedding weights compiled into the planar smoothing kernel for the coarse-grid
+    correction it adds to its tiles (stokes_embed_weights, evaluated at compile time from the P2
+    basis) equal the oracle's prolongation at the 16 fine lattice points each coarse square owns."""
+    from oracle import transfer
+    w = np.zeros(2 * 9 * 4 * 4)
+    assert lib.stokes_embed_weights(w.ctypes.data_as(ctypes.c_void_p)) == 0
+    w = w.reshape(2, 9, 4, 4)
+    coarse, fine = discs[k], discs[k + 1]
+    P2 = transfer.prolongation_full(coarse, fine)[0].toarray()
+    nc, nf = coarse.n, fine.n
+    orient = square_orientations(coarse.mesh)
+    for a in range(nc):
+        for b in range(nc):
+            o = orient[a, b]
+            for L in range(9):
+                cc = (2 * b + L // 3) * (2 * nc + 1) + 2 * a + L % 3
+                for fb in range(4):
+                    for fa in range(4):
+                        ff = (4 * b + fb) * (2 * nf + 1) + 4 * a + fa
+                        assert abs(P2[ff, cc] - w[o, L, fb, fa]) <= 1e-14, (a, b, L, fa, fb)
 
 
 @pytest.mark.parametrize("k", [1, 2, 3])
